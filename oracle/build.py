@@ -11,7 +11,9 @@ LIB = os.path.join(HERE, "_liboracle.so")
 
 
 def build(force: bool = False) -> str:
-    if (not force and os.path.exists(LIB)
+    stamp = LIB + ".machine"
+    if (not force and os.path.exists(LIB) and os.path.exists(stamp)
+            and open(stamp).read().strip() == platform.machine()
             and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
         return LIB
     cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp",
@@ -20,6 +22,8 @@ def build(force: bool = False) -> str:
         cmd.append("-lquadmath")
     subprocess.check_call(cmd)
     os.replace(LIB + ".tmp", LIB)
+    with open(stamp, "w") as f:
+        f.write(platform.machine())
     return LIB
 
 

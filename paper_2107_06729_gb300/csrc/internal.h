@@ -1,0 +1,115 @@
+// internal.h -- definitions shared by the host and device parts of libmmx.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/mmx.h"
+
+#define MMX_MAXS 8
+#define MMX_MAXP 6
+#define MMX_NHIST (MMX_MAXP + 1)
+
+// Integrator state kept in device memory; kernels read it at launch and the
+// controller (last block of the last stage) updates it.  Everything the host
+// needs to resume a run lives here.
+struct DevState {
+    double t;        // start time t0 of the current attempt
+    double h;        // step of the current attempt (possibly clipped)
+    double h_ctrl;   // step proposed by the controller (Eq. 5)
+    double t_end;
+    double last_err;
+    double hist_t[MMX_NHIST];   // times of the stored exact fields (Eq. 6)
+    unsigned long long err_bits;  // running max of the error norm (bit pattern)
+    unsigned int blocks_done;
+    int cur;         // which magnetisation buffer holds m0
+    int fbase;       // slot of F_1 in the stage-derivative ring (FSAL rotation)
+    int f1_valid;    // F_1 for this t0 already computed
+    int hist_n;      // history slots assigned (<= p+1), incl. the current t0
+    int head;        // slot of the current t0
+    int done;
+    int status;
+    int clipped;     // current attempt lands exactly on t_end
+    int loop_more;   // last value handed to the graph's while condition
+    long long accepted, rejected, exact_evals, extrap_evals, forced, attempts;
+    long long acc_target;     // stop when accepted reaches this
+    long long attempt_limit;  // attempts allowed in the current run
+    long long run_attempts;
+    unsigned long long t_start_ns, time_limit_ns;
+};
+
+struct TabArgs {
+    int s, order, adaptive, fsal;
+    double a[MMX_MAXS];
+    double b[MMX_MAXS][MMX_MAXS];
+    double c[MMX_MAXS];
+    double e[MMX_MAXS];  // c - c_hat
+};
+
+struct PhysArgs {
+    int nx, ny, nz;
+    long long n;
+    double wx, wy, wz;   // 2A/(mu0 Ms d^2) per axis
+    double can;          // 2K/(mu0 Ms)
+    double ku[3];
+    double gp;           // gamma / (1 + alpha^2)
+    double alpha;
+    double msN00[3];     // Ms * N00 (self demag)
+    double H0[3], pulse[3], t_on, t_off;
+};
+
+struct CtlArgs {
+    int p;         // extrapolation order, -1 = full
+    int adaptive;  // controller enabled (integrator flag and tableau)
+    int nslots;    // stage-derivative slots
+    int prime;     // this graph primes the history: stop once primed
+    double tol, hmin, hmax, cmin, cmax, safety;
+};
+
+struct mmx_ctx {
+    mmx_mesh mesh;
+    mmx_material mat;
+    mmx_field field;
+    mmx_integrator integ;
+    int prec;  // mmx_precision
+    size_t esz;
+    cudaStream_t stream;
+    cudaStream_t cap_stream;
+    int nx, ny, nz;
+    long long n;
+    int Px, Py, Pz, Hy, Hz;
+    long long rows;  // 3 * ny * nz
+    double N00[3];
+    TabArgs tab;
+    PhysArgs ph;
+    CtlArgs ctl;
+    // device buffers (element type per precision)
+    void *m[2], *Y[2], *F, *G, *hist, *S, *K, *twx, *twy, *twz;
+    DevState *st;
+    DevState *h_st;  // pinned host mirror
+    // graphs: [0] main loop, [1] priming loop
+    cudaGraphExec_t gexec[2];
+    cudaGraph_t graph[2];
+    bool graph_ok[2];
+    bool use_graphs;
+    // profiling
+    bool profiling;
+    double prof_ms[MMX_NPROF];
+    long long prof_n[MMX_NPROF];
+    cudaEvent_t ev_a, ev_b;
+    long long launches;
+    long long launches_dev_at_sync;
+    std::string err;
+};
+
+// kernels.cu
+int mmxk_setup_buffers(mmx_ctx *c, const double *Kspec_host);
+// one exact Eq. 2 evaluation: XF -> YZ -> XI
+//   stage0: skip when F_1 is still valid (rejected retry / FSAL)
+//   src_mode 0: src, 1: m[cur];  dst_mode 0: dst, 1: history slot head
+//   self_src != NULL: subtract Ms N00 self_src (full field, as in mmx_demag)
+void mmxk_demag(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src_mode,
+                const void *src, int dst_mode, void *dst, const void *self_src);
+void mmxk_stage(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime_graph,
+                cudaGraphConditionalHandle cond, int use_cond);

@@ -1,0 +1,876 @@
+// kernels.cu -- sm_103a kernels of libmmx.
+//
+// Demag field, Eq. 2 (Sec. II), by the convolution theorem on the zero-padded
+// grid Px = 2nx, Py = 2ny (1 if ny == 1), Pz = 2nz (1 if nz == 1), in three
+// passes that keep each byte of the spectrum in HBM/L2 exactly twice:
+//   XF  real-to-complex along x of every (c, z, y) row.  Two rows travel as
+//       one complex sequence; the zero upper half of the padded row is pruned
+//       from the first radix stage.  The real values at kx = 0 and kx = nx
+//       are packed into one complex word, so a row of nx reals becomes nx
+//       complex words.  Output is transposed to S[kx][c][z][y] so that the
+//       next pass reads one contiguous block per kx.
+//   YZ  one CTA per kx column: forward y and z transforms (pruned), the
+//       6-component symmetric tensor multiply H = K M, inverse z and y
+//       transforms truncated to the nz x ny original cells.  The packed
+//       kx = 0 / kx = nx column is unpacked and repacked in Fourier space.
+//   XI  complex-to-real along x, truncated to nx outputs, 1/P and -Ms
+//       already folded into K.  Writes G = H + N00 Ms m (non-self field).
+// All transforms are Stockham radix-8/4/2 FFTs in shared memory
+// (twiddles from a table in global memory).
+//
+// LLG stages, Eq. 1 and 3-4: one fused kernel per stage builds the effective
+// field (6-point exchange Laplacian with free boundaries, uniaxial
+// anisotropy, Zeeman, demag exact or extrapolated by Eq. 6 minus the exact
+// self term), the Landau-Lifshitz torque, and the next stage input.  The
+// last stage forms the propagated and embedded solutions, renormalises,
+// reduces the error norm, and its last CTA runs the controller of Eq. 5.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+template <typename T> struct cx {
+    T x, y;
+};
+
+template <typename T> __device__ __forceinline__ cx<T> mk(T x, T y)
+{
+    cx<T> r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+template <typename T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b)
+{
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __device__ __forceinline__ cx<T> cscale(T s, cx<T> a) { return mk(s * a.x, s * a.y); }
+
+// multiply by -i (forward) or +i (inverse)
+template <typename T, bool INV> __device__ __forceinline__ cx<T> rot(cx<T> a)
+{
+    return INV ? mk(-a.y, a.x) : mk(a.y, -a.x);
+}
+
+template <typename T, bool INV> __device__ __forceinline__ void dft4(cx<T> &v0, cx<T> &v1, cx<T> &v2, cx<T> &v3)
+{
+    cx<T> a = cadd(v0, v2), b = csub(v0, v2), c = cadd(v1, v3), d = rot<T, INV>(csub(v1, v3));
+    v0 = cadd(a, c);
+    v1 = cadd(b, d);
+    v2 = csub(a, c);
+    v3 = csub(b, d);
+}
+
+template <typename T, int R, bool INV> struct Dft;
+template <typename T, bool INV> struct Dft<T, 2, INV> {
+    static __device__ __forceinline__ void run(cx<T> *v)
+    {
+        cx<T> a = v[0];
+        v[0] = cadd(a, v[1]);
+        v[1] = csub(a, v[1]);
+    }
+};
+template <typename T, bool INV> struct Dft<T, 4, INV> {
+    static __device__ __forceinline__ void run(cx<T> *v) { dft4<T, INV>(v[0], v[1], v[2], v[3]); }
+};
+template <typename T, bool INV> struct Dft<T, 8, INV> {
+    static __device__ __forceinline__ void run(cx<T> *v)
+    {
+        cx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+        cx<T> o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+        dft4<T, INV>(e0, e1, e2, e3);
+        dft4<T, INV>(o0, o1, o2, o3);
+        const T r = (T)0.70710678118654752440084436210485;  // sqrt(1/2)
+        cx<T> t1, t2, t3;
+        if (!INV) {
+            t1 = mk(r * (o1.x + o1.y), r * (o1.y - o1.x));
+            t2 = mk(o2.y, -o2.x);
+            t3 = mk(r * (o3.y - o3.x), -r * (o3.x + o3.y));
+        } else {
+            t1 = mk(r * (o1.x - o1.y), r * (o1.x + o1.y));
+            t2 = mk(-o2.y, o2.x);
+            t3 = mk(-r * (o3.x + o3.y), r * (o3.x - o3.y));
+        }
+        v[0] = cadd(e0, o0);
+        v[4] = csub(e0, o0);
+        v[1] = cadd(e1, t1);
+        v[5] = csub(e1, t1);
+        v[2] = cadd(e2, t2);
+        v[6] = csub(e2, t2);
+        v[3] = cadd(e3, t3);
+        v[7] = csub(e3, t3);
+    }
+};
+
+// A batch of `count` transforms of length L held in shared memory; transform
+// tr starts at (tr >> lg_lo) * s_hi + (tr & (2^lg_lo - 1)) * s_lo and its
+// elements are es apart.
+struct FftShape {
+    int L, count, lg_lo, s_hi, s_lo, es;
+};
+
+// One Stockham stage (radix R, Ns = product of the previous radices).  All
+// threads of the CTA take part; loads of a window of whole transforms
+// complete before any store, so the stage runs in place.
+template <typename T, int R, bool INV, int ITEMS>
+__device__ __forceinline__ void fft_stage(cx<T> *buf, const FftShape &f, int Ns, const cx<T> *__restrict__ tw,
+                                          bool prune, bool trunc)
+{
+    const int per = f.L / R;
+    const int lgper = __ffs(per) - 1;
+    const int total = f.count * per;
+    const int W = blockDim.x * ITEMS;
+    const int tstride = f.L / (Ns * R);
+    const int half = f.L >> 1;
+    const int lomask = (1 << f.lg_lo) - 1;
+    for (int w0 = 0; w0 < total; w0 += W) {
+        cx<T> v[ITEMS][R];
+        int off[ITEMS], jj[ITEMS];
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) {
+            const int item = w0 + it * blockDim.x + threadIdx.x;
+            off[it] = -1;
+            jj[it] = 0;
+            if (item < total) {
+                const int tr = item >> lgper, j = item & (per - 1);
+                const int o = (tr >> f.lg_lo) * f.s_hi + (tr & lomask) * f.s_lo;
+                off[it] = o;
+                jj[it] = j;
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    v[it][r] = (prune && r >= R / 2) ? mk<T>(0, 0) : buf[o + (j + r * per) * f.es];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) {
+            if (off[it] < 0) continue;
+            const int j = jj[it], k = j & (Ns - 1);
+            if (Ns > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    cx<T> w = tw[r * k * tstride];
+                    if (INV) w.y = -w.y;
+                    v[it][r] = cmul(v[it][r], w);
+                }
+            }
+            Dft<T, R, INV>::run(v[it]);
+            const int d = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int pos = d + r * Ns;
+                if (!trunc || pos < half) buf[off[it] + pos * f.es] = v[it][r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Full transform: radix 8 while possible (16 as 4 x 4), then 4 or 2.
+// prune: the upper half of every input is zero and is not read.
+// trunc: only the lower half of the outputs is written.
+template <typename T, bool INV, int ITEMS>
+__device__ void fft_smem(cx<T> *buf, const FftShape &f, const cx<T> *__restrict__ tw, bool prune, bool trunc)
+{
+    int Ns = 1, rem = f.L;
+    bool first = true;
+    while (rem > 1) {
+        int R = (rem % 8 == 0 && rem != 16) ? 8 : (rem % 4 == 0 ? 4 : 2);
+        bool last = (rem == R);
+        if (R == 8)
+            fft_stage<T, 8, INV, ITEMS>(buf, f, Ns, tw, first && prune, last && trunc);
+        else if (R == 4)
+            fft_stage<T, 4, INV, ITEMS>(buf, f, Ns, tw, first && prune, last && trunc);
+        else
+            fft_stage<T, 2, INV, ITEMS>(buf, f, Ns, tw, first && prune, last && trunc);
+        Ns *= R;
+        rem /= R;
+        first = false;
+    }
+}
+
+__device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
+
+// ------------------------------------------------------------------ XF / XI
+template <typename T> struct XArgs {
+    const T *src;        // src_mode 0
+    const T *msrc0, *msrc1;  // src_mode 1: m[cur]
+    T *dst;              // dst_mode 0
+    T *hist;             // dst_mode 1: hist + head * 3n
+    const T *self_src;   // optional: subtract Ms N00 self_src
+    cx<T> *S;
+    const cx<T> *tw;
+    DevState *st;
+    long long rows, n;
+    int nx, trows, stage0, src_mode, dst_mode, plane;  // plane = ny*nz
+    double msN00[3];
+};
+
+constexpr int X_THREADS = 128;
+constexpr int X_ITEMS = 4;
+constexpr int YZ_THREADS = 256;
+constexpr int YZ_ITEMS = 2;
+
+template <typename T>
+__global__ void __launch_bounds__(X_THREADS) k_xf(const XArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<T> *sm = reinterpret_cast<cx<T> *>(smraw);
+    if (a.st) {
+        if (a.st->done) return;
+        if (a.stage0 && a.st->f1_valid) return;
+    }
+    const T *src = a.src_mode == 1 ? (a.st->cur ? a.msrc1 : a.msrc0) : a.src;
+    const int nx = a.nx, Px = 2 * nx, lgnx = ilog2(nx);
+    const int np = (a.trows + 1) >> 1;
+    const long long R = a.rows, r0 = (long long)blockIdx.x * a.trows;
+    for (int idx = threadIdx.x; idx < np * nx; idx += blockDim.x) {
+        const int p = idx >> lgnx, x = idx & (nx - 1);
+        const long long ra = r0 + 2 * p, rb = ra + 1;
+        T va = (2 * p < a.trows && ra < R) ? src[ra * nx + x] : (T)0;
+        T vb = (2 * p + 1 < a.trows && rb < R) ? src[rb * nx + x] : (T)0;
+        sm[p * Px + x] = mk(va, vb);
+    }
+    __syncthreads();
+    FftShape f{Px, np, 0, Px, 0, 1};
+    fft_smem<T, false, X_ITEMS>(sm, f, a.tw, true, false);
+    // separate the two real rows and pack kx = 0 with kx = nx
+    const int T_ = a.trows;
+    for (int idx = threadIdx.x; idx < nx * T_; idx += blockDim.x) {
+        const int k = idx / T_, t = idx - k * T_;
+        const long long r = r0 + t;
+        if (r >= R) continue;
+        const cx<T> *z = sm + (t >> 1) * Px;
+        cx<T> v;
+        if (k == 0) {
+            const cx<T> z0 = z[0], zn = z[nx];
+            v = (t & 1) ? mk(z0.y, zn.y) : mk(z0.x, zn.x);
+        } else {
+            const cx<T> zk = z[k], zm = z[Px - k];
+            const T hlf = (T)0.5;
+            v = (t & 1) ? mk(hlf * (zk.y + zm.y), hlf * (zm.x - zk.x)) : mk(hlf * (zk.x + zm.x), hlf * (zk.y - zm.y));
+        }
+        a.S[(long long)k * R + r] = v;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(X_THREADS) k_xi(const XArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<T> *sm = reinterpret_cast<cx<T> *>(smraw);
+    int head = 0;
+    if (a.st) {
+        if (a.st->done) return;
+        if (a.stage0 && a.st->f1_valid) return;
+        head = a.st->head;
+    }
+    const int nx = a.nx, Px = 2 * nx;
+    const int np = (a.trows + 1) >> 1;
+    const long long R = a.rows, r0 = (long long)blockIdx.x * a.trows;
+    for (int idx = threadIdx.x; idx < np * nx; idx += blockDim.x) {
+        const int k = idx / np, p = idx - k * np;
+        const long long ra = r0 + 2 * p, rb = ra + 1;
+        const cx<T> zero = mk<T>(0, 0);
+        const cx<T> va = (2 * p < a.trows && ra < R) ? a.S[(long long)k * R + ra] : zero;
+        const cx<T> vb = (2 * p + 1 < a.trows && rb < R) ? a.S[(long long)k * R + rb] : zero;
+        cx<T> *z = sm + p * Px;
+        if (k == 0) {
+            z[0] = mk(va.x, vb.x);
+            z[nx] = mk(va.y, vb.y);
+        } else {
+            z[k] = mk(va.x - vb.y, va.y + vb.x);
+            z[Px - k] = mk(va.x + vb.y, vb.x - va.y);
+        }
+    }
+    __syncthreads();
+    FftShape f{Px, np, 0, Px, 0, 1};
+    fft_smem<T, true, X_ITEMS>(sm, f, a.tw, false, true);
+    T *out = a.dst_mode == 1 ? a.hist + (size_t)head * 3 * a.n : a.dst;
+    const int T_ = a.trows, lgnx = ilog2(nx);
+    for (int idx = threadIdx.x; idx < T_ * nx; idx += blockDim.x) {
+        const int t = idx >> lgnx, x = idx & (nx - 1);
+        const long long r = r0 + t;
+        if (r >= R) continue;
+        const cx<T> z = sm[(t >> 1) * Px + x];
+        T v = (t & 1) ? z.y : z.x;
+        if (a.self_src) {
+            const int c = (int)(r / a.plane);
+            v -= (T)a.msN00[c] * a.self_src[r * nx + x];
+        }
+        out[r * nx + x] = v;
+    }
+    if (a.st && blockIdx.x == 0 && threadIdx.x == 0) a.st->exact_evals++;
+}
+
+// ---------------------------------------------------------------------- YZ
+template <typename T> struct YZArgs {
+    cx<T> *S;
+    const T *K;  // [(kx*Hz + kz)*Hy + ky][6]
+    const cx<T> *twy, *twz;
+    DevState *st;
+    long long rows;
+    int nx, ny, nz, Py, Pz, Hy, Hz, stage0;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_K(const T *K, int kx, int Hy, int Hz, int Py, int Pz, int ky, int kz, T k6[6])
+{
+    const bool fy = ky > (Py >> 1), fz = kz > (Pz >> 1);
+    const int y = fy ? Py - ky : ky, z = fz ? Pz - kz : kz;
+    const T *p = K + ((size_t)((size_t)kx * Hz + z) * Hy + y) * 6;
+    const T sy = fy ? (T)-1 : (T)1, sz = fz ? (T)-1 : (T)1;
+    k6[0] = p[0];
+    k6[1] = p[1];
+    k6[2] = p[2];
+    k6[3] = sy * p[3];
+    k6[4] = sz * p[4];
+    k6[5] = sy * sz * p[5];
+}
+
+template <typename T>
+__device__ __forceinline__ void apply_K(const T k[6], cx<T> mx, cx<T> my, cx<T> mz, cx<T> &hx, cx<T> &hy, cx<T> &hz)
+{
+    hx = mk(k[0] * mx.x + k[3] * my.x + k[4] * mz.x, k[0] * mx.y + k[3] * my.y + k[4] * mz.y);
+    hy = mk(k[3] * mx.x + k[1] * my.x + k[5] * mz.x, k[3] * mx.y + k[1] * my.y + k[5] * mz.y);
+    hz = mk(k[4] * mx.x + k[5] * my.x + k[2] * mz.x, k[4] * mx.y + k[5] * my.y + k[2] * mz.y);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(YZ_THREADS) k_yz(const YZArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<T> *B = reinterpret_cast<cx<T> *>(smraw);
+    if (a.st) {
+        if (a.st->done) return;
+        if (a.stage0 && a.st->f1_valid) return;
+    }
+    const int kx = blockIdx.x;
+    const int ny = a.ny, nz = a.nz, Py = a.Py, Pz = a.Pz;
+    const int plane = Py * Pz, lgny = ilog2(ny), lgnz = ilog2(nz), lgPy = ilog2(Py);
+    cx<T> *S = a.S + (size_t)kx * a.rows;
+    const int rows = (int)a.rows;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const int y = r & (ny - 1), cz = r >> lgny, z = cz & (nz - 1), c = cz >> lgnz;
+        B[c * plane + z * Py + y] = S[r];
+    }
+    __syncthreads();
+    const FftShape fy{Py, 3 * nz, lgnz, plane, Py, 1};
+    const FftShape fz{Pz, 3 * Py, lgPy, plane, 1, Py};
+    if (Py > 1) fft_smem<T, false, YZ_ITEMS>(B, fy, a.twy, true, false);
+    if (Pz > 1) fft_smem<T, false, YZ_ITEMS>(B, fz, a.twz, true, false);
+
+    // Fourier-space tensor multiply (Eq. 2): H = K M, K real symmetric
+    if (kx != 0) {
+        for (int q = threadIdx.x; q < plane; q += blockDim.x) {
+            const int ky = q & (Py - 1), kz = q >> lgPy;
+            T k6[6];
+            load_K(a.K, kx, a.Hy, a.Hz, Py, Pz, ky, kz, k6);
+            cx<T> hx, hy, hz;
+            apply_K(k6, B[q], B[plane + q], B[2 * plane + q], hx, hy, hz);
+            B[q] = hx;
+            B[plane + q] = hy;
+            B[2 * plane + q] = hz;
+        }
+    } else {
+        // packed column u = X(kx=0) + i X(kx=nx), both real along x:
+        // V(k) = P U(k) + Q conj(U(-k)), P = (K0 + KN)/2, Q = (K0 - KN)/2
+        for (int q = threadIdx.x; q < plane; q += blockDim.x) {
+            const int ky = q & (Py - 1), kz = q >> lgPy;
+            const int qm = ((Pz - kz) & (Pz - 1)) * Py + ((Py - ky) & (Py - 1));
+            if (q > qm) continue;
+            T k0[6], kn[6], P[6], Q[6];
+            load_K(a.K, 0, a.Hy, a.Hz, Py, Pz, ky, kz, k0);
+            load_K(a.K, a.nx, a.Hy, a.Hz, Py, Pz, ky, kz, kn);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                P[i] = (T)0.5 * (k0[i] + kn[i]);
+                Q[i] = (T)0.5 * (k0[i] - kn[i]);
+            }
+            const cx<T> ux = B[q], uy = B[plane + q], uz = B[2 * plane + q];
+            const cx<T> vx = B[qm], vy = B[plane + qm], vz = B[2 * plane + qm];
+            const cx<T> cvx = mk(vx.x, -vx.y), cvy = mk(vy.x, -vy.y), cvz = mk(vz.x, -vz.y);
+            cx<T> a1, a2, a3, b1, b2, b3;
+            apply_K(P, ux, uy, uz, a1, a2, a3);
+            apply_K(Q, cvx, cvy, cvz, b1, b2, b3);
+            B[q] = cadd(a1, b1);
+            B[plane + q] = cadd(a2, b2);
+            B[2 * plane + q] = cadd(a3, b3);
+            if (qm != q) {
+                const cx<T> cux = mk(ux.x, -ux.y), cuy = mk(uy.x, -uy.y), cuz = mk(uz.x, -uz.y);
+                apply_K(P, vx, vy, vz, a1, a2, a3);
+                apply_K(Q, cux, cuy, cuz, b1, b2, b3);
+                B[qm] = cadd(a1, b1);
+                B[plane + qm] = cadd(a2, b2);
+                B[2 * plane + qm] = cadd(a3, b3);
+            }
+        }
+    }
+    __syncthreads();
+    if (Pz > 1) fft_smem<T, true, YZ_ITEMS>(B, fz, a.twz, false, true);
+    if (Py > 1) fft_smem<T, true, YZ_ITEMS>(B, fy, a.twy, false, true);
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const int y = r & (ny - 1), cz = r >> lgny, z = cz & (nz - 1), c = cz >> lgnz;
+        S[r] = B[c * plane + z * Py + y];
+    }
+}
+
+// ------------------------------------------------------------------ stages
+template <typename T> struct StageArgs {
+    T *m0, *m1, *Y0, *Y1, *F, *G, *hist;
+    DevState *st;
+    TabArgs tab;
+    PhysArgs ph;
+    CtlArgs ctl;
+    int k, extrap, last, use_cond;
+    cudaGraphConditionalHandle cond;
+};
+
+constexpr int ST_THREADS = 256;
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <typename T> __device__ void controller(const StageArgs<T> &a)
+{
+    DevState *st = a.st;
+    const double e = __longlong_as_double((long long)atomicExch(&st->err_bits, 0ULL));
+    st->blocks_done = 0;
+    st->last_err = e;
+    st->attempts++;
+    st->run_attempts++;
+    const double h = st->h;
+    int more = 0;
+    if (!(e <= 1.7976931348623157e308)) {  // NaN or Inf
+        st->status = MMX_ERR_NONFINITE;
+        st->done = 1;
+    } else {
+        const bool adaptive = a.ctl.adaptive != 0;
+        bool accept = true, forced = false;
+        if (adaptive && e > a.ctl.tol) {
+            if (h <= a.ctl.hmin || st->h_ctrl <= a.ctl.hmin)
+                forced = true;
+            else
+                accept = false;
+        }
+        double hnew = st->h_ctrl;
+        if (adaptive) {
+            double cf = a.ctl.cmax;
+            if (e > 0) {
+                cf = pow(a.ctl.safety * a.ctl.tol / e, 1.0 / (a.tab.order + 1));
+                cf = fmin(fmax(cf, a.ctl.cmin), a.ctl.cmax);
+            }
+            hnew = fmin(fmax(h * cf, a.ctl.hmin), a.ctl.hmax);
+        }
+        if (accept) {
+            st->t = st->clipped ? st->t_end : st->t + h;
+            if (!st->clipped) st->h_ctrl = hnew;
+            st->cur ^= 1;
+            st->accepted++;
+            if (forced) st->forced++;
+            if (a.tab.fsal && a.ctl.p < 0) {
+                st->fbase = (st->fbase + a.tab.s - 1) % a.ctl.nslots;
+                st->f1_valid = 1;
+            } else {
+                st->f1_valid = 0;
+            }
+            if (a.ctl.p >= 0) {
+                const int np1 = a.ctl.p + 1;
+                st->head = (st->head + 1) % np1;
+                st->hist_t[st->head] = st->t;
+                if (st->hist_n < np1) st->hist_n++;
+            }
+        } else {
+            st->h_ctrl = hnew;
+            st->rejected++;
+        }
+        bool done = (st->t >= st->t_end) || (st->accepted >= st->acc_target);
+        if (!done && st->run_attempts >= st->attempt_limit) {
+            st->status = MMX_ERR_TIMEOUT;
+            done = true;
+        }
+        const unsigned long long now = global_ns();
+        if (st->t_start_ns == 0ULL) st->t_start_ns = now;
+        if (!done && st->time_limit_ns && now - st->t_start_ns > st->time_limit_ns) {
+            st->status = MMX_ERR_TIMEOUT;
+            done = true;
+        }
+        st->done = done ? 1 : 0;
+        if (!done) {
+            const double rem = st->t_end - st->t;
+            const double hh = st->h_ctrl;
+            const int cl = (hh * (1.0 + 1e-9) >= rem) ? 1 : 0;
+            st->h = cl ? rem : hh;
+            st->clipped = cl;
+        }
+        more = (!done && !(a.ctl.prime && st->hist_n >= a.ctl.p + 1)) ? 1 : 0;
+    }
+    st->loop_more = more;
+    if (a.use_cond) cudaGraphSetConditional(a.cond, (unsigned)more);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(ST_THREADS) k_stage(const StageArgs<T> a)
+{
+    __shared__ double s_w[MMX_NHIST];
+    __shared__ double s_H[3];
+    __shared__ double s_red[ST_THREADS / 32];
+    __shared__ int s_last;
+    DevState *st = a.st;
+    if (st->done) {
+        if (a.last && a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
+        return;
+    }
+    const int k = a.k;
+    const long long n = a.ph.n;
+    const int cur = st->cur, fbase = st->fbase, head = st->head;
+    const double h = st->h, t0 = st->t;
+    const bool f1v = (k == 0) && st->f1_valid;
+    const bool ext = a.extrap && k > 0;
+    const int np1 = a.ctl.p + 1;
+    if (threadIdx.x == 0) {
+        const double tk = t0 + a.tab.a[k] * h;
+        const bool on = (tk >= a.ph.t_on) && (tk < a.ph.t_off);
+        for (int c = 0; c < 3; ++c) s_H[c] = a.ph.H0[c] + (on ? a.ph.pulse[c] : 0.0);
+        if (ext) {
+            // Eq. 6: Lagrange basis at tau = a_k h over the stored times
+            const double tau = a.tab.a[k] * h;
+            for (int j = 0; j < np1; ++j) {
+                const double tj = st->hist_t[j] - t0;
+                double w = 1.0;
+                for (int l = 0; l < np1; ++l)
+                    if (l != j) {
+                        const double tl = st->hist_t[l] - t0;
+                        w *= (tau - tl) / (tj - tl);
+                    }
+                s_w[j] = w;
+            }
+        }
+    }
+    __syncthreads();
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    const int ns = a.ctl.nslots;
+    const size_t fstride = (size_t)3 * n;
+    T *Fk = a.F + (size_t)((fbase + k) % ns) * fstride;
+    const T *m0 = cur ? a.m1 : a.m0;
+    T f[3] = {0, 0, 0};
+    if (valid) {
+        if (f1v) {
+            for (int c = 0; c < 3; ++c) f[c] = Fk[c * n + i];
+        } else {
+            const T *Y = (k == 0) ? m0 : ((k & 1) ? a.Y1 : a.Y0);
+            const int nx = a.ph.nx, ny = a.ph.ny, nz = a.ph.nz;
+            const int x = (int)(i % nx);
+            const long long rest = i / nx;
+            const int y = (int)(rest % ny), z = (int)(rest / ny);
+            const long long sy = nx, sz = (long long)nx * ny;
+            const long long xm = x > 0 ? i - 1 : i, xp = x < nx - 1 ? i + 1 : i;
+            const long long ym = y > 0 ? i - sy : i, yp = y < ny - 1 ? i + sy : i;
+            const long long zm = z > 0 ? i - sz : i, zp = z < nz - 1 ? i + sz : i;
+            const T wx = (T)a.ph.wx, wy = (T)a.ph.wy, wz = (T)a.ph.wz;
+            T m[3], H[3];
+            for (int c = 0; c < 3; ++c) {
+                const T *Yc = Y + c * n;
+                const T cen = Yc[i];
+                m[c] = cen;
+                H[c] = wx * (Yc[xp] - 2 * cen + Yc[xm]) + wy * (Yc[yp] - 2 * cen + Yc[ym]) +
+                       wz * (Yc[zp] - 2 * cen + Yc[zm]);
+            }
+            const T mu = (T)(m[0] * (T)a.ph.ku[0] + m[1] * (T)a.ph.ku[1] + m[2] * (T)a.ph.ku[2]);
+            T g[3] = {0, 0, 0};
+            if (ext) {
+                for (int j = 0; j < np1; ++j) {
+                    const T *Gj = a.hist + (size_t)j * fstride;
+                    const T w = (T)s_w[j];
+                    for (int c = 0; c < 3; ++c) g[c] += w * Gj[c * n + i];
+                }
+            } else {
+                const T *Gk = (k == 0 && a.ctl.p >= 0) ? a.hist + (size_t)head * fstride : a.G;
+                for (int c = 0; c < 3; ++c) g[c] = Gk[c * n + i];
+            }
+            for (int c = 0; c < 3; ++c)
+                H[c] += (T)a.ph.can * mu * (T)a.ph.ku[c] + g[c] - (T)a.ph.msN00[c] * m[c] + (T)s_H[c];
+            // Eq. 1 in Landau-Lifshitz form: F = -gp (m x H + alpha m x (m x H))
+            const T cxh0 = m[1] * H[2] - m[2] * H[1];
+            const T cxh1 = m[2] * H[0] - m[0] * H[2];
+            const T cxh2 = m[0] * H[1] - m[1] * H[0];
+            const T dd0 = m[1] * cxh2 - m[2] * cxh1;
+            const T dd1 = m[2] * cxh0 - m[0] * cxh2;
+            const T dd2 = m[0] * cxh1 - m[1] * cxh0;
+            const T gp = (T)a.ph.gp, al = (T)a.ph.alpha;
+            f[0] = -gp * (cxh0 + al * dd0);
+            f[1] = -gp * (cxh1 + al * dd1);
+            f[2] = -gp * (cxh2 + al * dd2);
+            for (int c = 0; c < 3; ++c) Fk[c * n + i] = f[c];
+        }
+    }
+    if (!a.last) {
+        // Eq. 4: Y_{k+1} = m0 + h sum_{l<=k} b_{k+1,l} F_l
+        if (valid) {
+            T *Yn = ((k + 1) & 1) ? a.Y1 : a.Y0;
+            const double *brow = a.tab.b[k + 1];
+            for (int c = 0; c < 3; ++c) {
+                T acc = m0[c * n + i];
+                for (int l = 0; l < k; ++l) {
+                    if (brow[l] == 0.0) continue;
+                    const T *Fl = a.F + (size_t)((fbase + l) % ns) * fstride;
+                    acc += (T)(h * brow[l]) * Fl[c * n + i];
+                }
+                acc += (T)(h * brow[k]) * f[c];
+                Yn[c * n + i] = acc;
+            }
+        }
+        if (ext && blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
+        return;
+    }
+    // Eq. 3: propagated solution, embedded difference, renormalisation
+    double err = 0.0;
+    if (valid) {
+        T M[3], E[3];
+        const int s = a.tab.s;
+        for (int c = 0; c < 3; ++c) {
+            T acc = m0[c * n + i], ea = 0;
+            for (int l = 0; l < s - 1; ++l) {
+                const double cl = a.tab.c[l], el = a.tab.e[l];
+                if (cl == 0.0 && el == 0.0) continue;
+                const T *Fl = a.F + (size_t)((fbase + l) % ns) * fstride;
+                const T v = Fl[c * n + i];
+                acc += (T)(h * cl) * v;
+                ea += (T)(h * el) * v;
+            }
+            acc += (T)(h * a.tab.c[s - 1]) * f[c];
+            ea += (T)(h * a.tab.e[s - 1]) * f[c];
+            M[c] = acc;
+            E[c] = ea;
+        }
+        const T r = sqrt(M[0] * M[0] + M[1] * M[1] + M[2] * M[2]);
+        T *mo = cur ? a.m0 : a.m1;
+        for (int c = 0; c < 3; ++c) mo[c * n + i] = M[c] / r;
+        err = (double)sqrt(E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
+        if (!(err <= 1.7976931348623157e308)) err = INFINITY;
+        if (!(r == r) || r == (T)0) err = INFINITY;
+    }
+    if (ext && blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
+    for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = err;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, s_red[w]);
+        atomicMax(&st->err_bits, (unsigned long long)__double_as_longlong(mx));
+        __threadfence();
+        const unsigned prev = atomicAdd(&st->blocks_done, 1u);
+        s_last = (prev == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        controller(a);
+    }
+}
+
+// ----------------------------------------------------------- host helpers
+template <typename T> size_t x_smem(const mmx_ctx *c, int trows)
+{
+    return (size_t)((trows + 1) / 2) * 2 * c->nx * sizeof(cx<T>);
+}
+template <typename T> size_t yz_smem(const mmx_ctx *c) { return (size_t)3 * c->Py * c->Pz * sizeof(cx<T>); }
+
+int pick_trows(const mmx_ctx *c)
+{
+    // rows per CTA for the x passes: enough CTAs to cover the SMs twice
+    long long rows = c->rows;
+    int tr = 8;
+    while (tr > 2 && (rows + tr - 1) / tr < 2 * 152) tr >>= 1;
+    return tr;
+}
+
+template <typename T>
+void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src_mode, const void *src, int dst_mode,
+             void *dst, const void *self_src)
+{
+    const int trows = pick_trows(c);
+    XArgs<T> xa{};
+    xa.src = (const T *)src;
+    xa.msrc0 = (const T *)c->m[0];
+    xa.msrc1 = (const T *)c->m[1];
+    xa.dst = (T *)dst;
+    xa.hist = (T *)c->hist;
+    xa.self_src = (const T *)self_src;
+    xa.S = (cx<T> *)c->S;
+    xa.tw = (const cx<T> *)c->twx;
+    xa.st = const_cast<DevState *>(st);
+    xa.rows = c->rows;
+    xa.n = c->n;
+    xa.nx = c->nx;
+    xa.trows = trows;
+    xa.stage0 = stage0;
+    xa.src_mode = src_mode;
+    xa.dst_mode = dst_mode;
+    xa.plane = c->ny * c->nz;
+    for (int i = 0; i < 3; ++i) xa.msN00[i] = c->ph.msN00[i];
+    const int xgrid = (int)((c->rows + trows - 1) / trows);
+    const size_t xs = x_smem<T>(c, trows);
+
+    YZArgs<T> ya{};
+    ya.S = (cx<T> *)c->S;
+    ya.K = (const T *)c->K;
+    ya.twy = (const cx<T> *)c->twy;
+    ya.twz = (const cx<T> *)c->twz;
+    ya.st = const_cast<DevState *>(st);
+    ya.rows = c->rows;
+    ya.nx = c->nx;
+    ya.ny = c->ny;
+    ya.nz = c->nz;
+    ya.Py = c->Py;
+    ya.Pz = c->Pz;
+    ya.Hy = c->Hy;
+    ya.Hz = c->Hz;
+    ya.stage0 = stage0;
+    const size_t ys = yz_smem<T>(c);
+
+    const bool prof = c->profiling;
+    auto timed = [&](int cls, auto launch) {
+        if (prof) cudaEventRecord(c->ev_a, s);
+        launch();
+        c->launches++;
+        if (prof) {
+            cudaEventRecord(c->ev_b, s);
+            cudaEventSynchronize(c->ev_b);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, c->ev_a, c->ev_b);
+            c->prof_ms[cls] += ms;
+            c->prof_n[cls]++;
+        }
+    };
+    timed(0, [&] { k_xf<T><<<xgrid, X_THREADS, xs, s>>>(xa); });
+    timed(1, [&] { k_yz<T><<<c->nx, YZ_THREADS, ys, s>>>(ya); });
+    timed(2, [&] { k_xi<T><<<xgrid, X_THREADS, xs, s>>>(xa); });
+}
+
+template <typename T>
+void stage_t(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime, cudaGraphConditionalHandle cond, int use_cond)
+{
+    StageArgs<T> a{};
+    a.m0 = (T *)c->m[0];
+    a.m1 = (T *)c->m[1];
+    a.Y0 = (T *)c->Y[0];
+    a.Y1 = (T *)c->Y[1];
+    a.F = (T *)c->F;
+    a.G = (T *)c->G;
+    a.hist = (T *)c->hist;
+    a.st = c->st;
+    a.tab = c->tab;
+    a.ph = c->ph;
+    a.ctl = c->ctl;
+    a.ctl.prime = prime;
+    a.k = k;
+    a.extrap = extrap;
+    a.last = (k == c->tab.s - 1);
+    a.use_cond = use_cond;
+    a.cond = cond;
+    const int grid = (int)((c->n + ST_THREADS - 1) / ST_THREADS);
+    const int cls = a.last ? 4 : 3;
+    if (c->profiling) cudaEventRecord(c->ev_a, s);
+    k_stage<T><<<grid, ST_THREADS, 0, s>>>(a);
+    c->launches++;
+    if (c->profiling) {
+        cudaEventRecord(c->ev_b, s);
+        cudaEventSynchronize(c->ev_b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev_a, c->ev_b);
+        c->prof_ms[cls] += ms;
+        c->prof_n[cls]++;
+    }
+}
+
+template <typename T> void twiddles(int L, std::vector<cx<T>> &out)
+{
+    out.resize(L > 0 ? L : 1);
+    for (int m = 0; m < L; ++m) {
+        if ((4 * m) % L == 0) {
+            static const int cq[4] = {1, 0, -1, 0}, sq[4] = {0, 1, 0, -1};
+            const int q = ((4 * m) / L) & 3;
+            out[m].x = (T)cq[q];
+            out[m].y = (T)-sq[q];
+        } else {
+            const long double ang = 2.0L * 3.141592653589793238462643383279502884L * (long double)m / (long double)L;
+            out[m].x = (T)cosl(ang);
+            out[m].y = (T)-sinl(ang);
+        }
+    }
+}
+
+template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
+{
+    const size_t nK = (size_t)(c->nx + 1) * c->Hz * c->Hy * 6;
+    std::vector<T> Kh(nK);
+    for (size_t i = 0; i < nK; ++i) Kh[i] = (T)Kspec[i];
+    if (cudaMemcpy(c->K, Kh.data(), nK * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
+    std::vector<cx<T>> tw;
+    twiddles<T>(c->Px, tw);
+    if (cudaMemcpy(c->twx, tw.data(), c->Px * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
+    twiddles<T>(c->Py, tw);
+    if (cudaMemcpy(c->twy, tw.data(), c->Py * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
+    twiddles<T>(c->Pz, tw);
+    if (cudaMemcpy(c->twz, tw.data(), c->Pz * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
+    const int trows = pick_trows(c);
+    const size_t xs = x_smem<T>(c, trows), ys = yz_smem<T>(c);
+    if (xs > 48 * 1024) {
+        if (cudaFuncSetAttribute(k_xf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs) != cudaSuccess)
+            return MMX_ERR_CUDA;
+        if (cudaFuncSetAttribute(k_xi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs) != cudaSuccess)
+            return MMX_ERR_CUDA;
+    }
+    if (ys > 48 * 1024) {
+        if (cudaFuncSetAttribute(k_yz<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ys) != cudaSuccess)
+            return MMX_ERR_CUDA;
+    }
+    return 0;
+}
+
+}  // namespace
+
+size_t mmxk_yz_smem_bytes(const mmx_ctx *c)
+{
+    return c->prec == MMX_FP64 ? yz_smem<double>(c) : yz_smem<float>(c);
+}
+size_t mmxk_x_smem_bytes(const mmx_ctx *c)
+{
+    return c->prec == MMX_FP64 ? x_smem<double>(c, pick_trows(c)) : x_smem<float>(c, pick_trows(c));
+}
+
+int mmxk_setup_buffers(mmx_ctx *c, const double *Kspec_host)
+{
+    return c->prec == MMX_FP64 ? setup_t<double>(c, Kspec_host) : setup_t<float>(c, Kspec_host);
+}
+
+void mmxk_demag(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src_mode, const void *src,
+                int dst_mode, void *dst, const void *self_src)
+{
+    if (c->prec == MMX_FP64)
+        demag_t<double>(c, s, st, stage0, src_mode, src, dst_mode, dst, self_src);
+    else
+        demag_t<float>(c, s, st, stage0, src_mode, src, dst_mode, dst, self_src);
+}
+
+void mmxk_stage(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime_graph, cudaGraphConditionalHandle cond,
+                int use_cond)
+{
+    if (c->prec == MMX_FP64)
+        stage_t<double>(c, s, k, extrap, prime_graph, cond, use_cond);
+    else
+        stage_t<float>(c, s, k, extrap, prime_graph, cond, use_cond);
+}

@@ -1,0 +1,641 @@
+// mmx_api.cu -- C ABI of libmmx (declared in include/mmx.h).
+//
+// The integration loop runs on the device: one CUDA graph holds a
+// conditional WHILE node whose body is one attempted step (Eq. 3-4 stages,
+// demag FFTs where the schedule needs them); the controller of Eq. 5 in the
+// last stage kernel decides acceptance, the next step and whether the loop
+// continues.  A second graph with full demag at every stage primes the
+// extrapolation history (the first p steps, Sec. II after Eq. 6).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <climits>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "tensor_host.h"
+
+size_t mmxk_yz_smem_bytes(const mmx_ctx *c);
+size_t mmxk_x_smem_bytes(const mmx_ctx *c);
+
+namespace {
+
+thread_local std::string g_create_err;
+
+// Butcher tableaux of the methods of Sec. II (refs. [26]-[31]) as exact
+// fractions: rows of (numerator, denominator).
+struct Frac {
+    double n, d;
+};
+
+struct MethodDef {
+    int s, order, adaptive, fsal;
+    std::vector<Frac> a;
+    std::vector<std::vector<Frac>> b;
+    std::vector<Frac> c, chat;
+};
+
+MethodDef method_def(int m)
+{
+    MethodDef d{};
+    switch (m) {
+    case MMX_RK4:
+        d = {4, 4, 0, 0, {{0, 1}, {1, 2}, {1, 2}, {1, 1}},
+             {{}, {{1, 2}}, {{0, 1}, {1, 2}}, {{0, 1}, {0, 1}, {1, 1}}},
+             {{1, 6}, {1, 3}, {1, 3}, {1, 6}},
+             {{1, 6}, {1, 3}, {1, 3}, {1, 6}}};
+        break;
+    case MMX_HEUN12:
+        d = {2, 2, 1, 0, {{0, 1}, {1, 1}}, {{}, {{1, 1}}}, {{1, 2}, {1, 2}}, {{1, 1}, {0, 1}}};
+        break;
+    case MMX_RK23_BS:
+        d = {4, 3, 1, 1, {{0, 1}, {1, 2}, {3, 4}, {1, 1}},
+             {{}, {{1, 2}}, {{0, 1}, {3, 4}}, {{2, 9}, {1, 3}, {4, 9}}},
+             {{2, 9}, {1, 3}, {4, 9}, {0, 1}},
+             {{7, 24}, {1, 4}, {1, 3}, {1, 8}}};
+        break;
+    case MMX_RKF45:
+        d = {6, 4, 1, 0, {{0, 1}, {1, 4}, {3, 8}, {12, 13}, {1, 1}, {1, 2}},
+             {{},
+              {{1, 4}},
+              {{3, 32}, {9, 32}},
+              {{1932, 2197}, {-7200, 2197}, {7296, 2197}},
+              {{439, 216}, {-8, 1}, {3680, 513}, {-845, 4104}},
+              {{-8, 27}, {2, 1}, {-3544, 2565}, {1859, 4104}, {-11, 40}}},
+             {{25, 216}, {0, 1}, {1408, 2565}, {2197, 4104}, {-1, 5}, {0, 1}},
+             {{16, 135}, {0, 1}, {6656, 12825}, {28561, 56430}, {-9, 50}, {2, 55}}};
+        break;
+    case MMX_RKCK45:
+        d = {6, 4, 1, 0, {{0, 1}, {1, 5}, {3, 10}, {3, 5}, {1, 1}, {7, 8}},
+             {{},
+              {{1, 5}},
+              {{3, 40}, {9, 40}},
+              {{3, 10}, {-9, 10}, {6, 5}},
+              {{-11, 54}, {5, 2}, {-70, 27}, {35, 27}},
+              {{1631, 55296}, {175, 512}, {575, 13824}, {44275, 110592}, {253, 4096}}},
+             {{2825, 27648}, {0, 1}, {18575, 48384}, {13525, 55296}, {277, 14336}, {1, 4}},
+             {{37, 378}, {0, 1}, {250, 621}, {125, 594}, {0, 1}, {512, 1771}}};
+        break;
+    case MMX_RKDP54:
+        d = {7, 5, 1, 1, {{0, 1}, {1, 5}, {3, 10}, {4, 5}, {8, 9}, {1, 1}, {1, 1}},
+             {{},
+              {{1, 5}},
+              {{3, 40}, {9, 40}},
+              {{44, 45}, {-56, 15}, {32, 9}},
+              {{19372, 6561}, {-25360, 2187}, {64448, 6561}, {-212, 729}},
+              {{9017, 3168}, {-355, 33}, {46732, 5247}, {49, 176}, {-5103, 18656}},
+              {{35, 384}, {0, 1}, {500, 1113}, {125, 192}, {-2187, 6784}, {11, 84}}},
+             {{35, 384}, {0, 1}, {500, 1113}, {125, 192}, {-2187, 6784}, {11, 84}, {0, 1}},
+             {{5179, 57600}, {0, 1}, {7571, 16695}, {393, 640}, {-92097, 339200}, {187, 2100}, {1, 40}}};
+        break;
+    case MMX_RKF56:
+        d = {8, 5, 1, 0, {{0, 1}, {1, 6}, {4, 15}, {2, 3}, {4, 5}, {1, 1}, {0, 1}, {1, 1}},
+             {{},
+              {{1, 6}},
+              {{4, 75}, {16, 75}},
+              {{5, 6}, {-8, 3}, {5, 2}},
+              {{-8, 5}, {144, 25}, {-4, 1}, {16, 25}},
+              {{361, 320}, {-18, 5}, {407, 128}, {-11, 80}, {55, 128}},
+              {{-11, 640}, {0, 1}, {11, 256}, {-11, 160}, {11, 256}, {0, 1}},
+              {{93, 640}, {-18, 5}, {803, 256}, {-11, 160}, {99, 256}, {0, 1}, {1, 1}}},
+             {{31, 384}, {0, 1}, {1125, 2816}, {9, 32}, {125, 768}, {5, 66}, {0, 1}, {0, 1}},
+             {{7, 1408}, {0, 1}, {1125, 2816}, {9, 32}, {125, 768}, {0, 1}, {5, 66}, {5, 66}}};
+        break;
+    default:
+        d.s = 0;
+    }
+    return d;
+}
+
+bool pow2(int v) { return v >= 1 && (v & (v - 1)) == 0; }
+bool finite_pos(double v) { return std::isfinite(v) && v > 0; }
+
+int fail(mmx_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(mmx_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, MMX_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                        \
+    do {                                                                \
+        cudaError_t e__ = (call);                                       \
+        if (e__ != cudaSuccess) return cuda_fail(c, e__, #call);        \
+    } while (0)
+
+std::string validate(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *field,
+                     const mmx_integrator *in, int precision)
+{
+    if (!mesh || !mat || !field || !in) return "null argument";
+    if (!pow2(mesh->nx) || !pow2(mesh->ny) || !pow2(mesh->nz))
+        return "mesh sizes must be powers of two";
+    if (mesh->nx < 2) return "nx must be at least 2";
+    if (mesh->nx > 2048 || mesh->ny > 2048 || mesh->nz > 2048) return "mesh side above 2048 cells";
+    if (!finite_pos(mesh->dx) || !finite_pos(mesh->dy) || !finite_pos(mesh->dz)) return "cell sizes must be > 0";
+    if (!finite_pos(mat->Ms) || !finite_pos(mat->gamma)) return "Ms and gamma must be > 0";
+    if (!std::isfinite(mat->A) || mat->A < 0 || !std::isfinite(mat->alpha) || mat->alpha < 0 || !std::isfinite(mat->K))
+        return "A, alpha must be >= 0 and K finite";
+    double ku2 = mat->ku[0] * mat->ku[0] + mat->ku[1] * mat->ku[1] + mat->ku[2] * mat->ku[2];
+    if (mat->K != 0 && std::fabs(ku2 - 1.0) > 1e-9) return "anisotropy axis ku must be a unit vector";
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(field->H0[i]) || !std::isfinite(field->pulse_H[i])) return "field must be finite";
+    if (std::isnan(field->t_on) || std::isnan(field->t_off)) return "pulse window must not be NaN";
+    if (in->method < MMX_RK4 || in->method > MMX_RKF56) return "unknown method";
+    if (in->extrap_order < -1 || in->extrap_order > MMX_MAXP) return "extrap_order must be in [-1, 6]";
+    if (!finite_pos(in->h)) return "h must be > 0";
+    if (in->adaptive) {
+        if (!finite_pos(in->tol) || !finite_pos(in->hmin) || !finite_pos(in->hmax) || in->hmin > in->hmax)
+            return "adaptive: need tol > 0 and 0 < hmin <= hmax";
+        if (!finite_pos(in->cmin) || !(in->cmin <= 1.0) || !(in->cmax >= 1.0) || !std::isfinite(in->cmax))
+            return "adaptive: need 0 < cmin <= 1 <= cmax";
+        if (!(in->safety > 0 && in->safety <= 1)) return "adaptive: safety must be in (0, 1]";
+    }
+    if (precision != MMX_FP64 && precision != MMX_FP32_MIXED) return "unknown precision";
+    return "";
+}
+
+int read_state(mmx_ctx *c)
+{
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(c->h_st, c->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    return 0;
+}
+
+int write_state(mmx_ctx *c)
+{
+    CK(cudaMemcpyAsync(c->st, c->h_st, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return 0;
+}
+
+void reset_history(DevState *s)
+{
+    s->hist_n = 1;
+    s->head = 0;
+    for (int i = 0; i < MMX_NHIST; ++i) s->hist_t[i] = 0;
+    s->hist_t[0] = s->t;
+    s->f1_valid = 0;
+    s->fbase = 0;
+}
+
+// One attempted step, launched on stream s.  prime: full demag at every
+// stage (priming or extrap_order < 0).
+int body_kernels(mmx_ctx *c, cudaStream_t s, int prime, cudaGraphConditionalHandle cond, int use_cond)
+{
+    const int p = c->ctl.p;
+    const int extrap = (p >= 0 && !prime);
+    mmxk_demag(c, s, c->st, 1, 1, nullptr, p >= 0 ? 1 : 0, c->G, nullptr);
+    mmxk_stage(c, s, 0, extrap, prime && p >= 0, cond, use_cond);
+    for (int k = 1; k < c->tab.s; ++k) {
+        if (!extrap) mmxk_demag(c, s, c->st, 0, 0, c->Y[k & 1], 0, c->G, nullptr);
+        mmxk_stage(c, s, k, extrap, prime && p >= 0, cond, use_cond);
+    }
+    return 0;
+}
+
+int kernels_per_attempt(const mmx_ctx *c, int prime)
+{
+    const int p = c->ctl.p;
+    const int extrap = (p >= 0 && !prime);
+    return extrap ? 3 + c->tab.s : 4 * c->tab.s;
+}
+
+int build_graph(mmx_ctx *c, int which)
+{
+    if (c->graph_ok[which]) return 0;
+    const bool prof = c->profiling;
+    c->profiling = false;
+    const long long launches = c->launches;
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    body_kernels(c, c->cap_stream, which == 1 || c->ctl.p < 0, h, 1);
+    cudaGraph_t captured;
+    CK(cudaStreamEndCapture(c->cap_stream, &captured));
+    c->launches = launches;
+    c->profiling = prof;
+    cudaGraphExec_t ex;
+    CK(cudaGraphInstantiate(&ex, g, 0));
+    c->graph[which] = g;
+    c->gexec[which] = ex;
+    c->graph_ok[which] = true;
+    return 0;
+}
+
+// Runs attempts until the device says stop (done, or primed for which = 1).
+int run_loop(mmx_ctx *c, int which)
+{
+    const int prime = (which == 1 || c->ctl.p < 0);
+    if (c->use_graphs && !c->profiling) {
+        int rc = build_graph(c, which);
+        if (rc) return rc;
+        const long long before = c->h_st->run_attempts;
+        CK(cudaGraphLaunch(c->gexec[which], c->stream));
+        rc = read_state(c);
+        if (rc) return rc;
+        c->launches += (c->h_st->run_attempts - before) * kernels_per_attempt(c, prime);
+        return 0;
+    }
+    // one attempt at a time, synchronising to read the loop flag
+    for (;;) {
+        body_kernels(c, c->stream, prime, 0, 0);
+        int rc = read_state(c);
+        if (rc) return rc;
+        if (!c->h_st->loop_more) return 0;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *field, const mmx_integrator *integ,
+               int precision, void *cuda_stream, mmx_ctx **out)
+{
+    if (!out) return MMX_ERR_ARG;
+    *out = nullptr;
+    std::string why = validate(mesh, mat, field, integ, precision);
+    if (!why.empty()) {
+        g_create_err = why;
+        return MMX_ERR_ARG;
+    }
+    mmx_ctx *c = new (std::nothrow) mmx_ctx();
+    if (!c) return MMX_ERR_OOM;
+    c->mesh = *mesh;
+    c->mat = *mat;
+    c->field = *field;
+    c->integ = *integ;
+    c->prec = precision;
+    c->esz = precision == MMX_FP64 ? 8 : 4;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->nx = mesh->nx;
+    c->ny = mesh->ny;
+    c->nz = mesh->nz;
+    c->n = (long long)c->nx * c->ny * c->nz;
+    c->Px = 2 * c->nx;
+    c->Py = c->ny > 1 ? 2 * c->ny : 1;
+    c->Pz = c->nz > 1 ? 2 * c->nz : 1;
+    c->Hy = c->Py / 2 + 1;
+    c->Hz = c->Pz / 2 + 1;
+    c->rows = 3LL * c->ny * c->nz;
+    c->use_graphs = getenv("MMX_NO_GRAPH") == nullptr;
+    if (mmxk_yz_smem_bytes(c) > 227 * 1024 || mmxk_x_smem_bytes(c) > 227 * 1024) {
+        g_create_err = "mesh too large for the single-CTA yz/x FFT passes";
+        delete c;
+        return MMX_ERR_ARG;
+    }
+
+    // tableau
+    MethodDef md = method_def(integ->method);
+    TabArgs &T = c->tab;
+    memset(&T, 0, sizeof(T));
+    T.s = md.s;
+    T.order = md.order;
+    T.adaptive = md.adaptive;
+    T.fsal = md.fsal;
+    for (int i = 0; i < md.s; ++i) {
+        T.a[i] = md.a[i].n / md.a[i].d;
+        T.c[i] = md.c[i].n / md.c[i].d;
+        T.e[i] = md.c[i].n / md.c[i].d - md.chat[i].n / md.chat[i].d;
+        for (size_t j = 0; j < md.b[i].size(); ++j) T.b[i][j] = md.b[i][j].n / md.b[i][j].d;
+    }
+    // physics
+    const double mu0 = 4e-7 * M_PI;
+    PhysArgs &P = c->ph;
+    P.nx = c->nx;
+    P.ny = c->ny;
+    P.nz = c->nz;
+    P.n = c->n;
+    const double cex = 2.0 * mat->A / (mu0 * mat->Ms);
+    P.wx = cex / (mesh->dx * mesh->dx);
+    P.wy = cex / (mesh->dy * mesh->dy);
+    P.wz = cex / (mesh->dz * mesh->dz);
+    P.can = 2.0 * mat->K / (mu0 * mat->Ms);
+    for (int i = 0; i < 3; ++i) {
+        P.ku[i] = mat->ku[i];
+        P.H0[i] = field->H0[i];
+        P.pulse[i] = field->pulse_H[i];
+    }
+    P.t_on = field->t_on;
+    P.t_off = field->t_off;
+    P.gp = mat->gamma / (1.0 + mat->alpha * mat->alpha);
+    P.alpha = mat->alpha;
+    CtlArgs &C = c->ctl;
+    C.p = integ->extrap_order;
+    C.adaptive = (integ->adaptive && md.adaptive) ? 1 : 0;
+    C.nslots = md.s;
+    C.prime = 0;
+    C.tol = integ->tol;
+    C.hmin = integ->hmin;
+    C.hmax = integ->hmax;
+    C.cmin = integ->cmin;
+    C.cmax = integ->cmax;
+    C.safety = integ->safety;
+
+    // tensor and spectrum (host, binary128)
+    mmx_host_tensor_args ta{c->nx, c->ny, c->nz, mesh->dx, mesh->dy, mesh->dz, mat->Ms};
+    std::vector<double> N6((size_t)6 * c->n);
+    mmx_host_tensor(&ta, N6.data());
+    std::vector<double> Kspec((size_t)(c->nx + 1) * c->Hz * c->Hy * 6);
+    mmx_host_spectrum(&ta, N6.data(), c->N00, Kspec.data());
+    for (int i = 0; i < 3; ++i) P.msN00[i] = mat->Ms * c->N00[i];
+
+    // device buffers
+    auto alloc = [&](void **p, size_t bytes) -> bool {
+        *p = nullptr;
+        if (bytes == 0) bytes = 16;
+        return cudaMalloc(p, bytes) == cudaSuccess;
+    };
+    const size_t fb = (size_t)3 * c->n * c->esz;
+    const int nh = std::max(1, C.p + 1);
+    bool ok = true;
+    ok = ok && alloc(&c->m[0], fb) && alloc(&c->m[1], fb) && alloc(&c->Y[0], fb) && alloc(&c->Y[1], fb);
+    ok = ok && alloc(&c->F, fb * md.s) && alloc(&c->G, fb) && alloc(&c->hist, fb * nh);
+    ok = ok && alloc(&c->S, (size_t)c->rows * c->nx * 2 * c->esz);
+    ok = ok && alloc(&c->K, Kspec.size() * c->esz);
+    ok = ok && alloc(&c->twx, (size_t)c->Px * 2 * c->esz) && alloc(&c->twy, (size_t)c->Py * 2 * c->esz) &&
+         alloc(&c->twz, (size_t)c->Pz * 2 * c->esz);
+    ok = ok && alloc((void **)&c->st, sizeof(DevState));
+    ok = ok && cudaMallocHost((void **)&c->h_st, sizeof(DevState)) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreate(&c->ev_a) == cudaSuccess && cudaEventCreate(&c->ev_b) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        g_create_err = "device allocation failed";
+        mmx_destroy(c);
+        return MMX_ERR_OOM;
+    }
+    int rc = mmxk_setup_buffers(c, Kspec.data());
+    if (rc) {
+        g_create_err = "kernel set-up failed";
+        mmx_destroy(c);
+        return rc;
+    }
+    cudaMemset(c->m[0], 0, fb);
+    cudaMemset(c->m[1], 0, fb);
+    cudaMemset(c->F, 0, fb * md.s);
+    cudaMemset(c->hist, 0, fb * nh);
+    DevState &s = *c->h_st;
+    memset(&s, 0, sizeof(s));
+    s.t = 0;
+    s.h_ctrl = integ->h;
+    s.h = integ->h;
+    s.t_end = 0;
+    s.done = 1;
+    reset_history(&s);
+    if (cudaMemcpy(c->st, c->h_st, sizeof(DevState), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        g_create_err = "state upload failed";
+        mmx_destroy(c);
+        return MMX_ERR_CUDA;
+    }
+    *out = c;
+    return MMX_OK;
+}
+
+int mmx_set_m(mmx_ctx *c, const void *m)
+{
+    if (!c || !m) return MMX_ERR_ARG;
+    int rc = read_state(c);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(c->m[0], m, (size_t)3 * c->n * c->esz, cudaMemcpyDefault, c->stream));
+    c->h_st->cur = 0;
+    reset_history(c->h_st);
+    return write_state(c);
+}
+
+int mmx_get_m(mmx_ctx *c, void *m)
+{
+    if (!c || !m) return MMX_ERR_ARG;
+    int rc = read_state(c);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(m, c->m[c->h_st->cur], (size_t)3 * c->n * c->esz, cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MMX_OK;
+}
+
+int mmx_set_time(mmx_ctx *c, double t)
+{
+    if (!c || !std::isfinite(t)) return MMX_ERR_ARG;
+    int rc = read_state(c);
+    if (rc) return rc;
+    c->h_st->t = t;
+    reset_history(c->h_st);
+    return write_state(c);
+}
+
+int mmx_demag(mmx_ctx *c, const void *m_dev, void *H_dev)
+{
+    if (!c || !m_dev || !H_dev) return MMX_ERR_ARG;
+    mmxk_demag(c, c->stream, nullptr, 0, 0, m_dev, 0, H_dev, m_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "mmx_demag launch");
+    return MMX_OK;
+}
+
+static int run_common(mmx_ctx *c, double t_end, long long acc_more)
+{
+    int rc = read_state(c);
+    if (rc) return rc;
+    DevState &s = *c->h_st;
+    if (acc_more <= 0 && !(t_end > s.t)) return MMX_OK;
+    const long long forced0 = s.forced;
+    s.t_end = t_end;
+    s.acc_target = acc_more > 0 ? s.accepted + acc_more : LLONG_MAX;
+    s.done = 0;
+    s.status = 0;
+    s.run_attempts = 0;
+    s.attempt_limit = 50000000LL;
+    s.t_start_ns = 0;
+    const char *tl = getenv("MMX_TIME_LIMIT_S");
+    s.time_limit_ns = (unsigned long long)((tl ? atof(tl) : 300.0) * 1e9);
+    s.err_bits = 0;
+    s.blocks_done = 0;
+    {
+        const double rem = s.t_end - s.t;
+        const int cl = (s.h_ctrl * (1.0 + 1e-9) >= rem) ? 1 : 0;
+        s.h = cl ? rem : s.h_ctrl;
+        s.clipped = cl;
+    }
+    s.loop_more = 1;
+    rc = write_state(c);
+    if (rc) return rc;
+    for (int guard = 0; guard < 1000; ++guard) {
+        const int p = c->ctl.p;
+        const int which = (p >= 0 && s.hist_n < p + 1) ? 1 : 0;
+        rc = run_loop(c, which);
+        if (rc) return rc;
+        if (s.done) break;
+        if (which == 0) return fail(c, MMX_ERR_STATE, "device loop stopped before the run finished");
+    }
+    if (s.status) {
+        if (s.status == MMX_ERR_NONFINITE) return fail(c, s.status, "error estimate became non-finite");
+        if (s.status == MMX_ERR_TIMEOUT) return fail(c, s.status, "attempt or time limit of the run reached");
+        return fail(c, s.status, "device reported an error");
+    }
+    return s.forced > forced0 ? MMX_WARN_HMIN : MMX_OK;
+}
+
+int mmx_run(mmx_ctx *c, double t_end)
+{
+    if (!c || !std::isfinite(t_end)) return MMX_ERR_ARG;
+    return run_common(c, t_end, 0);
+}
+
+int mmx_step(mmx_ctx *c, int n_accepted)
+{
+    if (!c || n_accepted < 1) return MMX_ERR_ARG;
+    return run_common(c, DBL_MAX, n_accepted);
+}
+
+int mmx_get_stats(mmx_ctx *c, mmx_stats *o)
+{
+    if (!c || !o) return MMX_ERR_ARG;
+    int rc = read_state(c);
+    if (rc) return rc;
+    const DevState &s = *c->h_st;
+    o->t = s.t;
+    o->h = s.h_ctrl;
+    o->last_err = s.last_err;
+    o->accepted = s.accepted;
+    o->rejected = s.rejected;
+    o->exact_evals = s.exact_evals;
+    o->extrap_evals = s.extrap_evals;
+    o->forced_accepts = s.forced;
+    o->attempts = s.attempts;
+    o->kernel_launches = c->launches;
+    return MMX_OK;
+}
+
+struct BlobHeader {
+    uint64_t magic;
+    int32_t nx, ny, nz, prec, method, p, s;
+    int32_t pad;
+};
+static const uint64_t kMagic = 0x31305854534d4d58ULL;  // "XMMSTX01"
+
+int mmx_save_state(mmx_ctx *c, void *buf, size_t *len)
+{
+    if (!c || !len) return MMX_ERR_ARG;
+    const size_t fb = (size_t)3 * c->n * c->esz;
+    const int nh = std::max(1, c->ctl.p + 1);
+    const size_t need = sizeof(BlobHeader) + sizeof(DevState) + fb * (2 + c->tab.s + nh);
+    if (!buf) {
+        *len = need;
+        return MMX_OK;
+    }
+    if (*len < need) return fail(c, MMX_ERR_ARG, "buffer too small");
+    int rc = read_state(c);
+    if (rc) return rc;
+    char *p = (char *)buf;
+    BlobHeader hd{kMagic, c->nx, c->ny, c->nz, c->prec, c->integ.method, c->ctl.p, c->tab.s, 0};
+    memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    memcpy(p, c->h_st, sizeof(DevState));
+    p += sizeof(DevState);
+    CK(cudaMemcpy(p, c->m[0], fb, cudaMemcpyDeviceToHost));
+    p += fb;
+    CK(cudaMemcpy(p, c->m[1], fb, cudaMemcpyDeviceToHost));
+    p += fb;
+    CK(cudaMemcpy(p, c->F, fb * c->tab.s, cudaMemcpyDeviceToHost));
+    p += fb * c->tab.s;
+    CK(cudaMemcpy(p, c->hist, fb * nh, cudaMemcpyDeviceToHost));
+    *len = need;
+    return MMX_OK;
+}
+
+int mmx_load_state(mmx_ctx *c, const void *buf, size_t len)
+{
+    if (!c || !buf) return MMX_ERR_ARG;
+    const size_t fb = (size_t)3 * c->n * c->esz;
+    const int nh = std::max(1, c->ctl.p + 1);
+    const size_t need = sizeof(BlobHeader) + sizeof(DevState) + fb * (2 + c->tab.s + nh);
+    if (len < need) return fail(c, MMX_ERR_ARG, "state blob too short");
+    BlobHeader hd;
+    memcpy(&hd, buf, sizeof(hd));
+    if (hd.magic != kMagic || hd.nx != c->nx || hd.ny != c->ny || hd.nz != c->nz || hd.prec != c->prec ||
+        hd.method != c->integ.method || hd.p != c->ctl.p)
+        return fail(c, MMX_ERR_ARG, "state blob does not match this context");
+    const char *p = (const char *)buf + sizeof(hd);
+    CK(cudaStreamSynchronize(c->stream));
+    memcpy(c->h_st, p, sizeof(DevState));
+    p += sizeof(DevState);
+    CK(cudaMemcpy(c->m[0], p, fb, cudaMemcpyHostToDevice));
+    p += fb;
+    CK(cudaMemcpy(c->m[1], p, fb, cudaMemcpyHostToDevice));
+    p += fb;
+    CK(cudaMemcpy(c->F, p, fb * c->tab.s, cudaMemcpyHostToDevice));
+    p += fb * c->tab.s;
+    CK(cudaMemcpy(c->hist, p, fb * nh, cudaMemcpyHostToDevice));
+    c->h_st->done = 1;
+    return write_state(c);
+}
+
+int mmx_set_profiling(mmx_ctx *c, int enable)
+{
+    if (!c) return MMX_ERR_ARG;
+    c->profiling = enable != 0;
+    for (int i = 0; i < MMX_NPROF; ++i) {
+        c->prof_ms[i] = 0;
+        c->prof_n[i] = 0;
+    }
+    return MMX_OK;
+}
+
+int mmx_get_profile(mmx_ctx *c, double *ms, long long *launches)
+{
+    if (!c || !ms || !launches) return MMX_ERR_ARG;
+    for (int i = 0; i < MMX_NPROF; ++i) {
+        ms[i] = c->prof_ms[i];
+        launches[i] = c->prof_n[i];
+    }
+    return MMX_OK;
+}
+
+const char *mmx_last_error(const mmx_ctx *c)
+{
+    if (!c) return g_create_err.c_str();
+    return c->err.c_str();
+}
+
+void mmx_destroy(mmx_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < 2; ++i) {
+        if (c->graph_ok[i]) {
+            cudaGraphExecDestroy(c->gexec[i]);
+            cudaGraphDestroy(c->graph[i]);
+        }
+    }
+    void *bufs[] = {c->m[0], c->m[1], c->Y[0], c->Y[1], c->F, c->G, c->hist, c->S, c->K, c->twx, c->twy, c->twz, c->st};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (c->h_st) cudaFreeHost(c->h_st);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->ev_a) cudaEventDestroy(c->ev_a);
+    if (c->ev_b) cudaEventDestroy(c->ev_b);
+    delete c;
+}
+
+}  // extern "C"

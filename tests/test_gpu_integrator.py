@@ -1,0 +1,108 @@
+"""GPU parity of whole integrations (Eq. 1, 3-6) against the CPU oracle on
+the same seeded inputs: fixed-step RK4 with full demag, adaptive methods
+with demag extrapolation (matched step sequences in FP64), FP32 within the
+stated tolerance, checkpoint/resume and error reporting."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2107_06729_gb300 import workloads as W
+from gpu_util import gpu_run, oracle_run, gpu_context, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+MAT = {"Ms": 8e5, "A": 1.3e-11, "K": 2e4, "ku": (1.0, 0.0, 0.0), "alpha": 0.02, "gamma": W.GAMMA}
+FLD = {"H0": tuple(W.mT((-24.6, 4.3, 0.0))), "pulse": tuple(W.mT((0.0, 20.0, 0.0))),
+       "t_on": 1e-12, "t_off": 3e-12}
+
+
+@pytest.mark.parametrize("method,p,adaptive", [
+    ("RK4", -1, False), ("RK4", 3, False), ("RKDP54", 4, True), ("RKDP54", -1, True),
+    ("RK23", 2, True), ("RKF45", 4, True), ("RKCK45", 4, True), ("RKF56", 5, True), ("HEUN12", 1, True)])
+def test_fp64_matches_oracle_step_for_step(method, p, adaptive):
+    n, d = (16, 8, 2), (4e-9, 4e-9, 4e-9)
+    mesh = {"n": n, "d": d}
+    integ = {"method": method, "extrap_order": p, "adaptive": adaptive, "h": 1e-13, "tol": 1e-5}
+    m0 = W.m_uniform_noise(n, seed=3, noise=0.2)
+    t_end = 5e-12
+    got, gs = gpu_run(mesh, MAT, FLD, integ, m0, t_end, "fp64")
+    ref, rs = oracle_run(mesh, MAT, FLD, integ, m0, t_end)
+    assert gs["accepted"] == rs["accepted"] and gs["rejected"] == rs["rejected"]
+    assert gs["exact_evals"] == rs["exact_evals"] and gs["extrap_evals"] == rs["extrap_evals"]
+    assert gs["t"] == pytest.approx(t_end, rel=1e-15)
+    assert np.abs(got - ref).max() < 1e-10
+
+
+def test_fp32_dp54_extrapolated_within_tolerance():
+    n, d = (32, 16, 4), (2.5e-9, 2.5e-9, 1e-9)
+    mesh = {"n": n, "d": d}
+    integ = {"method": "RKDP54", "extrap_order": 4, "adaptive": True, "h": 1e-13, "tol": 1e-5}
+    mat = dict(MAT, K=5e4, alpha=0.01)
+    m0 = W.m_random(n, seed=0)
+    got, gs = gpu_run(mesh, mat, FLD, integ, m0, 5e-12, "fp32")
+    ref, rs = oracle_run(mesh, mat, FLD, integ, m0, 5e-12)
+    assert np.abs(got - ref).max() < 1e-4
+    assert abs(gs["accepted"] - rs["accepted"]) <= max(2, rs["accepted"] // 20)
+
+
+def test_chunked_runs_equal_one_run():
+    n, d = (16, 8, 1), (4e-9, 4e-9, 4e-9)
+    mesh = {"n": n, "d": d}
+    integ = {"method": "RK4", "extrap_order": -1, "adaptive": False, "h": 1e-13}
+    m0 = W.m_uniform_noise(n, seed=1)
+    a, _ = gpu_run(mesh, MAT, FLD, integ, m0, 2e-12, "fp64", chunks=1)
+    b, _ = gpu_run(mesh, MAT, FLD, integ, m0, 2e-12, "fp64", chunks=4)
+    assert np.array_equal(a, b)
+
+
+def test_checkpoint_resume_is_bitwise():
+    torch = torch_cuda()
+    n, d = (16, 8, 2), (4e-9, 4e-9, 4e-9)
+    mesh = {"n": n, "d": d}
+    integ = {"method": "RKDP54", "extrap_order": 4, "adaptive": True, "h": 1e-13, "tol": 1e-5}
+    m0 = torch.from_numpy(W.m_uniform_noise(n, seed=2, noise=0.3)).cuda()
+    ref = gpu_context(mesh, MAT, FLD, integ, "fp64")
+    ref.set_m(m0)
+    ref.run(4e-12)
+    want = torch.empty_like(m0)
+    ref.get_m(want)
+    a = gpu_context(mesh, MAT, FLD, integ, "fp64")
+    a.set_m(m0)
+    a.run(2e-12)
+    blob = a.save_state()
+    b = gpu_context(mesh, MAT, FLD, integ, "fp64")
+    b.load_state(blob)
+    b.run(4e-12)
+    got = torch.empty_like(m0)
+    b.get_m(got)
+    assert torch.equal(got, want)
+    assert b.stats()["accepted"] == ref.stats()["accepted"]
+    for c in (ref, a, b):
+        c.close()
+
+
+def test_nonfinite_input_is_reported():
+    torch = torch_cuda()
+    import paper_2107_06729_gb300 as pkg
+    n, d = (8, 4, 1), (4e-9, 4e-9, 4e-9)
+    integ = {"method": "RKDP54", "extrap_order": 4, "adaptive": True, "h": 1e-13, "tol": 1e-5}
+    m = W.m_random(n, seed=0)
+    m[0, 0, 1, 2] = np.nan  # planted on the host before upload
+    ctx = gpu_context({"n": n, "d": d}, MAT, FLD, integ, "fp64")
+    ctx.set_m(torch.from_numpy(m).cuda())
+    with pytest.raises(pkg.MMXError) as ei:
+        ctx.run(1e-12)
+    assert ei.value.code == pkg.MMX_ERR_NONFINITE
+    ctx.close()
+
+
+def test_two_cell_mesh_fixed_step():
+    m0 = np.array([0.8, 0.0, -0.6])
+    mesh = {"n": (2, 1, 1), "d": (3e-9, 3e-9, 3e-9)}
+    mat = {"Ms": 8e5, "A": 0.0, "K": 0.0, "alpha": 0.1, "gamma": 2.211e5}
+    fld = {"H0": (0.0, 0.0, 1e5)}
+    integ = {"method": "RKDP54", "extrap_order": 4, "adaptive": False, "h": 2e-14}
+    m = np.repeat(m0.reshape(3, 1, 1, 1), 2, axis=3)
+    got, _ = gpu_run(mesh, mat, fld, integ, m, 20e-12, "fp64")
+    ref, _ = oracle_run(mesh, mat, fld, integ, m, 20e-12)
+    assert np.abs(got - ref).max() < 1e-11
