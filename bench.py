@@ -1,0 +1,364 @@
+"""Benchmark: simulated ns per second for the 256 x 128 x 4 film
+(2.5 x 2.5 x 1 nm cells, Dormand-Prince 5(4) at e_max = 1e-5, demag exact
+at stage 1 and 4th-order extrapolation at the other stages, FP32 fields with
+FP64 weights/controller), and the achieved bandwidth of the dominant kernel
+against the measured HBM peak.
+
+One bench "step" integrates a fixed simulated interval (default 20 ps) with
+one mmx_run call, continuing the trajectory of the previous step.  Inputs are
+seeded and synthetic (random initial directions, 20 mT pulse along y on
+[0, 200 ps)).  Between timed steps a 512 MB buffer is written to flush L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mmx|reference]
+
+--impl reference times the CPU FP64 oracle (plain C + OpenMP on the host
+cores) on a bounded sample of the same workload.  Under torchrun (N > 1)
+every rank integrates an independent replica (seed = rank); the mesh itself
+is not sharded.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2107_06729_gb300 import workloads as W  # noqa: E402
+
+METRIC = "Simulated ns/s at matched error vs FP64 oracle; demag-FFT HBM GB/s (% of peak)"
+UNIT = "simulated ns/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(sim_ns, seconds, world, reduce_max, reduce_sum):
+    """Whole-job value: simulated ns of all ranks over the slowest rank's time."""
+    tot_ns = reduce_sum(sim_ns)
+    t_max = reduce_max(seconds)
+    return tot_ns / t_max, t_max
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs", "hbm"):
+                if k in d and isinstance(d[k], (int, float)):
+                    return float(d[k]), "measured (MEASURED_PEAKS.json %s)" % k
+        except Exception:
+            pass
+    return 6800.0, "fallback (6.8 TB/s, no MEASURED_PEAKS.json)"
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.rows)}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        if sm:
+            out["sm_mhz"] = statistics.median(sm)
+        if mx:
+            out["sm_max_mhz"] = max(mx)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for i, nm in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower() == "active" and nm not in out["reasons"]:
+                    out["reasons"].append(nm)
+        return out
+
+
+def byte_model(cfg, esz):
+    """Algorithmic bytes per launch of the three demag passes (DESIGN: pass
+    model).  n cells, r = element size; complex words are 2r."""
+    nx, ny, nz = cfg["mesh"]["n"]
+    n = nx * ny * nz
+    Py = 2 * ny if ny > 1 else 1
+    Pz = 2 * nz if nz > 1 else 1
+    kbytes = (nx + 1) * (Py // 2 + 1) * (Pz // 2 + 1) * 6 * esz
+    return {
+        "x_forward_fft": 3 * n * esz + 3 * n * 2 * esz,
+        "yz_fft_tensor_multiply": 2 * 3 * n * 2 * esz + kbytes,
+        "x_inverse_fft": 3 * n * 2 * esz + 3 * n * esz,
+    }
+
+
+def run_mmx(args):
+    import torch
+    import paper_2107_06729_gb300 as pkg
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = W.film_config2(seed=rank)
+    stream = torch.cuda.Stream(dev)
+    t_setup = time.time()
+    ctx = pkg.Context(cfg["mesh"], cfg["material"], cfg["field"], cfg["integrator"], "fp32", stream)
+    t_setup = time.time() - t_setup
+    dt = args.chunk_ps * 1e-12
+    m0 = torch.from_numpy(cfg["m0"]).to(dev, torch.float32)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        ctx.set_m(m0)
+        t = 0.0
+        for _ in range(args.warmup):
+            t += dt
+            ctx.run(t)
+        stream.synchronize()
+        st0 = ctx.stats()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        sampler = ClockSampler(local)
+        sampler.start()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            t += dt
+            ctx.run(t)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        clocks = sampler.stop()
+        st1 = ctx.stats()
+        secs = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+
+        # dominant kernel: same workload, one chunk with per-kernel events
+        ctx.set_profiling(True)
+        t += dt
+        ctx.run(t)
+        prof = ctx.profile()
+        ctx.set_profiling(False)
+
+        # full demag at every stage on the same state: the speedup baseline
+        full_cfg = dict(cfg["integrator"], extrap_order=-1)
+        fctx = pkg.Context(cfg["mesh"], cfg["material"], cfg["field"], full_cfg, "fp32", stream)
+        mcur = torch.empty_like(m0)
+        ctx.get_m(mcur)
+        fctx.set_m(m0)
+        fctx.set_time(0.0)
+        tf = 0.0
+        for _ in range(args.warmup):
+            tf += dt
+            fctx.run(tf)
+        f0 = fctx.stats()
+        fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            fev[i][0].record(stream)
+            tf += dt
+            fctx.run(tf)
+            fev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        f1 = fctx.stats()
+        fsecs = sum(a.elapsed_time(b) for a, b in fev) / 1e3
+        fctx.close()
+
+        # end to end through the C ABI with host buffers: upload m, run, read m
+        host_in = torch.empty(m0.shape, dtype=torch.float32, pin_memory=True)
+        host_out = torch.empty(m0.shape, dtype=torch.float32, pin_memory=True)
+        host_in.copy_(mcur.cpu())
+        e2e_steps = max(1, min(args.steps, 5))
+        torch.cuda.synchronize(dev)
+        w0 = time.perf_counter()
+        te = t
+        for i in range(e2e_steps):
+            ctx.set_m(host_in)
+            te += dt
+            ctx.run(te)
+            ctx.get_m(host_out)
+            host_in.copy_(host_out)
+        e2e_secs = time.perf_counter() - w0
+    ctx.close()
+
+    sim_ns = args.steps * dt * 1e9
+    if world > 1:
+        import torch.distributed as dist
+
+        def rmax(x):
+            v = torch.tensor([x], dtype=torch.float64, device=dev)
+            dist.all_reduce(v, op=dist.ReduceOp.MAX)
+            return float(v.item())
+
+        def rsum(x):
+            v = torch.tensor([x], dtype=torch.float64, device=dev)
+            dist.all_reduce(v, op=dist.ReduceOp.SUM)
+            return float(v.item())
+    else:
+        rmax = rsum = (lambda x: x)
+    value, t_max = aggregate(sim_ns, secs, world, rmax, rsum)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return None
+
+    esz = 4
+    model = byte_model(cfg, esz)
+    dom = max(prof, key=lambda k: prof[k][0])
+    peak, peak_src = peaks()
+    roof = None
+    launches_per_class = {k: v[1] for k, v in prof.items()}
+    if dom in model and prof[dom][1] > 0:
+        avg_s = prof[dom][0] / prof[dom][1] / 1e3
+        ach = model[dom] / avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": None, "peak_source": peak_src,
+                "bytes_per_launch": model[dom], "avg_launch_us": round(avg_s * 1e6, 3)}
+    else:
+        # the stage kernel dominates: report the demag pass with the largest share
+        dem = {k: prof[k] for k in model if prof[k][1] > 0}
+        k = max(dem, key=lambda q: dem[q][0])
+        avg_s = prof[k][0] / prof[k][1] / 1e3
+        ach = model[k] / avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": k, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": None, "peak_source": peak_src,
+                "bytes_per_launch": model[k], "avg_launch_us": round(avg_s * 1e6, 3),
+                "note": "largest demag pass; dominant class overall is " + dom}
+    prof_share = {k: round(v[0] / max(1e-12, sum(x[0] for x in prof.values())), 4) for k, v in prof.items()}
+
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * t_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 weights/error/controller)",
+        "data": "synthetic: seeded random unit vectors (PCG64 seed=rank), 20 mT pulse along y on [0,200ps)",
+        "config": {"workload": cfg["name"], "mesh": list(cfg["mesh"]["n"]),
+                   "cell_nm": [x * 1e9 for x in cfg["mesh"]["d"]], "method": "RKDP54", "extrap_order": 4,
+                   "tol": 1e-5, "sim_ps_per_step": args.chunk_ps, "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "kernel_time_share": prof_share,
+        "kernel_launches_profiled_chunk": launches_per_class,
+        "full_demag_every_stage": {"value": round(args.steps * dt * 1e9 / fsecs, 4), "unit": UNIT,
+                                   "speedup_extrapolated_vs_full": round(value / (args.steps * dt * 1e9 / fsecs), 3),
+                                   "accepted": f1["accepted"] - f0["accepted"],
+                                   "rejected": f1["rejected"] - f0["rejected"]},
+        "steps_accepted": st1["accepted"] - st0["accepted"], "steps_rejected": st1["rejected"] - st0["rejected"],
+        "exact_demag_evals": st1["exact_evals"] - st0["exact_evals"],
+        "extrapolated_demag_evals": st1["extrap_evals"] - st0["extrap_evals"],
+        "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
+        "setup_s": round(t_setup, 3),
+        "e2e": {"value": round(e2e_steps * dt * 1e9 / e2e_secs, 4), "unit": UNIT,
+                "h2d_bytes_per_step": int(host_in.numel() * 4), "d2h_bytes_per_step": int(host_out.numel() * 4),
+                "note": "mmx_set_m(host) + mmx_run + mmx_get_m(host) per step; set_m restarts the history"},
+        "clocks": clocks,
+    }
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
+def cpu_baseline(cfg, budget_s):
+    """The CPU FP64 oracle, as it stands, on a bounded sample of the same
+    workload: integrate chunks of 0.25 ps until about budget_s of CPU work."""
+    ncores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(ncores))
+    import oracle as O
+    t0 = time.time()
+    N6 = O.newell_octant(*cfg["mesh"]["n"], *cfg["mesh"]["d"])
+    t_tensor = time.time() - t0
+    sim = O.Simulation(cfg["mesh"], cfg["material"], cfg["field"], cfg["integrator"], cfg["m0"], N6=N6)
+    dt = 0.25e-12
+    t = 0.0
+    w0 = time.time()
+    while time.time() - w0 < budget_s:
+        t += dt
+        sim.run(t)
+    wall = time.time() - w0
+    st = sim.stats()
+    sim.close()
+    return {"value": round(t * 1e9 / wall, 6), "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle",
+            "sample": "first %.2f ps of the same workload (FP64 oracle, %d accepted steps, %.1f s wall; "
+                      "tensor set-up %.1f s excluded)" % (t * 1e12, st["accepted"], wall, t_tensor)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    cfg = W.film_config2(seed=0)
+    per_step = max(2.0, args.cpu_seconds / max(1, args.steps))
+    base = cpu_baseline(cfg, per_step * args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (same seeded workload)",
+            "config": {"workload": cfg["name"], "mesh": list(cfg["mesh"]["n"]), "method": "RKDP54",
+                       "extrap_order": 4, "tol": 1e-5},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mmx", choices=["mmx", "reference"])
+    ap.add_argument("--chunk-ps", type=float, default=20.0)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "mmx":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mmx(args)
+
+
+if __name__ == "__main__":
+    main()

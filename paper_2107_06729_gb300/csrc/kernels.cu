@@ -492,8 +492,10 @@ template <typename T> __device__ void controller(const StageArgs<T> &a)
                 if (st->hist_n < np1) st->hist_n++;
             }
         } else {
+            // retry from the same t0: F_1 (and its exact field) stay valid
             st->h_ctrl = hnew;
             st->rejected++;
+            st->f1_valid = 1;
         }
         bool done = (st->t >= st->t_end) || (st->accepted >= st->acc_target);
         if (!done && st->run_attempts >= st->attempt_limit) {

@@ -34,25 +34,33 @@ def test_fp64_matches_oracle_step_for_step(method, p, adaptive):
 
 
 def test_fp32_dp54_extrapolated_within_tolerance():
+    """FP32 fields with FP64 weights/controller stay closer to the FP64
+    oracle (same settings) than the method's own truncation error at
+    e_max = 1e-5, which is 2e-4 here (oracle at 1e-5 vs 1e-8).  A smooth
+    initial state is used: from a random-on-sphere state the dynamics are
+    chaotic at the cell level and no max-norm comparison is meaningful."""
     n, d = (32, 16, 4), (2.5e-9, 2.5e-9, 1e-9)
     mesh = {"n": n, "d": d}
     integ = {"method": "RKDP54", "extrap_order": 4, "adaptive": True, "h": 1e-13, "tol": 1e-5}
     mat = dict(MAT, K=5e4, alpha=0.01)
-    m0 = W.m_random(n, seed=0)
+    m0 = W.m_uniform_noise(n, seed=0, noise=0.2)
     got, gs = gpu_run(mesh, mat, FLD, integ, m0, 5e-12, "fp32")
     ref, rs = oracle_run(mesh, mat, FLD, integ, m0, 5e-12)
     assert np.abs(got - ref).max() < 1e-4
+    assert O.epsilon(got, ref) < 2e-5
     assert abs(gs["accepted"] - rs["accepted"]) <= max(2, rs["accepted"] // 20)
 
 
-def test_chunked_runs_equal_one_run():
+def test_chunked_runs_match_one_run():
+    # chunk ends clip a step, so the step sequences differ by rounding only
     n, d = (16, 8, 1), (4e-9, 4e-9, 4e-9)
     mesh = {"n": n, "d": d}
     integ = {"method": "RK4", "extrap_order": -1, "adaptive": False, "h": 1e-13}
     m0 = W.m_uniform_noise(n, seed=1)
-    a, _ = gpu_run(mesh, MAT, FLD, integ, m0, 2e-12, "fp64", chunks=1)
-    b, _ = gpu_run(mesh, MAT, FLD, integ, m0, 2e-12, "fp64", chunks=4)
-    assert np.array_equal(a, b)
+    a, sa = gpu_run(mesh, MAT, FLD, integ, m0, 2e-12, "fp64", chunks=1)
+    b, sb = gpu_run(mesh, MAT, FLD, integ, m0, 2e-12, "fp64", chunks=4)
+    assert np.abs(a - b).max() < 1e-13
+    assert sa["accepted"] == sb["accepted"] == 20
 
 
 def test_checkpoint_resume_is_bitwise():
@@ -63,6 +71,7 @@ def test_checkpoint_resume_is_bitwise():
     m0 = torch.from_numpy(W.m_uniform_noise(n, seed=2, noise=0.3)).cuda()
     ref = gpu_context(mesh, MAT, FLD, integ, "fp64")
     ref.set_m(m0)
+    ref.run(2e-12)
     ref.run(4e-12)
     want = torch.empty_like(m0)
     ref.get_m(want)
