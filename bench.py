@@ -276,6 +276,7 @@ def run_mmx(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roof,
         "kernel_time_share": prof_share,
+        "kernel_avg_us": {k: round(1e3 * v[0] / v[1], 3) for k, v in prof.items() if v[1]},
         "kernel_launches_profiled_chunk": launches_per_class,
         "full_demag_every_stage": {"value": round(args.steps * dt * 1e9 / fsecs, 4), "unit": UNIT,
                                    "speedup_extrapolated_vs_full": round(value / (args.steps * dt * 1e9 / fsecs), 3),

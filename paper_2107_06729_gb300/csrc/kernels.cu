@@ -423,11 +423,20 @@ __global__ void __launch_bounds__(YZ_THREADS) k_yz(const YZArgs<T> a)
 }
 
 // ------------------------------------------------------------------ stages
+// Field and torque constants in the arithmetic type of the stage kernel,
+// converted once on the host.
+template <typename T> struct PhysT {
+    T wx, wy, wz, can, gp, alpha;
+    T ku[3], msN00[3];
+    int nx, ny, nz, lgnx, lgny;
+};
+
 template <typename T> struct StageArgs {
     T *m0, *m1, *Y0, *Y1, *F, *G, *hist;
     DevState *st;
     TabArgs tab;
     PhysArgs ph;
+    PhysT<T> pt;
     CtlArgs ctl;
     int k, extrap, last, use_cond;
     cudaGraphConditionalHandle cond;
@@ -525,9 +534,11 @@ template <typename T> __device__ void controller(const StageArgs<T> &a)
 template <typename T>
 __global__ void __launch_bounds__(ST_THREADS) k_stage(const StageArgs<T> a)
 {
-    __shared__ double s_w[MMX_NHIST];
-    __shared__ double s_H[3];
-    __shared__ double s_red[ST_THREADS / 32];
+    __shared__ T s_w[MMX_NHIST];       // Eq. 6 weights
+    __shared__ T s_H[3];               // applied field at t0 + a_k h
+    __shared__ T s_cb[MMX_MAXS];       // h b_{k+1,l}  or  h c_l (last stage)
+    __shared__ T s_ce[MMX_MAXS];       // h (c_l - c_hat_l) (last stage)
+    __shared__ T s_red[ST_THREADS / 32];
     __shared__ int s_last;
     DevState *st = a.st;
     if (st->done) {
@@ -535,75 +546,89 @@ __global__ void __launch_bounds__(ST_THREADS) k_stage(const StageArgs<T> a)
         return;
     }
     const int k = a.k;
-    const long long n = a.ph.n;
+    const int n = (int)a.ph.n;
     const int cur = st->cur, fbase = st->fbase, head = st->head;
-    const double h = st->h, t0 = st->t;
     const bool f1v = (k == 0) && st->f1_valid;
     const bool ext = a.extrap && k > 0;
     const int np1 = a.ctl.p + 1;
-    if (threadIdx.x == 0) {
-        const double tk = t0 + a.tab.a[k] * h;
-        const bool on = (tk >= a.ph.t_on) && (tk < a.ph.t_off);
-        for (int c = 0; c < 3; ++c) s_H[c] = a.ph.H0[c] + (on ? a.ph.pulse[c] : 0.0);
-        if (ext) {
+    const int s = a.tab.s;
+    if (threadIdx.x < 32) {
+        // per-CTA set-up in FP64 (time, step, weights), used in T below
+        const double h = st->h, t0 = st->t;
+        const int l = threadIdx.x;
+        if (l == 0) {
+            const double tk = t0 + a.tab.a[k] * h;
+            const bool on = (tk >= a.ph.t_on) && (tk < a.ph.t_off);
+            for (int c = 0; c < 3; ++c) s_H[c] = (T)(a.ph.H0[c] + (on ? a.ph.pulse[c] : 0.0));
+        }
+        if (l < MMX_MAXS) {
+            if (a.last) {
+                s_cb[l] = (T)(h * a.tab.c[l]);
+                s_ce[l] = (T)(h * a.tab.e[l]);
+            } else {
+                s_cb[l] = (T)(h * a.tab.b[k + 1][l]);
+                s_ce[l] = (T)0;
+            }
+        }
+        if (ext && l < np1) {
             // Eq. 6: Lagrange basis at tau = a_k h over the stored times
             const double tau = a.tab.a[k] * h;
-            for (int j = 0; j < np1; ++j) {
-                const double tj = st->hist_t[j] - t0;
-                double w = 1.0;
-                for (int l = 0; l < np1; ++l)
-                    if (l != j) {
-                        const double tl = st->hist_t[l] - t0;
-                        w *= (tau - tl) / (tj - tl);
-                    }
-                s_w[j] = w;
-            }
+            const double tj = st->hist_t[l] - t0;
+            double w = 1.0;
+            for (int q = 0; q < np1; ++q)
+                if (q != l) {
+                    const double tq = st->hist_t[q] - t0;
+                    w *= (tau - tq) / (tj - tq);
+                }
+            s_w[l] = (T)w;
         }
     }
     __syncthreads();
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < n;
     const int ns = a.ctl.nslots;
     const size_t fstride = (size_t)3 * n;
     T *Fk = a.F + (size_t)((fbase + k) % ns) * fstride;
     const T *m0 = cur ? a.m1 : a.m0;
+    const PhysT<T> &P = a.pt;
     T f[3] = {0, 0, 0};
     if (valid) {
         if (f1v) {
             for (int c = 0; c < 3; ++c) f[c] = Fk[c * n + i];
         } else {
             const T *Y = (k == 0) ? m0 : ((k & 1) ? a.Y1 : a.Y0);
-            const int nx = a.ph.nx, ny = a.ph.ny, nz = a.ph.nz;
-            const int x = (int)(i % nx);
-            const long long rest = i / nx;
-            const int y = (int)(rest % ny), z = (int)(rest / ny);
-            const long long sy = nx, sz = (long long)nx * ny;
-            const long long xm = x > 0 ? i - 1 : i, xp = x < nx - 1 ? i + 1 : i;
-            const long long ym = y > 0 ? i - sy : i, yp = y < ny - 1 ? i + sy : i;
-            const long long zm = z > 0 ? i - sz : i, zp = z < nz - 1 ? i + sz : i;
-            const T wx = (T)a.ph.wx, wy = (T)a.ph.wy, wz = (T)a.ph.wz;
+            const int x = i & (P.nx - 1);
+            const int y = (i >> P.lgnx) & (P.ny - 1);
+            const int z = i >> (P.lgnx + P.lgny);
+            const int sy = P.nx, sz = P.nx * P.ny;
+            const int xm = x > 0 ? i - 1 : i, xp = x < P.nx - 1 ? i + 1 : i;
+            const int ym = y > 0 ? i - sy : i, yp = y < P.ny - 1 ? i + sy : i;
+            const int zm = z > 0 ? i - sz : i, zp = z < P.nz - 1 ? i + sz : i;
             T m[3], H[3];
+#pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const T *Yc = Y + c * n;
                 const T cen = Yc[i];
                 m[c] = cen;
-                H[c] = wx * (Yc[xp] - 2 * cen + Yc[xm]) + wy * (Yc[yp] - 2 * cen + Yc[ym]) +
-                       wz * (Yc[zp] - 2 * cen + Yc[zm]);
+                H[c] = P.wx * (Yc[xp] - 2 * cen + Yc[xm]) + P.wy * (Yc[yp] - 2 * cen + Yc[ym]) +
+                       P.wz * (Yc[zp] - 2 * cen + Yc[zm]);
             }
-            const T mu = (T)(m[0] * (T)a.ph.ku[0] + m[1] * (T)a.ph.ku[1] + m[2] * (T)a.ph.ku[2]);
+            const T mu = m[0] * P.ku[0] + m[1] * P.ku[1] + m[2] * P.ku[2];
             T g[3] = {0, 0, 0};
             if (ext) {
                 for (int j = 0; j < np1; ++j) {
                     const T *Gj = a.hist + (size_t)j * fstride;
-                    const T w = (T)s_w[j];
+                    const T w = s_w[j];
+#pragma unroll
                     for (int c = 0; c < 3; ++c) g[c] += w * Gj[c * n + i];
                 }
             } else {
                 const T *Gk = (k == 0 && a.ctl.p >= 0) ? a.hist + (size_t)head * fstride : a.G;
+#pragma unroll
                 for (int c = 0; c < 3; ++c) g[c] = Gk[c * n + i];
             }
-            for (int c = 0; c < 3; ++c)
-                H[c] += (T)a.ph.can * mu * (T)a.ph.ku[c] + g[c] - (T)a.ph.msN00[c] * m[c] + (T)s_H[c];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) H[c] += P.can * mu * P.ku[c] + g[c] - P.msN00[c] * m[c] + s_H[c];
             // Eq. 1 in Landau-Lifshitz form: F = -gp (m x H + alpha m x (m x H))
             const T cxh0 = m[1] * H[2] - m[2] * H[1];
             const T cxh1 = m[2] * H[0] - m[0] * H[2];
@@ -611,67 +636,69 @@ __global__ void __launch_bounds__(ST_THREADS) k_stage(const StageArgs<T> a)
             const T dd0 = m[1] * cxh2 - m[2] * cxh1;
             const T dd1 = m[2] * cxh0 - m[0] * cxh2;
             const T dd2 = m[0] * cxh1 - m[1] * cxh0;
-            const T gp = (T)a.ph.gp, al = (T)a.ph.alpha;
-            f[0] = -gp * (cxh0 + al * dd0);
-            f[1] = -gp * (cxh1 + al * dd1);
-            f[2] = -gp * (cxh2 + al * dd2);
+            f[0] = -P.gp * (cxh0 + P.alpha * dd0);
+            f[1] = -P.gp * (cxh1 + P.alpha * dd1);
+            f[2] = -P.gp * (cxh2 + P.alpha * dd2);
+#pragma unroll
             for (int c = 0; c < 3; ++c) Fk[c * n + i] = f[c];
         }
     }
     if (!a.last) {
         // Eq. 4: Y_{k+1} = m0 + h sum_{l<=k} b_{k+1,l} F_l
         if (valid) {
-            T *Yn = ((k + 1) & 1) ? a.Y1 : a.Y0;
-            const double *brow = a.tab.b[k + 1];
-            for (int c = 0; c < 3; ++c) {
-                T acc = m0[c * n + i];
-                for (int l = 0; l < k; ++l) {
-                    if (brow[l] == 0.0) continue;
-                    const T *Fl = a.F + (size_t)((fbase + l) % ns) * fstride;
-                    acc += (T)(h * brow[l]) * Fl[c * n + i];
-                }
-                acc += (T)(h * brow[k]) * f[c];
-                Yn[c * n + i] = acc;
+            T acc[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[c] = m0[c * n + i] + s_cb[k] * f[c];
+            for (int l = 0; l < k; ++l) {
+                if (a.tab.b[k + 1][l] == 0.0) continue;
+                const T *Fl = a.F + (size_t)((fbase + l) % ns) * fstride;
+                const T co = s_cb[l];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[c] += co * Fl[c * n + i];
             }
+            T *Yn = ((k + 1) & 1) ? a.Y1 : a.Y0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Yn[c * n + i] = acc[c];
         }
         if (ext && blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
         return;
     }
     // Eq. 3: propagated solution, embedded difference, renormalisation
-    double err = 0.0;
+    T err = 0;
     if (valid) {
         T M[3], E[3];
-        const int s = a.tab.s;
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
-            T acc = m0[c * n + i], ea = 0;
-            for (int l = 0; l < s - 1; ++l) {
-                const double cl = a.tab.c[l], el = a.tab.e[l];
-                if (cl == 0.0 && el == 0.0) continue;
-                const T *Fl = a.F + (size_t)((fbase + l) % ns) * fstride;
+            M[c] = m0[c * n + i] + s_cb[s - 1] * f[c];
+            E[c] = s_ce[s - 1] * f[c];
+        }
+        for (int l = 0; l < s - 1; ++l) {
+            if (a.tab.c[l] == 0.0 && a.tab.e[l] == 0.0) continue;
+            const T *Fl = a.F + (size_t)((fbase + l) % ns) * fstride;
+            const T cc = s_cb[l], ce = s_ce[l];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
                 const T v = Fl[c * n + i];
-                acc += (T)(h * cl) * v;
-                ea += (T)(h * el) * v;
+                M[c] += cc * v;
+                E[c] += ce * v;
             }
-            acc += (T)(h * a.tab.c[s - 1]) * f[c];
-            ea += (T)(h * a.tab.e[s - 1]) * f[c];
-            M[c] = acc;
-            E[c] = ea;
         }
         const T r = sqrt(M[0] * M[0] + M[1] * M[1] + M[2] * M[2]);
+        const T inv = (T)1 / r;
         T *mo = cur ? a.m0 : a.m1;
-        for (int c = 0; c < 3; ++c) mo[c * n + i] = M[c] / r;
-        err = (double)sqrt(E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
-        if (!(err <= 1.7976931348623157e308)) err = INFINITY;
-        if (!(r == r) || r == (T)0) err = INFINITY;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) mo[c * n + i] = M[c] * inv;
+        err = sqrt(E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
+        if (!(err <= (T)3.0e38) || !(r == r) || r == (T)0) err = (T)INFINITY;
     }
     if (ext && blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
     for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
     if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = err;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double mx = 0.0;
+        T mx = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, s_red[w]);
-        atomicMax(&st->err_bits, (unsigned long long)__double_as_longlong(mx));
+        atomicMax(&st->err_bits, (unsigned long long)__double_as_longlong((double)mx));
         __threadfence();
         const unsigned prev = atomicAdd(&st->blocks_done, 1u);
         s_last = (prev == gridDim.x - 1) ? 1 : 0;
@@ -776,6 +803,21 @@ void stage_t(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime, cudaGraph
     a.st = c->st;
     a.tab = c->tab;
     a.ph = c->ph;
+    a.pt.wx = (T)c->ph.wx;
+    a.pt.wy = (T)c->ph.wy;
+    a.pt.wz = (T)c->ph.wz;
+    a.pt.can = (T)c->ph.can;
+    a.pt.gp = (T)c->ph.gp;
+    a.pt.alpha = (T)c->ph.alpha;
+    for (int q = 0; q < 3; ++q) {
+        a.pt.ku[q] = (T)c->ph.ku[q];
+        a.pt.msN00[q] = (T)c->ph.msN00[q];
+    }
+    a.pt.nx = c->nx;
+    a.pt.ny = c->ny;
+    a.pt.nz = c->nz;
+    a.pt.lgnx = __builtin_ctz(c->nx);
+    a.pt.lgny = __builtin_ctz(c->ny);
     a.ctl = c->ctl;
     a.ctl.prime = prime;
     a.k = k;

@@ -141,6 +141,7 @@ std::string validate(const mmx_mesh *mesh, const mmx_material *mat, const mmx_fi
         return "mesh sizes must be powers of two";
     if (mesh->nx < 2) return "nx must be at least 2";
     if (mesh->nx > 2048 || mesh->ny > 2048 || mesh->nz > 2048) return "mesh side above 2048 cells";
+    if (3.0 * mesh->nx * mesh->ny * mesh->nz >= 2147483647.0) return "mesh above 2^31/3 cells";
     if (!finite_pos(mesh->dx) || !finite_pos(mesh->dy) || !finite_pos(mesh->dz)) return "cell sizes must be > 0";
     if (!finite_pos(mat->Ms) || !finite_pos(mat->gamma)) return "Ms and gamma must be > 0";
     if (!std::isfinite(mat->A) || mat->A < 0 || !std::isfinite(mat->alpha) || mat->alpha < 0 || !std::isfinite(mat->K))
