@@ -11,6 +11,17 @@
 #define MMX_MAXP 6
 #define MMX_NHIST (MMX_MAXP + 1)
 
+// Coefficients of one stage for the current attempt, prepared by one warp
+// (at the end of the previous attempt, or before the first one) so that the
+// stage kernels do no FP64 arithmetic.
+struct StageCoef {
+    double cb[MMX_MAXS];   // h b_{k+1,l}; at the last stage h c_l
+    double ce[MMX_MAXS];   // at the last stage h (c_l - c_hat_l)
+    double w[MMX_NHIST];   // Eq. 6 Lagrange weights at t0 + a_k h
+    double H[3];           // applied field at t0 + a_k h
+    float cbf[MMX_MAXS], cef[MMX_MAXS], wf[MMX_NHIST], Hf[3];
+};
+
 // Integrator state kept in device memory; kernels read it at launch and the
 // controller (last block of the last stage) updates it.  Everything the host
 // needs to resume a run lives here.
@@ -37,6 +48,7 @@ struct DevState {
     long long attempt_limit;  // attempts allowed in the current run
     long long run_attempts;
     unsigned long long t_start_ns, time_limit_ns;
+    StageCoef coef[MMX_MAXS];
 };
 
 struct TabArgs {
@@ -113,3 +125,5 @@ void mmxk_demag(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int 
                 const void *src, int dst_mode, void *dst, const void *self_src);
 void mmxk_stage(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime_graph,
                 cudaGraphConditionalHandle cond, int use_cond);
+// fills DevState::coef for the attempt described by the device state
+void mmxk_prepare(mmx_ctx *c, cudaStream_t s);

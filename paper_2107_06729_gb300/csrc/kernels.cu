@@ -451,6 +451,67 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
+// One warp fills the per-stage coefficients of the attempt that starts at
+// (st->t, st->h): Eq. 4 row weights times h, Eq. 3 weights times h, Eq. 6
+// Lagrange weights (when the history is primed) and the applied field.
+__device__ void prepare_coefs(DevState *st, const TabArgs &tab, const PhysArgs &ph, int p, int lane)
+{
+    const double h = st->h, t0 = st->t;
+    const int s = tab.s;
+    for (int it = lane; it < MMX_MAXS * MMX_MAXS; it += 32) {
+        const int k = it / MMX_MAXS, l = it % MMX_MAXS;
+        StageCoef &C = st->coef[k];
+        double cb = 0.0, ce = 0.0;
+        if (k < s) {
+            if (k == s - 1) {
+                cb = h * tab.c[l];
+                ce = h * tab.e[l];
+            } else {
+                cb = h * tab.b[k + 1][l];
+            }
+        }
+        C.cb[l] = cb;
+        C.ce[l] = ce;
+        C.cbf[l] = (float)cb;
+        C.cef[l] = (float)ce;
+    }
+    const int np1 = p + 1;
+    const bool primed = p >= 0 && st->hist_n >= np1;
+    for (int it = lane; it < MMX_MAXS * MMX_NHIST; it += 32) {
+        const int k = it / MMX_NHIST, j = it % MMX_NHIST;
+        double w = 0.0;
+        if (primed && k < s && j < np1) {
+            const double tau = tab.a[k] * h;
+            const double tj = st->hist_t[j] - t0;
+            double num = 1.0, den = 1.0;
+            for (int q = 0; q < np1; ++q)
+                if (q != j) {
+                    const double tq = st->hist_t[q] - t0;
+                    num *= tau - tq;
+                    den *= tj - tq;
+                }
+            w = num / den;
+        }
+        st->coef[k].w[j] = w;
+        st->coef[k].wf[j] = (float)w;
+    }
+    for (int k = lane; k < MMX_MAXS; k += 32) {
+        const double tk = t0 + tab.a[k] * h;
+        const bool on = (tk >= ph.t_on) && (tk < ph.t_off);
+        for (int c = 0; c < 3; ++c) {
+            const double v = ph.H0[c] + (on ? ph.pulse[c] : 0.0);
+            st->coef[k].H[c] = v;
+            st->coef[k].Hf[c] = (float)v;
+        }
+    }
+}
+
+__global__ void k_prepare(DevState *st, const TabArgs tab, const PhysArgs ph, int p)
+{
+    if (st->done) return;
+    prepare_coefs(st, tab, ph, p, threadIdx.x);
+}
+
 template <typename T> __device__ void controller(const StageArgs<T> &a)
 {
     DevState *st = a.st;
@@ -553,35 +614,14 @@ __global__ void __launch_bounds__(ST_THREADS) k_stage(const StageArgs<T> a)
     const int np1 = a.ctl.p + 1;
     const int s = a.tab.s;
     if (threadIdx.x < 32) {
-        // per-CTA set-up in FP64 (time, step, weights), used in T below
-        const double h = st->h, t0 = st->t;
+        const StageCoef &C = st->coef[k];
         const int l = threadIdx.x;
-        if (l == 0) {
-            const double tk = t0 + a.tab.a[k] * h;
-            const bool on = (tk >= a.ph.t_on) && (tk < a.ph.t_off);
-            for (int c = 0; c < 3; ++c) s_H[c] = (T)(a.ph.H0[c] + (on ? a.ph.pulse[c] : 0.0));
-        }
         if (l < MMX_MAXS) {
-            if (a.last) {
-                s_cb[l] = (T)(h * a.tab.c[l]);
-                s_ce[l] = (T)(h * a.tab.e[l]);
-            } else {
-                s_cb[l] = (T)(h * a.tab.b[k + 1][l]);
-                s_ce[l] = (T)0;
-            }
+            s_cb[l] = (sizeof(T) == 4) ? (T)C.cbf[l] : (T)C.cb[l];
+            s_ce[l] = (sizeof(T) == 4) ? (T)C.cef[l] : (T)C.ce[l];
         }
-        if (ext && l < np1) {
-            // Eq. 6: Lagrange basis at tau = a_k h over the stored times
-            const double tau = a.tab.a[k] * h;
-            const double tj = st->hist_t[l] - t0;
-            double w = 1.0;
-            for (int q = 0; q < np1; ++q)
-                if (q != l) {
-                    const double tq = st->hist_t[q] - t0;
-                    w *= (tau - tq) / (tj - tq);
-                }
-            s_w[l] = (T)w;
-        }
+        if (l < MMX_NHIST) s_w[l] = (sizeof(T) == 4) ? (T)C.wf[l] : (T)C.w[l];
+        if (l < 3) s_H[l] = (sizeof(T) == 4) ? (T)C.Hf[l] : (T)C.H[l];
     }
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -704,9 +744,14 @@ __global__ void __launch_bounds__(ST_THREADS) k_stage(const StageArgs<T> a)
         s_last = (prev == gridDim.x - 1) ? 1 : 0;
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        __threadfence();
-        controller(a);
+    if (s_last) {
+        if (threadIdx.x == 0) {
+            __threadfence();
+            controller(a);
+            __threadfence();
+        }
+        __syncthreads();
+        if (threadIdx.x < 32 && !st->done) prepare_coefs(st, a.tab, a.ph, a.ctl.p, threadIdx.x);
     }
 }
 
@@ -886,6 +931,12 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
 }
 
 }  // namespace
+
+void mmxk_prepare(mmx_ctx *c, cudaStream_t s)
+{
+    k_prepare<<<1, 32, 0, s>>>(c->st, c->tab, c->ph, c->ctl.p);
+    c->launches++;
+}
 
 size_t mmxk_yz_smem_bytes(const mmx_ctx *c)
 {

@@ -481,6 +481,7 @@ static int run_common(mmx_ctx *c, double t_end, long long acc_more)
     s.loop_more = 1;
     rc = write_state(c);
     if (rc) return rc;
+    mmxk_prepare(c, c->stream);
     for (int guard = 0; guard < 1000; ++guard) {
         const int p = c->ctl.p;
         const int which = (p >= 0 && s.hist_n < p + 1) ? 1 : 0;
