@@ -77,6 +77,7 @@ struct CtlArgs {
     int nslots;    // stage-derivative slots
     int prime;     // this graph primes the history: stop once primed
     double tol, hmin, hmax, cmin, cmax, safety;
+    double cmin_pow, cmax_pow;  // cmin^(n+1), cmax^(n+1): clamp limits of Eq. 5
 };
 
 struct mmx_ctx {

@@ -28,6 +28,7 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "internal.h"
@@ -214,11 +215,20 @@ template <typename T> struct XArgs {
 };
 
 constexpr int X_THREADS = 128;
-constexpr int X_ITEMS = 4;
 constexpr int YZ_THREADS = 256;
-constexpr int YZ_ITEMS = 2;
 
-template <typename T>
+// Items per thread of one FFT stage: a window of threads*items work items
+// must hold all items of one transform; the largest stage has L/4 of them
+// (L/2 only for L = 2).
+int items_for(int L, int threads)
+{
+    const int per = L <= 2 ? 1 : L / 4;
+    int it = 1;
+    while (threads * it < per) it *= 2;
+    return it;
+}
+
+template <typename T, int ITEMS>
 __global__ void __launch_bounds__(X_THREADS) k_xf(const XArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -240,7 +250,7 @@ __global__ void __launch_bounds__(X_THREADS) k_xf(const XArgs<T> a)
     }
     __syncthreads();
     FftShape f{Px, np, 0, Px, 0, 1};
-    fft_smem<T, false, X_ITEMS>(sm, f, a.tw, true, false);
+    fft_smem<T, false, ITEMS>(sm, f, a.tw, true, false);
     // separate the two real rows and pack kx = 0 with kx = nx
     const int T_ = a.trows;
     for (int idx = threadIdx.x; idx < nx * T_; idx += blockDim.x) {
@@ -261,7 +271,7 @@ __global__ void __launch_bounds__(X_THREADS) k_xf(const XArgs<T> a)
     }
 }
 
-template <typename T>
+template <typename T, int ITEMS>
 __global__ void __launch_bounds__(X_THREADS) k_xi(const XArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -292,7 +302,7 @@ __global__ void __launch_bounds__(X_THREADS) k_xi(const XArgs<T> a)
     }
     __syncthreads();
     FftShape f{Px, np, 0, Px, 0, 1};
-    fft_smem<T, true, X_ITEMS>(sm, f, a.tw, false, true);
+    fft_smem<T, true, ITEMS>(sm, f, a.tw, false, true);
     T *out = a.dst_mode == 1 ? a.hist + (size_t)head * 3 * a.n : a.dst;
     const int T_ = a.trows, lgnx = ilog2(nx);
     for (int idx = threadIdx.x; idx < T_ * nx; idx += blockDim.x) {
@@ -343,7 +353,7 @@ __device__ __forceinline__ void apply_K(const T k[6], cx<T> mx, cx<T> my, cx<T> 
     hz = mk(k[4] * mx.x + k[5] * my.x + k[2] * mz.x, k[4] * mx.y + k[5] * my.y + k[2] * mz.y);
 }
 
-template <typename T>
+template <typename T, int ITEMS>
 __global__ void __launch_bounds__(YZ_THREADS) k_yz(const YZArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -364,8 +374,8 @@ __global__ void __launch_bounds__(YZ_THREADS) k_yz(const YZArgs<T> a)
     __syncthreads();
     const FftShape fy{Py, 3 * nz, lgnz, plane, Py, 1};
     const FftShape fz{Pz, 3 * Py, lgPy, plane, 1, Py};
-    if (Py > 1) fft_smem<T, false, YZ_ITEMS>(B, fy, a.twy, true, false);
-    if (Pz > 1) fft_smem<T, false, YZ_ITEMS>(B, fz, a.twz, true, false);
+    if (Py > 1) fft_smem<T, false, ITEMS>(B, fy, a.twy, true, false);
+    if (Pz > 1) fft_smem<T, false, ITEMS>(B, fz, a.twz, true, false);
 
     // Fourier-space tensor multiply (Eq. 2): H = K M, K real symmetric
     if (kx != 0) {
@@ -414,8 +424,8 @@ __global__ void __launch_bounds__(YZ_THREADS) k_yz(const YZArgs<T> a)
         }
     }
     __syncthreads();
-    if (Pz > 1) fft_smem<T, true, YZ_ITEMS>(B, fz, a.twz, false, true);
-    if (Py > 1) fft_smem<T, true, YZ_ITEMS>(B, fy, a.twy, false, true);
+    if (Pz > 1) fft_smem<T, true, ITEMS>(B, fz, a.twz, false, true);
+    if (Py > 1) fft_smem<T, true, ITEMS>(B, fy, a.twy, false, true);
     for (int r = threadIdx.x; r < rows; r += blockDim.x) {
         const int y = r & (ny - 1), cz = r >> lgny, z = cz & (nz - 1), c = cz >> lgnz;
         S[r] = B[c * plane + z * Py + y];
@@ -451,14 +461,53 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// One warp fills the per-stage coefficients of the attempt that starts at
-// (st->t, st->h): Eq. 4 row weights times h, Eq. 3 weights times h, Eq. 6
-// Lagrange weights (when the history is primed) and the applied field.
-__device__ void prepare_coefs(DevState *st, const TabArgs &tab, const PhysArgs &ph, int p, int lane)
+// Reciprocal in FP64 from an FP32 seed and two Newton steps (relative error
+// at the FP64 rounding level for |v| in the FP32 range).
+__device__ __forceinline__ double recip64(double v)
 {
+    double r = (double)(1.0f / (float)v);
+    r = r * (2.0 - v * r);
+    r = r * (2.0 - v * r);
+    return r;
+}
+
+// x^(1/n1) for x in (cmin^n1, cmax^n1): FP32 seed, two Newton steps in FP64.
+__device__ __forceinline__ double root64(double x, int n1)
+{
+    double c = (double)exp2f(log2f((float)x) / (float)n1);
+    for (int it = 0; it < 2; ++it) {
+        double cp = 1.0;
+        for (int q = 0; q < n1 - 1; ++q) cp *= c;          // c^(n1-1)
+        const double f = cp * c - x;
+        const double d = (double)(1.0f / ((float)n1 * (float)cp));
+        c = c - f * d;
+    }
+    return c;
+}
+
+// The threads of one CTA fill the per-stage coefficients of the attempt that
+// starts at (st->t, st->h): Eq. 4 row weights times h, Eq. 3 weights times h,
+// Eq. 6 Lagrange weights (once the history is primed) and the applied field.
+// Lagrange weights: w_kj = prod_{q!=j} (a_k - s_q) / prod_{q!=j} (s_j - s_q)
+// with s_q = (t_q - t0)/h, the FP64 differences taken first.
+__device__ void prepare_coefs(DevState *st, const TabArgs &tab, const PhysArgs &ph, int p, double *sm_sig,
+                              double *sm_iden)
+{
+    const int tid = threadIdx.x;
     const double h = st->h, t0 = st->t;
     const int s = tab.s;
-    for (int it = lane; it < MMX_MAXS * MMX_MAXS; it += 32) {
+    const int np1 = p + 1;
+    const bool primed = p >= 0 && st->hist_n >= np1;
+    if (primed && tid < np1) sm_sig[tid] = (st->hist_t[tid] - t0) * recip64(h);
+    __syncthreads();
+    if (primed && tid < np1) {
+        double den = 1.0;
+        for (int q = 0; q < np1; ++q)
+            if (q != tid) den *= sm_sig[tid] - sm_sig[q];
+        sm_iden[tid] = recip64(den);
+    }
+    __syncthreads();
+    for (int it = tid; it < MMX_MAXS * MMX_MAXS; it += blockDim.x) {
         const int k = it / MMX_MAXS, l = it % MMX_MAXS;
         StageCoef &C = st->coef[k];
         double cb = 0.0, ce = 0.0;
@@ -475,27 +524,18 @@ __device__ void prepare_coefs(DevState *st, const TabArgs &tab, const PhysArgs &
         C.cbf[l] = (float)cb;
         C.cef[l] = (float)ce;
     }
-    const int np1 = p + 1;
-    const bool primed = p >= 0 && st->hist_n >= np1;
-    for (int it = lane; it < MMX_MAXS * MMX_NHIST; it += 32) {
+    for (int it = tid; it < MMX_MAXS * MMX_NHIST; it += blockDim.x) {
         const int k = it / MMX_NHIST, j = it % MMX_NHIST;
         double w = 0.0;
         if (primed && k < s && j < np1) {
-            const double tau = tab.a[k] * h;
-            const double tj = st->hist_t[j] - t0;
-            double num = 1.0, den = 1.0;
+            w = sm_iden[j];
             for (int q = 0; q < np1; ++q)
-                if (q != j) {
-                    const double tq = st->hist_t[q] - t0;
-                    num *= tau - tq;
-                    den *= tj - tq;
-                }
-            w = num / den;
+                if (q != j) w *= tab.a[k] - sm_sig[q];
         }
         st->coef[k].w[j] = w;
         st->coef[k].wf[j] = (float)w;
     }
-    for (int k = lane; k < MMX_MAXS; k += 32) {
+    for (int k = tid; k < MMX_MAXS; k += blockDim.x) {
         const double tk = t0 + tab.a[k] * h;
         const bool on = (tk >= ph.t_on) && (tk < ph.t_off);
         for (int c = 0; c < 3; ++c) {
@@ -508,8 +548,9 @@ __device__ void prepare_coefs(DevState *st, const TabArgs &tab, const PhysArgs &
 
 __global__ void k_prepare(DevState *st, const TabArgs tab, const PhysArgs ph, int p)
 {
+    __shared__ double sm_sig[MMX_NHIST], sm_iden[MMX_NHIST];
     if (st->done) return;
-    prepare_coefs(st, tab, ph, p, threadIdx.x);
+    prepare_coefs(st, tab, ph, p, sm_sig, sm_iden);
 }
 
 template <typename T> __device__ void controller(const StageArgs<T> &a)
@@ -536,10 +577,16 @@ template <typename T> __device__ void controller(const StageArgs<T> &a)
         }
         double hnew = st->h_ctrl;
         if (adaptive) {
+            // Eq. 5: c = clamp((safety e_max / e)^(1/(n+1)), cmin, cmax)
             double cf = a.ctl.cmax;
             if (e > 0) {
-                cf = pow(a.ctl.safety * a.ctl.tol / e, 1.0 / (a.tab.order + 1));
-                cf = fmin(fmax(cf, a.ctl.cmin), a.ctl.cmax);
+                const double x = a.ctl.safety * a.ctl.tol * recip64(e);
+                if (x <= a.ctl.cmin_pow)
+                    cf = a.ctl.cmin;
+                else if (x >= a.ctl.cmax_pow)
+                    cf = a.ctl.cmax;
+                else
+                    cf = fmin(fmax(root64(x, a.tab.order + 1), a.ctl.cmin), a.ctl.cmax);
             }
             hnew = fmin(fmax(h * cf, a.ctl.hmin), a.ctl.hmax);
         }
@@ -593,7 +640,7 @@ template <typename T> __device__ void controller(const StageArgs<T> &a)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(ST_THREADS) k_stage(const StageArgs<T> a)
+__global__ void __launch_bounds__(ST_THREADS, 2) k_stage(const StageArgs<T> a)
 {
     __shared__ T s_w[MMX_NHIST];       // Eq. 6 weights
     __shared__ T s_H[3];               // applied field at t0 + a_k h
@@ -601,6 +648,7 @@ __global__ void __launch_bounds__(ST_THREADS) k_stage(const StageArgs<T> a)
     __shared__ T s_ce[MMX_MAXS];       // h (c_l - c_hat_l) (last stage)
     __shared__ T s_red[ST_THREADS / 32];
     __shared__ int s_last;
+    __shared__ double s_sig[MMX_NHIST], s_iden[MMX_NHIST];
     DevState *st = a.st;
     if (st->done) {
         if (a.last && a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
@@ -631,9 +679,34 @@ __global__ void __launch_bounds__(ST_THREADS) k_stage(const StageArgs<T> a)
     T *Fk = a.F + (size_t)((fbase + k) % ns) * fstride;
     const T *m0 = cur ? a.m1 : a.m0;
     const PhysT<T> &P = a.pt;
+    const bool last = a.last != 0;
+    // Part of Eq. 4 (next stage input) or Eq. 3 (solution, embedded
+    // difference) that does not involve F_k: issued first so that these
+    // loads overlap the field evaluation.
+    T acc[3] = {0, 0, 0}, E[3] = {0, 0, 0};
+    if (valid) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] = m0[c * n + i];
+        const int lmax = last ? s - 1 : k;
+#pragma unroll
+        for (int l = 0; l < MMX_MAXS - 1; ++l) {
+            if (l >= lmax) break;
+            const bool use = last ? (a.tab.c[l] != 0.0 || a.tab.e[l] != 0.0) : (a.tab.b[k + 1][l] != 0.0);
+            if (!use) continue;
+            const T *Fl = a.F + (size_t)((fbase + l) % ns) * fstride;
+            const T cb = s_cb[l], ce = s_ce[l];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const T v = Fl[c * n + i];
+                acc[c] += cb * v;
+                if (last) E[c] += ce * v;
+            }
+        }
+    }
     T f[3] = {0, 0, 0};
     if (valid) {
         if (f1v) {
+#pragma unroll
             for (int c = 0; c < 3; ++c) f[c] = Fk[c * n + i];
         } else {
             const T *Y = (k == 0) ? m0 : ((k & 1) ? a.Y1 : a.Y0);
@@ -653,10 +726,11 @@ __global__ void __launch_bounds__(ST_THREADS) k_stage(const StageArgs<T> a)
                 H[c] = P.wx * (Yc[xp] - 2 * cen + Yc[xm]) + P.wy * (Yc[yp] - 2 * cen + Yc[ym]) +
                        P.wz * (Yc[zp] - 2 * cen + Yc[zm]);
             }
-            const T mu = m[0] * P.ku[0] + m[1] * P.ku[1] + m[2] * P.ku[2];
             T g[3] = {0, 0, 0};
             if (ext) {
-                for (int j = 0; j < np1; ++j) {
+#pragma unroll
+                for (int j = 0; j < MMX_NHIST; ++j) {
+                    if (j >= np1) break;
                     const T *Gj = a.hist + (size_t)j * fstride;
                     const T w = s_w[j];
 #pragma unroll
@@ -667,6 +741,7 @@ __global__ void __launch_bounds__(ST_THREADS) k_stage(const StageArgs<T> a)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) g[c] = Gk[c * n + i];
             }
+            const T mu = m[0] * P.ku[0] + m[1] * P.ku[1] + m[2] * P.ku[2];
 #pragma unroll
             for (int c = 0; c < 3; ++c) H[c] += P.can * mu * P.ku[c] + g[c] - P.msN00[c] * m[c] + s_H[c];
             // Eq. 1 in Landau-Lifshitz form: F = -gp (m x H + alpha m x (m x H))
@@ -683,22 +758,12 @@ __global__ void __launch_bounds__(ST_THREADS) k_stage(const StageArgs<T> a)
             for (int c = 0; c < 3; ++c) Fk[c * n + i] = f[c];
         }
     }
-    if (!a.last) {
+    if (!last) {
         // Eq. 4: Y_{k+1} = m0 + h sum_{l<=k} b_{k+1,l} F_l
         if (valid) {
-            T acc[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) acc[c] = m0[c * n + i] + s_cb[k] * f[c];
-            for (int l = 0; l < k; ++l) {
-                if (a.tab.b[k + 1][l] == 0.0) continue;
-                const T *Fl = a.F + (size_t)((fbase + l) % ns) * fstride;
-                const T co = s_cb[l];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) acc[c] += co * Fl[c * n + i];
-            }
             T *Yn = ((k + 1) & 1) ? a.Y1 : a.Y0;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) Yn[c * n + i] = acc[c];
+            for (int c = 0; c < 3; ++c) Yn[c * n + i] = acc[c] + s_cb[k] * f[c];
         }
         if (ext && blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
         return;
@@ -706,22 +771,11 @@ __global__ void __launch_bounds__(ST_THREADS) k_stage(const StageArgs<T> a)
     // Eq. 3: propagated solution, embedded difference, renormalisation
     T err = 0;
     if (valid) {
-        T M[3], E[3];
+        T M[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            M[c] = m0[c * n + i] + s_cb[s - 1] * f[c];
-            E[c] = s_ce[s - 1] * f[c];
-        }
-        for (int l = 0; l < s - 1; ++l) {
-            if (a.tab.c[l] == 0.0 && a.tab.e[l] == 0.0) continue;
-            const T *Fl = a.F + (size_t)((fbase + l) % ns) * fstride;
-            const T cc = s_cb[l], ce = s_ce[l];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const T v = Fl[c * n + i];
-                M[c] += cc * v;
-                E[c] += ce * v;
-            }
+            M[c] = acc[c] + s_cb[s - 1] * f[c];
+            E[c] += s_ce[s - 1] * f[c];
         }
         const T r = sqrt(M[0] * M[0] + M[1] * M[1] + M[2] * M[2]);
         const T inv = (T)1 / r;
@@ -751,7 +805,7 @@ __global__ void __launch_bounds__(ST_THREADS) k_stage(const StageArgs<T> a)
             __threadfence();
         }
         __syncthreads();
-        if (threadIdx.x < 32 && !st->done) prepare_coefs(st, a.tab, a.ph, a.ctl.p, threadIdx.x);
+        if (!st->done) prepare_coefs(st, a.tab, a.ph, a.ctl.p, s_sig, s_iden);
     }
 }
 
@@ -829,9 +883,22 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
             c->prof_n[cls]++;
         }
     };
-    timed(0, [&] { k_xf<T><<<xgrid, X_THREADS, xs, s>>>(xa); });
-    timed(1, [&] { k_yz<T><<<c->nx, YZ_THREADS, ys, s>>>(ya); });
-    timed(2, [&] { k_xi<T><<<xgrid, X_THREADS, xs, s>>>(xa); });
+    const int xi = items_for(c->Px, X_THREADS);
+    const int yi = std::max(items_for(c->Py, YZ_THREADS), items_for(c->Pz, YZ_THREADS));
+    timed(0, [&] {
+        if (xi == 1) k_xf<T, 1><<<xgrid, X_THREADS, xs, s>>>(xa);
+        else if (xi == 2) k_xf<T, 2><<<xgrid, X_THREADS, xs, s>>>(xa);
+        else k_xf<T, 4><<<xgrid, X_THREADS, xs, s>>>(xa);
+    });
+    timed(1, [&] {
+        if (yi == 1) k_yz<T, 1><<<c->nx, YZ_THREADS, ys, s>>>(ya);
+        else k_yz<T, 2><<<c->nx, YZ_THREADS, ys, s>>>(ya);
+    });
+    timed(2, [&] {
+        if (xi == 1) k_xi<T, 1><<<xgrid, X_THREADS, xs, s>>>(xa);
+        else if (xi == 2) k_xi<T, 2><<<xgrid, X_THREADS, xs, s>>>(xa);
+        else k_xi<T, 4><<<xgrid, X_THREADS, xs, s>>>(xa);
+    });
 }
 
 template <typename T>
@@ -917,16 +984,17 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
     if (cudaMemcpy(c->twz, tw.data(), c->Pz * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
     const int trows = pick_trows(c);
     const size_t xs = x_smem<T>(c, trows), ys = yz_smem<T>(c);
-    if (xs > 48 * 1024) {
-        if (cudaFuncSetAttribute(k_xf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs) != cudaSuccess)
-            return MMX_ERR_CUDA;
-        if (cudaFuncSetAttribute(k_xi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs) != cudaSuccess)
-            return MMX_ERR_CUDA;
-    }
-    if (ys > 48 * 1024) {
-        if (cudaFuncSetAttribute(k_yz<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ys) != cudaSuccess)
-            return MMX_ERR_CUDA;
-    }
+    const void *xk[] = {(const void *)k_xf<T, 1>, (const void *)k_xf<T, 2>, (const void *)k_xf<T, 4>,
+                        (const void *)k_xi<T, 1>, (const void *)k_xi<T, 2>, (const void *)k_xi<T, 4>};
+    if (xs > 48 * 1024)
+        for (const void *f : xk)
+            if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs) != cudaSuccess)
+                return MMX_ERR_CUDA;
+    const void *yk[] = {(const void *)k_yz<T, 1>, (const void *)k_yz<T, 2>};
+    if (ys > 48 * 1024)
+        for (const void *f : yk)
+            if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ys) != cudaSuccess)
+                return MMX_ERR_CUDA;
     return 0;
 }
 
@@ -934,7 +1002,7 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
 
 void mmxk_prepare(mmx_ctx *c, cudaStream_t s)
 {
-    k_prepare<<<1, 32, 0, s>>>(c->st, c->tab, c->ph, c->ctl.p);
+    k_prepare<<<1, 256, 0, s>>>(c->st, c->tab, c->ph, c->ctl.p);
     c->launches++;
 }
 

@@ -352,6 +352,8 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     C.cmin = integ->cmin;
     C.cmax = integ->cmax;
     C.safety = integ->safety;
+    C.cmin_pow = std::pow(integ->cmin, md.order + 1);
+    C.cmax_pow = std::pow(integ->cmax, md.order + 1);
 
     // tensor and spectrum (host, binary128)
     mmx_host_tensor_args ta{c->nx, c->ny, c->nz, mesh->dx, mesh->dy, mesh->dz, mat->Ms};
