@@ -159,6 +159,35 @@ int mmx_load_state(mmx_ctx *ctx, const void *buf, size_t len);
 int mmx_set_profiling(mmx_ctx *ctx, int enable);
 int mmx_get_profile(mmx_ctx *ctx, double *ms, long long *launches);
 
+/* Allocation-free exact demag evaluation.  No counterpart in the paper: it
+ * serves callers that cannot allocate device memory, e.g. code running while
+ * its stream is being captured into a CUDA graph (cudaMalloc is not allowed
+ * there) or code in a process whose device memory belongs to another
+ * allocator, and who therefore cannot create a context with mmx_create.
+ * It computes the same field as mmx_demag (Eq. 2, self term included) for a
+ * mesh with saturation magnetisation Ms, with the same FFT kernels, but the
+ * tensor spectrum, the twiddle tables and the FFT scratch live in one
+ * file-scope device array of MMX_STATIC_SCRATCH_BYTES inside this library,
+ * which every GPU that loads the library holds until the process exits.
+ * m_dev and H_dev are device pointers of the given precision's element
+ * type, layout [3][nz][ny][nx]; H in A/m; the work is enqueued on
+ * cuda_stream (NULL = default stream).
+ *   - No device memory is allocated or freed, and no CUDA library or torch
+ *     routine that allocates is called.  The first call on a device looks up
+ *     the array's device address (cudaGetSymbolAddress), and the first call
+ *     for a new mesh, Ms or precision computes the Newell tensor on the host
+ *     (host memory only) and copies its spectrum into the array; make that
+ *     first call before any stream capture.  Later calls with the same
+ *     description reuse the spectrum the array still holds.
+ *   - Every call shares the array: calls that overlap on the GPU (other
+ *     streams, other host threads) race; serialise them.
+ *   - Meshes whose spectrum, tables and scratch exceed the array return
+ *     MMX_ERR_ARG (text from mmx_last_error(NULL)); the other errors are
+ *     those of mmx_create and mmx_demag. */
+#define MMX_STATIC_SCRATCH_BYTES (16u << 20)
+int mmx_demag_static(const mmx_mesh *mesh, double Ms, int precision, const void *m_dev, void *H_dev,
+                     void *cuda_stream);
+
 /* Text of the last error (never NULL; "" if none).  ctx may be NULL, then
  * the text of the last failed mmx_create of this thread is returned. */
 const char *mmx_last_error(const mmx_ctx *ctx);

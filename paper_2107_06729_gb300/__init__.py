@@ -80,6 +80,7 @@ SIGNATURES = {
     "mmx_load_state": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "mmx_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int]),
     "mmx_get_profile": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    "mmx_demag_static": (ctypes.c_int, [ctypes.POINTER(mmx_mesh), ctypes.c_double, ctypes.c_int, _VP, _VP, _VP]),
     "mmx_last_error": (ctypes.c_char_p, [_VP]),
     "mmx_destroy": (None, [_VP]),
 }
@@ -191,6 +192,13 @@ def mmx_get_profile(ctx):
     n = (ctypes.c_longlong * MMX_NPROF)()
     _check(lib().mmx_get_profile(ctx, ms, n), ctx)
     return {PROFILE_CLASSES[i]: (ms[i], n[i]) for i in range(MMX_NPROF)}
+
+
+def mmx_demag_static(mesh, Ms, precision, m_dev, H_dev, cuda_stream=None):
+    """Allocation-free exact demag (see include/mmx.h); mesh is an mmx_mesh."""
+    rc = lib().mmx_demag_static(ctypes.byref(mesh), float(Ms), int(precision), _ptr(m_dev), _ptr(H_dev),
+                                cuda_stream)
+    return _check(rc, None)
 
 
 def mmx_last_error(ctx=None):

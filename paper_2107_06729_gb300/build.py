@@ -14,7 +14,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmmx.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "mmx_api.cu", "tensor_host.cpp"]
+SOURCES = ["kernels.cu", "mmx_api.cu", "static_demag.cu", "tensor_host.cpp"]
 
 
 def _deps():

@@ -268,6 +268,8 @@ int run_loop(mmx_ctx *c, int which)
 
 }  // namespace
 
+void mmx_set_thread_error(const char *msg) { g_create_err = msg ? msg : ""; }
+
 extern "C" {
 
 int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *field, const mmx_integrator *integ,
