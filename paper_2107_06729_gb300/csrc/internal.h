@@ -99,6 +99,8 @@ struct mmx_ctx {
     CtlArgs ctl;
     // device buffers (element type per precision)
     void *m[2], *Y[2], *F, *G, *hist, *S, *K, *twx, *twy, *twz;
+    void *Tb;    // split y/z path: y spectrum [kx][c nz + z][Py] (complex)
+    bool split;  // the y-z column does not fit one CTA: YF, ZM, YI instead of YZ
     DevState *st;
     DevState *h_st;  // pinned host mirror
     // graphs: [0] main loop, [1] priming loop

@@ -432,6 +432,193 @@ __global__ void __launch_bounds__(YZ_THREADS) k_yz(const YZArgs<T> a)
     }
 }
 
+// ------------------------------------------------------- split y / z passes
+// For meshes whose padded y-z column does not fit one CTA (3 Py Pz complex
+// words), the YZ pass is split into three streaming kernels over the buffer
+// Tb[kx][c*nz + z][ky] (complex, Py per row):
+//   YF  forward y transform of each (kx, c, z) row (pruned).
+//   ZM  per (kx, tile of W ky values): forward z transform (pruned), tensor
+//       multiply, inverse z transform truncated to nz.
+//   YI  inverse y transform truncated to ny.
+// The packed kx = 0 column (u = X(kx=0) + i X(kx=nx), both real in y and z)
+// is separated along y in YF, using A(ky) = (U(ky) + conj U(-ky))/2 and
+// B(ky) = (U(ky) - conj U(-ky))/(2i), both Hermitian in ky: slot ky in
+// [1, Py/2) holds A(ky), slot Py - ky holds B(ky), slots 0 and Py/2 hold
+// the real pair (A, B) there.  ZM multiplies A by K(kx=0), B by K(kx=nx),
+// and the two real-pair slots by the packed rule along kz; YI recombines.
+template <typename T> struct SplitArgs {
+    cx<T> *S;      // [kx][c][z][y]
+    cx<T> *Tb;     // [kx][c*nz + z][ky]
+    const T *K;
+    const cx<T> *twy, *twz;
+    DevState *st;
+    long long rows;  // 3 ny nz
+    int nx, ny, nz, Py, Pz, Hy, Hz, stage0, ry, W;
+};
+
+template <typename T, int ITEMS>
+__global__ void __launch_bounds__(YZ_THREADS) k_yf(const SplitArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<T> *sm = reinterpret_cast<cx<T> *>(smraw);
+    if (a.st) {
+        if (a.st->done) return;
+        if (a.stage0 && a.st->f1_valid) return;
+    }
+    const int kx = blockIdx.x, Py = a.Py, ny = a.ny, lgny = ilog2(ny);
+    const int nrows = 3 * a.nz, r0 = blockIdx.y * a.ry;
+    const int nr = min(a.ry, nrows - r0);
+    const cx<T> *src = a.S + (size_t)kx * a.rows + (size_t)r0 * ny;
+    for (int idx = threadIdx.x; idx < nr * ny; idx += blockDim.x) {
+        const int r = idx >> lgny, y = idx & (ny - 1);
+        sm[r * Py + y] = src[idx];
+    }
+    __syncthreads();
+    const FftShape f{Py, nr, 0, Py, 0, 1};
+    fft_smem<T, false, ITEMS>(sm, f, a.twy, true, false);
+    cx<T> *dst = a.Tb + ((size_t)kx * nrows + r0) * Py;
+    const int lgPy = ilog2(Py), half = Py >> 1;
+    for (int idx = threadIdx.x; idx < nr * Py; idx += blockDim.x) {
+        const int r = idx >> lgPy, q = idx & (Py - 1);
+        const cx<T> *u = sm + r * Py;
+        cx<T> v;
+        if (kx != 0) {
+            v = u[q];
+        } else if (q == 0 || q == half) {
+            const cx<T> z = u[q];  // A and B real here
+            v = z;
+        } else if (q < half) {
+            const cx<T> z = u[q], zm = u[Py - q];
+            v = mk((T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y));  // A(q)
+        } else {
+            const int ky = Py - q;
+            const cx<T> z = u[ky], zm = u[q];
+            v = mk((T)0.5 * (z.y + zm.y), (T)0.5 * (zm.x - z.x));  // B(ky)
+        }
+        dst[idx] = v;
+    }
+}
+
+template <typename T, int ITEMS>
+__global__ void __launch_bounds__(YZ_THREADS) k_zm(const SplitArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<T> *B = reinterpret_cast<cx<T> *>(smraw);
+    if (a.st) {
+        if (a.st->done) return;
+        if (a.stage0 && a.st->f1_valid) return;
+    }
+    const int kx = blockIdx.x, W = a.W, ky0 = blockIdx.y * W;
+    const int nz = a.nz, Pz = a.Pz, Py = a.Py, lgW = ilog2(W), lgnz = ilog2(nz);
+    const int nrows = 3 * nz, plane = Pz * W;
+    const cx<T> *src = a.Tb + (size_t)kx * nrows * Py + ky0;
+    for (int idx = threadIdx.x; idx < nrows * W; idx += blockDim.x) {
+        const int r = idx >> lgW, w = idx & (W - 1);
+        const int c = r >> lgnz, z = r & (nz - 1);
+        B[c * plane + z * W + w] = src[(size_t)r * Py + w];
+    }
+    __syncthreads();
+    const FftShape fz{Pz, 3 * W, lgW, plane, 1, W};
+    if (Pz > 1) fft_smem<T, false, ITEMS>(B, fz, a.twz, true, false);
+    const int half = Py >> 1;
+    for (int q = threadIdx.x; q < plane; q += blockDim.x) {
+        const int w = q & (W - 1), kz = q >> lgW, slot = ky0 + w;
+        if (kx != 0 || (slot != 0 && slot != half)) {
+            T k6[6];
+            if (kx != 0)
+                load_K(a.K, kx, a.Hy, a.Hz, Py, Pz, slot, kz, k6);
+            else if (slot < half)
+                load_K(a.K, 0, a.Hy, a.Hz, Py, Pz, slot, kz, k6);
+            else
+                load_K(a.K, a.nx, a.Hy, a.Hz, Py, Pz, Py - slot, kz, k6);
+            cx<T> hx, hy, hz;
+            apply_K(k6, B[q], B[plane + q], B[2 * plane + q], hx, hy, hz);
+            B[q] = hx;
+            B[plane + q] = hy;
+            B[2 * plane + q] = hz;
+        } else {
+            // real pair (A, B) in one slot: packed rule along kz
+            const int kzm = (Pz - kz) & (Pz - 1);
+            if (kz > kzm) continue;
+            const int qm = kzm * W + w;
+            T k0[6], kn[6], P[6], Q[6];
+            load_K(a.K, 0, a.Hy, a.Hz, Py, Pz, slot, kz, k0);
+            load_K(a.K, a.nx, a.Hy, a.Hz, Py, Pz, slot, kz, kn);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                P[i] = (T)0.5 * (k0[i] + kn[i]);
+                Q[i] = (T)0.5 * (k0[i] - kn[i]);
+            }
+            const cx<T> ux = B[q], uy = B[plane + q], uz = B[2 * plane + q];
+            const cx<T> vx = B[qm], vy = B[plane + qm], vz = B[2 * plane + qm];
+            cx<T> a1, a2, a3, b1, b2, b3;
+            apply_K(P, ux, uy, uz, a1, a2, a3);
+            apply_K(Q, mk(vx.x, -vx.y), mk(vy.x, -vy.y), mk(vz.x, -vz.y), b1, b2, b3);
+            B[q] = cadd(a1, b1);
+            B[plane + q] = cadd(a2, b2);
+            B[2 * plane + q] = cadd(a3, b3);
+            if (qm != q) {
+                apply_K(P, vx, vy, vz, a1, a2, a3);
+                apply_K(Q, mk(ux.x, -ux.y), mk(uy.x, -uy.y), mk(uz.x, -uz.y), b1, b2, b3);
+                B[qm] = cadd(a1, b1);
+                B[plane + qm] = cadd(a2, b2);
+                B[2 * plane + qm] = cadd(a3, b3);
+            }
+        }
+    }
+    __syncthreads();
+    if (Pz > 1) fft_smem<T, true, ITEMS>(B, fz, a.twz, false, true);
+    cx<T> *dst = a.Tb + (size_t)kx * nrows * Py + ky0;
+    for (int idx = threadIdx.x; idx < nrows * W; idx += blockDim.x) {
+        const int r = idx >> lgW, w = idx & (W - 1);
+        const int c = r >> lgnz, z = r & (nz - 1);
+        dst[(size_t)r * Py + w] = B[c * plane + z * W + w];
+    }
+}
+
+template <typename T, int ITEMS>
+__global__ void __launch_bounds__(YZ_THREADS) k_yi(const SplitArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<T> *sm = reinterpret_cast<cx<T> *>(smraw);
+    if (a.st) {
+        if (a.st->done) return;
+        if (a.stage0 && a.st->f1_valid) return;
+    }
+    const int kx = blockIdx.x, Py = a.Py, ny = a.ny, lgny = ilog2(ny), lgPy = ilog2(Py);
+    const int nrows = 3 * a.nz, r0 = blockIdx.y * a.ry;
+    const int nr = min(a.ry, nrows - r0);
+    const cx<T> *src = a.Tb + ((size_t)kx * nrows + r0) * Py;
+    const int half = Py >> 1;
+    if (kx != 0) {
+        for (int idx = threadIdx.x; idx < nr * Py; idx += blockDim.x) sm[idx] = src[idx];
+    } else {
+        // U = A + i B from the separated slots
+        for (int idx = threadIdx.x; idx < nr * half; idx += blockDim.x) {
+            const int r = idx / half, q = idx - r * half;
+            const cx<T> *t = src + (size_t)r * Py;
+            cx<T> *u = sm + r * Py;
+            if (q == 0) {
+                u[0] = t[0];
+                u[half] = t[half];
+            } else {
+                const cx<T> av = t[q], bv = t[Py - q];
+                u[q] = mk(av.x - bv.y, av.y + bv.x);
+                u[Py - q] = mk(av.x + bv.y, bv.x - av.y);
+            }
+        }
+    }
+    __syncthreads();
+    const FftShape f{Py, nr, 0, Py, 0, 1};
+    fft_smem<T, true, ITEMS>(sm, f, a.twy, false, true);
+    cx<T> *dst = a.S + (size_t)kx * a.rows + (size_t)r0 * ny;
+    for (int idx = threadIdx.x; idx < nr * ny; idx += blockDim.x) {
+        const int r = idx >> lgny, y = idx & (ny - 1);
+        dst[idx] = sm[r * Py + y];
+    }
+    (void)lgPy;
+}
+
 // ------------------------------------------------------------------ stages
 // Field and torque constants in the arithmetic type of the stage kernel,
 // converted once on the host.
@@ -816,6 +1003,16 @@ template <typename T> size_t x_smem(const mmx_ctx *c, int trows)
 }
 template <typename T> size_t yz_smem(const mmx_ctx *c) { return (size_t)3 * c->Py * c->Pz * sizeof(cx<T>); }
 
+// split path: rows per YF/YI CTA (about 32 KB of shared memory), ky tile of ZM
+template <typename T> int split_rows(const mmx_ctx *c)
+{
+    int r = (int)(32768 / ((size_t)c->Py * sizeof(cx<T>)));
+    if (r < 1) r = 1;
+    return std::min(r, 3 * c->nz);
+}
+int split_w(const mmx_ctx *c) { return std::min(c->Py, 32); }
+template <typename T> size_t zm_smem(const mmx_ctx *c) { return (size_t)3 * c->Pz * split_w(c) * sizeof(cx<T>); }
+
 int pick_trows(const mmx_ctx *c)
 {
     // rows per CTA for the x passes: enough CTAs to cover the SMs twice
@@ -890,10 +1087,44 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
         else if (xi == 2) k_xf<T, 2><<<xgrid, X_THREADS, xs, s>>>(xa);
         else k_xf<T, 4><<<xgrid, X_THREADS, xs, s>>>(xa);
     });
-    timed(1, [&] {
-        if (yi == 1) k_yz<T, 1><<<c->nx, YZ_THREADS, ys, s>>>(ya);
-        else k_yz<T, 2><<<c->nx, YZ_THREADS, ys, s>>>(ya);
-    });
+    if (!c->split) {
+        timed(1, [&] {
+            if (yi == 1) k_yz<T, 1><<<c->nx, YZ_THREADS, ys, s>>>(ya);
+            else k_yz<T, 2><<<c->nx, YZ_THREADS, ys, s>>>(ya);
+        });
+    } else {
+        SplitArgs<T> sa{};
+        sa.S = (cx<T> *)c->S;
+        sa.Tb = (cx<T> *)c->Tb;
+        sa.K = (const T *)c->K;
+        sa.twy = (const cx<T> *)c->twy;
+        sa.twz = (const cx<T> *)c->twz;
+        sa.st = const_cast<DevState *>(st);
+        sa.rows = c->rows;
+        sa.nx = c->nx;
+        sa.ny = c->ny;
+        sa.nz = c->nz;
+        sa.Py = c->Py;
+        sa.Pz = c->Pz;
+        sa.Hy = c->Hy;
+        sa.Hz = c->Hz;
+        sa.stage0 = stage0;
+        sa.ry = split_rows<T>(c);
+        sa.W = split_w(c);
+        const int nrows = 3 * c->nz;
+        const dim3 gy(c->nx, (nrows + sa.ry - 1) / sa.ry), gz(c->nx, c->Py / sa.W);
+        const size_t sy = (size_t)sa.ry * c->Py * sizeof(cx<T>), sz = zm_smem<T>(c);
+        const int iy = items_for(c->Py, YZ_THREADS), iz = items_for(c->Pz, YZ_THREADS);
+        timed(1, [&] {
+            if (iy == 1) k_yf<T, 1><<<gy, YZ_THREADS, sy, s>>>(sa);
+            else k_yf<T, 2><<<gy, YZ_THREADS, sy, s>>>(sa);
+            if (iz == 1) k_zm<T, 1><<<gz, YZ_THREADS, sz, s>>>(sa);
+            else k_zm<T, 2><<<gz, YZ_THREADS, sz, s>>>(sa);
+            if (iy == 1) k_yi<T, 1><<<gy, YZ_THREADS, sy, s>>>(sa);
+            else k_yi<T, 2><<<gy, YZ_THREADS, sy, s>>>(sa);
+            c->launches += 2;
+        });
+    }
     timed(2, [&] {
         if (xi == 1) k_xi<T, 1><<<xgrid, X_THREADS, xs, s>>>(xa);
         else if (xi == 2) k_xi<T, 2><<<xgrid, X_THREADS, xs, s>>>(xa);
@@ -991,10 +1222,24 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
             if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs) != cudaSuccess)
                 return MMX_ERR_CUDA;
     const void *yk[] = {(const void *)k_yz<T, 1>, (const void *)k_yz<T, 2>};
-    if (ys > 48 * 1024)
+    if (!c->split && ys > 48 * 1024)
         for (const void *f : yk)
             if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ys) != cudaSuccess)
                 return MMX_ERR_CUDA;
+    if (c->split) {
+        const size_t sy = (size_t)split_rows<T>(c) * c->Py * sizeof(cx<T>), sz = zm_smem<T>(c);
+        const void *fy[] = {(const void *)k_yf<T, 1>, (const void *)k_yf<T, 2>, (const void *)k_yi<T, 1>,
+                            (const void *)k_yi<T, 2>};
+        if (sy > 48 * 1024)
+            for (const void *f : fy)
+                if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sy) != cudaSuccess)
+                    return MMX_ERR_CUDA;
+        const void *fz[] = {(const void *)k_zm<T, 1>, (const void *)k_zm<T, 2>};
+        if (sz > 48 * 1024)
+            for (const void *f : fz)
+                if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz) != cudaSuccess)
+                    return MMX_ERR_CUDA;
+    }
     return 0;
 }
 
@@ -1004,6 +1249,13 @@ void mmxk_prepare(mmx_ctx *c, cudaStream_t s)
 {
     k_prepare<<<1, 256, 0, s>>>(c->st, c->tab, c->ph, c->ctl.p);
     c->launches++;
+}
+
+size_t mmxk_split_smem_bytes(const mmx_ctx *c)
+{
+    if (c->prec == MMX_FP64)
+        return std::max((size_t)split_rows<double>(c) * c->Py * sizeof(cx<double>), zm_smem<double>(c));
+    return std::max((size_t)split_rows<float>(c) * c->Py * sizeof(cx<float>), zm_smem<float>(c));
 }
 
 size_t mmxk_yz_smem_bytes(const mmx_ctx *c)

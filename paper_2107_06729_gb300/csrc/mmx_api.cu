@@ -23,6 +23,7 @@
 
 size_t mmxk_yz_smem_bytes(const mmx_ctx *c);
 size_t mmxk_x_smem_bytes(const mmx_ctx *c);
+size_t mmxk_split_smem_bytes(const mmx_ctx *c);
 
 namespace {
 
@@ -208,7 +209,8 @@ int kernels_per_attempt(const mmx_ctx *c, int prime)
 {
     const int p = c->ctl.p;
     const int extrap = (p >= 0 && !prime);
-    return extrap ? 3 + c->tab.s : 4 * c->tab.s;
+    const int nd = c->split ? 5 : 3;  // kernels per demag evaluation
+    return extrap ? nd + c->tab.s : (nd + 1) * c->tab.s;
 }
 
 int build_graph(mmx_ctx *c, int which)
@@ -302,8 +304,12 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     c->Hz = c->Pz / 2 + 1;
     c->rows = 3LL * c->ny * c->nz;
     c->use_graphs = getenv("MMX_NO_GRAPH") == nullptr;
-    if (mmxk_yz_smem_bytes(c) > 227 * 1024 || mmxk_x_smem_bytes(c) > 227 * 1024) {
-        g_create_err = "mesh too large for the single-CTA yz/x FFT passes";
+    // fused y-z pass while one column fits comfortably in one CTA, else split
+    c->split = mmxk_yz_smem_bytes(c) > 160 * 1024 || getenv("MMX_FORCE_SPLIT") != nullptr;
+    if (c->Py < 2) c->split = false;
+    if (mmxk_x_smem_bytes(c) > 227 * 1024 || (c->split && mmxk_split_smem_bytes(c) > 227 * 1024) ||
+        (!c->split && mmxk_yz_smem_bytes(c) > 227 * 1024)) {
+        g_create_err = "mesh too large for the FFT passes";
         delete c;
         return MMX_ERR_ARG;
     }
@@ -377,6 +383,7 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     ok = ok && alloc(&c->m[0], fb) && alloc(&c->m[1], fb) && alloc(&c->Y[0], fb) && alloc(&c->Y[1], fb);
     ok = ok && alloc(&c->F, fb * md.s) && alloc(&c->G, fb) && alloc(&c->hist, fb * nh);
     ok = ok && alloc(&c->S, (size_t)c->rows * c->nx * 2 * c->esz);
+    if (c->split) ok = ok && alloc(&c->Tb, (size_t)c->nx * 3 * c->nz * c->Py * 2 * c->esz);
     ok = ok && alloc(&c->K, Kspec.size() * c->esz);
     ok = ok && alloc(&c->twx, (size_t)c->Px * 2 * c->esz) && alloc(&c->twy, (size_t)c->Py * 2 * c->esz) &&
          alloc(&c->twz, (size_t)c->Pz * 2 * c->esz);
@@ -634,7 +641,8 @@ void mmx_destroy(mmx_ctx *c)
             cudaGraphDestroy(c->graph[i]);
         }
     }
-    void *bufs[] = {c->m[0], c->m[1], c->Y[0], c->Y[1], c->F, c->G, c->hist, c->S, c->K, c->twx, c->twy, c->twz, c->st};
+    void *bufs[] = {c->m[0], c->m[1], c->Y[0], c->Y[1], c->F, c->G, c->hist, c->S, c->K, c->twx, c->twy, c->twz, c->Tb,
+                    c->st};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->h_st) cudaFreeHost(c->h_st);

@@ -115,3 +115,16 @@ def test_two_cell_mesh_fixed_step():
     got, _ = gpu_run(mesh, mat, fld, integ, m, 20e-12, "fp64")
     ref, _ = oracle_run(mesh, mat, fld, integ, m, 20e-12)
     assert np.abs(got - ref).max() < 1e-11
+
+
+@pytest.mark.parametrize("method,p", [("RKDP54", 4), ("RK23", -1)])
+def test_split_path_integrator_matches_oracle(method, p, monkeypatch):
+    monkeypatch.setenv("MMX_FORCE_SPLIT", "1")
+    n, d = (16, 8, 4), (4e-9, 4e-9, 4e-9)
+    mesh = {"n": n, "d": d}
+    integ = {"method": method, "extrap_order": p, "adaptive": True, "h": 1e-13, "tol": 1e-5}
+    m0 = W.m_uniform_noise(n, seed=4, noise=0.2)
+    got, gs = gpu_run(mesh, MAT, FLD, integ, m0, 3e-12, "fp64")
+    ref, rs = oracle_run(mesh, MAT, FLD, integ, m0, 3e-12)
+    assert gs["accepted"] == rs["accepted"] and gs["exact_evals"] == rs["exact_evals"]
+    assert np.abs(got - ref).max() < 1e-10
