@@ -111,18 +111,78 @@ class ClockSampler:
 
 
 def byte_model(cfg, esz):
-    """Algorithmic bytes per launch of the three demag passes (DESIGN: pass
-    model).  n cells, r = element size; complex words are 2r."""
-    nx, ny, nz = cfg["mesh"]["n"]
+    """Algorithmic bytes per launch of the three demag passes of the film."""
+    return demag_pass_bytes(cfg["mesh"]["n"], esz, split=False)
+
+
+def demag_pass_bytes(n_xyz, esz, split):
+    """Algorithmic bytes of one exact demag evaluation (the pass model):
+    XF reads m (3 r/cell) and writes the packed half spectrum (3 c/cell,
+    c = 2r); the fused YZ pass reads and writes that spectrum once and reads
+    the tensor octant; the split path instead writes the y spectrum (Py/ny
+    times larger), reads and rewrites it with the tensor in ZM, and reads it
+    back in YI; XI reads the spectrum and writes the field."""
+    nx, ny, nz = n_xyz
     n = nx * ny * nz
     Py = 2 * ny if ny > 1 else 1
     Pz = 2 * nz if nz > 1 else 1
+    c = 2 * esz
     kbytes = (nx + 1) * (Py // 2 + 1) * (Pz // 2 + 1) * 6 * esz
-    return {
-        "x_forward_fft": 3 * n * esz + 3 * n * 2 * esz,
-        "yz_fft_tensor_multiply": 2 * 3 * n * 2 * esz + kbytes,
-        "x_inverse_fft": 3 * n * 2 * esz + 3 * n * esz,
-    }
+    xf = 3 * n * esz + 3 * n * c
+    xi = 3 * n * c + 3 * n * esz
+    if not split:
+        return {"x_forward_fft": xf, "yz_fft_tensor_multiply": 2 * 3 * n * c + kbytes, "x_inverse_fft": xi}
+    rowsy = 3 * nx * nz * Py  # complex words of the y spectrum
+    yz = (3 * n * c + rowsy * c) + (2 * rowsy * c + kbytes) + (rowsy * c + 3 * n * c)
+    return {"x_forward_fft": xf, "yz_fft_tensor_multiply": yz, "x_inverse_fft": xi}
+
+
+def large3d_demag(pkg, torch, dev, iters=20):
+    """Exact demag evaluations on the 512 x 512 x 16 box (4.2M cells, padded
+    1024 x 1024 x 32), FP32: the HBM-roofline run of the demag FFT path."""
+    cfg = W.film_large3d(seed=0)
+    stream = torch.cuda.Stream(dev)
+    t0 = time.time()
+    ctx = pkg.Context(cfg["mesh"], cfg["material"], cfg["field"], cfg["integrator"], "fp32", stream)
+    setup = time.time() - t0
+    with torch.cuda.stream(stream):
+        m = torch.from_numpy(cfg["m0_fn"]()).to(dev, torch.float32)
+        H = torch.empty_like(m)
+        for _ in range(3):
+            ctx.demag(m, H)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(iters):
+            ctx.demag(m, H)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        avg_s = ev[0].elapsed_time(ev[1]) / 1e3 / iters
+        ctx.set_profiling(True)
+        for _ in range(5):
+            ctx.demag(m, H)
+        prof = ctx.profile()
+        ctx.set_profiling(False)
+    ctx.close()
+    model = demag_pass_bytes(cfg["mesh"]["n"], 4, split=True)
+    total = sum(model.values())
+    peak, src = peaks()
+    per_kernel = {}
+    for k in model:
+        ms, nl = prof[k]
+        if nl:
+            t = ms / nl / 1e3
+            per_kernel[k] = {"avg_us": round(t * 1e6, 2), "bytes": model[k], "GBps": round(model[k] / t / 1e9, 1)}
+    ach = total / avg_s / 1e9
+    return {"workload": cfg["name"].replace("_rk23_p2", "") + "_exact_demag", "mesh": list(cfg["mesh"]["n"]),
+            "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+            "bytes_per_eval": total, "us_per_eval": round(avg_s * 1e6, 2), "traffic": None,
+            "peak_source": peak_src_note(src), "setup_s": round(setup, 1), "per_pass": per_kernel,
+            "note": "all passes of one evaluation, CUDA events over %d back-to-back evaluations; per-pass "
+                    "times from event pairs around each launch" % iters}
+
+
+def peak_src_note(src):
+    return src
 
 
 def run_mmx(args):
@@ -292,6 +352,8 @@ def run_mmx(args):
                 "note": "mmx_set_m(host) + mmx_run + mmx_get_m(host) per step; set_m restarts the history"},
         "clocks": clocks,
     }
+    if not args.no_large:
+        line["demag_roofline_large3d"] = large3d_demag(pkg, torch, dev)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -352,6 +414,7 @@ def main():
     ap.add_argument("--chunk-ps", type=float, default=20.0)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 512x512x16 demag roofline run")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mmx":
         args.warmup = 3
