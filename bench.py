@@ -415,11 +415,18 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 512x512x16 demag roofline run")
+    ap.add_argument("--only-large", action="store_true", help="only the 512x512x16 demag roofline run")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mmx":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.only_large:
+        import torch
+        import paper_2107_06729_gb300 as pkg
+        torch.cuda.set_device(0)
+        print(json.dumps({"demag_roofline_large3d": large3d_demag(pkg, torch, torch.device("cuda", 0),
+                                                                  iters=args.steps)}), flush=True)
     else:
         run_mmx(args)
 

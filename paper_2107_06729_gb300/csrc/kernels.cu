@@ -54,6 +54,21 @@ template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b)
 }
 template <typename T> __device__ __forceinline__ cx<T> cscale(T s, cx<T> a) { return mk(s * a.x, s * a.y); }
 
+// Shared-memory view with one padding word per 8 complex words: the
+// stride-R stores of the early Stockham stages then spread over all banks.
+template <typename T> struct Pad {
+    cx<T> *p;
+    int base;
+    __device__ __forceinline__ cx<T> &operator[](int i) const
+    {
+        const int j = base + i;
+        return p[j + (j >> 3)];
+    }
+    __device__ __forceinline__ Pad at(int off) const { return Pad{p, base + off}; }
+};
+// words of shared memory for n padded complex words
+__host__ __device__ constexpr size_t padded_words(size_t n) { return n + n / 8 + 1; }
+
 // multiply by -i (forward) or +i (inverse)
 template <typename T, bool INV> __device__ __forceinline__ cx<T> rot(cx<T> a)
 {
@@ -121,7 +136,7 @@ struct FftShape {
 // threads of the CTA take part; loads of a window of whole transforms
 // complete before any store, so the stage runs in place.
 template <typename T, int R, bool INV, int ITEMS>
-__device__ __forceinline__ void fft_stage(cx<T> *buf, const FftShape &f, int Ns, const cx<T> *__restrict__ tw,
+__device__ __forceinline__ void fft_stage(const Pad<T> buf, const FftShape &f, int Ns, const cx<T> *__restrict__ tw,
                                           bool prune, bool trunc)
 {
     const int per = f.L / R;
@@ -178,7 +193,7 @@ __device__ __forceinline__ void fft_stage(cx<T> *buf, const FftShape &f, int Ns,
 // prune: the upper half of every input is zero and is not read.
 // trunc: only the lower half of the outputs is written.
 template <typename T, bool INV, int ITEMS>
-__device__ void fft_smem(cx<T> *buf, const FftShape &f, const cx<T> *__restrict__ tw, bool prune, bool trunc)
+__device__ void fft_smem(const Pad<T> buf, const FftShape &f, const cx<T> *__restrict__ tw, bool prune, bool trunc)
 {
     int Ns = 1, rem = f.L;
     bool first = true;
@@ -232,7 +247,7 @@ template <typename T, int ITEMS>
 __global__ void __launch_bounds__(X_THREADS) k_xf(const XArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    cx<T> *sm = reinterpret_cast<cx<T> *>(smraw);
+    const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
     if (a.st) {
         if (a.st->done) return;
         if (a.stage0 && a.st->f1_valid) return;
@@ -257,7 +272,7 @@ __global__ void __launch_bounds__(X_THREADS) k_xf(const XArgs<T> a)
         const int k = idx / T_, t = idx - k * T_;
         const long long r = r0 + t;
         if (r >= R) continue;
-        const cx<T> *z = sm + (t >> 1) * Px;
+        const Pad<T> z = sm.at((t >> 1) * Px);
         cx<T> v;
         if (k == 0) {
             const cx<T> z0 = z[0], zn = z[nx];
@@ -275,7 +290,7 @@ template <typename T, int ITEMS>
 __global__ void __launch_bounds__(X_THREADS) k_xi(const XArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    cx<T> *sm = reinterpret_cast<cx<T> *>(smraw);
+    const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
     int head = 0;
     if (a.st) {
         if (a.st->done) return;
@@ -291,7 +306,7 @@ __global__ void __launch_bounds__(X_THREADS) k_xi(const XArgs<T> a)
         const cx<T> zero = mk<T>(0, 0);
         const cx<T> va = (2 * p < a.trows && ra < R) ? a.S[(long long)k * R + ra] : zero;
         const cx<T> vb = (2 * p + 1 < a.trows && rb < R) ? a.S[(long long)k * R + rb] : zero;
-        cx<T> *z = sm + p * Px;
+        const Pad<T> z = sm.at(p * Px);
         if (k == 0) {
             z[0] = mk(va.x, vb.x);
             z[nx] = mk(va.y, vb.y);
@@ -357,7 +372,7 @@ template <typename T, int ITEMS>
 __global__ void __launch_bounds__(YZ_THREADS) k_yz(const YZArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    cx<T> *B = reinterpret_cast<cx<T> *>(smraw);
+    const Pad<T> B{reinterpret_cast<cx<T> *>(smraw), 0};
     if (a.st) {
         if (a.st->done) return;
         if (a.stage0 && a.st->f1_valid) return;
@@ -460,7 +475,7 @@ template <typename T, int ITEMS>
 __global__ void __launch_bounds__(YZ_THREADS) k_yf(const SplitArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    cx<T> *sm = reinterpret_cast<cx<T> *>(smraw);
+    const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
     if (a.st) {
         if (a.st->done) return;
         if (a.stage0 && a.st->f1_valid) return;
@@ -480,7 +495,7 @@ __global__ void __launch_bounds__(YZ_THREADS) k_yf(const SplitArgs<T> a)
     const int lgPy = ilog2(Py), half = Py >> 1;
     for (int idx = threadIdx.x; idx < nr * Py; idx += blockDim.x) {
         const int r = idx >> lgPy, q = idx & (Py - 1);
-        const cx<T> *u = sm + r * Py;
+        const Pad<T> u = sm.at(r * Py);
         cx<T> v;
         if (kx != 0) {
             v = u[q];
@@ -503,7 +518,7 @@ template <typename T, int ITEMS>
 __global__ void __launch_bounds__(YZ_THREADS) k_zm(const SplitArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    cx<T> *B = reinterpret_cast<cx<T> *>(smraw);
+    const Pad<T> B{reinterpret_cast<cx<T> *>(smraw), 0};
     if (a.st) {
         if (a.st->done) return;
         if (a.stage0 && a.st->f1_valid) return;
@@ -580,7 +595,7 @@ template <typename T, int ITEMS>
 __global__ void __launch_bounds__(YZ_THREADS) k_yi(const SplitArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    cx<T> *sm = reinterpret_cast<cx<T> *>(smraw);
+    const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
     if (a.st) {
         if (a.st->done) return;
         if (a.stage0 && a.st->f1_valid) return;
@@ -597,7 +612,7 @@ __global__ void __launch_bounds__(YZ_THREADS) k_yi(const SplitArgs<T> a)
         for (int idx = threadIdx.x; idx < nr * half; idx += blockDim.x) {
             const int r = idx / half, q = idx - r * half;
             const cx<T> *t = src + (size_t)r * Py;
-            cx<T> *u = sm + r * Py;
+            const Pad<T> u = sm.at(r * Py);
             if (q == 0) {
                 u[0] = t[0];
                 u[half] = t[half];
@@ -999,9 +1014,9 @@ __global__ void __launch_bounds__(ST_THREADS, 2) k_stage(const StageArgs<T> a)
 // ----------------------------------------------------------- host helpers
 template <typename T> size_t x_smem(const mmx_ctx *c, int trows)
 {
-    return (size_t)((trows + 1) / 2) * 2 * c->nx * sizeof(cx<T>);
+    return padded_words((size_t)((trows + 1) / 2) * 2 * c->nx) * sizeof(cx<T>);
 }
-template <typename T> size_t yz_smem(const mmx_ctx *c) { return (size_t)3 * c->Py * c->Pz * sizeof(cx<T>); }
+template <typename T> size_t yz_smem(const mmx_ctx *c) { return padded_words((size_t)3 * c->Py * c->Pz) * sizeof(cx<T>); }
 
 // split path: rows per YF/YI CTA (about 32 KB of shared memory), ky tile of ZM
 template <typename T> int split_rows(const mmx_ctx *c)
@@ -1011,14 +1026,21 @@ template <typename T> int split_rows(const mmx_ctx *c)
     return std::min(r, 3 * c->nz);
 }
 int split_w(const mmx_ctx *c) { return std::min(c->Py, 32); }
-template <typename T> size_t zm_smem(const mmx_ctx *c) { return (size_t)3 * c->Pz * split_w(c) * sizeof(cx<T>); }
+template <typename T> size_t zm_smem(const mmx_ctx *c)
+{
+    return padded_words((size_t)3 * c->Pz * split_w(c)) * sizeof(cx<T>);
+}
+template <typename T> size_t yf_smem(const mmx_ctx *c, int ry) { return padded_words((size_t)ry * c->Py) * sizeof(cx<T>); }
 
 int pick_trows(const mmx_ctx *c)
 {
-    // rows per CTA for the x passes: enough CTAs to cover the SMs twice
-    long long rows = c->rows;
-    int tr = 8;
-    while (tr > 2 && (rows + tr - 1) / tr < 2 * 152) tr >>= 1;
+    // rows per CTA for the x passes: wide enough for 128-byte transposed
+    // stores, enough CTAs to cover the SMs twice, at most ~96 KB of smem
+    const long long rows = c->rows;
+    int tr = 16;
+    while (tr > 2 && ((rows + tr - 1) / tr < 2 * 152 ||
+                      padded_words((size_t)(tr / 2) * 2 * c->nx) * 2 * c->esz > 96 * 1024))
+        tr >>= 1;
     return tr;
 }
 
@@ -1113,7 +1135,7 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
         sa.W = split_w(c);
         const int nrows = 3 * c->nz;
         const dim3 gy(c->nx, (nrows + sa.ry - 1) / sa.ry), gz(c->nx, c->Py / sa.W);
-        const size_t sy = (size_t)sa.ry * c->Py * sizeof(cx<T>), sz = zm_smem<T>(c);
+        const size_t sy = yf_smem<T>(c, sa.ry), sz = zm_smem<T>(c);
         const int iy = items_for(c->Py, YZ_THREADS), iz = items_for(c->Pz, YZ_THREADS);
         timed(1, [&] {
             if (iy == 1) k_yf<T, 1><<<gy, YZ_THREADS, sy, s>>>(sa);
@@ -1227,7 +1249,7 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
             if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ys) != cudaSuccess)
                 return MMX_ERR_CUDA;
     if (c->split) {
-        const size_t sy = (size_t)split_rows<T>(c) * c->Py * sizeof(cx<T>), sz = zm_smem<T>(c);
+        const size_t sy = yf_smem<T>(c, split_rows<T>(c)), sz = zm_smem<T>(c);
         const void *fy[] = {(const void *)k_yf<T, 1>, (const void *)k_yf<T, 2>, (const void *)k_yi<T, 1>,
                             (const void *)k_yi<T, 2>};
         if (sy > 48 * 1024)
@@ -1253,9 +1275,8 @@ void mmxk_prepare(mmx_ctx *c, cudaStream_t s)
 
 size_t mmxk_split_smem_bytes(const mmx_ctx *c)
 {
-    if (c->prec == MMX_FP64)
-        return std::max((size_t)split_rows<double>(c) * c->Py * sizeof(cx<double>), zm_smem<double>(c));
-    return std::max((size_t)split_rows<float>(c) * c->Py * sizeof(cx<float>), zm_smem<float>(c));
+    if (c->prec == MMX_FP64) return std::max(yf_smem<double>(c, split_rows<double>(c)), zm_smem<double>(c));
+    return std::max(yf_smem<float>(c, split_rows<float>(c)), zm_smem<float>(c));
 }
 
 size_t mmxk_yz_smem_bytes(const mmx_ctx *c)
