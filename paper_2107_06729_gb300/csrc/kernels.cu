@@ -214,6 +214,147 @@ __device__ void fft_smem(const Pad<T> buf, const FftShape &f, const cx<T> *__res
 
 __device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
 
+// ---- warp-level transforms: one warp owns a whole transform of length L
+// (elements es apart in a padded shared-memory view) and runs the Stockham
+// stages with __syncwarp only, so warps of a CTA proceed independently.
+template <typename T, int R, bool INV, int IT>
+__device__ __forceinline__ void warp_stage(const Pad<T> buf, int L, int es, int Ns, const cx<T> *__restrict__ tw,
+                                           bool prune, bool trunc)
+{
+    const int lane = threadIdx.x & 31;
+    const int per = L / R;
+    const int tstride = L / (Ns * R);
+    const int half = L >> 1;
+    cx<T> v[IT][R];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int j = lane + 32 * it;
+        if (j < per) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                v[it][r] = (prune && r >= R / 2) ? mk<T>(0, 0) : buf[(j + r * per) * es];
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int j = lane + 32 * it;
+        if (j >= per) continue;
+        const int k = j & (Ns - 1);
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                cx<T> w = tw[r * k * tstride];
+                if (INV) w.y = -w.y;
+                v[it][r] = cmul(v[it][r], w);
+            }
+        }
+        Dft<T, R, INV>::run(v[it]);
+        const int d = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int pos = d + r * Ns;
+            if (!trunc || pos < half) buf[pos * es] = v[it][r];
+        }
+    }
+    __syncwarp();
+}
+
+// largest transform a single warp handles (register budget of the stages)
+template <typename T> __host__ __device__ constexpr int warp_max_len() { return sizeof(T) == 4 ? 1024 : 256; }
+
+// compile-time stage sequence of a length-L transform (radix 8 while
+// possible, 16 as 4 x 4, then 4 or 2): fixed shapes let the compiler keep
+// the register footprint of the largest stage only
+template <typename T, bool INV, int L, int NS> struct WarpFFT {
+    static __device__ __forceinline__ void run(const Pad<T> buf, int es, const cx<T> *tw, bool prune, bool trunc)
+    {
+        constexpr int REM = L / NS;
+        constexpr int R = (REM % 8 == 0 && REM != 16) ? 8 : ((REM % 4 == 0) ? 4 : 2);
+        constexpr int PER = L / R;
+        constexpr int IT = PER <= 32 ? 1 : PER / 32;
+        warp_stage<T, R, INV, IT>(buf, L, es, NS, tw, NS == 1 && prune, REM == R && trunc);
+        WarpFFT<T, INV, L, NS * R>::run(buf, es, tw, prune, trunc);
+    }
+};
+template <typename T, bool INV, int L> struct WarpFFT<T, INV, L, L> {
+    static __device__ __forceinline__ void run(const Pad<T>, int, const cx<T> *, bool, bool) {}
+};
+
+// items per thread when a CTA of 256 threads runs each stage of a length-L
+// transform together (transforms too long for one warp)
+__host__ __device__ constexpr int block_items(int L)
+{
+    return ((L <= 2 ? 1 : L / 4) <= 256) ? 1 : (L / 4) / 256;
+}
+
+// ---- register-level transforms for short lengths (the z axis): one thread
+// holds the whole sequence; Stockham stages unrolled at compile time.
+template <typename T, int L, int NS, bool INV> struct RegFFT {
+    static __device__ __forceinline__ void run(cx<T> *v, const cx<T> *__restrict__ tw)
+    {
+        constexpr int REM = L / NS;
+        constexpr int R = (REM % 8 == 0 && REM != 16) ? 8 : ((REM % 4 == 0) ? 4 : 2);
+        constexpr int PER = L / R;
+        cx<T> out[L];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            cx<T> u[R];
+            const int k = j % NS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                u[r] = v[j + r * PER];
+                if (NS > 1 && r > 0) {
+                    cx<T> w = tw[r * k * (L / (NS * R))];
+                    if (INV) w.y = -w.y;
+                    u[r] = cmul(u[r], w);
+                }
+            }
+            Dft<T, R, INV>::run(u);
+            const int d = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) out[d + r * NS] = u[r];
+        }
+#pragma unroll
+        for (int i = 0; i < L; ++i) v[i] = out[i];
+        RegFFT<T, L, NS * R, INV>::run(v, tw);
+    }
+};
+template <typename T, int L, bool INV> struct RegFFT<T, L, L, INV> {
+    static __device__ __forceinline__ void run(cx<T> *, const cx<T> *) {}
+};
+
+// one column of length L at buf[base + i*es]: the first nload entries are
+// read (the rest are zero), the first nstore results are written
+template <typename T, int L, bool INV>
+__device__ __forceinline__ void col_fft(const Pad<T> buf, int base, int es, int nload, int nstore,
+                                        const cx<T> *__restrict__ tw)
+{
+    cx<T> v[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) v[i] = i < nload ? buf[base + i * es] : mk<T>(0, 0);
+    RegFFT<T, L, 1, INV>::run(v, tw);
+#pragma unroll
+    for (int i = 0; i < L; ++i)
+        if (i < nstore) buf[base + i * es] = v[i];
+}
+
+template <typename T> __host__ __device__ constexpr int reg_max_len() { return sizeof(T) == 4 ? 16 : 8; }
+
+template <typename T, bool INV>
+__device__ __forceinline__ void col_fft_any(const Pad<T> buf, int L, int base, int es, int nload, int nstore,
+                                            const cx<T> *__restrict__ tw)
+{
+    switch (L) {
+    case 2: col_fft<T, 2, INV>(buf, base, es, nload, nstore, tw); break;
+    case 4: col_fft<T, 4, INV>(buf, base, es, nload, nstore, tw); break;
+    case 8: col_fft<T, 8, INV>(buf, base, es, nload, nstore, tw); break;
+    default:
+        if (sizeof(T) == 4) col_fft<T, (sizeof(T) == 4 ? 16 : 8), INV>(buf, base, es, nload, nstore, tw);
+        break;
+    }
+}
+
 // ------------------------------------------------------------------ XF / XI
 template <typename T> struct XArgs {
     const T *src;        // src_mode 0
@@ -243,8 +384,8 @@ int items_for(int L, int threads)
     return it;
 }
 
-template <typename T, int ITEMS>
-__global__ void __launch_bounds__(X_THREADS) k_xf(const XArgs<T> a)
+template <typename T, int PX>
+__global__ void __launch_bounds__(256, 2) k_xf(const XArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
@@ -264,8 +405,14 @@ __global__ void __launch_bounds__(X_THREADS) k_xf(const XArgs<T> a)
         sm[p * Px + x] = mk(va, vb);
     }
     __syncthreads();
-    FftShape f{Px, np, 0, Px, 0, 1};
-    fft_smem<T, false, ITEMS>(sm, f, a.tw, true, false);
+    if constexpr (PX <= warp_max_len<T>()) {
+        for (int pr = threadIdx.x >> 5; pr < np; pr += blockDim.x >> 5)
+            WarpFFT<T, false, PX, 1>::run(sm.at(pr * PX), 1, a.tw, true, false);
+        __syncthreads();
+    } else {
+        const FftShape f{PX, np, 0, PX, 0, 1};
+        fft_smem<T, false, block_items(PX)>(sm, f, a.tw, true, false);
+    }
     // separate the two real rows and pack kx = 0 with kx = nx
     const int T_ = a.trows;
     for (int idx = threadIdx.x; idx < nx * T_; idx += blockDim.x) {
@@ -286,8 +433,8 @@ __global__ void __launch_bounds__(X_THREADS) k_xf(const XArgs<T> a)
     }
 }
 
-template <typename T, int ITEMS>
-__global__ void __launch_bounds__(X_THREADS) k_xi(const XArgs<T> a)
+template <typename T, int PX>
+__global__ void __launch_bounds__(256, 2) k_xi(const XArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
@@ -316,8 +463,14 @@ __global__ void __launch_bounds__(X_THREADS) k_xi(const XArgs<T> a)
         }
     }
     __syncthreads();
-    FftShape f{Px, np, 0, Px, 0, 1};
-    fft_smem<T, true, ITEMS>(sm, f, a.tw, false, true);
+    if constexpr (PX <= warp_max_len<T>()) {
+        for (int pr = threadIdx.x >> 5; pr < np; pr += blockDim.x >> 5)
+            WarpFFT<T, true, PX, 1>::run(sm.at(pr * PX), 1, a.tw, false, true);
+        __syncthreads();
+    } else {
+        const FftShape f{PX, np, 0, PX, 0, 1};
+        fft_smem<T, true, block_items(PX)>(sm, f, a.tw, false, true);
+    }
     T *out = a.dst_mode == 1 ? a.hist + (size_t)head * 3 * a.n : a.dst;
     const int T_ = a.trows, lgnx = ilog2(nx);
     for (int idx = threadIdx.x; idx < T_ * nx; idx += blockDim.x) {
@@ -368,8 +521,8 @@ __device__ __forceinline__ void apply_K(const T k[6], cx<T> mx, cx<T> my, cx<T> 
     hz = mk(k[4] * mx.x + k[5] * my.x + k[2] * mz.x, k[4] * mx.y + k[5] * my.y + k[2] * mz.y);
 }
 
-template <typename T, int ITEMS>
-__global__ void __launch_bounds__(YZ_THREADS) k_yz(const YZArgs<T> a)
+template <typename T, int PY>
+__global__ void __launch_bounds__(YZ_THREADS, 2) k_yz(const YZArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> B{reinterpret_cast<cx<T> *>(smraw), 0};
@@ -389,8 +542,27 @@ __global__ void __launch_bounds__(YZ_THREADS) k_yz(const YZArgs<T> a)
     __syncthreads();
     const FftShape fy{Py, 3 * nz, lgnz, plane, Py, 1};
     const FftShape fz{Pz, 3 * Py, lgPy, plane, 1, Py};
-    if (Py > 1) fft_smem<T, false, ITEMS>(B, fy, a.twy, true, false);
-    if (Pz > 1) fft_smem<T, false, ITEMS>(B, fz, a.twz, true, false);
+    const bool rz = Pz <= reg_max_len<T>();
+    const int nwarp = blockDim.x >> 5, warp = threadIdx.x >> 5;
+    if constexpr (PY > 1) {
+        if constexpr (PY <= warp_max_len<T>()) {
+            for (int tr = warp; tr < 3 * nz; tr += nwarp)
+                WarpFFT<T, false, PY, 1>::run(B.at((tr >> lgnz) * plane + (tr & (nz - 1)) * PY), 1, a.twy, true,
+                                              false);
+            __syncthreads();
+        } else {
+            fft_smem<T, false, block_items(PY)>(B, fy, a.twy, true, false);
+        }
+    }
+    if (Pz > 1) {
+        if (rz) {
+            for (int tr = threadIdx.x; tr < 3 * Py; tr += blockDim.x)
+                col_fft_any<T, false>(B, Pz, (tr >> lgPy) * plane + (tr & (Py - 1)), Py, nz, Pz, a.twz);
+            __syncthreads();
+        } else {
+            fft_smem<T, false, 2>(B, fz, a.twz, true, false);
+        }
+    }
 
     // Fourier-space tensor multiply (Eq. 2): H = K M, K real symmetric
     if (kx != 0) {
@@ -439,8 +611,25 @@ __global__ void __launch_bounds__(YZ_THREADS) k_yz(const YZArgs<T> a)
         }
     }
     __syncthreads();
-    if (Pz > 1) fft_smem<T, true, ITEMS>(B, fz, a.twz, false, true);
-    if (Py > 1) fft_smem<T, true, ITEMS>(B, fy, a.twy, false, true);
+    if (Pz > 1) {
+        if (rz) {
+            for (int tr = threadIdx.x; tr < 3 * Py; tr += blockDim.x)
+                col_fft_any<T, true>(B, Pz, (tr >> lgPy) * plane + (tr & (Py - 1)), Py, Pz, nz, a.twz);
+            __syncthreads();
+        } else {
+            fft_smem<T, true, 2>(B, fz, a.twz, false, true);
+        }
+    }
+    if constexpr (PY > 1) {
+        if constexpr (PY <= warp_max_len<T>()) {
+            for (int tr = warp; tr < 3 * nz; tr += nwarp)
+                WarpFFT<T, true, PY, 1>::run(B.at((tr >> lgnz) * plane + (tr & (nz - 1)) * PY), 1, a.twy, false,
+                                             true);
+            __syncthreads();
+        } else {
+            fft_smem<T, true, block_items(PY)>(B, fy, a.twy, false, true);
+        }
+    }
     for (int r = threadIdx.x; r < rows; r += blockDim.x) {
         const int y = r & (ny - 1), cz = r >> lgny, z = cz & (nz - 1), c = cz >> lgnz;
         S[r] = B[c * plane + z * Py + y];
@@ -471,8 +660,8 @@ template <typename T> struct SplitArgs {
     int nx, ny, nz, Py, Pz, Hy, Hz, stage0, ry, W;
 };
 
-template <typename T, int ITEMS>
-__global__ void __launch_bounds__(YZ_THREADS) k_yf(const SplitArgs<T> a)
+template <typename T, int PY>
+__global__ void __launch_bounds__(256, 2) k_yf(const SplitArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
@@ -489,8 +678,14 @@ __global__ void __launch_bounds__(YZ_THREADS) k_yf(const SplitArgs<T> a)
         sm[r * Py + y] = src[idx];
     }
     __syncthreads();
-    const FftShape f{Py, nr, 0, Py, 0, 1};
-    fft_smem<T, false, ITEMS>(sm, f, a.twy, true, false);
+    if constexpr (PY <= warp_max_len<T>()) {
+        for (int r = threadIdx.x >> 5; r < nr; r += blockDim.x >> 5)
+            WarpFFT<T, false, PY, 1>::run(sm.at(r * PY), 1, a.twy, true, false);
+        __syncthreads();
+    } else {
+        const FftShape f{PY, nr, 0, PY, 0, 1};
+        fft_smem<T, false, block_items(PY)>(sm, f, a.twy, true, false);
+    }
     cx<T> *dst = a.Tb + ((size_t)kx * nrows + r0) * Py;
     const int lgPy = ilog2(Py), half = Py >> 1;
     for (int idx = threadIdx.x; idx < nr * Py; idx += blockDim.x) {
@@ -534,7 +729,16 @@ __global__ void __launch_bounds__(YZ_THREADS) k_zm(const SplitArgs<T> a)
     }
     __syncthreads();
     const FftShape fz{Pz, 3 * W, lgW, plane, 1, W};
-    if (Pz > 1) fft_smem<T, false, ITEMS>(B, fz, a.twz, true, false);
+    const bool rz = Pz <= reg_max_len<T>();
+    if (Pz > 1) {
+        if (rz) {
+            for (int tr = threadIdx.x; tr < 3 * W; tr += blockDim.x)
+                col_fft_any<T, false>(B, Pz, (tr >> lgW) * plane + (tr & (W - 1)), W, nz, Pz, a.twz);
+            __syncthreads();
+        } else {
+            fft_smem<T, false, ITEMS>(B, fz, a.twz, true, false);
+        }
+    }
     const int half = Py >> 1;
     for (int q = threadIdx.x; q < plane; q += blockDim.x) {
         const int w = q & (W - 1), kz = q >> lgW, slot = ky0 + w;
@@ -582,7 +786,15 @@ __global__ void __launch_bounds__(YZ_THREADS) k_zm(const SplitArgs<T> a)
         }
     }
     __syncthreads();
-    if (Pz > 1) fft_smem<T, true, ITEMS>(B, fz, a.twz, false, true);
+    if (Pz > 1) {
+        if (rz) {
+            for (int tr = threadIdx.x; tr < 3 * W; tr += blockDim.x)
+                col_fft_any<T, true>(B, Pz, (tr >> lgW) * plane + (tr & (W - 1)), W, Pz, nz, a.twz);
+            __syncthreads();
+        } else {
+            fft_smem<T, true, ITEMS>(B, fz, a.twz, false, true);
+        }
+    }
     cx<T> *dst = a.Tb + (size_t)kx * nrows * Py + ky0;
     for (int idx = threadIdx.x; idx < nrows * W; idx += blockDim.x) {
         const int r = idx >> lgW, w = idx & (W - 1);
@@ -591,8 +803,8 @@ __global__ void __launch_bounds__(YZ_THREADS) k_zm(const SplitArgs<T> a)
     }
 }
 
-template <typename T, int ITEMS>
-__global__ void __launch_bounds__(YZ_THREADS) k_yi(const SplitArgs<T> a)
+template <typename T, int PY>
+__global__ void __launch_bounds__(256, 2) k_yi(const SplitArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
@@ -624,8 +836,14 @@ __global__ void __launch_bounds__(YZ_THREADS) k_yi(const SplitArgs<T> a)
         }
     }
     __syncthreads();
-    const FftShape f{Py, nr, 0, Py, 0, 1};
-    fft_smem<T, true, ITEMS>(sm, f, a.twy, false, true);
+    if constexpr (PY <= warp_max_len<T>()) {
+        for (int r = threadIdx.x >> 5; r < nr; r += blockDim.x >> 5)
+            WarpFFT<T, true, PY, 1>::run(sm.at(r * PY), 1, a.twy, false, true);
+        __syncthreads();
+    } else {
+        const FftShape f{PY, nr, 0, PY, 0, 1};
+        fft_smem<T, true, block_items(PY)>(sm, f, a.twy, false, true);
+    }
     cx<T> *dst = a.S + (size_t)kx * a.rows + (size_t)r0 * ny;
     for (int idx = threadIdx.x; idx < nr * ny; idx += blockDim.x) {
         const int r = idx >> lgny, y = idx & (ny - 1);
@@ -1023,9 +1241,20 @@ template <typename T> int split_rows(const mmx_ctx *c)
 {
     int r = (int)(32768 / ((size_t)c->Py * sizeof(cx<T>)));
     if (r < 1) r = 1;
-    return std::min(r, 3 * c->nz);
+    return std::min(std::min(r, 8), 3 * c->nz);
 }
-int split_w(const mmx_ctx *c) { return std::min(c->Py, 32); }
+int split_w(const mmx_ctx *c) { return std::min(c->Py, 64); }
+// threads of the x passes and of YF / YI: one warp per transform (at least
+// two warps); 256 when the transforms are too long for one warp and the
+// whole CTA runs each stage
+template <typename T> int x_threads(const mmx_ctx *c, int trows)
+{
+    return c->Px > warp_max_len<T>() ? 256 : 32 * std::max(2, (trows + 1) / 2);
+}
+template <typename T> int y_threads(const mmx_ctx *c)
+{
+    return c->Py > warp_max_len<T>() ? 256 : 32 * std::max(2, split_rows<T>(c));
+}
 template <typename T> size_t zm_smem(const mmx_ctx *c)
 {
     return padded_words((size_t)3 * c->Pz * split_w(c)) * sizeof(cx<T>);
@@ -1042,6 +1271,48 @@ int pick_trows(const mmx_ctx *c)
                       padded_words((size_t)(tr / 2) * 2 * c->nx) * 2 * c->esz > 96 * 1024))
         tr >>= 1;
     return tr;
+}
+
+// kernel instances per transform length (powers of two)
+#define MMX_LEN_CASES(K, T) \
+    case 1: return (const void *)K<T, 1>; \
+    case 2: return (const void *)K<T, 2>; \
+    case 4: return (const void *)K<T, 4>; \
+    case 8: return (const void *)K<T, 8>; \
+    case 16: return (const void *)K<T, 16>; \
+    case 32: return (const void *)K<T, 32>; \
+    case 64: return (const void *)K<T, 64>; \
+    case 128: return (const void *)K<T, 128>; \
+    case 256: return (const void *)K<T, 256>; \
+    case 512: return (const void *)K<T, 512>; \
+    case 1024: return (const void *)K<T, 1024>; \
+    case 2048: return (const void *)K<T, 2048>; \
+    case 4096: return (const void *)K<T, 4096>;
+
+template <typename T> const void *xf_fn(int L)
+{
+    switch (L) { MMX_LEN_CASES(k_xf, T) }
+    return nullptr;
+}
+template <typename T> const void *xi_fn(int L)
+{
+    switch (L) { MMX_LEN_CASES(k_xi, T) }
+    return nullptr;
+}
+template <typename T> const void *yz_fn(int L)
+{
+    switch (L) { MMX_LEN_CASES(k_yz, T) }
+    return nullptr;
+}
+template <typename T> const void *yf_fn(int L)
+{
+    switch (L) { MMX_LEN_CASES(k_yf, T) }
+    return nullptr;
+}
+template <typename T> const void *yi_fn(int L)
+{
+    switch (L) { MMX_LEN_CASES(k_yi, T) }
+    return nullptr;
 }
 
 template <typename T>
@@ -1102,18 +1373,12 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
             c->prof_n[cls]++;
         }
     };
-    const int xi = items_for(c->Px, X_THREADS);
-    const int yi = std::max(items_for(c->Py, YZ_THREADS), items_for(c->Pz, YZ_THREADS));
-    timed(0, [&] {
-        if (xi == 1) k_xf<T, 1><<<xgrid, X_THREADS, xs, s>>>(xa);
-        else if (xi == 2) k_xf<T, 2><<<xgrid, X_THREADS, xs, s>>>(xa);
-        else k_xf<T, 4><<<xgrid, X_THREADS, xs, s>>>(xa);
-    });
+    const int xt = x_threads<T>(c, trows);
+    void *xargs[] = {(void *)&xa};
+    void *yargs[] = {(void *)&ya};
+    timed(0, [&] { cudaLaunchKernel(xf_fn<T>(c->Px), dim3(xgrid), dim3(xt), xargs, xs, s); });
     if (!c->split) {
-        timed(1, [&] {
-            if (yi == 1) k_yz<T, 1><<<c->nx, YZ_THREADS, ys, s>>>(ya);
-            else k_yz<T, 2><<<c->nx, YZ_THREADS, ys, s>>>(ya);
-        });
+        timed(1, [&] { cudaLaunchKernel(yz_fn<T>(c->Py), dim3(c->nx), dim3(YZ_THREADS), yargs, ys, s); });
     } else {
         SplitArgs<T> sa{};
         sa.S = (cx<T> *)c->S;
@@ -1136,22 +1401,18 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
         const int nrows = 3 * c->nz;
         const dim3 gy(c->nx, (nrows + sa.ry - 1) / sa.ry), gz(c->nx, c->Py / sa.W);
         const size_t sy = yf_smem<T>(c, sa.ry), sz = zm_smem<T>(c);
-        const int iy = items_for(c->Py, YZ_THREADS), iz = items_for(c->Pz, YZ_THREADS);
+        const int yt = y_threads<T>(c);
+        const int iz = items_for(c->Pz, YZ_THREADS);
+        void *sargs[] = {(void *)&sa};
         timed(1, [&] {
-            if (iy == 1) k_yf<T, 1><<<gy, YZ_THREADS, sy, s>>>(sa);
-            else k_yf<T, 2><<<gy, YZ_THREADS, sy, s>>>(sa);
+            cudaLaunchKernel(yf_fn<T>(c->Py), gy, dim3(yt), sargs, sy, s);
             if (iz == 1) k_zm<T, 1><<<gz, YZ_THREADS, sz, s>>>(sa);
             else k_zm<T, 2><<<gz, YZ_THREADS, sz, s>>>(sa);
-            if (iy == 1) k_yi<T, 1><<<gy, YZ_THREADS, sy, s>>>(sa);
-            else k_yi<T, 2><<<gy, YZ_THREADS, sy, s>>>(sa);
+            cudaLaunchKernel(yi_fn<T>(c->Py), gy, dim3(yt), sargs, sy, s);
             c->launches += 2;
         });
     }
-    timed(2, [&] {
-        if (xi == 1) k_xi<T, 1><<<xgrid, X_THREADS, xs, s>>>(xa);
-        else if (xi == 2) k_xi<T, 2><<<xgrid, X_THREADS, xs, s>>>(xa);
-        else k_xi<T, 4><<<xgrid, X_THREADS, xs, s>>>(xa);
-    });
+    timed(2, [&] { cudaLaunchKernel(xi_fn<T>(c->Px), dim3(xgrid), dim3(xt), xargs, xs, s); });
 }
 
 template <typename T>
@@ -1237,21 +1498,19 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
     if (cudaMemcpy(c->twz, tw.data(), c->Pz * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
     const int trows = pick_trows(c);
     const size_t xs = x_smem<T>(c, trows), ys = yz_smem<T>(c);
-    const void *xk[] = {(const void *)k_xf<T, 1>, (const void *)k_xf<T, 2>, (const void *)k_xf<T, 4>,
-                        (const void *)k_xi<T, 1>, (const void *)k_xi<T, 2>, (const void *)k_xi<T, 4>};
+    const void *xk[] = {xf_fn<T>(c->Px), xi_fn<T>(c->Px)};
     if (xs > 48 * 1024)
         for (const void *f : xk)
             if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs) != cudaSuccess)
                 return MMX_ERR_CUDA;
-    const void *yk[] = {(const void *)k_yz<T, 1>, (const void *)k_yz<T, 2>};
+    const void *yk[] = {yz_fn<T>(c->Py)};
     if (!c->split && ys > 48 * 1024)
         for (const void *f : yk)
             if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ys) != cudaSuccess)
                 return MMX_ERR_CUDA;
     if (c->split) {
         const size_t sy = yf_smem<T>(c, split_rows<T>(c)), sz = zm_smem<T>(c);
-        const void *fy[] = {(const void *)k_yf<T, 1>, (const void *)k_yf<T, 2>, (const void *)k_yi<T, 1>,
-                            (const void *)k_yi<T, 2>};
+        const void *fy[] = {yf_fn<T>(c->Py), yi_fn<T>(c->Py)};
         if (sy > 48 * 1024)
             for (const void *f : fy)
                 if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sy) != cudaSuccess)
