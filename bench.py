@@ -185,6 +185,43 @@ def peak_src_note(src):
     return src
 
 
+def eps_eq7(m, ref):
+    """Eq. 7 over cells: mean of |m_i - m~_i| (unit vectors)."""
+    return float(np.linalg.norm(m - ref, axis=0).mean())
+
+
+def accuracy(pkg, torch, dev, cfg, horizon_ps):
+    """Equal-error check on the first `horizon_ps` of the film: FP32 with the
+    extrapolation and FP32 with full demag at every stage, both at e_max =
+    1e-5, against a GPU FP64 full-demag reference at e_max = 1e-8 (that
+    path matches the CPU oracle step for step in the parity tests)."""
+    stream = torch.cuda.Stream(dev)
+    t_end = horizon_ps * 1e-12
+    out = {}
+    runs = {"reference_fp64_full_tol1e-8": ("fp64", dict(cfg["integrator"], extrap_order=-1, tol=1e-8)),
+            "fp32_extrapolated": ("fp32", cfg["integrator"]),
+            "fp32_full": ("fp32", dict(cfg["integrator"], extrap_order=-1)),
+            "fp64_extrapolated": ("fp64", cfg["integrator"])}
+    with torch.cuda.stream(stream):
+        for name, (prec, integ) in runs.items():
+            ctx = pkg.Context(cfg["mesh"], cfg["material"], cfg["field"], integ, prec, stream)
+            dt = torch.float64 if prec == "fp64" else torch.float32
+            m = torch.from_numpy(cfg["m0"]).to(dev, dt)
+            ctx.set_m(m)
+            ctx.run(t_end)
+            ctx.get_m(m)
+            torch.cuda.synchronize(dev)
+            out[name] = (m.double().cpu().numpy(), ctx.stats())
+            ctx.close()
+    ref = out["reference_fp64_full_tol1e-8"][0]
+    res = {"horizon_ps": horizon_ps, "metric": "Eq. 7 mean |m - m_ref| over cells",
+           "reference": "GPU FP64, full demag at every stage, e_max 1e-8"}
+    for name in ("fp32_extrapolated", "fp32_full", "fp64_extrapolated"):
+        res[name] = {"eps": eps_eq7(out[name][0], ref), "max": float(np.abs(out[name][0] - ref).max()),
+                     "accepted": out[name][1]["accepted"], "rejected": out[name][1]["rejected"]}
+    return res
+
+
 def run_mmx(args):
     import torch
     import paper_2107_06729_gb300 as pkg
@@ -352,6 +389,8 @@ def run_mmx(args):
                 "note": "mmx_set_m(host) + mmx_run + mmx_get_m(host) per step; set_m restarts the history"},
         "clocks": clocks,
     }
+    if not args.no_accuracy:
+        line["accuracy"] = accuracy(pkg, torch, dev, cfg, args.chunk_ps)
     if not args.no_large:
         line["demag_roofline_large3d"] = large3d_demag(pkg, torch, dev)
     if not args.no_cpu:
@@ -416,6 +455,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 512x512x16 demag roofline run")
     ap.add_argument("--only-large", action="store_true", help="only the 512x512x16 demag roofline run")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the equal-error check")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mmx":
         args.warmup = 3

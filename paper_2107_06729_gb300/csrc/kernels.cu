@@ -340,6 +340,8 @@ __device__ __forceinline__ void col_fft(const Pad<T> buf, int base, int es, int 
 }
 
 template <typename T> __host__ __device__ constexpr int reg_max_len() { return sizeof(T) == 4 ? 16 : 8; }
+// ZM holds nothing else in registers during its z transforms: one longer length
+template <typename T> __host__ __device__ constexpr int zm_reg_len() { return sizeof(T) == 4 ? 32 : 16; }
 
 template <typename T, bool INV>
 __device__ __forceinline__ void col_fft_any(const Pad<T> buf, int L, int base, int es, int nload, int nstore,
@@ -395,6 +397,7 @@ __global__ void __launch_bounds__(256, 2) k_xf(const XArgs<T> a)
     }
     const T *src = a.src_mode == 1 ? (a.st->cur ? a.msrc1 : a.msrc0) : a.src;
     const int nx = a.nx, Px = 2 * nx, lgnx = ilog2(nx);
+    constexpr int PXS = PX + 8;  // pair stride: pairs land in different banks
     const int np = (a.trows + 1) >> 1;
     const long long R = a.rows, r0 = (long long)blockIdx.x * a.trows;
     for (int idx = threadIdx.x; idx < np * nx; idx += blockDim.x) {
@@ -402,15 +405,15 @@ __global__ void __launch_bounds__(256, 2) k_xf(const XArgs<T> a)
         const long long ra = r0 + 2 * p, rb = ra + 1;
         T va = (2 * p < a.trows && ra < R) ? src[ra * nx + x] : (T)0;
         T vb = (2 * p + 1 < a.trows && rb < R) ? src[rb * nx + x] : (T)0;
-        sm[p * Px + x] = mk(va, vb);
+        sm[p * PXS + x] = mk(va, vb);
     }
     __syncthreads();
     if constexpr (PX <= warp_max_len<T>()) {
         for (int pr = threadIdx.x >> 5; pr < np; pr += blockDim.x >> 5)
-            WarpFFT<T, false, PX, 1>::run(sm.at(pr * PX), 1, a.tw, true, false);
+            WarpFFT<T, false, PX, 1>::run(sm.at(pr * PXS), 1, a.tw, true, false);
         __syncthreads();
     } else {
-        const FftShape f{PX, np, 0, PX, 0, 1};
+        const FftShape f{PX, np, 0, PXS, 0, 1};
         fft_smem<T, false, block_items(PX)>(sm, f, a.tw, true, false);
     }
     // separate the two real rows and pack kx = 0 with kx = nx
@@ -419,7 +422,7 @@ __global__ void __launch_bounds__(256, 2) k_xf(const XArgs<T> a)
         const int k = idx / T_, t = idx - k * T_;
         const long long r = r0 + t;
         if (r >= R) continue;
-        const Pad<T> z = sm.at((t >> 1) * Px);
+        const Pad<T> z = sm.at((t >> 1) * PXS);
         cx<T> v;
         if (k == 0) {
             const cx<T> z0 = z[0], zn = z[nx];
@@ -445,6 +448,7 @@ __global__ void __launch_bounds__(256, 2) k_xi(const XArgs<T> a)
         head = a.st->head;
     }
     const int nx = a.nx, Px = 2 * nx;
+    constexpr int PXS = PX + 8;  // pair stride: pairs land in different banks
     const int np = (a.trows + 1) >> 1;
     const long long R = a.rows, r0 = (long long)blockIdx.x * a.trows;
     for (int idx = threadIdx.x; idx < np * nx; idx += blockDim.x) {
@@ -453,7 +457,7 @@ __global__ void __launch_bounds__(256, 2) k_xi(const XArgs<T> a)
         const cx<T> zero = mk<T>(0, 0);
         const cx<T> va = (2 * p < a.trows && ra < R) ? a.S[(long long)k * R + ra] : zero;
         const cx<T> vb = (2 * p + 1 < a.trows && rb < R) ? a.S[(long long)k * R + rb] : zero;
-        const Pad<T> z = sm.at(p * Px);
+        const Pad<T> z = sm.at(p * PXS);
         if (k == 0) {
             z[0] = mk(va.x, vb.x);
             z[nx] = mk(va.y, vb.y);
@@ -465,10 +469,10 @@ __global__ void __launch_bounds__(256, 2) k_xi(const XArgs<T> a)
     __syncthreads();
     if constexpr (PX <= warp_max_len<T>()) {
         for (int pr = threadIdx.x >> 5; pr < np; pr += blockDim.x >> 5)
-            WarpFFT<T, true, PX, 1>::run(sm.at(pr * PX), 1, a.tw, false, true);
+            WarpFFT<T, true, PX, 1>::run(sm.at(pr * PXS), 1, a.tw, false, true);
         __syncthreads();
     } else {
-        const FftShape f{PX, np, 0, PX, 0, 1};
+        const FftShape f{PX, np, 0, PXS, 0, 1};
         fft_smem<T, true, block_items(PX)>(sm, f, a.tw, false, true);
     }
     T *out = a.dst_mode == 1 ? a.hist + (size_t)head * 3 * a.n : a.dst;
@@ -477,7 +481,7 @@ __global__ void __launch_bounds__(256, 2) k_xi(const XArgs<T> a)
         const int t = idx >> lgnx, x = idx & (nx - 1);
         const long long r = r0 + t;
         if (r >= R) continue;
-        const cx<T> z = sm[(t >> 1) * Px + x];
+        const cx<T> z = sm[(t >> 1) * PXS + x];
         T v = (t & 1) ? z.y : z.x;
         if (a.self_src) {
             const int c = (int)(r / a.plane);
@@ -709,7 +713,7 @@ __global__ void __launch_bounds__(256, 2) k_yf(const SplitArgs<T> a)
     }
 }
 
-template <typename T, int ITEMS>
+template <typename T, int PZ>
 __global__ void __launch_bounds__(YZ_THREADS) k_zm(const SplitArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -728,15 +732,14 @@ __global__ void __launch_bounds__(YZ_THREADS) k_zm(const SplitArgs<T> a)
         B[c * plane + z * W + w] = src[(size_t)r * Py + w];
     }
     __syncthreads();
-    const FftShape fz{Pz, 3 * W, lgW, plane, 1, W};
-    const bool rz = Pz <= reg_max_len<T>();
-    if (Pz > 1) {
-        if (rz) {
+    const FftShape fz{PZ, 3 * W, lgW, plane, 1, W};
+    if constexpr (PZ > 1) {
+        if constexpr (PZ <= zm_reg_len<T>()) {
             for (int tr = threadIdx.x; tr < 3 * W; tr += blockDim.x)
-                col_fft_any<T, false>(B, Pz, (tr >> lgW) * plane + (tr & (W - 1)), W, nz, Pz, a.twz);
+                col_fft<T, PZ, false>(B, (tr >> lgW) * plane + (tr & (W - 1)), W, nz, PZ, a.twz);
             __syncthreads();
         } else {
-            fft_smem<T, false, ITEMS>(B, fz, a.twz, true, false);
+            fft_smem<T, false, block_items(PZ)>(B, fz, a.twz, true, false);
         }
     }
     const int half = Py >> 1;
@@ -786,13 +789,13 @@ __global__ void __launch_bounds__(YZ_THREADS) k_zm(const SplitArgs<T> a)
         }
     }
     __syncthreads();
-    if (Pz > 1) {
-        if (rz) {
+    if constexpr (PZ > 1) {
+        if constexpr (PZ <= zm_reg_len<T>()) {
             for (int tr = threadIdx.x; tr < 3 * W; tr += blockDim.x)
-                col_fft_any<T, true>(B, Pz, (tr >> lgW) * plane + (tr & (W - 1)), W, Pz, nz, a.twz);
+                col_fft<T, PZ, true>(B, (tr >> lgW) * plane + (tr & (W - 1)), W, PZ, nz, a.twz);
             __syncthreads();
         } else {
-            fft_smem<T, true, ITEMS>(B, fz, a.twz, false, true);
+            fft_smem<T, true, block_items(PZ)>(B, fz, a.twz, false, true);
         }
     }
     cx<T> *dst = a.Tb + (size_t)kx * nrows * Py + ky0;
@@ -1232,7 +1235,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) k_stage(const StageArgs<T> a)
 // ----------------------------------------------------------- host helpers
 template <typename T> size_t x_smem(const mmx_ctx *c, int trows)
 {
-    return padded_words((size_t)((trows + 1) / 2) * 2 * c->nx) * sizeof(cx<T>);
+    return padded_words((size_t)((trows + 1) / 2) * (2 * c->nx + 8)) * sizeof(cx<T>);
 }
 template <typename T> size_t yz_smem(const mmx_ctx *c) { return padded_words((size_t)3 * c->Py * c->Pz) * sizeof(cx<T>); }
 
@@ -1268,7 +1271,7 @@ int pick_trows(const mmx_ctx *c)
     const long long rows = c->rows;
     int tr = 16;
     while (tr > 2 && ((rows + tr - 1) / tr < 2 * 152 ||
-                      padded_words((size_t)(tr / 2) * 2 * c->nx) * 2 * c->esz > 96 * 1024))
+                      padded_words((size_t)(tr / 2) * (2 * c->nx + 8)) * 2 * c->esz > 96 * 1024))
         tr >>= 1;
     return tr;
 }
@@ -1307,6 +1310,11 @@ template <typename T> const void *yz_fn(int L)
 template <typename T> const void *yf_fn(int L)
 {
     switch (L) { MMX_LEN_CASES(k_yf, T) }
+    return nullptr;
+}
+template <typename T> const void *zm_fn(int L)
+{
+    switch (L) { MMX_LEN_CASES(k_zm, T) }
     return nullptr;
 }
 template <typename T> const void *yi_fn(int L)
@@ -1402,12 +1410,10 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
         const dim3 gy(c->nx, (nrows + sa.ry - 1) / sa.ry), gz(c->nx, c->Py / sa.W);
         const size_t sy = yf_smem<T>(c, sa.ry), sz = zm_smem<T>(c);
         const int yt = y_threads<T>(c);
-        const int iz = items_for(c->Pz, YZ_THREADS);
         void *sargs[] = {(void *)&sa};
         timed(1, [&] {
             cudaLaunchKernel(yf_fn<T>(c->Py), gy, dim3(yt), sargs, sy, s);
-            if (iz == 1) k_zm<T, 1><<<gz, YZ_THREADS, sz, s>>>(sa);
-            else k_zm<T, 2><<<gz, YZ_THREADS, sz, s>>>(sa);
+            cudaLaunchKernel(zm_fn<T>(c->Pz), gz, dim3(YZ_THREADS), sargs, sz, s);
             cudaLaunchKernel(yi_fn<T>(c->Py), gy, dim3(yt), sargs, sy, s);
             c->launches += 2;
         });
@@ -1515,7 +1521,7 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
             for (const void *f : fy)
                 if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sy) != cudaSuccess)
                     return MMX_ERR_CUDA;
-        const void *fz[] = {(const void *)k_zm<T, 1>, (const void *)k_zm<T, 2>};
+        const void *fz[] = {zm_fn<T>(c->Pz)};
         if (sz > 48 * 1024)
             for (const void *f : fz)
                 if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz) != cudaSuccess)
