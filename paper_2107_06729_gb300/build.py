@@ -14,7 +14,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmmx.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "mmx_api.cu", "static_demag.cu", "tensor_host.cpp"]
+SOURCES = ["kernels.cu", "fft_fused_f32.cu", "fft_fused_f64.cu", "fft_split.cu", "fft_pipe.cu", "mmx_api.cu",
+           "static_demag.cu", "tensor_host.cpp"]
 
 
 def _deps():
@@ -53,7 +54,7 @@ def build(force=False, verbose=False):
     if not force and not _stale():
         return LIB
     os.makedirs(OUT, exist_ok=True)
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with ThreadPoolExecutor(max_workers=min(len(SOURCES), max(2, os.cpu_count() or 2))) as ex:
         results = list(ex.map(_compile, SOURCES))
     if verbose:
         for _, err in results:

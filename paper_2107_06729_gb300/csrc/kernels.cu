@@ -1,1536 +1,25 @@
-// kernels.cu -- sm_103a kernels of libmmx.
-//
-// Demag field, Eq. 2 (Sec. II), by the convolution theorem on the zero-padded
-// grid Px = 2nx, Py = 2ny (1 if ny == 1), Pz = 2nz (1 if nz == 1), in three
-// passes that keep each byte of the spectrum in HBM/L2 exactly twice:
-//   XF  real-to-complex along x of every (c, z, y) row.  Two rows travel as
-//       one complex sequence; the zero upper half of the padded row is pruned
-//       from the first radix stage.  The real values at kx = 0 and kx = nx
-//       are packed into one complex word, so a row of nx reals becomes nx
-//       complex words.  Output is transposed to S[kx][c][z][y] so that the
-//       next pass reads one contiguous block per kx.
-//   YZ  one CTA per kx column: forward y and z transforms (pruned), the
-//       6-component symmetric tensor multiply H = K M, inverse z and y
-//       transforms truncated to the nz x ny original cells.  The packed
-//       kx = 0 / kx = nx column is unpacked and repacked in Fourier space.
-//   XI  complex-to-real along x, truncated to nx outputs, 1/P and -Ms
-//       already folded into K.  Writes G = H + N00 Ms m (non-self field).
-// All transforms are Stockham radix-8/4/2 FFTs in shared memory
-// (twiddles from a table in global memory).
-//
-// LLG stages, Eq. 1 and 3-4: one fused kernel per stage builds the effective
-// field (6-point exchange Laplacian with free boundaries, uniaxial
-// anisotropy, Zeeman, demag exact or extrapolated by Eq. 6 minus the exact
-// self term), the Landau-Lifshitz torque, and the next stage input.  The
-// last stage forms the propagated and embedded solutions, renormalises,
-// reduces the error norm, and its last CTA runs the controller of Eq. 5.
-#include <cuda_runtime.h>
-#include <math.h>
-#include <stdio.h>
+// kernels.cu -- host entry points of the kernel layer of libmmx: precision
+// dispatch, the kernel-pointer table over the translation units that hold the
+// FFT kernel families, and the stage kernels (instantiated here).
+#include "kernels_impl.cuh"
 
-#include <algorithm>
-#include <vector>
+const void *mmxk_tab_fused(int kind, bool f64, int L);  // fft_fused_f32.cu / fft_fused_f64.cu
+const void *mmxk_tab_split(int kind, bool f64, int L);  // fft_split.cu
+const void *mmxk_tab_pipe(int kind, bool f64, int L);   // fft_pipe.cu
 
-#include "internal.h"
-
-namespace {
-
-template <typename T> struct cx {
-    T x, y;
-};
-
-template <typename T> __device__ __forceinline__ cx<T> mk(T x, T y)
+const void *mmxk_kernel(int kind, bool f64, int L)
 {
-    cx<T> r;
-    r.x = x;
-    r.y = y;
-    return r;
-}
-template <typename T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return mk(a.x + b.x, a.y + b.y); }
-template <typename T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return mk(a.x - b.x, a.y - b.y); }
-template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b)
-{
-    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-template <typename T> __device__ __forceinline__ cx<T> cscale(T s, cx<T> a) { return mk(s * a.x, s * a.y); }
-
-// Shared-memory view with one padding word per 8 complex words: the
-// stride-R stores of the early Stockham stages then spread over all banks.
-template <typename T> struct Pad {
-    cx<T> *p;
-    int base;
-    __device__ __forceinline__ cx<T> &operator[](int i) const
-    {
-        const int j = base + i;
-        return p[j + (j >> 3)];
-    }
-    __device__ __forceinline__ Pad at(int off) const { return Pad{p, base + off}; }
-};
-// words of shared memory for n padded complex words
-__host__ __device__ constexpr size_t padded_words(size_t n) { return n + n / 8 + 1; }
-
-// multiply by -i (forward) or +i (inverse)
-template <typename T, bool INV> __device__ __forceinline__ cx<T> rot(cx<T> a)
-{
-    return INV ? mk(-a.y, a.x) : mk(a.y, -a.x);
-}
-
-template <typename T, bool INV> __device__ __forceinline__ void dft4(cx<T> &v0, cx<T> &v1, cx<T> &v2, cx<T> &v3)
-{
-    cx<T> a = cadd(v0, v2), b = csub(v0, v2), c = cadd(v1, v3), d = rot<T, INV>(csub(v1, v3));
-    v0 = cadd(a, c);
-    v1 = cadd(b, d);
-    v2 = csub(a, c);
-    v3 = csub(b, d);
-}
-
-template <typename T, int R, bool INV> struct Dft;
-template <typename T, bool INV> struct Dft<T, 2, INV> {
-    static __device__ __forceinline__ void run(cx<T> *v)
-    {
-        cx<T> a = v[0];
-        v[0] = cadd(a, v[1]);
-        v[1] = csub(a, v[1]);
-    }
-};
-template <typename T, bool INV> struct Dft<T, 4, INV> {
-    static __device__ __forceinline__ void run(cx<T> *v) { dft4<T, INV>(v[0], v[1], v[2], v[3]); }
-};
-template <typename T, bool INV> struct Dft<T, 8, INV> {
-    static __device__ __forceinline__ void run(cx<T> *v)
-    {
-        cx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
-        cx<T> o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
-        dft4<T, INV>(e0, e1, e2, e3);
-        dft4<T, INV>(o0, o1, o2, o3);
-        const T r = (T)0.70710678118654752440084436210485;  // sqrt(1/2)
-        cx<T> t1, t2, t3;
-        if (!INV) {
-            t1 = mk(r * (o1.x + o1.y), r * (o1.y - o1.x));
-            t2 = mk(o2.y, -o2.x);
-            t3 = mk(r * (o3.y - o3.x), -r * (o3.x + o3.y));
-        } else {
-            t1 = mk(r * (o1.x - o1.y), r * (o1.x + o1.y));
-            t2 = mk(-o2.y, o2.x);
-            t3 = mk(-r * (o3.x + o3.y), r * (o3.x - o3.y));
-        }
-        v[0] = cadd(e0, o0);
-        v[4] = csub(e0, o0);
-        v[1] = cadd(e1, t1);
-        v[5] = csub(e1, t1);
-        v[2] = cadd(e2, t2);
-        v[6] = csub(e2, t2);
-        v[3] = cadd(e3, t3);
-        v[7] = csub(e3, t3);
-    }
-};
-
-// A batch of `count` transforms of length L held in shared memory; transform
-// tr starts at (tr >> lg_lo) * s_hi + (tr & (2^lg_lo - 1)) * s_lo and its
-// elements are es apart.
-struct FftShape {
-    int L, count, lg_lo, s_hi, s_lo, es;
-};
-
-// One Stockham stage (radix R, Ns = product of the previous radices).  All
-// threads of the CTA take part; loads of a window of whole transforms
-// complete before any store, so the stage runs in place.
-template <typename T, int R, bool INV, int ITEMS>
-__device__ __forceinline__ void fft_stage(const Pad<T> buf, const FftShape &f, int Ns, const cx<T> *__restrict__ tw,
-                                          bool prune, bool trunc)
-{
-    const int per = f.L / R;
-    const int lgper = __ffs(per) - 1;
-    const int total = f.count * per;
-    const int W = blockDim.x * ITEMS;
-    const int tstride = f.L / (Ns * R);
-    const int half = f.L >> 1;
-    const int lomask = (1 << f.lg_lo) - 1;
-    for (int w0 = 0; w0 < total; w0 += W) {
-        cx<T> v[ITEMS][R];
-        int off[ITEMS], jj[ITEMS];
-#pragma unroll
-        for (int it = 0; it < ITEMS; ++it) {
-            const int item = w0 + it * blockDim.x + threadIdx.x;
-            off[it] = -1;
-            jj[it] = 0;
-            if (item < total) {
-                const int tr = item >> lgper, j = item & (per - 1);
-                const int o = (tr >> f.lg_lo) * f.s_hi + (tr & lomask) * f.s_lo;
-                off[it] = o;
-                jj[it] = j;
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    v[it][r] = (prune && r >= R / 2) ? mk<T>(0, 0) : buf[o + (j + r * per) * f.es];
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int it = 0; it < ITEMS; ++it) {
-            if (off[it] < 0) continue;
-            const int j = jj[it], k = j & (Ns - 1);
-            if (Ns > 1) {
-#pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    cx<T> w = tw[r * k * tstride];
-                    if (INV) w.y = -w.y;
-                    v[it][r] = cmul(v[it][r], w);
-                }
-            }
-            Dft<T, R, INV>::run(v[it]);
-            const int d = (j - k) * R + k;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int pos = d + r * Ns;
-                if (!trunc || pos < half) buf[off[it] + pos * f.es] = v[it][r];
-            }
-        }
-        __syncthreads();
+    switch (kind) {
+    case K_XF:
+    case K_XI:
+    case K_YZ: return mmxk_tab_fused(kind, f64, L);
+    case K_YF:
+    case K_YI:
+    case K_ZM: return mmxk_tab_split(kind, f64, L);
+    default: return mmxk_tab_pipe(kind, f64, L);
     }
 }
 
-// Full transform: radix 8 while possible (16 as 4 x 4), then 4 or 2.
-// prune: the upper half of every input is zero and is not read.
-// trunc: only the lower half of the outputs is written.
-template <typename T, bool INV, int ITEMS>
-__device__ void fft_smem(const Pad<T> buf, const FftShape &f, const cx<T> *__restrict__ tw, bool prune, bool trunc)
-{
-    int Ns = 1, rem = f.L;
-    bool first = true;
-    while (rem > 1) {
-        int R = (rem % 8 == 0 && rem != 16) ? 8 : (rem % 4 == 0 ? 4 : 2);
-        bool last = (rem == R);
-        if (R == 8)
-            fft_stage<T, 8, INV, ITEMS>(buf, f, Ns, tw, first && prune, last && trunc);
-        else if (R == 4)
-            fft_stage<T, 4, INV, ITEMS>(buf, f, Ns, tw, first && prune, last && trunc);
-        else
-            fft_stage<T, 2, INV, ITEMS>(buf, f, Ns, tw, first && prune, last && trunc);
-        Ns *= R;
-        rem /= R;
-        first = false;
-    }
-}
-
-__device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
-
-// ---- warp-level transforms: one warp owns a whole transform of length L
-// (elements es apart in a padded shared-memory view) and runs the Stockham
-// stages with __syncwarp only, so warps of a CTA proceed independently.
-template <typename T, int R, bool INV, int IT>
-__device__ __forceinline__ void warp_stage(const Pad<T> buf, int L, int es, int Ns, const cx<T> *__restrict__ tw,
-                                           bool prune, bool trunc)
-{
-    const int lane = threadIdx.x & 31;
-    const int per = L / R;
-    const int tstride = L / (Ns * R);
-    const int half = L >> 1;
-    cx<T> v[IT][R];
-#pragma unroll
-    for (int it = 0; it < IT; ++it) {
-        const int j = lane + 32 * it;
-        if (j < per) {
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                v[it][r] = (prune && r >= R / 2) ? mk<T>(0, 0) : buf[(j + r * per) * es];
-        }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int it = 0; it < IT; ++it) {
-        const int j = lane + 32 * it;
-        if (j >= per) continue;
-        const int k = j & (Ns - 1);
-        if (Ns > 1) {
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                cx<T> w = tw[r * k * tstride];
-                if (INV) w.y = -w.y;
-                v[it][r] = cmul(v[it][r], w);
-            }
-        }
-        Dft<T, R, INV>::run(v[it]);
-        const int d = (j - k) * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int pos = d + r * Ns;
-            if (!trunc || pos < half) buf[pos * es] = v[it][r];
-        }
-    }
-    __syncwarp();
-}
-
-// largest transform a single warp handles (register budget of the stages)
-template <typename T> __host__ __device__ constexpr int warp_max_len() { return sizeof(T) == 4 ? 1024 : 256; }
-
-// compile-time stage sequence of a length-L transform (radix 8 while
-// possible, 16 as 4 x 4, then 4 or 2): fixed shapes let the compiler keep
-// the register footprint of the largest stage only
-template <typename T, bool INV, int L, int NS> struct WarpFFT {
-    static __device__ __forceinline__ void run(const Pad<T> buf, int es, const cx<T> *tw, bool prune, bool trunc)
-    {
-        constexpr int REM = L / NS;
-        constexpr int R = (REM % 8 == 0 && REM != 16) ? 8 : ((REM % 4 == 0) ? 4 : 2);
-        constexpr int PER = L / R;
-        constexpr int IT = PER <= 32 ? 1 : PER / 32;
-        warp_stage<T, R, INV, IT>(buf, L, es, NS, tw, NS == 1 && prune, REM == R && trunc);
-        WarpFFT<T, INV, L, NS * R>::run(buf, es, tw, prune, trunc);
-    }
-};
-template <typename T, bool INV, int L> struct WarpFFT<T, INV, L, L> {
-    static __device__ __forceinline__ void run(const Pad<T>, int, const cx<T> *, bool, bool) {}
-};
-
-// items per thread when a CTA of 256 threads runs each stage of a length-L
-// transform together (transforms too long for one warp)
-__host__ __device__ constexpr int block_items(int L)
-{
-    return ((L <= 2 ? 1 : L / 4) <= 256) ? 1 : (L / 4) / 256;
-}
-
-// ---- register-level transforms for short lengths (the z axis): one thread
-// holds the whole sequence; Stockham stages unrolled at compile time.
-template <typename T, int L, int NS, bool INV> struct RegFFT {
-    static __device__ __forceinline__ void run(cx<T> *v, const cx<T> *__restrict__ tw)
-    {
-        constexpr int REM = L / NS;
-        constexpr int R = (REM % 8 == 0 && REM != 16) ? 8 : ((REM % 4 == 0) ? 4 : 2);
-        constexpr int PER = L / R;
-        cx<T> out[L];
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            cx<T> u[R];
-            const int k = j % NS;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                u[r] = v[j + r * PER];
-                if (NS > 1 && r > 0) {
-                    cx<T> w = tw[r * k * (L / (NS * R))];
-                    if (INV) w.y = -w.y;
-                    u[r] = cmul(u[r], w);
-                }
-            }
-            Dft<T, R, INV>::run(u);
-            const int d = (j - k) * R + k;
-#pragma unroll
-            for (int r = 0; r < R; ++r) out[d + r * NS] = u[r];
-        }
-#pragma unroll
-        for (int i = 0; i < L; ++i) v[i] = out[i];
-        RegFFT<T, L, NS * R, INV>::run(v, tw);
-    }
-};
-template <typename T, int L, bool INV> struct RegFFT<T, L, L, INV> {
-    static __device__ __forceinline__ void run(cx<T> *, const cx<T> *) {}
-};
-
-// one column of length L at buf[base + i*es]: the first nload entries are
-// read (the rest are zero), the first nstore results are written
-template <typename T, int L, bool INV>
-__device__ __forceinline__ void col_fft(const Pad<T> buf, int base, int es, int nload, int nstore,
-                                        const cx<T> *__restrict__ tw)
-{
-    cx<T> v[L];
-#pragma unroll
-    for (int i = 0; i < L; ++i) v[i] = i < nload ? buf[base + i * es] : mk<T>(0, 0);
-    RegFFT<T, L, 1, INV>::run(v, tw);
-#pragma unroll
-    for (int i = 0; i < L; ++i)
-        if (i < nstore) buf[base + i * es] = v[i];
-}
-
-template <typename T> __host__ __device__ constexpr int reg_max_len() { return sizeof(T) == 4 ? 16 : 8; }
-// ZM holds nothing else in registers during its z transforms: one longer length
-template <typename T> __host__ __device__ constexpr int zm_reg_len() { return sizeof(T) == 4 ? 32 : 16; }
-
-template <typename T, bool INV>
-__device__ __forceinline__ void col_fft_any(const Pad<T> buf, int L, int base, int es, int nload, int nstore,
-                                            const cx<T> *__restrict__ tw)
-{
-    switch (L) {
-    case 2: col_fft<T, 2, INV>(buf, base, es, nload, nstore, tw); break;
-    case 4: col_fft<T, 4, INV>(buf, base, es, nload, nstore, tw); break;
-    case 8: col_fft<T, 8, INV>(buf, base, es, nload, nstore, tw); break;
-    default:
-        if (sizeof(T) == 4) col_fft<T, (sizeof(T) == 4 ? 16 : 8), INV>(buf, base, es, nload, nstore, tw);
-        break;
-    }
-}
-
-// ------------------------------------------------------------------ XF / XI
-template <typename T> struct XArgs {
-    const T *src;        // src_mode 0
-    const T *msrc0, *msrc1;  // src_mode 1: m[cur]
-    T *dst;              // dst_mode 0
-    T *hist;             // dst_mode 1: hist + head * 3n
-    const T *self_src;   // optional: subtract Ms N00 self_src
-    cx<T> *S;
-    const cx<T> *tw;
-    DevState *st;
-    long long rows, n;
-    int nx, trows, stage0, src_mode, dst_mode, plane;  // plane = ny*nz
-    double msN00[3];
-};
-
-constexpr int X_THREADS = 128;
-constexpr int YZ_THREADS = 256;
-
-// Items per thread of one FFT stage: a window of threads*items work items
-// must hold all items of one transform; the largest stage has L/4 of them
-// (L/2 only for L = 2).
-int items_for(int L, int threads)
-{
-    const int per = L <= 2 ? 1 : L / 4;
-    int it = 1;
-    while (threads * it < per) it *= 2;
-    return it;
-}
-
-template <typename T, int PX>
-__global__ void __launch_bounds__(256, 2) k_xf(const XArgs<T> a)
-{
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
-    if (a.st) {
-        if (a.st->done) return;
-        if (a.stage0 && a.st->f1_valid) return;
-    }
-    const T *src = a.src_mode == 1 ? (a.st->cur ? a.msrc1 : a.msrc0) : a.src;
-    const int nx = a.nx, Px = 2 * nx, lgnx = ilog2(nx);
-    constexpr int PXS = PX + 8;  // pair stride: pairs land in different banks
-    const int np = (a.trows + 1) >> 1;
-    const long long R = a.rows, r0 = (long long)blockIdx.x * a.trows;
-    for (int idx = threadIdx.x; idx < np * nx; idx += blockDim.x) {
-        const int p = idx >> lgnx, x = idx & (nx - 1);
-        const long long ra = r0 + 2 * p, rb = ra + 1;
-        T va = (2 * p < a.trows && ra < R) ? src[ra * nx + x] : (T)0;
-        T vb = (2 * p + 1 < a.trows && rb < R) ? src[rb * nx + x] : (T)0;
-        sm[p * PXS + x] = mk(va, vb);
-    }
-    __syncthreads();
-    if constexpr (PX <= warp_max_len<T>()) {
-        for (int pr = threadIdx.x >> 5; pr < np; pr += blockDim.x >> 5)
-            WarpFFT<T, false, PX, 1>::run(sm.at(pr * PXS), 1, a.tw, true, false);
-        __syncthreads();
-    } else {
-        const FftShape f{PX, np, 0, PXS, 0, 1};
-        fft_smem<T, false, block_items(PX)>(sm, f, a.tw, true, false);
-    }
-    // separate the two real rows and pack kx = 0 with kx = nx
-    const int T_ = a.trows;
-    for (int idx = threadIdx.x; idx < nx * T_; idx += blockDim.x) {
-        const int k = idx / T_, t = idx - k * T_;
-        const long long r = r0 + t;
-        if (r >= R) continue;
-        const Pad<T> z = sm.at((t >> 1) * PXS);
-        cx<T> v;
-        if (k == 0) {
-            const cx<T> z0 = z[0], zn = z[nx];
-            v = (t & 1) ? mk(z0.y, zn.y) : mk(z0.x, zn.x);
-        } else {
-            const cx<T> zk = z[k], zm = z[Px - k];
-            const T hlf = (T)0.5;
-            v = (t & 1) ? mk(hlf * (zk.y + zm.y), hlf * (zm.x - zk.x)) : mk(hlf * (zk.x + zm.x), hlf * (zk.y - zm.y));
-        }
-        a.S[(long long)k * R + r] = v;
-    }
-}
-
-template <typename T, int PX>
-__global__ void __launch_bounds__(256, 2) k_xi(const XArgs<T> a)
-{
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
-    int head = 0;
-    if (a.st) {
-        if (a.st->done) return;
-        if (a.stage0 && a.st->f1_valid) return;
-        head = a.st->head;
-    }
-    const int nx = a.nx, Px = 2 * nx;
-    constexpr int PXS = PX + 8;  // pair stride: pairs land in different banks
-    const int np = (a.trows + 1) >> 1;
-    const long long R = a.rows, r0 = (long long)blockIdx.x * a.trows;
-    for (int idx = threadIdx.x; idx < np * nx; idx += blockDim.x) {
-        const int k = idx / np, p = idx - k * np;
-        const long long ra = r0 + 2 * p, rb = ra + 1;
-        const cx<T> zero = mk<T>(0, 0);
-        const cx<T> va = (2 * p < a.trows && ra < R) ? a.S[(long long)k * R + ra] : zero;
-        const cx<T> vb = (2 * p + 1 < a.trows && rb < R) ? a.S[(long long)k * R + rb] : zero;
-        const Pad<T> z = sm.at(p * PXS);
-        if (k == 0) {
-            z[0] = mk(va.x, vb.x);
-            z[nx] = mk(va.y, vb.y);
-        } else {
-            z[k] = mk(va.x - vb.y, va.y + vb.x);
-            z[Px - k] = mk(va.x + vb.y, vb.x - va.y);
-        }
-    }
-    __syncthreads();
-    if constexpr (PX <= warp_max_len<T>()) {
-        for (int pr = threadIdx.x >> 5; pr < np; pr += blockDim.x >> 5)
-            WarpFFT<T, true, PX, 1>::run(sm.at(pr * PXS), 1, a.tw, false, true);
-        __syncthreads();
-    } else {
-        const FftShape f{PX, np, 0, PXS, 0, 1};
-        fft_smem<T, true, block_items(PX)>(sm, f, a.tw, false, true);
-    }
-    T *out = a.dst_mode == 1 ? a.hist + (size_t)head * 3 * a.n : a.dst;
-    const int T_ = a.trows, lgnx = ilog2(nx);
-    for (int idx = threadIdx.x; idx < T_ * nx; idx += blockDim.x) {
-        const int t = idx >> lgnx, x = idx & (nx - 1);
-        const long long r = r0 + t;
-        if (r >= R) continue;
-        const cx<T> z = sm[(t >> 1) * PXS + x];
-        T v = (t & 1) ? z.y : z.x;
-        if (a.self_src) {
-            const int c = (int)(r / a.plane);
-            v -= (T)a.msN00[c] * a.self_src[r * nx + x];
-        }
-        out[r * nx + x] = v;
-    }
-    if (a.st && blockIdx.x == 0 && threadIdx.x == 0) a.st->exact_evals++;
-}
-
-// ---------------------------------------------------------------------- YZ
-template <typename T> struct YZArgs {
-    cx<T> *S;
-    const T *K;  // [(kx*Hz + kz)*Hy + ky][6]
-    const cx<T> *twy, *twz;
-    DevState *st;
-    long long rows;
-    int nx, ny, nz, Py, Pz, Hy, Hz, stage0;
-};
-
-template <typename T>
-__device__ __forceinline__ void load_K(const T *K, int kx, int Hy, int Hz, int Py, int Pz, int ky, int kz, T k6[6])
-{
-    const bool fy = ky > (Py >> 1), fz = kz > (Pz >> 1);
-    const int y = fy ? Py - ky : ky, z = fz ? Pz - kz : kz;
-    const T *p = K + ((size_t)((size_t)kx * Hz + z) * Hy + y) * 6;
-    const T sy = fy ? (T)-1 : (T)1, sz = fz ? (T)-1 : (T)1;
-    k6[0] = p[0];
-    k6[1] = p[1];
-    k6[2] = p[2];
-    k6[3] = sy * p[3];
-    k6[4] = sz * p[4];
-    k6[5] = sy * sz * p[5];
-}
-
-template <typename T>
-__device__ __forceinline__ void apply_K(const T k[6], cx<T> mx, cx<T> my, cx<T> mz, cx<T> &hx, cx<T> &hy, cx<T> &hz)
-{
-    hx = mk(k[0] * mx.x + k[3] * my.x + k[4] * mz.x, k[0] * mx.y + k[3] * my.y + k[4] * mz.y);
-    hy = mk(k[3] * mx.x + k[1] * my.x + k[5] * mz.x, k[3] * mx.y + k[1] * my.y + k[5] * mz.y);
-    hz = mk(k[4] * mx.x + k[5] * my.x + k[2] * mz.x, k[4] * mx.y + k[5] * my.y + k[2] * mz.y);
-}
-
-template <typename T, int PY>
-__global__ void __launch_bounds__(YZ_THREADS, 2) k_yz(const YZArgs<T> a)
-{
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const Pad<T> B{reinterpret_cast<cx<T> *>(smraw), 0};
-    if (a.st) {
-        if (a.st->done) return;
-        if (a.stage0 && a.st->f1_valid) return;
-    }
-    const int kx = blockIdx.x;
-    const int ny = a.ny, nz = a.nz, Py = a.Py, Pz = a.Pz;
-    const int plane = Py * Pz, lgny = ilog2(ny), lgnz = ilog2(nz), lgPy = ilog2(Py);
-    cx<T> *S = a.S + (size_t)kx * a.rows;
-    const int rows = (int)a.rows;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-        const int y = r & (ny - 1), cz = r >> lgny, z = cz & (nz - 1), c = cz >> lgnz;
-        B[c * plane + z * Py + y] = S[r];
-    }
-    __syncthreads();
-    const FftShape fy{Py, 3 * nz, lgnz, plane, Py, 1};
-    const FftShape fz{Pz, 3 * Py, lgPy, plane, 1, Py};
-    const bool rz = Pz <= reg_max_len<T>();
-    const int nwarp = blockDim.x >> 5, warp = threadIdx.x >> 5;
-    if constexpr (PY > 1) {
-        if constexpr (PY <= warp_max_len<T>()) {
-            for (int tr = warp; tr < 3 * nz; tr += nwarp)
-                WarpFFT<T, false, PY, 1>::run(B.at((tr >> lgnz) * plane + (tr & (nz - 1)) * PY), 1, a.twy, true,
-                                              false);
-            __syncthreads();
-        } else {
-            fft_smem<T, false, block_items(PY)>(B, fy, a.twy, true, false);
-        }
-    }
-    if (Pz > 1) {
-        if (rz) {
-            for (int tr = threadIdx.x; tr < 3 * Py; tr += blockDim.x)
-                col_fft_any<T, false>(B, Pz, (tr >> lgPy) * plane + (tr & (Py - 1)), Py, nz, Pz, a.twz);
-            __syncthreads();
-        } else {
-            fft_smem<T, false, 2>(B, fz, a.twz, true, false);
-        }
-    }
-
-    // Fourier-space tensor multiply (Eq. 2): H = K M, K real symmetric
-    if (kx != 0) {
-        for (int q = threadIdx.x; q < plane; q += blockDim.x) {
-            const int ky = q & (Py - 1), kz = q >> lgPy;
-            T k6[6];
-            load_K(a.K, kx, a.Hy, a.Hz, Py, Pz, ky, kz, k6);
-            cx<T> hx, hy, hz;
-            apply_K(k6, B[q], B[plane + q], B[2 * plane + q], hx, hy, hz);
-            B[q] = hx;
-            B[plane + q] = hy;
-            B[2 * plane + q] = hz;
-        }
-    } else {
-        // packed column u = X(kx=0) + i X(kx=nx), both real along x:
-        // V(k) = P U(k) + Q conj(U(-k)), P = (K0 + KN)/2, Q = (K0 - KN)/2
-        for (int q = threadIdx.x; q < plane; q += blockDim.x) {
-            const int ky = q & (Py - 1), kz = q >> lgPy;
-            const int qm = ((Pz - kz) & (Pz - 1)) * Py + ((Py - ky) & (Py - 1));
-            if (q > qm) continue;
-            T k0[6], kn[6], P[6], Q[6];
-            load_K(a.K, 0, a.Hy, a.Hz, Py, Pz, ky, kz, k0);
-            load_K(a.K, a.nx, a.Hy, a.Hz, Py, Pz, ky, kz, kn);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                P[i] = (T)0.5 * (k0[i] + kn[i]);
-                Q[i] = (T)0.5 * (k0[i] - kn[i]);
-            }
-            const cx<T> ux = B[q], uy = B[plane + q], uz = B[2 * plane + q];
-            const cx<T> vx = B[qm], vy = B[plane + qm], vz = B[2 * plane + qm];
-            const cx<T> cvx = mk(vx.x, -vx.y), cvy = mk(vy.x, -vy.y), cvz = mk(vz.x, -vz.y);
-            cx<T> a1, a2, a3, b1, b2, b3;
-            apply_K(P, ux, uy, uz, a1, a2, a3);
-            apply_K(Q, cvx, cvy, cvz, b1, b2, b3);
-            B[q] = cadd(a1, b1);
-            B[plane + q] = cadd(a2, b2);
-            B[2 * plane + q] = cadd(a3, b3);
-            if (qm != q) {
-                const cx<T> cux = mk(ux.x, -ux.y), cuy = mk(uy.x, -uy.y), cuz = mk(uz.x, -uz.y);
-                apply_K(P, vx, vy, vz, a1, a2, a3);
-                apply_K(Q, cux, cuy, cuz, b1, b2, b3);
-                B[qm] = cadd(a1, b1);
-                B[plane + qm] = cadd(a2, b2);
-                B[2 * plane + qm] = cadd(a3, b3);
-            }
-        }
-    }
-    __syncthreads();
-    if (Pz > 1) {
-        if (rz) {
-            for (int tr = threadIdx.x; tr < 3 * Py; tr += blockDim.x)
-                col_fft_any<T, true>(B, Pz, (tr >> lgPy) * plane + (tr & (Py - 1)), Py, Pz, nz, a.twz);
-            __syncthreads();
-        } else {
-            fft_smem<T, true, 2>(B, fz, a.twz, false, true);
-        }
-    }
-    if constexpr (PY > 1) {
-        if constexpr (PY <= warp_max_len<T>()) {
-            for (int tr = warp; tr < 3 * nz; tr += nwarp)
-                WarpFFT<T, true, PY, 1>::run(B.at((tr >> lgnz) * plane + (tr & (nz - 1)) * PY), 1, a.twy, false,
-                                             true);
-            __syncthreads();
-        } else {
-            fft_smem<T, true, block_items(PY)>(B, fy, a.twy, false, true);
-        }
-    }
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-        const int y = r & (ny - 1), cz = r >> lgny, z = cz & (nz - 1), c = cz >> lgnz;
-        S[r] = B[c * plane + z * Py + y];
-    }
-}
-
-// ------------------------------------------------------- split y / z passes
-// For meshes whose padded y-z column does not fit one CTA (3 Py Pz complex
-// words), the YZ pass is split into three streaming kernels over the buffer
-// Tb[kx][c*nz + z][ky] (complex, Py per row):
-//   YF  forward y transform of each (kx, c, z) row (pruned).
-//   ZM  per (kx, tile of W ky values): forward z transform (pruned), tensor
-//       multiply, inverse z transform truncated to nz.
-//   YI  inverse y transform truncated to ny.
-// The packed kx = 0 column (u = X(kx=0) + i X(kx=nx), both real in y and z)
-// is separated along y in YF, using A(ky) = (U(ky) + conj U(-ky))/2 and
-// B(ky) = (U(ky) - conj U(-ky))/(2i), both Hermitian in ky: slot ky in
-// [1, Py/2) holds A(ky), slot Py - ky holds B(ky), slots 0 and Py/2 hold
-// the real pair (A, B) there.  ZM multiplies A by K(kx=0), B by K(kx=nx),
-// and the two real-pair slots by the packed rule along kz; YI recombines.
-template <typename T> struct SplitArgs {
-    cx<T> *S;      // [kx][c][z][y]
-    cx<T> *Tb;     // [kx][c*nz + z][ky]
-    const T *K;
-    const cx<T> *twy, *twz;
-    DevState *st;
-    long long rows;  // 3 ny nz
-    int nx, ny, nz, Py, Pz, Hy, Hz, stage0, ry, W;
-};
-
-template <typename T, int PY>
-__global__ void __launch_bounds__(256, 2) k_yf(const SplitArgs<T> a)
-{
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
-    if (a.st) {
-        if (a.st->done) return;
-        if (a.stage0 && a.st->f1_valid) return;
-    }
-    const int kx = blockIdx.x, Py = a.Py, ny = a.ny, lgny = ilog2(ny);
-    const int nrows = 3 * a.nz, r0 = blockIdx.y * a.ry;
-    const int nr = min(a.ry, nrows - r0);
-    const cx<T> *src = a.S + (size_t)kx * a.rows + (size_t)r0 * ny;
-    for (int idx = threadIdx.x; idx < nr * ny; idx += blockDim.x) {
-        const int r = idx >> lgny, y = idx & (ny - 1);
-        sm[r * Py + y] = src[idx];
-    }
-    __syncthreads();
-    if constexpr (PY <= warp_max_len<T>()) {
-        for (int r = threadIdx.x >> 5; r < nr; r += blockDim.x >> 5)
-            WarpFFT<T, false, PY, 1>::run(sm.at(r * PY), 1, a.twy, true, false);
-        __syncthreads();
-    } else {
-        const FftShape f{PY, nr, 0, PY, 0, 1};
-        fft_smem<T, false, block_items(PY)>(sm, f, a.twy, true, false);
-    }
-    cx<T> *dst = a.Tb + ((size_t)kx * nrows + r0) * Py;
-    const int lgPy = ilog2(Py), half = Py >> 1;
-    for (int idx = threadIdx.x; idx < nr * Py; idx += blockDim.x) {
-        const int r = idx >> lgPy, q = idx & (Py - 1);
-        const Pad<T> u = sm.at(r * Py);
-        cx<T> v;
-        if (kx != 0) {
-            v = u[q];
-        } else if (q == 0 || q == half) {
-            const cx<T> z = u[q];  // A and B real here
-            v = z;
-        } else if (q < half) {
-            const cx<T> z = u[q], zm = u[Py - q];
-            v = mk((T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y));  // A(q)
-        } else {
-            const int ky = Py - q;
-            const cx<T> z = u[ky], zm = u[q];
-            v = mk((T)0.5 * (z.y + zm.y), (T)0.5 * (zm.x - z.x));  // B(ky)
-        }
-        dst[idx] = v;
-    }
-}
-
-template <typename T, int PZ>
-__global__ void __launch_bounds__(YZ_THREADS) k_zm(const SplitArgs<T> a)
-{
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const Pad<T> B{reinterpret_cast<cx<T> *>(smraw), 0};
-    if (a.st) {
-        if (a.st->done) return;
-        if (a.stage0 && a.st->f1_valid) return;
-    }
-    const int kx = blockIdx.x, W = a.W, ky0 = blockIdx.y * W;
-    const int nz = a.nz, Pz = a.Pz, Py = a.Py, lgW = ilog2(W), lgnz = ilog2(nz);
-    const int nrows = 3 * nz, plane = Pz * W;
-    const cx<T> *src = a.Tb + (size_t)kx * nrows * Py + ky0;
-    for (int idx = threadIdx.x; idx < nrows * W; idx += blockDim.x) {
-        const int r = idx >> lgW, w = idx & (W - 1);
-        const int c = r >> lgnz, z = r & (nz - 1);
-        B[c * plane + z * W + w] = src[(size_t)r * Py + w];
-    }
-    __syncthreads();
-    const FftShape fz{PZ, 3 * W, lgW, plane, 1, W};
-    if constexpr (PZ > 1) {
-        if constexpr (PZ <= zm_reg_len<T>()) {
-            for (int tr = threadIdx.x; tr < 3 * W; tr += blockDim.x)
-                col_fft<T, PZ, false>(B, (tr >> lgW) * plane + (tr & (W - 1)), W, nz, PZ, a.twz);
-            __syncthreads();
-        } else {
-            fft_smem<T, false, block_items(PZ)>(B, fz, a.twz, true, false);
-        }
-    }
-    const int half = Py >> 1;
-    for (int q = threadIdx.x; q < plane; q += blockDim.x) {
-        const int w = q & (W - 1), kz = q >> lgW, slot = ky0 + w;
-        if (kx != 0 || (slot != 0 && slot != half)) {
-            T k6[6];
-            if (kx != 0)
-                load_K(a.K, kx, a.Hy, a.Hz, Py, Pz, slot, kz, k6);
-            else if (slot < half)
-                load_K(a.K, 0, a.Hy, a.Hz, Py, Pz, slot, kz, k6);
-            else
-                load_K(a.K, a.nx, a.Hy, a.Hz, Py, Pz, Py - slot, kz, k6);
-            cx<T> hx, hy, hz;
-            apply_K(k6, B[q], B[plane + q], B[2 * plane + q], hx, hy, hz);
-            B[q] = hx;
-            B[plane + q] = hy;
-            B[2 * plane + q] = hz;
-        } else {
-            // real pair (A, B) in one slot: packed rule along kz
-            const int kzm = (Pz - kz) & (Pz - 1);
-            if (kz > kzm) continue;
-            const int qm = kzm * W + w;
-            T k0[6], kn[6], P[6], Q[6];
-            load_K(a.K, 0, a.Hy, a.Hz, Py, Pz, slot, kz, k0);
-            load_K(a.K, a.nx, a.Hy, a.Hz, Py, Pz, slot, kz, kn);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                P[i] = (T)0.5 * (k0[i] + kn[i]);
-                Q[i] = (T)0.5 * (k0[i] - kn[i]);
-            }
-            const cx<T> ux = B[q], uy = B[plane + q], uz = B[2 * plane + q];
-            const cx<T> vx = B[qm], vy = B[plane + qm], vz = B[2 * plane + qm];
-            cx<T> a1, a2, a3, b1, b2, b3;
-            apply_K(P, ux, uy, uz, a1, a2, a3);
-            apply_K(Q, mk(vx.x, -vx.y), mk(vy.x, -vy.y), mk(vz.x, -vz.y), b1, b2, b3);
-            B[q] = cadd(a1, b1);
-            B[plane + q] = cadd(a2, b2);
-            B[2 * plane + q] = cadd(a3, b3);
-            if (qm != q) {
-                apply_K(P, vx, vy, vz, a1, a2, a3);
-                apply_K(Q, mk(ux.x, -ux.y), mk(uy.x, -uy.y), mk(uz.x, -uz.y), b1, b2, b3);
-                B[qm] = cadd(a1, b1);
-                B[plane + qm] = cadd(a2, b2);
-                B[2 * plane + qm] = cadd(a3, b3);
-            }
-        }
-    }
-    __syncthreads();
-    if constexpr (PZ > 1) {
-        if constexpr (PZ <= zm_reg_len<T>()) {
-            for (int tr = threadIdx.x; tr < 3 * W; tr += blockDim.x)
-                col_fft<T, PZ, true>(B, (tr >> lgW) * plane + (tr & (W - 1)), W, PZ, nz, a.twz);
-            __syncthreads();
-        } else {
-            fft_smem<T, true, block_items(PZ)>(B, fz, a.twz, false, true);
-        }
-    }
-    cx<T> *dst = a.Tb + (size_t)kx * nrows * Py + ky0;
-    for (int idx = threadIdx.x; idx < nrows * W; idx += blockDim.x) {
-        const int r = idx >> lgW, w = idx & (W - 1);
-        const int c = r >> lgnz, z = r & (nz - 1);
-        dst[(size_t)r * Py + w] = B[c * plane + z * W + w];
-    }
-}
-
-template <typename T, int PY>
-__global__ void __launch_bounds__(256, 2) k_yi(const SplitArgs<T> a)
-{
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
-    if (a.st) {
-        if (a.st->done) return;
-        if (a.stage0 && a.st->f1_valid) return;
-    }
-    const int kx = blockIdx.x, Py = a.Py, ny = a.ny, lgny = ilog2(ny), lgPy = ilog2(Py);
-    const int nrows = 3 * a.nz, r0 = blockIdx.y * a.ry;
-    const int nr = min(a.ry, nrows - r0);
-    const cx<T> *src = a.Tb + ((size_t)kx * nrows + r0) * Py;
-    const int half = Py >> 1;
-    if (kx != 0) {
-        for (int idx = threadIdx.x; idx < nr * Py; idx += blockDim.x) sm[idx] = src[idx];
-    } else {
-        // U = A + i B from the separated slots
-        for (int idx = threadIdx.x; idx < nr * half; idx += blockDim.x) {
-            const int r = idx / half, q = idx - r * half;
-            const cx<T> *t = src + (size_t)r * Py;
-            const Pad<T> u = sm.at(r * Py);
-            if (q == 0) {
-                u[0] = t[0];
-                u[half] = t[half];
-            } else {
-                const cx<T> av = t[q], bv = t[Py - q];
-                u[q] = mk(av.x - bv.y, av.y + bv.x);
-                u[Py - q] = mk(av.x + bv.y, bv.x - av.y);
-            }
-        }
-    }
-    __syncthreads();
-    if constexpr (PY <= warp_max_len<T>()) {
-        for (int r = threadIdx.x >> 5; r < nr; r += blockDim.x >> 5)
-            WarpFFT<T, true, PY, 1>::run(sm.at(r * PY), 1, a.twy, false, true);
-        __syncthreads();
-    } else {
-        const FftShape f{PY, nr, 0, PY, 0, 1};
-        fft_smem<T, true, block_items(PY)>(sm, f, a.twy, false, true);
-    }
-    cx<T> *dst = a.S + (size_t)kx * a.rows + (size_t)r0 * ny;
-    for (int idx = threadIdx.x; idx < nr * ny; idx += blockDim.x) {
-        const int r = idx >> lgny, y = idx & (ny - 1);
-        dst[idx] = sm[r * Py + y];
-    }
-    (void)lgPy;
-}
-
-// ------------------------------------------------------------------ stages
-// Field and torque constants in the arithmetic type of the stage kernel,
-// converted once on the host.
-template <typename T> struct PhysT {
-    T wx, wy, wz, can, gp, alpha;
-    T ku[3], msN00[3];
-    int nx, ny, nz, lgnx, lgny;
-};
-
-template <typename T> struct StageArgs {
-    T *m0, *m1, *Y0, *Y1, *F, *G, *hist;
-    DevState *st;
-    TabArgs tab;
-    PhysArgs ph;
-    PhysT<T> pt;
-    CtlArgs ctl;
-    int k, extrap, last, use_cond;
-    cudaGraphConditionalHandle cond;
-};
-
-constexpr int ST_THREADS = 256;
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Reciprocal in FP64 from an FP32 seed and two Newton steps (relative error
-// at the FP64 rounding level for |v| in the FP32 range).
-__device__ __forceinline__ double recip64(double v)
-{
-    double r = (double)(1.0f / (float)v);
-    r = r * (2.0 - v * r);
-    r = r * (2.0 - v * r);
-    return r;
-}
-
-// x^(1/n1) for x in (cmin^n1, cmax^n1): FP32 seed, two Newton steps in FP64.
-__device__ __forceinline__ double root64(double x, int n1)
-{
-    double c = (double)exp2f(log2f((float)x) / (float)n1);
-    for (int it = 0; it < 2; ++it) {
-        double cp = 1.0;
-        for (int q = 0; q < n1 - 1; ++q) cp *= c;          // c^(n1-1)
-        const double f = cp * c - x;
-        const double d = (double)(1.0f / ((float)n1 * (float)cp));
-        c = c - f * d;
-    }
-    return c;
-}
-
-// The threads of one CTA fill the per-stage coefficients of the attempt that
-// starts at (st->t, st->h): Eq. 4 row weights times h, Eq. 3 weights times h,
-// Eq. 6 Lagrange weights (once the history is primed) and the applied field.
-// Lagrange weights: w_kj = prod_{q!=j} (a_k - s_q) / prod_{q!=j} (s_j - s_q)
-// with s_q = (t_q - t0)/h, the FP64 differences taken first.
-__device__ void prepare_coefs(DevState *st, const TabArgs &tab, const PhysArgs &ph, int p, double *sm_sig,
-                              double *sm_iden)
-{
-    const int tid = threadIdx.x;
-    const double h = st->h, t0 = st->t;
-    const int s = tab.s;
-    const int np1 = p + 1;
-    const bool primed = p >= 0 && st->hist_n >= np1;
-    if (primed && tid < np1) sm_sig[tid] = (st->hist_t[tid] - t0) * recip64(h);
-    __syncthreads();
-    if (primed && tid < np1) {
-        double den = 1.0;
-        for (int q = 0; q < np1; ++q)
-            if (q != tid) den *= sm_sig[tid] - sm_sig[q];
-        sm_iden[tid] = recip64(den);
-    }
-    __syncthreads();
-    for (int it = tid; it < MMX_MAXS * MMX_MAXS; it += blockDim.x) {
-        const int k = it / MMX_MAXS, l = it % MMX_MAXS;
-        StageCoef &C = st->coef[k];
-        double cb = 0.0, ce = 0.0;
-        if (k < s) {
-            if (k == s - 1) {
-                cb = h * tab.c[l];
-                ce = h * tab.e[l];
-            } else {
-                cb = h * tab.b[k + 1][l];
-            }
-        }
-        C.cb[l] = cb;
-        C.ce[l] = ce;
-        C.cbf[l] = (float)cb;
-        C.cef[l] = (float)ce;
-    }
-    for (int it = tid; it < MMX_MAXS * MMX_NHIST; it += blockDim.x) {
-        const int k = it / MMX_NHIST, j = it % MMX_NHIST;
-        double w = 0.0;
-        if (primed && k < s && j < np1) {
-            w = sm_iden[j];
-            for (int q = 0; q < np1; ++q)
-                if (q != j) w *= tab.a[k] - sm_sig[q];
-        }
-        st->coef[k].w[j] = w;
-        st->coef[k].wf[j] = (float)w;
-    }
-    for (int k = tid; k < MMX_MAXS; k += blockDim.x) {
-        const double tk = t0 + tab.a[k] * h;
-        const bool on = (tk >= ph.t_on) && (tk < ph.t_off);
-        for (int c = 0; c < 3; ++c) {
-            const double v = ph.H0[c] + (on ? ph.pulse[c] : 0.0);
-            st->coef[k].H[c] = v;
-            st->coef[k].Hf[c] = (float)v;
-        }
-    }
-}
-
-__global__ void k_prepare(DevState *st, const TabArgs tab, const PhysArgs ph, int p)
-{
-    __shared__ double sm_sig[MMX_NHIST], sm_iden[MMX_NHIST];
-    if (st->done) return;
-    prepare_coefs(st, tab, ph, p, sm_sig, sm_iden);
-}
-
-template <typename T> __device__ void controller(const StageArgs<T> &a)
-{
-    DevState *st = a.st;
-    const double e = __longlong_as_double((long long)atomicExch(&st->err_bits, 0ULL));
-    st->blocks_done = 0;
-    st->last_err = e;
-    st->attempts++;
-    st->run_attempts++;
-    const double h = st->h;
-    int more = 0;
-    if (!(e <= 1.7976931348623157e308)) {  // NaN or Inf
-        st->status = MMX_ERR_NONFINITE;
-        st->done = 1;
-    } else {
-        const bool adaptive = a.ctl.adaptive != 0;
-        bool accept = true, forced = false;
-        if (adaptive && e > a.ctl.tol) {
-            if (h <= a.ctl.hmin || st->h_ctrl <= a.ctl.hmin)
-                forced = true;
-            else
-                accept = false;
-        }
-        double hnew = st->h_ctrl;
-        if (adaptive) {
-            // Eq. 5: c = clamp((safety e_max / e)^(1/(n+1)), cmin, cmax)
-            double cf = a.ctl.cmax;
-            if (e > 0) {
-                const double x = a.ctl.safety * a.ctl.tol * recip64(e);
-                if (x <= a.ctl.cmin_pow)
-                    cf = a.ctl.cmin;
-                else if (x >= a.ctl.cmax_pow)
-                    cf = a.ctl.cmax;
-                else
-                    cf = fmin(fmax(root64(x, a.tab.order + 1), a.ctl.cmin), a.ctl.cmax);
-            }
-            hnew = fmin(fmax(h * cf, a.ctl.hmin), a.ctl.hmax);
-        }
-        if (accept) {
-            st->t = st->clipped ? st->t_end : st->t + h;
-            if (!st->clipped) st->h_ctrl = hnew;
-            st->cur ^= 1;
-            st->accepted++;
-            if (forced) st->forced++;
-            if (a.tab.fsal && a.ctl.p < 0) {
-                st->fbase = (st->fbase + a.tab.s - 1) % a.ctl.nslots;
-                st->f1_valid = 1;
-            } else {
-                st->f1_valid = 0;
-            }
-            if (a.ctl.p >= 0) {
-                const int np1 = a.ctl.p + 1;
-                st->head = (st->head + 1) % np1;
-                st->hist_t[st->head] = st->t;
-                if (st->hist_n < np1) st->hist_n++;
-            }
-        } else {
-            // retry from the same t0: F_1 (and its exact field) stay valid
-            st->h_ctrl = hnew;
-            st->rejected++;
-            st->f1_valid = 1;
-        }
-        bool done = (st->t >= st->t_end) || (st->accepted >= st->acc_target);
-        if (!done && st->run_attempts >= st->attempt_limit) {
-            st->status = MMX_ERR_TIMEOUT;
-            done = true;
-        }
-        const unsigned long long now = global_ns();
-        if (st->t_start_ns == 0ULL) st->t_start_ns = now;
-        if (!done && st->time_limit_ns && now - st->t_start_ns > st->time_limit_ns) {
-            st->status = MMX_ERR_TIMEOUT;
-            done = true;
-        }
-        st->done = done ? 1 : 0;
-        if (!done) {
-            const double rem = st->t_end - st->t;
-            const double hh = st->h_ctrl;
-            const int cl = (hh * (1.0 + 1e-9) >= rem) ? 1 : 0;
-            st->h = cl ? rem : hh;
-            st->clipped = cl;
-        }
-        more = (!done && !(a.ctl.prime && st->hist_n >= a.ctl.p + 1)) ? 1 : 0;
-    }
-    st->loop_more = more;
-    if (a.use_cond) cudaGraphSetConditional(a.cond, (unsigned)more);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(ST_THREADS, 2) k_stage(const StageArgs<T> a)
-{
-    __shared__ T s_w[MMX_NHIST];       // Eq. 6 weights
-    __shared__ T s_H[3];               // applied field at t0 + a_k h
-    __shared__ T s_cb[MMX_MAXS];       // h b_{k+1,l}  or  h c_l (last stage)
-    __shared__ T s_ce[MMX_MAXS];       // h (c_l - c_hat_l) (last stage)
-    __shared__ T s_red[ST_THREADS / 32];
-    __shared__ int s_last;
-    __shared__ double s_sig[MMX_NHIST], s_iden[MMX_NHIST];
-    DevState *st = a.st;
-    if (st->done) {
-        if (a.last && a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
-        return;
-    }
-    const int k = a.k;
-    const int n = (int)a.ph.n;
-    const int cur = st->cur, fbase = st->fbase, head = st->head;
-    const bool f1v = (k == 0) && st->f1_valid;
-    const bool ext = a.extrap && k > 0;
-    const int np1 = a.ctl.p + 1;
-    const int s = a.tab.s;
-    if (threadIdx.x < 32) {
-        const StageCoef &C = st->coef[k];
-        const int l = threadIdx.x;
-        if (l < MMX_MAXS) {
-            s_cb[l] = (sizeof(T) == 4) ? (T)C.cbf[l] : (T)C.cb[l];
-            s_ce[l] = (sizeof(T) == 4) ? (T)C.cef[l] : (T)C.ce[l];
-        }
-        if (l < MMX_NHIST) s_w[l] = (sizeof(T) == 4) ? (T)C.wf[l] : (T)C.w[l];
-        if (l < 3) s_H[l] = (sizeof(T) == 4) ? (T)C.Hf[l] : (T)C.H[l];
-    }
-    __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = i < n;
-    const int ns = a.ctl.nslots;
-    const size_t fstride = (size_t)3 * n;
-    T *Fk = a.F + (size_t)((fbase + k) % ns) * fstride;
-    const T *m0 = cur ? a.m1 : a.m0;
-    const PhysT<T> &P = a.pt;
-    const bool last = a.last != 0;
-    // Part of Eq. 4 (next stage input) or Eq. 3 (solution, embedded
-    // difference) that does not involve F_k: issued first so that these
-    // loads overlap the field evaluation.
-    T acc[3] = {0, 0, 0}, E[3] = {0, 0, 0};
-    if (valid) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) acc[c] = m0[c * n + i];
-        const int lmax = last ? s - 1 : k;
-#pragma unroll
-        for (int l = 0; l < MMX_MAXS - 1; ++l) {
-            if (l >= lmax) break;
-            const bool use = last ? (a.tab.c[l] != 0.0 || a.tab.e[l] != 0.0) : (a.tab.b[k + 1][l] != 0.0);
-            if (!use) continue;
-            const T *Fl = a.F + (size_t)((fbase + l) % ns) * fstride;
-            const T cb = s_cb[l], ce = s_ce[l];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const T v = Fl[c * n + i];
-                acc[c] += cb * v;
-                if (last) E[c] += ce * v;
-            }
-        }
-    }
-    T f[3] = {0, 0, 0};
-    if (valid) {
-        if (f1v) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) f[c] = Fk[c * n + i];
-        } else {
-            const T *Y = (k == 0) ? m0 : ((k & 1) ? a.Y1 : a.Y0);
-            const int x = i & (P.nx - 1);
-            const int y = (i >> P.lgnx) & (P.ny - 1);
-            const int z = i >> (P.lgnx + P.lgny);
-            const int sy = P.nx, sz = P.nx * P.ny;
-            const int xm = x > 0 ? i - 1 : i, xp = x < P.nx - 1 ? i + 1 : i;
-            const int ym = y > 0 ? i - sy : i, yp = y < P.ny - 1 ? i + sy : i;
-            const int zm = z > 0 ? i - sz : i, zp = z < P.nz - 1 ? i + sz : i;
-            T m[3], H[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const T *Yc = Y + c * n;
-                const T cen = Yc[i];
-                m[c] = cen;
-                H[c] = P.wx * (Yc[xp] - 2 * cen + Yc[xm]) + P.wy * (Yc[yp] - 2 * cen + Yc[ym]) +
-                       P.wz * (Yc[zp] - 2 * cen + Yc[zm]);
-            }
-            T g[3] = {0, 0, 0};
-            if (ext) {
-#pragma unroll
-                for (int j = 0; j < MMX_NHIST; ++j) {
-                    if (j >= np1) break;
-                    const T *Gj = a.hist + (size_t)j * fstride;
-                    const T w = s_w[j];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) g[c] += w * Gj[c * n + i];
-                }
-            } else {
-                const T *Gk = (k == 0 && a.ctl.p >= 0) ? a.hist + (size_t)head * fstride : a.G;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) g[c] = Gk[c * n + i];
-            }
-            const T mu = m[0] * P.ku[0] + m[1] * P.ku[1] + m[2] * P.ku[2];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) H[c] += P.can * mu * P.ku[c] + g[c] - P.msN00[c] * m[c] + s_H[c];
-            // Eq. 1 in Landau-Lifshitz form: F = -gp (m x H + alpha m x (m x H))
-            const T cxh0 = m[1] * H[2] - m[2] * H[1];
-            const T cxh1 = m[2] * H[0] - m[0] * H[2];
-            const T cxh2 = m[0] * H[1] - m[1] * H[0];
-            const T dd0 = m[1] * cxh2 - m[2] * cxh1;
-            const T dd1 = m[2] * cxh0 - m[0] * cxh2;
-            const T dd2 = m[0] * cxh1 - m[1] * cxh0;
-            f[0] = -P.gp * (cxh0 + P.alpha * dd0);
-            f[1] = -P.gp * (cxh1 + P.alpha * dd1);
-            f[2] = -P.gp * (cxh2 + P.alpha * dd2);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) Fk[c * n + i] = f[c];
-        }
-    }
-    if (!last) {
-        // Eq. 4: Y_{k+1} = m0 + h sum_{l<=k} b_{k+1,l} F_l
-        if (valid) {
-            T *Yn = ((k + 1) & 1) ? a.Y1 : a.Y0;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) Yn[c * n + i] = acc[c] + s_cb[k] * f[c];
-        }
-        if (ext && blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
-        return;
-    }
-    // Eq. 3: propagated solution, embedded difference, renormalisation
-    T err = 0;
-    if (valid) {
-        T M[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            M[c] = acc[c] + s_cb[s - 1] * f[c];
-            E[c] += s_ce[s - 1] * f[c];
-        }
-        const T r = sqrt(M[0] * M[0] + M[1] * M[1] + M[2] * M[2]);
-        const T inv = (T)1 / r;
-        T *mo = cur ? a.m0 : a.m1;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) mo[c * n + i] = M[c] * inv;
-        err = sqrt(E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
-        if (!(err <= (T)3.0e38) || !(r == r) || r == (T)0) err = (T)INFINITY;
-    }
-    if (ext && blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
-    for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = err;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        T mx = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, s_red[w]);
-        atomicMax(&st->err_bits, (unsigned long long)__double_as_longlong((double)mx));
-        __threadfence();
-        const unsigned prev = atomicAdd(&st->blocks_done, 1u);
-        s_last = (prev == gridDim.x - 1) ? 1 : 0;
-    }
-    __syncthreads();
-    if (s_last) {
-        if (threadIdx.x == 0) {
-            __threadfence();
-            controller(a);
-            __threadfence();
-        }
-        __syncthreads();
-        if (!st->done) prepare_coefs(st, a.tab, a.ph, a.ctl.p, s_sig, s_iden);
-    }
-}
-
-// ----------------------------------------------------------- host helpers
-template <typename T> size_t x_smem(const mmx_ctx *c, int trows)
-{
-    return padded_words((size_t)((trows + 1) / 2) * (2 * c->nx + 8)) * sizeof(cx<T>);
-}
-template <typename T> size_t yz_smem(const mmx_ctx *c) { return padded_words((size_t)3 * c->Py * c->Pz) * sizeof(cx<T>); }
-
-// split path: rows per YF/YI CTA (about 32 KB of shared memory), ky tile of ZM
-template <typename T> int split_rows(const mmx_ctx *c)
-{
-    int r = (int)(32768 / ((size_t)c->Py * sizeof(cx<T>)));
-    if (r < 1) r = 1;
-    return std::min(std::min(r, 8), 3 * c->nz);
-}
-int split_w(const mmx_ctx *c) { return std::min(c->Py, 64); }
-// threads of the x passes and of YF / YI: one warp per transform (at least
-// two warps); 256 when the transforms are too long for one warp and the
-// whole CTA runs each stage
-template <typename T> int x_threads(const mmx_ctx *c, int trows)
-{
-    return c->Px > warp_max_len<T>() ? 256 : 32 * std::max(2, (trows + 1) / 2);
-}
-template <typename T> int y_threads(const mmx_ctx *c)
-{
-    return c->Py > warp_max_len<T>() ? 256 : 32 * std::max(2, split_rows<T>(c));
-}
-template <typename T> size_t zm_smem(const mmx_ctx *c)
-{
-    return padded_words((size_t)3 * c->Pz * split_w(c)) * sizeof(cx<T>);
-}
-template <typename T> size_t yf_smem(const mmx_ctx *c, int ry) { return padded_words((size_t)ry * c->Py) * sizeof(cx<T>); }
-
-int pick_trows(const mmx_ctx *c)
-{
-    // rows per CTA for the x passes: wide enough for 128-byte transposed
-    // stores, enough CTAs to cover the SMs twice, at most ~96 KB of smem
-    const long long rows = c->rows;
-    int tr = 16;
-    while (tr > 2 && ((rows + tr - 1) / tr < 2 * 152 ||
-                      padded_words((size_t)(tr / 2) * (2 * c->nx + 8)) * 2 * c->esz > 96 * 1024))
-        tr >>= 1;
-    return tr;
-}
-
-// kernel instances per transform length (powers of two)
-#define MMX_LEN_CASES(K, T) \
-    case 1: return (const void *)K<T, 1>; \
-    case 2: return (const void *)K<T, 2>; \
-    case 4: return (const void *)K<T, 4>; \
-    case 8: return (const void *)K<T, 8>; \
-    case 16: return (const void *)K<T, 16>; \
-    case 32: return (const void *)K<T, 32>; \
-    case 64: return (const void *)K<T, 64>; \
-    case 128: return (const void *)K<T, 128>; \
-    case 256: return (const void *)K<T, 256>; \
-    case 512: return (const void *)K<T, 512>; \
-    case 1024: return (const void *)K<T, 1024>; \
-    case 2048: return (const void *)K<T, 2048>; \
-    case 4096: return (const void *)K<T, 4096>;
-
-template <typename T> const void *xf_fn(int L)
-{
-    switch (L) { MMX_LEN_CASES(k_xf, T) }
-    return nullptr;
-}
-template <typename T> const void *xi_fn(int L)
-{
-    switch (L) { MMX_LEN_CASES(k_xi, T) }
-    return nullptr;
-}
-template <typename T> const void *yz_fn(int L)
-{
-    switch (L) { MMX_LEN_CASES(k_yz, T) }
-    return nullptr;
-}
-template <typename T> const void *yf_fn(int L)
-{
-    switch (L) { MMX_LEN_CASES(k_yf, T) }
-    return nullptr;
-}
-template <typename T> const void *zm_fn(int L)
-{
-    switch (L) { MMX_LEN_CASES(k_zm, T) }
-    return nullptr;
-}
-template <typename T> const void *yi_fn(int L)
-{
-    switch (L) { MMX_LEN_CASES(k_yi, T) }
-    return nullptr;
-}
-
-template <typename T>
-void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src_mode, const void *src, int dst_mode,
-             void *dst, const void *self_src)
-{
-    const int trows = pick_trows(c);
-    XArgs<T> xa{};
-    xa.src = (const T *)src;
-    xa.msrc0 = (const T *)c->m[0];
-    xa.msrc1 = (const T *)c->m[1];
-    xa.dst = (T *)dst;
-    xa.hist = (T *)c->hist;
-    xa.self_src = (const T *)self_src;
-    xa.S = (cx<T> *)c->S;
-    xa.tw = (const cx<T> *)c->twx;
-    xa.st = const_cast<DevState *>(st);
-    xa.rows = c->rows;
-    xa.n = c->n;
-    xa.nx = c->nx;
-    xa.trows = trows;
-    xa.stage0 = stage0;
-    xa.src_mode = src_mode;
-    xa.dst_mode = dst_mode;
-    xa.plane = c->ny * c->nz;
-    for (int i = 0; i < 3; ++i) xa.msN00[i] = c->ph.msN00[i];
-    const int xgrid = (int)((c->rows + trows - 1) / trows);
-    const size_t xs = x_smem<T>(c, trows);
-
-    YZArgs<T> ya{};
-    ya.S = (cx<T> *)c->S;
-    ya.K = (const T *)c->K;
-    ya.twy = (const cx<T> *)c->twy;
-    ya.twz = (const cx<T> *)c->twz;
-    ya.st = const_cast<DevState *>(st);
-    ya.rows = c->rows;
-    ya.nx = c->nx;
-    ya.ny = c->ny;
-    ya.nz = c->nz;
-    ya.Py = c->Py;
-    ya.Pz = c->Pz;
-    ya.Hy = c->Hy;
-    ya.Hz = c->Hz;
-    ya.stage0 = stage0;
-    const size_t ys = yz_smem<T>(c);
-
-    const bool prof = c->profiling;
-    auto timed = [&](int cls, auto launch) {
-        if (prof) cudaEventRecord(c->ev_a, s);
-        launch();
-        c->launches++;
-        if (prof) {
-            cudaEventRecord(c->ev_b, s);
-            cudaEventSynchronize(c->ev_b);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, c->ev_a, c->ev_b);
-            c->prof_ms[cls] += ms;
-            c->prof_n[cls]++;
-        }
-    };
-    const int xt = x_threads<T>(c, trows);
-    void *xargs[] = {(void *)&xa};
-    void *yargs[] = {(void *)&ya};
-    timed(0, [&] { cudaLaunchKernel(xf_fn<T>(c->Px), dim3(xgrid), dim3(xt), xargs, xs, s); });
-    if (!c->split) {
-        timed(1, [&] { cudaLaunchKernel(yz_fn<T>(c->Py), dim3(c->nx), dim3(YZ_THREADS), yargs, ys, s); });
-    } else {
-        SplitArgs<T> sa{};
-        sa.S = (cx<T> *)c->S;
-        sa.Tb = (cx<T> *)c->Tb;
-        sa.K = (const T *)c->K;
-        sa.twy = (const cx<T> *)c->twy;
-        sa.twz = (const cx<T> *)c->twz;
-        sa.st = const_cast<DevState *>(st);
-        sa.rows = c->rows;
-        sa.nx = c->nx;
-        sa.ny = c->ny;
-        sa.nz = c->nz;
-        sa.Py = c->Py;
-        sa.Pz = c->Pz;
-        sa.Hy = c->Hy;
-        sa.Hz = c->Hz;
-        sa.stage0 = stage0;
-        sa.ry = split_rows<T>(c);
-        sa.W = split_w(c);
-        const int nrows = 3 * c->nz;
-        const dim3 gy(c->nx, (nrows + sa.ry - 1) / sa.ry), gz(c->nx, c->Py / sa.W);
-        const size_t sy = yf_smem<T>(c, sa.ry), sz = zm_smem<T>(c);
-        const int yt = y_threads<T>(c);
-        void *sargs[] = {(void *)&sa};
-        timed(1, [&] {
-            cudaLaunchKernel(yf_fn<T>(c->Py), gy, dim3(yt), sargs, sy, s);
-            cudaLaunchKernel(zm_fn<T>(c->Pz), gz, dim3(YZ_THREADS), sargs, sz, s);
-            cudaLaunchKernel(yi_fn<T>(c->Py), gy, dim3(yt), sargs, sy, s);
-            c->launches += 2;
-        });
-    }
-    timed(2, [&] { cudaLaunchKernel(xi_fn<T>(c->Px), dim3(xgrid), dim3(xt), xargs, xs, s); });
-}
-
-template <typename T>
-void stage_t(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime, cudaGraphConditionalHandle cond, int use_cond)
-{
-    StageArgs<T> a{};
-    a.m0 = (T *)c->m[0];
-    a.m1 = (T *)c->m[1];
-    a.Y0 = (T *)c->Y[0];
-    a.Y1 = (T *)c->Y[1];
-    a.F = (T *)c->F;
-    a.G = (T *)c->G;
-    a.hist = (T *)c->hist;
-    a.st = c->st;
-    a.tab = c->tab;
-    a.ph = c->ph;
-    a.pt.wx = (T)c->ph.wx;
-    a.pt.wy = (T)c->ph.wy;
-    a.pt.wz = (T)c->ph.wz;
-    a.pt.can = (T)c->ph.can;
-    a.pt.gp = (T)c->ph.gp;
-    a.pt.alpha = (T)c->ph.alpha;
-    for (int q = 0; q < 3; ++q) {
-        a.pt.ku[q] = (T)c->ph.ku[q];
-        a.pt.msN00[q] = (T)c->ph.msN00[q];
-    }
-    a.pt.nx = c->nx;
-    a.pt.ny = c->ny;
-    a.pt.nz = c->nz;
-    a.pt.lgnx = __builtin_ctz(c->nx);
-    a.pt.lgny = __builtin_ctz(c->ny);
-    a.ctl = c->ctl;
-    a.ctl.prime = prime;
-    a.k = k;
-    a.extrap = extrap;
-    a.last = (k == c->tab.s - 1);
-    a.use_cond = use_cond;
-    a.cond = cond;
-    const int grid = (int)((c->n + ST_THREADS - 1) / ST_THREADS);
-    const int cls = a.last ? 4 : 3;
-    if (c->profiling) cudaEventRecord(c->ev_a, s);
-    k_stage<T><<<grid, ST_THREADS, 0, s>>>(a);
-    c->launches++;
-    if (c->profiling) {
-        cudaEventRecord(c->ev_b, s);
-        cudaEventSynchronize(c->ev_b);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, c->ev_a, c->ev_b);
-        c->prof_ms[cls] += ms;
-        c->prof_n[cls]++;
-    }
-}
-
-template <typename T> void twiddles(int L, std::vector<cx<T>> &out)
-{
-    out.resize(L > 0 ? L : 1);
-    for (int m = 0; m < L; ++m) {
-        if ((4 * m) % L == 0) {
-            static const int cq[4] = {1, 0, -1, 0}, sq[4] = {0, 1, 0, -1};
-            const int q = ((4 * m) / L) & 3;
-            out[m].x = (T)cq[q];
-            out[m].y = (T)-sq[q];
-        } else {
-            const long double ang = 2.0L * 3.141592653589793238462643383279502884L * (long double)m / (long double)L;
-            out[m].x = (T)cosl(ang);
-            out[m].y = (T)-sinl(ang);
-        }
-    }
-}
-
-template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
-{
-    const size_t nK = (size_t)(c->nx + 1) * c->Hz * c->Hy * 6;
-    std::vector<T> Kh(nK);
-    for (size_t i = 0; i < nK; ++i) Kh[i] = (T)Kspec[i];
-    if (cudaMemcpy(c->K, Kh.data(), nK * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
-    std::vector<cx<T>> tw;
-    twiddles<T>(c->Px, tw);
-    if (cudaMemcpy(c->twx, tw.data(), c->Px * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
-    twiddles<T>(c->Py, tw);
-    if (cudaMemcpy(c->twy, tw.data(), c->Py * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
-    twiddles<T>(c->Pz, tw);
-    if (cudaMemcpy(c->twz, tw.data(), c->Pz * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
-    const int trows = pick_trows(c);
-    const size_t xs = x_smem<T>(c, trows), ys = yz_smem<T>(c);
-    const void *xk[] = {xf_fn<T>(c->Px), xi_fn<T>(c->Px)};
-    if (xs > 48 * 1024)
-        for (const void *f : xk)
-            if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs) != cudaSuccess)
-                return MMX_ERR_CUDA;
-    const void *yk[] = {yz_fn<T>(c->Py)};
-    if (!c->split && ys > 48 * 1024)
-        for (const void *f : yk)
-            if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ys) != cudaSuccess)
-                return MMX_ERR_CUDA;
-    if (c->split) {
-        const size_t sy = yf_smem<T>(c, split_rows<T>(c)), sz = zm_smem<T>(c);
-        const void *fy[] = {yf_fn<T>(c->Py), yi_fn<T>(c->Py)};
-        if (sy > 48 * 1024)
-            for (const void *f : fy)
-                if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sy) != cudaSuccess)
-                    return MMX_ERR_CUDA;
-        const void *fz[] = {zm_fn<T>(c->Pz)};
-        if (sz > 48 * 1024)
-            for (const void *f : fz)
-                if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz) != cudaSuccess)
-                    return MMX_ERR_CUDA;
-    }
-    return 0;
-}
-
-}  // namespace
 
 void mmxk_prepare(mmx_ctx *c, cudaStream_t s)
 {
