@@ -7,6 +7,7 @@ const void *mmxk_tab_split(int kind, bool f64, int L)
     case K_YF: return f64 ? yf_fn<double>(L) : yf_fn<float>(L);
     case K_YI: return f64 ? yi_fn<double>(L) : yi_fn<float>(L);
     case K_ZM: return f64 ? zm_fn<double>(L) : zm_fn<float>(L);
+    case K_ZMR: return f64 ? zmr_fn<double>(L) : zmr_fn<float>(L);
     }
     return nullptr;
 }

@@ -15,7 +15,8 @@ const void *mmxk_kernel(int kind, bool f64, int L)
     case K_YZ: return mmxk_tab_fused(kind, f64, L);
     case K_YF:
     case K_YI:
-    case K_ZM: return mmxk_tab_split(kind, f64, L);
+    case K_ZM:
+    case K_ZMR: return mmxk_tab_split(kind, f64, L);
     default: return mmxk_tab_pipe(kind, f64, L);
     }
 }

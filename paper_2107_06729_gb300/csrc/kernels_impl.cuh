@@ -39,7 +39,7 @@
 #include "internal.h"
 
 // kernel families, instantiated in separate translation units
-enum MmxKernelKind { K_XF, K_XI, K_YZ, K_YF, K_YI, K_ZM, K_XFP, K_XIP, K_YFP, K_YIP, K_ZMP };
+enum MmxKernelKind { K_XF, K_XI, K_YZ, K_YF, K_YI, K_ZM, K_XFP, K_XIP, K_YFP, K_YIP, K_ZMP, K_ZMR };
 // pointer to the instance of `kind` for precision (f64) and transform length L
 const void *mmxk_kernel(int kind, bool f64, int L);
 
@@ -1041,14 +1041,15 @@ __global__ void __launch_bounds__(256, 2) k_xi_p(const XArgs<T> a)
     const int nitems = (int)(R / T_);
     const Pad<T> work{reinterpret_cast<cx<T> *>(smraw), 0};
     cx<T> *stg0 = reinterpret_cast<cx<T> *>(smraw) + padded_words((size_t)np * PXS);
-    cx<T> *stg[2] = {stg0, stg0 + (size_t)NX * T_};
+    const int SS = T_ + 2;  // staging row stride: spreads the view's reads over the banks
+    cx<T> *stg[2] = {stg0, stg0 + (size_t)NX * SS};
     const int rowbytes = T_ * (int)sizeof(cx<T>);  // a multiple of 16
     const int cpr = rowbytes >> 4;
     auto issue = [&](int itm, cx<T> *dst) {
         const cx<T> *g = a.S + (long long)itm * T_;
         for (int ch = threadIdx.x; ch < NX * cpr; ch += blockDim.x) {
             const int k = ch / cpr, q = ch - k * cpr;
-            cp_async16((char *)(dst + (size_t)k * T_) + (q << 4), (const char *)(g + (long long)k * R) + (q << 4));
+            cp_async16((char *)(dst + (size_t)k * SS) + (q << 4), (const char *)(g + (long long)k * R) + (q << 4));
         }
     };
     T *out = a.dst_mode == 1 ? a.hist + (size_t)head * 3 * a.n : a.dst;
@@ -1063,7 +1064,7 @@ __global__ void __launch_bounds__(256, 2) k_xi_p(const XArgs<T> a)
         __syncthreads();
         const int w = threadIdx.x >> 5;
         if (w < np) {
-            const XIView<T> v{stg[it & 1], T_, 2 * w, NX};
+            const XIView<T> v{stg[it & 1], SS, 2 * w, NX};
             WarpFFT<T, true, PX, 1>::run(v, work.at(w * PXS), 1, a.tw, false, true);
         }
         __syncthreads();
@@ -1285,6 +1286,87 @@ __global__ void __launch_bounds__(YZ_THREADS, 2) k_zm_p(const SplitArgs<T> a)
         }
         __syncthreads();
     }
+}
+
+// ZM with register z columns: thread (c, w) of a tile of W ky values loads
+// its z column straight from global memory (a warp reads 32 consecutive ky:
+// coalesced), transforms it in registers, and exchanges with the other two
+// components only through a [c][kz][w] tile for the tensor multiply
+// (consecutive threads touch consecutive words: no bank conflicts).
+template <typename T, int PZ>
+__global__ void __launch_bounds__(192) k_zm_r(const SplitArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<T> *B = reinterpret_cast<cx<T> *>(smraw);
+    if (a.st) {
+        if (a.st->done) return;
+        if (a.stage0 && a.st->f1_valid) return;
+    }
+    const int W = a.W, Py = a.Py, nz = a.nz, Pz = PZ;
+    const int lgW = ilog2(W);
+    const int nrows = 3 * nz, plane = PZ * W;
+    const int kx = blockIdx.x, ky0 = blockIdx.y * W;
+    const int c = threadIdx.x >> lgW, w = threadIdx.x & (W - 1);
+    cx<T> *g = a.Tb + ((size_t)kx * nrows + (size_t)c * nz) * Py + ky0 + w;
+    cx<T> v[PZ];
+#pragma unroll
+    for (int z = 0; z < PZ; ++z) v[z] = z < nz ? g[(size_t)z * Py] : mk<T>(0, 0);
+    RegFFT<T, PZ, 1, false>::run(v, a.twz);
+#pragma unroll
+    for (int kz = 0; kz < PZ; ++kz) B[c * plane + kz * W + w] = v[kz];
+    __syncthreads();
+    const int half = Py >> 1;
+    for (int q = threadIdx.x; q < plane; q += blockDim.x) {
+        const int ww = q & (W - 1), kz = q >> lgW, slot = ky0 + ww;
+        if (kx != 0 || (slot != 0 && slot != half)) {
+            T k6[6];
+            if (kx != 0)
+                load_K(a.K, kx, a.Hy, a.Hz, Py, Pz, slot, kz, k6);
+            else if (slot < half)
+                load_K(a.K, 0, a.Hy, a.Hz, Py, Pz, slot, kz, k6);
+            else
+                load_K(a.K, a.nx, a.Hy, a.Hz, Py, Pz, Py - slot, kz, k6);
+            cx<T> hx, hy, hz;
+            apply_K(k6, B[q], B[plane + q], B[2 * plane + q], hx, hy, hz);
+            B[q] = hx;
+            B[plane + q] = hy;
+            B[2 * plane + q] = hz;
+        } else {
+            const int kzm = (Pz - kz) & (Pz - 1);
+            if (kz > kzm) continue;
+            const int qm = kzm * W + ww;
+            T k0[6], kn[6], P[6], Q[6];
+            load_K(a.K, 0, a.Hy, a.Hz, Py, Pz, slot, kz, k0);
+            load_K(a.K, a.nx, a.Hy, a.Hz, Py, Pz, slot, kz, kn);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                P[i] = (T)0.5 * (k0[i] + kn[i]);
+                Q[i] = (T)0.5 * (k0[i] - kn[i]);
+            }
+            const cx<T> ux = B[q], uy = B[plane + q], uz = B[2 * plane + q];
+            const cx<T> vx = B[qm], vy = B[plane + qm], vz = B[2 * plane + qm];
+            cx<T> a1, a2, a3, b1, b2, b3;
+            apply_K(P, ux, uy, uz, a1, a2, a3);
+            apply_K(Q, mk(vx.x, -vx.y), mk(vy.x, -vy.y), mk(vz.x, -vz.y), b1, b2, b3);
+            B[q] = cadd(a1, b1);
+            B[plane + q] = cadd(a2, b2);
+            B[2 * plane + q] = cadd(a3, b3);
+            if (qm != q) {
+                apply_K(P, vx, vy, vz, a1, a2, a3);
+                apply_K(Q, mk(ux.x, -ux.y), mk(uy.x, -uy.y), mk(uz.x, -uz.y), b1, b2, b3);
+                B[qm] = cadd(a1, b1);
+                B[plane + qm] = cadd(a2, b2);
+                B[2 * plane + qm] = cadd(a3, b3);
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kz = 0; kz < PZ; ++kz) v[kz] = B[c * plane + kz * W + w];
+    RegFFT<T, PZ, 1, true>::run(v, a.twz);
+#pragma unroll
+    for (int z = 0; z < PZ; ++z)
+        if (z < nz) g[(size_t)z * Py] = v[z];
 }
 
 // ------------------------------------------------------------------ stages
@@ -1784,6 +1866,11 @@ template <typename T> const void *zmp_fn(int L)
     return nullptr;
 }
 
+// register-column ZM: ky tile of W values (3 W threads, at most 192) and
+// the longest z transform it holds in registers
+int zmr_w(const mmx_ctx *c) { return std::min(c->Py, 64); }
+template <typename T> constexpr int zmr_max() { return sizeof(T) == 4 ? 32 : 16; }
+
 // pipelined large-mesh passes: rows per item and shared-memory sizes
 constexpr int XF_P_ROWS = 16, XI_P_ROWS = 8;
 template <typename T> int pipe_ry(const mmx_ctx *c)
@@ -1801,7 +1888,7 @@ template <typename T> size_t xfp_smem(const mmx_ctx *c)
 template <typename T> size_t xip_smem(const mmx_ctx *c)
 {
     return padded_words((size_t)(XI_P_ROWS / 2) * (c->Px + 8)) * sizeof(cx<T>) +
-           2 * (size_t)XI_P_ROWS * c->nx * sizeof(cx<T>);
+           2 * (size_t)(XI_P_ROWS + 2) * c->nx * sizeof(cx<T>);
 }
 template <typename T> size_t yfp_smem(const mmx_ctx *c)
 {
@@ -1837,6 +1924,18 @@ int persistent_grid(const void *fn, int threads, size_t smem, long long items)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
     if (per < 1) per = 1;
     return (int)std::max(1LL, std::min(items, (long long)nsm * per));
+}
+
+template <typename T> const void *zmr_fn(int L)
+{
+    switch (L) {
+    case 2: return (const void *)k_zm_r<T, 2>;
+    case 4: return (const void *)k_zm_r<T, 4>;
+    case 8: return (const void *)k_zm_r<T, 8>;
+    case 16: return (const void *)k_zm_r<T, 16>;
+    case 32: if constexpr (sizeof(T) == 4) return (const void *)k_zm_r<T, 32>; else return nullptr;
+    }
+    return nullptr;
 }
 
 template <typename T> const void *zm_fn(int L)
@@ -1950,8 +2049,17 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
         });
         timed(1, [&] {
             cudaLaunchKernel(f_yf, dim3(persistent_grid(f_yf, tyy, s_yf, n_y)), dim3(tyy), sargs, s_yf, s);
-            cudaLaunchKernel(f_zm, dim3(persistent_grid(f_zm, YZ_THREADS, s_zm, n_z)), dim3(YZ_THREADS), sargs, s_zm,
-                             s);
+            if (c->Pz <= zmr_max<T>()) {
+                SplitArgs<T> sr = sa;
+                sr.W = zmr_w(c);
+                void *rargs[] = {(void *)&sr};
+                const size_t s_r = (size_t)3 * c->Pz * sr.W * sizeof(cx<T>);
+                cudaLaunchKernel(mmxk_kernel(K_ZMR, sizeof(T) == 8, c->Pz), dim3(c->nx, c->Py / sr.W),
+                                 dim3(3 * sr.W), rargs, s_r, s);
+            } else {
+                cudaLaunchKernel(f_zm, dim3(persistent_grid(f_zm, YZ_THREADS, s_zm, n_z)), dim3(YZ_THREADS), sargs,
+                                 s_zm, s);
+            }
             cudaLaunchKernel(f_yi, dim3(persistent_grid(f_yi, tyy, s_yi, n_y)), dim3(tyy), sargs, s_yi, s);
             c->launches += 2;
         });
