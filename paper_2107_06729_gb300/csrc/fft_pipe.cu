@@ -5,7 +5,6 @@ const void *mmxk_tab_pipe(int kind, bool f64, int L)
 {
     switch (kind) {
     case K_XFP: return f64 ? xfp_fn<double>(L) : xfp_fn<float>(L);
-    case K_XIP: return f64 ? xip_fn<double>(L) : xip_fn<float>(L);
     case K_YFP: return f64 ? yfp_fn<double>(L) : yfp_fn<float>(L);
     case K_YIP: return f64 ? yip_fn<double>(L) : yip_fn<float>(L);
     case K_ZMP: return f64 ? zmp_fn<double>(L) : zmp_fn<float>(L);

@@ -39,7 +39,7 @@
 #include "internal.h"
 
 // kernel families, instantiated in separate translation units
-enum MmxKernelKind { K_XF, K_XI, K_YZ, K_YF, K_YI, K_ZM, K_XFP, K_XIP, K_YFP, K_YIP, K_ZMP, K_ZMR };
+enum MmxKernelKind { K_XF, K_XI, K_YZ, K_YF, K_YI, K_ZM, K_XFP, K_YFP, K_YIP, K_ZMP, K_ZMR };
 // pointer to the instance of `kind` for precision (f64) and transform length L
 const void *mmxk_kernel(int kind, bool f64, int L);
 
@@ -317,6 +317,23 @@ template <typename T, bool INV, int L, int NS> struct WarpFFT {
     static __device__ __forceinline__ void run(const Pad<T> buf, int es, const cx<T> *tw, bool prune, bool trunc)
     {
         run(buf, buf, es, tw, prune, trunc);
+    }
+    // first stage only (src -> buf), and the stages after it (in place)
+    template <class SRC>
+    static __device__ __forceinline__ void first(const SRC src, const Pad<T> buf, int es, const cx<T> *tw, bool prune,
+                                                 bool trunc)
+    {
+        constexpr int REM = L / NS;
+        constexpr int R = (REM % 8 == 0 && REM != 16) ? 8 : ((REM % 4 == 0) ? 4 : 2);
+        constexpr int PER = L / R;
+        constexpr int IT = PER <= 32 ? 1 : PER / 32;
+        warp_stage<T, R, INV, IT>(src, buf, L, es, NS, tw, NS == 1 && prune, REM == R && trunc);
+    }
+    static __device__ __forceinline__ void rest(const Pad<T> buf, int es, const cx<T> *tw, bool prune, bool trunc)
+    {
+        constexpr int REM = L / NS;
+        constexpr int R = (REM % 8 == 0 && REM != 16) ? 8 : ((REM % 4 == 0) ? 4 : 2);
+        WarpFFT<T, INV, L, NS * R>::run(buf, buf, es, tw, prune, trunc);
     }
 };
 template <typename T, bool INV, int L> struct WarpFFT<T, INV, L, L> {
@@ -915,6 +932,7 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // copies n bytes (a multiple of 16, both addresses 16-byte aligned)
 __device__ __forceinline__ void stage_copy(void *dst, const void *src, size_t n)
@@ -928,31 +946,6 @@ __device__ __forceinline__ void stage_copy(void *dst, const void *src, size_t n)
 template <typename T> struct XPairView {
     const T *ra, *rb;  // rb == nullptr: missing second row (zero)
     __device__ __forceinline__ cx<T> operator[](int n) const { return mk(ra[n], rb ? rb[n] : (T)0); }
-};
-
-// XI: Z[k] = A[k] + i B[k] over k in [0, Px) from the staged packed spectra
-// A, B (tile [k][trows], pair columns 2p and 2p + 1)
-template <typename T> struct XIView {
-    const cx<T> *st;
-    int stride, col, nx;  // stride = trows
-    __device__ __forceinline__ cx<T> operator[](int k) const
-    {
-        if (k == 0) {
-            const cx<T> a = st[col], b = st[col + 1];
-            return mk(a.x, b.x);
-        }
-        if (k == nx) {
-            const cx<T> a = st[col], b = st[col + 1];
-            return mk(a.y, b.y);
-        }
-        if (k < nx) {
-            const cx<T> a = st[k * stride + col], b = st[k * stride + col + 1];
-            return mk(a.x - b.y, a.y + b.x);
-        }
-        const int q = 2 * nx - k;
-        const cx<T> a = st[q * stride + col], b = st[q * stride + col + 1];
-        return mk(a.x + b.y, b.x - a.y);
-    }
 };
 
 // YI, packed kx = 0 column: U(q) = A(q) + i B(q) from the separated slots
@@ -987,24 +980,24 @@ __global__ void __launch_bounds__(256, 2) k_xf_p(const XArgs<T> a)
     const long long R = a.rows;
     const int nitems = (int)(R / T_);
     const Pad<T> work{reinterpret_cast<cx<T> *>(smraw), 0};
-    T *stg0 = reinterpret_cast<T *>(reinterpret_cast<cx<T> *>(smraw) + padded_words((size_t)np * PXS));
-    T *stg[2] = {stg0, stg0 + (size_t)T_ * NX};
+    T *stg = reinterpret_cast<T *>(reinterpret_cast<cx<T> *>(smraw) + padded_words((size_t)np * PXS));
     const size_t bytes = (size_t)T_ * NX * sizeof(T);
+    const int w = threadIdx.x >> 5;
     int item = blockIdx.x;
-    if (item < nitems) stage_copy(stg[0], src + (size_t)item * T_ * NX, bytes);
+    if (item < nitems) stage_copy(stg, src + (size_t)item * T_ * NX, bytes);
     cp_async_commit();
-    for (int it = 0; item < nitems; item += gridDim.x, ++it) {
-        const int next = item + gridDim.x;
-        if (next < nitems) stage_copy(stg[(it + 1) & 1], src + (size_t)next * T_ * NX, bytes);
-        cp_async_commit();
-        cp_async_wait1();
+    for (; item < nitems; item += gridDim.x) {
+        cp_async_wait0();
         __syncthreads();
-        const T *sb = stg[it & 1];
-        const int w = threadIdx.x >> 5;
         if (w < np) {
-            const XPairView<T> v{sb + (size_t)(2 * w) * NX, sb + (size_t)(2 * w + 1) * NX};
-            WarpFFT<T, false, PX, 1>::run(v, work.at(w * PXS), 1, a.tw, true, false);
+            const XPairView<T> v{stg + (size_t)(2 * w) * NX, stg + (size_t)(2 * w + 1) * NX};
+            WarpFFT<T, false, PX, 1>::first(v, work.at(w * PXS), 1, a.tw, true, false);
         }
+        __syncthreads();  // staging consumed: prefetch the next item behind the remaining stages
+        const int next = item + gridDim.x;
+        if (next < nitems) stage_copy(stg, src + (size_t)next * T_ * NX, bytes);
+        cp_async_commit();
+        if (w < np) WarpFFT<T, false, PX, 1>::rest(work.at(w * PXS), 1, a.tw, true, false);
         __syncthreads();
         const long long r0 = (long long)item * T_;
         for (int idx = threadIdx.x; idx < NX * T_; idx += blockDim.x) {
@@ -1021,70 +1014,9 @@ __global__ void __launch_bounds__(256, 2) k_xf_p(const XArgs<T> a)
             }
             a.S[(long long)k * R + r0 + t] = v;
         }
-        __syncthreads();
     }
 }
 
-template <typename T, int PX>
-__global__ void __launch_bounds__(256, 2) k_xi_p(const XArgs<T> a)
-{
-    extern __shared__ __align__(16) unsigned char smraw[];
-    int head = 0;
-    if (a.st) {
-        if (a.st->done) return;
-        if (a.stage0 && a.st->f1_valid) return;
-        head = a.st->head;
-    }
-    constexpr int NX = PX / 2, PXS = PX + 8;
-    const int T_ = a.trows, np = T_ >> 1;
-    const long long R = a.rows;
-    const int nitems = (int)(R / T_);
-    const Pad<T> work{reinterpret_cast<cx<T> *>(smraw), 0};
-    cx<T> *stg0 = reinterpret_cast<cx<T> *>(smraw) + padded_words((size_t)np * PXS);
-    const int SS = T_ + 2;  // staging row stride: spreads the view's reads over the banks
-    cx<T> *stg[2] = {stg0, stg0 + (size_t)NX * SS};
-    const int rowbytes = T_ * (int)sizeof(cx<T>);  // a multiple of 16
-    const int cpr = rowbytes >> 4;
-    auto issue = [&](int itm, cx<T> *dst) {
-        const cx<T> *g = a.S + (long long)itm * T_;
-        for (int ch = threadIdx.x; ch < NX * cpr; ch += blockDim.x) {
-            const int k = ch / cpr, q = ch - k * cpr;
-            cp_async16((char *)(dst + (size_t)k * SS) + (q << 4), (const char *)(g + (long long)k * R) + (q << 4));
-        }
-    };
-    T *out = a.dst_mode == 1 ? a.hist + (size_t)head * 3 * a.n : a.dst;
-    int item = blockIdx.x;
-    if (item < nitems) issue(item, stg[0]);
-    cp_async_commit();
-    for (int it = 0; item < nitems; item += gridDim.x, ++it) {
-        const int next = item + gridDim.x;
-        if (next < nitems) issue(next, stg[(it + 1) & 1]);
-        cp_async_commit();
-        cp_async_wait1();
-        __syncthreads();
-        const int w = threadIdx.x >> 5;
-        if (w < np) {
-            const XIView<T> v{stg[it & 1], SS, 2 * w, NX};
-            WarpFFT<T, true, PX, 1>::run(v, work.at(w * PXS), 1, a.tw, false, true);
-        }
-        __syncthreads();
-        const long long r0 = (long long)item * T_;
-        constexpr int LG = __builtin_ctz(NX);
-        for (int idx = threadIdx.x; idx < T_ * NX; idx += blockDim.x) {
-            const int t = idx >> LG, x = idx & (NX - 1);
-            const long long r = r0 + t;
-            const cx<T> z = work[(t >> 1) * PXS + x];
-            T v = (t & 1) ? z.y : z.x;
-            if (a.self_src) {
-                const int c = (int)(r / a.plane);
-                v -= (T)a.msN00[c] * a.self_src[r * NX + x];
-            }
-            out[r * NX + x] = v;
-        }
-        __syncthreads();
-    }
-    if (a.st && blockIdx.x == 0 && threadIdx.x == 0) a.st->exact_evals++;
-}
 
 template <typename T, int PY>
 __global__ void __launch_bounds__(256, 2) k_yf_p(const SplitArgs<T> a)
@@ -1098,25 +1030,26 @@ __global__ void __launch_bounds__(256, 2) k_yf_p(const SplitArgs<T> a)
     const int nrows = 3 * a.nz, ry = a.ry, nby = nrows / ry;  // ry divides 3 nz
     const int nitems = a.nx * nby;
     const Pad<T> work{reinterpret_cast<cx<T> *>(smraw), 0};
-    cx<T> *stg0 = reinterpret_cast<cx<T> *>(smraw) + padded_words((size_t)ry * PY);
-    cx<T> *stg[2] = {stg0, stg0 + (size_t)ry * NY};
+    cx<T> *stg = reinterpret_cast<cx<T> *>(smraw) + padded_words((size_t)ry * PY);
     const size_t bytes = (size_t)ry * NY * sizeof(cx<T>);
     auto srcp = [&](int itm) {
         const int kx = itm / nby, rb = itm - kx * nby;
         return a.S + (size_t)kx * a.rows + (size_t)rb * ry * NY;
     };
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int item = blockIdx.x;
-    if (item < nitems) stage_copy(stg[0], srcp(item), bytes);
+    if (item < nitems) stage_copy(stg, srcp(item), bytes);
     cp_async_commit();
-    for (int it = 0; item < nitems; item += gridDim.x, ++it) {
-        const int next = item + gridDim.x;
-        if (next < nitems) stage_copy(stg[(it + 1) & 1], srcp(next), bytes);
-        cp_async_commit();
-        cp_async_wait1();
+    for (; item < nitems; item += gridDim.x) {
+        cp_async_wait0();
         __syncthreads();
-        const Lin<T> sb{stg[it & 1], 0};
-        for (int r = threadIdx.x >> 5; r < ry; r += blockDim.x >> 5)
-            WarpFFT<T, false, PY, 1>::run(sb.at(r * NY), work.at(r * PY), 1, a.twy, true, false);
+        const Lin<T> sb{stg, 0};
+        for (int r = w; r < ry; r += nw) WarpFFT<T, false, PY, 1>::first(sb.at(r * NY), work.at(r * PY), 1, a.twy, true, false);
+        __syncthreads();
+        const int next = item + gridDim.x;
+        if (next < nitems) stage_copy(stg, srcp(next), bytes);
+        cp_async_commit();
+        for (int r = w; r < ry; r += nw) WarpFFT<T, false, PY, 1>::rest(work.at(r * PY), 1, a.twy, true, false);
         __syncthreads();
         const int kx = item / nby, rb = item - kx * nby;
         cx<T> *dst = a.Tb + ((size_t)kx * nrows + (size_t)rb * ry) * PY;
@@ -1139,7 +1072,6 @@ __global__ void __launch_bounds__(256, 2) k_yf_p(const SplitArgs<T> a)
             }
             dst[idx] = v;
         }
-        __syncthreads();
     }
 }
 
@@ -1155,32 +1087,32 @@ __global__ void __launch_bounds__(256, 2) k_yi_p(const SplitArgs<T> a)
     const int nrows = 3 * a.nz, ry = a.ry, nby = nrows / ry;
     const int nitems = a.nx * nby;
     const Pad<T> work{reinterpret_cast<cx<T> *>(smraw), 0};
-    cx<T> *stg0 = reinterpret_cast<cx<T> *>(smraw) + padded_words((size_t)ry * PY);
-    cx<T> *stg[2] = {stg0, stg0 + (size_t)ry * PY};
+    cx<T> *stg = reinterpret_cast<cx<T> *>(smraw) + padded_words((size_t)ry * PY);
     const size_t bytes = (size_t)ry * PY * sizeof(cx<T>);
     auto srcp = [&](int itm) {
         const int kx = itm / nby, rb = itm - kx * nby;
         return a.Tb + ((size_t)kx * nrows + (size_t)rb * ry) * PY;
     };
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int item = blockIdx.x;
-    if (item < nitems) stage_copy(stg[0], srcp(item), bytes);
+    if (item < nitems) stage_copy(stg, srcp(item), bytes);
     cp_async_commit();
-    for (int it = 0; item < nitems; item += gridDim.x, ++it) {
-        const int next = item + gridDim.x;
-        if (next < nitems) stage_copy(stg[(it + 1) & 1], srcp(next), bytes);
-        cp_async_commit();
-        cp_async_wait1();
+    for (; item < nitems; item += gridDim.x) {
+        cp_async_wait0();
         __syncthreads();
         const int kx = item / nby, rb = item - kx * nby;
-        const cx<T> *sb = stg[it & 1];
-        for (int r = threadIdx.x >> 5; r < ry; r += blockDim.x >> 5) {
+        for (int r = w; r < ry; r += nw) {
             if (kx != 0)
-                WarpFFT<T, true, PY, 1>::run(Lin<T>{const_cast<cx<T> *>(sb), r * PY}, work.at(r * PY), 1, a.twy,
-                                             false, true);
+                WarpFFT<T, true, PY, 1>::first(Lin<T>{stg, r * PY}, work.at(r * PY), 1, a.twy, false, true);
             else
-                WarpFFT<T, true, PY, 1>::run(YIView<T>{sb + (size_t)r * PY, PY}, work.at(r * PY), 1, a.twy, false,
-                                             true);
+                WarpFFT<T, true, PY, 1>::first(YIView<T>{stg + (size_t)r * PY, PY}, work.at(r * PY), 1, a.twy, false,
+                                               true);
         }
+        __syncthreads();
+        const int next = item + gridDim.x;
+        if (next < nitems) stage_copy(stg, srcp(next), bytes);
+        cp_async_commit();
+        for (int r = w; r < ry; r += nw) WarpFFT<T, true, PY, 1>::rest(work.at(r * PY), 1, a.twy, false, true);
         __syncthreads();
         cx<T> *dst = a.S + (size_t)kx * a.rows + (size_t)rb * ry * NY;
         constexpr int LG = __builtin_ctz(NY);
@@ -1188,7 +1120,6 @@ __global__ void __launch_bounds__(256, 2) k_yi_p(const SplitArgs<T> a)
             const int r = idx >> LG, y = idx & (NY - 1);
             dst[idx] = work[r * PY + y];
         }
-        __syncthreads();
     }
 }
 
@@ -1840,11 +1771,6 @@ template <typename T> const void *xfp_fn(int L)
     switch (L) { MMX_PIPE_CASES(k_xf_p, T) }
     return nullptr;
 }
-template <typename T> const void *xip_fn(int L)
-{
-    switch (L) { MMX_PIPE_CASES(k_xi_p, T) }
-    return nullptr;
-}
 template <typename T> const void *yfp_fn(int L)
 {
     switch (L) { MMX_PIPE_CASES(k_yf_p, T) }
@@ -1872,7 +1798,7 @@ int zmr_w(const mmx_ctx *c) { return std::min(c->Py, 64); }
 template <typename T> constexpr int zmr_max() { return sizeof(T) == 4 ? 32 : 16; }
 
 // pipelined large-mesh passes: rows per item and shared-memory sizes
-constexpr int XF_P_ROWS = 16, XI_P_ROWS = 8;
+constexpr int XF_P_ROWS = 16;
 template <typename T> int pipe_ry(const mmx_ctx *c)
 {
     int r = std::max(1, std::min((int)(32768 / ((size_t)c->Py * sizeof(cx<T>))), 8));
@@ -1882,23 +1808,17 @@ template <typename T> int pipe_ry(const mmx_ctx *c)
 }
 template <typename T> size_t xfp_smem(const mmx_ctx *c)
 {
-    return padded_words((size_t)(XF_P_ROWS / 2) * (c->Px + 8)) * sizeof(cx<T>) +
-           2 * (size_t)XF_P_ROWS * c->nx * sizeof(T);
-}
-template <typename T> size_t xip_smem(const mmx_ctx *c)
-{
-    return padded_words((size_t)(XI_P_ROWS / 2) * (c->Px + 8)) * sizeof(cx<T>) +
-           2 * (size_t)(XI_P_ROWS + 2) * c->nx * sizeof(cx<T>);
+    return padded_words((size_t)(XF_P_ROWS / 2) * (c->Px + 8)) * sizeof(cx<T>) + (size_t)XF_P_ROWS * c->nx * sizeof(T);
 }
 template <typename T> size_t yfp_smem(const mmx_ctx *c)
 {
     const int ry = pipe_ry<T>(c);
-    return padded_words((size_t)ry * c->Py) * sizeof(cx<T>) + 2 * (size_t)ry * (c->Py / 2) * sizeof(cx<T>);
+    return padded_words((size_t)ry * c->Py) * sizeof(cx<T>) + (size_t)ry * (c->Py / 2) * sizeof(cx<T>);
 }
 template <typename T> size_t yip_smem(const mmx_ctx *c)
 {
     const int ry = pipe_ry<T>(c);
-    return padded_words((size_t)ry * c->Py) * sizeof(cx<T>) + 2 * (size_t)ry * c->Py * sizeof(cx<T>);
+    return padded_words((size_t)ry * c->Py) * sizeof(cx<T>) + (size_t)ry * c->Py * sizeof(cx<T>);
 }
 template <typename T> size_t zmp_smem(const mmx_ctx *c)
 {
@@ -1912,7 +1832,7 @@ template <typename T> bool pipe_ok(const mmx_ctx *c)
     return c->split && c->Px >= 32 && c->Py >= 32 && c->Pz >= 4 && c->Px <= warp_max_len<T>() &&
            c->Py <= warp_max_len<T>() && c->Pz <= 1024 && c->rows % XF_P_ROWS == 0 &&
            (c->nx * sizeof(T)) % 16 == 0 && (c->ny * sizeof(cx<T>)) % 16 == 0 &&
-           (split_w(c) * sizeof(cx<T>)) % 16 == 0 && xfp_smem<T>(c) <= 200 * 1024 && xip_smem<T>(c) <= 200 * 1024 &&
+           (split_w(c) * sizeof(cx<T>)) % 16 == 0 && xfp_smem<T>(c) <= 200 * 1024 &&
            yfp_smem<T>(c) <= 200 * 1024 && yip_smem<T>(c) <= 200 * 1024 && zmp_smem<T>(c) <= 200 * 1024;
 }
 // resident CTAs per SM times SMs, capped by the number of items
@@ -2012,11 +1932,9 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
     void *yargs[] = {(void *)&ya};
     const void *xsrc = src_mode == 1 ? c->m[0] : src;
     if (pipe_ok<T>(c) && ((uintptr_t)xsrc & 15) == 0 && ((uintptr_t)c->m[1] & 15) == 0) {
-        XArgs<T> xf = xa, xi = xa;
+        XArgs<T> xf = xa;
         xf.trows = XF_P_ROWS;
-        xi.trows = XI_P_ROWS;
         void *xfa[] = {(void *)&xf};
-        void *xia[] = {(void *)&xi};
         SplitArgs<T> sa{};
         sa.S = (cx<T> *)c->S;
         sa.Tb = (cx<T> *)c->Tb;
@@ -2036,13 +1954,13 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
         sa.ry = pipe_ry<T>(c);
         sa.W = split_w(c);
         void *sargs[] = {(void *)&sa};
-        const int txf = 32 * (XF_P_ROWS / 2), txi = 32 * std::max(2, XI_P_ROWS / 2);
+        const int txf = 32 * (XF_P_ROWS / 2);
         const int tyy = 32 * std::max(2, sa.ry);
-        const size_t s_xf = xfp_smem<T>(c), s_xi = xip_smem<T>(c), s_yf = yfp_smem<T>(c), s_yi = yip_smem<T>(c),
+        const size_t s_xf = xfp_smem<T>(c), s_yf = yfp_smem<T>(c), s_yi = yip_smem<T>(c),
                      s_zm = zmp_smem<T>(c);
-        const long long n_x = c->rows / XF_P_ROWS, n_xi = c->rows / XI_P_ROWS;
+        const long long n_x = c->rows / XF_P_ROWS;
         const long long n_y = (long long)c->nx * (3 * c->nz / sa.ry), n_z = (long long)c->nx * (c->Py / sa.W);
-        const void *f_xf = mmxk_kernel(K_XFP, sizeof(T) == 8, c->Px), *f_xi = mmxk_kernel(K_XIP, sizeof(T) == 8, c->Px), *f_yf = mmxk_kernel(K_YFP, sizeof(T) == 8, c->Py),
+        const void *f_xf = mmxk_kernel(K_XFP, sizeof(T) == 8, c->Px), *f_yf = mmxk_kernel(K_YFP, sizeof(T) == 8, c->Py),
                    *f_yi = mmxk_kernel(K_YIP, sizeof(T) == 8, c->Py), *f_zm = mmxk_kernel(K_ZMP, sizeof(T) == 8, c->Pz);
         timed(0, [&] {
             cudaLaunchKernel(f_xf, dim3(persistent_grid(f_xf, txf, s_xf, n_x)), dim3(txf), xfa, s_xf, s);
@@ -2063,9 +1981,7 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
             cudaLaunchKernel(f_yi, dim3(persistent_grid(f_yi, tyy, s_yi, n_y)), dim3(tyy), sargs, s_yi, s);
             c->launches += 2;
         });
-        timed(2, [&] {
-            cudaLaunchKernel(f_xi, dim3(persistent_grid(f_xi, txi, s_xi, n_xi)), dim3(txi), xia, s_xi, s);
-        });
+        timed(2, [&] { cudaLaunchKernel(mmxk_kernel(K_XI, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s); });
         return;
     }
     timed(0, [&] { cudaLaunchKernel(mmxk_kernel(K_XF, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s); });
@@ -2200,7 +2116,6 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
                 return MMX_ERR_CUDA;
     if (pipe_ok<T>(c)) {
         const std::pair<const void *, size_t> fk[] = {{mmxk_kernel(K_XFP, sizeof(T) == 8, c->Px), xfp_smem<T>(c)},
-                                                      {mmxk_kernel(K_XIP, sizeof(T) == 8, c->Px), xip_smem<T>(c)},
                                                       {mmxk_kernel(K_YFP, sizeof(T) == 8, c->Py), yfp_smem<T>(c)},
                                                       {mmxk_kernel(K_YIP, sizeof(T) == 8, c->Py), yip_smem<T>(c)},
                                                       {mmxk_kernel(K_ZMP, sizeof(T) == 8, c->Pz), zmp_smem<T>(c)}};
