@@ -32,6 +32,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdint>
 #include <utility>
 #include <vector>
@@ -514,6 +515,7 @@ __global__ void __launch_bounds__(256, 2) k_xi(const XArgs<T> a)
     constexpr int PXS = PX + 8;  // pair stride: pairs land in different banks
     const int np = (a.trows + 1) >> 1;
     const long long R = a.rows, r0 = (long long)blockIdx.x * a.trows;
+#pragma unroll 8
     for (int idx = threadIdx.x; idx < np * nx; idx += blockDim.x) {
         const int k = idx / np, p = idx - k * np;
         const long long ra = r0 + 2 * p, rb = ra + 1;
@@ -570,14 +572,17 @@ __device__ __forceinline__ void load_K(const T *K, int kx, int Hy, int Hz, int P
 {
     const bool fy = ky > (Py >> 1), fz = kz > (Pz >> 1);
     const int y = fy ? Py - ky : ky, z = fz ? Pz - kz : kz;
-    const T *p = K + ((size_t)((size_t)kx * Hz + z) * Hy + y) * 6;
+    // one 6-component record as three aligned pairs through the read-only path
+    using V2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    const V2 *q = reinterpret_cast<const V2 *>(K + ((size_t)((size_t)kx * Hz + z) * Hy + y) * 6);
+    const V2 p0 = __ldg(q), p1 = __ldg(q + 1), p2 = __ldg(q + 2);
     const T sy = fy ? (T)-1 : (T)1, sz = fz ? (T)-1 : (T)1;
-    k6[0] = p[0];
-    k6[1] = p[1];
-    k6[2] = p[2];
-    k6[3] = sy * p[3];
-    k6[4] = sz * p[4];
-    k6[5] = sy * sz * p[5];
+    k6[0] = (T)p0.x;
+    k6[1] = (T)p0.y;
+    k6[2] = (T)p1.x;
+    k6[3] = sy * (T)p1.y;
+    k6[4] = sz * (T)p2.x;
+    k6[5] = sy * sz * (T)p2.y;
 }
 
 template <typename T>
@@ -633,6 +638,7 @@ __global__ void __launch_bounds__(YZ_THREADS, 2) k_yz(const YZArgs<T> a)
 
     // Fourier-space tensor multiply (Eq. 2): H = K M, K real symmetric
     if (kx != 0) {
+#pragma unroll 4
         for (int q = threadIdx.x; q < plane; q += blockDim.x) {
             const int ky = q & (Py - 1), kz = q >> lgPy;
             T k6[6];
@@ -1247,6 +1253,7 @@ __global__ void __launch_bounds__(192) k_zm_r(const SplitArgs<T> a)
     for (int kz = 0; kz < PZ; ++kz) B[c * plane + kz * W + w] = v[kz];
     __syncthreads();
     const int half = Py >> 1;
+#pragma unroll 4
     for (int q = threadIdx.x; q < plane; q += blockDim.x) {
         const int ww = q & (W - 1), kz = q >> lgW, slot = ky0 + ww;
         if (kx != 0 || (slot != 0 && slot != half)) {
