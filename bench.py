@@ -390,7 +390,10 @@ def run_mmx(args):
         "clocks": clocks,
     }
     if not args.no_accuracy:
-        line["accuracy"] = accuracy(pkg, torch, dev, cfg, args.chunk_ps)
+        # 2 ps: before the random-on-sphere state has diverged chaotically;
+        # one full chunk: after (every mode then differs from the reference
+        # by O(1) in the cells that switched differently)
+        line["accuracy"] = [accuracy(pkg, torch, dev, cfg, 2.0), accuracy(pkg, torch, dev, cfg, args.chunk_ps)]
     if not args.no_large:
         line["demag_roofline_large3d"] = large3d_demag(pkg, torch, dev)
     if not args.no_cpu:

@@ -51,6 +51,8 @@ struct DevState {
     StageCoef coef[MMX_MAXS];
 };
 
+static_assert(sizeof(DevState) % 8 == 0, "DevState is copied as 8-byte words");
+
 struct TabArgs {
     int s, order, adaptive, fsal;
     double a[MMX_MAXS];

@@ -1428,10 +1428,12 @@ __global__ void k_prepare(DevState *st, const TabArgs tab, const PhysArgs ph, in
     prepare_coefs(st, tab, ph, p, sm_sig, sm_iden);
 }
 
-template <typename T> __device__ void controller(const StageArgs<T> &a)
+// Eq. 5 controller on a shared-memory copy `st` of the device state (the
+// caller loads it and writes it back); the error accumulator and the block
+// counter live in global memory (gst) and are reset here.
+template <typename T> __device__ void controller(const StageArgs<T> &a, DevState *st, DevState *gst, double e)
 {
-    DevState *st = a.st;
-    const double e = __longlong_as_double((long long)atomicExch(&st->err_bits, 0ULL));
+    st->err_bits = 0;
     st->blocks_done = 0;
     st->last_err = e;
     st->attempts++;
@@ -1674,13 +1676,23 @@ __global__ void __launch_bounds__(ST_THREADS, 2) k_stage(const StageArgs<T> a)
     }
     __syncthreads();
     if (s_last) {
+        // the state in shared memory: one coalesced read and one write-back
+        // instead of dozens of dependent global round trips in the controller
+        __shared__ __align__(16) DevState sst;
+        __threadfence();
+        const int nw = (int)(sizeof(DevState) / 8);
+        unsigned long long *gw = reinterpret_cast<unsigned long long *>(st);
+        unsigned long long *sw = reinterpret_cast<unsigned long long *>(&sst);
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) sw[i] = ((volatile unsigned long long *)gw)[i];
+        __syncthreads();
         if (threadIdx.x == 0) {
-            __threadfence();
-            controller(a);
-            __threadfence();
+            const double e = __longlong_as_double((long long)atomicExch(&st->err_bits, 0ULL));
+            controller(a, &sst, st, e);
         }
         __syncthreads();
-        if (!st->done) prepare_coefs(st, a.tab, a.ph, a.ctl.p, s_sig, s_iden);
+        if (!sst.done) prepare_coefs(&sst, a.tab, a.ph, a.ctl.p, s_sig, s_iden);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) gw[i] = sw[i];
     }
 }
 
