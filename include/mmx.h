@@ -188,6 +188,45 @@ int mmx_get_profile(mmx_ctx *ctx, double *ms, long long *launches);
 int mmx_demag_static(const mmx_mesh *mesh, double Ms, int precision, const void *m_dev, void *H_dev,
                      void *cuda_stream);
 
+/* Batched ensemble of independent simulations (no counterpart in the paper:
+ * the method of Sec. II applied to many unrelated samples at once).  A batch
+ * groups n existing contexts of any mesh size, material, method, order and
+ * precision; mmx_batch_run integrates every member to its own end time with
+ * ONE CUDA-graph launch on cuda_stream (NULL = default stream).  The graph
+ * holds, per member, the preparation kernel and the member's own device-side
+ * loops (the priming loop, then the extrapolated loop, each a conditional
+ * while node stepped by the member's controller), with no dependency between
+ * members, so the GPU runs the members side by side.  Every member keeps its
+ * own step size, accept/reject decisions and history (Eq. 5, Eq. 6): the
+ * result of each member is the one mmx_run(member, t_end[i]) gives.
+ *   - members: n distinct contexts (1 <= n <= 4096), owned by the caller, that
+ *     must outlive the batch; the batch only reads their buffers.  While the
+ *     batch exists, the members may still be used on their own (mmx_set_m,
+ *     mmx_run, ...), but not concurrently with mmx_batch_run.
+ *   - The graph is built at the first mmx_batch_run, kept, and reused.
+ *   - MMX_ERR_ARG for a NULL or duplicate member or n out of range (text from
+ *     mmx_last_error(NULL)). */
+typedef struct mmx_batch mmx_batch;
+int mmx_batch_create(int n, mmx_ctx *const *members, void *cuda_stream, mmx_batch **out);
+
+/* Integrates member i from its current time to t_end[i] (host array of n);
+ * members with t_end[i] <= their time are left as they are.  status, if not
+ * NULL, receives per member what mmx_run would have returned (MMX_OK,
+ * MMX_WARN_HMIN, MMX_ERR_NONFINITE, MMX_ERR_TIMEOUT, ...; the member's own
+ * mmx_last_error holds the text).  Returns the most severe member status
+ * (the first negative one, else MMX_WARN_HMIN if any, else MMX_OK), or a
+ * batch error (MMX_ERR_CUDA, text from mmx_batch_last_error).  Synchronises
+ * cuda_stream.  Per-member counters: mmx_get_stats on each member. */
+int mmx_batch_run(mmx_batch *b, const double *t_end, int *status);
+
+/* Text of the batch's own error from its last mmx_batch_run ("" when the
+ * run had none, e.g. when only members failed); with b == NULL the text of
+ * the last failed mmx_batch_create of this thread. */
+const char *mmx_batch_last_error(const mmx_batch *b);
+
+/* Frees the batch's graph (not its members). */
+void mmx_batch_destroy(mmx_batch *b);
+
 /* Text of the last error (never NULL; "" if none).  ctx may be NULL, then
  * the text of the last failed mmx_create of this thread is returned. */
 const char *mmx_last_error(const mmx_ctx *ctx);

@@ -81,6 +81,10 @@ SIGNATURES = {
     "mmx_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int]),
     "mmx_get_profile": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "mmx_demag_static": (ctypes.c_int, [ctypes.POINTER(mmx_mesh), ctypes.c_double, ctypes.c_int, _VP, _VP, _VP]),
+    "mmx_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_VP), _VP, ctypes.POINTER(_VP)]),
+    "mmx_batch_run": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    "mmx_batch_last_error": (ctypes.c_char_p, [_VP]),
+    "mmx_batch_destroy": (None, [_VP]),
     "mmx_last_error": (ctypes.c_char_p, [_VP]),
     "mmx_destroy": (None, [_VP]),
 }
@@ -201,6 +205,38 @@ def mmx_demag_static(mesh, Ms, precision, m_dev, H_dev, cuda_stream=None):
     return _check(rc, None)
 
 
+def mmx_batch_create(members, cuda_stream=None):
+    """Groups context handles into a batch run by one graph launch."""
+    arr = (_VP * len(members))(*members)
+    out = _VP()
+    _check(lib().mmx_batch_create(len(members), arr, cuda_stream, ctypes.byref(out)), None)
+    return out.value
+
+
+def mmx_batch_run(batch, t_end):
+    """Integrates member i to t_end[i]; returns (overall code, per-member
+    codes).  Raises on an error of the batch itself; member errors are left
+    in the codes (text from each member's mmx_last_error)."""
+    n = len(t_end)
+    te = (ctypes.c_double * n)(*[float(t) for t in t_end])
+    st = (ctypes.c_int * n)()
+    rc = lib().mmx_batch_run(batch, te, st)
+    msg = mmx_batch_last_error(batch)
+    if rc < 0 and msg:
+        raise MMXError(rc, msg)
+    return rc, list(st)
+
+
+def mmx_batch_last_error(batch=None):
+    msg = lib().mmx_batch_last_error(batch)
+    return msg.decode() if msg else ""
+
+
+def mmx_batch_destroy(batch):
+    if batch:
+        lib().mmx_batch_destroy(batch)
+
+
 def mmx_last_error(ctx=None):
     msg = lib().mmx_last_error(ctx)
     return msg.decode() if msg else ""
@@ -295,6 +331,38 @@ class Context:
     def close(self):
         if getattr(self, "handle", None):
             mmx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owner of a batch over existing Context objects (kept alive here)."""
+
+    def __init__(self, contexts, stream=None):
+        self.contexts = list(contexts)
+        handle = stream
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            handle = stream.cuda_stream
+        self.handle = mmx_batch_create([c.handle for c in self.contexts], handle)
+
+    def run(self, t_end):
+        """t_end: one time for every member, or a sequence of len(members)."""
+        if not hasattr(t_end, "__len__"):
+            t_end = [t_end] * len(self.contexts)
+        rc, status = mmx_batch_run(self.handle, t_end)
+        for c, r in zip(self.contexts, status):
+            if r < 0:
+                raise MMXError(r, mmx_last_error(c.handle))
+        return rc, status
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mmx_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -47,6 +47,7 @@ struct DevState {
     long long acc_target;     // stop when accepted reaches this
     long long attempt_limit;  // attempts allowed in the current run
     long long run_attempts;
+    long long prime_attempts;  // attempts made by priming loops (launch accounting)
     unsigned long long t_start_ns, time_limit_ns;
     StageCoef coef[MMX_MAXS];
 };
@@ -132,3 +133,8 @@ void mmxk_stage(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime_graph,
                 cudaGraphConditionalHandle cond, int use_cond);
 // fills DevState::coef for the attempt described by the device state
 void mmxk_prepare(mmx_ctx *c, cudaStream_t s);
+// batched runs: the same preparation as an explicit graph node, and a node
+// that sets a loop's while condition from the device state
+int mmxk_add_prepare_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t nd, mmx_ctx *c, cudaGraphNode_t *out);
+int mmxk_add_gate_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t nd, mmx_ctx *c,
+                       cudaGraphConditionalHandle h, int prime_loop, cudaGraphNode_t *out);

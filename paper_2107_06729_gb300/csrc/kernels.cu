@@ -28,6 +28,46 @@ void mmxk_prepare(mmx_ctx *c, cudaStream_t s)
     c->launches++;
 }
 
+// Sets the while condition of one loop of a batched run from the device state
+// before the loop starts: a member that is done, or (priming loop) already
+// primed, skips the loop.  Batched graphs do not reset conditions at launch.
+__global__ void k_gate(const DevState *st, int p, int prime_loop, cudaGraphConditionalHandle h)
+{
+    const bool run = !st->done && (!prime_loop || st->hist_n < p + 1);
+    cudaGraphSetConditional(h, run ? 1u : 0u);
+}
+
+static int add_kernel_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t nd, const void *fn, dim3 grid,
+                           dim3 block, void **args, cudaGraphNode_t *out)
+{
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void *>(fn);
+    kp.gridDim = grid;
+    kp.blockDim = block;
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    return cudaGraphAddKernelNode(out, g, deps, nd, &kp) == cudaSuccess ? 0 : MMX_ERR_CUDA;
+}
+
+int mmxk_add_prepare_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t nd, mmx_ctx *c, cudaGraphNode_t *out)
+{
+    DevState *st = c->st;
+    TabArgs tab = c->tab;
+    PhysArgs ph = c->ph;
+    int p = c->ctl.p;
+    void *args[] = {&st, &tab, &ph, &p};
+    return add_kernel_node(g, deps, nd, (const void *)k_prepare, dim3(1), dim3(256), args, out);
+}
+
+int mmxk_add_gate_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t nd, mmx_ctx *c,
+                       cudaGraphConditionalHandle h, int prime_loop, cudaGraphNode_t *out)
+{
+    const DevState *st = c->st;
+    int p = c->ctl.p;
+    void *args[] = {&st, &p, &prime_loop, &h};
+    return add_kernel_node(g, deps, nd, (const void *)k_gate, dim3(1), dim3(1), args, out);
+}
+
 size_t mmxk_split_smem_bytes(const mmx_ctx *c)
 {
     if (c->prec == MMX_FP64) return std::max(yf_smem<double>(c, split_rows<double>(c)), zm_smem<double>(c));

@@ -34,6 +34,7 @@
 #include <algorithm>
 #include <type_traits>
 #include <cstdint>
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -1438,6 +1439,7 @@ template <typename T> __device__ void controller(const StageArgs<T> &a, DevState
     st->last_err = e;
     st->attempts++;
     st->run_attempts++;
+    if (a.ctl.prime) st->prime_attempts++;
     const double h = st->h;
     int more = 0;
     if (!(e <= 1.7976931348623157e308)) {  // NaN or Inf
@@ -2108,6 +2110,20 @@ template <typename T> void twiddles(int L, std::vector<cx<T>> &out)
     }
 }
 
+// The dynamic shared-memory limit is a property of the kernel, shared by
+// every context in the process: only ever raise it, so that a context with a
+// smaller need cannot lower it under another live context of the same
+// transform length.
+inline bool raise_smem_limit(const void *f, size_t bytes)
+{
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    cudaFuncAttributes at;
+    if (cudaFuncGetAttributes(&at, f) != cudaSuccess) return false;
+    if ((size_t)at.maxDynamicSharedSizeBytes >= bytes) return true;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
+}
+
 template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
 {
     const size_t nK = (size_t)(c->nx + 1) * c->Hz * c->Hy * 6;
@@ -2126,36 +2142,29 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
     const void *xk[] = {mmxk_kernel(K_XF, sizeof(T) == 8, c->Px), mmxk_kernel(K_XI, sizeof(T) == 8, c->Px)};
     if (xs > 48 * 1024)
         for (const void *f : xk)
-            if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs) != cudaSuccess)
-                return MMX_ERR_CUDA;
+            if (!raise_smem_limit(f, xs)) return MMX_ERR_CUDA;
     const void *yk[] = {mmxk_kernel(K_YZ, sizeof(T) == 8, c->Py)};
     if (!c->split && ys > 48 * 1024)
         for (const void *f : yk)
-            if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ys) != cudaSuccess)
-                return MMX_ERR_CUDA;
+            if (!raise_smem_limit(f, ys)) return MMX_ERR_CUDA;
     if (pipe_ok<T>(c)) {
         const std::pair<const void *, size_t> fk[] = {{mmxk_kernel(K_XFP, sizeof(T) == 8, c->Px), xfp_smem<T>(c)},
                                                       {mmxk_kernel(K_YFP, sizeof(T) == 8, c->Py), yfp_smem<T>(c)},
                                                       {mmxk_kernel(K_YIP, sizeof(T) == 8, c->Py), yip_smem<T>(c)},
                                                       {mmxk_kernel(K_ZMP, sizeof(T) == 8, c->Pz), zmp_smem<T>(c)}};
         for (const auto &f : fk)
-            if (f.second > 48 * 1024 &&
-                cudaFuncSetAttribute(f.first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.second) !=
-                    cudaSuccess)
-                return MMX_ERR_CUDA;
+            if (f.second > 48 * 1024 && !raise_smem_limit(f.first, f.second)) return MMX_ERR_CUDA;
     }
     if (c->split) {
         const size_t sy = yf_smem<T>(c, split_rows<T>(c)), sz = zm_smem<T>(c);
         const void *fy[] = {mmxk_kernel(K_YF, sizeof(T) == 8, c->Py), mmxk_kernel(K_YI, sizeof(T) == 8, c->Py)};
         if (sy > 48 * 1024)
             for (const void *f : fy)
-                if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sy) != cudaSuccess)
-                    return MMX_ERR_CUDA;
+                if (!raise_smem_limit(f, sy)) return MMX_ERR_CUDA;
         const void *fz[] = {mmxk_kernel(K_ZM, sizeof(T) == 8, c->Pz)};
         if (sz > 48 * 1024)
             for (const void *f : fz)
-                if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz) != cudaSuccess)
-                    return MMX_ERR_CUDA;
+                if (!raise_smem_limit(f, sz)) return MMX_ERR_CUDA;
     }
     return 0;
 }

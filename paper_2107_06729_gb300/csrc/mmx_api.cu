@@ -15,6 +15,9 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -268,6 +271,44 @@ int run_loop(mmx_ctx *c, int which)
     }
 }
 
+// Process-wide cache of Newell tensors by mesh (the tensor does not depend on
+// Ms): contexts of an ensemble that share a mesh compute it once.  Entries
+// are dropped oldest first above kTensorCacheBytes.
+const size_t kTensorCacheBytes = (size_t)512 << 20;
+
+struct TensorEntry {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    std::shared_ptr<const std::vector<double>> N6;
+};
+
+std::mutex g_tensor_mu;
+std::deque<TensorEntry> g_tensors;
+
+std::shared_ptr<const std::vector<double>> tensor_for(const mmx_host_tensor_args &ta)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_tensor_mu);
+        for (const TensorEntry &e : g_tensors)
+            if (e.nx == ta.nx && e.ny == ta.ny && e.nz == ta.nz && e.dx == ta.dx && e.dy == ta.dy && e.dz == ta.dz)
+                return e.N6;
+    }
+    auto N6 = std::make_shared<std::vector<double>>((size_t)6 * ta.nx * ta.ny * ta.nz);
+    mmx_host_tensor(&ta, N6->data());
+    const size_t bytes = N6->size() * sizeof(double);
+    if (bytes <= kTensorCacheBytes / 4) {
+        std::lock_guard<std::mutex> lk(g_tensor_mu);
+        size_t total = bytes;
+        for (const TensorEntry &e : g_tensors) total += e.N6->size() * sizeof(double);
+        while (!g_tensors.empty() && total > kTensorCacheBytes) {
+            total -= g_tensors.front().N6->size() * sizeof(double);
+            g_tensors.pop_front();
+        }
+        g_tensors.push_back({ta.nx, ta.ny, ta.nz, ta.dx, ta.dy, ta.dz, N6});
+    }
+    return N6;
+}
+
 }  // namespace
 
 void mmx_set_thread_error(const char *msg) { g_create_err = msg ? msg : ""; }
@@ -363,12 +404,11 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     C.cmin_pow = std::pow(integ->cmin, md.order + 1);
     C.cmax_pow = std::pow(integ->cmax, md.order + 1);
 
-    // tensor and spectrum (host, binary128)
+    // tensor (host, binary128; shared by contexts of the same mesh) and spectrum
     mmx_host_tensor_args ta{c->nx, c->ny, c->nz, mesh->dx, mesh->dy, mesh->dz, mat->Ms};
-    std::vector<double> N6((size_t)6 * c->n);
-    mmx_host_tensor(&ta, N6.data());
+    std::shared_ptr<const std::vector<double>> N6 = tensor_for(ta);
     std::vector<double> Kspec((size_t)(c->nx + 1) * c->Hz * c->Hy * 6);
-    mmx_host_spectrum(&ta, N6.data(), c->N00, Kspec.data());
+    mmx_host_spectrum(&ta, N6->data(), c->N00, Kspec.data());
     for (int i = 0; i < 3; ++i) P.msN00[i] = mat->Ms * c->N00[i];
 
     // device buffers
@@ -465,13 +505,13 @@ int mmx_demag(mmx_ctx *c, const void *m_dev, void *H_dev)
     return MMX_OK;
 }
 
-static int run_common(mmx_ctx *c, double t_end, long long acc_more)
+// Host-side set-up, on the mirror c->h_st, of a run to t_end or of acc_more
+// more accepted steps; false when there is nothing to do.  The caller holds
+// a fresh copy of the device state and uploads it afterwards.
+static bool begin_run(mmx_ctx *c, double t_end, long long acc_more)
 {
-    int rc = read_state(c);
-    if (rc) return rc;
     DevState &s = *c->h_st;
-    if (acc_more <= 0 && !(t_end > s.t)) return MMX_OK;
-    const long long forced0 = s.forced;
+    if (acc_more <= 0 && !(t_end > s.t)) return false;
     s.t_end = t_end;
     s.acc_target = acc_more > 0 ? s.accepted + acc_more : LLONG_MAX;
     s.done = 0;
@@ -483,13 +523,34 @@ static int run_common(mmx_ctx *c, double t_end, long long acc_more)
     s.time_limit_ns = (unsigned long long)((tl ? atof(tl) : 300.0) * 1e9);
     s.err_bits = 0;
     s.blocks_done = 0;
-    {
-        const double rem = s.t_end - s.t;
-        const int cl = (s.h_ctrl * (1.0 + 1e-9) >= rem) ? 1 : 0;
-        s.h = cl ? rem : s.h_ctrl;
-        s.clipped = cl;
-    }
+    const double rem = s.t_end - s.t;
+    const int cl = (s.h_ctrl * (1.0 + 1e-9) >= rem) ? 1 : 0;
+    s.h = cl ? rem : s.h_ctrl;
+    s.clipped = cl;
     s.loop_more = 1;
+    return true;
+}
+
+// What the run that began with forced0 forced accepts returns (device
+// status and the h_min warning), from the mirror read after the run.
+static int end_status(mmx_ctx *c, long long forced0)
+{
+    const DevState &s = *c->h_st;
+    if (s.status) {
+        if (s.status == MMX_ERR_NONFINITE) return fail(c, s.status, "error estimate became non-finite");
+        if (s.status == MMX_ERR_TIMEOUT) return fail(c, s.status, "attempt or time limit of the run reached");
+        return fail(c, s.status, "device reported an error");
+    }
+    return s.forced > forced0 ? MMX_WARN_HMIN : MMX_OK;
+}
+
+static int run_common(mmx_ctx *c, double t_end, long long acc_more)
+{
+    int rc = read_state(c);
+    if (rc) return rc;
+    DevState &s = *c->h_st;
+    const long long forced0 = s.forced;
+    if (!begin_run(c, t_end, acc_more)) return MMX_OK;
     rc = write_state(c);
     if (rc) return rc;
     mmxk_prepare(c, c->stream);
@@ -501,12 +562,7 @@ static int run_common(mmx_ctx *c, double t_end, long long acc_more)
         if (s.done) break;
         if (which == 0) return fail(c, MMX_ERR_STATE, "device loop stopped before the run finished");
     }
-    if (s.status) {
-        if (s.status == MMX_ERR_NONFINITE) return fail(c, s.status, "error estimate became non-finite");
-        if (s.status == MMX_ERR_TIMEOUT) return fail(c, s.status, "attempt or time limit of the run reached");
-        return fail(c, s.status, "device reported an error");
-    }
-    return s.forced > forced0 ? MMX_WARN_HMIN : MMX_OK;
+    return end_status(c, forced0);
 }
 
 int mmx_run(mmx_ctx *c, double t_end)
@@ -650,6 +706,230 @@ void mmx_destroy(mmx_ctx *c)
     if (c->ev_a) cudaEventDestroy(c->ev_a);
     if (c->ev_b) cudaEventDestroy(c->ev_b);
     delete c;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ batched runs
+
+struct mmx_batch {
+    std::vector<mmx_ctx *> c;
+    std::vector<cudaStream_t> member_streams;  // distinct streams of the members
+    std::vector<cudaEvent_t> ev;               // one per distinct member stream
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_ok = false;
+    std::vector<long long> forced0, prime0;
+    std::vector<char> active;
+    std::string err;
+};
+
+namespace {
+
+int bfail(mmx_batch *b, int code, const std::string &msg)
+{
+    b->err = msg;
+    return code;
+}
+
+#define BK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e__ = (call);                                                                 \
+        if (e__ != cudaSuccess) return bfail(b, MMX_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+// One parent graph; per member a chain  prepare -> gate -> while(priming
+// attempt) -> gate -> while(extrapolated attempt)  (the priming pair only
+// when p >= 0), the members' chains independent of one another.  The while
+// bodies are the members' own attempts, captured as in build_graph, and
+// each member's controller drives its own condition handles.
+int build_batch_graph(mmx_batch *b)
+{
+    if (b->graph_ok) return 0;
+    cudaGraph_t g;
+    BK(cudaGraphCreate(&g, 0));
+    for (mmx_ctx *c : b->c) {
+        const long long launches = c->launches;
+        cudaGraphNode_t prev;
+        if (mmxk_add_prepare_node(g, nullptr, 0, c, &prev)) {
+            cudaGraphDestroy(g);
+            return bfail(b, MMX_ERR_CUDA, "adding a preparation node failed");
+        }
+        const int first = c->ctl.p >= 0 ? 1 : 0;
+        for (int which = first; which >= 0; --which) {
+            cudaGraphConditionalHandle h;
+            cudaGraphNode_t gate, node;
+            cudaGraphNodeParams cp{};
+            cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+            if (e == cudaSuccess && mmxk_add_gate_node(g, &prev, 1, c, h, which, &gate)) e = cudaErrorUnknown;
+            if (e == cudaSuccess) {
+                cp.type = cudaGraphNodeTypeConditional;
+                cp.conditional.handle = h;
+                cp.conditional.type = cudaGraphCondTypeWhile;
+                cp.conditional.size = 1;
+                e = cudaGraphAddNode(&node, g, &gate, nullptr, 1, &cp);
+            }
+            if (e == cudaSuccess)
+                e = cudaStreamBeginCaptureToGraph(c->cap_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeRelaxed);
+            if (e == cudaSuccess) {
+                body_kernels(c, c->cap_stream, which == 1 || c->ctl.p < 0, h, 1);
+                cudaGraph_t captured;
+                e = cudaStreamEndCapture(c->cap_stream, &captured);
+            }
+            if (e != cudaSuccess) {
+                c->launches = launches;
+                cudaGraphDestroy(g);
+                return bfail(b, MMX_ERR_CUDA, std::string("building the batch graph: ") + cudaGetErrorString(e));
+            }
+            prev = node;
+        }
+        c->launches = launches;
+    }
+    cudaGraphExec_t ex;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return bfail(b, MMX_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    b->graph = g;
+    b->gexec = ex;
+    b->graph_ok = true;
+    return 0;
+}
+
+// severity order of member results: errors, then the h_min warning
+int combine(int acc, int rc)
+{
+    if (acc < 0) return acc;
+    if (rc < 0) return rc;
+    return std::max(acc, rc);
+}
+
+}  // namespace
+
+extern "C" {
+
+int mmx_batch_create(int n, mmx_ctx *const *members, void *cuda_stream, mmx_batch **out)
+{
+    if (!out) return MMX_ERR_ARG;
+    *out = nullptr;
+    if (n < 1 || n > 4096 || !members) {
+        g_create_err = "batch: need 1 <= n <= 4096 members";
+        return MMX_ERR_ARG;
+    }
+    std::vector<mmx_ctx *> v(members, members + n);
+    for (int i = 0; i < n; ++i) {
+        if (!v[i]) {
+            g_create_err = "batch: NULL member";
+            return MMX_ERR_ARG;
+        }
+    }
+    std::vector<mmx_ctx *> sorted = v;
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) {
+        g_create_err = "batch: a context appears twice";
+        return MMX_ERR_ARG;
+    }
+    mmx_batch *b = new (std::nothrow) mmx_batch();
+    if (!b) return MMX_ERR_OOM;
+    b->c = v;
+    b->stream = (cudaStream_t)cuda_stream;
+    for (mmx_ctx *c : v)
+        if (std::find(b->member_streams.begin(), b->member_streams.end(), c->stream) == b->member_streams.end())
+            b->member_streams.push_back(c->stream);
+    bool ok = true;
+    for (size_t i = 0; ok && i < b->member_streams.size(); ++i) {
+        cudaEvent_t e;
+        ok = cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        if (ok) b->ev.push_back(e);
+    }
+    if (!ok) {
+        cudaGetLastError();
+        g_create_err = "batch: event creation failed";
+        mmx_batch_destroy(b);
+        return MMX_ERR_CUDA;
+    }
+    b->forced0.assign(n, 0);
+    b->prime0.assign(n, 0);
+    b->active.assign(n, 0);
+    *out = b;
+    return MMX_OK;
+}
+
+int mmx_batch_run(mmx_batch *b, const double *t_end, int *status)
+{
+    if (!b || !t_end) return MMX_ERR_ARG;
+    b->err.clear();
+    const int n = (int)b->c.size();
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(t_end[i])) return bfail(b, MMX_ERR_ARG, "batch: t_end must be finite");
+    bool graphs = true;
+    for (mmx_ctx *c : b->c) graphs = graphs && c->use_graphs && !c->profiling;
+    int rc_all = MMX_OK;
+    if (!graphs) {
+        // graphs disabled or a member is being profiled: the members' own runs
+        for (int i = 0; i < n; ++i) {
+            const int rc = run_common(b->c[i], t_end[i], 0);
+            if (status) status[i] = rc;
+            rc_all = combine(rc_all, rc);
+        }
+        return rc_all;
+    }
+    int rc = build_batch_graph(b);
+    if (rc) return rc;
+    // after the members' pending work
+    for (size_t j = 0; j < b->member_streams.size(); ++j) {
+        BK(cudaEventRecord(b->ev[j], b->member_streams[j]));
+        BK(cudaStreamWaitEvent(b->stream, b->ev[j], 0));
+    }
+    for (mmx_ctx *c : b->c) BK(cudaMemcpyAsync(c->h_st, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < n; ++i) {
+        mmx_ctx *c = b->c[i];
+        b->forced0[i] = c->h_st->forced;
+        b->prime0[i] = c->h_st->prime_attempts;
+        b->active[i] = begin_run(c, t_end[i], 0) ? 1 : 0;
+        if (!b->active[i]) c->h_st->done = 1;
+        BK(cudaMemcpyAsync(c->st, c->h_st, sizeof(DevState), cudaMemcpyHostToDevice, b->stream));
+    }
+    BK(cudaGraphLaunch(b->gexec, b->stream));
+    for (mmx_ctx *c : b->c) BK(cudaMemcpyAsync(c->h_st, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < n; ++i) {
+        mmx_ctx *c = b->c[i];
+        const DevState &s = *c->h_st;
+        const long long pa = s.prime_attempts - b->prime0[i];
+        const int gates = c->ctl.p >= 0 ? 2 : 1;
+        c->launches += 1 + gates;
+        int r = MMX_OK;
+        if (b->active[i]) {
+            c->launches += pa * kernels_per_attempt(c, 1) + (s.run_attempts - pa) * kernels_per_attempt(c, c->ctl.p < 0);
+            r = s.done ? end_status(c, b->forced0[i]) : fail(c, MMX_ERR_STATE, "batched loops stopped before the run finished");
+        }
+        if (status) status[i] = r;
+        rc_all = combine(rc_all, r);
+    }
+    return rc_all;
+}
+
+const char *mmx_batch_last_error(const mmx_batch *b)
+{
+    if (!b) return g_create_err.c_str();
+    return b->err.c_str();
+}
+
+void mmx_batch_destroy(mmx_batch *b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    if (b->graph_ok) {
+        cudaGraphExecDestroy(b->gexec);
+        cudaGraphDestroy(b->graph);
+    }
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    delete b;
 }
 
 }  // extern "C"

@@ -132,3 +132,41 @@ def film_large3d(seed=0):
         "t_end": 1e-10,
         "m0_fn": lambda: m_vortex(n, d, seed=seed),
     }
+
+
+def ensemble_config3(seed=0, n_samples=64):
+    """Batched ensemble of independent films of uneven sizes: side lengths
+    drawn from {32, 64, 128, 256} per axis, 1 or 2 layers, 4 nm cells; per
+    sample Ms ~ U[4e5, 1.2e6] A/m, alpha ~ U[0.005, 0.1], and a static
+    in-plane field of magnitude ~ U[0, 50] mT at a uniform random angle;
+    A = 13 pJ/m, no anisotropy.  Initial m: a random in-plane direction plus
+    U(-0.05, 0.05) noise, renormalised.  RKF45 at e_max = 1e-5 with
+    4th-order extrapolation, FP32 fields.  Returns a list of sample dicts in
+    the format of the single-film configurations."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    sides = (32, 64, 128, 256)
+    out = []
+    for i in range(n_samples):
+        nx = int(rng.choice(sides))
+        ny = int(rng.choice(sides))
+        nz = int(rng.integers(1, 3))
+        Ms = float(rng.uniform(4e5, 1.2e6))
+        alpha = float(rng.uniform(0.005, 0.1))
+        b = float(rng.uniform(0.0, 50.0))
+        phi = float(rng.uniform(0.0, 2 * np.pi))
+        psi = float(rng.uniform(0.0, 2 * np.pi))
+        m_seed = int(rng.integers(0, 2 ** 31))
+        n = (nx, ny, nz)
+        out.append({
+            "name": "film_%dx%dx%d_rkf45_p4_fp32" % n,
+            "mesh": {"n": n, "d": (4e-9, 4e-9, 4e-9)},
+            "material": {"Ms": Ms, "A": 1.3e-11, "K": 0.0, "ku": (1.0, 0.0, 0.0),
+                         "alpha": alpha, "gamma": GAMMA},
+            "field": {"H0": tuple(mT((b * np.cos(phi), b * np.sin(phi), 0.0))),
+                      "pulse": (0.0, 0.0, 0.0), "t_on": 0.0, "t_off": 0.0},
+            "integrator": {"method": "RKF45", "extrap_order": 4, "adaptive": True, "h": 1e-13,
+                           "tol": 1e-5, "hmin": 1e-15, "hmax": 3e-12, "cmin": 0.01, "cmax": 2.0},
+            "precision": "fp32",
+            "m0": m_uniform_noise(n, direction=(np.cos(psi), np.sin(psi), 0.0), seed=m_seed),
+        })
+    return out

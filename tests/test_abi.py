@@ -83,3 +83,20 @@ def test_unknown_method_and_precision(libpath):
     I.method = 0
     with pytest.raises(pkg.MMXError):
         pkg.mmx_create(M, A, F, I, 7)
+
+
+def test_batch_arguments_are_checked_on_the_host(libpath):
+    """mmx_batch_create rejects an empty batch and NULL members before any
+    CUDA call; mmx_last_error(NULL) / mmx_batch_last_error(NULL) say why."""
+    import ctypes
+    import paper_2107_06729_gb300 as pkg
+    L = pkg.lib()
+    out = ctypes.c_void_p(123)
+    assert L.mmx_batch_create(0, None, None, ctypes.byref(out)) == pkg.MMX_ERR_ARG
+    assert out.value is None
+    assert "n <= 4096" in pkg.mmx_batch_last_error(None)
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert L.mmx_batch_create(2, arr, None, ctypes.byref(out)) == pkg.MMX_ERR_ARG
+    assert "NULL member" in pkg.mmx_last_error(None)
+    assert L.mmx_batch_run(None, None, None) == pkg.MMX_ERR_ARG
+    L.mmx_batch_destroy(None)

@@ -102,3 +102,29 @@ def test_large_column_uses_split_path_and_matches_oracle(prec, tol):
     n, d, m, ref = _large_case()
     got = gpu_demag({"n": n, "d": d}, MAT, m, prec)
     assert rel_max(got, ref) < tol
+
+
+def test_live_contexts_of_one_length_keep_their_shared_memory():
+    """Two live FP32 contexts whose fused y-z pass has the same transform
+    length (Py = 128) but different shared-memory needs (110 KB for nz = 16,
+    55 KB for nz = 8): creating the smaller one after the larger must not
+    lower the kernel's limit under the larger one."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_util import gpu_context
+    d = (2e-9, 2e-9, 2e-9)
+    big = gpu_context({"n": (8, 64, 16), "d": d}, MAT, {}, {"method": "RK4", "h": 1e-13}, "fp32")
+    small = gpu_context({"n": (8, 64, 8), "d": d}, MAT, {}, {"method": "RK4", "h": 1e-13}, "fp32")
+    try:
+        for ctx, n in ((big, (8, 64, 16)), (small, (8, 64, 8)), (big, (8, 64, 16))):
+            m = W.m_random(n, seed=5)
+            ref = O.demag_fft(O.newell_octant(*n, *d), MAT["Ms"], m)
+            m_t = torch.from_numpy(m).to("cuda", torch.float32)
+            H_t = torch.empty_like(m_t)
+            ctx.demag(m_t, H_t)
+            torch.cuda.synchronize()
+            assert rel_max(H_t.double().cpu().numpy(), ref) < 1e-5
+    finally:
+        big.close()
+        small.close()
