@@ -104,6 +104,9 @@ struct mmx_ctx {
     void *m[2], *Y[2], *F, *G, *hist, *S, *K, *twx, *twy, *twz;
     void *Tb;    // split y/z path: y spectrum [kx][c nz + z][Py] (complex)
     bool split;  // the y-z column does not fit one CTA: YF, ZM, YI instead of YZ
+    bool cluster;     // ... and a thread-block cluster per kx column runs it instead (YZC)
+    int yzc_C, yzc_W; // cluster size and z sub-tile width of YZC
+    int nd;           // kernels per exact demag evaluation
     DevState *st;
     DevState *h_st;  // pinned host mirror
     // graphs: [0] main loop, [1] priming loop
@@ -131,6 +134,9 @@ void mmxk_demag(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int 
                 const void *src, int dst_mode, void *dst, const void *self_src);
 void mmxk_stage(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime_graph,
                 cudaGraphConditionalHandle cond, int use_cond);
+// decides whether the cluster-fused y-z pass runs a split-size mesh (sets
+// cluster, yzc_C, yzc_W); 0 or MMX_ERR_CUDA
+int mmxk_cluster_plan(mmx_ctx *c);
 // fills DevState::coef for the attempt described by the device state
 void mmxk_prepare(mmx_ctx *c, cudaStream_t s);
 // batched runs: the same preparation as an explicit graph node, and a node

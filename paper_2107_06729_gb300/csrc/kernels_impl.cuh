@@ -27,6 +27,7 @@
 // self term), the Landau-Lifshitz torque, and the next stage input.  The
 // last stage forms the propagated and embedded solutions, renormalises,
 // reduces the error norm, and its last CTA runs the controller of Eq. 5.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -44,6 +45,8 @@
 enum MmxKernelKind { K_XF, K_XI, K_YZ, K_YF, K_YI, K_ZM, K_XFP, K_YFP, K_YIP, K_ZMP, K_ZMR };
 // pointer to the instance of `kind` for precision (f64) and transform length L
 const void *mmxk_kernel(int kind, bool f64, int L);
+// the cluster-fused y-z pass (FP32) for lengths Py and Pz, or NULL
+const void *mmxk_yzc_kernel(int Py, int Pz);
 
 namespace {
 
@@ -1308,6 +1311,167 @@ __global__ void __launch_bounds__(192) k_zm_r(const SplitArgs<T> a)
         if (z < nz) g[(size_t)z * Py] = v[z];
 }
 
+// ---------------------------------------------- cluster-fused y-z pass (YZC)
+// For meshes whose y-z column does not fit one CTA.  A cluster of C CTAs
+// takes one kx column.  CTA j holds the rows (c nz + z) in [j RC, (j+1) RC)
+// (RC = 3 nz / C) in shared memory and transforms them along y (the packed
+// kx = 0 column is then separated into its two real-x spectra, A in the slots
+// below Py/2 and B above, as in YF).  It then owns the ky slots
+// [j Py/C, (j+1) Py/C): per sub-tile of W slots, each thread gathers one
+// (c, ky) column over z from the rows of all CTAs through distributed shared
+// memory, transforms it along z in registers, the tensor multiply runs on a
+// shared tile, and the inverse z transforms are written back in place.  Last,
+// every CTA recombines (kx = 0) and transforms its rows back along y.  The
+// y spectrum never leaves the cluster: one read and one write of the x
+// spectrum per evaluation, plus the tensor.
+template <typename T, int PY, int PZ>
+__global__ void __launch_bounds__(192, 2) k_yzc(const SplitArgs<T> a)
+{
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cg::cluster_group cl = cg::this_cluster();
+    if (a.st) {
+        // the state is not written during an evaluation: every CTA of the
+        // cluster takes the same decision, before any cluster barrier
+        if (a.st->done) return;
+        if (a.stage0 && a.st->f1_valid) return;
+    }
+    const int C = (int)cl.num_blocks(), j = (int)cl.block_rank();
+    const int RC = a.ry, W = a.W, nz = a.nz, ny = a.ny;
+    const int kx = blockIdx.x / C;
+    cx<T> *ybuf = reinterpret_cast<cx<T> *>(smraw);
+    cx<T> *B = ybuf + padded_words((size_t)RC * PY);
+    const Pad<T> Y{ybuf, 0};
+    constexpr int half = PY / 2;
+    const int wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    cx<T> *S = a.S + (size_t)kx * a.rows + (size_t)j * RC * ny;
+    const int lgny = ilog2(ny);
+
+    // 1. own rows, forward along y (input zero above ny)
+    for (int idx = threadIdx.x; idx < RC * ny; idx += blockDim.x) {
+        const int r = idx >> lgny, y = idx & (ny - 1);
+        Y[r * PY + y] = S[idx];
+    }
+    __syncthreads();
+    for (int r = wp; r < RC; r += nw) WarpFFT<T, false, PY, 1>::run(Y.at(r * PY), 1, a.twy, true, false);
+    if (kx == 0) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < RC * (half - 1); idx += blockDim.x) {
+            const int r = idx / (half - 1), q = 1 + idx - r * (half - 1);
+            const Pad<T> u = Y.at(r * PY);
+            const cx<T> z = u[q], zm = u[PY - q];
+            u[q] = mk((T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y));       // A(q)
+            u[PY - q] = mk((T)0.5 * (z.y + zm.y), (T)0.5 * (zm.x - z.x));  // B(q)
+        }
+    }
+    cl.sync();
+
+    // 2. the owned ky slots: z transform, tensor multiply, inverse z
+    const int lgW = ilog2(W), plane = PZ * W, Wc = PY / C;
+    const bool zt = threadIdx.x < 3 * W;
+    const int c = zt ? (int)threadIdx.x >> lgW : 0, ww = (int)threadIdx.x & (W - 1);
+    for (int s0 = j * Wc; s0 < (j + 1) * Wc; s0 += W) {
+        const int slot = s0 + ww;
+        cx<T> v[PZ];
+        if (zt) {
+#pragma unroll
+            for (int z = 0; z < PZ; ++z) {
+                if (z < nz) {
+                    const int row = c * nz + z, own = row / RC, lr = row - own * RC;
+                    const Pad<T> R{cl.map_shared_rank(ybuf, own), 0};
+                    v[z] = R[lr * PY + slot];
+                } else {
+                    v[z] = mk<T>(0, 0);
+                }
+            }
+            RegFFT<T, PZ, 1, false>::run(v, a.twz);
+#pragma unroll
+            for (int kz = 0; kz < PZ; ++kz) B[c * plane + kz * W + ww] = v[kz];
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < plane; q += blockDim.x) {
+            const int qw = q & (W - 1), kz = q >> lgW, sl = s0 + qw;
+            if (kx != 0 || (sl != 0 && sl != half)) {
+                T k6[6];
+                if (kx != 0)
+                    load_K(a.K, kx, a.Hy, a.Hz, PY, PZ, sl, kz, k6);
+                else if (sl < half)
+                    load_K(a.K, 0, a.Hy, a.Hz, PY, PZ, sl, kz, k6);
+                else
+                    load_K(a.K, a.nx, a.Hy, a.Hz, PY, PZ, PY - sl, kz, k6);
+                cx<T> hx, hy, hz;
+                apply_K(k6, B[q], B[plane + q], B[2 * plane + q], hx, hy, hz);
+                B[q] = hx;
+                B[plane + q] = hy;
+                B[2 * plane + q] = hz;
+            } else {
+                // slots 0 and Py/2 of the packed column: A and B share the
+                // slot; separate them along z with the mirror kz -> -kz
+                const int kzm = (PZ - kz) & (PZ - 1);
+                if (kz > kzm) continue;
+                const int qm = kzm * W + qw;
+                T k0[6], kn[6], P[6], Q[6];
+                load_K(a.K, 0, a.Hy, a.Hz, PY, PZ, sl, kz, k0);
+                load_K(a.K, a.nx, a.Hy, a.Hz, PY, PZ, sl, kz, kn);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    P[i] = (T)0.5 * (k0[i] + kn[i]);
+                    Q[i] = (T)0.5 * (k0[i] - kn[i]);
+                }
+                const cx<T> ux = B[q], uy = B[plane + q], uz = B[2 * plane + q];
+                const cx<T> vx = B[qm], vy = B[plane + qm], vz = B[2 * plane + qm];
+                cx<T> a1, a2, a3, b1, b2, b3;
+                apply_K(P, ux, uy, uz, a1, a2, a3);
+                apply_K(Q, mk(vx.x, -vx.y), mk(vy.x, -vy.y), mk(vz.x, -vz.y), b1, b2, b3);
+                B[q] = cadd(a1, b1);
+                B[plane + q] = cadd(a2, b2);
+                B[2 * plane + q] = cadd(a3, b3);
+                if (qm != q) {
+                    apply_K(P, vx, vy, vz, a1, a2, a3);
+                    apply_K(Q, mk(ux.x, -ux.y), mk(uy.x, -uy.y), mk(uz.x, -uz.y), b1, b2, b3);
+                    B[qm] = cadd(a1, b1);
+                    B[plane + qm] = cadd(a2, b2);
+                    B[2 * plane + qm] = cadd(a3, b3);
+                }
+            }
+        }
+        __syncthreads();
+        if (zt) {
+#pragma unroll
+            for (int kz = 0; kz < PZ; ++kz) v[kz] = B[c * plane + kz * W + ww];
+            RegFFT<T, PZ, 1, true>::run(v, a.twz);
+#pragma unroll
+            for (int z = 0; z < PZ; ++z) {
+                if (z < nz) {
+                    const int row = c * nz + z, own = row / RC, lr = row - own * RC;
+                    const Pad<T> R{cl.map_shared_rank(ybuf, own), 0};
+                    R[lr * PY + slot] = v[z];
+                }
+            }
+        }
+        __syncthreads();  // B is refilled by the next sub-tile
+    }
+    cl.sync();
+
+    // 3. own rows back along y (kx = 0: U = A + i B first), truncated to ny
+    if (kx == 0) {
+        for (int idx = threadIdx.x; idx < RC * (half - 1); idx += blockDim.x) {
+            const int r = idx / (half - 1), q = 1 + idx - r * (half - 1);
+            const Pad<T> u = Y.at(r * PY);
+            const cx<T> av = u[q], bv = u[PY - q];
+            u[q] = mk(av.x - bv.y, av.y + bv.x);
+            u[PY - q] = mk(av.x + bv.y, bv.x - av.y);
+        }
+        __syncthreads();
+    }
+    for (int r = wp; r < RC; r += nw) WarpFFT<T, true, PY, 1>::run(Y.at(r * PY), 1, a.twy, false, true);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < RC * ny; idx += blockDim.x) {
+        const int r = idx >> lgny, y = idx & (ny - 1);
+        S[idx] = Y[r * PY + y];
+    }
+}
+
 // ------------------------------------------------------------------ stages
 // Field and torque constants in the arithmetic type of the stage kernel,
 // converted once on the host.
@@ -1879,6 +2043,24 @@ template <typename T> const void *zmr_fn(int L)
     return nullptr;
 }
 
+// cluster-fused y-z pass: rows per CTA, shared memory and threads
+int yzc_rows(const mmx_ctx *c, int C) { return 3 * c->nz / C; }
+size_t yzc_smem(const mmx_ctx *c, int C, int W)
+{
+    return padded_words((size_t)yzc_rows(c, C) * c->Py) * sizeof(cx<float>) + (size_t)3 * c->Pz * W * sizeof(cx<float>);
+}
+int yzc_threads(int W) { return std::max(32, (3 * W + 31) / 32 * 32); }
+template <int PY> const void *yzc_fn_z(int Pz)
+{
+    switch (Pz) {
+    case 4: return (const void *)k_yzc<float, PY, 4>;
+    case 8: return (const void *)k_yzc<float, PY, 8>;
+    case 16: return (const void *)k_yzc<float, PY, 16>;
+    case 32: return (const void *)k_yzc<float, PY, 32>;
+    }
+    return nullptr;
+}
+
 template <typename T> const void *zm_fn(int L)
 {
     switch (L) { MMX_LEN_CASES(k_zm, T) }
@@ -1948,6 +2130,40 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
             c->prof_n[cls]++;
         }
     };
+    // cluster-fused y-z pass: one cluster of yzc_C CTAs per kx column
+    auto launch_yzc = [&]() {
+        SplitArgs<T> za{};
+        za.S = (cx<T> *)c->S;
+        za.K = (const T *)c->K;
+        za.twy = (const cx<T> *)c->twy;
+        za.twz = (const cx<T> *)c->twz;
+        za.st = const_cast<DevState *>(st);
+        za.rows = c->rows;
+        za.nx = c->nx;
+        za.ny = c->ny;
+        za.nz = c->nz;
+        za.Py = c->Py;
+        za.Pz = c->Pz;
+        za.Hy = c->Hy;
+        za.Hz = c->Hz;
+        za.stage0 = stage0;
+        za.ry = yzc_rows(c, c->yzc_C);
+        za.W = c->yzc_W;
+        void *zargs[] = {(void *)&za};
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)(c->nx * c->yzc_C));
+        cfg.blockDim = dim3((unsigned)yzc_threads(c->yzc_W));
+        cfg.dynamicSmemBytes = yzc_smem(c, c->yzc_C, c->yzc_W);
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)c->yzc_C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelExC(&cfg, mmxk_yzc_kernel(c->Py, c->Pz), zargs);
+    };
     const int xt = x_threads<T>(c, trows);
     void *xargs[] = {(void *)&xa};
     void *yargs[] = {(void *)&ya};
@@ -1987,6 +2203,10 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
             cudaLaunchKernel(f_xf, dim3(persistent_grid(f_xf, txf, s_xf, n_x)), dim3(txf), xfa, s_xf, s);
         });
         timed(1, [&] {
+            if (c->cluster) {
+                launch_yzc();
+                return;
+            }
             cudaLaunchKernel(f_yf, dim3(persistent_grid(f_yf, tyy, s_yf, n_y)), dim3(tyy), sargs, s_yf, s);
             if (c->Pz <= zmr_max<T>()) {
                 SplitArgs<T> sr = sa;
@@ -2006,7 +2226,9 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
         return;
     }
     timed(0, [&] { cudaLaunchKernel(mmxk_kernel(K_XF, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s); });
-    if (!c->split) {
+    if (c->cluster) {
+        timed(1, launch_yzc);
+    } else if (!c->split) {
         timed(1, [&] { cudaLaunchKernel(mmxk_kernel(K_YZ, sizeof(T) == 8, c->Py), dim3(c->nx), dim3(YZ_THREADS), yargs, ys, s); });
     } else {
         SplitArgs<T> sa{};

@@ -212,7 +212,7 @@ int kernels_per_attempt(const mmx_ctx *c, int prime)
 {
     const int p = c->ctl.p;
     const int extrap = (p >= 0 && !prime);
-    const int nd = c->split ? 5 : 3;  // kernels per demag evaluation
+    const int nd = c->nd;  // kernels per demag evaluation
     return extrap ? nd + c->tab.s : (nd + 1) * c->tab.s;
 }
 
@@ -345,10 +345,23 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     c->Hz = c->Pz / 2 + 1;
     c->rows = 3LL * c->ny * c->nz;
     c->use_graphs = getenv("MMX_NO_GRAPH") == nullptr;
-    // fused y-z pass while one column fits comfortably in one CTA, else split
-    c->split = mmxk_yz_smem_bytes(c) > 160 * 1024 || getenv("MMX_FORCE_SPLIT") != nullptr;
-    if (c->Py < 2) c->split = false;
-    if (mmxk_x_smem_bytes(c) > 227 * 1024 || (c->split && mmxk_split_smem_bytes(c) > 227 * 1024) ||
+    // fused y-z pass while one column fits comfortably in one CTA; else one
+    // thread-block cluster per column where that applies, else split passes
+    // (MMX_FORCE_SPLIT / MMX_FORCE_CLUSTER force either for testing)
+    const bool big = mmxk_yz_smem_bytes(c) > 160 * 1024;
+    const bool force_split = getenv("MMX_FORCE_SPLIT") != nullptr;
+    const bool force_cluster = getenv("MMX_FORCE_CLUSTER") != nullptr && !force_split;
+    c->split = (big || force_split || force_cluster) && c->Py >= 2;
+    c->cluster = false;
+    if (c->split && !force_split && mmxk_cluster_plan(c) != 0) {
+        cudaGetLastError();
+        g_create_err = "cluster set-up failed";
+        delete c;
+        return MMX_ERR_CUDA;
+    }
+    if (force_cluster && !c->cluster) c->split = big && c->Py >= 2;
+    c->nd = (c->split && !c->cluster) ? 5 : 3;
+    if (mmxk_x_smem_bytes(c) > 227 * 1024 || (c->split && !c->cluster && mmxk_split_smem_bytes(c) > 227 * 1024) ||
         (!c->split && mmxk_yz_smem_bytes(c) > 227 * 1024)) {
         g_create_err = "mesh too large for the FFT passes";
         delete c;
@@ -423,7 +436,7 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     ok = ok && alloc(&c->m[0], fb) && alloc(&c->m[1], fb) && alloc(&c->Y[0], fb) && alloc(&c->Y[1], fb);
     ok = ok && alloc(&c->F, fb * md.s) && alloc(&c->G, fb) && alloc(&c->hist, fb * nh);
     ok = ok && alloc(&c->S, (size_t)c->rows * c->nx * 2 * c->esz);
-    if (c->split) ok = ok && alloc(&c->Tb, (size_t)c->nx * 3 * c->nz * c->Py * 2 * c->esz);
+    if (c->split && !c->cluster) ok = ok && alloc(&c->Tb, (size_t)c->nx * 3 * c->nz * c->Py * 2 * c->esz);
     ok = ok && alloc(&c->K, Kspec.size() * c->esz);
     ok = ok && alloc(&c->twx, (size_t)c->Px * 2 * c->esz) && alloc(&c->twy, (size_t)c->Py * 2 * c->esz) &&
          alloc(&c->twz, (size_t)c->Pz * 2 * c->esz);

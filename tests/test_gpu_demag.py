@@ -128,3 +128,50 @@ def test_live_contexts_of_one_length_keep_their_shared_memory():
     finally:
         big.close()
         small.close()
+
+
+CLUSTER_SHAPES = [((16, 64, 4), (2e-9, 2e-9, 1e-9)), ((4, 64, 2), (1e-9, 3e-9, 2e-9)),
+                  ((8, 128, 16), (2e-9, 2e-9, 2e-9)), ((2, 256, 8), (1e-9, 1e-9, 1e-9)),
+                  ((32, 64, 8), (3e-9, 2e-9, 1e-9))]
+
+
+def _launches_of_one_demag(n, d, m, prec):
+    torch = pytest.importorskip("torch")
+    from gpu_util import gpu_context
+    ctx = gpu_context({"n": n, "d": d}, MAT, {}, {"method": "RK4", "h": 1e-13}, prec)
+    try:
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        m_t = torch.from_numpy(np.ascontiguousarray(m)).to("cuda", dt)
+        H_t = torch.empty_like(m_t)
+        before = ctx.stats()["kernel_launches"]
+        ctx.demag(m_t, H_t)
+        torch.cuda.synchronize()
+        return H_t.double().cpu().numpy(), ctx.stats()["kernel_launches"] - before
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("n,d", CLUSTER_SHAPES)
+def test_cluster_yz_path_matches_oracle(n, d, monkeypatch):
+    """The thread-block-cluster y-z pass (one cluster per kx column, the y
+    spectrum exchanged through distributed shared memory), forced on meshes
+    small enough for the oracle: XF, YZC, XI = three launches."""
+    monkeypatch.setenv("MMX_FORCE_CLUSTER", "1")
+    m = W.m_random(n, seed=sum(n) + 11)
+    ref = O.demag_fft(O.newell_octant(*n, *d), MAT["Ms"], m)
+    got, launches = _launches_of_one_demag(n, d, m, "fp32")
+    assert launches == 3
+    assert rel_max(got, ref) < 1e-5
+
+
+def test_cluster_path_is_taken_naturally_and_matches_oracle():
+    """16 x 128 x 16: the y-z column (256 x 32 x 3 complex words, 221 KB)
+    does not fit one CTA; in FP32 a cluster of CTAs runs it (three launches,
+    no y-spectrum buffer), in FP64 the split passes do (five launches)."""
+    n, d = (16, 128, 16), (2e-9, 2e-9, 2e-9)
+    m = W.m_vortex(n, d, seed=2)
+    ref = O.demag_fft(O.newell_octant(*n, *d), MAT["Ms"], m)
+    got, launches = _launches_of_one_demag(n, d, m, "fp32")
+    assert launches == 3 and rel_max(got, ref) < 1e-5
+    got, launches = _launches_of_one_demag(n, d, m, "fp64")
+    assert launches == 5 and rel_max(got, ref) < 1e-12
