@@ -69,6 +69,34 @@ template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b)
 }
 template <typename T> __device__ __forceinline__ cx<T> cscale(T s, cx<T> a) { return mk(s * a.x, s * a.y); }
 
+// Twiddles w^r, r = 1..R-1, of one radix-R butterfly.  FP64 reads each from
+// the table; FP32 reads w^1 only and forms the powers by complex products
+// (at most three deep, a few ulp): the table reads of a warp hit scattered
+// addresses and cost one L1 wavefront each, the products cost FMAs.
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void twiddle_row(const cx<T> *__restrict__ tw, int k, int tstride, cx<T> (&w)[R])
+{
+    if constexpr (sizeof(T) == 4 && R >= 4) {
+        cx<T> w1 = tw[k * tstride];
+        if (INV) w1.y = -w1.y;
+        w[1] = w1;
+        w[2] = cmul(w1, w1);
+        w[3] = cmul(w[2], w1);
+        if constexpr (R == 8) {
+            w[4] = cmul(w[2], w[2]);
+            w[5] = cmul(w[4], w1);
+            w[6] = cmul(w[3], w[3]);
+            w[7] = cmul(w[4], w[3]);
+        }
+    } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            w[r] = tw[r * k * tstride];
+            if (INV) w[r].y = -w[r].y;
+        }
+    }
+}
+
 // Shared-memory view with one padding word per 8 complex words: the
 // stride-R stores of the early Stockham stages then spread over all banks.
 template <typename T> struct Pad {
@@ -194,12 +222,10 @@ __device__ __forceinline__ void fft_stage(const SRC src, const Pad<T> buf, const
             if (off[it] < 0) continue;
             const int j = jj[it], k = j & (Ns - 1);
             if (Ns > 1) {
+                cx<T> w[R];
+                twiddle_row<T, R, INV>(tw, k, tstride, w);
 #pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    cx<T> w = tw[r * k * tstride];
-                    if (INV) w.y = -w.y;
-                    v[it][r] = cmul(v[it][r], w);
-                }
+                for (int r = 1; r < R; ++r) v[it][r] = cmul(v[it][r], w[r]);
             }
             Dft<T, R, INV>::run(v[it]);
             const int d = (j - k) * R + k;
@@ -281,12 +307,10 @@ __device__ __forceinline__ void warp_stage(const SRC src, const DST buf, int L, 
         if (j >= per) continue;
         const int k = j & (Ns - 1);
         if (Ns > 1) {
+            cx<T> w[R];
+            twiddle_row<T, R, INV>(tw, k, tstride, w);
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                cx<T> w = tw[r * k * tstride];
-                if (INV) w.y = -w.y;
-                v[it][r] = cmul(v[it][r], w);
-            }
+            for (int r = 1; r < R; ++r) v[it][r] = cmul(v[it][r], w[r]);
         }
         Dft<T, R, INV>::run(v[it]);
         const int d = (j - k) * R + k;
@@ -1389,6 +1413,7 @@ __global__ void __launch_bounds__(192, 2) k_yzc(const SplitArgs<T> a)
             for (int kz = 0; kz < PZ; ++kz) B[c * plane + kz * W + ww] = v[kz];
         }
         __syncthreads();
+#pragma unroll 4
         for (int q = threadIdx.x; q < plane; q += blockDim.x) {
             const int qw = q & (W - 1), kz = q >> lgW, sl = s0 + qw;
             if (kx != 0 || (sl != 0 && sl != half)) {
