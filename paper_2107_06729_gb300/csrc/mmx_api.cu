@@ -345,15 +345,16 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     c->Hz = c->Pz / 2 + 1;
     c->rows = 3LL * c->ny * c->nz;
     c->use_graphs = getenv("MMX_NO_GRAPH") == nullptr;
-    // fused y-z pass while one column fits comfortably in one CTA; else one
-    // thread-block cluster per column where that applies, else split passes
-    // (MMX_FORCE_SPLIT / MMX_FORCE_CLUSTER force either for testing)
+    // fused y-z pass while one column fits comfortably in one CTA, else the
+    // split passes; MMX_FORCE_SPLIT forces the split passes, MMX_FORCE_CLUSTER
+    // the thread-block-cluster pass where it applies (on GB300 it measures
+    // slower than the split passes at 512 x 512 x 16, so it is not the default)
     const bool big = mmxk_yz_smem_bytes(c) > 160 * 1024;
     const bool force_split = getenv("MMX_FORCE_SPLIT") != nullptr;
     const bool force_cluster = getenv("MMX_FORCE_CLUSTER") != nullptr && !force_split;
     c->split = (big || force_split || force_cluster) && c->Py >= 2;
     c->cluster = false;
-    if (c->split && !force_split && mmxk_cluster_plan(c) != 0) {
+    if (c->split && force_cluster && mmxk_cluster_plan(c) != 0) {
         cudaGetLastError();
         g_create_err = "cluster set-up failed";
         delete c;

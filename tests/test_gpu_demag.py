@@ -164,14 +164,17 @@ def test_cluster_yz_path_matches_oracle(n, d, monkeypatch):
     assert rel_max(got, ref) < 1e-5
 
 
-def test_cluster_path_is_taken_naturally_and_matches_oracle():
+def test_large_column_fp32_split_and_cluster_paths_match_oracle(monkeypatch):
     """16 x 128 x 16: the y-z column (256 x 32 x 3 complex words, 221 KB)
-    does not fit one CTA; in FP32 a cluster of CTAs runs it (three launches,
-    no y-spectrum buffer), in FP64 the split passes do (five launches)."""
+    does not fit one CTA.  By default the split passes run it (five
+    launches); forced, one thread-block cluster per kx column (three)."""
     n, d = (16, 128, 16), (2e-9, 2e-9, 2e-9)
     m = W.m_vortex(n, d, seed=2)
     ref = O.demag_fft(O.newell_octant(*n, *d), MAT["Ms"], m)
     got, launches = _launches_of_one_demag(n, d, m, "fp32")
-    assert launches == 3 and rel_max(got, ref) < 1e-5
+    assert launches == 5 and rel_max(got, ref) < 1e-5
     got, launches = _launches_of_one_demag(n, d, m, "fp64")
     assert launches == 5 and rel_max(got, ref) < 1e-12
+    monkeypatch.setenv("MMX_FORCE_CLUSTER", "1")
+    got, launches = _launches_of_one_demag(n, d, m, "fp32")
+    assert launches == 3 and rel_max(got, ref) < 1e-5
