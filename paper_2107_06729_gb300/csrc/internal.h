@@ -1,6 +1,7 @@
 // internal.h -- definitions shared by the host and device parts of libmmx.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
@@ -43,6 +44,7 @@ struct DevState {
     int status;
     int clipped;     // current attempt lands exactly on t_end
     int loop_more;   // last value handed to the graph's while condition
+    int fault;       // a bounded device wait gave up (the context is unusable)
     long long accepted, rejected, exact_evals, extrap_evals, forced, attempts;
     long long acc_target;     // stop when accepted reaches this
     long long attempt_limit;  // attempts allowed in the current run
@@ -107,6 +109,9 @@ struct mmx_ctx {
     bool cluster;     // ... and a thread-block cluster per kx column runs it instead (YZC)
     int yzc_C, yzc_W; // cluster size and z sub-tile width of YZC
     int nd;           // kernels per exact demag evaluation
+    bool allow_tma;   // TMA passes allowed (the context owns a fault word)
+    bool xi_tma;      // XI runs with TMA tile loads
+    CUtensorMap xi_tmap;  // the x spectrum S as [nx][rows] 8-byte words
     DevState *st;
     DevState *h_st;  // pinned host mirror
     // graphs: [0] main loop, [1] priming loop

@@ -28,7 +28,9 @@
 // last stage forms the propagated and embedded solutions, renormalises,
 // reduces the error norm, and its last CTA runs the controller of Eq. 5.
 #include <cooperative_groups.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <stdio.h>
 
@@ -42,7 +44,7 @@
 #include "internal.h"
 
 // kernel families, instantiated in separate translation units
-enum MmxKernelKind { K_XF, K_XI, K_YZ, K_YF, K_YI, K_ZM, K_XFP, K_YFP, K_YIP, K_ZMP, K_ZMR };
+enum MmxKernelKind { K_XF, K_XI, K_YZ, K_YF, K_YI, K_ZM, K_XFP, K_YFP, K_YIP, K_ZMP, K_ZMR, K_XIT };
 // pointer to the instance of `kind` for precision (f64) and transform length L
 const void *mmxk_kernel(int kind, bool f64, int L);
 // the cluster-fused y-z pass (FP32) for lengths Py and Pz, or NULL
@@ -462,6 +464,7 @@ template <typename T> struct XArgs {
     long long rows, n;
     int nx, trows, stage0, src_mode, dst_mode, plane;  // plane = ny*nz
     double msN00[3];
+    int *fault;          // set when a bounded device wait gives up (TMA passes)
 };
 
 constexpr int X_THREADS = 128;
@@ -581,6 +584,166 @@ __global__ void __launch_bounds__(256, 2) k_xi(const XArgs<T> a)
             v -= (T)a.msN00[c] * a.self_src[r * nx + x];
         }
         out[r * nx + x] = v;
+    }
+    if (a.st && blockIdx.x == 0 && threadIdx.x == 0) a.st->exact_evals++;
+}
+
+// ------------------------------------------------- XI with TMA tile loads
+// The x spectrum S[kx][row] is read by XI across all kx for a tile of 16
+// consecutive rows: 128-byte pieces 8 * rows bytes apart.  Here a persistent
+// CTA loads whole tiles with tensor-memory-access copies (one 2-D box of
+// 16 rows x up to 256 kx per instruction, completion counted on an
+// mbarrier), two tiles in flight, while its warps transform the previous
+// tile.  Waits are bounded in time: on expiry the kernel sets *fault, waits
+// (bounded) for its own copies in flight and returns.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *m, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *m, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase with the given parity; false after ~limit_ns
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, unsigned parity, unsigned long long limit_ns)
+{
+    unsigned long long t0 = 0;
+    for (unsigned i = 0;; ++i) {
+        if (mbar_try_wait(m, parity)) return true;
+        if ((i & 255) == 0) {
+            unsigned long long t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > limit_ns) return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *m)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(tm), "r"(x), "r"(y), "r"(smem_u32(m))
+        : "memory");
+}
+
+constexpr int XIT_ROWS = 16;
+constexpr unsigned long long XIT_WAIT_NS = 2000000000ULL;  // 2 s
+
+template <typename T, int PX>
+__global__ void __launch_bounds__(256) k_xi_t(const XArgs<T> a, const __grid_constant__ CUtensorMap tm)
+{
+    static_assert(sizeof(T) == 4, "TMA XI: FP32 spectrum (8-byte elements)");
+    extern __shared__ __align__(1024) unsigned char smtma[];
+    int head = 0;
+    if (a.st) {
+        if (a.st->done) return;
+        if (a.stage0 && a.st->f1_valid) return;
+        head = a.st->head;
+    }
+    constexpr int NX = PX / 2, TR = XIT_ROWS, NP = TR / 2, PXS = PX + 8;
+    constexpr int BK = NX < 256 ? NX : 256, NB = NX / BK;
+    constexpr unsigned TILE_BYTES = (unsigned)NX * TR * sizeof(cx<T>);
+    // layout: two staging tiles, the padded pair rows, two mbarriers
+    cx<T> *const stg0 = reinterpret_cast<cx<T> *>(smtma);  // tile b at stg0 + b * NX * TR
+    const Pad<T> work{reinterpret_cast<cx<T> *>(smtma) + 2 * NX * TR, 0};
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(reinterpret_cast<cx<T> *>(smtma) + 2 * NX * TR +
+                                                  padded_words((size_t)NP * PXS));
+    if (smem_u32(smtma) & 127) {  // tile copies need 128-byte aligned destinations
+        if (threadIdx.x == 0 && a.fault) atomicExch(a.fault, 2);
+        return;
+    }
+    const long long R = a.rows;
+    const int ntiles = (int)(R / TR);
+    const int nx = a.nx, lgnx = ilog2(nx);
+    T *out = a.dst_mode == 1 ? a.hist + (size_t)head * 3 * a.n : a.dst;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int b, int tile) {
+        mbar_expect_tx(&mbar[b], TILE_BYTES);
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            tma_load_2d(stg0 + (size_t)b * NX * TR + (size_t)j * BK * TR, &tm, tile * TR, j * BK, &mbar[b]);
+    };
+    if (threadIdx.x == 0) {
+        if ((int)blockIdx.x < ntiles) issue(0, blockIdx.x);
+        if ((int)(blockIdx.x + gridDim.x) < ntiles) issue(1, blockIdx.x + gridDim.x);
+    }
+    // bit b: a copy into tile b is in flight / the parity tile b waits for
+    unsigned pend = ((int)blockIdx.x < ntiles ? 1u : 0u) | ((int)(blockIdx.x + gridDim.x) < ntiles ? 2u : 0u);
+    unsigned phase = 0;
+    bool failed = false;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int b = it & 1;
+        const bool ok = mbar_wait_bounded(&mbar[b], (phase >> b) & 1u, XIT_WAIT_NS);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        phase ^= 1u << b;
+        pend &= ~(1u << b);
+        // unpack the tile [kx][16 rows] into 8 complex pair rows (Hermitian
+        // halves of two real rows), as k_xi does from global memory
+        const cx<T> *g = stg0 + (size_t)b * NX * TR;
+        for (int idx = threadIdx.x; idx < NP * NX; idx += blockDim.x) {
+            const int k = idx / NP, p = idx - k * NP;
+            const cx<T> va = g[k * TR + 2 * p], vb = g[k * TR + 2 * p + 1];
+            const Pad<T> z = work.at(p * PXS);
+            if (k == 0) {
+                z[0] = mk(va.x, vb.x);
+                z[NX] = mk(va.y, vb.y);
+            } else {
+                z[k] = mk(va.x - vb.y, va.y + vb.x);
+                z[PX - k] = mk(va.x + vb.y, vb.x - va.y);
+            }
+        }
+        __syncthreads();  // staging b consumed: refill it with the tile after next
+        const int nxt = tile + 2 * (int)gridDim.x;
+        if (nxt < ntiles) {
+            if (threadIdx.x == 0) issue(b, nxt);
+            pend |= 1u << b;
+        }
+        const int w = threadIdx.x >> 5;
+        if (w < NP) WarpFFT<T, true, PX, 1>::run(work.at(w * PXS), 1, a.tw, false, true);
+        __syncthreads();
+        const long long r0 = (long long)tile * TR;
+        for (int idx = threadIdx.x; idx < TR * nx; idx += blockDim.x) {
+            const int t = idx >> lgnx, x = idx & (nx - 1);
+            const long long r = r0 + t;
+            const cx<T> z = work[(t >> 1) * PXS + x];
+            T v = (t & 1) ? z.y : z.x;
+            if (a.self_src) {
+                const int c = (int)(r / a.plane);
+                v -= (T)a.msN00[c] * a.self_src[r * nx + x];
+            }
+            out[r * nx + x] = v;
+        }
+        __syncthreads();  // work is refilled by the next tile
+    }
+    if (failed) {
+        if (threadIdx.x == 0 && a.fault) atomicExch(a.fault, 1);
+        // let copies still in flight land before the CTA's memory goes away
+        for (int b = 0; b < 2; ++b)
+            if ((pend >> b) & 1u) (void)mbar_wait_bounded(&mbar[b], (phase >> b) & 1u, XIT_WAIT_NS);
+        return;
     }
     if (a.st && blockIdx.x == 0 && threadIdx.x == 0) a.st->exact_evals++;
 }
@@ -1976,6 +2139,48 @@ template <typename T> const void *yf_fn(int L)
     case 512: if constexpr (warp_max_len<T>() >= 512) return (const void *)K<T, 512>; else return nullptr; \
     case 1024: if constexpr (warp_max_len<T>() >= 1024) return (const void *)K<T, 1024>; else return nullptr;
 
+template <typename T> const void *xit_fn(int L)
+{
+    if constexpr (sizeof(T) == 4) {
+        switch (L) {
+        case 64: return (const void *)k_xi_t<T, 64>;
+        case 128: return (const void *)k_xi_t<T, 128>;
+        case 256: return (const void *)k_xi_t<T, 256>;
+        case 512: return (const void *)k_xi_t<T, 512>;
+        case 1024: return (const void *)k_xi_t<T, 1024>;
+        }
+    }
+    return nullptr;
+}
+// TMA XI: two staging tiles of nx x 16 complex words and the padded pair rows
+size_t xit_smem(const mmx_ctx *c)
+{
+    return (size_t)2 * c->nx * XIT_ROWS * sizeof(cx<float>) +
+           padded_words((size_t)(XIT_ROWS / 2) * (c->Px + 8)) * sizeof(cx<float>) + 2 * sizeof(uint64_t);
+}
+// tensor map of the x spectrum S as [nx][rows] 8-byte words, box 16 x min(nx, 256)
+bool encode_xi_tmap(mmx_ctx *c)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+    if (!enc) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return false;
+        }
+        enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)c->rows, (cuuint64_t)c->nx};
+    const cuuint64_t strides[1] = {(cuuint64_t)c->rows * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)XIT_ROWS, (cuuint32_t)std::min(c->nx, 256)};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(&c->xi_tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, c->S, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 template <typename T> const void *xfp_fn(int L)
 {
     switch (L) { MMX_PIPE_CASES(k_xf_p, T) }
@@ -2121,6 +2326,7 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
     xa.dst_mode = dst_mode;
     xa.plane = c->ny * c->nz;
     for (int i = 0; i < 3; ++i) xa.msN00[i] = c->ph.msN00[i];
+    xa.fault = c->xi_tma ? &c->st->fault : nullptr;
     const int xgrid = (int)((c->rows + trows - 1) / trows);
     const size_t xs = x_smem<T>(c, trows);
 
@@ -2191,6 +2397,17 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
     };
     const int xt = x_threads<T>(c, trows);
     void *xargs[] = {(void *)&xa};
+    // XI: TMA tiles through a persistent CTA per SM where set up, else plain
+    auto launch_xi = [&]() {
+        if (c->xi_tma) {
+            const void *f = mmxk_kernel(K_XIT, false, c->Px);
+            const size_t sm = xit_smem(c);
+            void *targs[] = {(void *)&xa, (void *)&c->xi_tmap};
+            cudaLaunchKernel(f, dim3(persistent_grid(f, 256, sm, c->rows / XIT_ROWS)), dim3(256), targs, sm, s);
+        } else {
+            cudaLaunchKernel(mmxk_kernel(K_XI, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s);
+        }
+    };
     void *yargs[] = {(void *)&ya};
     const void *xsrc = src_mode == 1 ? c->m[0] : src;
     if (pipe_ok<T>(c) && ((uintptr_t)xsrc & 15) == 0 && ((uintptr_t)c->m[1] & 15) == 0) {
@@ -2247,7 +2464,7 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
             cudaLaunchKernel(f_yi, dim3(persistent_grid(f_yi, tyy, s_yi, n_y)), dim3(tyy), sargs, s_yi, s);
             c->launches += 2;
         });
-        timed(2, [&] { cudaLaunchKernel(mmxk_kernel(K_XI, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s); });
+        timed(2, launch_xi);
         return;
     }
     timed(0, [&] { cudaLaunchKernel(mmxk_kernel(K_XF, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s); });
@@ -2286,7 +2503,7 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
             c->launches += 2;
         });
     }
-    timed(2, [&] { cudaLaunchKernel(mmxk_kernel(K_XI, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s); });
+    timed(2, launch_xi);
 }
 
 template <typename T>
@@ -2384,6 +2601,12 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
     if (cudaMemcpy(c->twy, tw.data(), c->Py * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
     twiddles<T>(c->Pz, tw);
     if (cudaMemcpy(c->twz, tw.data(), c->Pz * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
+    c->xi_tma = false;
+    if (sizeof(T) == 4 && c->allow_tma && c->rows % XIT_ROWS == 0 && mmxk_kernel(K_XIT, false, c->Px) &&
+        xit_smem(c) <= 227 * 1024 && getenv("MMX_NO_TMA") == nullptr) {
+        if (encode_xi_tmap(c) && raise_smem_limit(mmxk_kernel(K_XIT, false, c->Px), xit_smem(c))) c->xi_tma = true;
+        cudaGetLastError();
+    }
     const int trows = pick_trows(c);
     const size_t xs = x_smem<T>(c, trows), ys = yz_smem<T>(c);
     const void *xk[] = {mmxk_kernel(K_XF, sizeof(T) == 8, c->Px), mmxk_kernel(K_XI, sizeof(T) == 8, c->Px)};

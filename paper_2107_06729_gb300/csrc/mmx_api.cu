@@ -173,6 +173,7 @@ int read_state(mmx_ctx *c)
 {
     CK(cudaStreamSynchronize(c->stream));
     CK(cudaMemcpy(c->h_st, c->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    if (c->h_st->fault) return fail(c, MMX_ERR_CUDA, "a bounded device wait gave up (TMA copy not completed)");
     return 0;
 }
 
@@ -362,6 +363,7 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     }
     if (force_cluster && !c->cluster) c->split = big && c->Py >= 2;
     c->nd = (c->split && !c->cluster) ? 5 : 3;
+    c->allow_tma = true;
     if (mmxk_x_smem_bytes(c) > 227 * 1024 || (c->split && !c->cluster && mmxk_split_smem_bytes(c) > 227 * 1024) ||
         (!c->split && mmxk_yz_smem_bytes(c) > 227 * 1024)) {
         g_create_err = "mesh too large for the FFT passes";
@@ -920,7 +922,11 @@ int mmx_batch_run(mmx_batch *b, const double *t_end, int *status)
         int r = MMX_OK;
         if (b->active[i]) {
             c->launches += pa * kernels_per_attempt(c, 1) + (s.run_attempts - pa) * kernels_per_attempt(c, c->ctl.p < 0);
-            r = s.done ? end_status(c, b->forced0[i]) : fail(c, MMX_ERR_STATE, "batched loops stopped before the run finished");
+            if (s.fault)
+                r = fail(c, MMX_ERR_CUDA, "a bounded device wait gave up (TMA copy not completed)");
+            else
+                r = s.done ? end_status(c, b->forced0[i])
+                           : fail(c, MMX_ERR_STATE, "batched loops stopped before the run finished");
         }
         if (status) status[i] = r;
         rc_all = combine(rc_all, r);
