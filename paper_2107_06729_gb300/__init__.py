@@ -63,6 +63,12 @@ class mmx_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong)]
 
 
+class mmx_plan(ctypes.Structure):
+    _fields_ = [("yz_pass", ctypes.c_int), ("x_rows", ctypes.c_int), ("xi_tma", ctypes.c_int),
+                ("cluster_ctas", ctypes.c_int), ("tuned", ctypes.c_int), ("kernels_per_demag", ctypes.c_int),
+                ("demag_us", ctypes.c_double)]
+
+
 # every entry point declared in include/mmx.h, with its C signature
 _VP = ctypes.c_void_p
 SIGNATURES = {
@@ -80,6 +86,7 @@ SIGNATURES = {
     "mmx_load_state": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "mmx_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int]),
     "mmx_get_profile": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    "mmx_get_plan": (ctypes.c_int, [_VP, ctypes.POINTER(mmx_plan)]),
     "mmx_demag_static": (ctypes.c_int, [ctypes.POINTER(mmx_mesh), ctypes.c_double, ctypes.c_int, _VP, _VP, _VP]),
     "mmx_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_VP), _VP, ctypes.POINTER(_VP)]),
     "mmx_batch_run": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
@@ -196,6 +203,12 @@ def mmx_get_profile(ctx):
     n = (ctypes.c_longlong * MMX_NPROF)()
     _check(lib().mmx_get_profile(ctx, ms, n), ctx)
     return {PROFILE_CLASSES[i]: (ms[i], n[i]) for i in range(MMX_NPROF)}
+
+
+def mmx_get_plan(ctx):
+    p = mmx_plan()
+    _check(lib().mmx_get_plan(ctx, ctypes.byref(p)), ctx)
+    return {k: getattr(p, k) for k, _ in mmx_plan._fields_}
 
 
 def mmx_demag_static(mesh, Ms, precision, m_dev, H_dev, cuda_stream=None):
@@ -324,6 +337,9 @@ class Context:
 
     def set_profiling(self, on):
         return mmx_set_profiling(self.handle, on)
+
+    def plan(self):
+        return mmx_get_plan(self.handle)
 
     def profile(self):
         return mmx_get_profile(self.handle)

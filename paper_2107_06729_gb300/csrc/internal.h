@@ -110,7 +110,11 @@ struct mmx_ctx {
     int yzc_C, yzc_W; // cluster size and z sub-tile width of YZC
     int nd;           // kernels per exact demag evaluation
     bool allow_tma;   // TMA passes allowed (the context owns a fault word)
+    bool xi_tma_ok;   // the TMA XI is set up for this mesh
     bool xi_tma;      // XI runs with TMA tile loads
+    int trows;        // rows per CTA of the plain x passes
+    bool tuned;       // pass configuration chosen by timing (autotuner)
+    double demag_us;  // timed exact evaluation of the chosen configuration
     CUtensorMap xi_tmap;  // the x spectrum S as [nx][rows] 8-byte words
     DevState *st;
     DevState *h_st;  // pinned host mirror
@@ -139,6 +143,10 @@ void mmxk_demag(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int 
                 const void *src, int dst_mode, void *dst, const void *self_src);
 void mmxk_stage(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime_graph,
                 cudaGraphConditionalHandle cond, int use_cond);
+// rows per CTA of the plain x passes: the default, and setting a candidate
+// (raises the kernels' shared-memory limit; MMX_ERR_ARG if it does not fit)
+int mmxk_default_trows(const mmx_ctx *c);
+int mmxk_set_trows(mmx_ctx *c, int trows);
 // decides whether the cluster-fused y-z pass runs a split-size mesh (sets
 // cluster, yzc_C, yzc_W); 0 or MMX_ERR_CUDA
 int mmxk_cluster_plan(mmx_ctx *c);

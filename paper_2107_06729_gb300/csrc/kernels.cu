@@ -68,6 +68,20 @@ int mmxk_add_gate_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t nd, mm
     return add_kernel_node(g, deps, nd, (const void *)k_gate, dim3(1), dim3(1), args, out);
 }
 
+int mmxk_default_trows(const mmx_ctx *c) { return pick_trows(c); }
+
+int mmxk_set_trows(mmx_ctx *c, int tr)
+{
+    const bool f64 = c->prec == MMX_FP64;
+    const size_t xs = f64 ? x_smem<double>(c, tr) : x_smem<float>(c, tr);
+    if (tr < 1 || tr > 16 || xs > 200 * 1024) return MMX_ERR_ARG;
+    if (xs > 48 * 1024)
+        for (int kind : {(int)K_XF, (int)K_XI})
+            if (!raise_smem_limit(mmxk_kernel(kind, f64, c->Px), xs)) return MMX_ERR_CUDA;
+    c->trows = tr;
+    return 0;
+}
+
 int mmxk_cluster_plan(mmx_ctx *c)
 {
     c->cluster = false;
@@ -123,7 +137,8 @@ size_t mmxk_yz_smem_bytes(const mmx_ctx *c)
 }
 size_t mmxk_x_smem_bytes(const mmx_ctx *c)
 {
-    return c->prec == MMX_FP64 ? x_smem<double>(c, pick_trows(c)) : x_smem<float>(c, pick_trows(c));
+    const int tr = c->trows ? c->trows : pick_trows(c);
+    return c->prec == MMX_FP64 ? x_smem<double>(c, tr) : x_smem<float>(c, tr);
 }
 
 int mmxk_setup_buffers(mmx_ctx *c, const double *Kspec_host)

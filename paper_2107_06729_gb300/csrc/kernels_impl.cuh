@@ -2306,7 +2306,7 @@ template <typename T>
 void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src_mode, const void *src, int dst_mode,
              void *dst, const void *self_src)
 {
-    const int trows = pick_trows(c);
+    const int trows = c->trows ? c->trows : pick_trows(c);
     XArgs<T> xa{};
     xa.src = (const T *)src;
     xa.msrc0 = (const T *)c->m[0];
@@ -2601,13 +2601,14 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
     if (cudaMemcpy(c->twy, tw.data(), c->Py * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
     twiddles<T>(c->Pz, tw);
     if (cudaMemcpy(c->twz, tw.data(), c->Pz * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
-    c->xi_tma = false;
+    c->xi_tma = c->xi_tma_ok = false;
     if (sizeof(T) == 4 && c->allow_tma && c->rows % XIT_ROWS == 0 && mmxk_kernel(K_XIT, false, c->Px) &&
         xit_smem(c) <= 227 * 1024 && getenv("MMX_NO_TMA") == nullptr) {
-        if (encode_xi_tmap(c) && raise_smem_limit(mmxk_kernel(K_XIT, false, c->Px), xit_smem(c))) c->xi_tma = true;
+        if (encode_xi_tmap(c) && raise_smem_limit(mmxk_kernel(K_XIT, false, c->Px), xit_smem(c)))
+            c->xi_tma = c->xi_tma_ok = true;
         cudaGetLastError();
     }
-    const int trows = pick_trows(c);
+    const int trows = c->trows ? c->trows : pick_trows(c);
     const size_t xs = x_smem<T>(c, trows), ys = yz_smem<T>(c);
     const void *xk[] = {mmxk_kernel(K_XF, sizeof(T) == 8, c->Px), mmxk_kernel(K_XI, sizeof(T) == 8, c->Px)};
     if (xs > 48 * 1024)

@@ -310,6 +310,92 @@ std::shared_ptr<const std::vector<double>> tensor_for(const mmx_host_tensor_args
     return N6;
 }
 
+// ------------------------------------------------------------ autotuner
+// Pass configurations of one exact demag evaluation: rows per CTA of the
+// plain x passes, XI with TMA tile loads or plain, and for meshes whose y-z
+// column does not fit one CTA the split passes or the thread-block-cluster
+// pass.  Each candidate is timed (CUDA events, one warm-up and three
+// evaluations of the zero field on the context's own buffers) and the
+// fastest kept; results are cached per mesh and precision for the process.
+struct Plan {
+    int trows;
+    bool xi_tma, cluster;
+    double us;
+};
+struct PlanKey {
+    int nx, ny, nz, prec;
+    bool operator==(const PlanKey &o) const { return nx == o.nx && ny == o.ny && nz == o.nz && prec == o.prec; }
+};
+std::mutex g_plan_mu;
+std::vector<std::pair<PlanKey, Plan>> g_plans;
+
+double time_demag(mmx_ctx *c)
+{
+    mmxk_demag(c, c->stream, nullptr, 0, 0, c->m[0], 0, c->G, nullptr);
+    cudaEventRecord(c->ev_a, c->stream);
+    for (int i = 0; i < 3; ++i) mmxk_demag(c, c->stream, nullptr, 0, 0, c->m[0], 0, c->G, nullptr);
+    cudaEventRecord(c->ev_b, c->stream);
+    float ms = 0.f;
+    if (cudaEventSynchronize(c->ev_b) != cudaSuccess || cudaEventElapsedTime(&ms, c->ev_a, c->ev_b) != cudaSuccess) {
+        cudaGetLastError();
+        return 1e30;
+    }
+    if (cudaGetLastError() != cudaSuccess) return 1e30;
+    return 1e3 * ms / 3.0;
+}
+
+void apply_plan(mmx_ctx *c, const Plan &p)
+{
+    mmxk_set_trows(c, p.trows);
+    c->xi_tma = p.xi_tma && c->xi_tma_ok;
+    c->cluster = p.cluster && c->yzc_C > 0;
+    c->nd = (c->split && !c->cluster) ? 5 : 3;
+    c->demag_us = p.us;
+}
+
+int autotune(mmx_ctx *c)
+{
+    const PlanKey key{c->nx, c->ny, c->nz, c->prec};
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        for (const auto &e : g_plans)
+            if (e.first == key) {
+                apply_plan(c, e.second);
+                c->tuned = true;
+                return 0;
+            }
+    }
+    const long long launches = c->launches;
+    std::vector<int> rows;
+    for (int tr = 2; tr <= 16; tr *= 2)
+        if (mmxk_set_trows(c, tr) == 0) rows.push_back(tr);
+    const int tr0 = mmxk_default_trows(c);
+    if (std::find(rows.begin(), rows.end(), tr0) == rows.end()) rows.push_back(tr0);
+    // cluster candidate: sets yzc_C / yzc_W when feasible
+    bool cl_ok = false;
+    if (c->split) {
+        mmxk_cluster_plan(c);
+        cl_ok = c->cluster;
+        c->cluster = false;
+    }
+    Plan best{tr0, c->xi_tma_ok, false, 1e30};
+    for (int cl = 0; cl <= (cl_ok ? 1 : 0); ++cl)
+        for (int xt = 0; xt <= (c->xi_tma_ok ? 1 : 0); ++xt)
+            for (int tr : rows) {
+                Plan p{tr, xt == 1, cl == 1, 0};
+                apply_plan(c, p);
+                p.us = time_demag(c);
+                if (p.us < best.us) best = p;
+            }
+    apply_plan(c, best);
+    c->launches = launches;
+    c->tuned = true;
+    if (best.us >= 1e30) return MMX_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans.push_back({key, best});
+    return 0;
+}
+
 }  // namespace
 
 void mmx_set_thread_error(const char *msg) { g_create_err = msg ? msg : ""; }
@@ -364,6 +450,7 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     if (force_cluster && !c->cluster) c->split = big && c->Py >= 2;
     c->nd = (c->split && !c->cluster) ? 5 : 3;
     c->allow_tma = true;
+    c->trows = mmxk_default_trows(c);
     if (mmxk_x_smem_bytes(c) > 227 * 1024 || (c->split && !c->cluster && mmxk_split_smem_bytes(c) > 227 * 1024) ||
         (!c->split && mmxk_yz_smem_bytes(c) > 227 * 1024)) {
         g_create_err = "mesh too large for the FFT passes";
@@ -463,6 +550,22 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     cudaMemset(c->m[1], 0, fb);
     cudaMemset(c->F, 0, fb * md.s);
     cudaMemset(c->hist, 0, fb * nh);
+    // pass configuration by timing, unless forced or switched off
+    {
+        const char *at = getenv("MMX_AUTOTUNE");
+        const char *trs = getenv("MMX_TROWS");
+        const bool forced = force_split || force_cluster || getenv("MMX_NO_TMA") != nullptr || trs != nullptr;
+        if (trs) mmxk_set_trows(c, atoi(trs));
+        if (!forced && !(at && at[0] == '0') && autotune(c) != 0) {
+            g_create_err = "autotuning the demag passes failed";
+            mmx_destroy(c);
+            return MMX_ERR_CUDA;
+        }
+        if (c->cluster && c->Tb) {  // the cluster pass keeps the y spectrum on chip
+            cudaFree(c->Tb);
+            c->Tb = nullptr;
+        }
+    }
     DevState &s = *c->h_st;
     memset(&s, 0, sizeof(s));
     s.t = 0;
@@ -694,6 +797,19 @@ int mmx_get_profile(mmx_ctx *c, double *ms, long long *launches)
         ms[i] = c->prof_ms[i];
         launches[i] = c->prof_n[i];
     }
+    return MMX_OK;
+}
+
+int mmx_get_plan(const mmx_ctx *c, mmx_plan *out)
+{
+    if (!c || !out) return MMX_ERR_ARG;
+    out->yz_pass = !c->split ? 0 : (c->cluster ? 2 : 1);
+    out->x_rows = c->trows;
+    out->xi_tma = c->xi_tma ? 1 : 0;
+    out->cluster_ctas = c->cluster ? c->yzc_C : 0;
+    out->tuned = c->tuned ? 1 : 0;
+    out->demag_us = c->tuned ? c->demag_us : 0.0;
+    out->kernels_per_demag = c->nd;
     return MMX_OK;
 }
 

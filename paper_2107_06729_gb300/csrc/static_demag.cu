@@ -83,8 +83,9 @@ extern "C" int mmx_demag_static(const mmx_mesh *mesh, double Ms, int precision, 
     c.cluster = false;
     c.nd = 3;
     c.allow_tma = false;  // no device state word to report a bounded wait in
-    c.xi_tma = false;
+    c.xi_tma = c.xi_tma_ok = false;
     c.st = nullptr;
+    c.trows = mmxk_default_trows(&c);
     c.Tb = nullptr;
     if (mmxk_yz_smem_bytes(&c) > 227 * 1024 || mmxk_x_smem_bytes(&c) > 227 * 1024)
         return fail(MMX_ERR_ARG, "mesh too large for the single-CTA FFT passes");

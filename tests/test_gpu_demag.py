@@ -178,3 +178,40 @@ def test_large_column_fp32_split_and_cluster_paths_match_oracle(monkeypatch):
     monkeypatch.setenv("MMX_FORCE_CLUSTER", "1")
     got, launches = _launches_of_one_demag(n, d, m, "fp32")
     assert launches == 3 and rel_max(got, ref) < 1e-5
+
+
+@pytest.mark.parametrize("env", [{"MMX_AUTOTUNE": "0"}, {"MMX_NO_TMA": "1"}, {"MMX_TROWS": "2"},
+                                 {"MMX_TROWS": "4"}, {"MMX_TROWS": "8"}, {"MMX_TROWS": "16"}])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_each_pass_configuration_matches_oracle(env, prec, tol, monkeypatch):
+    """Every configuration the autotuner chooses from, forced one at a time:
+    x rows per CTA 2..16, XI with or without TMA tile copies."""
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    for n, d in (((32, 16, 4), (2e-9, 3e-9, 1e-9)), ((64, 32, 1), (4e-9, 4e-9, 4e-9))):
+        m = W.m_random(n, seed=sum(n) + 3)
+        ref = O.demag_fft(O.newell_octant(*n, *d), MAT["Ms"], m)
+        got = gpu_demag({"n": n, "d": d}, MAT, m, prec)
+        assert rel_max(got, ref) < tol
+
+
+def test_autotuned_plan_is_reported():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_util import gpu_context
+    ctx = gpu_context({"n": (64, 32, 2), "d": (4e-9,) * 3}, MAT, {}, {"method": "RK4", "h": 1e-13}, "fp32")
+    try:
+        p = ctx.plan()
+        assert p["tuned"] == 1 and p["demag_us"] > 0
+        assert p["yz_pass"] == 0 and p["kernels_per_demag"] == 3 and p["x_rows"] in (2, 4, 8, 16)
+    finally:
+        ctx.close()
+    big = gpu_context({"n": (16, 128, 16), "d": (2e-9,) * 3}, MAT, {}, {"method": "RK4", "h": 1e-13}, "fp32")
+    try:
+        p = big.plan()
+        assert p["yz_pass"] in (1, 2)
+        assert p["kernels_per_demag"] == (5 if p["yz_pass"] == 1 else 3)
+        assert (p["cluster_ctas"] > 1) == (p["yz_pass"] == 2)
+    finally:
+        big.close()
