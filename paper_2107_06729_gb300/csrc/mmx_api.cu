@@ -314,9 +314,10 @@ std::shared_ptr<const std::vector<double>> tensor_for(const mmx_host_tensor_args
 // Pass configurations of one exact demag evaluation: rows per CTA of the
 // plain x passes, XI with TMA tile loads or plain, and for meshes whose y-z
 // column does not fit one CTA the split passes or the thread-block-cluster
-// pass.  Each candidate is timed (CUDA events, one warm-up and three
-// evaluations of the zero field on the context's own buffers) and the
-// fastest kept; results are cached per mesh and precision for the process.
+// pass.  After about 20 ms of warm-up evaluations, each candidate is timed
+// twice, round robin (CUDA events, one warm-up and three evaluations of the
+// zero field on the context's own buffers), and the fastest minimum kept;
+// results are cached per mesh and precision for the process.
 struct Plan {
     int trows;
     bool xi_tma, cluster;
@@ -378,15 +379,23 @@ int autotune(mmx_ctx *c)
         cl_ok = c->cluster;
         c->cluster = false;
     }
-    Plan best{tr0, c->xi_tma_ok, false, 1e30};
+    std::vector<Plan> cand;
     for (int cl = 0; cl <= (cl_ok ? 1 : 0); ++cl)
         for (int xt = 0; xt <= (c->xi_tma_ok ? 1 : 0); ++xt)
-            for (int tr : rows) {
-                Plan p{tr, xt == 1, cl == 1, 0};
-                apply_plan(c, p);
-                p.us = time_demag(c);
-                if (p.us < best.us) best = p;
-            }
+            for (int tr : rows) cand.push_back(Plan{tr, xt == 1, cl == 1, 1e30});
+    // bring the clocks up first (about 20 ms of evaluations), then two
+    // round-robin passes over the candidates, keeping each one's minimum
+    apply_plan(c, cand[0]);
+    double spent = 0;
+    for (int i = 0; i < 200 && spent < 20000; ++i) spent += 4 * time_demag(c);
+    for (int round = 0; round < 2; ++round)
+        for (Plan &p : cand) {
+            apply_plan(c, p);
+            p.us = std::min(p.us, time_demag(c));
+        }
+    Plan best = cand[0];
+    for (const Plan &p : cand)
+        if (p.us < best.us) best = p;
     apply_plan(c, best);
     c->launches = launches;
     c->tuned = true;
