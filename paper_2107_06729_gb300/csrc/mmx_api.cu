@@ -315,8 +315,9 @@ std::shared_ptr<const std::vector<double>> tensor_for(const mmx_host_tensor_args
 // plain x passes, XI with TMA tile loads or plain, and for meshes whose y-z
 // column does not fit one CTA the split passes or the thread-block-cluster
 // pass.  After about 20 ms of warm-up evaluations, each candidate is timed
-// twice, round robin (CUDA events, one warm-up and three evaluations of the
-// zero field on the context's own buffers), and the fastest minimum kept;
+// twice, round robin (CUDA events, one warm-up and three evaluations of a
+// seeded pseudo-random field on the context's own buffers), and the fastest
+// minimum kept;
 // results are cached per mesh and precision for the process.
 struct Plan {
     int trows;
@@ -367,6 +368,28 @@ int autotune(mmx_ctx *c)
             }
     }
     const long long launches = c->launches;
+    // time on a seeded pseudo-random field (not zeros) in m[0]; cleared after
+    {
+        const size_t cnt = (size_t)3 * c->n;
+        std::vector<unsigned char> host(cnt * c->esz);
+        uint64_t x = 0x9E3779B97F4A7C15ULL;
+        for (size_t i = 0; i < cnt; ++i) {
+            x ^= x << 13;
+            x ^= x >> 7;
+            x ^= x << 17;
+            const double v = (double)(x >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+            if (c->esz == 8)
+                memcpy(&host[i * 8], &v, 8);
+            else {
+                const float f = (float)v;
+                memcpy(&host[i * 4], &f, 4);
+            }
+        }
+        if (cudaMemcpy(c->m[0], host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            return MMX_ERR_CUDA;
+        }
+    }
     std::vector<int> rows;
     for (int tr = 2; tr <= 16; tr *= 2)
         if (mmxk_set_trows(c, tr) == 0) rows.push_back(tr);
@@ -397,6 +420,7 @@ int autotune(mmx_ctx *c)
     for (const Plan &p : cand)
         if (p.us < best.us) best = p;
     apply_plan(c, best);
+    cudaMemset(c->m[0], 0, (size_t)3 * c->n * c->esz);
     c->launches = launches;
     c->tuned = true;
     if (best.us >= 1e30) return MMX_ERR_CUDA;
