@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(256, 2) k_xi(const XArgs<T> a)
         const cx<T> z = sm[(t >> 1) * PXS + x];
         T v = (t & 1) ? z.y : z.x;
         if (a.self_src) {
-            const int c = (int)(r / a.plane);
+            const int c = (int)(r >> ilog2(a.plane));  // plane = ny nz, a power of two
             v -= (T)a.msN00[c] * a.self_src[r * nx + x];
         }
         out[r * nx + x] = v;
@@ -731,7 +731,7 @@ __global__ void __launch_bounds__(256) k_xi_t(const XArgs<T> a, const __grid_con
             const cx<T> z = work[(t >> 1) * PXS + x];
             T v = (t & 1) ? z.y : z.x;
             if (a.self_src) {
-                const int c = (int)(r / a.plane);
+                const int c = (int)(r >> ilog2(a.plane));  // plane = ny nz, a power of two
                 v -= (T)a.msN00[c] * a.self_src[r * nx + x];
             }
             out[r * nx + x] = v;
