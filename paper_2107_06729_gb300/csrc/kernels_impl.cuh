@@ -531,6 +531,52 @@ __global__ void __launch_bounds__(256, 2) k_xf(const XArgs<T> a)
     }
 }
 
+// Output of the x-inverse passes: rows [r0, r0 + nrows) (rows >= R skipped)
+// from the pair rows in `work` (row t is the real part of pair t/2 for even
+// t, the imaginary part for odd t), minus Ms N00 self_src where given.  FP32
+// with 16-byte aligned buffers: four x per thread, loads and stores as
+// float4, four rows in flight per thread; otherwise one element per thread.
+template <typename T, int PXS>
+__device__ __forceinline__ void xi_store(const Pad<T> work, const XArgs<T> &a, T *out, long long r0, int nrows,
+                                         long long R)
+{
+    const int nx = a.nx, lgnx = ilog2(nx), lgpl = ilog2(a.plane);
+    if constexpr (sizeof(T) == 4) {
+        if (nx >= 4 && (((uintptr_t)out | (uintptr_t)a.self_src) & 15) == 0) {
+            const int nv = nx >> 2, lgnv = lgnx - 2;
+#pragma unroll 4
+            for (int idx = threadIdx.x; idx < nrows * nv; idx += blockDim.x) {
+                const int t = idx >> lgnv, x0 = (idx & (nv - 1)) << 2;
+                const long long r = r0 + t;
+                if (r >= R) continue;
+                const Pad<T> z = work.at((t >> 1) * PXS + x0);
+                float4 v;
+                if (t & 1) {
+                    v.x = z[0].y; v.y = z[1].y; v.z = z[2].y; v.w = z[3].y;
+                } else {
+                    v.x = z[0].x; v.y = z[1].x; v.z = z[2].x; v.w = z[3].x;
+                }
+                if (a.self_src) {
+                    const float ms = (float)a.msN00[(int)(r >> lgpl)];
+                    const float4 q = __ldg(reinterpret_cast<const float4 *>(a.self_src + r * nx + x0));
+                    v.x -= ms * q.x; v.y -= ms * q.y; v.z -= ms * q.z; v.w -= ms * q.w;
+                }
+                *reinterpret_cast<float4 *>(out + r * nx + x0) = v;
+            }
+            return;
+        }
+    }
+    for (int idx = threadIdx.x; idx < nrows * nx; idx += blockDim.x) {
+        const int t = idx >> lgnx, x = idx & (nx - 1);
+        const long long r = r0 + t;
+        if (r >= R) continue;
+        const cx<T> z = work[(t >> 1) * PXS + x];
+        T v = (t & 1) ? z.y : z.x;
+        if (a.self_src) v -= (T)a.msN00[(int)(r >> lgpl)] * a.self_src[r * nx + x];  // plane = ny nz, 2^k
+        out[r * nx + x] = v;
+    }
+}
+
 template <typename T, int PX>
 __global__ void __launch_bounds__(256, 2) k_xi(const XArgs<T> a)
 {
@@ -572,19 +618,7 @@ __global__ void __launch_bounds__(256, 2) k_xi(const XArgs<T> a)
         fft_smem<T, true, block_items(PX)>(sm, f, a.tw, false, true);
     }
     T *out = a.dst_mode == 1 ? a.hist + (size_t)head * 3 * a.n : a.dst;
-    const int T_ = a.trows, lgnx = ilog2(nx);
-    for (int idx = threadIdx.x; idx < T_ * nx; idx += blockDim.x) {
-        const int t = idx >> lgnx, x = idx & (nx - 1);
-        const long long r = r0 + t;
-        if (r >= R) continue;
-        const cx<T> z = sm[(t >> 1) * PXS + x];
-        T v = (t & 1) ? z.y : z.x;
-        if (a.self_src) {
-            const int c = (int)(r >> ilog2(a.plane));  // plane = ny nz, a power of two
-            v -= (T)a.msN00[c] * a.self_src[r * nx + x];
-        }
-        out[r * nx + x] = v;
-    }
+    xi_store<T, PXS>(sm, a, out, r0, a.trows, R);
     if (a.st && blockIdx.x == 0 && threadIdx.x == 0) a.st->exact_evals++;
 }
 
@@ -724,18 +758,7 @@ __global__ void __launch_bounds__(256) k_xi_t(const XArgs<T> a, const __grid_con
         const int w = threadIdx.x >> 5;
         if (w < NP) WarpFFT<T, true, PX, 1>::run(work.at(w * PXS), 1, a.tw, false, true);
         __syncthreads();
-        const long long r0 = (long long)tile * TR;
-        for (int idx = threadIdx.x; idx < TR * nx; idx += blockDim.x) {
-            const int t = idx >> lgnx, x = idx & (nx - 1);
-            const long long r = r0 + t;
-            const cx<T> z = work[(t >> 1) * PXS + x];
-            T v = (t & 1) ? z.y : z.x;
-            if (a.self_src) {
-                const int c = (int)(r >> ilog2(a.plane));  // plane = ny nz, a power of two
-                v -= (T)a.msN00[c] * a.self_src[r * nx + x];
-            }
-            out[r * nx + x] = v;
-        }
+        xi_store<T, PXS>(work, a, out, (long long)tile * TR, TR, R);
         __syncthreads();  // work is refilled by the next tile
     }
     if (failed) {
