@@ -418,19 +418,21 @@ template <typename T, int L, bool INV> struct RegFFT<T, L, L, INV> {
     static __device__ __forceinline__ void run(cx<T> *, const cx<T> *) {}
 };
 
-// one column of length L at buf[base + i*es]: the first nload entries are
-// read (the rest are zero), the first nstore results are written
+// one zero-padded column of length L at buf[base + i*es]: the forward
+// transform reads the first L/2 entries (the padding is zero and is not
+// read), the inverse writes the first L/2 results (the rest are truncated);
+// both halves are compile-time, so the zero inputs and unused outputs fold away
 template <typename T, int L, bool INV>
-__device__ __forceinline__ void col_fft(const Pad<T> buf, int base, int es, int nload, int nstore,
-                                        const cx<T> *__restrict__ tw)
+__device__ __forceinline__ void col_fft(const Pad<T> buf, int base, int es, const cx<T> *__restrict__ tw)
 {
+    constexpr int NLOAD = INV ? L : (L > 1 ? L / 2 : 1), NSTORE = INV ? (L > 1 ? L / 2 : 1) : L;
     cx<T> v[L];
 #pragma unroll
-    for (int i = 0; i < L; ++i) v[i] = i < nload ? buf[base + i * es] : mk<T>(0, 0);
+    for (int i = 0; i < L; ++i) v[i] = i < NLOAD ? buf[base + i * es] : mk<T>(0, 0);
     RegFFT<T, L, 1, INV>::run(v, tw);
 #pragma unroll
     for (int i = 0; i < L; ++i)
-        if (i < nstore) buf[base + i * es] = v[i];
+        if (i < NSTORE) buf[base + i * es] = v[i];
 }
 
 template <typename T> __host__ __device__ constexpr int reg_max_len() { return sizeof(T) == 4 ? 16 : 8; }
@@ -438,15 +440,14 @@ template <typename T> __host__ __device__ constexpr int reg_max_len() { return s
 template <typename T> __host__ __device__ constexpr int zm_reg_len() { return sizeof(T) == 4 ? 32 : 16; }
 
 template <typename T, bool INV>
-__device__ __forceinline__ void col_fft_any(const Pad<T> buf, int L, int base, int es, int nload, int nstore,
-                                            const cx<T> *__restrict__ tw)
+__device__ __forceinline__ void col_fft_any(const Pad<T> buf, int L, int base, int es, const cx<T> *__restrict__ tw)
 {
     switch (L) {
-    case 2: col_fft<T, 2, INV>(buf, base, es, nload, nstore, tw); break;
-    case 4: col_fft<T, 4, INV>(buf, base, es, nload, nstore, tw); break;
-    case 8: col_fft<T, 8, INV>(buf, base, es, nload, nstore, tw); break;
+    case 2: col_fft<T, 2, INV>(buf, base, es, tw); break;
+    case 4: col_fft<T, 4, INV>(buf, base, es, tw); break;
+    case 8: col_fft<T, 8, INV>(buf, base, es, tw); break;
     default:
-        if (sizeof(T) == 4) col_fft<T, (sizeof(T) == 4 ? 16 : 8), INV>(buf, base, es, nload, nstore, tw);
+        if (sizeof(T) == 4) col_fft<T, (sizeof(T) == 4 ? 16 : 8), INV>(buf, base, es, tw);
         break;
     }
 }
@@ -843,7 +844,7 @@ __global__ void __launch_bounds__(YZ_THREADS, 2) k_yz(const YZArgs<T> a)
     if (Pz > 1) {
         if (rz) {
             for (int tr = threadIdx.x; tr < 3 * Py; tr += blockDim.x)
-                col_fft_any<T, false>(B, Pz, (tr >> lgPy) * plane + (tr & (Py - 1)), Py, nz, Pz, a.twz);
+                col_fft_any<T, false>(B, Pz, (tr >> lgPy) * plane + (tr & (Py - 1)), Py, a.twz);  // Pz = 2 nz
             __syncthreads();
         } else {
             fft_smem<T, false, 2>(B, fz, a.twz, true, false);
@@ -901,7 +902,7 @@ __global__ void __launch_bounds__(YZ_THREADS, 2) k_yz(const YZArgs<T> a)
     if (Pz > 1) {
         if (rz) {
             for (int tr = threadIdx.x; tr < 3 * Py; tr += blockDim.x)
-                col_fft_any<T, true>(B, Pz, (tr >> lgPy) * plane + (tr & (Py - 1)), Py, Pz, nz, a.twz);
+                col_fft_any<T, true>(B, Pz, (tr >> lgPy) * plane + (tr & (Py - 1)), Py, a.twz);
             __syncthreads();
         } else {
             fft_smem<T, true, 2>(B, fz, a.twz, false, true);
@@ -1019,7 +1020,7 @@ __global__ void __launch_bounds__(YZ_THREADS) k_zm(const SplitArgs<T> a)
     if constexpr (PZ > 1) {
         if constexpr (PZ <= zm_reg_len<T>()) {
             for (int tr = threadIdx.x; tr < 3 * W; tr += blockDim.x)
-                col_fft<T, PZ, false>(B, (tr >> lgW) * plane + (tr & (W - 1)), W, nz, PZ, a.twz);
+                col_fft<T, PZ, false>(B, (tr >> lgW) * plane + (tr & (W - 1)), W, a.twz);
             __syncthreads();
         } else {
             fft_smem<T, false, block_items(PZ)>(B, fz, a.twz, true, false);
@@ -1075,7 +1076,7 @@ __global__ void __launch_bounds__(YZ_THREADS) k_zm(const SplitArgs<T> a)
     if constexpr (PZ > 1) {
         if constexpr (PZ <= zm_reg_len<T>()) {
             for (int tr = threadIdx.x; tr < 3 * W; tr += blockDim.x)
-                col_fft<T, PZ, true>(B, (tr >> lgW) * plane + (tr & (W - 1)), W, PZ, nz, a.twz);
+                col_fft<T, PZ, true>(B, (tr >> lgW) * plane + (tr & (W - 1)), W, a.twz);
             __syncthreads();
         } else {
             fft_smem<T, true, block_items(PZ)>(B, fz, a.twz, false, true);
@@ -1461,7 +1462,7 @@ __global__ void __launch_bounds__(192) k_zm_r(const SplitArgs<T> a)
     cx<T> *g = a.Tb + ((size_t)kx * nrows + (size_t)c * nz) * Py + ky0 + w;
     cx<T> v[PZ];
 #pragma unroll
-    for (int z = 0; z < PZ; ++z) v[z] = z < nz ? g[(size_t)z * Py] : mk<T>(0, 0);
+    for (int z = 0; z < PZ; ++z) v[z] = z < PZ / 2 ? g[(size_t)z * Py] : mk<T>(0, 0);  // Pz = 2 nz
     RegFFT<T, PZ, 1, false>::run(v, a.twz);
 #pragma unroll
     for (int kz = 0; kz < PZ; ++kz) B[c * plane + kz * W + w] = v[kz];
@@ -1518,7 +1519,7 @@ __global__ void __launch_bounds__(192) k_zm_r(const SplitArgs<T> a)
     RegFFT<T, PZ, 1, true>::run(v, a.twz);
 #pragma unroll
     for (int z = 0; z < PZ; ++z)
-        if (z < nz) g[(size_t)z * Py] = v[z];
+        if (z < PZ / 2) g[(size_t)z * Py] = v[z];
 }
 
 // ---------------------------------------------- cluster-fused y-z pass (YZC)
@@ -1586,7 +1587,7 @@ __global__ void __launch_bounds__(192, 2) k_yzc(const SplitArgs<T> a)
         if (zt) {
 #pragma unroll
             for (int z = 0; z < PZ; ++z) {
-                if (z < nz) {
+                if (z < PZ / 2) {  // Pz = 2 nz
                     const int row = c * nz + z, own = row / RC, lr = row - own * RC;
                     const Pad<T> R{cl.map_shared_rank(ybuf, own), 0};
                     v[z] = R[lr * PY + slot];
@@ -1653,7 +1654,7 @@ __global__ void __launch_bounds__(192, 2) k_yzc(const SplitArgs<T> a)
             RegFFT<T, PZ, 1, true>::run(v, a.twz);
 #pragma unroll
             for (int z = 0; z < PZ; ++z) {
-                if (z < nz) {
+                if (z < PZ / 2) {
                     const int row = c * nz + z, own = row / RC, lr = row - own * RC;
                     const Pad<T> R{cl.map_shared_rank(ybuf, own), 0};
                     R[lr * PY + slot] = v[z];
