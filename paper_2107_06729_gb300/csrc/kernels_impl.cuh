@@ -71,6 +71,16 @@ template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b)
 }
 template <typename T> __device__ __forceinline__ cx<T> cscale(T s, cx<T> a) { return mk(s * a.x, s * a.y); }
 
+// Programmatic dependent launch: wait until the kernel before this one in
+// the stream has completed and its writes are visible (a no-op for a launch
+// without the attribute), then allow the next kernel's CTAs to be scheduled,
+// so that they are resident and waiting here when this kernel ends.
+__device__ __forceinline__ void pdl_entry()
+{
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // Twiddles w^r, r = 1..R-1, of one radix-R butterfly.  FP64 reads each from
 // the table; FP32 reads w^1 only and forms the powers by complex products
 // (at most three deep, a few ulp): the table reads of a warp hit scattered
@@ -485,6 +495,7 @@ int items_for(int L, int threads)
 template <typename T, int PX>
 __global__ void __launch_bounds__(256, 2) k_xf(const XArgs<T> a)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
     if (a.st) {
@@ -581,6 +592,7 @@ __device__ __forceinline__ void xi_store(const Pad<T> work, const XArgs<T> &a, T
 template <typename T, int PX>
 __global__ void __launch_bounds__(256, 2) k_xi(const XArgs<T> a)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
     int head = 0;
@@ -680,6 +692,7 @@ constexpr unsigned long long XIT_WAIT_NS = 2000000000ULL;  // 2 s
 template <typename T, int PX>
 __global__ void __launch_bounds__(256) k_xi_t(const XArgs<T> a, const __grid_constant__ CUtensorMap tm)
 {
+    pdl_entry();
     static_assert(sizeof(T) == 4, "TMA XI: FP32 spectrum (8-byte elements)");
     extern __shared__ __align__(1024) unsigned char smtma[];
     int head = 0;
@@ -811,6 +824,7 @@ __device__ __forceinline__ void apply_K(const T k[6], cx<T> mx, cx<T> my, cx<T> 
 template <typename T, int PY>
 __global__ void __launch_bounds__(YZ_THREADS, 2) k_yz(const YZArgs<T> a)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> B{reinterpret_cast<cx<T> *>(smraw), 0};
     if (a.st) {
@@ -951,6 +965,7 @@ template <typename T> struct SplitArgs {
 template <typename T, int PY>
 __global__ void __launch_bounds__(256, 2) k_yf(const SplitArgs<T> a)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
     if (a.st) {
@@ -1000,6 +1015,7 @@ __global__ void __launch_bounds__(256, 2) k_yf(const SplitArgs<T> a)
 template <typename T, int PZ>
 __global__ void __launch_bounds__(YZ_THREADS) k_zm(const SplitArgs<T> a)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> B{reinterpret_cast<cx<T> *>(smraw), 0};
     if (a.st) {
@@ -1093,6 +1109,7 @@ __global__ void __launch_bounds__(YZ_THREADS) k_zm(const SplitArgs<T> a)
 template <typename T, int PY>
 __global__ void __launch_bounds__(256, 2) k_yi(const SplitArgs<T> a)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
     if (a.st) {
@@ -1190,6 +1207,7 @@ template <typename T> struct YIView {
 template <typename T, int PX>
 __global__ void __launch_bounds__(256, 2) k_xf_p(const XArgs<T> a)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     if (a.st) {
         if (a.st->done) return;
@@ -1242,6 +1260,7 @@ __global__ void __launch_bounds__(256, 2) k_xf_p(const XArgs<T> a)
 template <typename T, int PY>
 __global__ void __launch_bounds__(256, 2) k_yf_p(const SplitArgs<T> a)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     if (a.st) {
         if (a.st->done) return;
@@ -1299,6 +1318,7 @@ __global__ void __launch_bounds__(256, 2) k_yf_p(const SplitArgs<T> a)
 template <typename T, int PY>
 __global__ void __launch_bounds__(256, 2) k_yi_p(const SplitArgs<T> a)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     if (a.st) {
         if (a.st->done) return;
@@ -1347,6 +1367,7 @@ __global__ void __launch_bounds__(256, 2) k_yi_p(const SplitArgs<T> a)
 template <typename T, int PZ>
 __global__ void __launch_bounds__(YZ_THREADS, 2) k_zm_p(const SplitArgs<T> a)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     if (a.st) {
         if (a.st->done) return;
@@ -1448,6 +1469,7 @@ __global__ void __launch_bounds__(YZ_THREADS, 2) k_zm_p(const SplitArgs<T> a)
 template <typename T, int PZ>
 __global__ void __launch_bounds__(192) k_zm_r(const SplitArgs<T> a)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     cx<T> *B = reinterpret_cast<cx<T> *>(smraw);
     if (a.st) {
@@ -1538,6 +1560,7 @@ __global__ void __launch_bounds__(192) k_zm_r(const SplitArgs<T> a)
 template <typename T, int PY, int PZ>
 __global__ void __launch_bounds__(192, 2) k_yzc(const SplitArgs<T> a)
 {
+    pdl_entry();
     namespace cg = cooperative_groups;
     extern __shared__ __align__(16) unsigned char smraw[];
     cg::cluster_group cl = cg::this_cluster();
@@ -1897,6 +1920,7 @@ template <typename T> __device__ void controller(const StageArgs<T> &a, DevState
 template <typename T>
 __global__ void __launch_bounds__(ST_THREADS, 2) k_stage(const StageArgs<T> a)
 {
+    pdl_entry();
     __shared__ T s_w[MMX_NHIST];       // Eq. 6 weights
     __shared__ T s_H[3];               // applied field at t0 + a_k h
     __shared__ T s_cb[MMX_MAXS];       // h b_{k+1,l}  or  h c_l (last stage)
@@ -2326,6 +2350,23 @@ template <typename T> const void *yi_fn(int L)
     return nullptr;
 }
 
+// Launches f on stream s; with c->pdl as a programmatic dependent launch
+// (the kernels start with pdl_entry, so ordering is that of the stream).
+inline void launch_k(const mmx_ctx *c, const void *f, dim3 grid, dim3 block, void **args, size_t smem, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = c->pdl ? 1 : 0;
+    cudaLaunchKernelExC(&cfg, f, args);
+}
+
 template <typename T>
 void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src_mode, const void *src, int dst_mode,
              void *dst, const void *self_src)
@@ -2427,9 +2468,9 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
             const void *f = mmxk_kernel(K_XIT, false, c->Px);
             const size_t sm = xit_smem(c);
             void *targs[] = {(void *)&xa, (void *)&c->xi_tmap};
-            cudaLaunchKernel(f, dim3(persistent_grid(f, 256, sm, c->rows / XIT_ROWS)), dim3(256), targs, sm, s);
+            launch_k(c, f, dim3(persistent_grid(f, 256, sm, c->rows / XIT_ROWS)), dim3(256), targs, sm, s);
         } else {
-            cudaLaunchKernel(mmxk_kernel(K_XI, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s);
+            launch_k(c, mmxk_kernel(K_XI, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s);
         }
     };
     void *yargs[] = {(void *)&ya};
@@ -2466,36 +2507,36 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
         const void *f_xf = mmxk_kernel(K_XFP, sizeof(T) == 8, c->Px), *f_yf = mmxk_kernel(K_YFP, sizeof(T) == 8, c->Py),
                    *f_yi = mmxk_kernel(K_YIP, sizeof(T) == 8, c->Py), *f_zm = mmxk_kernel(K_ZMP, sizeof(T) == 8, c->Pz);
         timed(0, [&] {
-            cudaLaunchKernel(f_xf, dim3(persistent_grid(f_xf, txf, s_xf, n_x)), dim3(txf), xfa, s_xf, s);
+            launch_k(c, f_xf, dim3(persistent_grid(f_xf, txf, s_xf, n_x)), dim3(txf), xfa, s_xf, s);
         });
         timed(1, [&] {
             if (c->cluster) {
                 launch_yzc();
                 return;
             }
-            cudaLaunchKernel(f_yf, dim3(persistent_grid(f_yf, tyy, s_yf, n_y)), dim3(tyy), sargs, s_yf, s);
+            launch_k(c, f_yf, dim3(persistent_grid(f_yf, tyy, s_yf, n_y)), dim3(tyy), sargs, s_yf, s);
             if (c->Pz <= zmr_max<T>()) {
                 SplitArgs<T> sr = sa;
                 sr.W = zmr_w(c);
                 void *rargs[] = {(void *)&sr};
                 const size_t s_r = (size_t)3 * c->Pz * sr.W * sizeof(cx<T>);
-                cudaLaunchKernel(mmxk_kernel(K_ZMR, sizeof(T) == 8, c->Pz), dim3(c->nx, c->Py / sr.W),
+                launch_k(c, mmxk_kernel(K_ZMR, sizeof(T) == 8, c->Pz), dim3(c->nx, c->Py / sr.W),
                                  dim3(3 * sr.W), rargs, s_r, s);
             } else {
-                cudaLaunchKernel(f_zm, dim3(persistent_grid(f_zm, YZ_THREADS, s_zm, n_z)), dim3(YZ_THREADS), sargs,
+                launch_k(c, f_zm, dim3(persistent_grid(f_zm, YZ_THREADS, s_zm, n_z)), dim3(YZ_THREADS), sargs,
                                  s_zm, s);
             }
-            cudaLaunchKernel(f_yi, dim3(persistent_grid(f_yi, tyy, s_yi, n_y)), dim3(tyy), sargs, s_yi, s);
+            launch_k(c, f_yi, dim3(persistent_grid(f_yi, tyy, s_yi, n_y)), dim3(tyy), sargs, s_yi, s);
             c->launches += 2;
         });
         timed(2, launch_xi);
         return;
     }
-    timed(0, [&] { cudaLaunchKernel(mmxk_kernel(K_XF, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s); });
+    timed(0, [&] { launch_k(c, mmxk_kernel(K_XF, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s); });
     if (c->cluster) {
         timed(1, launch_yzc);
     } else if (!c->split) {
-        timed(1, [&] { cudaLaunchKernel(mmxk_kernel(K_YZ, sizeof(T) == 8, c->Py), dim3(c->nx), dim3(YZ_THREADS), yargs, ys, s); });
+        timed(1, [&] { launch_k(c, mmxk_kernel(K_YZ, sizeof(T) == 8, c->Py), dim3(c->nx), dim3(YZ_THREADS), yargs, ys, s); });
     } else {
         SplitArgs<T> sa{};
         sa.S = (cx<T> *)c->S;
@@ -2521,9 +2562,9 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
         const int yt = y_threads<T>(c);
         void *sargs[] = {(void *)&sa};
         timed(1, [&] {
-            cudaLaunchKernel(mmxk_kernel(K_YF, sizeof(T) == 8, c->Py), gy, dim3(yt), sargs, sy, s);
-            cudaLaunchKernel(mmxk_kernel(K_ZM, sizeof(T) == 8, c->Pz), gz, dim3(YZ_THREADS), sargs, sz, s);
-            cudaLaunchKernel(mmxk_kernel(K_YI, sizeof(T) == 8, c->Py), gy, dim3(yt), sargs, sy, s);
+            launch_k(c, mmxk_kernel(K_YF, sizeof(T) == 8, c->Py), gy, dim3(yt), sargs, sy, s);
+            launch_k(c, mmxk_kernel(K_ZM, sizeof(T) == 8, c->Pz), gz, dim3(YZ_THREADS), sargs, sz, s);
+            launch_k(c, mmxk_kernel(K_YI, sizeof(T) == 8, c->Py), gy, dim3(yt), sargs, sy, s);
             c->launches += 2;
         });
     }
@@ -2569,7 +2610,8 @@ void stage_t(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime, cudaGraph
     const int grid = (int)((c->n + ST_THREADS - 1) / ST_THREADS);
     const int cls = a.last ? 4 : 3;
     if (c->profiling) cudaEventRecord(c->ev_a, s);
-    k_stage<T><<<grid, ST_THREADS, 0, s>>>(a);
+    void *sargs[] = {(void *)&a};
+    launch_k(c, (const void *)k_stage<T>, dim3(grid), dim3(ST_THREADS), sargs, 0, s);
     c->launches++;
     if (c->profiling) {
         cudaEventRecord(c->ev_b, s);
