@@ -483,7 +483,10 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     if (force_cluster && !c->cluster) c->split = big && c->Py >= 2;
     c->nd = (c->split && !c->cluster) ? 5 : 3;
     c->allow_tma = true;
-    c->pdl = getenv("MMX_NO_PDL") == nullptr;
+    // programmatic dependent launches measured slower on GB300 for both the
+    // film and the large box (resident waiting CTAs cost more than the launch
+    // latency they hide), so they are opt-in
+    c->pdl = getenv("MMX_PDL") != nullptr;
     c->trows = mmxk_default_trows(c);
     if (mmxk_x_smem_bytes(c) > 227 * 1024 || (c->split && !c->cluster && mmxk_split_smem_bytes(c) > 227 * 1024) ||
         (!c->split && mmxk_yz_smem_bytes(c) > 227 * 1024)) {
