@@ -149,3 +149,17 @@ def test_cluster_path_integrator_matches_split_path_and_oracle(method, p, monkey
     assert gs["accepted"] == ss["accepted"]
     assert np.abs(got - spl).max() < 1e-6
     assert np.abs(got - ref).max() < 1e-4
+
+
+def test_programmatic_dependent_launch_option_matches_oracle(monkeypatch):
+    """MMX_PDL=1 launches every kernel as a programmatic dependent launch;
+    the kernels wait at entry, so results equal the oracle step for step."""
+    monkeypatch.setenv("MMX_PDL", "1")
+    n, d = (16, 8, 2), (4e-9, 4e-9, 4e-9)
+    mesh = {"n": n, "d": d}
+    integ = {"method": "RKDP54", "extrap_order": 4, "adaptive": True, "h": 1e-13, "tol": 1e-5}
+    m0 = W.m_uniform_noise(n, seed=3, noise=0.2)
+    got, gs = gpu_run(mesh, MAT, FLD, integ, m0, 5e-12, "fp64")
+    ref, rs = oracle_run(mesh, MAT, FLD, integ, m0, 5e-12)
+    assert gs["accepted"] == rs["accepted"] and gs["rejected"] == rs["rejected"]
+    assert np.abs(got - ref).max() < 1e-10
