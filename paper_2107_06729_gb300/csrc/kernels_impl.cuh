@@ -109,15 +109,17 @@ __device__ __forceinline__ void twiddle_row(const cx<T> *__restrict__ tw, int k,
     }
 }
 
-// Shared-memory view with one padding word per 8 complex words: the
-// stride-R stores of the early Stockham stages then spread over all banks.
+// Shared-memory view with one padding word per 16 complex words: every load
+// and every stride-R store of the warp-level Stockham stages (lengths 256 to
+// 1024, radix 8 / 4) then needs the minimum two wavefronts per warp (a bank
+// model of those accesses gives 1.33-1.38x that with one word per 8).
 template <typename T> struct Pad {
     cx<T> *p;
     int base;
     __device__ __forceinline__ cx<T> &operator[](int i) const
     {
         const int j = base + i;
-        return p[j + (j >> 3)];
+        return p[j + (j >> 4)];
     }
     __device__ __forceinline__ Pad at(int off) const { return Pad{p, base + off}; }
 };
@@ -131,7 +133,11 @@ template <typename T> struct Lin {
 
 // words of shared memory for n padded complex words (rounded up to an even
 // count, so that a buffer placed after it starts 16-byte aligned)
-__host__ __device__ constexpr size_t padded_words(size_t n) { return (n + n / 8 + 2) & ~(size_t)1; }
+__host__ __device__ constexpr size_t padded_words(size_t n) { return (n + n / 16 + 2) & ~(size_t)1; }
+// distance between the pair rows of the x passes beyond PX: with the padding
+// above, the pack / unpack loops (8 pair rows x consecutive k) then hit
+// distinct banks
+constexpr int XPAIR_GAP = 32;
 
 // multiply by -i (forward) or +i (inverse)
 template <typename T, bool INV> __device__ __forceinline__ cx<T> rot(cx<T> a)
@@ -504,7 +510,7 @@ __global__ void __launch_bounds__(256, 2) k_xf(const XArgs<T> a)
     }
     const T *src = a.src_mode == 1 ? (a.st->cur ? a.msrc1 : a.msrc0) : a.src;
     const int nx = a.nx, Px = 2 * nx, lgnx = ilog2(nx);
-    constexpr int PXS = PX + 8;  // pair stride: pairs land in different banks
+    constexpr int PXS = PX + XPAIR_GAP;  // pair stride: pairs land in different banks
     const int np = (a.trows + 1) >> 1;
     const long long R = a.rows, r0 = (long long)blockIdx.x * a.trows;
     for (int idx = threadIdx.x; idx < np * nx; idx += blockDim.x) {
@@ -602,7 +608,7 @@ __global__ void __launch_bounds__(256, 2) k_xi(const XArgs<T> a)
         head = a.st->head;
     }
     const int nx = a.nx, Px = 2 * nx;
-    constexpr int PXS = PX + 8;  // pair stride: pairs land in different banks
+    constexpr int PXS = PX + XPAIR_GAP;  // pair stride: pairs land in different banks
     const int np = (a.trows + 1) >> 1;
     const long long R = a.rows, r0 = (long long)blockIdx.x * a.trows;
 #pragma unroll 8
@@ -701,7 +707,7 @@ __global__ void __launch_bounds__(256) k_xi_t(const XArgs<T> a, const __grid_con
         if (a.stage0 && a.st->f1_valid) return;
         head = a.st->head;
     }
-    constexpr int NX = PX / 2, TR = XIT_ROWS, NP = TR / 2, PXS = PX + 8;
+    constexpr int NX = PX / 2, TR = XIT_ROWS, NP = TR / 2, PXS = PX + XPAIR_GAP;
     constexpr int BK = NX < 256 ? NX : 256, NB = NX / BK;
     constexpr unsigned TILE_BYTES = (unsigned)NX * TR * sizeof(cx<T>);
     // layout: two staging tiles, the padded pair rows, two mbarriers
@@ -1213,7 +1219,7 @@ __global__ void __launch_bounds__(256, 2) k_xf_p(const XArgs<T> a)
         if (a.st->done) return;
         if (a.stage0 && a.st->f1_valid) return;
     }
-    constexpr int NX = PX / 2, PXS = PX + 8;
+    constexpr int NX = PX / 2, PXS = PX + XPAIR_GAP;
     const T *src = a.src_mode == 1 ? (a.st->cur ? a.msrc1 : a.msrc0) : a.src;
     const int T_ = a.trows, np = T_ >> 1;
     const long long R = a.rows;
@@ -2101,7 +2107,7 @@ __global__ void __launch_bounds__(ST_THREADS, 2) k_stage(const StageArgs<T> a)
 // ----------------------------------------------------------- host helpers
 template <typename T> size_t x_smem(const mmx_ctx *c, int trows)
 {
-    return padded_words((size_t)((trows + 1) / 2) * (2 * c->nx + 8)) * sizeof(cx<T>);
+    return padded_words((size_t)((trows + 1) / 2) * (2 * c->nx + XPAIR_GAP)) * sizeof(cx<T>);
 }
 template <typename T> size_t yz_smem(const mmx_ctx *c) { return padded_words((size_t)3 * c->Py * c->Pz) * sizeof(cx<T>); }
 
@@ -2137,7 +2143,7 @@ int pick_trows(const mmx_ctx *c)
     const long long rows = c->rows;
     int tr = 16;
     while (tr > 2 && ((rows + tr - 1) / tr < 2 * 152 ||
-                      padded_words((size_t)(tr / 2) * (2 * c->nx + 8)) * 2 * c->esz > 96 * 1024))
+                      padded_words((size_t)(tr / 2) * (2 * c->nx + XPAIR_GAP)) * 2 * c->esz > 96 * 1024))
         tr >>= 1;
     return tr;
 }
@@ -2204,7 +2210,7 @@ template <typename T> const void *xit_fn(int L)
 size_t xit_smem(const mmx_ctx *c)
 {
     return (size_t)2 * c->nx * XIT_ROWS * sizeof(cx<float>) +
-           padded_words((size_t)(XIT_ROWS / 2) * (c->Px + 8)) * sizeof(cx<float>) + 2 * sizeof(uint64_t);
+           padded_words((size_t)(XIT_ROWS / 2) * (c->Px + XPAIR_GAP)) * sizeof(cx<float>) + 2 * sizeof(uint64_t);
 }
 // tensor map of the x spectrum S as [nx][rows] 8-byte words, box 16 x min(nx, 256)
 bool encode_xi_tmap(mmx_ctx *c)
@@ -2271,7 +2277,7 @@ template <typename T> int pipe_ry(const mmx_ctx *c)
 }
 template <typename T> size_t xfp_smem(const mmx_ctx *c)
 {
-    return padded_words((size_t)(XF_P_ROWS / 2) * (c->Px + 8)) * sizeof(cx<T>) + (size_t)XF_P_ROWS * c->nx * sizeof(T);
+    return padded_words((size_t)(XF_P_ROWS / 2) * (c->Px + XPAIR_GAP)) * sizeof(cx<T>) + (size_t)XF_P_ROWS * c->nx * sizeof(T);
 }
 template <typename T> size_t yfp_smem(const mmx_ctx *c)
 {
