@@ -1485,7 +1485,10 @@ __global__ void __launch_bounds__(192) k_zm_r(const SplitArgs<T> a)
     const int W = a.W, Py = a.Py, nz = a.nz, Pz = PZ;
     const int lgW = ilog2(W);
     const int nrows = 3 * nz, plane = PZ * W;
-    const int kx = blockIdx.x, ky0 = blockIdx.y * W;
+    // ky tiles of one kx column are adjacent in launch order, so the tensor
+    // records shared by ky and Py - ky (and the column's rows) are read from
+    // L2 by the second tile instead of DRAM
+    const int kx = blockIdx.y, ky0 = blockIdx.x * W;
     const int c = threadIdx.x >> lgW, w = threadIdx.x & (W - 1);
     cx<T> *g = a.Tb + ((size_t)kx * nrows + (size_t)c * nz) * Py + ky0 + w;
     cx<T> v[PZ];
@@ -2526,7 +2529,7 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
                 sr.W = zmr_w(c);
                 void *rargs[] = {(void *)&sr};
                 const size_t s_r = (size_t)3 * c->Pz * sr.W * sizeof(cx<T>);
-                launch_k(c, mmxk_kernel(K_ZMR, sizeof(T) == 8, c->Pz), dim3(c->nx, c->Py / sr.W),
+                launch_k(c, mmxk_kernel(K_ZMR, sizeof(T) == 8, c->Pz), dim3(c->Py / sr.W, c->nx),
                                  dim3(3 * sr.W), rargs, s_r, s);
             } else {
                 launch_k(c, f_zm, dim3(persistent_grid(f_zm, YZ_THREADS, s_zm, n_z)), dim3(YZ_THREADS), sargs,
