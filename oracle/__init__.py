@@ -21,7 +21,7 @@ from . import build as _build
 
 _lib = None
 
-METHODS = {"RK4": 0, "HEUN12": 1, "RK23": 2, "RKF45": 3, "RKCK45": 4, "RKDP54": 5, "RKF56": 6}
+METHODS = {"RK4": 0, "HEUN12": 1, "RK23": 2, "RKF45": 3, "RKCK45": 4, "RKDP54": 5, "RKF56": 6, "ABM2": 7}
 MU0 = 4e-7 * np.pi
 
 

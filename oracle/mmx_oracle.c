@@ -49,6 +49,15 @@
  *   R9 e > e_max is accepted, and counted as a forced accept, when the step
  *      cannot be reduced: the attempted h or the controller's proposal (the
  *      attempt may be the clipped last step) is at h_min.
+ *   R10 The second-order Adams-Bashforth-Moulton method (Sec. II, ref. [32];
+ *      the paper gives only its name, order and two evaluations per step) is
+ *      read as the variable-step AB2 predictor
+ *        P = M_n + h [(1 + w/2) F_n - (w/2) F_{n-1}],  w = h / h_{n-1},
+ *      the trapezoidal (AM2) corrector M_{n+1} = M_n + h/2 [F_n + F(t+h, P)],
+ *      and e = |M_{n+1} - P| (R4 norm), controller order 2.  The two
+ *      evaluations are F_n (stage 1, exact demag) and F(t+h, P) (stage 2,
+ *      Eq. 6 at t + h).  The first step after a start uses w = 0 (Euler
+ *      predictor); a rejection keeps F_n and F_{n-1}.
  *
  * The integrator works on the unit magnetisation m = M/Ms; fields are A/m.
  */
@@ -424,7 +433,7 @@ typedef struct {
     double a[OM_MAXS], b[OM_MAXS][OM_MAXS], c[OM_MAXS], chat[OM_MAXS];
 } om_tableau;
 
-enum { OM_RK4 = 0, OM_HEUN12, OM_RK23, OM_RKF45, OM_RKCK45, OM_RKDP54, OM_RKF56, OM_NMETHODS };
+enum { OM_RK4 = 0, OM_HEUN12, OM_RK23, OM_RKF45, OM_RKCK45, OM_RKDP54, OM_RKF56, OM_ABM2, OM_NMETHODS };
 
 static void set_row(double *dst, int n, const double *src)
 {
@@ -514,6 +523,12 @@ int om_get_tableau(int method, om_tableau *T)
         set_row(T->c, 7, c);
         set_row(T->chat, 7, ch);
         return 0; }
+    case OM_ABM2: { /* Adams-Bashforth-Moulton 2 (R10): not a Runge-Kutta
+                     * tableau; only the evaluation times (t0, t0 + h) and the
+                     * order are given here, the step is in attempt_step */
+        T->s = 2; T->order = 2; T->adaptive = 1;
+        T->a[1] = 1;
+        return 0; }
     case OM_RKF56: { /* Runge-Kutta-Fehlberg 5(6), ref. [29]; propagates order 5 */
         T->s = 8; T->order = 5; T->adaptive = 1;
         double a[] = {0, 1.0 / 6, 4.0 / 15, 2.0 / 3, 0.8, 1, 0, 1};
@@ -572,7 +587,7 @@ double om_epsilon(long n, const double *m, const double *mref)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Integrator: Eq. 3-6 with the readings R1-R9.                             */
+/* Integrator: Eq. 3-6 with the readings R1-R10.                            */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int method;
@@ -603,6 +618,8 @@ typedef struct {
     double hist_t[OM_MAXP + 1];
     int hist_n;          /* number of stored exact fields (<= p+1) */
     int f1_valid;        /* F[0] already holds F_1 for the current t0 */
+    double *Fprev;       /* ABM2: F at the previous accepted step start */
+    double h_prev;       /* ABM2: previous accepted step, 0 after a start */
     double t, h_ctrl;
     om_stats st;
 } om_sim;
@@ -638,6 +655,8 @@ void *om_sim_create(const om_problem *prob, const om_integrator *integ, const do
     S->Hd = calloc(3 * n, sizeof(double));
     S->M1 = calloc(3 * n, sizeof(double));
     S->G = calloc(3 * n, sizeof(double));
+    S->Fprev = calloc(3 * n, sizeof(double));
+    S->h_prev = 0;
     for (int i = 0; i <= OM_MAXP; i++) S->hist[i] = calloc(3 * n, sizeof(double));
     S->t = 0;
     S->h_ctrl = integ->h;
@@ -651,7 +670,7 @@ void om_sim_destroy(void *handle)
     kernel_free(&S->K);
     free(S->m);
     for (int k = 0; k < S->T.s; k++) free(S->F[k]);
-    free(S->Y); free(S->H); free(S->Hd); free(S->M1); free(S->G);
+    free(S->Y); free(S->H); free(S->Hd); free(S->M1); free(S->G); free(S->Fprev);
     for (int i = 0; i <= OM_MAXP; i++) free(S->hist[i]);
     free(S);
 }
@@ -704,12 +723,20 @@ static int attempt_step(om_sim *S, double h, int *stop_err)
         S->f1_valid = 1;
     }
 
+    const int abm = (S->integ.method == OM_ABM2);
     for (int k = k0; k < s; k++) {
-        /* Y_k = m0 + h sum_{l<k} b_kl F_l  (Eq. 4, reading R2) */
-        for (long i = 0; i < 3 * n; i++) {
-            double acc = S->m[i];
-            for (int l = 0; l < k; l++) acc += h * T->b[k][l] * S->F[l][i];
-            S->Y[i] = acc;
+        if (abm) {
+            /* R10: AB2 predictor P = M_n + h [(1 + w/2) F_n - (w/2) F_{n-1}] */
+            double w = S->h_prev > 0 ? h / S->h_prev : 0.0;
+            for (long i = 0; i < 3 * n; i++)
+                S->Y[i] = S->m[i] + h * ((1.0 + 0.5 * w) * S->F[0][i] - 0.5 * w * S->Fprev[i]);
+        } else {
+            /* Y_k = m0 + h sum_{l<k} b_kl F_l  (Eq. 4, reading R2) */
+            for (long i = 0; i < 3 * n; i++) {
+                double acc = S->m[i];
+                for (int l = 0; l < k; l++) acc += h * T->b[k][l] * S->F[l][i];
+                S->Y[i] = acc;
+            }
         }
         double tk = t0 + T->a[k] * h;
         if (!extrap) {
@@ -737,9 +764,16 @@ static int attempt_step(om_sim *S, double h, int *stop_err)
         double d2 = 0;
         for (int a = 0; a < 3; a++) {
             double acc = S->m[a * n + i], dd = 0;
-            for (int l = 0; l < s; l++) {
-                acc += h * T->c[l] * S->F[l][a * n + i];
-                dd += h * (T->c[l] - T->chat[l]) * S->F[l][a * n + i];
+            if (abm) {
+                /* R10: trapezoidal corrector; e from corrector - predictor */
+                long j = a * n + i;
+                acc = S->m[j] + 0.5 * h * (S->F[0][j] + S->F[1][j]);
+                dd = acc - S->Y[j];
+            } else {
+                for (int l = 0; l < s; l++) {
+                    acc += h * T->c[l] * S->F[l][a * n + i];
+                    dd += h * (T->c[l] - T->chat[l]) * S->F[l][a * n + i];
+                }
             }
             S->M1[a * n + i] = acc;
             d2 += dd * dd;
@@ -771,7 +805,14 @@ static int attempt_step(om_sim *S, double h, int *stop_err)
     S->st.accepted++;
     /* FSAL reuse (R6): only without extrapolation (p < 0), where no exact
      * stage-1 field has to be stored for the history. */
-    if (T->fsal && p < 0) {
+    if (abm) {
+        /* R10: F_n becomes F_{n-1} of the next step */
+        double *tmp = S->Fprev;
+        S->Fprev = S->F[0];
+        S->F[0] = tmp;
+        S->h_prev = h;
+        S->f1_valid = 0;
+    } else if (T->fsal && p < 0) {
         double *tmp = S->F[0];
         S->F[0] = S->F[s - 1];
         S->F[s - 1] = tmp;

@@ -372,3 +372,93 @@ def test_epsilon_metric():
     b = a.copy()
     b[:, 0, 0, 0] = -a[:, 0, 0, 0]
     assert O.epsilon(a, b) == pytest.approx(2.0 / 6)
+
+
+# ------------------------------------------------------ ABM2 (reading R10) --
+ABM_N, ABM_D = (6, 4, 2), (4e-9, 4e-9, 4e-9)
+ABM_MAT = {"Ms": 8e5, "A": 1.3e-11, "K": 3e4, "ku": (0.0, 1.0, 0.0), "alpha": 0.05, "gamma": W.GAMMA}
+ABM_FLD = {"H0": tuple(W.mT((-20.0, 6.0, 3.0)))}
+
+
+def _field_rhs(N6, t, m):
+    """F(t, m) of Eq. 1 assembled from the separately pinned field terms."""
+    mesh = {"n": ABM_N, "d": ABM_D}
+    H = (O.demag_fft(N6, ABM_MAT["Ms"], m) + O.exchange_anisotropy(mesh, ABM_MAT, m)
+         + O.applied_field(mesh, ABM_MAT, ABM_FLD, t).reshape(3, 1, 1, 1))
+    return O.llg_rhs(ABM_MAT["gamma"], ABM_MAT["alpha"], m, H)
+
+
+def _abm_run(method, h, t_end, N6, m0):
+    s = O.Simulation({"n": ABM_N, "d": ABM_D}, ABM_MAT, ABM_FLD,
+                     {"method": method, "extrap_order": -1, "adaptive": False, "h": h}, m0, N6=N6)
+    s.run(t_end)
+    out = s.m(), s.stats()
+    s.close()
+    return out
+
+
+def test_abm2_first_step_is_heun():
+    """With no previous derivative the AB2 predictor is an Euler step, and
+    Euler predictor + trapezoidal corrector is Heun's method."""
+    N6 = O.newell_octant(*ABM_N, *ABM_D)
+    m0 = W.m_smooth(ABM_N, seed=5)
+    h = 5e-14
+    a, sa = _abm_run("ABM2", h, h, N6, m0)
+    b, sb = _abm_run("HEUN12", h, h, N6, m0)
+    assert np.abs(a - b).max() < 1e-15
+    assert sa["last_err"] == pytest.approx(sb["last_err"], rel=1e-12)
+
+
+def test_abm2_steps_are_adams_bashforth_predictor_and_trapezoid_corrector():
+    """Steps 2 and 3 (the third clipped to half a step, w = 1/2) rebuilt from
+    the field terms: P = m + h [(1 + w/2) F_n - (w/2) F_(n-1)], then
+    m + h/2 [F_n + F(t + h, P)], renormalised."""
+    N6 = O.newell_octant(*ABM_N, *ABM_D)
+    m0 = W.m_smooth(ABM_N, seed=6)
+    h = 5e-14
+    m1, _ = _abm_run("ABM2", h, h, N6, m0)
+    F0 = _field_rhs(N6, 0.0, m0)
+
+    def step(m, t, hh, F_n, F_prev, w):
+        P = m + hh * ((1 + w / 2) * F_n - (w / 2) * F_prev)
+        M = m + hh / 2 * (F_n + _field_rhs(N6, t + hh, P))
+        return M / np.linalg.norm(M, axis=0, keepdims=True), np.linalg.norm(M - P, axis=0).max()  # R4
+
+    F1 = _field_rhs(N6, h, m1)
+    m2, _ = step(m1, h, h, F1, F0, 1.0)
+    got2, _ = _abm_run("ABM2", h, 2 * h, N6, m0)
+    assert np.abs(got2 - m2).max() < 1e-14
+    F2 = _field_rhs(N6, 2 * h, m2)
+    m3, e3 = step(m2, 2 * h, h / 2, F2, F1, 0.5)
+    got3, st3 = _abm_run("ABM2", h, 2.5 * h, N6, m0)
+    assert np.abs(got3 - m3).max() < 1e-14
+    assert st3["accepted"] == 3 and st3["last_err"] == pytest.approx(e3, rel=1e-9)
+
+
+@pytest.mark.parametrize("p,expect", [(-1, 2), (1, 2), (0, 1)])
+def test_abm2_convergence_order(conv_problem, p, expect):
+    """ABM2 is second order; with extrapolation of order p the global order
+    is min(2, p + 1) (Sec. II after Eq. 6)."""
+    sl = _slopes(conv_problem, "ABM2", p)
+    assert sl[-1] == pytest.approx(expect, abs=0.3)
+
+
+def test_abm2_two_evaluations_per_step_and_adaptive_run():
+    """Two right-hand-side evaluations per attempt (Sec. III: 2 sub-steps),
+    one exact demag and one Eq. 6 extrapolation once primed; the adaptive
+    controller keeps the error at or below e_max."""
+    N6 = O.newell_octant(*ABM_N, *ABM_D)
+    m0 = W.m_smooth(ABM_N, seed=7)
+    s = O.Simulation({"n": ABM_N, "d": ABM_D}, ABM_MAT, ABM_FLD,
+                     {"method": "ABM2", "extrap_order": 1, "adaptive": True, "h": 1e-13, "tol": 1e-5},
+                     m0, N6=N6)
+    s.run(20e-12)
+    st = s.stats()
+    s.close()
+    att = st["accepted"] + st["rejected"]
+    assert st["exact_evals"] + st["extrap_evals"] == 2 * att - st["rejected"]
+    # every attempt after priming (the first accepted step and the
+    # rejections before it run in full mode) extrapolates its second field
+    assert att - 1 - st["rejected"] <= st["extrap_evals"] <= att - 1
+    assert st["last_err"] <= 1e-5
+    assert st["t"] == pytest.approx(20e-12, rel=1e-15)
