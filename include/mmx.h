@@ -67,7 +67,12 @@ typedef enum {
     MMX_RKF45 = 3,   /* Runge-Kutta-Fehlberg, propagates order 4         */
     MMX_RKCK45 = 4,  /* Cash-Karp, propagates order 4                    */
     MMX_RKDP54 = 5,  /* Dormand-Prince 5(4), FSAL                        */
-    MMX_RKF56 = 6    /* Runge-Kutta-Fehlberg, propagates order 5         */
+    MMX_RKF56 = 6,   /* Runge-Kutta-Fehlberg, propagates order 5         */
+    MMX_ABM2 = 7     /* Adams-Bashforth-Moulton 2, predictor-corrector:
+                      * variable-step AB2 predictor, trapezoidal corrector,
+                      * error = corrector - predictor, two evaluations per
+                      * step (at t and, extrapolated when p >= 0, t + h);
+                      * the first step after a (re)start predicts by Euler */
 } mmx_method;
 
 /* Integrator settings.  extrap_order = p >= 0 evaluates Eq. 2 once per step

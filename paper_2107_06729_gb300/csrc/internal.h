@@ -32,6 +32,7 @@ struct DevState {
     double h_ctrl;   // step proposed by the controller (Eq. 5)
     double t_end;
     double last_err;
+    double h_prev;   // ABM2: last accepted step (0 after a (re)start)
     double hist_t[MMX_NHIST];   // times of the stored exact fields (Eq. 6)
     unsigned long long err_bits;  // running max of the error norm (bit pattern)
     unsigned int blocks_done;
@@ -58,6 +59,7 @@ static_assert(sizeof(DevState) % 8 == 0, "DevState is copied as 8-byte words");
 
 struct TabArgs {
     int s, order, adaptive, fsal;
+    int abm;  // Adams-Bashforth-Moulton 2: coefficients per attempt, F_{n-1} in slot s
     double a[MMX_MAXS];
     double b[MMX_MAXS][MMX_MAXS];
     double c[MMX_MAXS];

@@ -1795,7 +1795,18 @@ __device__ void prepare_coefs(DevState *st, const TabArgs &tab, const PhysArgs &
         const int k = it / MMX_MAXS, l = it % MMX_MAXS;
         StageCoef &C = st->coef[k];
         double cb = 0.0, ce = 0.0;
-        if (k < s) {
+        if (tab.abm) {
+            // ABM2: predictor P = m0 + h [(1 + w/2) F_n - (w/2) F_{n-1}]
+            // (w = h / h_prev, 0 after a restart), corrector m0 + h/2 (F_n +
+            // F(t0 + h, P)), error corrector - predictor; F_{n-1} is slot s
+            const double w = st->h_prev > 0 ? h * recip64(st->h_prev) : 0.0;
+            if (k == 0) {
+                cb = l == 0 ? h * (1.0 + 0.5 * w) : (l == s ? -0.5 * h * w : 0.0);
+            } else if (k == 1) {
+                cb = l < 2 ? 0.5 * h : 0.0;
+                ce = l == 0 ? -0.5 * h * (1.0 + w) : (l == 1 ? 0.5 * h : (l == s ? 0.5 * h * w : 0.0));
+            }
+        } else if (k < s) {
             if (k == s - 1) {
                 cb = h * tab.c[l];
                 ce = h * tab.e[l];
@@ -1883,7 +1894,12 @@ template <typename T> __device__ void controller(const StageArgs<T> &a, DevState
             st->cur ^= 1;
             st->accepted++;
             if (forced) st->forced++;
-            if (a.tab.fsal && a.ctl.p < 0) {
+            if (a.tab.abm) {
+                // F_n becomes F_{n-1}: its slot moves to s, the others are reused
+                st->h_prev = h;
+                st->fbase = (st->fbase + 1) % a.ctl.nslots;
+                st->f1_valid = 0;
+            } else if (a.tab.fsal && a.ctl.p < 0) {
                 st->fbase = (st->fbase + a.tab.s - 1) % a.ctl.nslots;
                 st->f1_valid = 1;
             } else {
@@ -1986,6 +2002,18 @@ __global__ void __launch_bounds__(ST_THREADS, 2) k_stage(const StageArgs<T> a)
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const T v = Fl[c * n + i];
+                acc[c] += cb * v;
+                if (last) E[c] += ce * v;
+            }
+        }
+        // ABM2: F_{n-1} in slot s enters the predictor and the error (its
+        // coefficients are zero, and the slot unread, on a restart)
+        if (a.tab.abm && (s_cb[s] != (T)0 || s_ce[s] != (T)0)) {
+            const T *Fp = a.F + (size_t)((fbase + s) % ns) * fstride;
+            const T cb = s_cb[s], ce = s_ce[s];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const T v = Fp[c * n + i];
                 acc[c] += cb * v;
                 if (last) E[c] += ce * v;
             }

@@ -111,6 +111,11 @@ MethodDef method_def(int m)
              {{31, 384}, {0, 1}, {1125, 2816}, {9, 32}, {125, 768}, {5, 66}, {0, 1}, {0, 1}},
              {{7, 1408}, {0, 1}, {1125, 2816}, {9, 32}, {125, 768}, {0, 1}, {5, 66}, {5, 66}}};
         break;
+    case MMX_ABM2:
+        // stage times and order only: the predictor and error coefficients
+        // depend on the step ratio and are set per attempt on the device
+        d = {2, 2, 1, 0, {{0, 1}, {1, 1}}, {{}, {{1, 1}}}, {{1, 2}, {1, 2}}, {{1, 1}, {0, 1}}};
+        break;
     default:
         d.s = 0;
     }
@@ -155,7 +160,7 @@ std::string validate(const mmx_mesh *mesh, const mmx_material *mat, const mmx_fi
     for (int i = 0; i < 3; ++i)
         if (!std::isfinite(field->H0[i]) || !std::isfinite(field->pulse_H[i])) return "field must be finite";
     if (std::isnan(field->t_on) || std::isnan(field->t_off)) return "pulse window must not be NaN";
-    if (in->method < MMX_RK4 || in->method > MMX_RKF56) return "unknown method";
+    if (in->method < MMX_RK4 || in->method > MMX_ABM2) return "unknown method";
     if (in->extrap_order < -1 || in->extrap_order > MMX_MAXP) return "extrap_order must be in [-1, 6]";
     if (!finite_pos(in->h)) return "h must be > 0";
     if (in->adaptive) {
@@ -192,6 +197,7 @@ void reset_history(DevState *s)
     s->hist_t[0] = s->t;
     s->f1_valid = 0;
     s->fbase = 0;
+    s->h_prev = 0;  // ABM2 restarts with the Euler predictor
 }
 
 // One attempted step, launched on stream s.  prime: full demag at every
@@ -503,6 +509,7 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     T.order = md.order;
     T.adaptive = md.adaptive;
     T.fsal = md.fsal;
+    T.abm = integ->method == MMX_ABM2 ? 1 : 0;
     for (int i = 0; i < md.s; ++i) {
         T.a[i] = md.a[i].n / md.a[i].d;
         T.c[i] = md.c[i].n / md.c[i].d;
@@ -533,7 +540,7 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     CtlArgs &C = c->ctl;
     C.p = integ->extrap_order;
     C.adaptive = (integ->adaptive && md.adaptive) ? 1 : 0;
-    C.nslots = md.s;
+    C.nslots = md.s + T.abm;  // ABM2 keeps F_{n-1} in one more slot
     C.prime = 0;
     C.tol = integ->tol;
     C.hmin = integ->hmin;
@@ -561,7 +568,7 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     const int nh = std::max(1, C.p + 1);
     bool ok = true;
     ok = ok && alloc(&c->m[0], fb) && alloc(&c->m[1], fb) && alloc(&c->Y[0], fb) && alloc(&c->Y[1], fb);
-    ok = ok && alloc(&c->F, fb * md.s) && alloc(&c->G, fb) && alloc(&c->hist, fb * nh);
+    ok = ok && alloc(&c->F, fb * C.nslots) && alloc(&c->G, fb) && alloc(&c->hist, fb * nh);
     ok = ok && alloc(&c->S, (size_t)c->rows * c->nx * 2 * c->esz);
     if (c->split && !c->cluster) ok = ok && alloc(&c->Tb, (size_t)c->nx * 3 * c->nz * c->Py * 2 * c->esz);
     ok = ok && alloc(&c->K, Kspec.size() * c->esz);
@@ -585,7 +592,7 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     }
     cudaMemset(c->m[0], 0, fb);
     cudaMemset(c->m[1], 0, fb);
-    cudaMemset(c->F, 0, fb * md.s);
+    cudaMemset(c->F, 0, fb * C.nslots);
     cudaMemset(c->hist, 0, fb * nh);
     // pass configuration by timing, unless forced or switched off
     {
@@ -764,7 +771,7 @@ int mmx_save_state(mmx_ctx *c, void *buf, size_t *len)
     if (!c || !len) return MMX_ERR_ARG;
     const size_t fb = (size_t)3 * c->n * c->esz;
     const int nh = std::max(1, c->ctl.p + 1);
-    const size_t need = sizeof(BlobHeader) + sizeof(DevState) + fb * (2 + c->tab.s + nh);
+    const size_t need = sizeof(BlobHeader) + sizeof(DevState) + fb * (2 + c->ctl.nslots + nh);
     if (!buf) {
         *len = need;
         return MMX_OK;
@@ -782,8 +789,8 @@ int mmx_save_state(mmx_ctx *c, void *buf, size_t *len)
     p += fb;
     CK(cudaMemcpy(p, c->m[1], fb, cudaMemcpyDeviceToHost));
     p += fb;
-    CK(cudaMemcpy(p, c->F, fb * c->tab.s, cudaMemcpyDeviceToHost));
-    p += fb * c->tab.s;
+    CK(cudaMemcpy(p, c->F, fb * c->ctl.nslots, cudaMemcpyDeviceToHost));
+    p += fb * c->ctl.nslots;
     CK(cudaMemcpy(p, c->hist, fb * nh, cudaMemcpyDeviceToHost));
     *len = need;
     return MMX_OK;
@@ -794,7 +801,7 @@ int mmx_load_state(mmx_ctx *c, const void *buf, size_t len)
     if (!c || !buf) return MMX_ERR_ARG;
     const size_t fb = (size_t)3 * c->n * c->esz;
     const int nh = std::max(1, c->ctl.p + 1);
-    const size_t need = sizeof(BlobHeader) + sizeof(DevState) + fb * (2 + c->tab.s + nh);
+    const size_t need = sizeof(BlobHeader) + sizeof(DevState) + fb * (2 + c->ctl.nslots + nh);
     if (len < need) return fail(c, MMX_ERR_ARG, "state blob too short");
     BlobHeader hd;
     memcpy(&hd, buf, sizeof(hd));
@@ -809,8 +816,8 @@ int mmx_load_state(mmx_ctx *c, const void *buf, size_t len)
     p += fb;
     CK(cudaMemcpy(c->m[1], p, fb, cudaMemcpyHostToDevice));
     p += fb;
-    CK(cudaMemcpy(c->F, p, fb * c->tab.s, cudaMemcpyHostToDevice));
-    p += fb * c->tab.s;
+    CK(cudaMemcpy(c->F, p, fb * c->ctl.nslots, cudaMemcpyHostToDevice));
+    p += fb * c->ctl.nslots;
     CK(cudaMemcpy(c->hist, p, fb * nh, cudaMemcpyHostToDevice));
     c->h_st->done = 1;
     return write_state(c);

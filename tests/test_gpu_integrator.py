@@ -18,7 +18,8 @@ FLD = {"H0": tuple(W.mT((-24.6, 4.3, 0.0))), "pulse": tuple(W.mT((0.0, 20.0, 0.0
 
 @pytest.mark.parametrize("method,p,adaptive", [
     ("RK4", -1, False), ("RK4", 3, False), ("RKDP54", 4, True), ("RKDP54", -1, True),
-    ("RK23", 2, True), ("RKF45", 4, True), ("RKCK45", 4, True), ("RKF56", 5, True), ("HEUN12", 1, True)])
+    ("RK23", 2, True), ("RKF45", 4, True), ("RKCK45", 4, True), ("RKF56", 5, True), ("HEUN12", 1, True),
+    ("ABM2", 1, True), ("ABM2", -1, True), ("ABM2", 1, False)])
 def test_fp64_matches_oracle_step_for_step(method, p, adaptive):
     n, d = (16, 8, 2), (4e-9, 4e-9, 4e-9)
     mesh = {"n": n, "d": d}
@@ -63,11 +64,14 @@ def test_chunked_runs_match_one_run():
     assert sa["accepted"] == sb["accepted"] == 20
 
 
-def test_checkpoint_resume_is_bitwise():
+@pytest.mark.parametrize("method,p", [("RKDP54", 4), ("ABM2", 1)])
+def test_checkpoint_resume_is_bitwise(method, p):
+    """The blob carries every stage slot (for ABM2 also F_(n-1) and the
+    previous step), so a resumed run continues bit for bit."""
     torch = torch_cuda()
     n, d = (16, 8, 2), (4e-9, 4e-9, 4e-9)
     mesh = {"n": n, "d": d}
-    integ = {"method": "RKDP54", "extrap_order": 4, "adaptive": True, "h": 1e-13, "tol": 1e-5}
+    integ = {"method": method, "extrap_order": p, "adaptive": True, "h": 1e-13, "tol": 1e-5}
     m0 = torch.from_numpy(W.m_uniform_noise(n, seed=2, noise=0.3)).cuda()
     ref = gpu_context(mesh, MAT, FLD, integ, "fp64")
     ref.set_m(m0)
