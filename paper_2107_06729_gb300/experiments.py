@@ -1,0 +1,156 @@
+"""Paper-style experiments on synthetic stand-ins (Sec. III), on the GPU.
+
+    python -m paper_2107_06729_gb300.experiments [--t-end-ps 200] [--only NAME]
+
+prints one JSON line per experiment:
+
+* ``method_sweep`` (Fig. 5(b) analog): every adaptive method of Sec. II at
+  e_max = 1e-5, with demag extrapolation of order p and with the exact demag
+  at every sub-step; simulated ns per second of both, the speedup factor and
+  the error (Eq. 7) of each against a reference run.
+* ``order_sweep`` (Fig. 2(a) analog): RKF56 with p = 0 .. 5 and full demag,
+  the error against the reference.
+* ``fixed_step_sweep``: RK4 at h = 100 .. 500 fs with p = 3 and with full
+  demag, the error against the reference.
+
+The slab stands in for the paper's 3.2 um x 1.6 um x 20 nm Py slab with
+5 nm cells (640 x 320 x 4, S-state start, field (-20, 1, 0) kA/m): the mesh
+is 512 x 256 x 4 cells of 5 nm (mesh sides are powers of two here), Ms = 800
+kA/m, A = 13 pJ/m, alpha = 0.02, the same field, and an S-like start (m
+along +x, the end regions tilted towards +y and -y, plus U(-0.02, 0.02)
+noise) since the paper does not give its S-state.  The reference is an FP64
+run with RKDP54, full demag and e_max = 1e-9.  Everything runs through the
+library's C ABI; FP32 fields unless stated.
+"""
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import workloads as W
+
+METHOD_P = [("HEUN12", 1), ("ABM2", 1), ("RK23", 2), ("RKF45", 4), ("RKCK45", 4), ("RKDP54", 4), ("RKF56", 5)]
+
+
+def slab_config(seed=0):
+    """512 x 256 x 4 cells of 5 nm, Py, field (-20, 1, 0) kA/m, S-like start."""
+    n = (512, 256, 4)
+    d = (5e-9, 5e-9, 5e-9)
+    nx, ny, nz = n
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    x = (np.arange(nx) + 0.5) / nx
+    tilt = 0.6 * (np.exp(-((x - 0.0) / 0.08) ** 2) - np.exp(-((x - 1.0) / 0.08) ** 2))
+    m = np.zeros((3, nz, ny, nx))
+    m[0] = 1.0
+    m[1] = tilt.reshape(1, 1, nx)
+    m = m + rng.uniform(-0.02, 0.02, size=m.shape)
+    m = m / np.linalg.norm(m, axis=0, keepdims=True)
+    return {
+        "name": "slab_512x256x4_5nm",
+        "mesh": {"n": n, "d": d},
+        "material": {"Ms": 8e5, "A": 1.3e-11, "K": 0.0, "ku": (1.0, 0.0, 0.0), "alpha": 0.02, "gamma": W.GAMMA},
+        "field": {"H0": (-20e3, 1e3, 0.0), "pulse": (0.0, 0.0, 0.0), "t_on": 0.0, "t_off": 0.0},
+        "m0": m,
+    }
+
+
+def _adaptive(method, p, tol=1e-5):
+    return {"method": method, "extrap_order": p, "adaptive": True, "h": 1e-13, "tol": tol, "hmin": 1e-15,
+            "hmax": 3e-12, "cmin": 0.01, "cmax": 2.0}
+
+
+def _run(pkg, torch, cfg, integ, prec, t_end):
+    """One run from the start state; returns (m as float64 numpy, stats,
+    device seconds of the run)."""
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    ctx = pkg.Context(cfg["mesh"], cfg["material"], cfg["field"], integ, prec)
+    try:
+        m = torch.from_numpy(cfg["m0"]).to("cuda", dt)
+        ctx.set_m(m)
+        # a short warm-up run builds the graphs; the timed run restarts from
+        # the start state (the step the controller proposed is kept)
+        ctx.run(1e-13)
+        ctx.set_m(m)
+        ctx.set_time(0.0)
+        s0 = ctx.stats()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.run(t_end)
+        e1.record()
+        torch.cuda.synchronize()
+        out = torch.empty_like(m)
+        ctx.get_m(out)
+        s1 = ctx.stats()
+        st = {k: s1[k] - s0[k] for k in ("accepted", "rejected", "exact_evals", "extrap_evals")}
+        return out.double().cpu().numpy(), st, e0.elapsed_time(e1) / 1e3
+    finally:
+        ctx.close()
+
+
+def eps(m, ref):
+    """Eq. 7: mean over cells of |m - m_ref|."""
+    return float(np.linalg.norm(m - ref, axis=0).mean())
+
+
+def method_sweep(pkg, torch, cfg, ref, t_end):
+    rows = []
+    for method, p in METHOD_P:
+        mx, sx, tx = _run(pkg, torch, cfg, _adaptive(method, p), "fp32", t_end)
+        mf, sf, tf = _run(pkg, torch, cfg, _adaptive(method, -1), "fp32", t_end)
+        rows.append({"method": method, "p": p, "ns_per_s_extrap": round(t_end * 1e9 / tx, 4),
+                     "ns_per_s_full": round(t_end * 1e9 / tf, 4), "speedup": round(tf / tx, 3),
+                     "eps_extrap": eps(mx, ref), "eps_full": eps(mf, ref),
+                     "steps_extrap": sx["accepted"], "steps_full": sf["accepted"],
+                     "rejected_extrap": sx["rejected"], "rejected_full": sf["rejected"]})
+    return {"experiment": "method_sweep", "tol": 1e-5, "rows": rows}
+
+
+def order_sweep(pkg, torch, cfg, ref, t_end):
+    rows = []
+    for p in [-1, 0, 1, 2, 3, 4, 5]:
+        m, st, secs = _run(pkg, torch, cfg, _adaptive("RKF56", p), "fp32", t_end)
+        rows.append({"p": p, "eps": eps(m, ref), "steps": st["accepted"], "rejected": st["rejected"],
+                     "ns_per_s": round(t_end * 1e9 / secs, 4)})
+    return {"experiment": "order_sweep", "method": "RKF56", "tol": 1e-5, "rows": rows}
+
+
+def fixed_step_sweep(pkg, torch, cfg, ref, t_end):
+    rows = []
+    for h_fs in (100, 200, 300, 400, 500):
+        for p in (3, -1):
+            integ = {"method": "RK4", "extrap_order": p, "adaptive": False, "h": h_fs * 1e-15}
+            m, st, secs = _run(pkg, torch, cfg, integ, "fp32", t_end)
+            rows.append({"h_fs": h_fs, "p": p, "eps": eps(m, ref), "steps": st["accepted"],
+                         "ns_per_s": round(t_end * 1e9 / secs, 4)})
+    return {"experiment": "fixed_step_sweep", "method": "RK4", "rows": rows}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--t-end-ps", type=float, default=200.0)
+    ap.add_argument("--only", choices=["method_sweep", "order_sweep", "fixed_step_sweep"])
+    args = ap.parse_args(argv)
+    import torch
+    import paper_2107_06729_gb300 as pkg
+    cfg = slab_config()
+    t_end = args.t_end_ps * 1e-12
+    t0 = time.time()
+    ref, rst, rsecs = _run(pkg, torch, cfg, _adaptive("RKDP54", -1, tol=1e-9), "fp64", t_end)
+    print(json.dumps({"experiment": "reference", "workload": cfg["name"], "t_end_ps": args.t_end_ps,
+                      "method": "RKDP54", "p": -1, "tol": 1e-9, "precision": "fp64", "steps": rst["accepted"],
+                      "seconds": round(rsecs, 2)}), flush=True)
+    for name, fn in (("method_sweep", method_sweep), ("order_sweep", order_sweep),
+                     ("fixed_step_sweep", fixed_step_sweep)):
+        if args.only and args.only != name:
+            continue
+        out = fn(pkg, torch, cfg, ref, t_end)
+        out["workload"] = cfg["name"]
+        out["t_end_ps"] = args.t_end_ps
+        print(json.dumps(out), flush=True)
+    print(json.dumps({"experiment": "done", "wall_s": round(time.time() - t0, 1)}), flush=True)
+
+
+if __name__ == "__main__":
+    main()
