@@ -17,7 +17,8 @@
  *     (NULL = legacy default stream).  Calls that return host-visible results
  *     (mmx_run, mmx_step, mmx_get_stats, mmx_save_state) synchronise it.
  *   - Mesh sizes: nx, ny, nz must be powers of two; nx >= 2; ny and nz may be
- *     1 (no padding along that axis).  Other sizes return MMX_ERR_ARG.
+ *     1 (no padding along that axis); ny = 1 together with nz > 8 (FP32) or
+ *     nz > 4 (FP64) is not supported.  Other sizes return MMX_ERR_ARG.
  */
 #ifndef MMX_H
 #define MMX_H
@@ -211,7 +212,9 @@ int mmx_get_plan(const mmx_ctx *ctx, mmx_plan *out);
  *     description reuse the spectrum the array still holds.
  *   - Every call shares the array: calls that overlap on the GPU (other
  *     streams, other host threads) race; serialise them.
- *   - Meshes whose spectrum, tables and scratch exceed the array return
+ *   - Meshes whose spectrum, tables and scratch exceed the array, or whose
+ *     y-z column does not fit one CTA (the split passes need a second
+ *     spectrum buffer; this includes nz > 8 in FP32, nz > 4 in FP64), return
  *     MMX_ERR_ARG (text from mmx_last_error(NULL)); the other errors are
  *     those of mmx_create and mmx_demag. */
 #define MMX_STATIC_SCRATCH_BYTES (16u << 20)

@@ -149,6 +149,9 @@ void mmxk_stage(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime_graph,
 // rows per CTA of the plain x passes: the default, and setting a candidate
 // (raises the kernels' shared-memory limit; MMX_ERR_ARG if it does not fit)
 int mmxk_default_trows(const mmx_ctx *c);
+// longest z transform of the fused y-z pass (its z columns are held in
+// registers); taller meshes take the split passes
+int mmxk_yz_max_pz(const mmx_ctx *c);
 int mmxk_set_trows(mmx_ctx *c, int trows);
 // decides whether the cluster-fused y-z pass runs a split-size mesh (sets
 // cluster, yzc_C, yzc_W); 0 or MMX_ERR_CUDA

@@ -131,6 +131,8 @@ size_t mmxk_split_smem_bytes(const mmx_ctx *c)
     return std::max(yf_smem<float>(c, split_rows<float>(c)), zm_smem<float>(c));
 }
 
+int mmxk_yz_max_pz(const mmx_ctx *c) { return c->prec == MMX_FP64 ? reg_max_len<double>() : reg_max_len<float>(); }
+
 size_t mmxk_yz_smem_bytes(const mmx_ctx *c)
 {
     return c->prec == MMX_FP64 ? yz_smem<double>(c) : yz_smem<float>(c);

@@ -848,8 +848,7 @@ __global__ void __launch_bounds__(YZ_THREADS, 2) k_yz(const YZArgs<T> a)
     }
     __syncthreads();
     const FftShape fy{Py, 3 * nz, lgnz, plane, Py, 1};
-    const FftShape fz{Pz, 3 * Py, lgPy, plane, 1, Py};
-    const bool rz = Pz <= reg_max_len<T>();
+    // Pz <= reg_max_len<T>() here: taller columns take the split passes
     const int nwarp = blockDim.x >> 5, warp = threadIdx.x >> 5;
     if constexpr (PY > 1) {
         if constexpr (PY <= warp_max_len<T>()) {
@@ -862,13 +861,9 @@ __global__ void __launch_bounds__(YZ_THREADS, 2) k_yz(const YZArgs<T> a)
         }
     }
     if (Pz > 1) {
-        if (rz) {
-            for (int tr = threadIdx.x; tr < 3 * Py; tr += blockDim.x)
-                col_fft_any<T, false>(B, Pz, (tr >> lgPy) * plane + (tr & (Py - 1)), Py, a.twz);  // Pz = 2 nz
-            __syncthreads();
-        } else {
-            fft_smem<T, false, 2>(B, fz, a.twz, true, false);
-        }
+        for (int tr = threadIdx.x; tr < 3 * Py; tr += blockDim.x)
+            col_fft_any<T, false>(B, Pz, (tr >> lgPy) * plane + (tr & (Py - 1)), Py, a.twz);  // Pz = 2 nz
+        __syncthreads();
     }
 
     // Fourier-space tensor multiply (Eq. 2): H = K M, K real symmetric
@@ -920,13 +915,9 @@ __global__ void __launch_bounds__(YZ_THREADS, 2) k_yz(const YZArgs<T> a)
     }
     __syncthreads();
     if (Pz > 1) {
-        if (rz) {
-            for (int tr = threadIdx.x; tr < 3 * Py; tr += blockDim.x)
-                col_fft_any<T, true>(B, Pz, (tr >> lgPy) * plane + (tr & (Py - 1)), Py, a.twz);
-            __syncthreads();
-        } else {
-            fft_smem<T, true, 2>(B, fz, a.twz, false, true);
-        }
+        for (int tr = threadIdx.x; tr < 3 * Py; tr += blockDim.x)
+            col_fft_any<T, true>(B, Pz, (tr >> lgPy) * plane + (tr & (Py - 1)), Py, a.twz);
+        __syncthreads();
     }
     if constexpr (PY > 1) {
         if constexpr (PY <= warp_max_len<T>()) {

@@ -475,7 +475,12 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     // split passes; MMX_FORCE_SPLIT forces the split passes, MMX_FORCE_CLUSTER
     // the thread-block-cluster pass where it applies (on GB300 it measures
     // slower than the split passes at 512 x 512 x 16, so it is not the default)
-    const bool big = mmxk_yz_smem_bytes(c) > 160 * 1024;
+    const bool big = mmxk_yz_smem_bytes(c) > 160 * 1024 || c->Pz > mmxk_yz_max_pz(c);
+    if (c->Pz > mmxk_yz_max_pz(c) && c->Py < 2) {
+        g_create_err = "ny = 1 with nz above 8 (FP32) or 4 (FP64) is not supported";
+        delete c;
+        return MMX_ERR_ARG;
+    }
     const bool force_split = getenv("MMX_FORCE_SPLIT") != nullptr;
     const bool force_cluster = getenv("MMX_FORCE_CLUSTER") != nullptr && !force_split;
     c->split = (big || force_split || force_cluster) && c->Py >= 2;

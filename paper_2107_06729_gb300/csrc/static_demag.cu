@@ -88,7 +88,7 @@ extern "C" int mmx_demag_static(const mmx_mesh *mesh, double Ms, int precision, 
     c.st = nullptr;
     c.trows = mmxk_default_trows(&c);
     c.Tb = nullptr;
-    if (mmxk_yz_smem_bytes(&c) > 227 * 1024 || mmxk_x_smem_bytes(&c) > 227 * 1024)
+    if (mmxk_yz_smem_bytes(&c) > 227 * 1024 || mmxk_x_smem_bytes(&c) > 227 * 1024 || c.Pz > mmxk_yz_max_pz(&c))
         return fail(MMX_ERR_ARG, "mesh too large for the single-CTA FFT passes");
     const size_t kbytes = align256((size_t)(c.nx + 1) * c.Hz * c.Hy * 6 * c.esz);
     const size_t txb = align256((size_t)c.Px * 2 * c.esz), tyb = align256((size_t)c.Py * 2 * c.esz),
