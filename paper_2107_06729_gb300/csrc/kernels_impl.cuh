@@ -1464,7 +1464,7 @@ __global__ void __launch_bounds__(YZ_THREADS, 2) k_zm_p(const SplitArgs<T> a)
 // components only through a [c][kz][w] tile for the tensor multiply
 // (consecutive threads touch consecutive words: no bank conflicts).
 template <typename T, int PZ>
-__global__ void __launch_bounds__(192) k_zm_r(const SplitArgs<T> a)
+__global__ void __launch_bounds__(192, 4) k_zm_r(const SplitArgs<T> a)
 {
     pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
