@@ -1935,7 +1935,7 @@ template <typename T> __device__ void controller(const StageArgs<T> &a, DevState
 }
 
 template <typename T>
-__global__ void __launch_bounds__(ST_THREADS, 2) k_stage(const StageArgs<T> a)
+__global__ void __launch_bounds__(ST_THREADS, 4) k_stage(const StageArgs<T> a)
 {
     pdl_entry();
     __shared__ T s_w[MMX_NHIST];       // Eq. 6 weights
