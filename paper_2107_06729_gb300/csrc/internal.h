@@ -107,7 +107,6 @@ struct mmx_ctx {
     // device buffers (element type per precision)
     void *m[2], *Y[2], *F, *G, *hist, *S, *K, *twx, *twy, *twz;
     void *Tb;    // split y/z path: y spectrum [kx][c nz + z][Py] (complex)
-    double *errp;  // per-CTA error maxima of the last stage kernel
     bool split;  // the y-z column does not fit one CTA: YF, ZM, YI instead of YZ
     bool cluster;     // ... and a thread-block cluster per kx column runs it instead (YZC)
     int yzc_C, yzc_W; // cluster size and z sub-tile width of YZC

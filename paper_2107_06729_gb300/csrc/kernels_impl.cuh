@@ -1718,7 +1718,6 @@ template <typename T> struct PhysT {
 
 template <typename T> struct StageArgs {
     T *m0, *m1, *Y0, *Y1, *F, *G, *hist;
-    double *errp;  // last stage: per-CTA maximum of the error norm
     DevState *st;
     TabArgs tab;
     PhysArgs ph;
@@ -1943,7 +1942,6 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stage(const StageArgs<T> a)
     __shared__ T s_cb[MMX_MAXS];       // h b_{k+1,l}  or  h c_l (last stage)
     __shared__ T s_ce[MMX_MAXS];       // h (c_l - c_hat_l) (last stage)
     __shared__ T s_red[ST_THREADS / 32];
-    __shared__ double s_erd[ST_THREADS / 32];
     __shared__ int s_last;
     __shared__ double s_sig[MMX_NHIST], s_iden[MMX_NHIST];
     DevState *st = a.st;
@@ -2101,21 +2099,13 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stage(const StageArgs<T> a)
     if (threadIdx.x == 0) {
         T mx = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, s_red[w]);
-        // the CTA's maximum goes to its own slot (no contended atomic); the
-        // last CTA to arrive reduces the slots
-        a.errp[blockIdx.x] = (double)mx;  // infinite where an estimate was not finite
+        atomicMax(&st->err_bits, (unsigned long long)__double_as_longlong((double)mx));
         __threadfence();
         const unsigned prev = atomicAdd(&st->blocks_done, 1u);
         s_last = (prev == gridDim.x - 1) ? 1 : 0;
     }
     __syncthreads();
     if (s_last) {
-        __threadfence();
-        double em = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) em = fmax(em, ((volatile double *)a.errp)[b]);
-        for (int o = 16; o > 0; o >>= 1) em = fmax(em, __shfl_xor_sync(0xffffffffu, em, o));
-        if ((threadIdx.x & 31) == 0) s_erd[threadIdx.x >> 5] = em;
-        __syncthreads();
         // the state in shared memory: one coalesced read and one write-back
         // instead of dozens of dependent global round trips in the controller
         __shared__ __align__(16) DevState sst;
@@ -2126,8 +2116,7 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stage(const StageArgs<T> a)
         for (int i = threadIdx.x; i < nw; i += blockDim.x) sw[i] = ((volatile unsigned long long *)gw)[i];
         __syncthreads();
         if (threadIdx.x == 0) {
-            double e = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) e = fmax(e, s_erd[w]);
+            const double e = __longlong_as_double((long long)atomicExch(&st->err_bits, 0ULL));
             controller(a, &sst, st, e);
         }
         __syncthreads();
@@ -2621,7 +2610,6 @@ void stage_t(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime, cudaGraph
     a.F = (T *)c->F;
     a.G = (T *)c->G;
     a.hist = (T *)c->hist;
-    a.errp = c->errp;
     a.st = c->st;
     a.tab = c->tab;
     a.ph = c->ph;

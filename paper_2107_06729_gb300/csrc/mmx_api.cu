@@ -580,7 +580,6 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     ok = ok && alloc(&c->twx, (size_t)c->Px * 2 * c->esz) && alloc(&c->twy, (size_t)c->Py * 2 * c->esz) &&
          alloc(&c->twz, (size_t)c->Pz * 2 * c->esz);
     ok = ok && alloc((void **)&c->st, sizeof(DevState));
-    ok = ok && alloc((void **)&c->errp, sizeof(double) * (size_t)((c->n + 255) / 256));
     ok = ok && cudaMallocHost((void **)&c->h_st, sizeof(DevState)) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
     ok = ok && cudaEventCreate(&c->ev_a) == cudaSuccess && cudaEventCreate(&c->ev_b) == cudaSuccess;
@@ -880,7 +879,7 @@ void mmx_destroy(mmx_ctx *c)
         }
     }
     void *bufs[] = {c->m[0], c->m[1], c->Y[0], c->Y[1], c->F, c->G, c->hist, c->S, c->K, c->twx, c->twy, c->twz, c->Tb,
-                    c->st, c->errp};
+                    c->st};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->h_st) cudaFreeHost(c->h_st);
