@@ -692,11 +692,11 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, in
         : "memory");
 }
 
-constexpr int XIT_ROWS = 16;
+constexpr int XIT_ROWS = 8;  // rows per tile: four pair rows, one warp each
 constexpr unsigned long long XIT_WAIT_NS = 2000000000ULL;  // 2 s
 
 template <typename T, int PX>
-__global__ void __launch_bounds__(256) k_xi_t(const XArgs<T> a, const __grid_constant__ CUtensorMap tm)
+__global__ void __launch_bounds__(32 * XIT_ROWS / 2, 3) k_xi_t(const XArgs<T> a, const __grid_constant__ CUtensorMap tm)
 {
     pdl_entry();
     static_assert(sizeof(T) == 4, "TMA XI: FP32 spectrum (8-byte elements)");
@@ -710,10 +710,13 @@ __global__ void __launch_bounds__(256) k_xi_t(const XArgs<T> a, const __grid_con
     constexpr int NX = PX / 2, TR = XIT_ROWS, NP = TR / 2, PXS = PX + XPAIR_GAP;
     constexpr int BK = NX < 256 ? NX : 256, NB = NX / BK;
     constexpr unsigned TILE_BYTES = (unsigned)NX * TR * sizeof(cx<T>);
-    // layout: two staging tiles, the padded pair rows, two mbarriers
-    cx<T> *const stg0 = reinterpret_cast<cx<T> *>(smtma);  // tile b at stg0 + b * NX * TR
-    const Pad<T> work{reinterpret_cast<cx<T> *>(smtma) + 2 * NX * TR, 0};
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(reinterpret_cast<cx<T> *>(smtma) + 2 * NX * TR +
+    // layout: one staging tile, the padded pair rows, one mbarrier.  The copy
+    // of the next tile starts as soon as this one is unpacked, so it overlaps
+    // the transforms and the stores; several CTAs per SM keep several tiles
+    // in flight.
+    cx<T> *const stg = reinterpret_cast<cx<T> *>(smtma);
+    const Pad<T> work{reinterpret_cast<cx<T> *>(smtma) + NX * TR, 0};
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(reinterpret_cast<cx<T> *>(smtma) + NX * TR +
                                                   padded_words((size_t)NP * PXS));
     if (smem_u32(smtma) & 127) {  // tile copies need 128-byte aligned destinations
         if (threadIdx.x == 0 && a.fault) atomicExch(a.fault, 2);
@@ -721,45 +724,35 @@ __global__ void __launch_bounds__(256) k_xi_t(const XArgs<T> a, const __grid_con
     }
     const long long R = a.rows;
     const int ntiles = (int)(R / TR);
-    const int nx = a.nx, lgnx = ilog2(nx);
     T *out = a.dst_mode == 1 ? a.hist + (size_t)head * 3 * a.n : a.dst;
 
     if (threadIdx.x == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        mbar_init(mbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
-    auto issue = [&](int b, int tile) {
-        mbar_expect_tx(&mbar[b], TILE_BYTES);
+    auto issue = [&](int tile) {
+        mbar_expect_tx(mbar, TILE_BYTES);
 #pragma unroll
-        for (int j = 0; j < NB; ++j)
-            tma_load_2d(stg0 + (size_t)b * NX * TR + (size_t)j * BK * TR, &tm, tile * TR, j * BK, &mbar[b]);
+        for (int j = 0; j < NB; ++j) tma_load_2d(stg + (size_t)j * BK * TR, &tm, tile * TR, j * BK, mbar);
     };
-    if (threadIdx.x == 0) {
-        if ((int)blockIdx.x < ntiles) issue(0, blockIdx.x);
-        if ((int)(blockIdx.x + gridDim.x) < ntiles) issue(1, blockIdx.x + gridDim.x);
-    }
-    // bit b: a copy into tile b is in flight / the parity tile b waits for
-    unsigned pend = ((int)blockIdx.x < ntiles ? 1u : 0u) | ((int)(blockIdx.x + gridDim.x) < ntiles ? 2u : 0u);
+    if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
+    bool pend = (int)blockIdx.x < ntiles;  // a copy is in flight
     unsigned phase = 0;
     bool failed = false;
-    int it = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-        const int b = it & 1;
-        const bool ok = mbar_wait_bounded(&mbar[b], (phase >> b) & 1u, XIT_WAIT_NS);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const bool ok = mbar_wait_bounded(mbar, phase, XIT_WAIT_NS);
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
         }
-        phase ^= 1u << b;
-        pend &= ~(1u << b);
-        // unpack the tile [kx][16 rows] into 8 complex pair rows (Hermitian
-        // halves of two real rows), as k_xi does from global memory
-        const cx<T> *g = stg0 + (size_t)b * NX * TR;
+        phase ^= 1u;
+        pend = false;
+        // unpack the tile [kx][TR rows] into TR/2 complex pair rows
+        // (Hermitian halves of two real rows), as k_xi does from global memory
         for (int idx = threadIdx.x; idx < NP * NX; idx += blockDim.x) {
             const int k = idx / NP, p = idx - k * NP;
-            const cx<T> va = g[k * TR + 2 * p], vb = g[k * TR + 2 * p + 1];
+            const cx<T> va = stg[k * TR + 2 * p], vb = stg[k * TR + 2 * p + 1];
             const Pad<T> z = work.at(p * PXS);
             if (k == 0) {
                 z[0] = mk(va.x, vb.x);
@@ -769,11 +762,11 @@ __global__ void __launch_bounds__(256) k_xi_t(const XArgs<T> a, const __grid_con
                 z[PX - k] = mk(va.x + vb.y, vb.x - va.y);
             }
         }
-        __syncthreads();  // staging b consumed: refill it with the tile after next
-        const int nxt = tile + 2 * (int)gridDim.x;
+        __syncthreads();  // staging consumed: start the copy of the next tile
+        const int nxt = tile + (int)gridDim.x;
         if (nxt < ntiles) {
-            if (threadIdx.x == 0) issue(b, nxt);
-            pend |= 1u << b;
+            if (threadIdx.x == 0) issue(nxt);
+            pend = true;
         }
         const int w = threadIdx.x >> 5;
         if (w < NP) WarpFFT<T, true, PX, 1>::run(work.at(w * PXS), 1, a.tw, false, true);
@@ -783,9 +776,8 @@ __global__ void __launch_bounds__(256) k_xi_t(const XArgs<T> a, const __grid_con
     }
     if (failed) {
         if (threadIdx.x == 0 && a.fault) atomicExch(a.fault, 1);
-        // let copies still in flight land before the CTA's memory goes away
-        for (int b = 0; b < 2; ++b)
-            if ((pend >> b) & 1u) (void)mbar_wait_bounded(&mbar[b], (phase >> b) & 1u, XIT_WAIT_NS);
+        // let a copy still in flight land before the CTA's memory goes away
+        if (pend) (void)mbar_wait_bounded(mbar, phase, XIT_WAIT_NS);
         return;
     }
     if (a.st && blockIdx.x == 0 && threadIdx.x == 0) a.st->exact_evals++;
@@ -2231,8 +2223,8 @@ template <typename T> const void *xit_fn(int L)
 // TMA XI: two staging tiles of nx x 16 complex words and the padded pair rows
 size_t xit_smem(const mmx_ctx *c)
 {
-    return (size_t)2 * c->nx * XIT_ROWS * sizeof(cx<float>) +
-           padded_words((size_t)(XIT_ROWS / 2) * (c->Px + XPAIR_GAP)) * sizeof(cx<float>) + 2 * sizeof(uint64_t);
+    return (size_t)c->nx * XIT_ROWS * sizeof(cx<float>) +
+           padded_words((size_t)(XIT_ROWS / 2) * (c->Px + XPAIR_GAP)) * sizeof(cx<float>) + sizeof(uint64_t);
 }
 // tensor map of the x spectrum S as [nx][rows] 8-byte words, box 16 x min(nx, 256)
 bool encode_xi_tmap(mmx_ctx *c)
@@ -2496,7 +2488,8 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
             const void *f = mmxk_kernel(K_XIT, false, c->Px);
             const size_t sm = xit_smem(c);
             void *targs[] = {(void *)&xa, (void *)&c->xi_tmap};
-            launch_k(c, f, dim3(persistent_grid(f, 256, sm, c->rows / XIT_ROWS)), dim3(256), targs, sm, s);
+            launch_k(c, f, dim3(persistent_grid(f, 32 * XIT_ROWS / 2, sm, c->rows / XIT_ROWS)), dim3(32 * XIT_ROWS / 2),
+                     targs, sm, s);
         } else {
             launch_k(c, mmxk_kernel(K_XI, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s);
         }
