@@ -94,11 +94,21 @@ __device__ __forceinline__ void twiddle_row(const cx<T> *__restrict__ tw, int k,
         w[1] = w1;
         w[2] = cmul(w1, w1);
         w[3] = cmul(w[2], w1);
-        if constexpr (R == 8) {
+        if constexpr (R >= 8) {
             w[4] = cmul(w[2], w[2]);
             w[5] = cmul(w[4], w1);
             w[6] = cmul(w[3], w[3]);
             w[7] = cmul(w[4], w[3]);
+        }
+        if constexpr (R == 16) {
+            w[8] = cmul(w[4], w[4]);
+            w[9] = cmul(w[8], w1);
+            w[10] = cmul(w[5], w[5]);
+            w[11] = cmul(w[8], w[3]);
+            w[12] = cmul(w[6], w[6]);
+            w[13] = cmul(w[8], w[5]);
+            w[14] = cmul(w[7], w[7]);
+            w[15] = cmul(w[8], w[7]);
         }
     } else {
 #pragma unroll
@@ -192,6 +202,34 @@ template <typename T, bool INV> struct Dft<T, 8, INV> {
         v[6] = csub(e2, t2);
         v[3] = cadd(e3, t3);
         v[7] = csub(e3, t3);
+    }
+};
+
+// 16 points: DFT-8 of the even and of the odd samples, joined by the 16th
+// roots of unity w^k = exp(-+2 pi i k / 16), k = 0..7
+template <typename T, bool INV> struct Dft<T, 16, INV> {
+    static __device__ __forceinline__ void run(cx<T> *v)
+    {
+        cx<T> e[8], o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            e[k] = v[2 * k];
+            o[k] = v[2 * k + 1];
+        }
+        Dft<T, 8, INV>::run(e);
+        Dft<T, 8, INV>::run(o);
+        const T c1 = (T)0.92387953251128675612818318939678;  // cos(pi/8)
+        const T s1 = (T)0.38268343236508977172845998403040;  // sin(pi/8)
+        const T r = (T)0.70710678118654752440084436210485;   // sqrt(1/2)
+        const T sg = INV ? (T)1 : (T)-1;                     // sign of the imaginary parts
+        const cx<T> w[8] = {mk((T)1, (T)0), mk(c1, sg * s1), mk(r, sg * r), mk(s1, sg * c1),
+                            mk((T)0, sg),   mk(-s1, sg * c1), mk(-r, sg * r), mk(-c1, sg * s1)};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const cx<T> t = (k == 0) ? o[0] : cmul(o[k], w[k]);
+            v[k] = cadd(e[k], t);
+            v[k + 8] = csub(e[k], t);
+        }
     }
 };
 
@@ -345,8 +383,11 @@ __device__ __forceinline__ void warp_stage(const SRC src, const DST buf, int L, 
 template <typename T> __host__ __device__ constexpr int warp_max_len() { return sizeof(T) == 4 ? 1024 : 256; }
 
 // compile-time stage sequence of a length-L transform (radix 8 while
-// possible, 16 as 4 x 4, then 4 or 2): fixed shapes let the compiler keep
-// the register footprint of the largest stage only
+// possible, 16 as 4 x 4, then 4 or 2; 1024 points as 8 x 8 x 16, three
+// stages, which by a bank model of the accesses move a quarter fewer
+// shared-memory wavefronts than 8 x 8 x 4 x 4 — for 128 points a radix-16
+// last stage costs more): fixed shapes let the compiler keep the register
+// footprint of the largest stage only
 template <typename T, bool INV, int L, int NS> struct WarpFFT {
     // the first stage reads src (which may be a staging buffer or a
     // transforming view), every stage writes buf, later stages run in place
@@ -355,7 +396,7 @@ template <typename T, bool INV, int L, int NS> struct WarpFFT {
                                                bool trunc)
     {
         constexpr int REM = L / NS;
-        constexpr int R = (REM % 8 == 0 && REM != 16) ? 8 : ((REM % 4 == 0) ? 4 : 2);
+        constexpr int R = (REM == 16 && L >= 1024) ? 16 : ((REM % 8 == 0 && REM != 16) ? 8 : ((REM % 4 == 0) ? 4 : 2));
         constexpr int PER = L / R;
         constexpr int IT = PER <= 32 ? 1 : PER / 32;
         warp_stage<T, R, INV, IT>(src, buf, L, es, NS, tw, NS == 1 && prune, REM == R && trunc);
@@ -371,7 +412,7 @@ template <typename T, bool INV, int L, int NS> struct WarpFFT {
                                                  bool trunc)
     {
         constexpr int REM = L / NS;
-        constexpr int R = (REM % 8 == 0 && REM != 16) ? 8 : ((REM % 4 == 0) ? 4 : 2);
+        constexpr int R = (REM == 16 && L >= 1024) ? 16 : ((REM % 8 == 0 && REM != 16) ? 8 : ((REM % 4 == 0) ? 4 : 2));
         constexpr int PER = L / R;
         constexpr int IT = PER <= 32 ? 1 : PER / 32;
         warp_stage<T, R, INV, IT>(src, buf, L, es, NS, tw, NS == 1 && prune, REM == R && trunc);
@@ -379,7 +420,7 @@ template <typename T, bool INV, int L, int NS> struct WarpFFT {
     static __device__ __forceinline__ void rest(const Pad<T> buf, int es, const cx<T> *tw, bool prune, bool trunc)
     {
         constexpr int REM = L / NS;
-        constexpr int R = (REM % 8 == 0 && REM != 16) ? 8 : ((REM % 4 == 0) ? 4 : 2);
+        constexpr int R = (REM == 16 && L >= 1024) ? 16 : ((REM % 8 == 0 && REM != 16) ? 8 : ((REM % 4 == 0) ? 4 : 2));
         WarpFFT<T, INV, L, NS * R>::run(buf, buf, es, tw, prune, trunc);
     }
 };
