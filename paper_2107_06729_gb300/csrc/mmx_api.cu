@@ -12,6 +12,7 @@
 #include <cfloat>
 #include <climits>
 #include <cmath>
+#include <cstdio>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -425,6 +426,13 @@ int autotune(mmx_ctx *c)
     Plan best = cand[0];
     for (const Plan &p : cand)
         if (p.us < best.us) best = p;
+    if (getenv("MMX_AUTOTUNE_LOG"))
+        for (const Plan &p : cand)
+            fprintf(stderr, "mmx autotune %dx%dx%d %s: x_rows %d xi_tma %d cluster %d -> %.1f us%s\n", c->nx, c->ny,
+                    c->nz, c->prec == MMX_FP64 ? "fp64" : "fp32", p.trows, (int)p.xi_tma, (int)p.cluster, p.us,
+                    (&p == &best || (p.trows == best.trows && p.xi_tma == best.xi_tma && p.cluster == best.cluster))
+                        ? "  (kept)"
+                        : "");
     apply_plan(c, best);
     cudaMemset(c->m[0], 0, (size_t)3 * c->n * c->esz);
     c->launches = launches;
