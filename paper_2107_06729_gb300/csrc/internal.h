@@ -112,7 +112,6 @@ struct mmx_ctx {
     int yzc_C, yzc_W; // cluster size and z sub-tile width of YZC
     int nd;           // kernels per exact demag evaluation
     bool pdl;         // kernels launched as programmatic dependent launches
-    bool zm_kpre;     // ZM prefetches its tensor records into shared memory
     bool allow_tma;   // TMA passes allowed (the context owns a fault word)
     bool xi_tma_ok;   // the TMA XI is set up for this mesh
     bool xi_tma;      // XI runs with TMA tile loads

@@ -990,7 +990,6 @@ template <typename T> struct SplitArgs {
     DevState *st;
     long long rows;  // 3 ny nz
     int nx, ny, nz, Py, Pz, Hy, Hz, stage0, ry, W;
-    int kpre;  // ZM: prefetch the tile's tensor records into shared memory
 };
 
 template <typename T, int PY>
@@ -1198,11 +1197,6 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
@@ -1520,22 +1514,6 @@ __global__ void __launch_bounds__(192, 4) k_zm_r(const SplitArgs<T> a)
     // L2 by the second tile instead of DRAM
     const int kx = blockIdx.y, ky0 = blockIdx.x * W;
     const int c = threadIdx.x >> lgW, w = threadIdx.x & (W - 1);
-    const int half = Py >> 1;
-    // kpre (FP32, kx != 0): the tile's tensor records -- z in [0, PZ/2], y in
-    // one contiguous range [ylo, ylo + W) (tiles do not straddle Py/2) --
-    // are copied into shared memory while the z columns load and transform
-    float *Ks = reinterpret_cast<float *>(B + 3 * plane);
-    const bool kp = sizeof(T) == 4 && a.kpre && kx != 0;
-    const int ylo = ky0 < half ? ky0 : Py - ky0 - W + 1;
-    if (kp) {
-        const float *Kf = reinterpret_cast<const float *>(a.K);
-        const int nch = (PZ / 2 + 1) * W * 3;  // 8-byte pieces, three per record
-        for (int idx = threadIdx.x; idx < nch; idx += blockDim.x) {
-            const int z = idx / (W * 3), rem = idx - z * (W * 3);
-            cp_async8(Ks + (size_t)z * W * 6 + rem * 2, Kf + (((size_t)kx * a.Hz + z) * a.Hy + ylo) * 6 + rem * 2);
-        }
-        cp_async_commit();
-    }
     cx<T> *g = a.Tb + ((size_t)kx * nrows + (size_t)c * nz) * Py + ky0 + w;
     cx<T> v[PZ];
 #pragma unroll
@@ -1543,24 +1521,14 @@ __global__ void __launch_bounds__(192, 4) k_zm_r(const SplitArgs<T> a)
     RegFFT<T, PZ, 1, false>::run(v, a.twz);
 #pragma unroll
     for (int kz = 0; kz < PZ; ++kz) B[c * plane + kz * W + w] = v[kz];
-    if (kp) cp_async_wait0();
     __syncthreads();
+    const int half = Py >> 1;
 #pragma unroll 4
     for (int q = threadIdx.x; q < plane; q += blockDim.x) {
         const int ww = q & (W - 1), kz = q >> lgW, slot = ky0 + ww;
         if (kx != 0 || (slot != 0 && slot != half)) {
             T k6[6];
-            if (kp) {
-                const bool fy = slot > half, fz = kz > (PZ >> 1);
-                const float *r = Ks + ((size_t)(fz ? PZ - kz : kz) * W + ((fy ? Py - slot : slot) - ylo)) * 6;
-                const T sy = fy ? (T)-1 : (T)1, sz = fz ? (T)-1 : (T)1;
-                k6[0] = (T)r[0];
-                k6[1] = (T)r[1];
-                k6[2] = (T)r[2];
-                k6[3] = sy * (T)r[3];
-                k6[4] = sz * (T)r[4];
-                k6[5] = sy * sz * (T)r[5];
-            } else if (kx != 0)
+            if (kx != 0)
                 load_K(a.K, kx, a.Hy, a.Hz, Py, Pz, slot, kz, k6);
             else if (slot < half)
                 load_K(a.K, 0, a.Hy, a.Hz, Py, Pz, slot, kz, k6);
@@ -2351,13 +2319,6 @@ template <typename T> const void *zmp_fn(int L)
 // register-column ZM: ky tile of W values (3 W threads, at most 192) and
 // the longest z transform it holds in registers
 int zmr_w(const mmx_ctx *c) { return std::min(c->Py, 64); }
-// ZM tensor-record prefetch: FP32 and ky tiles that do not straddle Py/2
-template <typename T> bool zmr_kpre(const mmx_ctx *c) { return sizeof(T) == 4 && c->zm_kpre && c->Py >= 128; }
-template <typename T> size_t zmr_smem(const mmx_ctx *c)
-{
-    const int W = zmr_w(c);
-    return (size_t)3 * c->Pz * W * sizeof(cx<T>) + (zmr_kpre<T>(c) ? (size_t)(c->Pz / 2 + 1) * W * 6 * sizeof(float) : 0);
-}
 template <typename T> constexpr int zmr_max() { return sizeof(T) == 4 ? 32 : 16; }
 
 // pipelined large-mesh passes: rows per item and shared-memory sizes
@@ -2619,9 +2580,8 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
             if (c->Pz <= zmr_max<T>()) {
                 SplitArgs<T> sr = sa;
                 sr.W = zmr_w(c);
-                sr.kpre = zmr_kpre<T>(c) ? 1 : 0;
                 void *rargs[] = {(void *)&sr};
-                const size_t s_r = zmr_smem<T>(c);
+                const size_t s_r = (size_t)3 * c->Pz * sr.W * sizeof(cx<T>);
                 launch_k(c, mmxk_kernel(K_ZMR, sizeof(T) == 8, c->Pz), dim3(c->Py / sr.W, c->nx),
                                  dim3(3 * sr.W), rargs, s_r, s);
             } else {
@@ -2800,9 +2760,6 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
         if (sy > 48 * 1024)
             for (const void *f : fy)
                 if (!raise_smem_limit(f, sy)) return MMX_ERR_CUDA;
-        if (c->Pz <= zmr_max<T>() && zmr_smem<T>(c) > 48 * 1024 &&
-            !raise_smem_limit(mmxk_kernel(K_ZMR, sizeof(T) == 8, c->Pz), zmr_smem<T>(c)))
-            return MMX_ERR_CUDA;
         const void *fz[] = {mmxk_kernel(K_ZM, sizeof(T) == 8, c->Pz)};
         if (sz > 48 * 1024)
             for (const void *f : fz)

@@ -506,7 +506,6 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     // film and the large box (resident waiting CTAs cost more than the launch
     // latency they hide), so they are opt-in
     c->pdl = getenv("MMX_PDL") != nullptr;
-    c->zm_kpre = getenv("MMX_ZM_KPRE") == nullptr || getenv("MMX_ZM_KPRE")[0] != '0';
     c->trows = mmxk_default_trows(c);
     if (mmxk_x_smem_bytes(c) > 227 * 1024 || (c->split && !c->cluster && mmxk_split_smem_bytes(c) > 227 * 1024) ||
         (!c->split && mmxk_yz_smem_bytes(c) > 227 * 1024)) {

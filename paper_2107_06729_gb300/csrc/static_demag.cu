@@ -83,7 +83,6 @@ extern "C" int mmx_demag_static(const mmx_mesh *mesh, double Ms, int precision, 
     c.cluster = false;
     c.nd = 3;
     c.pdl = false;
-    c.zm_kpre = false;
     c.allow_tma = false;  // no device state word to report a bounded wait in
     c.xi_tma = c.xi_tma_ok = false;
     c.st = nullptr;
