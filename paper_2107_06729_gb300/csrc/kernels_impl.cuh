@@ -793,7 +793,9 @@ __global__ void __launch_bounds__(32 * XIT_ROWS / 2, 3) k_xi_t(const XArgs<T> a,
         // (Hermitian halves of two real rows), as k_xi does from global memory
         for (int idx = threadIdx.x; idx < NP * NX; idx += blockDim.x) {
             const int k = idx / NP, p = idx - k * NP;
-            const cx<T> va = stg[k * TR + 2 * p], vb = stg[k * TR + 2 * p + 1];
+            // the pair's two rows are adjacent in the tile: one 16-byte read
+            const float4 q = *reinterpret_cast<const float4 *>(stg + k * TR + 2 * p);
+            const cx<T> va = mk<T>(q.x, q.y), vb = mk<T>(q.z, q.w);
             const Pad<T> z = work.at(p * PXS);
             if (k == 0) {
                 z[0] = mk(va.x, vb.x);
