@@ -184,7 +184,7 @@ int mmxk_chain_plan(mmx_ctx *c)
         return 0;
     }
     const void *fn = c->prec == MMX_FP64 ? (const void *)k_chain<double> : (const void *)k_chain<float>;
-    if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, CHAIN_THREADS, 0) != cudaSuccess || per < 1) {
+    if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, ST_THREADS, 0) != cudaSuccess || per < 1) {
         cudaGetLastError();
         return 0;
     }

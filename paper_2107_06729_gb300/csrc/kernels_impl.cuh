@@ -2211,8 +2211,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks)
             atomicAdd(bar + 1, 1u);
         } else {
             const unsigned long long t0 = global_ns();
-            for (unsigned it = 1; *vgen == g; ++it) {
-                if ((it & 255) == 0 && global_ns() - t0 > 1000000000ULL) {
+            while (*vgen == g) {
+                if (global_ns() - t0 > 1000000000ULL) {
                     ok = 0;
                     break;
                 }
@@ -2228,13 +2228,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks)
 // a grid barrier separates the stages (stage k + 1 reads the neighbours of
 // every cell of Y_{k+1}); the last stage ends as in k_stage.  A barrier that
 // gives up sets the fault word, ends the run and the graph loop.
-constexpr int CHAIN_THREADS = 1024;  // few, large CTAs: few arrivals per grid barrier
-
 template <typename T>
-__global__ void __launch_bounds__(CHAIN_THREADS, 1) k_chain(const StageArgs<T> a)
+__global__ void __launch_bounds__(ST_THREADS, 4) k_chain(const StageArgs<T> a)
 {
     __shared__ StageSmem<T> S;
-    __shared__ T s_red[CHAIN_THREADS / 32];
+    __shared__ T s_red[ST_THREADS / 32];
     __shared__ int s_last;
     __shared__ double s_sig[MMX_NHIST], s_iden[MMX_NHIST];
     DevState *st = a.st;
@@ -2243,7 +2241,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS, 1) k_chain(const StageArgs<T> a
         return;
     }
     const int s = a.tab.s, n = (int)a.ph.n;
-    const int nblk = (n + CHAIN_THREADS - 1) / CHAIN_THREADS;
+    const int nblk = (n + ST_THREADS - 1) / ST_THREADS;
     T err = 0;
     for (int k = a.k; k < s; ++k) {
         const bool last = k == s - 1;
@@ -2259,7 +2257,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS, 1) k_chain(const StageArgs<T> a
         load_stage_coef(st, k, S);
         __syncthreads();
         for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-            const T e = stage_cell(a, st, k, last, true, false, blk * CHAIN_THREADS + (int)threadIdx.x, S);
+            const T e = stage_cell(a, st, k, last, true, false, blk * ST_THREADS + (int)threadIdx.x, S);
             err = fmax(err, e);
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
@@ -2788,8 +2786,8 @@ void stage_t(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime, cudaGraph
         // stages k .. s-1 in one cooperative launch, the grid within what is
         // resident at once
         cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3((unsigned)std::min((int)((c->n + CHAIN_THREADS - 1) / CHAIN_THREADS), c->chain_grid));
-        cfg.blockDim = dim3(CHAIN_THREADS);
+        cfg.gridDim = dim3((unsigned)std::min(grid, c->chain_grid));
+        cfg.blockDim = dim3(ST_THREADS);
         cfg.dynamicSmemBytes = 0;
         cfg.stream = s;
         cudaLaunchAttribute at[1];
