@@ -107,9 +107,6 @@ struct mmx_ctx {
     // device buffers (element type per precision)
     void *m[2], *Y[2], *F, *G, *hist, *S, *K, *twx, *twy, *twz;
     void *Tb;    // split y/z path: y spectrum [kx][c nz + z][Py] (complex)
-    unsigned *bar;   // grid barrier words of the chain kernel
-    bool chain;      // extrapolated attempts run stages 1 .. s-1 as one cooperative launch
-    int chain_grid;  // resident CTAs of the chain kernel
     bool split;  // the y-z column does not fit one CTA: YF, ZM, YI instead of YZ
     bool cluster;     // ... and a thread-block cluster per kx column runs it instead (YZC)
     int yzc_C, yzc_W; // cluster size and z sub-tile width of YZC
@@ -149,10 +146,6 @@ void mmxk_demag(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int 
                 const void *src, int dst_mode, void *dst, const void *self_src);
 void mmxk_stage(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime_graph,
                 cudaGraphConditionalHandle cond, int use_cond);
-// stages k0 .. s-1 of an extrapolated attempt in one cooperative launch
-void mmxk_chain(mmx_ctx *c, cudaStream_t s, int k0, cudaGraphConditionalHandle cond, int use_cond);
-// sets chain_grid (resident CTAs of the chain kernel; 0: no cooperative launch)
-int mmxk_chain_plan(mmx_ctx *c);
 // rows per CTA of the plain x passes: the default, and setting a candidate
 // (raises the kernels' shared-memory limit; MMX_ERR_ARG if it does not fit)
 int mmxk_default_trows(const mmx_ctx *c);

@@ -165,29 +165,3 @@ void mmxk_stage(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime_graph, 
     else
         stage_t<float>(c, s, k, extrap, prime_graph, cond, use_cond);
 }
-
-void mmxk_chain(mmx_ctx *c, cudaStream_t s, int k0, cudaGraphConditionalHandle cond, int use_cond)
-{
-    if (c->prec == MMX_FP64)
-        stage_t<double>(c, s, k0, 1, 0, cond, use_cond, true);
-    else
-        stage_t<float>(c, s, k0, 1, 0, cond, use_cond, true);
-}
-
-int mmxk_chain_plan(mmx_ctx *c)
-{
-    c->chain_grid = 0;
-    int dev = 0, coop = 0, nsm = 0, per = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    const void *fn = c->prec == MMX_FP64 ? (const void *)k_chain<double> : (const void *)k_chain<float>;
-    if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, ST_THREADS, 0) != cudaSuccess || per < 1) {
-        cudaGetLastError();
-        return 0;
-    }
-    c->chain_grid = per * nsm;
-    return 0;
-}

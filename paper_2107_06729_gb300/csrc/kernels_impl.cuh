@@ -1753,7 +1753,6 @@ template <typename T> struct PhysT {
 
 template <typename T> struct StageArgs {
     T *m0, *m1, *Y0, *Y1, *F, *G, *hist;
-    unsigned *bar;  // k_chain: grid barrier counter and generation
     DevState *st;
     TabArgs tab;
     PhysArgs ph;
@@ -1969,47 +1968,48 @@ template <typename T> __device__ void controller(const StageArgs<T> &a, DevState
     if (a.use_cond) cudaGraphSetConditional(a.cond, (unsigned)more);
 }
 
-// The coefficients of one stage in shared memory (FP32 or FP64 copies).
-template <typename T> struct StageSmem {
-    T w[MMX_NHIST];     // Eq. 6 weights
-    T H[3];             // applied field at t0 + a_k h
-    T cb[MMX_MAXS];     // h b_{k+1,l}  or  h c_l (last stage)
-    T ce[MMX_MAXS];     // h (c_l - c_hat_l) (last stage)
-};
-
-template <typename T> __device__ __forceinline__ void load_stage_coef(const DevState *st, int k, StageSmem<T> &S)
+template <typename T>
+__global__ void __launch_bounds__(ST_THREADS, 4) k_stage(const StageArgs<T> a)
 {
+    pdl_entry();
+    __shared__ T s_w[MMX_NHIST];       // Eq. 6 weights
+    __shared__ T s_H[3];               // applied field at t0 + a_k h
+    __shared__ T s_cb[MMX_MAXS];       // h b_{k+1,l}  or  h c_l (last stage)
+    __shared__ T s_ce[MMX_MAXS];       // h (c_l - c_hat_l) (last stage)
+    __shared__ T s_red[ST_THREADS / 32];
+    __shared__ int s_last;
+    __shared__ double s_sig[MMX_NHIST], s_iden[MMX_NHIST];
+    DevState *st = a.st;
+    if (st->done) {
+        if (a.last && a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
+        return;
+    }
+    const int k = a.k;
+    const int n = (int)a.ph.n;
+    const int cur = st->cur, fbase = st->fbase, head = st->head;
+    const bool f1v = (k == 0) && st->f1_valid;
+    const bool ext = a.extrap && k > 0;
+    const int np1 = a.ctl.p + 1;
+    const int s = a.tab.s;
     if (threadIdx.x < 32) {
         const StageCoef &C = st->coef[k];
         const int l = threadIdx.x;
         if (l < MMX_MAXS) {
-            S.cb[l] = (sizeof(T) == 4) ? (T)C.cbf[l] : (T)C.cb[l];
-            S.ce[l] = (sizeof(T) == 4) ? (T)C.cef[l] : (T)C.ce[l];
+            s_cb[l] = (sizeof(T) == 4) ? (T)C.cbf[l] : (T)C.cb[l];
+            s_ce[l] = (sizeof(T) == 4) ? (T)C.cef[l] : (T)C.ce[l];
         }
-        if (l < MMX_NHIST) S.w[l] = (sizeof(T) == 4) ? (T)C.wf[l] : (T)C.w[l];
-        if (l < 3) S.H[l] = (sizeof(T) == 4) ? (T)C.Hf[l] : (T)C.H[l];
+        if (l < MMX_NHIST) s_w[l] = (sizeof(T) == 4) ? (T)C.wf[l] : (T)C.w[l];
+        if (l < 3) s_H[l] = (sizeof(T) == 4) ? (T)C.Hf[l] : (T)C.H[l];
     }
-}
-
-// Stage k for cell i: F_k = F(t0 + a_k h, Y_k) with the exact field G (or
-// the history slot at stage 1) or, with ext, the Eq. 6 extrapolation; then
-// Y_{k+1} = m0 + h sum_{l<=k} b_{k+1,l} F_l (Eq. 4), or on the last stage
-// the propagated solution (Eq. 3), renormalised, and its embedded
-// difference.  Returns the cell's error norm on the last stage, else 0.
-template <typename T>
-__device__ __forceinline__ T stage_cell(const StageArgs<T> &a, const DevState *st, int k, bool last, bool ext, bool f1v,
-                                        int i, const StageSmem<T> &S)
-{
-    const int n = (int)a.ph.n;
-    const int cur = st->cur, fbase = st->fbase, head = st->head;
-    const int np1 = a.ctl.p + 1;
-    const int s = a.tab.s;
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < n;
     const int ns = a.ctl.nslots;
     const size_t fstride = (size_t)3 * n;
     T *Fk = a.F + (size_t)((fbase + k) % ns) * fstride;
     const T *m0 = cur ? a.m1 : a.m0;
     const PhysT<T> &P = a.pt;
+    const bool last = a.last != 0;
     // Part of Eq. 4 (next stage input) or Eq. 3 (solution, embedded
     // difference) that does not involve F_k: issued first so that these
     // loads overlap the field evaluation.
@@ -2024,7 +2024,7 @@ __device__ __forceinline__ T stage_cell(const StageArgs<T> &a, const DevState *s
             const bool use = last ? (a.tab.c[l] != 0.0 || a.tab.e[l] != 0.0) : (a.tab.b[k + 1][l] != 0.0);
             if (!use) continue;
             const T *Fl = a.F + (size_t)((fbase + l) % ns) * fstride;
-            const T cb = S.cb[l], ce = S.ce[l];
+            const T cb = s_cb[l], ce = s_ce[l];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const T v = Fl[c * n + i];
@@ -2034,9 +2034,9 @@ __device__ __forceinline__ T stage_cell(const StageArgs<T> &a, const DevState *s
         }
         // ABM2: F_{n-1} in slot s enters the predictor and the error (its
         // coefficients are zero, and the slot unread, on a restart)
-        if (a.tab.abm && (S.cb[s] != (T)0 || S.ce[s] != (T)0)) {
+        if (a.tab.abm && (s_cb[s] != (T)0 || s_ce[s] != (T)0)) {
             const T *Fp = a.F + (size_t)((fbase + s) % ns) * fstride;
-            const T cb = S.cb[s], ce = S.ce[s];
+            const T cb = s_cb[s], ce = s_ce[s];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const T v = Fp[c * n + i];
@@ -2074,7 +2074,7 @@ __device__ __forceinline__ T stage_cell(const StageArgs<T> &a, const DevState *s
                 for (int j = 0; j < MMX_NHIST; ++j) {
                     if (j >= np1) break;
                     const T *Gj = a.hist + (size_t)j * fstride;
-                    const T w = S.w[j];
+                    const T w = s_w[j];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) g[c] += w * Gj[c * n + i];
                 }
@@ -2085,7 +2085,7 @@ __device__ __forceinline__ T stage_cell(const StageArgs<T> &a, const DevState *s
             }
             const T mu = m[0] * P.ku[0] + m[1] * P.ku[1] + m[2] * P.ku[2];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) H[c] += P.can * mu * P.ku[c] + g[c] - P.msN00[c] * m[c] + S.H[c];
+            for (int c = 0; c < 3; ++c) H[c] += P.can * mu * P.ku[c] + g[c] - P.msN00[c] * m[c] + s_H[c];
             // Eq. 1 in Landau-Lifshitz form: F = -gp (m x H + alpha m x (m x H))
             const T cxh0 = m[1] * H[2] - m[2] * H[1];
             const T cxh1 = m[2] * H[0] - m[0] * H[2];
@@ -2105,9 +2105,10 @@ __device__ __forceinline__ T stage_cell(const StageArgs<T> &a, const DevState *s
         if (valid) {
             T *Yn = ((k + 1) & 1) ? a.Y1 : a.Y0;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) Yn[c * n + i] = acc[c] + S.cb[k] * f[c];
+            for (int c = 0; c < 3; ++c) Yn[c * n + i] = acc[c] + s_cb[k] * f[c];
         }
-        return (T)0;
+        if (ext && blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
+        return;
     }
     // Eq. 3: propagated solution, embedded difference, renormalisation
     T err = 0;
@@ -2115,8 +2116,8 @@ __device__ __forceinline__ T stage_cell(const StageArgs<T> &a, const DevState *s
         T M[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            M[c] = acc[c] + S.cb[s - 1] * f[c];
-            E[c] += S.ce[s - 1] * f[c];
+            M[c] = acc[c] + s_cb[s - 1] * f[c];
+            E[c] += s_ce[s - 1] * f[c];
         }
         const T r = sqrt(M[0] * M[0] + M[1] * M[1] + M[2] * M[2]);
         const T inv = (T)1 / r;
@@ -2126,18 +2127,7 @@ __device__ __forceinline__ T stage_cell(const StageArgs<T> &a, const DevState *s
         err = sqrt(E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
         if (!(err <= (T)3.0e38) || !(r == r) || r == (T)0) err = (T)INFINITY;
     }
-    return err;
-}
-
-// Last stage, after the cells: the CTA's maximum error goes to the device
-// state; the last CTA to finish runs the controller (Eq. 5) and prepares
-// the next attempt's coefficients, on a shared-memory copy of the state (one
-// coalesced read and one write-back instead of dozens of dependent global
-// round trips).
-template <typename T>
-__device__ __forceinline__ void stage_finish(const StageArgs<T> &a, DevState *st, T err, T *s_red, int *s_last,
-                                             double *s_sig, double *s_iden)
-{
+    if (ext && blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
     for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
     if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = err;
     __syncthreads();
@@ -2147,10 +2137,12 @@ __device__ __forceinline__ void stage_finish(const StageArgs<T> &a, DevState *st
         atomicMax(&st->err_bits, (unsigned long long)__double_as_longlong((double)mx));
         __threadfence();
         const unsigned prev = atomicAdd(&st->blocks_done, 1u);
-        *s_last = (prev == gridDim.x - 1) ? 1 : 0;
+        s_last = (prev == gridDim.x - 1) ? 1 : 0;
     }
     __syncthreads();
-    if (*s_last) {
+    if (s_last) {
+        // the state in shared memory: one coalesced read and one write-back
+        // instead of dozens of dependent global round trips in the controller
         __shared__ __align__(16) DevState sst;
         __threadfence();
         const int nw = (int)(sizeof(DevState) / 8);
@@ -2167,103 +2159,6 @@ __device__ __forceinline__ void stage_finish(const StageArgs<T> &a, DevState *st
         __syncthreads();
         for (int i = threadIdx.x; i < nw; i += blockDim.x) gw[i] = sw[i];
     }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(ST_THREADS, 4) k_stage(const StageArgs<T> a)
-{
-    pdl_entry();
-    __shared__ StageSmem<T> S;
-    __shared__ T s_red[ST_THREADS / 32];
-    __shared__ int s_last;
-    __shared__ double s_sig[MMX_NHIST], s_iden[MMX_NHIST];
-    DevState *st = a.st;
-    if (st->done) {
-        if (a.last && a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
-        return;
-    }
-    const int k = a.k;
-    const bool last = a.last != 0;
-    const bool ext = a.extrap && k > 0;
-    const bool f1v = (k == 0) && st->f1_valid;
-    load_stage_coef(st, k, S);
-    __syncthreads();
-    const T err = stage_cell(a, st, k, last, ext, f1v, (int)(blockIdx.x * blockDim.x + threadIdx.x), S);
-    if (ext && blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
-    if (!last) return;
-    stage_finish(a, st, err, s_red, &s_last, s_sig, s_iden);
-}
-
-// Grid-wide barrier of a cooperative launch (all CTAs resident): a counter
-// and a generation word in global memory.  The wait is bounded (1 s of
-// %globaltimer); false when it gave up.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks)
-{
-    __syncthreads();
-    int ok = 1;
-    if (threadIdx.x == 0) {
-        volatile unsigned *vgen = bar + 1;
-        const unsigned g = *vgen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            const unsigned long long t0 = global_ns();
-            while (*vgen == g) {
-                if (global_ns() - t0 > 1000000000ULL) {
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        __threadfence();
-    }
-    return __syncthreads_and(ok) != 0;
-}
-
-// Stages a.k .. s-1 of an extrapolated attempt (no demag between them) in
-// one cooperative launch: persistent CTAs walk the cell blocks of a stage,
-// a grid barrier separates the stages (stage k + 1 reads the neighbours of
-// every cell of Y_{k+1}); the last stage ends as in k_stage.  A barrier that
-// gives up sets the fault word, ends the run and the graph loop.
-template <typename T>
-__global__ void __launch_bounds__(ST_THREADS, 4) k_chain(const StageArgs<T> a)
-{
-    __shared__ StageSmem<T> S;
-    __shared__ T s_red[ST_THREADS / 32];
-    __shared__ int s_last;
-    __shared__ double s_sig[MMX_NHIST], s_iden[MMX_NHIST];
-    DevState *st = a.st;
-    if (st->done) {
-        if (a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
-        return;
-    }
-    const int s = a.tab.s, n = (int)a.ph.n;
-    const int nblk = (n + ST_THREADS - 1) / ST_THREADS;
-    T err = 0;
-    for (int k = a.k; k < s; ++k) {
-        const bool last = k == s - 1;
-        if (k > a.k && !grid_barrier(a.bar, gridDim.x)) {
-            if (threadIdx.x == 0) {
-                atomicExch(&st->fault, 3);
-                st->status = MMX_ERR_TIMEOUT;
-                st->done = 1;
-                if (a.use_cond) cudaGraphSetConditional(a.cond, 0u);
-            }
-            return;
-        }
-        load_stage_coef(st, k, S);
-        __syncthreads();
-        for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-            const T e = stage_cell(a, st, k, last, true, false, blk * ST_THREADS + (int)threadIdx.x, S);
-            err = fmax(err, e);
-        }
-        if (blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
-        __syncthreads();  // S is reloaded by the next stage
-    }
-    stage_finish(a, st, err, s_red, &s_last, s_sig, s_iden);
 }
 
 // ----------------------------------------------------------- host helpers
@@ -2741,11 +2636,9 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
 }
 
 template <typename T>
-void stage_t(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime, cudaGraphConditionalHandle cond, int use_cond,
-             bool chain = false)
+void stage_t(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime, cudaGraphConditionalHandle cond, int use_cond)
 {
     StageArgs<T> a{};
-    a.bar = c->bar;
     a.m0 = (T *)c->m[0];
     a.m1 = (T *)c->m[1];
     a.Y0 = (T *)c->Y[0];
@@ -2775,30 +2668,14 @@ void stage_t(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime, cudaGraph
     a.ctl.prime = prime;
     a.k = k;
     a.extrap = extrap;
-    a.last = chain ? 1 : (k == c->tab.s - 1);
+    a.last = (k == c->tab.s - 1);
     a.use_cond = use_cond;
     a.cond = cond;
     const int grid = (int)((c->n + ST_THREADS - 1) / ST_THREADS);
-    const int cls = (a.last && !chain) ? 4 : 3;
+    const int cls = a.last ? 4 : 3;
     if (c->profiling) cudaEventRecord(c->ev_a, s);
     void *sargs[] = {(void *)&a};
-    if (chain) {
-        // stages k .. s-1 in one cooperative launch, the grid within what is
-        // resident at once
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3((unsigned)std::min(grid, c->chain_grid));
-        cfg.blockDim = dim3(ST_THREADS);
-        cfg.dynamicSmemBytes = 0;
-        cfg.stream = s;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeCooperative;
-        at[0].val.cooperative = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        cudaLaunchKernelExC(&cfg, (const void *)k_chain<T>, sargs);
-    } else {
-        launch_k(c, (const void *)k_stage<T>, dim3(grid), dim3(ST_THREADS), sargs, 0, s);
-    }
+    launch_k(c, (const void *)k_stage<T>, dim3(grid), dim3(ST_THREADS), sargs, 0, s);
     c->launches++;
     if (c->profiling) {
         cudaEventRecord(c->ev_b, s);

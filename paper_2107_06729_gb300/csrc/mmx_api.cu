@@ -203,26 +203,12 @@ void reset_history(DevState *s)
 
 // One attempted step, launched on stream s.  prime: full demag at every
 // stage (priming or extrap_order < 0).
-// Whether an attempt (prime or extrapolated) runs its stages 1 .. s-1 as
-// one cooperative chain launch: extrapolated attempts only (no demag between
-// those stages), at least two such stages, and not inside batch graphs
-// (concurrent cooperative grids are not guaranteed to be resident together).
-bool use_chain(const mmx_ctx *c, int prime, bool allow)
-{
-    return allow && c->chain && c->ctl.p >= 0 && !prime && c->tab.s >= 3;
-}
-
-int body_kernels(mmx_ctx *c, cudaStream_t s, int prime, cudaGraphConditionalHandle cond, int use_cond,
-                 bool allow_chain = true)
+int body_kernels(mmx_ctx *c, cudaStream_t s, int prime, cudaGraphConditionalHandle cond, int use_cond)
 {
     const int p = c->ctl.p;
     const int extrap = (p >= 0 && !prime);
     mmxk_demag(c, s, c->st, 1, 1, nullptr, p >= 0 ? 1 : 0, c->G, nullptr);
     mmxk_stage(c, s, 0, extrap, prime && p >= 0, cond, use_cond);
-    if (use_chain(c, prime, allow_chain)) {
-        mmxk_chain(c, s, 1, cond, use_cond);
-        return 0;
-    }
     for (int k = 1; k < c->tab.s; ++k) {
         if (!extrap) mmxk_demag(c, s, c->st, 0, 0, c->Y[k & 1], 0, c->G, nullptr);
         mmxk_stage(c, s, k, extrap, prime && p >= 0, cond, use_cond);
@@ -230,12 +216,11 @@ int body_kernels(mmx_ctx *c, cudaStream_t s, int prime, cudaGraphConditionalHand
     return 0;
 }
 
-int kernels_per_attempt(const mmx_ctx *c, int prime, bool allow_chain = true)
+int kernels_per_attempt(const mmx_ctx *c, int prime)
 {
     const int p = c->ctl.p;
     const int extrap = (p >= 0 && !prime);
     const int nd = c->nd;  // kernels per demag evaluation
-    if (use_chain(c, prime, allow_chain)) return nd + 2;
     return extrap ? nd + c->tab.s : (nd + 1) * c->tab.s;
 }
 
@@ -603,7 +588,6 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     ok = ok && alloc(&c->twx, (size_t)c->Px * 2 * c->esz) && alloc(&c->twy, (size_t)c->Py * 2 * c->esz) &&
          alloc(&c->twz, (size_t)c->Pz * 2 * c->esz);
     ok = ok && alloc((void **)&c->st, sizeof(DevState));
-    ok = ok && alloc((void **)&c->bar, 2 * sizeof(unsigned));
     ok = ok && cudaMallocHost((void **)&c->h_st, sizeof(DevState)) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
     ok = ok && cudaEventCreate(&c->ev_a) == cudaSuccess && cudaEventCreate(&c->ev_b) == cudaSuccess;
@@ -621,12 +605,6 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     }
     cudaMemset(c->m[0], 0, fb);
     cudaMemset(c->m[1], 0, fb);
-    cudaMemset(c->bar, 0, 2 * sizeof(unsigned));
-    c->chain = false;
-    if (getenv("MMX_NO_CHAIN") == nullptr) {
-        mmxk_chain_plan(c);
-        c->chain = c->chain_grid > 0;
-    }
     cudaMemset(c->F, 0, fb * C.nslots);
     cudaMemset(c->hist, 0, fb * nh);
     // pass configuration by timing, unless forced or switched off
@@ -909,7 +887,7 @@ void mmx_destroy(mmx_ctx *c)
         }
     }
     void *bufs[] = {c->m[0], c->m[1], c->Y[0], c->Y[1], c->F, c->G, c->hist, c->S, c->K, c->twx, c->twy, c->twz, c->Tb,
-                    c->st, (void *)c->bar};
+                    c->st};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->h_st) cudaFreeHost(c->h_st);
@@ -985,7 +963,7 @@ int build_batch_graph(mmx_batch *b)
                 e = cudaStreamBeginCaptureToGraph(c->cap_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeRelaxed);
             if (e == cudaSuccess) {
-                body_kernels(c, c->cap_stream, which == 1 || c->ctl.p < 0, h, 1, false);
+                body_kernels(c, c->cap_stream, which == 1 || c->ctl.p < 0, h, 1);
                 cudaGraph_t captured;
                 e = cudaStreamEndCapture(c->cap_stream, &captured);
             }
@@ -1116,8 +1094,7 @@ int mmx_batch_run(mmx_batch *b, const double *t_end, int *status)
         c->launches += 1 + gates;
         int r = MMX_OK;
         if (b->active[i]) {
-            c->launches += pa * kernels_per_attempt(c, 1, false) +
-                           (s.run_attempts - pa) * kernels_per_attempt(c, c->ctl.p < 0, false);
+            c->launches += pa * kernels_per_attempt(c, 1) + (s.run_attempts - pa) * kernels_per_attempt(c, c->ctl.p < 0);
             if (s.fault)
                 r = fail(c, MMX_ERR_CUDA, "a bounded device wait gave up (TMA copy not completed)");
             else
