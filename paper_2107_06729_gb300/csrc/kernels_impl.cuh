@@ -733,6 +733,54 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, in
         : "memory");
 }
 
+// contiguous bulk copy global -> shared (16-byte aligned ends, size a
+// multiple of 16), completion counted on the mbarrier
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes, uint64_t *m)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(m))
+                 : "memory");
+}
+
+// One staging buffer of a persistent pass, refilled by one bulk copy per
+// work item (issued by one thread instead of a 16-byte copy per thread and
+// chunk).  Waits are bounded: on expiry the fault word is set, the copy
+// still in flight is waited for (bounded) and the caller returns.
+struct BulkStage {
+    uint64_t *mb;
+    unsigned phase;
+    __device__ __forceinline__ void init(uint64_t *m)
+    {
+        mb = m;
+        phase = 0;
+        if (threadIdx.x == 0) {
+            mbar_init(mb, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        }
+        __syncthreads();
+    }
+    __device__ __forceinline__ void issue(void *dst, const void *src, unsigned bytes)
+    {
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(mb, bytes);
+            bulk_copy(dst, src, bytes, mb);
+        }
+    }
+    // all threads: true once the copy landed
+    __device__ __forceinline__ bool wait(int *fault, unsigned long long limit_ns)
+    {
+        const bool ok = mbar_wait_bounded(mb, phase, limit_ns);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0 && fault) atomicExch(fault, 1);
+            (void)mbar_wait_bounded(mb, phase, limit_ns);
+            return false;
+        }
+        phase ^= 1u;
+        return true;
+    }
+};
+
 constexpr int XIT_ROWS = 8;  // rows per tile: four pair rows, one warp each
 constexpr unsigned long long XIT_WAIT_NS = 2000000000ULL;  // 2 s
 
@@ -992,6 +1040,7 @@ template <typename T> struct SplitArgs {
     DevState *st;
     long long rows;  // 3 ny nz
     int nx, ny, nz, Py, Pz, Hy, Hz, stage0, ry, W;
+    int *fault;  // bounded waits of the pipelined passes give up here
 };
 
 template <typename T, int PY>
@@ -1253,21 +1302,20 @@ __global__ void __launch_bounds__(256, 2) k_xf_p(const XArgs<T> a)
     const Pad<T> work{reinterpret_cast<cx<T> *>(smraw), 0};
     T *stg = reinterpret_cast<T *>(reinterpret_cast<cx<T> *>(smraw) + padded_words((size_t)np * PXS));
     const size_t bytes = (size_t)T_ * NX * sizeof(T);
+    BulkStage bs;
+    bs.init(reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(stg) + bytes));
     const int w = threadIdx.x >> 5;
     int item = blockIdx.x;
-    if (item < nitems) stage_copy(stg, src + (size_t)item * T_ * NX, bytes);
-    cp_async_commit();
+    if (item < nitems) bs.issue(stg, src + (size_t)item * T_ * NX, (unsigned)bytes);
     for (; item < nitems; item += gridDim.x) {
-        cp_async_wait0();
-        __syncthreads();
+        if (!bs.wait(a.fault, XIT_WAIT_NS)) return;
         if (w < np) {
             const XPairView<T> v{stg + (size_t)(2 * w) * NX, stg + (size_t)(2 * w + 1) * NX};
             WarpFFT<T, false, PX, 1>::first(v, work.at(w * PXS), 1, a.tw, true, false);
         }
         __syncthreads();  // staging consumed: prefetch the next item behind the remaining stages
         const int next = item + gridDim.x;
-        if (next < nitems) stage_copy(stg, src + (size_t)next * T_ * NX, bytes);
-        cp_async_commit();
+        if (next < nitems) bs.issue(stg, src + (size_t)next * T_ * NX, (unsigned)bytes);
         if (w < np) WarpFFT<T, false, PX, 1>::rest(work.at(w * PXS), 1, a.tw, true, false);
         __syncthreads();
         const long long r0 = (long long)item * T_;
@@ -1308,19 +1356,18 @@ __global__ void __launch_bounds__(256, 2) k_yf_p(const SplitArgs<T> a)
         const int kx = itm / nby, rb = itm - kx * nby;
         return a.S + (size_t)kx * a.rows + (size_t)rb * ry * NY;
     };
+    BulkStage bs;
+    bs.init(reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(stg) + bytes));
     const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int item = blockIdx.x;
-    if (item < nitems) stage_copy(stg, srcp(item), bytes);
-    cp_async_commit();
+    if (item < nitems) bs.issue(stg, srcp(item), (unsigned)bytes);
     for (; item < nitems; item += gridDim.x) {
-        cp_async_wait0();
-        __syncthreads();
+        if (!bs.wait(a.fault, XIT_WAIT_NS)) return;
         const Lin<T> sb{stg, 0};
         for (int r = w; r < ry; r += nw) WarpFFT<T, false, PY, 1>::first(sb.at(r * NY), work.at(r * PY), 1, a.twy, true, false);
         __syncthreads();
         const int next = item + gridDim.x;
-        if (next < nitems) stage_copy(stg, srcp(next), bytes);
-        cp_async_commit();
+        if (next < nitems) bs.issue(stg, srcp(next), (unsigned)bytes);
         for (int r = w; r < ry; r += nw) WarpFFT<T, false, PY, 1>::rest(work.at(r * PY), 1, a.twy, true, false);
         __syncthreads();
         const int kx = item / nby, rb = item - kx * nby;
@@ -1366,13 +1413,13 @@ __global__ void __launch_bounds__(256, 2) k_yi_p(const SplitArgs<T> a)
         const int kx = itm / nby, rb = itm - kx * nby;
         return a.Tb + ((size_t)kx * nrows + (size_t)rb * ry) * PY;
     };
+    BulkStage bs;
+    bs.init(reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(stg) + bytes));
     const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int item = blockIdx.x;
-    if (item < nitems) stage_copy(stg, srcp(item), bytes);
-    cp_async_commit();
+    if (item < nitems) bs.issue(stg, srcp(item), (unsigned)bytes);
     for (; item < nitems; item += gridDim.x) {
-        cp_async_wait0();
-        __syncthreads();
+        if (!bs.wait(a.fault, XIT_WAIT_NS)) return;
         const int kx = item / nby, rb = item - kx * nby;
         for (int r = w; r < ry; r += nw) {
             if (kx != 0)
@@ -1383,8 +1430,7 @@ __global__ void __launch_bounds__(256, 2) k_yi_p(const SplitArgs<T> a)
         }
         __syncthreads();
         const int next = item + gridDim.x;
-        if (next < nitems) stage_copy(stg, srcp(next), bytes);
-        cp_async_commit();
+        if (next < nitems) bs.issue(stg, srcp(next), (unsigned)bytes);
         for (int r = w; r < ry; r += nw) WarpFFT<T, true, PY, 1>::rest(work.at(r * PY), 1, a.twy, false, true);
         __syncthreads();
         cx<T> *dst = a.S + (size_t)kx * a.rows + (size_t)rb * ry * NY;
@@ -2334,17 +2380,18 @@ template <typename T> int pipe_ry(const mmx_ctx *c)
 }
 template <typename T> size_t xfp_smem(const mmx_ctx *c)
 {
-    return padded_words((size_t)(XF_P_ROWS / 2) * (c->Px + XPAIR_GAP)) * sizeof(cx<T>) + (size_t)XF_P_ROWS * c->nx * sizeof(T);
+    return padded_words((size_t)(XF_P_ROWS / 2) * (c->Px + XPAIR_GAP)) * sizeof(cx<T>) + (size_t)XF_P_ROWS * c->nx * sizeof(T) +
+           16;  // + the staging mbarrier
 }
 template <typename T> size_t yfp_smem(const mmx_ctx *c)
 {
     const int ry = pipe_ry<T>(c);
-    return padded_words((size_t)ry * c->Py) * sizeof(cx<T>) + (size_t)ry * (c->Py / 2) * sizeof(cx<T>);
+    return padded_words((size_t)ry * c->Py) * sizeof(cx<T>) + (size_t)ry * (c->Py / 2) * sizeof(cx<T>) + 16;
 }
 template <typename T> size_t yip_smem(const mmx_ctx *c)
 {
     const int ry = pipe_ry<T>(c);
-    return padded_words((size_t)ry * c->Py) * sizeof(cx<T>) + (size_t)ry * c->Py * sizeof(cx<T>);
+    return padded_words((size_t)ry * c->Py) * sizeof(cx<T>) + (size_t)ry * c->Py * sizeof(cx<T>) + 16;
 }
 template <typename T> size_t zmp_smem(const mmx_ctx *c)
 {
@@ -2454,7 +2501,7 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
     xa.dst_mode = dst_mode;
     xa.plane = c->ny * c->nz;
     for (int i = 0; i < 3; ++i) xa.msN00[i] = c->ph.msN00[i];
-    xa.fault = c->xi_tma ? &c->st->fault : nullptr;
+    xa.fault = c->allow_tma ? &c->st->fault : nullptr;
     const int xgrid = (int)((c->rows + trows - 1) / trows);
     const size_t xs = x_smem<T>(c, trows);
 
@@ -2561,6 +2608,7 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
         sa.stage0 = stage0;
         sa.ry = pipe_ry<T>(c);
         sa.W = split_w(c);
+        sa.fault = c->allow_tma ? &c->st->fault : nullptr;
         void *sargs[] = {(void *)&sa};
         const int txf = 32 * (XF_P_ROWS / 2);
         const int tyy = 32 * std::max(2, sa.ry);
