@@ -173,8 +173,6 @@ int mmx_get_profile(mmx_ctx *ctx, double *ms, long long *launches);
  * life of the process.  The candidates:
  *   x_rows   rows of the x transforms per CTA in the plain x passes (2-16);
  *   xi_tma   inverse x pass fed by tensor-memory-access tile copies (FP32);
- *   zm_tma   z pass of the split path fed by tensor-memory-access tiles
- *            (FP32, persistent, the next tile's copy overlapping the work);
  *   yz_pass  0: one CTA transforms a whole y-z column (meshes where it
  *            fits); 1: split y / z passes through an HBM y spectrum;
  *            2: one thread-block cluster of cluster_ctas CTAs per column,
@@ -188,7 +186,6 @@ typedef struct {
     int cluster_ctas;
     int tuned;
     int kernels_per_demag;
-    int zm_tma;
     double demag_us;
 } mmx_plan;
 int mmx_get_plan(const mmx_ctx *ctx, mmx_plan *out);

@@ -9,7 +9,6 @@ const void *mmxk_tab_pipe(int kind, bool f64, int L)
     case K_YIP: return f64 ? yip_fn<double>(L) : yip_fn<float>(L);
     case K_ZMP: return f64 ? zmp_fn<double>(L) : zmp_fn<float>(L);
     case K_XIT: return f64 ? nullptr : xit_fn<float>(L);
-    case K_ZMT: return f64 ? nullptr : zmt_fn<float>(L);
     }
     return nullptr;
 }

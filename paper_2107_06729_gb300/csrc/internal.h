@@ -119,9 +119,6 @@ struct mmx_ctx {
     bool tuned;       // pass configuration chosen by timing (autotuner)
     double demag_us;  // timed exact evaluation of the chosen configuration
     CUtensorMap xi_tmap;  // the x spectrum S as [nx][rows] 8-byte words
-    bool zm_tma_ok;   // the TMA ZM is set up for this mesh
-    bool zm_tma;      // ZM runs with TMA tiles
-    CUtensorMap zm_tmap;  // the y spectrum Tb as [nx * 3 nz][Py] 8-byte words
     DevState *st;
     DevState *h_st;  // pinned host mirror
     // graphs: [0] main loop, [1] priming loop

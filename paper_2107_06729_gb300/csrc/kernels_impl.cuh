@@ -44,7 +44,7 @@
 #include "internal.h"
 
 // kernel families, instantiated in separate translation units
-enum MmxKernelKind { K_XF, K_XI, K_YZ, K_YF, K_YI, K_ZM, K_XFP, K_YFP, K_YIP, K_ZMP, K_ZMR, K_XIT, K_ZMT };
+enum MmxKernelKind { K_XF, K_XI, K_YZ, K_YF, K_YI, K_ZM, K_XFP, K_YFP, K_YIP, K_ZMP, K_ZMR, K_XIT };
 // pointer to the instance of `kind` for precision (f64) and transform length L
 const void *mmxk_kernel(int kind, bool f64, int L);
 // the cluster-fused y-z pass (FP32) for lengths Py and Pz, or NULL
@@ -1544,14 +1544,32 @@ __global__ void __launch_bounds__(YZ_THREADS, 2) k_zm_p(const SplitArgs<T> a)
 // coalesced), transforms it in registers, and exchanges with the other two
 // components only through a [c][kz][w] tile for the tensor multiply
 // (consecutive threads touch consecutive words: no bank conflicts).
-// Eq. 2 in Fourier space for one ZM tile (kx, slots ky0 .. ky0 + W) held as
-// B[c][kz][w]: H = K M with the symmetric 6-component tensor; the packed
-// kx = 0 column (kx = 0 in slots below Py/2, kx = nx above) and its slots 0
-// and Py/2, where both share a slot, as in YZ.
 template <typename T, int PZ>
-__device__ __forceinline__ void zm_multiply(cx<T> *B, const SplitArgs<T> &a, int kx, int ky0, int W, int lgW)
+__global__ void __launch_bounds__(192, 4) k_zm_r(const SplitArgs<T> a)
 {
-    const int Py = a.Py, Pz = PZ, plane = PZ * W;
+    pdl_entry();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<T> *B = reinterpret_cast<cx<T> *>(smraw);
+    if (a.st) {
+        if (a.st->done) return;
+        if (a.stage0 && a.st->f1_valid) return;
+    }
+    const int W = a.W, Py = a.Py, nz = a.nz, Pz = PZ;
+    const int lgW = ilog2(W);
+    const int nrows = 3 * nz, plane = PZ * W;
+    // ky tiles of one kx column are adjacent in launch order, so the tensor
+    // records shared by ky and Py - ky (and the column's rows) are read from
+    // L2 by the second tile instead of DRAM
+    const int kx = blockIdx.y, ky0 = blockIdx.x * W;
+    const int c = threadIdx.x >> lgW, w = threadIdx.x & (W - 1);
+    cx<T> *g = a.Tb + ((size_t)kx * nrows + (size_t)c * nz) * Py + ky0 + w;
+    cx<T> v[PZ];
+#pragma unroll
+    for (int z = 0; z < PZ; ++z) v[z] = z < PZ / 2 ? g[(size_t)z * Py] : mk<T>(0, 0);  // Pz = 2 nz
+    RegFFT<T, PZ, 1, false>::run(v, a.twz);
+#pragma unroll
+    for (int kz = 0; kz < PZ; ++kz) B[c * plane + kz * W + w] = v[kz];
+    __syncthreads();
     const int half = Py >> 1;
 #pragma unroll 4
     for (int q = threadIdx.x; q < plane; q += blockDim.x) {
@@ -1598,35 +1616,6 @@ __device__ __forceinline__ void zm_multiply(cx<T> *B, const SplitArgs<T> &a, int
             }
         }
     }
-}
-
-template <typename T, int PZ>
-__global__ void __launch_bounds__(192, 4) k_zm_r(const SplitArgs<T> a)
-{
-    pdl_entry();
-    extern __shared__ __align__(16) unsigned char smraw[];
-    cx<T> *B = reinterpret_cast<cx<T> *>(smraw);
-    if (a.st) {
-        if (a.st->done) return;
-        if (a.stage0 && a.st->f1_valid) return;
-    }
-    const int W = a.W, Py = a.Py, nz = a.nz, Pz = PZ;
-    const int lgW = ilog2(W);
-    const int nrows = 3 * nz, plane = PZ * W;
-    // ky tiles of one kx column are adjacent in launch order, so the tensor
-    // records shared by ky and Py - ky (and the column's rows) are read from
-    // L2 by the second tile instead of DRAM
-    const int kx = blockIdx.y, ky0 = blockIdx.x * W;
-    const int c = threadIdx.x >> lgW, w = threadIdx.x & (W - 1);
-    cx<T> *g = a.Tb + ((size_t)kx * nrows + (size_t)c * nz) * Py + ky0 + w;
-    cx<T> v[PZ];
-#pragma unroll
-    for (int z = 0; z < PZ; ++z) v[z] = z < PZ / 2 ? g[(size_t)z * Py] : mk<T>(0, 0);  // Pz = 2 nz
-    RegFFT<T, PZ, 1, false>::run(v, a.twz);
-#pragma unroll
-    for (int kz = 0; kz < PZ; ++kz) B[c * plane + kz * W + w] = v[kz];
-    __syncthreads();
-    zm_multiply<T, PZ>(B, a, kx, ky0, W, lgW);
     __syncthreads();
 #pragma unroll
     for (int kz = 0; kz < PZ; ++kz) v[kz] = B[c * plane + kz * W + w];
@@ -1634,79 +1623,6 @@ __global__ void __launch_bounds__(192, 4) k_zm_r(const SplitArgs<T> a)
 #pragma unroll
     for (int z = 0; z < PZ; ++z)
         if (z < PZ / 2) g[(size_t)z * Py] = v[z];
-}
-
-// ZM with tensor-memory-access tiles (FP32): persistent CTAs walk the
-// (kx, ky tile) items, ky tiles of a column adjacent; the 3 nz x W tile of
-// an item (its rows c nz + z, slots ky0 .. ky0 + W) arrives by one 2-D
-// tensor copy, and the next item's copy is issued as soon as the tile is in
-// registers, so it overlaps the transforms, the multiply and the stores.
-// The wait is bounded (fault word).
-template <typename T, int PZ>
-__global__ void __launch_bounds__(192, 3) k_zm_t(const SplitArgs<T> a, const __grid_constant__ CUtensorMap tm)
-{
-    pdl_entry();
-    static_assert(sizeof(T) == 4, "TMA ZM: FP32 spectrum (8-byte elements)");
-    extern __shared__ __align__(1024) unsigned char smzt[];
-    if (a.st) {
-        if (a.st->done) return;
-        if (a.stage0 && a.st->f1_valid) return;
-    }
-    constexpr int NZ = PZ / 2;  // Pz = 2 nz
-    const int W = a.W, Py = a.Py, lgW = ilog2(W);
-    const int nrows = 3 * NZ, plane = PZ * W, ntile = Py / W;
-    const int nitems = a.nx * ntile;
-    cx<T> *tile = reinterpret_cast<cx<T> *>(smzt);  // [nrows][W], written by the tensor copy
-    cx<T> *B = tile + nrows * W;                     // [3][PZ][W]
-    uint64_t *mb = reinterpret_cast<uint64_t *>(B + 3 * plane);
-    if (smem_u32(smzt) & 127) {
-        if (threadIdx.x == 0 && a.fault) atomicExch(a.fault, 2);
-        return;
-    }
-    if (threadIdx.x == 0) {
-        mbar_init(mb, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    __syncthreads();
-    const unsigned tbytes = (unsigned)(nrows * W * sizeof(cx<T>));
-    auto issue = [&](int item) {
-        if (threadIdx.x == 0) {
-            const int kx = item / ntile, t = item - kx * ntile;
-            mbar_expect_tx(mb, tbytes);
-            tma_load_2d(tile, &tm, t * W, kx * nrows, mb);
-        }
-    };
-    if ((int)blockIdx.x < nitems) issue(blockIdx.x);
-    unsigned phase = 0;
-    const int c = threadIdx.x >> lgW, w = threadIdx.x & (W - 1);
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const bool ok = mbar_wait_bounded(mb, phase, XIT_WAIT_NS);
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0 && a.fault) atomicExch(a.fault, 1);
-            (void)mbar_wait_bounded(mb, phase, XIT_WAIT_NS);
-            return;
-        }
-        phase ^= 1u;
-        const int kx = item / ntile, ky0 = (item - kx * ntile) * W;
-        cx<T> v[PZ];
-#pragma unroll
-        for (int z = 0; z < PZ; ++z) v[z] = z < NZ ? tile[(c * NZ + z) * W + w] : mk<T>(0, 0);
-        __syncthreads();  // tile consumed: the next item's copy overlaps the rest
-        const int next = item + (int)gridDim.x;
-        if (next < nitems) issue(next);
-        RegFFT<T, PZ, 1, false>::run(v, a.twz);
-#pragma unroll
-        for (int kz = 0; kz < PZ; ++kz) B[c * plane + kz * W + w] = v[kz];
-        __syncthreads();
-        zm_multiply<T, PZ>(B, a, kx, ky0, W, lgW);
-        __syncthreads();
-#pragma unroll
-        for (int kz = 0; kz < PZ; ++kz) v[kz] = B[c * plane + kz * W + w];
-        RegFFT<T, PZ, 1, true>::run(v, a.twz);
-        cx<T> *g = a.Tb + ((size_t)kx * nrows + (size_t)c * NZ) * Py + ky0 + w;
-#pragma unroll
-        for (int z = 0; z < NZ; ++z) g[(size_t)z * Py] = v[z];
-    }
 }
 
 // ---------------------------------------------- cluster-fused y-z pass (YZC)
@@ -2422,48 +2338,6 @@ bool encode_xi_tmap(mmx_ctx *c)
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
-template <typename T> const void *zmt_fn(int L)
-{
-    if constexpr (sizeof(T) == 4) {
-        switch (L) {
-        case 4: return (const void *)k_zm_t<T, 4>;
-        case 8: return (const void *)k_zm_t<T, 8>;
-        case 16: return (const void *)k_zm_t<T, 16>;
-        case 32: return (const void *)k_zm_t<T, 32>;
-        }
-    }
-    return nullptr;
-}
-// TMA ZM: the item tile (3 nz rows x 64 slots), the multiply tile, the mbarrier
-size_t zmt_smem(const mmx_ctx *c)
-{
-    const int W = std::min(c->Py, 64);
-    return (size_t)3 * c->nz * W * sizeof(cx<float>) + (size_t)3 * c->Pz * W * sizeof(cx<float>) + 16;
-}
-// tensor map of the y spectrum Tb as [nx * 3 nz rows][Py] 8-byte words, box 64 x 3 nz
-bool encode_zm_tmap(mmx_ctx *c)
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
-    if (!enc) {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn) {
-            cudaGetLastError();
-            return false;
-        }
-        enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-    }
-    const int W = std::min(c->Py, 64);
-    const cuuint64_t dims[2] = {(cuuint64_t)c->Py, (cuuint64_t)c->nx * 3 * c->nz};
-    const cuuint64_t strides[1] = {(cuuint64_t)c->Py * 8};
-    const cuuint32_t box[2] = {(cuuint32_t)W, (cuuint32_t)(3 * c->nz)};
-    const cuuint32_t es[2] = {1, 1};
-    return enc(&c->zm_tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, c->Tb, dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
 template <typename T> const void *xfp_fn(int L)
 {
     switch (L) { MMX_PIPE_CASES(k_xf_p, T) }
@@ -2757,17 +2631,9 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
                 SplitArgs<T> sr = sa;
                 sr.W = zmr_w(c);
                 void *rargs[] = {(void *)&sr};
-                if (c->zm_tma) {
-                    const void *f = mmxk_kernel(K_ZMT, false, c->Pz);
-                    const size_t sm = zmt_smem(c);
-                    void *targs[] = {(void *)&sr, (void *)&c->zm_tmap};
-                    launch_k(c, f, dim3(persistent_grid(f, 3 * sr.W, sm, (long long)c->nx * (c->Py / sr.W))),
-                             dim3(3 * sr.W), targs, sm, s);
-                } else {
-                    const size_t s_r = (size_t)3 * c->Pz * sr.W * sizeof(cx<T>);
-                    launch_k(c, mmxk_kernel(K_ZMR, sizeof(T) == 8, c->Pz), dim3(c->Py / sr.W, c->nx),
-                             dim3(3 * sr.W), rargs, s_r, s);
-                }
+                const size_t s_r = (size_t)3 * c->Pz * sr.W * sizeof(cx<T>);
+                launch_k(c, mmxk_kernel(K_ZMR, sizeof(T) == 8, c->Pz), dim3(c->Py / sr.W, c->nx),
+                                 dim3(3 * sr.W), rargs, s_r, s);
             } else {
                 launch_k(c, f_zm, dim3(persistent_grid(f_zm, YZ_THREADS, s_zm, n_z)), dim3(YZ_THREADS), sargs,
                                  s_zm, s);
@@ -2913,13 +2779,6 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
     if (cudaMemcpy(c->twy, tw.data(), c->Py * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
     twiddles<T>(c->Pz, tw);
     if (cudaMemcpy(c->twz, tw.data(), c->Pz * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
-    c->zm_tma = c->zm_tma_ok = false;
-    if (sizeof(T) == 4 && c->allow_tma && pipe_ok<T>(c) && c->Tb && c->Pz >= 4 && c->Pz <= 32 && c->Py >= 64 &&
-        mmxk_kernel(K_ZMT, false, c->Pz) && zmt_smem(c) <= 227 * 1024 && getenv("MMX_NO_TMA") == nullptr) {
-        if (encode_zm_tmap(c) && raise_smem_limit(mmxk_kernel(K_ZMT, false, c->Pz), zmt_smem(c)))
-            c->zm_tma = c->zm_tma_ok = true;
-        cudaGetLastError();
-    }
     c->xi_tma = c->xi_tma_ok = false;
     if (sizeof(T) == 4 && c->allow_tma && c->rows % XIT_ROWS == 0 && mmxk_kernel(K_XIT, false, c->Px) &&
         xit_smem(c) <= 227 * 1024 && getenv("MMX_NO_TMA") == nullptr) {

@@ -328,7 +328,7 @@ std::shared_ptr<const std::vector<double>> tensor_for(const mmx_host_tensor_args
 // results are cached per mesh and precision for the process.
 struct Plan {
     int trows;
-    bool xi_tma, cluster, zm_tma;
+    bool xi_tma, cluster;
     double us;
 };
 struct PlanKey {
@@ -357,7 +357,6 @@ void apply_plan(mmx_ctx *c, const Plan &p)
 {
     mmxk_set_trows(c, p.trows);
     c->xi_tma = p.xi_tma && c->xi_tma_ok;
-    c->zm_tma = p.zm_tma && c->zm_tma_ok;
     c->cluster = p.cluster && c->yzc_C > 0;
     c->nd = (c->split && !c->cluster) ? 5 : 3;
     c->demag_us = p.us;
@@ -412,9 +411,8 @@ int autotune(mmx_ctx *c)
     }
     std::vector<Plan> cand;
     for (int cl = 0; cl <= (cl_ok ? 1 : 0); ++cl)
-        for (int zt = 0; zt <= ((c->zm_tma_ok && !cl) ? 1 : 0); ++zt)
-            for (int xt = 0; xt <= (c->xi_tma_ok ? 1 : 0); ++xt)
-                for (int tr : rows) cand.push_back(Plan{tr, xt == 1, cl == 1, zt == 1, 1e30});
+        for (int xt = 0; xt <= (c->xi_tma_ok ? 1 : 0); ++xt)
+            for (int tr : rows) cand.push_back(Plan{tr, xt == 1, cl == 1, 1e30});
     // bring the clocks up first (about 20 ms of evaluations), then two
     // round-robin passes over the candidates, keeping each one's minimum
     apply_plan(c, cand[0]);
@@ -430,11 +428,9 @@ int autotune(mmx_ctx *c)
         if (p.us < best.us) best = p;
     if (getenv("MMX_AUTOTUNE_LOG"))
         for (const Plan &p : cand)
-            fprintf(stderr, "mmx autotune %dx%dx%d %s: x_rows %d xi_tma %d zm_tma %d cluster %d -> %.1f us%s\n", c->nx,
-                    c->ny, c->nz, c->prec == MMX_FP64 ? "fp64" : "fp32", p.trows, (int)p.xi_tma, (int)p.zm_tma,
-                    (int)p.cluster, p.us,
-                    (&p == &best || (p.trows == best.trows && p.xi_tma == best.xi_tma && p.cluster == best.cluster &&
-                                     p.zm_tma == best.zm_tma))
+            fprintf(stderr, "mmx autotune %dx%dx%d %s: x_rows %d xi_tma %d cluster %d -> %.1f us%s\n", c->nx, c->ny,
+                    c->nz, c->prec == MMX_FP64 ? "fp64" : "fp32", p.trows, (int)p.xi_tma, (int)p.cluster, p.us,
+                    (&p == &best || (p.trows == best.trows && p.xi_tma == best.xi_tma && p.cluster == best.cluster))
                         ? "  (kept)"
                         : "");
     apply_plan(c, best);
@@ -868,7 +864,6 @@ int mmx_get_plan(const mmx_ctx *c, mmx_plan *out)
     out->x_rows = c->trows;
     out->xi_tma = c->xi_tma ? 1 : 0;
     out->cluster_ctas = c->cluster ? c->yzc_C : 0;
-    out->zm_tma = c->zm_tma ? 1 : 0;
     out->tuned = c->tuned ? 1 : 0;
     out->demag_us = c->tuned ? c->demag_us : 0.0;
     out->kernels_per_demag = c->nd;

@@ -85,7 +85,6 @@ extern "C" int mmx_demag_static(const mmx_mesh *mesh, double Ms, int precision, 
     c.pdl = false;
     c.allow_tma = false;  // no device state word to report a bounded wait in
     c.xi_tma = c.xi_tma_ok = false;
-    c.zm_tma = c.zm_tma_ok = false;
     c.st = nullptr;
     c.trows = mmxk_default_trows(&c);
     c.Tb = nullptr;

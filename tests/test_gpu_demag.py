@@ -215,24 +215,3 @@ def test_autotuned_plan_is_reported():
         assert (p["cluster_ctas"] > 1) == (p["yz_pass"] == 2)
     finally:
         big.close()
-
-
-@pytest.mark.parametrize("n,d", [((16, 128, 16), (2e-9, 2e-9, 2e-9)), ((32, 64, 4), (1e-9, 2e-9, 3e-9)),
-                                 ((32, 256, 2), (2e-9, 1e-9, 1e-9))])
-def test_split_path_with_tma_z_pass_matches_oracle(n, d, monkeypatch):
-    """FP32 split passes with the default configuration (the TMA-fed
-    persistent z pass where it applies), forced and natural."""
-    torch = pytest.importorskip("torch")
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
-    from gpu_util import gpu_context
-    monkeypatch.setenv("MMX_AUTOTUNE", "0")
-    monkeypatch.setenv("MMX_FORCE_SPLIT", "1")
-    ctx = gpu_context({"n": n, "d": d}, MAT, {}, {"method": "RK4", "h": 1e-13}, "fp32")
-    try:
-        assert ctx.plan()["zm_tma"] == 1
-    finally:
-        ctx.close()
-    m = W.m_random(n, seed=sum(n) + 21)
-    ref = O.demag_fft(O.newell_octant(*n, *d), MAT["Ms"], m)
-    assert rel_max(gpu_demag({"n": n, "d": d}, MAT, m, "fp32"), ref) < 1e-5
