@@ -1808,7 +1808,7 @@ template <typename T> struct StageArgs {
     cudaGraphConditionalHandle cond;
 };
 
-constexpr int ST_THREADS = 256;
+constexpr int ST_THREADS = 128;
 
 __device__ __forceinline__ unsigned long long global_ns()
 {
@@ -2015,7 +2015,7 @@ template <typename T> __device__ void controller(const StageArgs<T> &a, DevState
 }
 
 template <typename T>
-__global__ void __launch_bounds__(ST_THREADS, 4) k_stage(const StageArgs<T> a)
+__global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
 {
     pdl_entry();
     __shared__ T s_w[MMX_NHIST];       // Eq. 6 weights
