@@ -113,6 +113,7 @@ struct mmx_ctx {
     int nd;           // kernels per exact demag evaluation
     bool pdl;         // kernels launched as programmatic dependent launches
     bool allow_tma;   // TMA passes allowed (the context owns a fault word)
+    bool stall_test;  // MMX_TEST_STALL_TMA: the TMA XI's waits run out (failure-path test)
     bool xi_tma_ok;   // the TMA XI is set up for this mesh
     bool xi_tma;      // XI runs with TMA tile loads
     int trows;        // rows per CTA of the plain x passes

@@ -523,6 +523,8 @@ template <typename T> struct XArgs {
     int nx, trows, stage0, src_mode, dst_mode, plane;  // plane = ny*nz
     double msN00[3];
     int *fault;          // set when a bounded device wait gives up (TMA passes)
+    int stall_test;      // test only: the tile copies announce 16 bytes more than they bring, so
+                         // the bounded wait runs out (after 20 ms) and the fault path is taken
 };
 
 constexpr int X_THREADS = 128;
@@ -820,8 +822,9 @@ __global__ void __launch_bounds__(32 * XIT_ROWS / 2, 3) k_xi_t(const XArgs<T> a,
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
+    const unsigned long long wait_ns = a.stall_test ? 20000000ULL : XIT_WAIT_NS;
     auto issue = [&](int tile) {
-        mbar_expect_tx(mbar, TILE_BYTES);
+        mbar_expect_tx(mbar, TILE_BYTES + (a.stall_test ? 16u : 0u));
 #pragma unroll
         for (int j = 0; j < NB; ++j) tma_load_2d(stg + (size_t)j * BK * TR, &tm, tile * TR, j * BK, mbar);
     };
@@ -830,7 +833,7 @@ __global__ void __launch_bounds__(32 * XIT_ROWS / 2, 3) k_xi_t(const XArgs<T> a,
     unsigned phase = 0;
     bool failed = false;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const bool ok = mbar_wait_bounded(mbar, phase, XIT_WAIT_NS);
+        const bool ok = mbar_wait_bounded(mbar, phase, wait_ns);
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
@@ -868,7 +871,7 @@ __global__ void __launch_bounds__(32 * XIT_ROWS / 2, 3) k_xi_t(const XArgs<T> a,
     if (failed) {
         if (threadIdx.x == 0 && a.fault) atomicExch(a.fault, 1);
         // let a copy still in flight land before the CTA's memory goes away
-        if (pend) (void)mbar_wait_bounded(mbar, phase, XIT_WAIT_NS);
+        if (pend) (void)mbar_wait_bounded(mbar, phase, wait_ns);
         return;
     }
     if (a.st && blockIdx.x == 0 && threadIdx.x == 0) a.st->exact_evals++;
@@ -2502,6 +2505,7 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
     xa.plane = c->ny * c->nz;
     for (int i = 0; i < 3; ++i) xa.msN00[i] = c->ph.msN00[i];
     xa.fault = c->allow_tma ? &c->st->fault : nullptr;
+    xa.stall_test = c->stall_test ? 1 : 0;
     const int xgrid = (int)((c->rows + trows - 1) / trows);
     const size_t xs = x_smem<T>(c, trows);
 

@@ -502,6 +502,7 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     if (force_cluster && !c->cluster) c->split = big && c->Py >= 2;
     c->nd = (c->split && !c->cluster) ? 5 : 3;
     c->allow_tma = true;
+    c->stall_test = getenv("MMX_TEST_STALL_TMA") != nullptr;
     // programmatic dependent launches measured slower on GB300 for both the
     // film and the large box (resident waiting CTAs cost more than the launch
     // latency they hide), so they are opt-in

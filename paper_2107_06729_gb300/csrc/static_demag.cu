@@ -84,6 +84,7 @@ extern "C" int mmx_demag_static(const mmx_mesh *mesh, double Ms, int precision, 
     c.nd = 3;
     c.pdl = false;
     c.allow_tma = false;  // no device state word to report a bounded wait in
+    c.stall_test = false;
     c.xi_tma = c.xi_tma_ok = false;
     c.st = nullptr;
     c.trows = mmxk_default_trows(&c);

@@ -215,3 +215,36 @@ def test_autotuned_plan_is_reported():
         assert (p["cluster_ctas"] > 1) == (p["yz_pass"] == 2)
     finally:
         big.close()
+
+
+def test_bounded_tma_wait_runs_out_and_is_reported(monkeypatch):
+    """Failure path of the TMA passes, without a GPU fault: with the test
+    switch MMX_TEST_STALL_TMA the XI tile copies announce 16 bytes more than
+    they bring, so every mbarrier wait runs out after its 20 ms limit; the
+    kernel sets the context's fault word and returns, the host reports
+    MMX_ERR_CUDA, and the CUDA context stays usable."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2107_06729_gb300 as pkg
+    from gpu_util import gpu_context
+    n, d = (64, 32, 2), (4e-9, 4e-9, 4e-9)
+    monkeypatch.setenv("MMX_AUTOTUNE", "0")
+    monkeypatch.setenv("MMX_TEST_STALL_TMA", "1")
+    ctx = gpu_context({"n": n, "d": d}, MAT, {}, {"method": "RK4", "h": 1e-13}, "fp32")
+    try:
+        assert ctx.plan()["xi_tma"] == 1
+        m = torch.from_numpy(W.m_random(n, seed=9)).to("cuda", torch.float32)
+        H = torch.empty_like(m)
+        ctx.demag(m, H)
+        with pytest.raises(pkg.MMXError) as ei:
+            ctx.stats()
+        assert ei.value.code == pkg.MMX_ERR_CUDA and "bounded device wait" in str(ei.value)
+        x = torch.ones(4, device="cuda")
+        assert float((2 * x).sum()) == 8.0
+    finally:
+        ctx.close()
+    monkeypatch.delenv("MMX_TEST_STALL_TMA")
+    m = W.m_random(n, seed=9)
+    ref = O.demag_fft(O.newell_octant(*n, *d), MAT["Ms"], m)
+    assert rel_max(gpu_demag({"n": n, "d": d}, MAT, m, "fp32"), ref) < 1e-5
