@@ -170,3 +170,21 @@ def ensemble_config3(seed=0, n_samples=64):
             "m0": m_uniform_noise(n, direction=(np.cos(psi), np.sin(psi), 0.0), seed=m_seed),
         })
     return out
+
+
+# layer widths (cin, cout) of the learned residual net, in parameter order
+RNET_LAYERS = ((6, 32), (32, 32), (32, 32), (32, 3))
+
+
+def rnet_params(seed=0, out_scale=0.1):
+    """Seeded initial parameters of the residual net, flat float32 in the
+    library's layout (per layer W[27][cout][cin], then b[cout]): He-uniform
+    weights U(-sqrt(6/fan_in), +sqrt(6/fan_in)), fan_in = 27 cin, the last
+    layer's scaled by out_scale, small uniform biases."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    parts = []
+    for li, (ci, co) in enumerate(RNET_LAYERS):
+        lim = np.sqrt(6.0 / (27 * ci)) * (out_scale if li == len(RNET_LAYERS) - 1 else 1.0)
+        parts.append(rng.uniform(-lim, lim, size=27 * co * ci))
+        parts.append(rng.uniform(-0.01, 0.01, size=co))
+    return np.concatenate(parts).astype(np.float32)
