@@ -189,6 +189,72 @@ def large3d_demag(pkg, torch, dev, iters=20):
                     "times from event pairs around each launch" % iters}
 
 
+def bf16_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            if isinstance(d.get("bf16_tflops"), (int, float)):
+                return float(d["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+        except Exception:
+            pass
+    return 1900.0, "fallback (1.9 PFLOP/s bf16 burst, no MEASURED_PEAKS.json)"
+
+
+def residual_net(pkg, torch, dev, iters=50):
+    """The learned residual net's forward on a 128 x 128 x 4 film of 4 nm
+    cells (6 -> 32 -> 32 -> 32 -> 3 channels, 3x3x3 taps, BF16 tensor cores),
+    timed beside one exact FP32 demag evaluation of the same mesh and one
+    training step."""
+    n = (128, 128, 4)
+    nx, ny, nz = n
+    cells = nx * ny * nz
+    stream = torch.cuda.Stream(dev)
+    rng = np.random.default_rng(np.random.PCG64(0))
+    x = np.concatenate([W.m_uniform_noise(n, seed=0, noise=0.3), rng.normal(0, 0.3, (3, nz, ny, nx))])
+    mesh = {"n": n, "d": (4e-9, 4e-9, 4e-9)}
+    mat = {"Ms": 8e5, "A": 1.3e-11, "K": 0.0, "alpha": 0.02, "gamma": W.GAMMA}
+    with torch.cuda.stream(stream):
+        xd = torch.from_numpy(x).to(dev, torch.float32)
+        td = torch.zeros((3, nz, ny, nx), dtype=torch.float32, device=dev)
+        r = torch.empty((3, nz, ny, nx), dtype=torch.float32, device=dev)
+        net = pkg.RNet(cells, W.rnet_params(0), stream)
+        ctx = pkg.Context(mesh, mat, {}, {"method": "RK4", "h": 1e-13}, "fp32", stream)
+        m = xd[:3].contiguous()
+        H = torch.empty_like(m)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        for _ in range(5):
+            net.forward(xd, r)
+            ctx.demag(m, H)
+        ev[0].record(stream)
+        for _ in range(iters):
+            net.forward(xd, r)
+        ev[1].record(stream)
+        for _ in range(iters):
+            ctx.demag(m, H)
+        ev[2].record(stream)
+        net.train_step(xd, td, 1e-4)
+        ev[3].record(stream)
+        for _ in range(10):
+            pkg.mmx_rnet_train_step(net.handle, n, xd, td, 1e-4)
+        ev[4].record(stream)
+        torch.cuda.synchronize(dev)
+        fwd_s = ev[0].elapsed_time(ev[1]) / 1e3 / iters
+        dmg_s = ev[1].elapsed_time(ev[2]) / 1e3 / iters
+        trn_s = ev[3].elapsed_time(ev[4]) / 1e3 / 10
+        net.close()
+        ctx.close()
+    flops = 2.0 * cells * 27 * sum(ci * co for ci, co in W.RNET_LAYERS)
+    peak, src = bf16_peak()
+    ach = flops / fwd_s / 1e12
+    return {"workload": "residual_net_128x128x4_forward", "bound": "tensor", "achieved": round(ach, 2),
+            "peak": peak, "unit": "TFLOP/s", "frac": round(ach / peak, 4), "peak_source": src,
+            "flops_per_forward": flops, "us_per_forward": round(fwd_s * 1e6, 2),
+            "exact_demag_us_same_mesh": round(dmg_s * 1e6, 2), "train_step_us": round(trn_s * 1e6, 1),
+            "note": "4 conv launches + input pack per forward (mma.sync m16n8k16 BF16, FP32 accumulate); "
+                    "algorithmic flops of the real channel counts; inputs (1.5 MB) stay in L2"}
+
+
 def ensemble(pkg, torch, dev, chunk_ps, steps, warmup):
     """The 64-film ensemble of uneven sizes (RKF45, 4th-order extrapolation,
     FP32): every film advanced chunk_ps per step by one batch graph launch,
@@ -486,6 +552,8 @@ def run_mmx(args):
     if not args.no_ensemble:
         line["ensemble_batched"] = ensemble(pkg, torch, dev, args.chunk_ps, max(2, min(args.steps, 5)),
                                             args.warmup)
+    if not args.no_residual:
+        line["learned_residual"] = residual_net(pkg, torch, dev)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -551,6 +619,8 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true", help="skip the equal-error check")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-film batched ensemble run")
     ap.add_argument("--only-ensemble", action="store_true", help="only the 64-film batched ensemble run")
+    ap.add_argument("--no-residual", action="store_true", help="skip the learned-residual net timing")
+    ap.add_argument("--only-residual", action="store_true", help="only the learned-residual net timing")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mmx":
         args.warmup = 3
@@ -562,6 +632,11 @@ def main():
         torch.cuda.set_device(0)
         print(json.dumps({"demag_roofline_large3d": large3d_demag(pkg, torch, torch.device("cuda", 0),
                                                                   iters=args.steps)}), flush=True)
+    elif args.only_residual:
+        import torch
+        import paper_2107_06729_gb300 as pkg
+        torch.cuda.set_device(0)
+        print(json.dumps({"learned_residual": residual_net(pkg, torch, torch.device("cuda", 0))}), flush=True)
     elif args.only_ensemble:
         import torch
         import paper_2107_06729_gb300 as pkg

@@ -94,7 +94,22 @@ SIGNATURES = {
     "mmx_batch_destroy": (None, [_VP]),
     "mmx_last_error": (ctypes.c_char_p, [_VP]),
     "mmx_destroy": (None, [_VP]),
+    # learned residual correction (include/mmx_residual.h)
+    "mmx_rnet_create": (ctypes.c_int, [ctypes.c_longlong, _VP, ctypes.POINTER(_VP)]),
+    "mmx_rnet_set_params": (ctypes.c_int, [_VP, _VP]),
+    "mmx_rnet_get_params": (ctypes.c_int, [_VP, _VP]),
+    "mmx_rnet_forward": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    "mmx_rnet_train_step": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_float,
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "mmx_rnet_get_grads": (ctypes.c_int, [_VP, _VP]),
+    "mmx_rnet_get_activation": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_size_t]),
+    "mmx_rnet_last_error": (ctypes.c_char_p, [_VP]),
+    "mmx_rnet_destroy": (None, [_VP]),
+    "mmx_residual_sample": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_double), _VP,
+                                           ctypes.c_double, _VP, _VP]),
 }
+
+MMX_RNET_PARAMS = 63171
 
 _lib = None
 
@@ -258,6 +273,130 @@ def mmx_last_error(ctx=None):
 def mmx_destroy(ctx):
     if ctx:
         lib().mmx_destroy(ctx)
+
+
+# ------------------------------------------- learned residual (mmx_residual.h) --
+def _rcheck(rc, net):
+    if rc < 0:
+        raise MMXError(rc, mmx_rnet_last_error(net))
+    return rc
+
+
+def mmx_rnet_create(max_cells, cuda_stream=None):
+    out = _VP()
+    rc = lib().mmx_rnet_create(int(max_cells), cuda_stream, ctypes.byref(out))
+    if rc < 0:
+        raise MMXError(rc, "mmx_rnet_create failed")
+    return out.value
+
+
+def mmx_rnet_set_params(net, params):
+    """params: host float32 array of MMX_RNET_PARAMS values."""
+    return _rcheck(lib().mmx_rnet_set_params(net, _ptr(params)), net)
+
+
+def mmx_rnet_get_params(net, params):
+    return _rcheck(lib().mmx_rnet_get_params(net, _ptr(params)), net)
+
+
+def mmx_rnet_forward(net, n, x_dev, r_dev=None):
+    """n = (nx, ny, nz); x_dev float32 [6][cells], r_dev float32 [3][cells] or None."""
+    return _rcheck(lib().mmx_rnet_forward(net, *n, _ptr(x_dev), _ptr(r_dev) if r_dev is not None else None), net)
+
+
+def mmx_rnet_train_step(net, n, x_dev, target_dev, lr):
+    """One Adam step; returns the loss before the update."""
+    loss = ctypes.c_double()
+    _rcheck(lib().mmx_rnet_train_step(net, *n, _ptr(x_dev), _ptr(target_dev), float(lr), ctypes.byref(loss)), net)
+    return loss.value
+
+
+def mmx_rnet_get_grads(net, grads):
+    return _rcheck(lib().mmx_rnet_get_grads(net, _ptr(grads)), net)
+
+
+def mmx_rnet_get_activation(net, layer, dst):
+    """dst: host array (uint16 for layers 0-3, float32 for layer 4) of the exact size."""
+    return _rcheck(lib().mmx_rnet_get_activation(net, int(layer), _ptr(dst), dst.nbytes), net)
+
+
+def mmx_rnet_last_error(net=None):
+    msg = lib().mmx_rnet_last_error(net)
+    return msg.decode() if msg else ""
+
+
+def mmx_rnet_destroy(net):
+    if net:
+        lib().mmx_rnet_destroy(net)
+
+
+def mmx_residual_sample(ctx, p, m_nodes_dev, t_nodes, m_dev, t, x_dev, target_dev):
+    """Training pair (x, target) of the residual net from ctx's exact demag."""
+    tn = (ctypes.c_double * (p + 1))(*[float(v) for v in t_nodes])
+    rc = lib().mmx_residual_sample(ctx, int(p), _ptr(m_nodes_dev), tn, _ptr(m_dev), float(t), _ptr(x_dev),
+                                   _ptr(target_dev))
+    return _check(rc, ctx)
+
+
+class RNet:
+    """Owner of one residual net (the C calls above underneath)."""
+
+    def __init__(self, max_cells, params=None, stream=None):
+        handle = stream
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            handle = stream.cuda_stream
+        self.handle = mmx_rnet_create(max_cells, handle)
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, params):
+        import numpy as np
+        mmx_rnet_set_params(self.handle, np.ascontiguousarray(params, dtype=np.float32))
+
+    def params(self):
+        import numpy as np
+        out = np.empty(MMX_RNET_PARAMS, dtype=np.float32)
+        mmx_rnet_get_params(self.handle, out)
+        return out
+
+    def grads(self):
+        import numpy as np
+        out = np.empty(MMX_RNET_PARAMS, dtype=np.float32)
+        mmx_rnet_get_grads(self.handle, out)
+        return out
+
+    def forward(self, x, r=None):
+        """x: CUDA float32 tensor [6, nz, ny, nx]; returns r [3, nz, ny, nx]."""
+        if r is None:
+            r = x.new_empty((3,) + tuple(x.shape[1:]))
+        mmx_rnet_forward(self.handle, (x.shape[3], x.shape[2], x.shape[1]), x, r)
+        return r
+
+    def train_step(self, x, target, lr):
+        return mmx_rnet_train_step(self.handle, (x.shape[3], x.shape[2], x.shape[1]), x, target, lr)
+
+    def activation(self, layer, cells):
+        """Layer 0-3: the BF16 input of that layer as float32 [cells, channels];
+        layer 4: the output r as float32 [3, cells]."""
+        import numpy as np
+        if layer == 4:
+            out = np.empty((3, cells), dtype=np.float32)
+            mmx_rnet_get_activation(self.handle, 4, out)
+            return out
+        raw = np.empty((cells, 16 if layer == 0 else 32), dtype=np.uint16)
+        mmx_rnet_get_activation(self.handle, layer, raw)
+        return (raw.astype(np.uint32) << 16).view(np.float32)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mmx_rnet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------- marshalling --

@@ -1,0 +1,641 @@
+// Learned residual correction of the extrapolated demag field (declared in
+// include/mmx_residual.h).  The paper's extrapolation (Sec. II, Eq. 6) has
+// no learned part; this net predicts its error from the stage state.
+//
+// Forward: each 3x3x3 layer is an implicit GEMM, M = cells, N = output
+// channels, K = 27 taps x input channels, on the tensor cores
+// (mma.sync m16n8k16, BF16 operands, FP32 accumulation).  A CTA takes a
+// 32 (x) x 4 (y) tile of cells at one z; it stages the input halo
+// (34 x 6 x 3 cells, channels last, padded by 8 channels so that the eight
+// 16-byte rows an ldmatrix phase reads fall in distinct banks) in shared
+// memory once and feeds every tap's A fragments from it with ldmatrix; the
+// B fragments (weights [tap][cout][cin], 55 KB for a hidden layer) come
+// through L1.  Bias, ReLU and the BF16 rounding of the output are fused.
+// Backward (training only): FP32 SIMT kernels for the input gradient (one
+// thread per cell and channel) and the weight gradient (per tap, chunks of
+// cells staged in shared memory, atomics into the FP32 gradient).
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/mmx_residual.h"
+#include "internal.h"
+
+namespace {
+
+constexpr int RN_TX = 32, RN_TY = 4;  // tile of cells per CTA (4 warps, one y row each)
+constexpr int NLAYER = 4;
+constexpr int CIN[NLAYER] = {6, 32, 32, 32}, COUT[NLAYER] = {32, 32, 32, 3};
+constexpr int CINP[NLAYER] = {16, 32, 32, 32}, COUTP[NLAYER] = {32, 32, 32, 8};
+
+constexpr long long p_off(int l)
+{
+    return l == 0 ? 0 : p_off(l - 1) + 27LL * COUT[l - 1] * CIN[l - 1] + COUT[l - 1];
+}
+constexpr long long w_off(int l)
+{
+    return l == 0 ? 0 : w_off(l - 1) + 27LL * COUTP[l - 1] * CINP[l - 1];
+}
+static_assert(p_off(NLAYER) == MMX_RNET_PARAMS, "parameter count");
+// the same offsets as scalars, for device code
+constexpr long long WO1 = 13824, WO2 = 41472, WO3 = 69120, WQ_TOTAL = 76032;
+constexpr long long PO1 = 5216, PO2 = 32896, PO3 = 60576;
+static_assert(w_off(1) == WO1 && w_off(2) == WO2 && w_off(3) == WO3 && w_off(4) == WQ_TOTAL, "weight offsets");
+static_assert(p_off(1) == PO1 && p_off(2) == PO2 && p_off(3) == PO3, "parameter offsets");
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t r[4], uint32_t addr)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int CINP_>
+constexpr size_t conv_smem()
+{
+    return (size_t)3 * (RN_TY + 2) * (RN_TX + 2) * (CINP_ + 8) * 2;
+}
+
+// x (FP32, [6][cells]) -> layer-0 input (BF16, [cells][16], channels 6..15 zero)
+__global__ void k_rnet_pack(const float *__restrict__ x, long long n, __nv_bfloat16 *__restrict__ a0)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    __align__(16) __nv_bfloat16 v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(c < 6 ? x[c * n + i] : 0.0f);
+    uint4 *dst = (uint4 *)(a0 + i * 16);
+    dst[0] = ((const uint4 *)v)[0];
+    dst[1] = ((const uint4 *)v)[1];
+}
+
+// One layer: out = act(b + sum_t W_t in(shifted by t)).  Hidden layers write
+// BF16 [cells][32] after ReLU; the last layer writes FP32 [3][cells].
+template <int CINP_, int COUTP_, bool LAST>
+__global__ void __launch_bounds__(128) k_rnet_conv(const __nv_bfloat16 *__restrict__ in,
+                                                   const __nv_bfloat16 *__restrict__ Wq,
+                                                   const float *__restrict__ bias, int cout, void *out, int nx,
+                                                   int ny, int nz)
+{
+    constexpr int CS = CINP_ + 8;
+    constexpr int HX = RN_TX + 2, HY = RN_TY + 2;
+    constexpr int V = CINP_ / 8;  // 16-byte vectors per cell
+    extern __shared__ __align__(16) unsigned char rn_smem[];
+    __nv_bfloat16 *hal = (__nv_bfloat16 *)rn_smem;  // [3][HY][HX][CS]
+    const int x0 = blockIdx.x * RN_TX, y0 = blockIdx.y * RN_TY, z = blockIdx.z;
+    for (int e = threadIdx.x; e < 3 * HY * HX * V; e += blockDim.x) {
+        const int v = e % V, cell = e / V;
+        const int hx = cell % HX, hy = (cell / HX) % HY, hz = cell / (HX * HY);
+        const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z + hz - 1;
+        uint4 val = make_uint4(0u, 0u, 0u, 0u);
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
+            val = ((const uint4 *)(in + ((size_t)(gz * ny + gy) * nx + gx) * CINP_))[v];
+        *(uint4 *)(hal + (size_t)cell * CS + v * 8) = val;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, q = lane & 3;
+    constexpr int NT = COUTP_ / 8;
+    float acc[2][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[mt][nt][j] = 0.0f;
+    // ldmatrix: lanes 0-7 / 8-15 give rows 0-7 / 8-15 at k 0-7, lanes 16-31 the same rows at k 8-15
+    const int lrow = (lane & 7) + ((lane >> 3) & 1) * 8, lk = (lane >> 4) * 8;
+    const uint32_t hal_s = smem_u32(hal);
+    for (int t = 0; t < 27; ++t) {
+        const int tz = t / 9, ty = (t / 3) % 3, tx = t % 3;
+        const int cell0 = (tz * HY + warp + ty) * HX + lrow + tx;
+        const __nv_bfloat16 *Wt = Wq + (size_t)t * COUTP_ * CINP_;
+#pragma unroll
+        for (int kc = 0; kc < CINP_ / 16; ++kc) {
+            uint32_t a[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+                ldmatrix_x4(a[mt], hal_s + (uint32_t)(((cell0 + mt * 16) * CS + kc * 16 + lk) * 2));
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const __nv_bfloat16 *wp = Wt + (nt * 8 + g) * CINP_ + kc * 16 + 2 * q;
+                const uint32_t b0 = __ldg((const unsigned int *)wp);
+                const uint32_t b1 = __ldg((const unsigned int *)(wp + 8));
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) mma_bf16(acc[mt][nt], a[mt], b0, b1);
+            }
+        }
+    }
+    const int y = y0 + warp;
+    const size_t ncell = (size_t)nx * ny * nz;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int x = x0 + mt * 16 + g + half * 8;
+            if (x >= nx || y >= ny) continue;
+            const size_t cell = ((size_t)z * ny + y) * nx + x;
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int col = nt * 8 + 2 * q;
+                const float v0 = acc[mt][nt][half * 2], v1 = acc[mt][nt][half * 2 + 1];
+                if (!LAST) {
+                    const __nv_bfloat162 h =
+                        __floats2bfloat162_rn(fmaxf(v0 + bias[col], 0.0f), fmaxf(v1 + bias[col + 1], 0.0f));
+                    *(__nv_bfloat162 *)((__nv_bfloat16 *)out + cell * 32 + col) = h;
+                } else {
+                    float *r = (float *)out;
+                    if (col < cout) r[col * ncell + cell] = v0 + bias[col];
+                    if (col + 1 < cout) r[(col + 1) * ncell + cell] = v1 + bias[col + 1];
+                }
+            }
+        }
+}
+
+// loss terms: dz3 [cells][8] = 2 (r - target) / (3 cells), sum of squares into *loss
+__global__ void k_rnet_loss(const float *__restrict__ r, const float *__restrict__ tgt, long long n,
+                            float *__restrict__ dz3, double *loss)
+{
+    __shared__ double s_sum[8];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (i < n) {
+        const float k = (float)(2.0 / (3.0 * (double)n));
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            float d = 0.0f;
+            if (c < 3) {
+                d = r[c * n + i] - tgt[c * n + i];
+                sq += (double)d * d;
+            }
+            dz3[i * 8 + c] = k * d;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += s_sum[w];
+        atomicAdd(loss, s);
+    }
+}
+
+// gradient with respect to the layer input, masked by ReLU' of that input:
+// dzp[p][c] = [A[p][c] > 0] sum_t sum_o W_t[o][c] dz[p - t][o]
+template <int COUTP_>
+__global__ void __launch_bounds__(256) k_rnet_dgrad(const float *__restrict__ dz, const __nv_bfloat16 *__restrict__ Wq,
+                                                    int cout, const __nv_bfloat16 *__restrict__ A,
+                                                    float *__restrict__ dzp, int nx, int ny, int nz)
+{
+    const long long n = (long long)nx * ny * nz;
+    const int c = threadIdx.x & 31;
+    const long long p = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (p >= n) return;
+    const int x = (int)(p % nx), y = (int)((p / nx) % ny), z = (int)(p / ((long long)nx * ny));
+    float acc = 0.0f;
+    for (int t = 0; t < 27; ++t) {
+        const int qx = x - (t % 3 - 1), qy = y - ((t / 3) % 3 - 1), qz = z - (t / 9 - 1);
+        if (qx < 0 || qx >= nx || qy < 0 || qy >= ny || qz < 0 || qz >= nz) continue;
+        const float *d = dz + (((long long)qz * ny + qy) * nx + qx) * COUTP_;
+        const __nv_bfloat16 *w = Wq + (size_t)t * COUTP_ * 32 + c;
+        for (int o = 0; o < cout; ++o) acc += __bfloat162float(w[o * 32]) * d[o];
+    }
+    dzp[p * 32 + c] = (__bfloat162float(A[p * 32 + c]) > 0.0f) ? acc : 0.0f;
+}
+
+// weight (and, at the centre tap, bias) gradient of one layer:
+// gW[t][o][c] += sum_p dz[p][o] A[p + t][c] over a chunk of cells
+template <int CINP_, int COUTP_>
+__global__ void __launch_bounds__(256) k_rnet_wgrad(const float *__restrict__ dz, const __nv_bfloat16 *__restrict__ A,
+                                                    int cin, int cout, float *gW, float *gb, int nx, int ny, int nz,
+                                                    int chunk)
+{
+    constexpr int SUB = 64;
+    constexpr int PAIRS = COUTP_ * CINP_;
+    constexpr int PT = (PAIRS + 255) / 256;
+    __shared__ float s_dz[SUB][COUTP_];
+    __shared__ float s_A[SUB][CINP_ + 1];
+    const long long n = (long long)nx * ny * nz;
+    const int t = blockIdx.y;
+    const int dxx = t % 3 - 1, dyy = (t / 3) % 3 - 1, dzz = t / 9 - 1;
+    const long long c0 = (long long)blockIdx.x * chunk;
+    const long long c1 = min(c0 + chunk, n);
+    float acc[PT];
+#pragma unroll
+    for (int k = 0; k < PT; ++k) acc[k] = 0.0f;
+    float bacc = 0.0f;
+    for (long long s0 = c0; s0 < c1; s0 += SUB) {
+        for (int e = threadIdx.x; e < SUB * COUTP_; e += blockDim.x) {
+            const long long p = s0 + e / COUTP_;
+            s_dz[e / COUTP_][e % COUTP_] = (p < c1) ? dz[p * COUTP_ + e % COUTP_] : 0.0f;
+        }
+        for (int e = threadIdx.x; e < SUB * CINP_; e += blockDim.x) {
+            const long long p = s0 + e / CINP_;
+            float v = 0.0f;
+            if (p < c1) {
+                const int x = (int)(p % nx) + dxx, y = (int)((p / nx) % ny) + dyy,
+                          z = (int)(p / ((long long)nx * ny)) + dzz;
+                if (x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz)
+                    v = __bfloat162float(A[(((long long)z * ny + y) * nx + x) * CINP_ + e % CINP_]);
+            }
+            s_A[e / CINP_][e % CINP_] = v;
+        }
+        __syncthreads();
+        for (int i = 0; i < SUB; ++i) {
+#pragma unroll
+            for (int k = 0; k < PT; ++k) {
+                const int j = threadIdx.x + k * 256;
+                if (j < PAIRS) acc[k] += s_dz[i][j / CINP_] * s_A[i][j % CINP_];
+            }
+            if (t == 13 && threadIdx.x < COUTP_) bacc += s_dz[i][threadIdx.x];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < PT; ++k) {
+        const int j = threadIdx.x + k * 256;
+        const int o = j / CINP_, c = j % CINP_;
+        if (j < PAIRS && o < cout && c < cin) atomicAdd(&gW[((size_t)t * cout + o) * cin + c], acc[k]);
+    }
+    if (t == 13 && threadIdx.x < cout) atomicAdd(&gb[threadIdx.x], bacc);
+}
+
+__global__ void k_rnet_adam(float *__restrict__ P, float *__restrict__ M, float *__restrict__ Vv,
+                            const float *__restrict__ G, int n, float lr, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = G[i];
+    const float m = 0.9f * M[i] + 0.1f * g;
+    const float v = 0.999f * Vv[i] + 0.001f * g * g;
+    M[i] = m;
+    Vv[i] = v;
+    P[i] -= lr * (m * c1) / (sqrtf(v * c2) + 1e-8f);
+}
+
+// BF16 weights, padded to [27][COUTP][CINP] per layer, from the FP32 master parameters
+__global__ void k_rnet_cast(const float *__restrict__ P, __nv_bfloat16 *__restrict__ Wq)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= WQ_TOTAL) return;
+    long long j, po;
+    int cin, cout, cinp, coutp;
+    if (i < WO1) {
+        j = i, po = 0, cin = 6, cout = 32, cinp = 16, coutp = 32;
+    } else if (i < WO2) {
+        j = i - WO1, po = PO1, cin = 32, cout = 32, cinp = 32, coutp = 32;
+    } else if (i < WO3) {
+        j = i - WO2, po = PO2, cin = 32, cout = 32, cinp = 32, coutp = 32;
+    } else {
+        j = i - WO3, po = PO3, cin = 32, cout = 3, cinp = 32, coutp = 8;
+    }
+    const int cp = (int)(j % cinp), op = (int)((j / cinp) % coutp), t = (int)(j / (cinp * coutp));
+    float v = 0.0f;
+    if (cp < cin && op < cout) v = P[po + ((long long)t * cout + op) * cin + cp];
+    Wq[i] = __float2bfloat16_rn(v);
+}
+
+// training pairs: xg (T, [3][cells]) = sum_j w_j G_j
+template <typename T>
+__global__ void k_res_accum(const T *__restrict__ G, double w, T *__restrict__ acc, long long n3, int first)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    const T v = (T)w * G[i];
+    acc[i] = first ? v : acc[i] + v;
+}
+
+template <typename T>
+__global__ void k_res_finish(const T *__restrict__ m, const T *__restrict__ G, const T *__restrict__ Gext,
+                             double inv_Ms, long long n, float *__restrict__ x, float *__restrict__ target)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    x[i] = (float)m[i];
+    x[3 * n + i] = (float)(Gext[i] * (T)inv_Ms);
+    target[i] = (float)((G[i] - Gext[i]) * (T)inv_Ms);
+}
+
+}  // namespace
+
+struct mmx_rnet {
+    cudaStream_t s = nullptr;
+    long long max_cells = 0;
+    float *P = nullptr, *Pm = nullptr, *Pv = nullptr, *grad = nullptr;
+    __nv_bfloat16 *Wq = nullptr;
+    __nv_bfloat16 *a[NLAYER] = {nullptr, nullptr, nullptr, nullptr};
+    float *r = nullptr, *dz3 = nullptr, *dzA = nullptr, *dzB = nullptr;
+    double *loss_d = nullptr;
+    int step = 0;
+    int nx = 0, ny = 0, nz = 0;
+    std::string err;
+};
+
+namespace {
+
+int rfail(mmx_rnet *net, int code, const std::string &msg)
+{
+    if (net) net->err = msg;
+    return code;
+}
+
+#define RCK(call)                                                                                      \
+    do {                                                                                               \
+        cudaError_t e__ = (call);                                                                      \
+        if (e__ != cudaSuccess) return rfail(net, MMX_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+bool smem_ready = false;
+
+cudaError_t raise_conv_smem()
+{
+    if (smem_ready) return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_rnet_conv<16, 32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)conv_smem<16>())) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_rnet_conv<32, 32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)conv_smem<32>())) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_rnet_conv<32, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)conv_smem<32>())) != cudaSuccess)
+        return e;
+    smem_ready = true;
+    return cudaSuccess;
+}
+
+int check_mesh(mmx_rnet *net, int nx, int ny, int nz)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || nz > 65535 || (long long)nx * ny * nz > net->max_cells)
+        return rfail(net, MMX_ERR_ARG, "mesh size out of range for this net");
+    return MMX_OK;
+}
+
+// forward through all layers from the packed input a[0]; output in net->r
+void forward_layers(mmx_rnet *net, int nx, int ny, int nz)
+{
+    const dim3 grid((nx + RN_TX - 1) / RN_TX, (ny + RN_TY - 1) / RN_TY, nz);
+    k_rnet_conv<16, 32, false><<<grid, 128, conv_smem<16>(), net->s>>>(net->a[0], net->Wq + w_off(0),
+                                                                       net->P + p_off(0) + 27 * 32 * 6, 32,
+                                                                       net->a[1], nx, ny, nz);
+    k_rnet_conv<32, 32, false><<<grid, 128, conv_smem<32>(), net->s>>>(net->a[1], net->Wq + w_off(1),
+                                                                       net->P + p_off(1) + 27 * 32 * 32, 32,
+                                                                       net->a[2], nx, ny, nz);
+    k_rnet_conv<32, 32, false><<<grid, 128, conv_smem<32>(), net->s>>>(net->a[2], net->Wq + w_off(2),
+                                                                       net->P + p_off(2) + 27 * 32 * 32, 32,
+                                                                       net->a[3], nx, ny, nz);
+    k_rnet_conv<32, 8, true><<<grid, 128, conv_smem<32>(), net->s>>>(net->a[3], net->Wq + w_off(3),
+                                                                     net->P + p_off(3) + 27 * 3 * 32, 3, net->r,
+                                                                     nx, ny, nz);
+}
+
+int refresh_weights(mmx_rnet *net)
+{
+    k_rnet_cast<<<(unsigned)((WQ_TOTAL + 255) / 256), 256, 0, net->s>>>(net->P, net->Wq);
+    RCK(cudaGetLastError());
+    return MMX_OK;
+}
+
+void lagrange(int p, const double *tau_nodes, double tau, double *w)
+{
+    for (int i = 0; i <= p; ++i) {
+        double L = 1.0;
+        for (int j = 0; j <= p; ++j)
+            if (j != i) L *= (tau - tau_nodes[j]) / (tau_nodes[i] - tau_nodes[j]);
+        w[i] = L;
+    }
+}
+
+template <typename T>
+int sample_t(mmx_ctx *c, int p, const void *m_nodes, const double *t_nodes, const void *m, double t, float *x,
+             float *target)
+{
+    const long long n = c->n, n3 = 3 * n;
+    double tau[6], w[6];
+    for (int i = 0; i <= p; ++i) tau[i] = t_nodes[i] - t_nodes[p];
+    lagrange(p, tau, t - t_nodes[p], w);
+    T *Gext = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&Gext, n3 * sizeof(T), c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("cudaMallocAsync: ") + cudaGetErrorString(e);
+        return MMX_ERR_OOM;
+    }
+    const unsigned nb3 = (unsigned)((n3 + 255) / 256);
+    for (int j = 0; j <= p; ++j) {
+        mmxk_demag(c, c->stream, nullptr, 0, 0, (const T *)m_nodes + (size_t)j * n3, 0, c->G, nullptr);
+        k_res_accum<T><<<nb3, 256, 0, c->stream>>>((const T *)c->G, w[j], Gext, n3, j == 0);
+    }
+    mmxk_demag(c, c->stream, nullptr, 0, 0, m, 0, c->G, nullptr);
+    k_res_finish<T><<<nb3, 256, 0, c->stream>>>((const T *)m, (const T *)c->G, Gext, 1.0 / c->mat.Ms, n, x, target);
+    e = cudaGetLastError();
+    cudaFreeAsync(Gext, c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("mmx_residual_sample launch: ") + cudaGetErrorString(e);
+        return MMX_ERR_CUDA;
+    }
+    return MMX_OK;
+}
+
+}  // namespace
+
+extern "C" int mmx_rnet_create(long long max_cells, void *cuda_stream, mmx_rnet **out)
+{
+    if (!out || max_cells < 1 || max_cells > (1LL << 26)) return MMX_ERR_ARG;
+    *out = nullptr;
+    mmx_rnet *net = new mmx_rnet();
+    net->s = (cudaStream_t)cuda_stream;
+    net->max_cells = max_cells;
+    const size_t P = MMX_RNET_PARAMS * sizeof(float);
+    bool ok = cudaMalloc(&net->P, P) == cudaSuccess && cudaMalloc(&net->Pm, P) == cudaSuccess &&
+              cudaMalloc(&net->Pv, P) == cudaSuccess && cudaMalloc(&net->grad, P) == cudaSuccess &&
+              cudaMalloc(&net->Wq, WQ_TOTAL * sizeof(__nv_bfloat16)) == cudaSuccess &&
+              cudaMalloc(&net->a[0], max_cells * 16 * sizeof(__nv_bfloat16)) == cudaSuccess &&
+              cudaMalloc(&net->r, max_cells * 3 * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&net->dz3, max_cells * 8 * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&net->dzA, max_cells * 32 * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&net->dzB, max_cells * 32 * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&net->loss_d, sizeof(double)) == cudaSuccess;
+    for (int l = 1; l < NLAYER && ok; ++l)
+        ok = cudaMalloc(&net->a[l], max_cells * 32 * sizeof(__nv_bfloat16)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        mmx_rnet_destroy(net);
+        return MMX_ERR_OOM;
+    }
+    if (raise_conv_smem() != cudaSuccess ||
+        cudaMemsetAsync(net->P, 0, P, net->s) != cudaSuccess ||
+        cudaMemsetAsync(net->Pm, 0, P, net->s) != cudaSuccess ||
+        cudaMemsetAsync(net->Pv, 0, P, net->s) != cudaSuccess ||
+        cudaMemsetAsync(net->grad, 0, P, net->s) != cudaSuccess || refresh_weights(net) != MMX_OK) {
+        cudaGetLastError();
+        mmx_rnet_destroy(net);
+        return MMX_ERR_CUDA;
+    }
+    *out = net;
+    return MMX_OK;
+}
+
+extern "C" int mmx_rnet_set_params(mmx_rnet *net, const float *params_host)
+{
+    if (!net || !params_host) return rfail(net, MMX_ERR_ARG, "NULL argument");
+    const size_t P = MMX_RNET_PARAMS * sizeof(float);
+    RCK(cudaMemcpyAsync(net->P, params_host, P, cudaMemcpyHostToDevice, net->s));
+    RCK(cudaMemsetAsync(net->Pm, 0, P, net->s));
+    RCK(cudaMemsetAsync(net->Pv, 0, P, net->s));
+    net->step = 0;
+    if (int rc = refresh_weights(net)) return rc;
+    RCK(cudaStreamSynchronize(net->s));
+    return MMX_OK;
+}
+
+extern "C" int mmx_rnet_get_params(mmx_rnet *net, float *params_host)
+{
+    if (!net || !params_host) return rfail(net, MMX_ERR_ARG, "NULL argument");
+    RCK(cudaMemcpyAsync(params_host, net->P, MMX_RNET_PARAMS * sizeof(float), cudaMemcpyDeviceToHost, net->s));
+    RCK(cudaStreamSynchronize(net->s));
+    return MMX_OK;
+}
+
+extern "C" int mmx_rnet_forward(mmx_rnet *net, int nx, int ny, int nz, const float *x_dev, float *r_dev)
+{
+    if (!net || !x_dev) return rfail(net, MMX_ERR_ARG, "NULL argument");
+    if (int rc = check_mesh(net, nx, ny, nz)) return rc;
+    const long long n = (long long)nx * ny * nz;
+    k_rnet_pack<<<(unsigned)((n + 255) / 256), 256, 0, net->s>>>(x_dev, n, net->a[0]);
+    forward_layers(net, nx, ny, nz);
+    if (r_dev) RCK(cudaMemcpyAsync(r_dev, net->r, n * 3 * sizeof(float), cudaMemcpyDeviceToDevice, net->s));
+    RCK(cudaGetLastError());
+    net->nx = nx;
+    net->ny = ny;
+    net->nz = nz;
+    return MMX_OK;
+}
+
+extern "C" int mmx_rnet_train_step(mmx_rnet *net, int nx, int ny, int nz, const float *x_dev,
+                                   const float *target_dev, float lr, double *loss_out)
+{
+    if (!net || !x_dev || !target_dev) return rfail(net, MMX_ERR_ARG, "NULL argument");
+    if (!(lr > 0.0f)) return rfail(net, MMX_ERR_ARG, "learning rate must be positive");
+    if (int rc = mmx_rnet_forward(net, nx, ny, nz, x_dev, nullptr)) return rc;
+    const long long n = (long long)nx * ny * nz;
+    cudaStream_t s = net->s;
+    RCK(cudaMemsetAsync(net->loss_d, 0, sizeof(double), s));
+    RCK(cudaMemsetAsync(net->grad, 0, MMX_RNET_PARAMS * sizeof(float), s));
+    k_rnet_loss<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(net->r, target_dev, n, net->dz3, net->loss_d);
+    const int chunk = 1024;
+    const dim3 wg((unsigned)((n + chunk - 1) / chunk), 27);
+    const unsigned dg = (unsigned)((n + 7) / 8);
+    float *G = net->grad;
+    // layer 3 (32 -> 3)
+    k_rnet_wgrad<32, 8><<<wg, 256, 0, s>>>(net->dz3, net->a[3], 32, 3, G + p_off(3), G + p_off(3) + 27 * 3 * 32,
+                                           nx, ny, nz, chunk);
+    k_rnet_dgrad<8><<<dg, 256, 0, s>>>(net->dz3, net->Wq + w_off(3), 3, net->a[3], net->dzA, nx, ny, nz);
+    // layer 2
+    k_rnet_wgrad<32, 32><<<wg, 256, 0, s>>>(net->dzA, net->a[2], 32, 32, G + p_off(2),
+                                            G + p_off(2) + 27 * 32 * 32, nx, ny, nz, chunk);
+    k_rnet_dgrad<32><<<dg, 256, 0, s>>>(net->dzA, net->Wq + w_off(2), 32, net->a[2], net->dzB, nx, ny, nz);
+    // layer 1
+    k_rnet_wgrad<32, 32><<<wg, 256, 0, s>>>(net->dzB, net->a[1], 32, 32, G + p_off(1),
+                                            G + p_off(1) + 27 * 32 * 32, nx, ny, nz, chunk);
+    k_rnet_dgrad<32><<<dg, 256, 0, s>>>(net->dzB, net->Wq + w_off(1), 32, net->a[1], net->dzA, nx, ny, nz);
+    // layer 0 (6 -> 32; input padded to 16 channels)
+    k_rnet_wgrad<16, 32><<<wg, 256, 0, s>>>(net->dzA, net->a[0], 6, 32, G + p_off(0), G + p_off(0) + 27 * 32 * 6,
+                                            nx, ny, nz, chunk);
+    net->step++;
+    const double c1 = 1.0 / (1.0 - pow(0.9, net->step)), c2 = 1.0 / (1.0 - pow(0.999, net->step));
+    k_rnet_adam<<<(MMX_RNET_PARAMS + 255) / 256, 256, 0, s>>>(net->P, net->Pm, net->Pv, G, MMX_RNET_PARAMS, lr,
+                                                               (float)c1, (float)c2);
+    if (int rc = refresh_weights(net)) return rc;
+    RCK(cudaGetLastError());
+    if (loss_out) {
+        double l = 0.0;
+        RCK(cudaMemcpyAsync(&l, net->loss_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+        RCK(cudaStreamSynchronize(s));
+        *loss_out = l / (3.0 * (double)n);
+    }
+    return MMX_OK;
+}
+
+extern "C" int mmx_rnet_get_grads(mmx_rnet *net, float *grads_host)
+{
+    if (!net || !grads_host) return rfail(net, MMX_ERR_ARG, "NULL argument");
+    RCK(cudaMemcpyAsync(grads_host, net->grad, MMX_RNET_PARAMS * sizeof(float), cudaMemcpyDeviceToHost, net->s));
+    RCK(cudaStreamSynchronize(net->s));
+    return MMX_OK;
+}
+
+extern "C" int mmx_rnet_get_activation(mmx_rnet *net, int layer, void *dst_host, size_t bytes)
+{
+    if (!net || !dst_host || layer < 0 || layer > NLAYER) return rfail(net, MMX_ERR_ARG, "invalid argument");
+    const size_t n = (size_t)net->nx * net->ny * net->nz;
+    if (n == 0) return rfail(net, MMX_ERR_STATE, "no forward pass yet");
+    const size_t want = layer == NLAYER ? n * 3 * sizeof(float) : n * (layer == 0 ? 16 : 32) * 2;
+    if (bytes != want) return rfail(net, MMX_ERR_ARG, "size does not match the last forward pass");
+    const void *src = layer == NLAYER ? (const void *)net->r : (const void *)net->a[layer];
+    RCK(cudaMemcpyAsync(dst_host, src, bytes, cudaMemcpyDeviceToHost, net->s));
+    RCK(cudaStreamSynchronize(net->s));
+    return MMX_OK;
+}
+
+extern "C" const char *mmx_rnet_last_error(const mmx_rnet *net)
+{
+    return net ? net->err.c_str() : "";
+}
+
+extern "C" void mmx_rnet_destroy(mmx_rnet *net)
+{
+    if (!net) return;
+    if (net->s) cudaStreamSynchronize(net->s);
+    void *bufs[] = {net->P,  net->Pm,  net->Pv,  net->grad, net->Wq,    net->a[0], net->a[1],
+                    net->a[2], net->a[3], net->r, net->dz3,  net->dzA, net->dzB,  net->loss_d};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete net;
+}
+
+extern "C" int mmx_residual_sample(mmx_ctx *c, int p, const void *m_nodes_dev, const double *t_nodes,
+                                   const void *m_dev, double t, float *x_dev, float *target_dev)
+{
+    if (!c) return MMX_ERR_ARG;
+    if (p < 0 || p > 5 || !m_nodes_dev || !t_nodes || !m_dev || !x_dev || !target_dev) {
+        c->err = "mmx_residual_sample: invalid argument";
+        return MMX_ERR_ARG;
+    }
+    const size_t field_bytes = (size_t)3 * c->n * c->esz;
+    for (int i = 0; i <= p; ++i)
+        if (((uintptr_t)m_nodes_dev + i * field_bytes) % 16 != 0) {
+            c->err = "mmx_residual_sample: every node field must start on a 16-byte boundary";
+            return MMX_ERR_ARG;
+        }
+    if ((uintptr_t)m_dev % 16 != 0 || (uintptr_t)x_dev % 16 != 0 || (uintptr_t)target_dev % 16 != 0) {
+        c->err = "mmx_residual_sample: arrays must start on a 16-byte boundary";
+        return MMX_ERR_ARG;
+    }
+    for (int i = 0; i <= p; ++i)
+        for (int j = 0; j < i; ++j)
+            if (!(t_nodes[i] != t_nodes[j])) {
+                c->err = "mmx_residual_sample: node times must be distinct";
+                return MMX_ERR_ARG;
+            }
+    return c->prec == MMX_FP64 ? sample_t<double>(c, p, m_nodes_dev, t_nodes, m_dev, t, x_dev, target_dev)
+                               : sample_t<float>(c, p, m_nodes_dev, t_nodes, m_dev, t, x_dev, target_dev);
+}

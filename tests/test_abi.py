@@ -1,5 +1,5 @@
 """The C-ABI library: it builds for sm_103a, loads, exports every entry
-point that include/mmx.h declares, and rejects invalid descriptions on the
+point that include/*.h declares, and rejects invalid descriptions on the
 host (no CUDA call is made for those)."""
 import os
 import re
@@ -9,10 +9,12 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "mmx.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
 def declared_symbols():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(mmx_[a-z_]+)\s*\(", text)))
 
@@ -100,3 +102,17 @@ def test_batch_arguments_are_checked_on_the_host(libpath):
     assert "NULL member" in pkg.mmx_last_error(None)
     assert L.mmx_batch_run(None, None, None) == pkg.MMX_ERR_ARG
     L.mmx_batch_destroy(None)
+
+
+def test_residual_net_rejects_invalid_arguments_on_the_host(libpath):
+    """No CUDA call is made for these."""
+    import ctypes
+    import paper_2107_06729_gb300 as pkg
+    L = pkg.lib()
+    out = ctypes.c_void_p()
+    assert L.mmx_rnet_create(0, None, ctypes.byref(out)) == pkg.MMX_ERR_ARG
+    assert L.mmx_rnet_create(1 << 27, None, ctypes.byref(out)) == pkg.MMX_ERR_ARG
+    assert L.mmx_rnet_create(16, None, None) == pkg.MMX_ERR_ARG
+    assert L.mmx_residual_sample(None, 2, None, None, None, 0.0, None, None) == pkg.MMX_ERR_ARG
+    assert L.mmx_rnet_forward(None, 4, 4, 1, None, None) == pkg.MMX_ERR_ARG
+    assert pkg.mmx_rnet_last_error(None) == ""
