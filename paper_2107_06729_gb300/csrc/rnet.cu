@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <string>
@@ -169,6 +170,265 @@ __global__ void __launch_bounds__(128) k_rnet_conv(const __nv_bfloat16 *__restri
         }
 }
 
+// ---- tcgen05 version of the layer ------------------------------------------
+// The CTA computes D[128][N] = sum over taps and k-steps of A_t[128][16] B_t[16][N]
+// on the 5th-generation tensor cores: row j = oy*32 + ox of the tile is the
+// cell (x0 + ox - 1, y0 + oy, z) for ox = 1..30 (ox = 0 and 31 are computed
+// and dropped).  The input halo is kept in shared memory as 16-byte rows
+// [k-chunk][cell] with cells (hz, hy, hx), hx = 0..31, in row-major order
+// after one leading pad row, i.e. in the canonical K-major layout without
+// swizzle (8-row core matrices of 16-byte rows); the A operand of tap
+// (tz, ty, tx) is then the same layout starting (tz*6 + ty)*32 + tx rows in.
+// The weights are [tap][k-chunk][n] 16-byte rows, the same layout for B.
+// One thread issues the MMAs into a TMEM accumulator (FP32, N columns) and
+// commits them to an mbarrier; the wait is bounded in time, after which the
+// kernel sets *fault, waits once more (bounded) and frees its TMEM.
+constexpr int TC_HY = RN_TY + 2, TC_ROWS = 3 * TC_HY * 32;  // halo cells
+constexpr int TC_NE = 584;  // rows per k-chunk: pad + halo + the overrun of the last taps (>= 578)
+constexpr int TC_TX = 30;   // valid cells per tile row
+// weights in the shared-memory layout of the tensor-core layers, per layer
+// [27][Cin/8][N][8] BF16 (N = 32, or 16 for the last layer): one bulk copy each
+constexpr long long TCO1 = 13824, TCO2 = 41472, TCO3 = 69120, TC_TOTAL = 82944;
+constexpr unsigned long long TC_WAIT_NS = 1000000000ULL;
+// independent accumulators (32 TMEM columns apart): consecutive MMAs of a tile
+// go to different ones, so that they do not wait on each other's results
+constexpr int TC_NACC = 4;
+
+__host__ __device__ constexpr size_t tc_smem(int cinp, int n, int nbuf)
+{
+    return (size_t)nbuf * (cinp / 8) * TC_NE * 16 + (size_t)27 * (cinp / 8) * n * 16 + 32;
+}
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes)
+{
+    // start address, leading and stride byte offsets in 16-byte units; version 1; no swizzle
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo_bytes >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+template <int N_>
+__host__ __device__ constexpr uint32_t umma_idesc_bf16()
+{
+    // D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1), both K-major,
+    // N >> 3 at bit 17, M >> 4 at bit 24 (M = 128)
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N_ >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mbar_init(uint32_t m)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(m) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+__device__ __forceinline__ bool tc_mbar_wait(uint32_t m, unsigned parity, unsigned long long limit_ns)
+{
+    unsigned long long t0 = 0;
+    for (unsigned i = 0;; ++i) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(m), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((i & 255) == 0) {
+            unsigned long long t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > limit_ns) return false;
+        }
+    }
+}
+
+template <int CINP_, int N_, bool LAST, int NBUF>
+__global__ void __launch_bounds__(128) k_rnet_conv_tc(const __nv_bfloat16 *__restrict__ in,
+                                                      const __nv_bfloat16 *__restrict__ Wtc,
+                                                      const float *__restrict__ bias, int cout, void *out, int nx,
+                                                      int ny, int nz, int *fault)
+{
+    constexpr int KC = CINP_ / 8;  // 16-byte k-chunks per cell
+    extern __shared__ __align__(128) unsigned char tc_smem_raw[];
+    uint4 *hal2 = (uint4 *)tc_smem_raw;                // halo buffers [NBUF][KC][TC_NE]
+    uint4 *wsm = hal2 + NBUF * KC * TC_NE;             // [27][KC][N_]
+    uint64_t *mbar = (uint64_t *)(wsm + 27 * KC * N_); // [0]: MMAs done, [1]: weights landed
+    uint32_t *tmem_slot = (uint32_t *)(mbar + 2);      // 4 bytes
+    constexpr uint32_t WBYTES = 27u * KC * N_ * 16u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int txc = (nx + TC_TX - 1) / TC_TX, tyc = (ny + RN_TY - 1) / RN_TY;
+    const int ntiles = txc * tyc * nz;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                     "r"(32 * TC_NACC)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (threadIdx.x == 32) {
+        tc_mbar_init(smem_u32(mbar));
+        tc_mbar_init(smem_u32(mbar + 1));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    // weights: one bulk copy of the layer's [27][KC][N] rows, counted on mbar[1]
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mbar + 1)),
+                     "r"(WBYTES)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                smem_u32(wsm)),
+            "l"(Wtc), "r"(WBYTES), "r"(smem_u32(mbar + 1))
+            : "memory");
+    }
+    const uint32_t mb = smem_u32(mbar);
+    bool wok = true;
+    // input halo of a tile: cell (hz, hy, hx) -> global (z + hz - 1, y0 + hy - 1, x0 + hx - 1),
+    // row 1 + cell; 16-byte asynchronous copies, zero-filled outside the mesh
+    auto stage = [&](int tl, uint4 *hb) {
+        const int sx0 = (tl % txc) * TC_TX, sy0 = ((tl / txc) % tyc) * RN_TY, sz = tl / (txc * tyc);
+        for (int e = threadIdx.x; e < TC_ROWS * KC; e += blockDim.x) {
+            const int v = e % KC, cell = e / KC;
+            const int hx = cell & 31, hy = (cell >> 5) % TC_HY, hz = (cell >> 5) / TC_HY;
+            const int gx = sx0 + hx - 1, gy = sy0 + hy - 1, gz = sz + hz - 1;
+            const bool inside = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz;
+            const __nv_bfloat16 *src = inside ? in + ((size_t)(gz * ny + gy) * nx + gx) * CINP_ + v * 8 : in;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(hb + v * TC_NE + 1 + cell)),
+                         "l"(src), "r"(inside ? 16 : 0)
+                         : "memory");
+        }
+    };
+    if (NBUF == 2 && (int)blockIdx.x < ntiles) stage(blockIdx.x, hal2);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    // pad rows (never written by the copies): zero in every buffer
+    for (int e = threadIdx.x; e < NBUF * KC * (TC_NE - TC_ROWS); e += blockDim.x) {
+        const int v = e / (TC_NE - TC_ROWS), r = e % (TC_NE - TC_ROWS);
+        hal2[v * TC_NE + (r == 0 ? 0 : TC_ROWS + r)] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    // persistent loop over tiles; the weights stay in shared memory and the
+    // next tile's halo is copied in while this tile's MMAs and epilogue run
+    for (int tile = blockIdx.x, it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+    const int x0 = (tile % txc) * TC_TX, y0 = ((tile / txc) % tyc) * RN_TY, z = tile / (txc * tyc);
+    uint4 *hal = hal2 + (NBUF == 2 ? (it & 1) : 0) * KC * TC_NE;
+    if constexpr (NBUF == 2) {
+        // the next tile's halo goes to the other buffer while this one is used
+        if (tile + (int)gridDim.x < ntiles) stage(tile + gridDim.x, hal2 + ((it + 1) & 1) * KC * TC_NE);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // all but the newest group: this tile's halo
+    } else {
+        stage(tile, hal);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 0) {
+    if (lane == 0) {
+        const uint32_t hal_s = smem_u32(hal), w_s = smem_u32(wsm);
+        constexpr uint32_t idesc = umma_idesc_bf16<N_>();
+        if (it == 0) {
+            wok = tc_mbar_wait(smem_u32(mbar + 1), 0, TC_WAIT_NS);
+            if (!wok) {
+                atomicExch(fault, 1);
+                (void)tc_mbar_wait(smem_u32(mbar + 1), 0, TC_WAIT_NS);  // the copy in flight
+            }
+        }
+        for (int t = 0; t < (wok ? 27 : 0); ++t) {
+            const int tz = t / 9, ty = (t / 3) % 3, tx = t % 3;
+            const uint32_t row0 = (uint32_t)((tz * TC_HY + ty) * 32 + tx);
+#pragma unroll
+            for (int ks = 0; ks < KC / 2; ++ks) {
+                const uint64_t ad = umma_desc(hal_s + ((uint32_t)(2 * ks * TC_NE) + row0) * 16u, TC_NE * 16u, 128u);
+                const uint64_t bd = umma_desc(w_s + (uint32_t)((t * KC + 2 * ks) * N_) * 16u, N_ * 16u, 128u);
+                const int i = t * (KC / 2) + ks;
+                const uint32_t acc = (i >= TC_NACC) ? 1u : 0u;  // the first MMA of each accumulator overwrites it
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + 32u * (i % TC_NACC)),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb)
+                     : "memory");
+    }
+    __syncwarp();  // the other lanes of the issuing warp do not spin beside it
+    }
+    bool ok = tc_mbar_wait(mb, it & 1, TC_WAIT_NS);
+    if (!ok) {
+        if (lane == 0) atomicExch(fault, 1);
+        ok = tc_mbar_wait(mb, it & 1, TC_WAIT_NS);  // let the MMAs in flight finish before TMEM is freed
+    }
+    // one decision for the whole CTA (the TMEM loads below are warp-collective)
+    ok = __syncthreads_and(ok) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (!ok) break;  // the barrier phase is lost: stop, free TMEM below
+    {
+        // warp w reads TMEM lanes 32w..32w+31 = tile rows oy = w, ox = lane; the
+        // accumulators are summed in FP32
+        float v[N_];
+#pragma unroll
+        for (int c = 0; c < N_; ++c) v[c] = 0.0f;
+#pragma unroll
+        for (int a = 0; a < TC_NACC; ++a) {
+            uint32_t u[N_];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + 32u * a;
+            if constexpr (N_ == 32) {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                    : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+                      "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
+                      "=r"(u[15]), "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]),
+                      "=r"(u[22]), "=r"(u[23]), "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]),
+                      "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+                    : "r"(taddr));
+            } else {
+                static_assert(N_ == 16, "N is 16 or 32");
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];\n"
+                    : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+                      "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
+                      "=r"(u[15])
+                    : "r"(taddr));
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+            for (int c = 0; c < N_; ++c) v[c] += __uint_as_float(u[c]);
+        }
+        const int x = x0 + lane - 1, y = y0 + warp;
+        if (lane >= 1 && lane <= TC_TX && x < nx && y < ny) {
+            const size_t ncell = (size_t)nx * ny * nz;
+            const size_t cell = ((size_t)z * ny + y) * nx + x;
+            if constexpr (!LAST) {
+                __align__(16) __nv_bfloat162 h[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    h[c] = __floats2bfloat162_rn(fmaxf(v[2 * c] + bias[2 * c], 0.0f),
+                                                 fmaxf(v[2 * c + 1] + bias[2 * c + 1], 0.0f));
+                uint4 *dst = (uint4 *)((__nv_bfloat16 *)out + cell * 32);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dst[q] = ((const uint4 *)h)[q];
+            } else {
+                float *r = (float *)out;
+                for (int c = 0; c < cout; ++c) r[c * ncell + cell] = v[c] + bias[c];
+            }
+        }
+    }
+    // TMEM reads and halo reads of this tile done before the next tile refills them
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (threadIdx.x == 0 && (int)blockIdx.x >= ntiles) (void)tc_mbar_wait(smem_u32(mbar + 1), 0, TC_WAIT_NS);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(32 * TC_NACC)
+                     : "memory");
+}
+
 // loss terms: dz3 [cells][8] = 2 (r - target) / (3 cells), sum of squares into *loss
 __global__ void k_rnet_loss(const float *__restrict__ r, const float *__restrict__ tgt, long long n,
                             float *__restrict__ dz3, double *loss)
@@ -314,6 +574,32 @@ __global__ void k_rnet_cast(const float *__restrict__ P, __nv_bfloat16 *__restri
     Wq[i] = __float2bfloat16_rn(v);
 }
 
+// the same weights in the tensor-core layers' shared-memory layout:
+// per layer [27][Cin_pad/8][N][8], N = 32 (16 for the last layer), zero padded
+__global__ void k_rnet_cast_tc(const float *__restrict__ P, __nv_bfloat16 *__restrict__ Wtc)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= TC_TOTAL) return;
+    long long j, po;
+    int cin, cout, kcn, nn;
+    if (i < TCO1) {
+        j = i, po = 0, cin = 6, cout = 32, kcn = 2, nn = 32;
+    } else if (i < TCO2) {
+        j = i - TCO1, po = PO1, cin = 32, cout = 32, kcn = 4, nn = 32;
+    } else if (i < TCO3) {
+        j = i - TCO2, po = PO2, cin = 32, cout = 32, kcn = 4, nn = 32;
+    } else {
+        j = i - TCO3, po = PO3, cin = 32, cout = 3, kcn = 4, nn = 16;
+    }
+    const int e = (int)(j % 8);
+    const long long row = j / 8;
+    const int n = (int)(row % nn), kc = (int)((row / nn) % kcn), t = (int)(row / ((long long)nn * kcn));
+    const int k = kc * 8 + e;
+    float v = 0.0f;
+    if (n < cout && k < cin) v = P[po + ((long long)t * cout + n) * cin + k];
+    Wtc[i] = __float2bfloat16_rn(v);
+}
+
 // training pairs: xg (T, [3][cells]) = sum_j w_j G_j
 template <typename T>
 __global__ void k_res_accum(const T *__restrict__ G, double w, T *__restrict__ acc, long long n3, int first)
@@ -341,10 +627,14 @@ struct mmx_rnet {
     cudaStream_t s = nullptr;
     long long max_cells = 0;
     float *P = nullptr, *Pm = nullptr, *Pv = nullptr, *grad = nullptr;
-    __nv_bfloat16 *Wq = nullptr;
+    __nv_bfloat16 *Wq = nullptr, *Wtc = nullptr;
     __nv_bfloat16 *a[NLAYER] = {nullptr, nullptr, nullptr, nullptr};
     float *r = nullptr, *dz3 = nullptr, *dzA = nullptr, *dzB = nullptr;
     double *loss_d = nullptr;
+    int *fault = nullptr;  // set by a tensor-core layer whose bounded wait ran out
+    int nsm = 1;
+    int tc_nbuf = 1;       // MMX_RNET_NBUF: halo buffers per tensor-core CTA (1 or 2)
+    bool mma_sync = false; // MMX_RNET_MMA_SYNC=1: the mma.sync layers instead of tcgen05
     int step = 0;
     int nx = 0, ny = 0, nz = 0;
     std::string err;
@@ -366,10 +656,31 @@ int rfail(mmx_rnet *net, int code, const std::string &msg)
 
 bool smem_ready = false;
 
+template <int NB>
+cudaError_t set_tc_smem()
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<16, 32, false, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tc_smem(16, 32, NB))) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<32, 32, false, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tc_smem(32, 32, NB))) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_rnet_conv_tc<32, 16, true, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tc_smem(32, 16, NB));
+}
+
+// the four layers on the tensor-core kernels; NB halo buffers per CTA
+// (1: two CTAs per SM overlap each other; 2: one CTA per SM overlaps its own copies)
+template <int NB>
+void forward_tc(mmx_rnet *net, int nx, int ny, int nz);
+
 cudaError_t raise_conv_smem()
 {
     if (smem_ready) return cudaSuccess;
     cudaError_t e;
+    if ((e = set_tc_smem<1>()) != cudaSuccess) return e;
+    if ((e = set_tc_smem<2>()) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_rnet_conv<16, 32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)conv_smem<16>())) != cudaSuccess)
         return e;
@@ -383,6 +694,15 @@ cudaError_t raise_conv_smem()
     return cudaSuccess;
 }
 
+// after a stream synchronisation: the fault word of the tensor-core layers
+int check_fault(mmx_rnet *net)
+{
+    int f = 0;
+    RCK(cudaMemcpy(&f, net->fault, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f) return rfail(net, MMX_ERR_CUDA, "a bounded tensor-core wait gave up (MMA not completed)");
+    return MMX_OK;
+}
+
 int check_mesh(mmx_rnet *net, int nx, int ny, int nz)
 {
     if (nx < 1 || ny < 1 || nz < 1 || nz > 65535 || (long long)nx * ny * nz > net->max_cells)
@@ -393,6 +713,13 @@ int check_mesh(mmx_rnet *net, int nx, int ny, int nz)
 // forward through all layers from the packed input a[0]; output in net->r
 void forward_layers(mmx_rnet *net, int nx, int ny, int nz)
 {
+    if (!net->mma_sync) {
+        if (net->tc_nbuf == 2)
+            forward_tc<2>(net, nx, ny, nz);
+        else
+            forward_tc<1>(net, nx, ny, nz);
+        return;
+    }
     const dim3 grid((nx + RN_TX - 1) / RN_TX, (ny + RN_TY - 1) / RN_TY, nz);
     k_rnet_conv<16, 32, false><<<grid, 128, conv_smem<16>(), net->s>>>(net->a[0], net->Wq + w_off(0),
                                                                        net->P + p_off(0) + 27 * 32 * 6, 32,
@@ -408,9 +735,26 @@ void forward_layers(mmx_rnet *net, int nx, int ny, int nz)
                                                                      nx, ny, nz);
 }
 
+template <int NB>
+void forward_tc(mmx_rnet *net, int nx, int ny, int nz)
+{
+    const long long tiles = (long long)((nx + TC_TX - 1) / TC_TX) * ((ny + RN_TY - 1) / RN_TY) * nz;
+    const long long cap = (long long)net->nsm * (NB == 1 ? 2 : 1);
+    const dim3 g((unsigned)(tiles < cap ? tiles : cap));
+    k_rnet_conv_tc<16, 32, false, NB><<<g, 128, tc_smem(16, 32, NB), net->s>>>(
+        net->a[0], net->Wtc, net->P + p_off(0) + 27 * 32 * 6, 32, net->a[1], nx, ny, nz, net->fault);
+    k_rnet_conv_tc<32, 32, false, NB><<<g, 128, tc_smem(32, 32, NB), net->s>>>(
+        net->a[1], net->Wtc + TCO1, net->P + p_off(1) + 27 * 32 * 32, 32, net->a[2], nx, ny, nz, net->fault);
+    k_rnet_conv_tc<32, 32, false, NB><<<g, 128, tc_smem(32, 32, NB), net->s>>>(
+        net->a[2], net->Wtc + TCO2, net->P + p_off(2) + 27 * 32 * 32, 32, net->a[3], nx, ny, nz, net->fault);
+    k_rnet_conv_tc<32, 16, true, NB><<<g, 128, tc_smem(32, 16, NB), net->s>>>(
+        net->a[3], net->Wtc + TCO3, net->P + p_off(3) + 27 * 3 * 32, 3, net->r, nx, ny, nz, net->fault);
+}
+
 int refresh_weights(mmx_rnet *net)
 {
     k_rnet_cast<<<(unsigned)((WQ_TOTAL + 255) / 256), 256, 0, net->s>>>(net->P, net->Wq);
+    k_rnet_cast_tc<<<(unsigned)((TC_TOTAL + 255) / 256), 256, 0, net->s>>>(net->P, net->Wtc);
     RCK(cudaGetLastError());
     return MMX_OK;
 }
@@ -468,12 +812,14 @@ extern "C" int mmx_rnet_create(long long max_cells, void *cuda_stream, mmx_rnet 
     bool ok = cudaMalloc(&net->P, P) == cudaSuccess && cudaMalloc(&net->Pm, P) == cudaSuccess &&
               cudaMalloc(&net->Pv, P) == cudaSuccess && cudaMalloc(&net->grad, P) == cudaSuccess &&
               cudaMalloc(&net->Wq, WQ_TOTAL * sizeof(__nv_bfloat16)) == cudaSuccess &&
+              cudaMalloc(&net->Wtc, TC_TOTAL * sizeof(__nv_bfloat16)) == cudaSuccess &&
               cudaMalloc(&net->a[0], max_cells * 16 * sizeof(__nv_bfloat16)) == cudaSuccess &&
               cudaMalloc(&net->r, max_cells * 3 * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&net->dz3, max_cells * 8 * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&net->dzA, max_cells * 32 * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&net->dzB, max_cells * 32 * sizeof(float)) == cudaSuccess &&
-              cudaMalloc(&net->loss_d, sizeof(double)) == cudaSuccess;
+              cudaMalloc(&net->loss_d, sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&net->fault, sizeof(int)) == cudaSuccess;
     for (int l = 1; l < NLAYER && ok; ++l)
         ok = cudaMalloc(&net->a[l], max_cells * 32 * sizeof(__nv_bfloat16)) == cudaSuccess;
     if (!ok) {
@@ -481,7 +827,15 @@ extern "C" int mmx_rnet_create(long long max_cells, void *cuda_stream, mmx_rnet 
         mmx_rnet_destroy(net);
         return MMX_ERR_OOM;
     }
-    if (raise_conv_smem() != cudaSuccess ||
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&net->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || net->nsm < 1)
+        net->nsm = 1;
+    const char *ms = getenv("MMX_RNET_MMA_SYNC");
+    net->mma_sync = ms && atoi(ms) != 0;
+    const char *nb = getenv("MMX_RNET_NBUF");
+    net->tc_nbuf = (nb && atoi(nb) == 2) ? 2 : 1;
+    if (raise_conv_smem() != cudaSuccess || cudaMemsetAsync(net->fault, 0, sizeof(int), net->s) != cudaSuccess ||
         cudaMemsetAsync(net->P, 0, P, net->s) != cudaSuccess ||
         cudaMemsetAsync(net->Pm, 0, P, net->s) != cudaSuccess ||
         cudaMemsetAsync(net->Pv, 0, P, net->s) != cudaSuccess ||
@@ -512,7 +866,7 @@ extern "C" int mmx_rnet_get_params(mmx_rnet *net, float *params_host)
     if (!net || !params_host) return rfail(net, MMX_ERR_ARG, "NULL argument");
     RCK(cudaMemcpyAsync(params_host, net->P, MMX_RNET_PARAMS * sizeof(float), cudaMemcpyDeviceToHost, net->s));
     RCK(cudaStreamSynchronize(net->s));
-    return MMX_OK;
+    return check_fault(net);
 }
 
 extern "C" int mmx_rnet_forward(mmx_rnet *net, int nx, int ny, int nz, const float *x_dev, float *r_dev)
@@ -570,6 +924,7 @@ extern "C" int mmx_rnet_train_step(mmx_rnet *net, int nx, int ny, int nz, const 
         double l = 0.0;
         RCK(cudaMemcpyAsync(&l, net->loss_d, sizeof(double), cudaMemcpyDeviceToHost, s));
         RCK(cudaStreamSynchronize(s));
+        if (int rc = check_fault(net)) return rc;
         *loss_out = l / (3.0 * (double)n);
     }
     return MMX_OK;
@@ -580,7 +935,7 @@ extern "C" int mmx_rnet_get_grads(mmx_rnet *net, float *grads_host)
     if (!net || !grads_host) return rfail(net, MMX_ERR_ARG, "NULL argument");
     RCK(cudaMemcpyAsync(grads_host, net->grad, MMX_RNET_PARAMS * sizeof(float), cudaMemcpyDeviceToHost, net->s));
     RCK(cudaStreamSynchronize(net->s));
-    return MMX_OK;
+    return check_fault(net);
 }
 
 extern "C" int mmx_rnet_get_activation(mmx_rnet *net, int layer, void *dst_host, size_t bytes)
@@ -593,7 +948,7 @@ extern "C" int mmx_rnet_get_activation(mmx_rnet *net, int layer, void *dst_host,
     const void *src = layer == NLAYER ? (const void *)net->r : (const void *)net->a[layer];
     RCK(cudaMemcpyAsync(dst_host, src, bytes, cudaMemcpyDeviceToHost, net->s));
     RCK(cudaStreamSynchronize(net->s));
-    return MMX_OK;
+    return check_fault(net);
 }
 
 extern "C" const char *mmx_rnet_last_error(const mmx_rnet *net)
@@ -605,8 +960,8 @@ extern "C" void mmx_rnet_destroy(mmx_rnet *net)
 {
     if (!net) return;
     if (net->s) cudaStreamSynchronize(net->s);
-    void *bufs[] = {net->P,  net->Pm,  net->Pv,  net->grad, net->Wq,    net->a[0], net->a[1],
-                    net->a[2], net->a[3], net->r, net->dz3,  net->dzA, net->dzB,  net->loss_d};
+    void *bufs[] = {net->P,   net->Pm,  net->Pv,  net->grad, net->Wq,  net->a[0],  net->a[1], net->a[2],
+                    net->a[3], net->r, net->dz3, net->dzA,  net->dzB, net->loss_d, net->fault, net->Wtc};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete net;

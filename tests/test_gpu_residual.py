@@ -45,8 +45,15 @@ def _net(torch, cells, params):
     return pkg.RNet(cells, params, torch.cuda.current_stream())
 
 
-@pytest.mark.parametrize("n", [(40, 12, 3), (8, 8, 1), (64, 32, 4), (5, 3, 2), (1, 1, 1)])
-def test_forward_layer_by_layer_matches_oracle(n):
+@pytest.mark.parametrize("path", ["tcgen05", "tcgen05_2buf", "mma_sync"])
+@pytest.mark.parametrize("n", [(40, 12, 3), (8, 8, 1), (64, 32, 4), (5, 3, 2), (1, 1, 1), (61, 9, 2)])
+def test_forward_layer_by_layer_matches_oracle(n, path, monkeypatch):
+    """Every layer kernel: tcgen05 with one halo buffer (default) or two
+    (MMX_RNET_NBUF=2), and mma.sync (MMX_RNET_MMA_SYNC=1)."""
+    if path == "mma_sync":
+        monkeypatch.setenv("MMX_RNET_MMA_SYNC", "1")
+    if path == "tcgen05_2buf":
+        monkeypatch.setenv("MMX_RNET_NBUF", "2")
     torch = torch_cuda()
     nx, ny, nz = n
     cells = nx * ny * nz
