@@ -3,14 +3,16 @@
 // no learned part; this net predicts its error from the stage state.
 //
 // Forward: each 3x3x3 layer is an implicit GEMM, M = cells, N = output
-// channels, K = 27 taps x input channels, on the tensor cores
-// (mma.sync m16n8k16, BF16 operands, FP32 accumulation).  A CTA takes a
-// 32 (x) x 4 (y) tile of cells at one z; it stages the input halo
-// (34 x 6 x 3 cells, channels last, padded by 8 channels so that the eight
-// 16-byte rows an ldmatrix phase reads fall in distinct banks) in shared
-// memory once and feeds every tap's A fragments from it with ldmatrix; the
-// B fragments (weights [tap][cout][cin], 55 KB for a hidden layer) come
-// through L1.  Bias, ReLU and the BF16 rounding of the output are fused.
+// channels, K = 27 taps x input channels.  Default kernel (k_rnet_conv_tc):
+// tcgen05.mma 128 x N x 16 on the 5th-generation tensor cores with FP32
+// accumulators in TMEM; the input halo sits in shared memory in the
+// canonical K-major layout so that every tap's A operand is the same layout
+// at a shifted start address; the weights arrive by one bulk copy per CTA.
+// Alternative (MMX_RNET_MMA_SYNC=1, k_rnet_conv): mma.sync m16n8k16 with
+// ldmatrix A fragments from a channels-last halo (cell stride padded by 16
+// bytes so that each 8-row ldmatrix phase hits distinct banks) and B
+// fragments through L1.  Bias, ReLU and the BF16 rounding of the output are
+// fused into both.
 // Backward (training only): FP32 SIMT kernels for the input gradient (one
 // thread per cell and channel) and the weight gradient (per tap, chunks of
 // cells staged in shared memory, atomics into the FP32 gradient).
