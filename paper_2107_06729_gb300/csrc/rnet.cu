@@ -7,7 +7,9 @@
 // tcgen05.mma 128 x N x 16 on the 5th-generation tensor cores with FP32
 // accumulators in TMEM; the input halo sits in shared memory in the
 // canonical K-major layout so that every tap's A operand is the same layout
-// at a shifted start address; the weights arrive by one bulk copy per CTA.
+// at a shifted start address; each k-chunk plane of the halo is one 5-D
+// tensor-memory-access copy (zero-filled outside the mesh) and the weights
+// arrive by one bulk copy per CTA.
 // Alternative (MMX_RNET_MMA_SYNC=1, k_rnet_conv): mma.sync m16n8k16 with
 // ldmatrix A fragments from a channels-last halo (cell stride padded by 16
 // bytes so that each 8-row ldmatrix phase hits distinct banks) and B
@@ -17,6 +19,7 @@
 // thread per cell and channel) and the weight gradient (per tap, chunks of
 // cells staged in shared memory, atomics into the FP32 gradient).
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -178,16 +181,23 @@ __global__ void __launch_bounds__(128) k_rnet_conv(const __nv_bfloat16 *__restri
 // cell (x0 + ox - 1, y0 + oy, z) for ox = 1..30 (ox = 0 and 31 are computed
 // and dropped).  The input halo is kept in shared memory as 16-byte rows
 // [k-chunk][cell] with cells (hz, hy, hx), hx = 0..31, in row-major order
-// after one leading pad row, i.e. in the canonical K-major layout without
+// after TC_PAD pad rows, i.e. in the canonical K-major layout without
 // swizzle (8-row core matrices of 16-byte rows); the A operand of tap
-// (tz, ty, tx) is then the same layout starting (tz*6 + ty)*32 + tx rows in.
-// The weights are [tap][k-chunk][n] 16-byte rows, the same layout for B.
-// One thread issues the MMAs into a TMEM accumulator (FP32, N columns) and
-// commits them to an mbarrier; the wait is bounded in time, after which the
-// kernel sets *fault, waits once more (bounded) and frees its TMEM.
+// (tz, ty, tx) is then the same layout starting TC_PAD - 1 + (tz*6 + ty)*32
+// + tx rows in.  Each k-chunk plane of a tile's halo is one tensor-memory-
+// access copy: a 5-D view (8 channels, k-chunk, x, y, z) of the channels-last
+// activations, box (8, 1, 32, 6, 3) at (0, kc, x0 - 1, y0 - 1, z - 1), which
+// lands in exactly this row order and is zero-filled outside the mesh.  The
+// weights are [tap][k-chunk][n] 16-byte rows (the same layout for B) and
+// arrive by one bulk copy per CTA.  One lane issues the MMAs into TMEM
+// accumulators (FP32) and commits them to an mbarrier.  Every wait is
+// bounded in time; on expiry the kernel sets *fault, waits once more
+// (bounded) for its own operations in flight and frees its TMEM.
 constexpr int TC_HY = RN_TY + 2, TC_ROWS = 3 * TC_HY * 32;  // halo cells
-constexpr int TC_NE = 584;  // rows per k-chunk: pad + halo + the overrun of the last taps (>= 578)
-constexpr int TC_TX = 30;   // valid cells per tile row
+constexpr int TC_PAD = 8;    // leading pad rows: the halo copy lands 128-byte aligned
+constexpr int TC_NE = 592;   // rows per k-chunk plane (>= TC_PAD + the last tap's overrun = 585); 74 x 128 B
+constexpr int TC_TX = 30;    // valid cells per tile row
+constexpr uint32_t TC_PLANE_BYTES = (uint32_t)TC_ROWS * 16;  // one halo copy
 // weights in the shared-memory layout of the tensor-core layers, per layer
 // [27][Cin/8][N][8] BF16 (N = 32, or 16 for the last layer): one bulk copy each
 constexpr long long TCO1 = 13824, TCO2 = 41472, TCO3 = 69120, TC_TOTAL = 82944;
@@ -198,7 +208,8 @@ constexpr int TC_NACC = 4;
 
 __host__ __device__ constexpr size_t tc_smem(int cinp, int n, int nbuf)
 {
-    return (size_t)nbuf * (cinp / 8) * TC_NE * 16 + (size_t)27 * (cinp / 8) * n * 16 + 32;
+    // 128 bytes of alignment slack, halo planes, weights, 4 mbarriers + TMEM slot
+    return 128 + (size_t)nbuf * (cinp / 8) * TC_NE * 16 + (size_t)27 * (cinp / 8) * n * 16 + 64;
 }
 
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes)
@@ -242,18 +253,34 @@ __device__ __forceinline__ bool tc_mbar_wait(uint32_t m, unsigned parity, unsign
     }
 }
 
+// the halo planes of one tile (KC copies) into the buffer at hb, counted on mbar
+template <int KC>
+__device__ __forceinline__ void tc_load_halo(const CUtensorMap *tm, uint32_t hb, uint32_t mbar, int x0, int y0, int z)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(KC * TC_PLANE_BYTES)
+                 : "memory");
+#pragma unroll
+    for (int v = 0; v < KC; ++v)
+        asm volatile(
+            "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+            "%5, %6}], [%7];\n" ::"r"(hb + (uint32_t)(v * TC_NE + TC_PAD) * 16u),
+            "l"(tm), "r"(0), "r"(v), "r"(x0 - 1), "r"(y0 - 1), "r"(z - 1), "r"(mbar)
+            : "memory");
+}
+
 template <int CINP_, int N_, bool LAST, int NBUF>
-__global__ void __launch_bounds__(128) k_rnet_conv_tc(const __nv_bfloat16 *__restrict__ in,
+__global__ void __launch_bounds__(128) k_rnet_conv_tc(const __grid_constant__ CUtensorMap tmap,
                                                       const __nv_bfloat16 *__restrict__ Wtc,
                                                       const float *__restrict__ bias, int cout, void *out, int nx,
                                                       int ny, int nz, int *fault)
 {
     constexpr int KC = CINP_ / 8;  // 16-byte k-chunks per cell
     extern __shared__ __align__(128) unsigned char tc_smem_raw[];
-    uint4 *hal2 = (uint4 *)tc_smem_raw;                // halo buffers [NBUF][KC][TC_NE]
+    unsigned char *base = tc_smem_raw + ((128u - (smem_u32(tc_smem_raw) & 127u)) & 127u);
+    uint4 *hal2 = (uint4 *)base;                       // halo planes [NBUF][KC][TC_NE], 128-byte aligned
     uint4 *wsm = hal2 + NBUF * KC * TC_NE;             // [27][KC][N_]
-    uint64_t *mbar = (uint64_t *)(wsm + 27 * KC * N_); // [0]: MMAs done, [1]: weights landed
-    uint32_t *tmem_slot = (uint32_t *)(mbar + 2);      // 4 bytes
+    uint64_t *mbar = (uint64_t *)(wsm + 27 * KC * N_); // [0] MMAs done, [1] weights, [2 + b] halo buffer b
+    uint32_t *tmem_slot = (uint32_t *)(mbar + 4);
     constexpr uint32_t WBYTES = 27u * KC * N_ * 16u;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int txc = (nx + TC_TX - 1) / TC_TX, tyc = (ny + RN_TY - 1) / RN_TY;
@@ -264,168 +291,177 @@ __global__ void __launch_bounds__(128) k_rnet_conv_tc(const __nv_bfloat16 *__res
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
-    if (threadIdx.x == 32) {
-        tc_mbar_init(smem_u32(mbar));
-        tc_mbar_init(smem_u32(mbar + 1));
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const uint32_t tmem = *tmem_slot;
-    // weights: one bulk copy of the layer's [27][KC][N] rows, counted on mbar[1]
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mbar + 1)),
-                     "r"(WBYTES)
-                     : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                smem_u32(wsm)),
-            "l"(Wtc), "r"(WBYTES), "r"(smem_u32(mbar + 1))
-            : "memory");
-    }
-    const uint32_t mb = smem_u32(mbar);
-    bool wok = true;
-    // input halo of a tile: cell (hz, hy, hx) -> global (z + hz - 1, y0 + hy - 1, x0 + hx - 1),
-    // row 1 + cell; 16-byte asynchronous copies, zero-filled outside the mesh
-    auto stage = [&](int tl, uint4 *hb) {
-        const int sx0 = (tl % txc) * TC_TX, sy0 = ((tl / txc) % tyc) * RN_TY, sz = tl / (txc * tyc);
-        for (int e = threadIdx.x; e < TC_ROWS * KC; e += blockDim.x) {
-            const int v = e % KC, cell = e / KC;
-            const int hx = cell & 31, hy = (cell >> 5) % TC_HY, hz = (cell >> 5) / TC_HY;
-            const int gx = sx0 + hx - 1, gy = sy0 + hy - 1, gz = sz + hz - 1;
-            const bool inside = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz;
-            const __nv_bfloat16 *src = inside ? in + ((size_t)(gz * ny + gy) * nx + gx) * CINP_ + v * 8 : in;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(hb + v * TC_NE + 1 + cell)),
-                         "l"(src), "r"(inside ? 16 : 0)
-                         : "memory");
-        }
-    };
-    if (NBUF == 2 && (int)blockIdx.x < ntiles) stage(blockIdx.x, hal2);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    // pad rows (never written by the copies): zero in every buffer
+    if (threadIdx.x == 32)
+        for (int i = 0; i < 4; ++i) tc_mbar_init(smem_u32(mbar + i));
+    // pad rows (never written by the copies): zero in every plane
     for (int e = threadIdx.x; e < NBUF * KC * (TC_NE - TC_ROWS); e += blockDim.x) {
         const int v = e / (TC_NE - TC_ROWS), r = e % (TC_NE - TC_ROWS);
-        hal2[v * TC_NE + (r == 0 ? 0 : TC_ROWS + r)] = make_uint4(0u, 0u, 0u, 0u);
-    }
-    // persistent loop over tiles; the weights stay in shared memory and the
-    // next tile's halo is copied in while this tile's MMAs and epilogue run
-    for (int tile = blockIdx.x, it = 0; tile < ntiles; tile += gridDim.x, ++it) {
-    const int x0 = (tile % txc) * TC_TX, y0 = ((tile / txc) % tyc) * RN_TY, z = tile / (txc * tyc);
-    uint4 *hal = hal2 + (NBUF == 2 ? (it & 1) : 0) * KC * TC_NE;
-    if constexpr (NBUF == 2) {
-        // the next tile's halo goes to the other buffer while this one is used
-        if (tile + (int)gridDim.x < ntiles) stage(tile + gridDim.x, hal2 + ((it + 1) & 1) * KC * TC_NE);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-        asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // all but the newest group: this tile's halo
-    } else {
-        stage(tile, hal);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        hal2[v * TC_NE + (r < TC_PAD ? r : TC_ROWS + r)] = make_uint4(0u, 0u, 0u, 0u);
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (warp == 0) {
-    if (lane == 0) {
-        const uint32_t hal_s = smem_u32(hal), w_s = smem_u32(wsm);
-        constexpr uint32_t idesc = umma_idesc_bf16<N_>();
-        if (it == 0) {
-            wok = tc_mbar_wait(smem_u32(mbar + 1), 0, TC_WAIT_NS);
-            if (!wok) {
-                atomicExch(fault, 1);
-                (void)tc_mbar_wait(smem_u32(mbar + 1), 0, TC_WAIT_NS);  // the copy in flight
-            }
-        }
-        for (int t = 0; t < (wok ? 27 : 0); ++t) {
-            const int tz = t / 9, ty = (t / 3) % 3, tx = t % 3;
-            const uint32_t row0 = (uint32_t)((tz * TC_HY + ty) * 32 + tx);
-#pragma unroll
-            for (int ks = 0; ks < KC / 2; ++ks) {
-                const uint64_t ad = umma_desc(hal_s + ((uint32_t)(2 * ks * TC_NE) + row0) * 16u, TC_NE * 16u, 128u);
-                const uint64_t bd = umma_desc(w_s + (uint32_t)((t * KC + 2 * ks) * N_) * 16u, N_ * 16u, 128u);
-                const int i = t * (KC / 2) + ks;
-                const uint32_t acc = (i >= TC_NACC) ? 1u : 0u;  // the first MMA of each accumulator overwrites it
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + 32u * (i % TC_NACC)),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                    : "memory");
-            }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb)
-                     : "memory");
-    }
-    __syncwarp();  // the other lanes of the issuing warp do not spin beside it
-    }
-    bool ok = tc_mbar_wait(mb, it & 1, TC_WAIT_NS);
-    if (!ok) {
-        if (lane == 0) atomicExch(fault, 1);
-        ok = tc_mbar_wait(mb, it & 1, TC_WAIT_NS);  // let the MMAs in flight finish before TMEM is freed
-    }
-    // one decision for the whole CTA (the TMEM loads below are warp-collective)
-    ok = __syncthreads_and(ok) != 0;
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (!ok) break;  // the barrier phase is lost: stop, free TMEM below
-    {
-        // warp w reads TMEM lanes 32w..32w+31 = tile rows oy = w, ox = lane; the
-        // accumulators are summed in FP32
-        float v[N_];
-#pragma unroll
-        for (int c = 0; c < N_; ++c) v[c] = 0.0f;
-#pragma unroll
-        for (int a = 0; a < TC_NACC; ++a) {
-            uint32_t u[N_];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + 32u * a;
-            if constexpr (N_ == 32) {
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-                    : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
-                      "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
-                      "=r"(u[15]), "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]),
-                      "=r"(u[22]), "=r"(u[23]), "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]),
-                      "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
-                    : "r"(taddr));
-            } else {
-                static_assert(N_ == 16, "N is 16 or 32");
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];\n"
-                    : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
-                      "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
-                      "=r"(u[15])
-                    : "r"(taddr));
-            }
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-            for (int c = 0; c < N_; ++c) v[c] += __uint_as_float(u[c]);
-        }
-        const int x = x0 + lane - 1, y = y0 + warp;
-        if (lane >= 1 && lane <= TC_TX && x < nx && y < ny) {
-            const size_t ncell = (size_t)nx * ny * nz;
-            const size_t cell = ((size_t)z * ny + y) * nx + x;
-            if constexpr (!LAST) {
-                __align__(16) __nv_bfloat162 h[16];
-#pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    h[c] = __floats2bfloat162_rn(fmaxf(v[2 * c] + bias[2 * c], 0.0f),
-                                                 fmaxf(v[2 * c + 1] + bias[2 * c + 1], 0.0f));
-                uint4 *dst = (uint4 *)((__nv_bfloat16 *)out + cell * 32);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) dst[q] = ((const uint4 *)h)[q];
-            } else {
-                float *r = (float *)out;
-                for (int c = 0; c < cout; ++c) r[c * ncell + cell] = v[c] + bias[c];
-            }
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t mb = smem_u32(mbar), mw = smem_u32(mbar + 1);
+    const uint32_t hal_s = smem_u32(hal2), w_s = smem_u32(wsm);
+    auto tile_xyz = [&](int tl, int &x0, int &y0, int &z) {
+        x0 = (tl % txc) * TC_TX;
+        y0 = ((tl / txc) % tyc) * RN_TY;
+        z = tl / (txc * tyc);
+    };
+    // lane 0 of warp 0: weights and the first tile's halo in flight
+    bool wok = true;
+    int uses[2] = {0, 0};  // completed uses of each halo buffer's barrier (its parity)
+    bool pending = false;  // a halo copy issued and not yet waited for
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mw), "r"(WBYTES) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(w_s),
+            "l"(Wtc), "r"(WBYTES), "r"(mw)
+            : "memory");
+        if ((int)blockIdx.x < ntiles) {
+            int x0, y0, z;
+            tile_xyz(blockIdx.x, x0, y0, z);
+            tc_load_halo<KC>(&tmap, hal_s, smem_u32(mbar + 2), x0, y0, z);
+            pending = true;
         }
     }
-    // TMEM reads and halo reads of this tile done before the next tile refills them
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
+    // persistent loop over tiles; the weights stay in shared memory and the
+    // next tile's halo is copied in while this tile's MMAs or epilogue run
+    for (int tile = blockIdx.x, it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+        int x0, y0, z;
+        tile_xyz(tile, x0, y0, z);
+        const int b = NBUF == 2 ? (it & 1) : 0;
+        const int next = tile + (int)gridDim.x;
+        if (warp == 0) {
+            if (lane == 0) {
+                if (it == 0) {
+                    wok = tc_mbar_wait(mw, 0, TC_WAIT_NS);
+                    if (!wok) {
+                        atomicExch(fault, 1);
+                        (void)tc_mbar_wait(mw, 0, TC_WAIT_NS);  // the copy in flight
+                    }
+                }
+                bool hok = tc_mbar_wait(smem_u32(mbar + 2 + b), uses[b] & 1, TC_WAIT_NS);
+                if (!hok) {
+                    atomicExch(fault, 1);
+                    hok = tc_mbar_wait(smem_u32(mbar + 2 + b), uses[b] & 1, TC_WAIT_NS);
+                }
+                uses[b]++;
+                pending = !hok;
+                if (wok && hok) {
+                    constexpr uint32_t idesc = umma_idesc_bf16<N_>();
+                    const uint32_t hb = hal_s + (uint32_t)(b * KC * TC_NE) * 16u;
+                    for (int t = 0; t < 27; ++t) {
+                        const int tz = t / 9, ty = (t / 3) % 3, tx = t % 3;
+                        const uint32_t row0 = (uint32_t)(TC_PAD - 1 + (tz * TC_HY + ty) * 32 + tx);
+#pragma unroll
+                        for (int ks = 0; ks < KC / 2; ++ks) {
+                            const uint64_t ad = umma_desc(hb + ((uint32_t)(2 * ks * TC_NE) + row0) * 16u, TC_NE * 16u, 128u);
+                            const uint64_t bd = umma_desc(w_s + (uint32_t)((t * KC + 2 * ks) * N_) * 16u, N_ * 16u, 128u);
+                            const int i = t * (KC / 2) + ks;
+                            const uint32_t acc = (i >= TC_NACC) ? 1u : 0u;  // the first MMA of each accumulator overwrites it
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                    tmem + 32u * (i % TC_NACC)),
+                                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                                : "memory");
+                        }
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb)
+                             : "memory");
+                // two buffers: the other one was last read by the previous tile's MMAs, which completed
+                if (NBUF == 2 && hok && next < ntiles) {
+                    int nx0, ny0, nz0;
+                    tile_xyz(next, nx0, ny0, nz0);
+                    tc_load_halo<KC>(&tmap, hal_s + (uint32_t)((b ^ 1) * KC * TC_NE) * 16u, smem_u32(mbar + 2 + (b ^ 1)),
+                                     nx0, ny0, nz0);
+                    pending = true;
+                }
+            }
+            __syncwarp();  // the other lanes of the issuing warp do not spin beside it
+        }
+        bool ok = tc_mbar_wait(mb, it & 1, TC_WAIT_NS);
+        if (!ok) {
+            if (lane == 0) atomicExch(fault, 1);
+            ok = tc_mbar_wait(mb, it & 1, TC_WAIT_NS);  // let the MMAs in flight finish before TMEM is freed
+        }
+        // one buffer: this tile's MMAs are done with it, so the next tile's halo can come in now
+        if (NBUF == 1 && threadIdx.x == 0 && ok && next < ntiles) {
+            int nx0, ny0, nz0;
+            tile_xyz(next, nx0, ny0, nz0);
+            tc_load_halo<KC>(&tmap, hal_s, smem_u32(mbar + 2), nx0, ny0, nz0);
+            pending = true;
+        }
+        // one decision for the whole CTA (the TMEM loads below are warp-collective)
+        ok = __syncthreads_and(ok) != 0;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (!ok) break;  // the barrier phase is lost: stop, free TMEM below
+        {
+            // warp w reads TMEM lanes 32w..32w+31 = tile rows oy = w, ox = lane; the
+            // accumulators are summed in FP32
+            float v[N_];
+#pragma unroll
+            for (int c = 0; c < N_; ++c) v[c] = 0.0f;
+#pragma unroll
+            for (int a = 0; a < TC_NACC; ++a) {
+                uint32_t u[N_];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + 32u * a;
+                if constexpr (N_ == 32) {
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+                          "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]),
+                          "=r"(u[14]), "=r"(u[15]), "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]),
+                          "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]),
+                          "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+                        : "r"(taddr));
+                } else {
+                    static_assert(N_ == 16, "N is 16 or 32");
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                        "[%16];\n"
+                        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+                          "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]),
+                          "=r"(u[14]), "=r"(u[15])
+                        : "r"(taddr));
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+                for (int c = 0; c < N_; ++c) v[c] += __uint_as_float(u[c]);
+            }
+            const int x = x0 + lane - 1, y = y0 + warp;
+            if (lane >= 1 && lane <= TC_TX && x < nx && y < ny) {
+                const size_t ncell = (size_t)nx * ny * nz;
+                const size_t cell = ((size_t)z * ny + y) * nx + x;
+                if constexpr (!LAST) {
+                    __align__(16) __nv_bfloat162 h[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c)
+                        h[c] = __floats2bfloat162_rn(fmaxf(v[2 * c] + bias[2 * c], 0.0f),
+                                                     fmaxf(v[2 * c + 1] + bias[2 * c + 1], 0.0f));
+                    uint4 *dst = (uint4 *)((__nv_bfloat16 *)out + cell * 32);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) dst[q] = ((const uint4 *)h)[q];
+                } else {
+                    float *r = (float *)out;
+                    for (int c = 0; c < cout; ++c) r[c * ncell + cell] = v[c] + bias[c];
+                }
+            }
+        }
+        // TMEM reads of this tile done before the next tile's MMAs overwrite the accumulators
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    if (threadIdx.x == 0 && (int)blockIdx.x >= ntiles) (void)tc_mbar_wait(smem_u32(mbar + 1), 0, TC_WAIT_NS);
+    // a halo copy still in flight (only after a lost barrier phase): let it land first
+    if (threadIdx.x == 0 && pending) {
+        for (int bb = 0; bb < NBUF; ++bb) (void)tc_mbar_wait(smem_u32(mbar + 2 + bb), uses[bb] & 1, TC_WAIT_NS);
+    }
+    if (threadIdx.x == 0 && (int)blockIdx.x >= ntiles) (void)tc_mbar_wait(mw, 0, TC_WAIT_NS);
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(32 * TC_NACC)
                      : "memory");
@@ -636,6 +672,9 @@ struct mmx_rnet {
     int *fault = nullptr;  // set by a tensor-core layer whose bounded wait ran out
     int nsm = 1;
     int tc_nbuf = 1;       // MMX_RNET_NBUF: halo buffers per tensor-core CTA (1 or 2)
+    CUtensorMap tm[NLAYER];  // 5-D views of the layer inputs for the halo copies
+    int tm_nx = 0, tm_ny = 0, tm_nz = 0;
+    bool tm_ok = false;
     bool mma_sync = false; // MMX_RNET_MMA_SYNC=1: the mma.sync layers instead of tcgen05
     int step = 0;
     int nx = 0, ny = 0, nz = 0;
@@ -677,6 +716,44 @@ cudaError_t set_tc_smem()
 template <int NB>
 void forward_tc(mmx_rnet *net, int nx, int ny, int nz);
 
+// 5-D view (8 channels, k-chunk, x, y, z) of channels-last BF16 activations
+// with cinp channels per cell; box (8, 1, 32, 6, 3), zero fill outside
+bool encode_halo_map(CUtensorMap *tm, const void *base, int cinp, int nx, int ny, int nz)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+    if (!enc) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return false;
+        }
+        enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const cuuint64_t dims[5] = {8, (cuuint64_t)(cinp / 8), (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t row = (cuuint64_t)cinp * 2;
+    const cuuint64_t strides[4] = {16, row, row * nx, row * nx * ny};
+    const cuuint32_t box[5] = {8, 1, 32, (cuuint32_t)TC_HY, 3};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool halo_maps(mmx_rnet *net, int nx, int ny, int nz)
+{
+    if (net->tm_nx == nx && net->tm_ny == ny && net->tm_nz == nz) return net->tm_ok;
+    bool ok = true;
+    for (int l = 0; l < NLAYER && ok; ++l) ok = encode_halo_map(&net->tm[l], net->a[l], CINP[l], nx, ny, nz);
+    net->tm_nx = nx;
+    net->tm_ny = ny;
+    net->tm_nz = nz;
+    net->tm_ok = ok;
+    return ok;
+}
+
 cudaError_t raise_conv_smem()
 {
     if (smem_ready) return cudaSuccess;
@@ -715,7 +792,7 @@ int check_mesh(mmx_rnet *net, int nx, int ny, int nz)
 // forward through all layers from the packed input a[0]; output in net->r
 void forward_layers(mmx_rnet *net, int nx, int ny, int nz)
 {
-    if (!net->mma_sync) {
+    if (!net->mma_sync && halo_maps(net, nx, ny, nz)) {
         if (net->tc_nbuf == 2)
             forward_tc<2>(net, nx, ny, nz);
         else
@@ -744,13 +821,13 @@ void forward_tc(mmx_rnet *net, int nx, int ny, int nz)
     const long long cap = (long long)net->nsm * (NB == 1 ? 2 : 1);
     const dim3 g((unsigned)(tiles < cap ? tiles : cap));
     k_rnet_conv_tc<16, 32, false, NB><<<g, 128, tc_smem(16, 32, NB), net->s>>>(
-        net->a[0], net->Wtc, net->P + p_off(0) + 27 * 32 * 6, 32, net->a[1], nx, ny, nz, net->fault);
+        net->tm[0], net->Wtc, net->P + p_off(0) + 27 * 32 * 6, 32, net->a[1], nx, ny, nz, net->fault);
     k_rnet_conv_tc<32, 32, false, NB><<<g, 128, tc_smem(32, 32, NB), net->s>>>(
-        net->a[1], net->Wtc + TCO1, net->P + p_off(1) + 27 * 32 * 32, 32, net->a[2], nx, ny, nz, net->fault);
+        net->tm[1], net->Wtc + TCO1, net->P + p_off(1) + 27 * 32 * 32, 32, net->a[2], nx, ny, nz, net->fault);
     k_rnet_conv_tc<32, 32, false, NB><<<g, 128, tc_smem(32, 32, NB), net->s>>>(
-        net->a[2], net->Wtc + TCO2, net->P + p_off(2) + 27 * 32 * 32, 32, net->a[3], nx, ny, nz, net->fault);
+        net->tm[2], net->Wtc + TCO2, net->P + p_off(2) + 27 * 32 * 32, 32, net->a[3], nx, ny, nz, net->fault);
     k_rnet_conv_tc<32, 16, true, NB><<<g, 128, tc_smem(32, 16, NB), net->s>>>(
-        net->a[3], net->Wtc + TCO3, net->P + p_off(3) + 27 * 3 * 32, 3, net->r, nx, ny, nz, net->fault);
+        net->tm[3], net->Wtc + TCO3, net->P + p_off(3) + 27 * 3 * 32, 3, net->r, nx, ny, nz, net->fault);
 }
 
 int refresh_weights(mmx_rnet *net)
