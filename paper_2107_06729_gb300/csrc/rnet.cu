@@ -675,6 +675,7 @@ struct mmx_rnet {
     CUtensorMap tm[NLAYER];  // 5-D views of the layer inputs for the halo copies
     int tm_nx = 0, tm_ny = 0, tm_nz = 0;
     bool tm_ok = false;
+    bool require_tc = false;  // MMX_RNET_REQUIRE_TC=1: no fallback when the halo copies cannot be encoded
     bool mma_sync = false; // MMX_RNET_MMA_SYNC=1: the mma.sync layers instead of tcgen05
     int step = 0;
     int nx = 0, ny = 0, nz = 0;
@@ -912,6 +913,8 @@ extern "C" int mmx_rnet_create(long long max_cells, void *cuda_stream, mmx_rnet 
         net->nsm = 1;
     const char *ms = getenv("MMX_RNET_MMA_SYNC");
     net->mma_sync = ms && atoi(ms) != 0;
+    const char *rq = getenv("MMX_RNET_REQUIRE_TC");
+    net->require_tc = rq && atoi(rq) != 0;
     const char *nb = getenv("MMX_RNET_NBUF");
     net->tc_nbuf = (nb && atoi(nb) == 2) ? 2 : 1;
     if (raise_conv_smem() != cudaSuccess || cudaMemsetAsync(net->fault, 0, sizeof(int), net->s) != cudaSuccess ||
@@ -953,6 +956,8 @@ extern "C" int mmx_rnet_forward(mmx_rnet *net, int nx, int ny, int nz, const flo
     if (!net || !x_dev) return rfail(net, MMX_ERR_ARG, "NULL argument");
     if (int rc = check_mesh(net, nx, ny, nz)) return rc;
     const long long n = (long long)nx * ny * nz;
+    if (!net->mma_sync && net->require_tc && !halo_maps(net, nx, ny, nz))
+        return rfail(net, MMX_ERR_ARG, "the halo tensor maps cannot be encoded for this mesh");
     k_rnet_pack<<<(unsigned)((n + 255) / 256), 256, 0, net->s>>>(x_dev, n, net->a[0]);
     forward_layers(net, nx, ny, nz);
     if (r_dev) RCK(cudaMemcpyAsync(r_dev, net->r, n * 3 * sizeof(float), cudaMemcpyDeviceToDevice, net->s));

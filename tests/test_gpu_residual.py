@@ -52,6 +52,8 @@ def test_forward_layer_by_layer_matches_oracle(n, path, monkeypatch):
     (MMX_RNET_NBUF=2), and mma.sync (MMX_RNET_MMA_SYNC=1)."""
     if path == "mma_sync":
         monkeypatch.setenv("MMX_RNET_MMA_SYNC", "1")
+    else:
+        monkeypatch.setenv("MMX_RNET_REQUIRE_TC", "1")  # the tensor-core path, no fallback
     if path == "tcgen05_2buf":
         monkeypatch.setenv("MMX_RNET_NBUF", "2")
     torch = torch_cuda()
