@@ -20,7 +20,9 @@ for the parity tests:
   output is not rounded;
 * training loss: the mean over cells and the 3 channels of (r - target)^2;
   gradients treat the BF16 roundings as the identity (straight-through) and
-  use the rounded weights and stored activations; Adam (Kingma and Ba,
+  use the rounded weights and stored activations; with the tensor-core
+  backward the output gradient of each layer is rounded to BF16 where it
+  enters the input-gradient convolution (``quantize_grad``); Adam (Kingma and Ba,
   2015: beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected moments) updates
   the FP32 master parameters.
 
@@ -113,10 +115,14 @@ def loss(r, target):
     return float(np.mean((np.asarray(r, dtype=np.float64) - target) ** 2))
 
 
-def backward(acts, params, target, quantize=True):
+def backward(acts, params, target, quantize=True, quantize_grad=False):
     """Gradient of ``loss(acts[-1], target)`` with respect to the flat
-    parameters, given the activations of ``forward``."""
+    parameters, given the activations of ``forward``.  With quantize_grad,
+    the output gradient of each layer l > 0 is rounded to BF16 where it
+    enters the input-gradient convolution (the tensor-core backward); the
+    weight gradient uses it unrounded."""
     q = bf16_round if quantize else (lambda v: np.asarray(v, dtype=np.float64))
+    qg = bf16_round if quantize_grad else (lambda v: v)
     layers = unpack(params)
     r = acts[-1]
     dz = 2.0 * (r - target) / r.size
@@ -131,8 +137,9 @@ def backward(acts, params, target, quantize=True):
         grads[l] = (dW, db)
         if l > 0:
             dA = np.zeros_like(A)
+            dzq = qg(dz)
             for t, (tz, ty, tx) in enumerate(TAPS):
-                dA += np.einsum("oc,ozyx->czyx", Wq[t], shift(dz, -tz, -ty, -tx))
+                dA += np.einsum("oc,ozyx->czyx", Wq[t], shift(dzq, -tz, -ty, -tx))
             dz = dA * (A > 0)
     return np.concatenate([np.concatenate([dW.ravel(), db]) for dW, db in grads])
 

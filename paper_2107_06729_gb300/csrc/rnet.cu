@@ -268,11 +268,16 @@ __device__ __forceinline__ void tc_load_halo(const CUtensorMap *tm, uint32_t hb,
             : "memory");
 }
 
-template <int CINP_, int N_, bool LAST, int NBUF>
+// MODE 0: hidden layer (bias, ReLU, BF16 [cells][32] out); 1: last layer (bias,
+// FP32 [3][cells] out); 2: input gradient of a layer (tap-flipped, transposed
+// weights; FP32 [cells][32] out, masked by ReLU' of the layer input `mask`,
+// and its BF16 copy in out2)
+template <int CINP_, int N_, int MODE, int NBUF>
 __global__ void __launch_bounds__(128) k_rnet_conv_tc(const __grid_constant__ CUtensorMap tmap,
                                                       const __nv_bfloat16 *__restrict__ Wtc,
                                                       const float *__restrict__ bias, int cout, void *out, int nx,
-                                                      int ny, int nz, int *fault)
+                                                      int ny, int nz, int *fault,
+                                                      const __nv_bfloat16 *__restrict__ mask, void *out2)
 {
     constexpr int KC = CINP_ / 8;  // 16-byte k-chunks per cell
     extern __shared__ __align__(128) unsigned char tc_smem_raw[];
@@ -438,7 +443,7 @@ __global__ void __launch_bounds__(128) k_rnet_conv_tc(const __grid_constant__ CU
             if (lane >= 1 && lane <= TC_TX && x < nx && y < ny) {
                 const size_t ncell = (size_t)nx * ny * nz;
                 const size_t cell = ((size_t)z * ny + y) * nx + x;
-                if constexpr (!LAST) {
+                if constexpr (MODE == 0) {
                     __align__(16) __nv_bfloat162 h[16];
 #pragma unroll
                     for (int c = 0; c < 16; ++c)
@@ -447,6 +452,22 @@ __global__ void __launch_bounds__(128) k_rnet_conv_tc(const __grid_constant__ CU
                     uint4 *dst = (uint4 *)((__nv_bfloat16 *)out + cell * 32);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) dst[q] = ((const uint4 *)h)[q];
+                } else if constexpr (MODE == 2) {
+                    __align__(16) __nv_bfloat16 mk[32];
+                    __align__(16) float g[32];
+                    __align__(16) __nv_bfloat162 h[16];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) ((uint4 *)mk)[q] = ((const uint4 *)(mask + cell * 32))[q];
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) g[c] = (__bfloat162float(mk[c]) > 0.0f) ? v[c] : 0.0f;
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) h[c] = __floats2bfloat162_rn(g[2 * c], g[2 * c + 1]);
+                    uint4 *df = (uint4 *)((float *)out + cell * 32);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) df[q] = ((const uint4 *)g)[q];
+                    uint4 *db = (uint4 *)((__nv_bfloat16 *)out2 + cell * 32);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) db[q] = ((const uint4 *)h)[q];
                 } else {
                     float *r = (float *)out;
                     for (int c = 0; c < cout; ++c) r[c * ncell + cell] = v[c] + bias[c];
@@ -469,7 +490,7 @@ __global__ void __launch_bounds__(128) k_rnet_conv_tc(const __grid_constant__ CU
 
 // loss terms: dz3 [cells][8] = 2 (r - target) / (3 cells), sum of squares into *loss
 __global__ void k_rnet_loss(const float *__restrict__ r, const float *__restrict__ tgt, long long n,
-                            float *__restrict__ dz3, double *loss)
+                            float *__restrict__ dz3, __nv_bfloat16 *__restrict__ dz3b, double *loss)
 {
     __shared__ double s_sum[8];
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -484,6 +505,8 @@ __global__ void k_rnet_loss(const float *__restrict__ r, const float *__restrict
                 sq += (double)d * d;
             }
             dz3[i * 8 + c] = k * d;
+            dz3b[i * 16 + c] = __float2bfloat16_rn(k * d);
+            dz3b[i * 16 + 8 + c] = __float2bfloat16_rn(0.0f);
         }
     }
 #pragma unroll
@@ -638,6 +661,33 @@ __global__ void k_rnet_cast_tc(const float *__restrict__ P, __nv_bfloat16 *__res
     Wtc[i] = __float2bfloat16_rn(v);
 }
 
+// input-gradient weights in the tensor-core layout: for layer l = 3, 2, 1,
+// [27][Cout_pad/8][32][8] with W'[t'][n = ci][k = co] = W[26 - t'][co][ci]
+// (taps flipped: the gradient reads dz at p - offset); Cout_pad = 16 for the
+// last layer, 32 otherwise
+constexpr long long TT2 = 13824, TT1 = 41472, TT_TOTAL = 69120;
+__global__ void k_rnet_cast_tc_t(const float *__restrict__ P, __nv_bfloat16 *__restrict__ Wt)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= TT_TOTAL) return;
+    long long j, po;
+    int cout, kcn;
+    if (i < TT2) {
+        j = i, po = PO3, cout = 3, kcn = 2;
+    } else if (i < TT1) {
+        j = i - TT2, po = PO2, cout = 32, kcn = 4;
+    } else {
+        j = i - TT1, po = PO1, cout = 32, kcn = 4;
+    }
+    const int e = (int)(j % 8);
+    const long long row = j / 8;
+    const int n = (int)(row % 32), kc = (int)((row / 32) % kcn), tp = (int)(row / (32LL * kcn));
+    const int k = kc * 8 + e;
+    float v = 0.0f;
+    if (k < cout) v = P[po + ((long long)(26 - tp) * cout + k) * 32 + n];
+    Wt[i] = __float2bfloat16_rn(v);
+}
+
 // training pairs: xg (T, [3][cells]) = sum_j w_j G_j
 template <typename T>
 __global__ void k_res_accum(const T *__restrict__ G, double w, T *__restrict__ acc, long long n3, int first)
@@ -665,7 +715,8 @@ struct mmx_rnet {
     cudaStream_t s = nullptr;
     long long max_cells = 0;
     float *P = nullptr, *Pm = nullptr, *Pv = nullptr, *grad = nullptr;
-    __nv_bfloat16 *Wq = nullptr, *Wtc = nullptr;
+    __nv_bfloat16 *Wq = nullptr, *Wtc = nullptr, *Wtt = nullptr;
+    __nv_bfloat16 *dz3b = nullptr, *dzAb = nullptr, *dzBb = nullptr;  // BF16 copies of the output gradients
     __nv_bfloat16 *a[NLAYER] = {nullptr, nullptr, nullptr, nullptr};
     float *r = nullptr, *dz3 = nullptr, *dzA = nullptr, *dzB = nullptr;
     double *loss_d = nullptr;
@@ -673,6 +724,8 @@ struct mmx_rnet {
     int nsm = 1;
     int tc_nbuf = 1;       // MMX_RNET_NBUF: halo buffers per tensor-core CTA (1 or 2)
     CUtensorMap tm[NLAYER];  // 5-D views of the layer inputs for the halo copies
+    CUtensorMap tmg[3];      // the same for the gradients dz3b, dzAb, dzBb
+    bool simt_bwd = false;   // MMX_RNET_SIMT_BWD=1: the FP32 SIMT input-gradient kernels
     int tm_nx = 0, tm_ny = 0, tm_nz = 0;
     bool tm_ok = false;
     bool require_tc = false;  // MMX_RNET_REQUIRE_TC=1: no fallback when the halo copies cannot be encoded
@@ -702,13 +755,19 @@ template <int NB>
 cudaError_t set_tc_smem()
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<16, 32, false, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<16, 32, 0, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)tc_smem(16, 32, NB))) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<32, 32, false, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<32, 32, 0, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)tc_smem(32, 32, NB))) != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(k_rnet_conv_tc<32, 16, true, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<16, 32, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tc_smem(16, 32, 1))) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<32, 32, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tc_smem(32, 32, 1))) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_rnet_conv_tc<32, 16, 1, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)tc_smem(32, 16, NB));
 }
 
@@ -748,6 +807,9 @@ bool halo_maps(mmx_rnet *net, int nx, int ny, int nz)
     if (net->tm_nx == nx && net->tm_ny == ny && net->tm_nz == nz) return net->tm_ok;
     bool ok = true;
     for (int l = 0; l < NLAYER && ok; ++l) ok = encode_halo_map(&net->tm[l], net->a[l], CINP[l], nx, ny, nz);
+    ok = ok && encode_halo_map(&net->tmg[0], net->dz3b, 16, nx, ny, nz) &&
+         encode_halo_map(&net->tmg[1], net->dzAb, 32, nx, ny, nz) &&
+         encode_halo_map(&net->tmg[2], net->dzBb, 32, nx, ny, nz);
     net->tm_nx = nx;
     net->tm_ny = ny;
     net->tm_nz = nz;
@@ -821,20 +883,21 @@ void forward_tc(mmx_rnet *net, int nx, int ny, int nz)
     const long long tiles = (long long)((nx + TC_TX - 1) / TC_TX) * ((ny + RN_TY - 1) / RN_TY) * nz;
     const long long cap = (long long)net->nsm * (NB == 1 ? 2 : 1);
     const dim3 g((unsigned)(tiles < cap ? tiles : cap));
-    k_rnet_conv_tc<16, 32, false, NB><<<g, 128, tc_smem(16, 32, NB), net->s>>>(
-        net->tm[0], net->Wtc, net->P + p_off(0) + 27 * 32 * 6, 32, net->a[1], nx, ny, nz, net->fault);
-    k_rnet_conv_tc<32, 32, false, NB><<<g, 128, tc_smem(32, 32, NB), net->s>>>(
-        net->tm[1], net->Wtc + TCO1, net->P + p_off(1) + 27 * 32 * 32, 32, net->a[2], nx, ny, nz, net->fault);
-    k_rnet_conv_tc<32, 32, false, NB><<<g, 128, tc_smem(32, 32, NB), net->s>>>(
-        net->tm[2], net->Wtc + TCO2, net->P + p_off(2) + 27 * 32 * 32, 32, net->a[3], nx, ny, nz, net->fault);
-    k_rnet_conv_tc<32, 16, true, NB><<<g, 128, tc_smem(32, 16, NB), net->s>>>(
-        net->tm[3], net->Wtc + TCO3, net->P + p_off(3) + 27 * 3 * 32, 3, net->r, nx, ny, nz, net->fault);
+    k_rnet_conv_tc<16, 32, 0, NB><<<g, 128, tc_smem(16, 32, NB), net->s>>>(
+        net->tm[0], net->Wtc, net->P + p_off(0) + 27 * 32 * 6, 32, net->a[1], nx, ny, nz, net->fault, nullptr, nullptr);
+    k_rnet_conv_tc<32, 32, 0, NB><<<g, 128, tc_smem(32, 32, NB), net->s>>>(
+        net->tm[1], net->Wtc + TCO1, net->P + p_off(1) + 27 * 32 * 32, 32, net->a[2], nx, ny, nz, net->fault, nullptr, nullptr);
+    k_rnet_conv_tc<32, 32, 0, NB><<<g, 128, tc_smem(32, 32, NB), net->s>>>(
+        net->tm[2], net->Wtc + TCO2, net->P + p_off(2) + 27 * 32 * 32, 32, net->a[3], nx, ny, nz, net->fault, nullptr, nullptr);
+    k_rnet_conv_tc<32, 16, 1, NB><<<g, 128, tc_smem(32, 16, NB), net->s>>>(
+        net->tm[3], net->Wtc + TCO3, net->P + p_off(3) + 27 * 3 * 32, 3, net->r, nx, ny, nz, net->fault, nullptr, nullptr);
 }
 
 int refresh_weights(mmx_rnet *net)
 {
     k_rnet_cast<<<(unsigned)((WQ_TOTAL + 255) / 256), 256, 0, net->s>>>(net->P, net->Wq);
     k_rnet_cast_tc<<<(unsigned)((TC_TOTAL + 255) / 256), 256, 0, net->s>>>(net->P, net->Wtc);
+    k_rnet_cast_tc_t<<<(unsigned)((TT_TOTAL + 255) / 256), 256, 0, net->s>>>(net->P, net->Wtt);
     RCK(cudaGetLastError());
     return MMX_OK;
 }
@@ -893,6 +956,10 @@ extern "C" int mmx_rnet_create(long long max_cells, void *cuda_stream, mmx_rnet 
               cudaMalloc(&net->Pv, P) == cudaSuccess && cudaMalloc(&net->grad, P) == cudaSuccess &&
               cudaMalloc(&net->Wq, WQ_TOTAL * sizeof(__nv_bfloat16)) == cudaSuccess &&
               cudaMalloc(&net->Wtc, TC_TOTAL * sizeof(__nv_bfloat16)) == cudaSuccess &&
+              cudaMalloc(&net->Wtt, TT_TOTAL * sizeof(__nv_bfloat16)) == cudaSuccess &&
+              cudaMalloc(&net->dz3b, max_cells * 16 * sizeof(__nv_bfloat16)) == cudaSuccess &&
+              cudaMalloc(&net->dzAb, max_cells * 32 * sizeof(__nv_bfloat16)) == cudaSuccess &&
+              cudaMalloc(&net->dzBb, max_cells * 32 * sizeof(__nv_bfloat16)) == cudaSuccess &&
               cudaMalloc(&net->a[0], max_cells * 16 * sizeof(__nv_bfloat16)) == cudaSuccess &&
               cudaMalloc(&net->r, max_cells * 3 * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&net->dz3, max_cells * 8 * sizeof(float)) == cudaSuccess &&
@@ -913,6 +980,8 @@ extern "C" int mmx_rnet_create(long long max_cells, void *cuda_stream, mmx_rnet 
         net->nsm = 1;
     const char *ms = getenv("MMX_RNET_MMA_SYNC");
     net->mma_sync = ms && atoi(ms) != 0;
+    const char *sb = getenv("MMX_RNET_SIMT_BWD");
+    net->simt_bwd = sb && atoi(sb) != 0;
     const char *rq = getenv("MMX_RNET_REQUIRE_TC");
     net->require_tc = rq && atoi(rq) != 0;
     const char *nb = getenv("MMX_RNET_NBUF");
@@ -978,7 +1047,12 @@ extern "C" int mmx_rnet_train_step(mmx_rnet *net, int nx, int ny, int nz, const 
     cudaStream_t s = net->s;
     RCK(cudaMemsetAsync(net->loss_d, 0, sizeof(double), s));
     RCK(cudaMemsetAsync(net->grad, 0, MMX_RNET_PARAMS * sizeof(float), s));
-    k_rnet_loss<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(net->r, target_dev, n, net->dz3, net->loss_d);
+    k_rnet_loss<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(net->r, target_dev, n, net->dz3, net->dz3b,
+                                                           net->loss_d);
+    // input gradients on the tensor cores (dz rounded to BF16 where it enters), or FP32 SIMT
+    const bool tc_bwd = !net->simt_bwd && halo_maps(net, nx, ny, nz);
+    const long long tiles = (long long)((nx + TC_TX - 1) / TC_TX) * ((ny + RN_TY - 1) / RN_TY) * nz;
+    const dim3 gt((unsigned)(tiles < 2LL * net->nsm ? tiles : 2LL * net->nsm));
     const int chunk = 1024;
     const dim3 wg((unsigned)((n + chunk - 1) / chunk), 27);
     const unsigned dg = (unsigned)((n + 7) / 8);
@@ -986,15 +1060,29 @@ extern "C" int mmx_rnet_train_step(mmx_rnet *net, int nx, int ny, int nz, const 
     // layer 3 (32 -> 3)
     k_rnet_wgrad<32, 8><<<wg, 256, 0, s>>>(net->dz3, net->a[3], 32, 3, G + p_off(3), G + p_off(3) + 27 * 3 * 32,
                                            nx, ny, nz, chunk);
-    k_rnet_dgrad<8><<<dg, 256, 0, s>>>(net->dz3, net->Wq + w_off(3), 3, net->a[3], net->dzA, nx, ny, nz);
+    if (tc_bwd)
+        k_rnet_conv_tc<16, 32, 2, 1><<<gt, 128, tc_smem(16, 32, 1), s>>>(net->tmg[0], net->Wtt, nullptr, 32, net->dzA,
+                                                                         nx, ny, nz, net->fault, net->a[3], net->dzAb);
+    else
+        k_rnet_dgrad<8><<<dg, 256, 0, s>>>(net->dz3, net->Wq + w_off(3), 3, net->a[3], net->dzA, nx, ny, nz);
     // layer 2
     k_rnet_wgrad<32, 32><<<wg, 256, 0, s>>>(net->dzA, net->a[2], 32, 32, G + p_off(2),
                                             G + p_off(2) + 27 * 32 * 32, nx, ny, nz, chunk);
-    k_rnet_dgrad<32><<<dg, 256, 0, s>>>(net->dzA, net->Wq + w_off(2), 32, net->a[2], net->dzB, nx, ny, nz);
+    if (tc_bwd)
+        k_rnet_conv_tc<32, 32, 2, 1><<<gt, 128, tc_smem(32, 32, 1), s>>>(net->tmg[1], net->Wtt + TT2, nullptr, 32,
+                                                                         net->dzB, nx, ny, nz, net->fault, net->a[2],
+                                                                         net->dzBb);
+    else
+        k_rnet_dgrad<32><<<dg, 256, 0, s>>>(net->dzA, net->Wq + w_off(2), 32, net->a[2], net->dzB, nx, ny, nz);
     // layer 1
     k_rnet_wgrad<32, 32><<<wg, 256, 0, s>>>(net->dzB, net->a[1], 32, 32, G + p_off(1),
                                             G + p_off(1) + 27 * 32 * 32, nx, ny, nz, chunk);
-    k_rnet_dgrad<32><<<dg, 256, 0, s>>>(net->dzB, net->Wq + w_off(1), 32, net->a[1], net->dzA, nx, ny, nz);
+    if (tc_bwd)
+        k_rnet_conv_tc<32, 32, 2, 1><<<gt, 128, tc_smem(32, 32, 1), s>>>(net->tmg[2], net->Wtt + TT1, nullptr, 32,
+                                                                         net->dzA, nx, ny, nz, net->fault, net->a[1],
+                                                                         net->dzAb);
+    else
+        k_rnet_dgrad<32><<<dg, 256, 0, s>>>(net->dzB, net->Wq + w_off(1), 32, net->a[1], net->dzA, nx, ny, nz);
     // layer 0 (6 -> 32; input padded to 16 channels)
     k_rnet_wgrad<16, 32><<<wg, 256, 0, s>>>(net->dzA, net->a[0], 6, 32, G + p_off(0), G + p_off(0) + 27 * 32 * 6,
                                             nx, ny, nz, chunk);
@@ -1045,7 +1133,8 @@ extern "C" void mmx_rnet_destroy(mmx_rnet *net)
     if (!net) return;
     if (net->s) cudaStreamSynchronize(net->s);
     void *bufs[] = {net->P,   net->Pm,  net->Pv,  net->grad, net->Wq,  net->a[0],  net->a[1], net->a[2],
-                    net->a[3], net->r, net->dz3, net->dzA,  net->dzB, net->loss_d, net->fault, net->Wtc};
+                    net->a[3], net->r, net->dz3, net->dzA,  net->dzB, net->loss_d, net->fault, net->Wtc,
+                    net->Wtt,  net->dz3b, net->dzAb, net->dzBb};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete net;

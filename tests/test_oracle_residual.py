@@ -115,3 +115,21 @@ def test_residual_sample_is_zero_for_an_exactly_extrapolated_field(p):
     assert np.abs(target).max() < 1e-9 * scale
     assert np.array_equal(x[:3], m)
     assert np.abs(x[3:] - G(t) / Ms).max() < 1e-9 * scale
+
+
+def test_backward_gradient_rounding_only_enters_the_input_gradient():
+    """quantize_grad rounds the output gradient where it enters the
+    input-gradient convolution: the last layer's gradient is unchanged, the
+    earlier ones move by a few BF16 units at most."""
+    rng = np.random.default_rng(12)
+    shape = (2, 3, 4)
+    p = W.rnet_params(13, out_scale=1.0).astype(np.float64)
+    x = rng.standard_normal((6,) + shape)
+    target = rng.standard_normal((3,) + shape) * 0.1
+    acts = R.forward(x, p)
+    g0 = R.backward(acts, p, target)
+    g1 = R.backward(acts, p, target, quantize_grad=True)
+    n3 = 27 * 3 * 32 + 3
+    assert np.array_equal(g0[-n3:], g1[-n3:])
+    assert not np.array_equal(g0[:-n3], g1[:-n3])
+    assert np.abs(g1 - g0).max() <= 2 ** -6 * np.abs(g0).max()
