@@ -92,6 +92,19 @@ void mmx_rnet_destroy(mmx_rnet *net);
 int mmx_residual_sample(mmx_ctx *ctx, int p, const void *m_nodes_dev, const double *t_nodes, const void *m_dev,
                         double t, float *x_dev, float *target_dev);
 
+/* Attaches net to an FP32 context that extrapolates (extrap_order >= 0), or
+ * detaches it (net = NULL).  While attached, every extrapolated stage k >= 2
+ * of every attempt (Eq. 4-6) uses the non-self field G_ext + Ms r with r =
+ * net(Y_k, G_ext / Ms) instead of G_ext; stage 1 and the priming steps keep
+ * the exact evaluation, and step control is unchanged (Eq. 5).  The net's
+ * parameters are read at each use (train it between runs if wanted); it must
+ * outlive the attachment, including any batch built while it is attached,
+ * and must not be used by another context's run at the same time.
+ * MMX_ERR_ARG for an FP64 context, extrap_order < 0 or a net created for
+ * fewer cells than the mesh.  Synchronises the context's stream and drops
+ * its captured attempt graphs (rebuilt at the next run). */
+int mmx_set_residual(mmx_ctx *ctx, mmx_rnet *net);
+
 #ifdef __cplusplus
 }
 #endif

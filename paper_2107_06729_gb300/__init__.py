@@ -107,6 +107,7 @@ SIGNATURES = {
     "mmx_rnet_destroy": (None, [_VP]),
     "mmx_residual_sample": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_double), _VP,
                                            ctypes.c_double, _VP, _VP]),
+    "mmx_set_residual": (ctypes.c_int, [_VP, _VP]),
 }
 
 MMX_RNET_PARAMS = 63171
@@ -338,6 +339,11 @@ def mmx_residual_sample(ctx, p, m_nodes_dev, t_nodes, m_dev, t, x_dev, target_de
     return _check(rc, ctx)
 
 
+def mmx_set_residual(ctx, net):
+    """Attaches the residual net (handle) to ctx's extrapolated stages; None detaches."""
+    return _check(lib().mmx_set_residual(ctx, net), ctx)
+
+
 class RNet:
     """Owner of one residual net (the C calls above underneath)."""
 
@@ -476,6 +482,11 @@ class Context:
 
     def set_profiling(self, on):
         return mmx_set_profiling(self.handle, on)
+
+    def set_residual(self, net):
+        """Attaches an RNet (kept alive here) to the extrapolated stages; None detaches."""
+        mmx_set_residual(self.handle, net.handle if net is not None else None)
+        self._rnet = net
 
     def plan(self):
         return mmx_get_plan(self.handle)

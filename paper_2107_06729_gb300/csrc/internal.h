@@ -126,6 +126,7 @@ struct mmx_ctx {
     cudaGraphExec_t gexec[2];
     cudaGraph_t graph[2];
     bool graph_ok[2];
+    struct mmx_rnet *rnet = nullptr;  // learned residual at the extrapolated stages (mmx_set_residual)
     bool use_graphs;
     // profiling
     bool profiling;
@@ -161,6 +162,9 @@ int mmxk_cluster_plan(mmx_ctx *c);
 void mmxk_prepare(mmx_ctx *c, cudaStream_t s);
 // batched runs: the same preparation as an explicit graph node, and a node
 // that sets a loop's while condition from the device state
+// the learned residual at stage k of an extrapolated attempt: G = G_ext + Ms r
+// into c->G (launched on s); returns the number of kernels launched
+int mmxk_rnet_stage(struct mmx_rnet *net, mmx_ctx *c, cudaStream_t s, int k);
 int mmxk_add_prepare_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t nd, mmx_ctx *c, cudaGraphNode_t *out);
 int mmxk_add_gate_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t nd, mmx_ctx *c,
                        cudaGraphConditionalHandle h, int prime_loop, cudaGraphNode_t *out);

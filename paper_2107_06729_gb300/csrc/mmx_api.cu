@@ -211,7 +211,11 @@ int body_kernels(mmx_ctx *c, cudaStream_t s, int prime, cudaGraphConditionalHand
     mmxk_stage(c, s, 0, extrap, prime && p >= 0, cond, use_cond);
     for (int k = 1; k < c->tab.s; ++k) {
         if (!extrap) mmxk_demag(c, s, c->st, 0, 0, c->Y[k & 1], 0, c->G, nullptr);
-        mmxk_stage(c, s, k, extrap, prime && p >= 0, cond, use_cond);
+        // learned residual: its kernels leave G = G_ext + Ms r in c->G, which the
+        // stage then reads like an exact evaluation
+        const bool res = extrap && c->rnet;
+        if (res) c->launches += mmxk_rnet_stage(c->rnet, c, s, k);
+        mmxk_stage(c, s, k, res ? 0 : extrap, prime && p >= 0, cond, use_cond);
     }
     return 0;
 }
@@ -221,7 +225,7 @@ int kernels_per_attempt(const mmx_ctx *c, int prime)
     const int p = c->ctl.p;
     const int extrap = (p >= 0 && !prime);
     const int nd = c->nd;  // kernels per demag evaluation
-    return extrap ? nd + c->tab.s : (nd + 1) * c->tab.s;
+    return extrap ? nd + c->tab.s + (c->rnet ? 6 * (c->tab.s - 1) : 0) : (nd + 1) * c->tab.s;
 }
 
 int build_graph(mmx_ctx *c, int which)

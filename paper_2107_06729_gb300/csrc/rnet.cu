@@ -688,6 +688,48 @@ __global__ void k_rnet_cast_tc_t(const float *__restrict__ P, __nv_bfloat16 *__r
     Wt[i] = __float2bfloat16_rn(v);
 }
 
+// stage k of an extrapolated attempt with the learned residual: Eq. 6 with
+// the attempt's weights (the same sum, in the same order, as the stage
+// kernel's) into G, and the net's packed input (Y_k, G_ext / Ms)
+__global__ void k_res_stage_in(DevState *st, int k, int np1, const float *__restrict__ hist,
+                               const float *__restrict__ Y, long long n, float inv_Ms, float *__restrict__ G,
+                               __nv_bfloat16 *__restrict__ a0)
+{
+    if (st->done) return;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
+    if (i >= n) return;
+    const float *wf = st->coef[k].wf;
+    float g[3] = {0.0f, 0.0f, 0.0f};
+    for (int j = 0; j < np1; ++j) {
+        const float w = wf[j];
+        const float *Gj = hist + (size_t)j * 3 * n;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) g[c] += w * Gj[c * n + i];
+    }
+    __align__(16) __nv_bfloat16 v[16];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        G[c * n + i] = g[c];
+        v[c] = __float2bfloat16_rn(Y[c * n + i]);
+        v[3 + c] = __float2bfloat16_rn(g[c] * inv_Ms);
+    }
+#pragma unroll
+    for (int c = 6; c < 16; ++c) v[c] = __float2bfloat16_rn(0.0f);
+    uint4 *dst = (uint4 *)(a0 + i * 16);
+    dst[0] = ((const uint4 *)v)[0];
+    dst[1] = ((const uint4 *)v)[1];
+}
+
+// G += Ms r (the net's output, [3][cells])
+__global__ void k_res_stage_out(const DevState *st, const float *__restrict__ r, long long n3, float Ms,
+                                float *__restrict__ G)
+{
+    if (st->done) return;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n3) G[i] += Ms * r[i];
+}
+
 // training pairs: xg (T, [3][cells]) = sum_j w_j G_j
 template <typename T>
 __global__ void k_res_accum(const T *__restrict__ G, double w, T *__restrict__ acc, long long n3, int first)
@@ -1166,4 +1208,55 @@ extern "C" int mmx_residual_sample(mmx_ctx *c, int p, const void *m_nodes_dev, c
             }
     return c->prec == MMX_FP64 ? sample_t<double>(c, p, m_nodes_dev, t_nodes, m_dev, t, x_dev, target_dev)
                                : sample_t<float>(c, p, m_nodes_dev, t_nodes, m_dev, t, x_dev, target_dev);
+}
+
+int mmxk_rnet_stage(mmx_rnet *net, mmx_ctx *c, cudaStream_t s, int k)
+{
+    const long long n = c->n;
+    cudaStream_t keep = net->s;
+    net->s = s;  // the context's stream, possibly being captured
+    k_res_stage_in<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->st, k, c->ctl.p + 1, (const float *)c->hist,
+                                                             (const float *)c->Y[k & 1], n, (float)(1.0 / c->mat.Ms),
+                                                             (float *)c->G, net->a[0]);
+    forward_layers(net, c->nx, c->ny, c->nz);
+    k_res_stage_out<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(c->st, net->r, 3 * n, (float)c->mat.Ms,
+                                                                  (float *)c->G);
+    net->s = keep;
+    net->nx = c->nx;
+    net->ny = c->ny;
+    net->nz = c->nz;
+    return 6;
+}
+
+extern "C" int mmx_set_residual(mmx_ctx *c, mmx_rnet *net)
+{
+    if (!c) return MMX_ERR_ARG;
+    if (net) {
+        if (c->prec != MMX_FP32_MIXED) {
+            c->err = "mmx_set_residual: the learned residual runs with FP32 fields only";
+            return MMX_ERR_ARG;
+        }
+        if (c->ctl.p < 0) {
+            c->err = "mmx_set_residual: the context does not extrapolate (extrap_order < 0)";
+            return MMX_ERR_ARG;
+        }
+        if (c->n > net->max_cells) {
+            c->err = "mmx_set_residual: the mesh has more cells than the net was created for";
+            return MMX_ERR_ARG;
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("mmx_set_residual: ") + cudaGetErrorString(e);
+        return MMX_ERR_CUDA;
+    }
+    // the captured attempt graphs hold the old stage sequence
+    for (int i = 0; i < 2; ++i)
+        if (c->graph_ok[i]) {
+            cudaGraphExecDestroy(c->gexec[i]);
+            cudaGraphDestroy(c->graph[i]);
+            c->graph_ok[i] = false;
+        }
+    c->rnet = net;
+    return MMX_OK;
 }

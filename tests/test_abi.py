@@ -116,3 +116,4 @@ def test_residual_net_rejects_invalid_arguments_on_the_host(libpath):
     assert L.mmx_residual_sample(None, 2, None, None, None, 0.0, None, None) == pkg.MMX_ERR_ARG
     assert L.mmx_rnet_forward(None, 4, 4, 1, None, None) == pkg.MMX_ERR_ARG
     assert pkg.mmx_rnet_last_error(None) == ""
+    assert L.mmx_set_residual(None, None) == pkg.MMX_ERR_ARG

@@ -263,3 +263,64 @@ def test_learned_correction_gain_over_extrapolation_alone():
     assert np.isfinite(g_train) and np.isfinite(g_test)
     # measured on a GB300: 9.0 on the training pairs, 2.2 held out
     assert g_train > 2.0 and g_test > 1.3
+
+
+def _film_run(torch, ctx, blob, t_end):
+    """From the saved start state (time, step, history, counters) to t_end."""
+    ctx.load_state(blob)
+    ctx.run(t_end)
+    out = torch.empty(ctx.shape, dtype=torch.float32, device="cuda")
+    ctx.get_m(out)
+    return out.double().cpu().numpy(), ctx.stats()
+
+
+def test_residual_in_the_stage_loop():
+    """mmx_set_residual: a zero net reproduces the plain extrapolated run
+    (G_ext + Ms * 0 is G_ext, summed the same way), a small random net
+    changes it slightly, detaching restores the plain run; invalid
+    attachments are refused."""
+    torch = torch_cuda()
+    import paper_2107_06729_gb300 as pkg
+    n = (32, 16, 2)
+    nx, ny, nz = n
+    mesh = {"n": n, "d": (4e-9, 4e-9, 4e-9)}
+    fld = {"H0": tuple(W.mT((-24.6, 4.3, 0.0))), "pulse": tuple(W.mT((0.0, 20.0, 0.0))), "t_on": 1e-12,
+           "t_off": 3e-12}
+    integ = {"method": "RKDP54", "extrap_order": 4, "adaptive": True, "h": 1e-13, "tol": 1e-5}
+    m0 = W.m_uniform_noise(n, seed=5, noise=0.2)
+    ctx = gpu_context(mesh, MAT, fld, integ, "fp32")
+    zero = pkg.RNet(nx * ny * nz, np.zeros(pkg.MMX_RNET_PARAMS, dtype=np.float32), torch.cuda.current_stream())
+    small = pkg.RNet(nx * ny * nz, W.rnet_params(seed=6, out_scale=1e-3), torch.cuda.current_stream())
+    try:
+        ctx.set_m(torch.from_numpy(m0).to("cuda", torch.float32))
+        blob = ctx.save_state()
+        ref, rs = _film_run(torch, ctx, blob, 5e-12)
+        ctx.set_residual(zero)
+        got, gs = _film_run(torch, ctx, blob, 5e-12)
+        assert gs["accepted"] == rs["accepted"] and gs["rejected"] == rs["rejected"]
+        assert gs["extrap_evals"] == rs["extrap_evals"] and gs["exact_evals"] == rs["exact_evals"]
+        assert np.abs(got - ref).max() <= 1e-6
+        ctx.set_residual(small)
+        per, ps = _film_run(torch, ctx, blob, 5e-12)
+        d = np.abs(per - ref).max()
+        assert np.all(np.isfinite(per)) and 0 < d < 1e-2, d
+        ctx.set_residual(None)
+        back, bs = _film_run(torch, ctx, blob, 5e-12)
+        assert np.array_equal(back, ref) and bs["accepted"] == rs["accepted"]
+        # refused: FP64 context, no extrapolation, a net for fewer cells
+        c64 = gpu_context(mesh, MAT, fld, integ, "fp64")
+        cfull = gpu_context(mesh, MAT, fld, dict(integ, extrap_order=-1), "fp32")
+        tiny = pkg.RNet(8, None, torch.cuda.current_stream())
+        try:
+            for c, net in ((c64, zero), (cfull, zero), (ctx, tiny)):
+                with pytest.raises(pkg.MMXError) as ei:
+                    c.set_residual(net)
+                assert ei.value.code == pkg.MMX_ERR_ARG
+        finally:
+            tiny.close()
+            c64.close()
+            cfull.close()
+    finally:
+        ctx.close()
+        zero.close()
+        small.close()
