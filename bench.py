@@ -276,6 +276,29 @@ def residual_net(pkg, torch, dev, iters=50):
             torch.cuda.synchronize(dev)
             other[name] = round(ev[0].elapsed_time(ev[1]) / 1e3 / iters * 1e6, 2)
             net2.close()
+        # in the stage loop: 5 ps of DP54 p = 4 (FP32) on the same film, plain
+        # extrapolation against the net attached (zero parameters: same steps)
+        integ = {"method": "RKDP54", "extrap_order": 4, "adaptive": True, "h": 1e-13, "tol": 1e-5}
+        fld = {"H0": tuple(W.mT((-24.6, 4.3, 0.0))), "pulse": tuple(W.mT((0.0, 20.0, 0.0))), "t_on": 0.0,
+               "t_off": 2e-10}
+        loop = {}
+        zero = pkg.RNet(cells, np.zeros(pkg.MMX_RNET_PARAMS, dtype=np.float32), stream)
+        for name, net_ in (("extrapolated", None), ("extrapolated_plus_net", zero)):
+            c = pkg.Context(mesh, mat, fld, integ, "fp32", stream)
+            c.set_m(xd[:3].contiguous())
+            if net_ is not None:
+                c.set_residual(net_)
+            c.run(1e-12)  # priming and graph capture
+            s0 = c.stats()
+            ev[0].record(stream)
+            c.run(6e-12)
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            s1 = c.stats()
+            loop[name] = {"ns_per_s": round(5e-12 * 1e9 / (ev[0].elapsed_time(ev[1]) / 1e3), 4),
+                          "accepted": s1["accepted"] - s0["accepted"]}
+            c.close()
+        zero.close()
     flops = 2.0 * cells * 27 * sum(ci * co for ci, co in W.RNET_LAYERS)
     peak, src = bf16_peak()
     ach = flops / fwd_s / 1e12
@@ -285,6 +308,7 @@ def residual_net(pkg, torch, dev, iters=50):
             "us_per_forward_other_kernels": other,
             "exact_demag_us_same_mesh": round(dmg_s * 1e6, 2), "train_step_us": round(trn_s * 1e6, 1),
             "train_step_us_simt_input_grad": round(trn_simt_s * 1e6, 1),
+            "in_stage_loop_dp54_p4_5ps": loop,
             "note": "4 conv launches + input pack per forward (tcgen05.mma 128xNx16 BF16, FP32 accumulate in "
                     "TMEM; the mma.sync m16n8k16 kernels beside it); "
                     "algorithmic flops of the real channel counts; inputs (1.5 MB) stay in L2"}

@@ -25,6 +25,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
 
 #include "../../include/mmx_residual.h"
@@ -791,7 +792,8 @@ int rfail(mmx_rnet *net, int code, const std::string &msg)
         if (e__ != cudaSuccess) return rfail(net, MMX_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
     } while (0)
 
-bool smem_ready = false;
+std::once_flag smem_once;
+cudaError_t smem_status = cudaSuccess;
 
 template <int NB>
 cudaError_t set_tc_smem()
@@ -859,9 +861,8 @@ bool halo_maps(mmx_rnet *net, int nx, int ny, int nz)
     return ok;
 }
 
-cudaError_t raise_conv_smem()
+cudaError_t raise_conv_smem_once()
 {
-    if (smem_ready) return cudaSuccess;
     cudaError_t e;
     if ((e = set_tc_smem<1>()) != cudaSuccess) return e;
     if ((e = set_tc_smem<2>()) != cudaSuccess) return e;
@@ -874,8 +875,14 @@ cudaError_t raise_conv_smem()
     if ((e = cudaFuncSetAttribute(k_rnet_conv<32, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)conv_smem<32>())) != cudaSuccess)
         return e;
-    smem_ready = true;
     return cudaSuccess;
+}
+
+// the shared-memory limits of every layer kernel, raised once per process
+cudaError_t raise_conv_smem()
+{
+    std::call_once(smem_once, [] { smem_status = raise_conv_smem_once(); });
+    return smem_status;
 }
 
 // after a stream synchronisation: the fault word of the tensor-core layers
