@@ -324,3 +324,26 @@ def test_residual_in_the_stage_loop():
         ctx.close()
         zero.close()
         small.close()
+
+
+def test_net_refuses_invalid_calls_before_launching():
+    torch = torch_cuda()
+    import paper_2107_06729_gb300 as pkg
+    net = pkg.RNet(64, W.rnet_params(0), torch.cuda.current_stream())
+    try:
+        x = torch.zeros((6, 2, 8, 8), dtype=torch.float32, device="cuda")  # 128 cells > 64
+        with pytest.raises(pkg.MMXError) as ei:
+            net.forward(x)
+        assert ei.value.code == pkg.MMX_ERR_ARG and "out of range" in str(ei.value)
+        x = torch.zeros((6, 1, 8, 8), dtype=torch.float32, device="cuda")
+        t = torch.zeros((3, 1, 8, 8), dtype=torch.float32, device="cuda")
+        with pytest.raises(pkg.MMXError) as ei:
+            net.train_step(x, t, 0.0)
+        assert ei.value.code == pkg.MMX_ERR_ARG
+        net.forward(x)
+        with pytest.raises(pkg.MMXError) as ei:
+            pkg.mmx_rnet_get_activation(net.handle, 1, np.empty((64, 16), dtype=np.uint16))  # wrong size
+        assert ei.value.code == pkg.MMX_ERR_ARG
+        assert net.activation(1, 64).shape == (64, 32)
+    finally:
+        net.close()
