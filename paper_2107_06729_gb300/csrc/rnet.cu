@@ -822,20 +822,22 @@ void forward_tc(mmx_rnet *net, int nx, int ny, int nz);
 
 // 5-D view (8 channels, k-chunk, x, y, z) of channels-last BF16 activations
 // with cinp channels per cell; box (8, 1, 32, 6, 3), zero fill outside
+PFN_cuTensorMapEncodeTiled_v12000 lookup_encoder()
+{
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (PFN_cuTensorMapEncodeTiled_v12000)fn;
+}
+
 bool encode_halo_map(CUtensorMap *tm, const void *base, int cinp, int nx, int ny, int nz)
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
-    if (!enc) {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn) {
-            cudaGetLastError();
-            return false;
-        }
-        enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-    }
+    static const PFN_cuTensorMapEncodeTiled_v12000 enc = lookup_encoder();  // once, thread-safe
+    if (!enc) return false;
     const cuuint64_t dims[5] = {8, (cuuint64_t)(cinp / 8), (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
     const cuuint64_t row = (cuuint64_t)cinp * 2;
     const cuuint64_t strides[4] = {16, row, row * nx, row * nx * ny};
