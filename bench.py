@@ -433,6 +433,73 @@ def accuracy(pkg, torch, dev, cfg, horizon_ps):
     return res
 
 
+def equal_error(pkg, torch, dev, cfg, horizon_ps=2.0, tols=(3e-6, 1e-5, 3e-5, 1e-4, 3e-4)):
+    """Equal-error comparison on the first `horizon_ps` of the film: FP32 with
+    the extrapolation (p as configured) and with full demag at every stage,
+    each over a sweep of e_max; error = Eq. 7 against a GPU FP64 full-demag
+    run at e_max 1e-8; log(ns/s) interpolated linearly in log(error); the
+    speed ratio at the error the extrapolated run reaches at the configured
+    e_max.  Each timed run repeats a warm run from the same saved state."""
+    stream = torch.cuda.Stream(dev)
+    t_end = horizon_ps * 1e-12
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(stream):
+        ctx = pkg.Context(cfg["mesh"], cfg["material"], cfg["field"],
+                          dict(cfg["integrator"], extrap_order=-1, tol=1e-8), "fp64", stream)
+        m = torch.from_numpy(cfg["m0"]).to(dev, torch.float64)
+        ctx.set_m(m)
+        ctx.run(t_end)
+        ctx.get_m(m)
+        torch.cuda.synchronize(dev)
+        ref = m.cpu().numpy()
+        ctx.close()
+        rows = {}
+        for mode, p in (("extrapolated", cfg["integrator"]["extrap_order"]), ("full", -1)):
+            rows[mode] = []
+            for tol in tols:
+                c = pkg.Context(cfg["mesh"], cfg["material"], cfg["field"],
+                                dict(cfg["integrator"], extrap_order=p, tol=tol), "fp32", stream)
+                mf = torch.from_numpy(cfg["m0"]).to(dev, torch.float32)
+                c.set_m(mf)
+                blob = c.save_state()
+                c.run(t_end)  # warm: builds the attempt graphs
+                c.load_state(blob)
+                ev[0].record(stream)
+                c.run(t_end)
+                ev[1].record(stream)
+                torch.cuda.synchronize(dev)
+                secs = ev[0].elapsed_time(ev[1]) / 1e3
+                c.get_m(mf)
+                torch.cuda.synchronize(dev)
+                st = c.stats()
+                rows[mode].append({"tol": tol, "eps": eps_eq7(mf.double().cpu().numpy(), ref),
+                                   "ns_per_s": round(horizon_ps * 1e-3 / secs, 4), "accepted": st["accepted"]})
+                c.close()
+
+    def at(mode, eps):
+        pts = sorted(rows[mode], key=lambda r: r["eps"])
+        x = np.log([r["eps"] for r in pts])
+        y = np.log([r["ns_per_s"] for r in pts])
+        lx = np.log(eps)
+        inside = bool(x[0] <= lx <= x[-1])
+        if inside:
+            return float(np.exp(np.interp(lx, x, y))), True
+        i = (0, 1) if lx < x[0] else (-2, -1)  # linear extension from the nearest two points
+        k = (y[i[1]] - y[i[0]]) / (x[i[1]] - x[i[0]]) if x[i[1]] != x[i[0]] else 0.0
+        return float(np.exp(y[i[0]] + k * (lx - x[i[0]]))), False
+
+    tol0 = cfg["integrator"]["tol"]
+    target = [r for r in rows["extrapolated"] if r["tol"] == tol0]
+    eps_star = target[0]["eps"] if target else rows["extrapolated"][len(tols) // 2]["eps"]
+    v_ex, in_ex = at("extrapolated", eps_star)
+    v_full, in_full = at("full", eps_star)
+    return {"horizon_ps": horizon_ps, "metric": "Eq. 7 mean |m - m_ref| over cells",
+            "reference": "GPU FP64, full demag at every stage, e_max 1e-8", "sweep": rows,
+            "eps_star": eps_star, "ns_per_s_extrapolated_at_eps_star": round(v_ex, 4),
+            "ns_per_s_full_at_eps_star": round(v_full, 4), "speedup_at_equal_error": round(v_ex / v_full, 3),
+            "interpolated": in_ex and in_full}
+
+
 def run_mmx(args):
     import torch
     import paper_2107_06729_gb300 as pkg
@@ -606,6 +673,8 @@ def run_mmx(args):
         # one full chunk: after (every mode then differs from the reference
         # by O(1) in the cells that switched differently)
         line["accuracy"] = [accuracy(pkg, torch, dev, cfg, 2.0), accuracy(pkg, torch, dev, cfg, args.chunk_ps)]
+    if not args.no_equal_error:
+        line["equal_error"] = equal_error(pkg, torch, dev, cfg)
     if not args.no_large:
         line["demag_roofline_large3d"] = large3d_demag(pkg, torch, dev)
     if not args.no_ensemble:
@@ -679,6 +748,8 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-film batched ensemble run")
     ap.add_argument("--only-ensemble", action="store_true", help="only the 64-film batched ensemble run")
     ap.add_argument("--no-residual", action="store_true", help="skip the learned-residual net timing")
+    ap.add_argument("--no-equal-error", action="store_true", help="skip the e_max sweep at equal error")
+    ap.add_argument("--only-equal-error", action="store_true", help="only the e_max sweep at equal error")
     ap.add_argument("--only-residual", action="store_true", help="only the learned-residual net timing")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mmx":
@@ -691,6 +762,12 @@ def main():
         torch.cuda.set_device(0)
         print(json.dumps({"demag_roofline_large3d": large3d_demag(pkg, torch, torch.device("cuda", 0),
                                                                   iters=args.steps)}), flush=True)
+    elif args.only_equal_error:
+        import torch
+        import paper_2107_06729_gb300 as pkg
+        torch.cuda.set_device(0)
+        print(json.dumps({"equal_error": equal_error(pkg, torch, torch.device("cuda", 0), W.film_config2(seed=0))}),
+              flush=True)
     elif args.only_residual:
         import torch
         import paper_2107_06729_gb300 as pkg
