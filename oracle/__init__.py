@@ -194,9 +194,21 @@ def controller_factor(e, e_max, order, cmin=0.01, cmax=2.0):
 
 
 def epsilon(m, mref):
+    """Eq. 7 over cells (epsilon_space): m, mref arrays [3, ...]."""
     m = _f64(m)
     mref = _f64(mref)
     return lib().om_epsilon(m.size // 3, _p(m), _p(mref))
+
+
+def epsilon_time(mbar, mbar_ref):
+    """Eq. 7 with its N points taken as time samples of the mean
+    magnetisation (the reading for the paper's error-versus-time curves,
+    Sec. III): mbar, mbar_ref arrays [3, S] of <m> at the same S times."""
+    mbar = _f64(mbar).reshape(3, -1)
+    mbar_ref = _f64(mbar_ref).reshape(3, -1)
+    if mbar.shape != mbar_ref.shape:
+        raise ValueError("sample counts differ")
+    return lib().om_epsilon(mbar.shape[1], _p(mbar), _p(mbar_ref))
 
 
 class Simulation:

@@ -7,7 +7,8 @@ prints one JSON line per experiment:
 * ``method_sweep`` (Fig. 5(b) analog): every adaptive method of Sec. II at
   e_max = 1e-5, with demag extrapolation of order p and with the exact demag
   at every sub-step; simulated ns per second of both, the speedup factor and
-  the error (Eq. 7) of each against a reference run.
+  the error (Eq. 7) of each against a reference run; with --eps-time also
+  Eq. 7 over 1 ps samples of the mean magnetisation (extra untimed runs).
 * ``order_sweep`` (Fig. 2(a) analog): RKF56 with p = 0 .. 5 and full demag,
   the error against the reference.
 * ``fixed_step_sweep``: RK4 at h = 100 .. 500 fs with p = 3 and with full
@@ -94,16 +95,45 @@ def eps(m, ref):
     return float(np.linalg.norm(m - ref, axis=0).mean())
 
 
-def method_sweep(pkg, torch, cfg, ref, t_end):
+def eps_time(mbar, mbar_ref):
+    """Eq. 7 with time samples of the mean magnetisation <m> as its points
+    (the reading for the paper's error-versus-time curves): [3, S] arrays."""
+    return float(np.linalg.norm(np.asarray(mbar) - np.asarray(mbar_ref), axis=0).mean())
+
+
+def _mean_history(pkg, torch, cfg, integ, prec, t_end, dt=1e-12):
+    """<m> every dt up to t_end ([3, S]), from a run in dt chunks (untimed)."""
+    tdt = torch.float64 if prec == "fp64" else torch.float32
+    ctx = pkg.Context(cfg["mesh"], cfg["material"], cfg["field"], integ, prec)
+    try:
+        m = torch.from_numpy(cfg["m0"]).to("cuda", tdt)
+        ctx.set_m(m)
+        out = []
+        for k in range(1, int(round(t_end / dt)) + 1):
+            ctx.run(k * dt)
+            ctx.get_m(m)
+            out.append(m.double().mean(dim=(1, 2, 3)).cpu().numpy())
+        return np.stack(out, axis=1)
+    finally:
+        ctx.close()
+
+
+def method_sweep(pkg, torch, cfg, ref, t_end, ref_hist=None):
     rows = []
     for method, p in METHOD_P:
         mx, sx, tx = _run(pkg, torch, cfg, _adaptive(method, p), "fp32", t_end)
         mf, sf, tf = _run(pkg, torch, cfg, _adaptive(method, -1), "fp32", t_end)
-        rows.append({"method": method, "p": p, "ns_per_s_extrap": round(t_end * 1e9 / tx, 4),
-                     "ns_per_s_full": round(t_end * 1e9 / tf, 4), "speedup": round(tf / tx, 3),
-                     "eps_extrap": eps(mx, ref), "eps_full": eps(mf, ref),
-                     "steps_extrap": sx["accepted"], "steps_full": sf["accepted"],
-                     "rejected_extrap": sx["rejected"], "rejected_full": sf["rejected"]})
+        row = {"method": method, "p": p, "ns_per_s_extrap": round(t_end * 1e9 / tx, 4),
+               "ns_per_s_full": round(t_end * 1e9 / tf, 4), "speedup": round(tf / tx, 3),
+               "eps_extrap": eps(mx, ref), "eps_full": eps(mf, ref),
+               "steps_extrap": sx["accepted"], "steps_full": sf["accepted"],
+               "rejected_extrap": sx["rejected"], "rejected_full": sf["rejected"]}
+        if ref_hist is not None:
+            row["eps_time_extrap"] = eps_time(_mean_history(pkg, torch, cfg, _adaptive(method, p), "fp32", t_end),
+                                              ref_hist)
+            row["eps_time_full"] = eps_time(_mean_history(pkg, torch, cfg, _adaptive(method, -1), "fp32", t_end),
+                                            ref_hist)
+        rows.append(row)
     return {"experiment": "method_sweep", "tol": 1e-5, "rows": rows}
 
 
@@ -131,6 +161,8 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--t-end-ps", type=float, default=200.0)
     ap.add_argument("--only", choices=["method_sweep", "order_sweep", "fixed_step_sweep"])
+    ap.add_argument("--eps-time", action="store_true",
+                    help="also Eq. 7 over 1 ps samples of <m> in the method sweep (extra untimed chunked runs)")
     args = ap.parse_args(argv)
     import torch
     import paper_2107_06729_gb300 as pkg
@@ -141,11 +173,14 @@ def main(argv=None):
     print(json.dumps({"experiment": "reference", "workload": cfg["name"], "t_end_ps": args.t_end_ps,
                       "method": "RKDP54", "p": -1, "tol": 1e-9, "precision": "fp64", "steps": rst["accepted"],
                       "seconds": round(rsecs, 2)}), flush=True)
+    ref_hist = None
+    if args.eps_time and args.only in (None, "method_sweep"):
+        ref_hist = _mean_history(pkg, torch, cfg, _adaptive("RKDP54", -1, tol=1e-9), "fp64", t_end)
     for name, fn in (("method_sweep", method_sweep), ("order_sweep", order_sweep),
                      ("fixed_step_sweep", fixed_step_sweep)):
         if args.only and args.only != name:
             continue
-        out = fn(pkg, torch, cfg, ref, t_end)
+        out = fn(pkg, torch, cfg, ref, t_end, ref_hist) if name == "method_sweep" else fn(pkg, torch, cfg, ref, t_end)
         out["workload"] = cfg["name"]
         out["t_end_ps"] = args.t_end_ps
         print(json.dumps(out), flush=True)

@@ -374,6 +374,22 @@ def test_epsilon_metric():
     assert O.epsilon(a, b) == pytest.approx(2.0 / 6)
 
 
+def test_epsilon_over_time_samples():
+    """Eq. 7 with time samples of <m> as its points: zero for equal
+    histories; a constant offset d gives |d|; one differing sample out of S
+    gives |difference| / S; the sample counts must agree."""
+    rng = np.random.default_rng(3)
+    mbar = rng.uniform(-1, 1, size=(3, 40))
+    assert O.epsilon_time(mbar, mbar) == 0.0
+    d = np.array([3e-3, -4e-3, 0.0])
+    assert O.epsilon_time(mbar + d.reshape(3, 1), mbar) == pytest.approx(5e-3, rel=1e-12)
+    other = mbar.copy()
+    other[:, 7] += np.array([0.0, 0.0, 0.2])
+    assert O.epsilon_time(other, mbar) == pytest.approx(0.2 / 40, rel=1e-12)
+    with pytest.raises(ValueError):
+        O.epsilon_time(mbar, mbar[:, :39])
+
+
 # ------------------------------------------------------ ABM2 (reading R10) --
 ABM_N, ABM_D = (6, 4, 2), (4e-9, 4e-9, 4e-9)
 ABM_MAT = {"Ms": 8e5, "A": 1.3e-11, "K": 3e4, "ku": (0.0, 1.0, 0.0), "alpha": 0.05, "gamma": W.GAMMA}
