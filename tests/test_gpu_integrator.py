@@ -167,3 +167,18 @@ def test_programmatic_dependent_launch_option_matches_oracle(monkeypatch):
     ref, rs = oracle_run(mesh, MAT, FLD, integ, m0, 5e-12)
     assert gs["accepted"] == rs["accepted"] and gs["rejected"] == rs["rejected"]
     assert np.abs(got - ref).max() < 1e-10
+
+
+def test_large_box_recipe_on_a_subbox_matches_oracle():
+    """The 512 x 512 x 16 box's recipe (2 nm cells, Py, vortex with noise,
+    RK23 with p = 2) on a 64 x 64 x 4 sub-box, FP64, step for step against
+    the oracle for 1 ps: the oracle check of the large-box configuration."""
+    cfg = W.film_large3d(seed=0)
+    n, d = (64, 64, 4), cfg["mesh"]["d"]
+    mesh = {"n": n, "d": d}
+    m0 = W.m_vortex(n, d, seed=0)
+    got, gs = gpu_run(mesh, cfg["material"], cfg["field"], cfg["integrator"], m0, 1e-12, "fp64")
+    ref, rs = oracle_run(mesh, cfg["material"], cfg["field"], cfg["integrator"], m0, 1e-12)
+    assert gs["accepted"] == rs["accepted"] and gs["rejected"] == rs["rejected"]
+    assert gs["exact_evals"] == rs["exact_evals"] and gs["extrap_evals"] == rs["extrap_evals"]
+    assert np.abs(got - ref).max() < 1e-10
