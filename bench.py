@@ -433,6 +433,21 @@ def accuracy(pkg, torch, dev, cfg, horizon_ps):
     return res
 
 
+def speed_at_error(rows, eps):
+    """ns/s at error eps from sweep rows ({"eps", "ns_per_s"}): log ns/s
+    linear in log eps between the neighbouring points, extended linearly from
+    the nearest two outside the sweep; returns (ns/s, inside the sweep)."""
+    pts = sorted(rows, key=lambda r: r["eps"])
+    x = np.log([r["eps"] for r in pts])
+    y = np.log([r["ns_per_s"] for r in pts])
+    lx = np.log(eps)
+    if x[0] <= lx <= x[-1]:
+        return float(np.exp(np.interp(lx, x, y))), True
+    i = (0, 1) if lx < x[0] else (-2, -1)
+    k = (y[i[1]] - y[i[0]]) / (x[i[1]] - x[i[0]]) if x[i[1]] != x[i[0]] else 0.0
+    return float(np.exp(y[i[0]] + k * (lx - x[i[0]]))), False
+
+
 def equal_error(pkg, torch, dev, cfg, horizon_ps=2.0, tols=(3e-6, 1e-5, 3e-5, 1e-4, 3e-4)):
     """Equal-error comparison on the first `horizon_ps` of the film: FP32 with
     the extrapolation (p as configured) and with full demag at every stage,
@@ -477,16 +492,7 @@ def equal_error(pkg, torch, dev, cfg, horizon_ps=2.0, tols=(3e-6, 1e-5, 3e-5, 1e
                 c.close()
 
     def at(mode, eps):
-        pts = sorted(rows[mode], key=lambda r: r["eps"])
-        x = np.log([r["eps"] for r in pts])
-        y = np.log([r["ns_per_s"] for r in pts])
-        lx = np.log(eps)
-        inside = bool(x[0] <= lx <= x[-1])
-        if inside:
-            return float(np.exp(np.interp(lx, x, y))), True
-        i = (0, 1) if lx < x[0] else (-2, -1)  # linear extension from the nearest two points
-        k = (y[i[1]] - y[i[0]]) / (x[i[1]] - x[i[0]]) if x[i[1]] != x[i[0]] else 0.0
-        return float(np.exp(y[i[0]] + k * (lx - x[i[0]]))), False
+        return speed_at_error(rows[mode], eps)
 
     tol0 = cfg["integrator"]["tol"]
     target = [r for r in rows["extrapolated"] if r["tol"] == tol0]

@@ -1,0 +1,60 @@
+"""Host-side pieces of bench.py: the algorithmic byte model behind the
+roofline figures (pass by pass, against per-cell counts and the large box's
+total), the equal-error interpolation, and the whole-job aggregation."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def test_fused_pass_model_per_cell():
+    """Film 256x128x4 in FP32 (r = 4, complex c = 8 bytes): XF reads m (3r)
+    and writes the packed half spectrum (3c) = 36 B/cell; XI the reverse;
+    the fused YZ pass reads and writes the spectrum (6c = 48 B/cell) plus the
+    tensor octant (nx+1)(Py/2+1)(Pz/2+1) x 6 components once."""
+    n = (256, 128, 4)
+    cells = 256 * 128 * 4
+    m = bench.demag_pass_bytes(n, 4, split=False)
+    assert m["x_forward_fft"] == 36 * cells
+    assert m["x_inverse_fft"] == 36 * cells
+    assert m["yz_fft_tensor_multiply"] == 48 * cells + 257 * 129 * 5 * 6 * 4
+    # FP64 doubles every term
+    m8 = bench.demag_pass_bytes(n, 8, split=False)
+    assert all(m8[k] == 2 * m[k] for k in m)
+    assert bench.byte_model({"mesh": {"n": n}}, 4) == m
+
+
+def test_split_pass_model_of_the_large_box():
+    """512x512x16 FP32 with the split y-z passes: the y spectrum is Py/ny = 2
+    times the packed half spectrum; one evaluation moves 1.41 GB, the figure
+    the large-box roofline divides by the measured time."""
+    n = (512, 512, 16)
+    cells = 512 * 512 * 16
+    m = bench.demag_pass_bytes(n, 4, split=True)
+    assert m["x_forward_fft"] == 36 * cells
+    # YF: spectrum in (3c/cell), y spectrum out (2 x 3c/cell); ZM: y spectrum in
+    # and out + tensor; YI: y spectrum in, spectrum out
+    yspec = 2 * 24 * cells
+    tensor = 513 * 513 * 17 * 6 * 4
+    assert m["yz_fft_tensor_multiply"] == (24 * cells + yspec) + (2 * yspec + tensor) + (yspec + 24 * cells)
+    assert sum(m.values()) == pytest.approx(1.41e9, rel=0.01)
+
+
+def test_speed_at_error_interpolates_in_log_log():
+    rows = [{"eps": 1e-5, "ns_per_s": 1.0}, {"eps": 1e-3, "ns_per_s": 4.0}, {"eps": 1e-4, "ns_per_s": 2.0}]
+    assert bench.speed_at_error(rows, 1e-4) == (pytest.approx(2.0), True)        # a sweep point
+    v, inside = bench.speed_at_error(rows, np.sqrt(1e-5 * 1e-4))                   # geometric midpoint
+    assert inside and v == pytest.approx(np.sqrt(2.0))
+    v, inside = bench.speed_at_error(rows, 1e-2)                                   # beyond: same slope
+    assert not inside and v == pytest.approx(8.0)
+    v, inside = bench.speed_at_error(rows, 1e-6)
+    assert not inside and v == pytest.approx(0.5)
+
+
+def test_aggregate_is_all_units_over_the_slowest_rank():
+    value, t_max = bench.aggregate(0.2, 1.5, 4, lambda x: 2.0 * x, lambda x: 4.0 * x)
+    assert t_max == 3.0 and value == pytest.approx(0.8 / 3.0)
