@@ -38,3 +38,19 @@ def test_slab_stand_in():
     assert m[1, :, :, :8].mean() > 0.3 and m[1, :, :, -8:].mean() < -0.3
     assert m[0].mean() > 0.9
     assert c["field"]["H0"] == (-20e3, 1e3, 0.0)
+
+
+def test_rnet_params_are_seeded_and_within_the_he_bounds():
+    a, b, c = W.rnet_params(3), W.rnet_params(3), W.rnet_params(4)
+    assert a.dtype == np.float32 and a.size == 63171
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    off = 0
+    for li, (ci, co) in enumerate(W.RNET_LAYERS):
+        lim = np.sqrt(6.0 / (27 * ci)) * (0.1 if li == len(W.RNET_LAYERS) - 1 else 1.0)
+        w = a[off:off + 27 * co * ci]
+        off += 27 * co * ci
+        bias = a[off:off + co]
+        off += co
+        assert np.abs(w).max() <= lim and np.abs(w).max() > 0.9 * lim
+        assert np.abs(bias).max() <= 0.01
+    assert off == a.size
