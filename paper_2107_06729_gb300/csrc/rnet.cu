@@ -340,6 +340,9 @@ __global__ void __launch_bounds__(128) k_rnet_conv_tc(const __grid_constant__ CU
         tile_xyz(tile, x0, y0, z);
         const int b = NBUF == 2 ? (it & 1) : 0;
         const int next = tile + (int)gridDim.x;
+        // this tile's MMAs overwrite the accumulators the previous tile's TMEM
+        // loads read before the barrier that ended that iteration
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         if (warp == 0) {
             if (lane == 0) {
                 if (it == 0) {
@@ -772,6 +775,7 @@ struct mmx_rnet {
     int tm_nx = 0, tm_ny = 0, tm_nz = 0;
     bool tm_ok = false;
     bool require_tc = false;  // MMX_RNET_REQUIRE_TC=1: no fallback when the halo copies cannot be encoded
+    int grid_cap = 0;         // MMX_RNET_GRID_CAP=n: at most n persistent CTAs (0: two per SM)
     bool mma_sync = false; // MMX_RNET_MMA_SYNC=1: the mma.sync layers instead of tcgen05
     int step = 0;
     int nx = 0, ny = 0, nz = 0;
@@ -932,7 +936,8 @@ template <int NB>
 void forward_tc(mmx_rnet *net, int nx, int ny, int nz)
 {
     const long long tiles = (long long)((nx + TC_TX - 1) / TC_TX) * ((ny + RN_TY - 1) / RN_TY) * nz;
-    const long long cap = (long long)net->nsm * (NB == 1 ? 2 : 1);
+    long long cap = (long long)net->nsm * (NB == 1 ? 2 : 1);
+    if (net->grid_cap > 0 && net->grid_cap < cap) cap = net->grid_cap;
     const dim3 g((unsigned)(tiles < cap ? tiles : cap));
     k_rnet_conv_tc<16, 32, 0, NB><<<g, 128, tc_smem(16, 32, NB), net->s>>>(
         net->tm[0], net->Wtc, net->P + p_off(0) + 27 * 32 * 6, 32, net->a[1], nx, ny, nz, net->fault, nullptr, nullptr);
@@ -1033,6 +1038,8 @@ extern "C" int mmx_rnet_create(long long max_cells, void *cuda_stream, mmx_rnet 
     net->mma_sync = ms && atoi(ms) != 0;
     const char *sb = getenv("MMX_RNET_SIMT_BWD");
     net->simt_bwd = sb && atoi(sb) != 0;
+    const char *gcap = getenv("MMX_RNET_GRID_CAP");
+    net->grid_cap = gcap ? atoi(gcap) : 0;
     const char *rq = getenv("MMX_RNET_REQUIRE_TC");
     net->require_tc = rq && atoi(rq) != 0;
     const char *nb = getenv("MMX_RNET_NBUF");
@@ -1103,7 +1110,9 @@ extern "C" int mmx_rnet_train_step(mmx_rnet *net, int nx, int ny, int nz, const 
     // input gradients on the tensor cores (dz rounded to BF16 where it enters), or FP32 SIMT
     const bool tc_bwd = !net->simt_bwd && halo_maps(net, nx, ny, nz);
     const long long tiles = (long long)((nx + TC_TX - 1) / TC_TX) * ((ny + RN_TY - 1) / RN_TY) * nz;
-    const dim3 gt((unsigned)(tiles < 2LL * net->nsm ? tiles : 2LL * net->nsm));
+    long long gcap_bwd = 2LL * net->nsm;
+    if (net->grid_cap > 0 && net->grid_cap < gcap_bwd) gcap_bwd = net->grid_cap;
+    const dim3 gt((unsigned)(tiles < gcap_bwd ? tiles : gcap_bwd));
     const int chunk = 1024;
     const dim3 wg((unsigned)((n + chunk - 1) / chunk), 27);
     const unsigned dg = (unsigned)((n + 7) / 8);

@@ -347,3 +347,54 @@ def test_net_refuses_invalid_calls_before_launching():
         assert net.activation(1, 64).shape == (64, 32)
     finally:
         net.close()
+
+
+# The tensor-core kernels are persistent: a CTA takes tile after tile, with
+# the halo barrier's and the MMA barrier's parity alternating and the next
+# tile's copies issued while the current one finishes.  The cases above fit
+# one tile per CTA; these cap the grid (MMX_RNET_GRID_CAP) so that every CTA
+# runs many tiles, and check the size the bench times.
+def test_multi_tile_ctas_forward_and_gradient(monkeypatch):
+    monkeypatch.setenv("MMX_RNET_REQUIRE_TC", "1")
+    monkeypatch.setenv("MMX_RNET_GRID_CAP", "3")
+    test_forward_layer_by_layer_matches_oracle((64, 32, 4), "tcgen05", monkeypatch)
+    test_train_step_gradient_and_adam_update_match_oracle((33, 5, 3), "tcgen05", monkeypatch)
+    monkeypatch.setenv("MMX_RNET_GRID_CAP", "1")
+    test_train_step_gradient_and_adam_update_match_oracle((24, 8, 2), "tcgen05", monkeypatch)
+
+
+def test_forward_at_the_timed_size_layer_by_layer(monkeypatch):
+    """The 128 x 128 x 4 film the bench times, in its launch configuration
+    (tcgen05 layers, persistent grid): every layer within one BF16 unit of
+    the exact convolution of the GPU's own layer input, the output within
+    FP32 accumulation error."""
+    monkeypatch.setenv("MMX_RNET_REQUIRE_TC", "1")
+    torch = torch_cuda()
+    n = (128, 128, 4)
+    nx, ny, nz = n
+    cells = nx * ny * nz
+    params = W.rnet_params(seed=0)
+    x = _input(n, seed=0)
+    net = _net(torch, cells, params)
+    try:
+        r = net.forward(torch.from_numpy(x).cuda())
+        torch.cuda.synchronize()
+        acts = [net.activation(l, cells) for l in range(4)]
+        r_gpu = r.cpu().numpy().astype(np.float64)
+    finally:
+        net.close()
+    assert np.array_equal(_to_cf(acts[0], n, 6), R.bf16_round(x))
+    layers = R.unpack(params.astype(np.float64))
+    for l in range(4):
+        ci, co, relu = R.LAYERS[l]
+        A = _to_cf(acts[l], n, ci)
+        Wq = R.bf16_round(layers[l][0])
+        b = layers[l][1].astype(np.float32).astype(np.float64)
+        exact = R.conv3d(A, Wq, b)
+        mag = R.conv3d(np.abs(A), np.abs(Wq), np.abs(b))
+        if relu:
+            want = np.maximum(exact, 0.0)
+            got = _to_cf(acts[l + 1], n, co)
+            assert np.all(np.abs(got - want) <= _ulp_bf16(want) + 1e-5 * mag + 1e-30), l
+        else:
+            assert np.all(np.abs(r_gpu - exact) <= 1e-5 * mag + 1e-30)
