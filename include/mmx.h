@@ -208,8 +208,11 @@ int mmx_get_plan(const mmx_ctx *ctx, mmx_plan *out);
  *     the array's device address (cudaGetSymbolAddress), and the first call
  *     for a new mesh, Ms or precision computes the Newell tensor on the host
  *     (host memory only) and copies its spectrum into the array; make that
- *     first call before any stream capture.  Later calls with the same
- *     description reuse the spectrum the array still holds.
+ *     first call before any stream capture (such a first call made while
+ *     cuda_stream is capturing returns MMX_ERR_ARG and enqueues nothing).
+ *     Later calls with the same description (mesh sizes, cell sizes, Ms and
+ *     precision compared field by field) reuse the spectrum the array still
+ *     holds.
  *   - Every call shares the array: calls that overlap on the GPU (other
  *     streams, other host threads) race; serialise them.
  *   - Meshes whose spectrum, tables and scratch exceed the array, or whose

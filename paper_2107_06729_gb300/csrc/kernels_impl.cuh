@@ -1936,7 +1936,10 @@ template <typename T> __device__ void controller(const StageArgs<T> &a, DevState
     if (a.ctl.prime) st->prime_attempts++;
     const double h = st->h;
     int more = 0;
-    if (!(e <= 1.7976931348623157e308)) {  // NaN or Inf
+    if (st->fault) {  // a bounded wait of this attempt's kernels gave up: stop the run
+        st->status = MMX_ERR_CUDA;
+        st->done = 1;
+    } else if (!(e <= 1.7976931348623157e308)) {  // NaN or Inf
         st->status = MMX_ERR_NONFINITE;
         st->done = 1;
     } else {

@@ -179,7 +179,7 @@ int read_state(mmx_ctx *c)
 {
     CK(cudaStreamSynchronize(c->stream));
     CK(cudaMemcpy(c->h_st, c->st, sizeof(DevState), cudaMemcpyDeviceToHost));
-    if (c->h_st->fault) return fail(c, MMX_ERR_CUDA, "a bounded device wait gave up (TMA copy not completed)");
+    if (c->h_st->fault) return fail(c, MMX_ERR_CUDA, "a bounded device wait gave up (a tensor copy or tensor-core operation did not complete)");
     return 0;
 }
 
@@ -1101,7 +1101,7 @@ int mmx_batch_run(mmx_batch *b, const double *t_end, int *status)
         if (b->active[i]) {
             c->launches += pa * kernels_per_attempt(c, 1) + (s.run_attempts - pa) * kernels_per_attempt(c, c->ctl.p < 0);
             if (s.fault)
-                r = fail(c, MMX_ERR_CUDA, "a bounded device wait gave up (TMA copy not completed)");
+                r = fail(c, MMX_ERR_CUDA, "a bounded device wait gave up (a tensor copy or tensor-core operation did not complete)");
             else
                 r = s.done ? end_status(c, b->forced0[i])
                            : fail(c, MMX_ERR_STATE, "batched loops stopped before the run finished");

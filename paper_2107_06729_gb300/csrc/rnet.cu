@@ -320,6 +320,7 @@ __global__ void __launch_bounds__(128) k_rnet_conv_tc(const __grid_constant__ CU
     bool wok = true;
     int uses[2] = {0, 0};  // completed uses of each halo buffer's barrier (its parity)
     bool pending = false;  // a halo copy issued and not yet waited for
+    bool inok = true;      // thread 0: the weights and this tile's halo arrived
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mw), "r"(WBYTES) : "memory");
         asm volatile(
@@ -359,6 +360,7 @@ __global__ void __launch_bounds__(128) k_rnet_conv_tc(const __grid_constant__ CU
                 }
                 uses[b]++;
                 pending = !hok;
+                inok = wok && hok;
                 if (wok && hok) {
                     constexpr uint32_t idesc = umma_idesc_bf16<N_>();
                     const uint32_t hb = hal_s + (uint32_t)(b * KC * TC_NE) * 16u;
@@ -405,10 +407,12 @@ __global__ void __launch_bounds__(128) k_rnet_conv_tc(const __grid_constant__ CU
             tc_load_halo<KC>(&tmap, hal_s, smem_u32(mbar + 2), nx0, ny0, nz0);
             pending = true;
         }
-        // one decision for the whole CTA (the TMEM loads below are warp-collective)
-        ok = __syncthreads_and(ok) != 0;
+        // one decision for the whole CTA (the TMEM loads below are warp-collective);
+        // a weight or halo copy that never arrived also ends the loop, so that a
+        // fault costs a bounded number of waits whatever the number of tiles
+        ok = __syncthreads_and(ok && inok) != 0;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        if (!ok) break;  // the barrier phase is lost: stop, free TMEM below
+        if (!ok) break;  // a barrier phase or a copy is lost: stop, free TMEM below
         {
             // warp w reads TMEM lanes 32w..32w+31 = tile rows oy = w, ox = lane; the
             // accumulators are summed in FP32
@@ -1232,7 +1236,11 @@ int mmxk_rnet_stage(mmx_rnet *net, mmx_ctx *c, cudaStream_t s, int k)
 {
     const long long n = c->n;
     cudaStream_t keep = net->s;
+    int *keep_fault = net->fault;
     net->s = s;  // the context's stream, possibly being captured
+    // the layers report an expired bounded wait through the context's fault
+    // word, which the controller and every state read of the context check
+    net->fault = &c->st->fault;
     k_res_stage_in<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->st, k, c->ctl.p + 1, (const float *)c->hist,
                                                              (const float *)c->Y[k & 1], n, (float)(1.0 / c->mat.Ms),
                                                              (float *)c->G, net->a[0]);
@@ -1240,6 +1248,7 @@ int mmxk_rnet_stage(mmx_rnet *net, mmx_ctx *c, cudaStream_t s, int k)
     k_res_stage_out<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(c->st, net->r, 3 * n, (float)c->mat.Ms,
                                                                   (float *)c->G);
     net->s = keep;
+    net->fault = keep_fault;
     net->nx = c->nx;
     net->ny = c->ny;
     net->nz = c->nz;

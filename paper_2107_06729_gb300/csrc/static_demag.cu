@@ -8,7 +8,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -121,9 +120,21 @@ extern "C" int mmx_demag_static(const mmx_mesh *mesh, double Ms, int precision, 
     c.twy = slot.base + kbytes + txb;
     c.twz = slot.base + kbytes + txb + tyb;
     c.S = slot.base + kbytes + txb + tyb + tzb;
-    const bool same = slot.cached && slot.prec == precision && slot.Ms == Ms &&
-                      memcmp(&slot.key, mesh, sizeof(mmx_mesh)) == 0;
+    // field by field: the struct has padding after nz that callers need not clear
+    const bool same = slot.cached && slot.prec == precision && slot.Ms == Ms && slot.key.nx == mesh->nx &&
+                      slot.key.ny == mesh->ny && slot.key.nz == mesh->nz && slot.key.dx == mesh->dx &&
+                      slot.key.dy == mesh->dy && slot.key.dz == mesh->dz;
     if (!same) {
+        // a new description needs a stream synchronisation and a blocking copy,
+        // neither of which is allowed while the stream is being captured
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (c.stream && cudaStreamIsCapturing(c.stream, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MMX_ERR_CUDA, "cudaStreamIsCapturing failed");
+        }
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(MMX_ERR_ARG, "mmx_demag_static: first call for this mesh, Ms and precision made during "
+                                     "stream capture; make it before the capture");
         // tensor spectrum for this mesh (host set-up, then a copy into the array)
         slot.cached = false;
         mmx_host_tensor_args ta{c.nx, c.ny, c.nz, mesh->dx, mesh->dy, mesh->dz, Ms};

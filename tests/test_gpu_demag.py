@@ -248,3 +248,32 @@ def test_bounded_tma_wait_runs_out_and_is_reported(monkeypatch):
     m = W.m_random(n, seed=9)
     ref = O.demag_fft(O.newell_octant(*n, *d), MAT["Ms"], m)
     assert rel_max(gpu_demag({"n": n, "d": d}, MAT, m, "fp32"), ref) < 1e-5
+
+
+def test_bounded_wait_fault_stops_an_integration(monkeypatch):
+    """The controller ends a run as soon as any kernel of the attempt has set
+    the context's fault word (the demag passes' and the learned residual's
+    tensor copies and tensor-core waits all report there): with the stall
+    switch of the TMA x-inverse pass, mmx_run returns MMX_ERR_CUDA after its
+    first attempt instead of integrating on with stale fields."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2107_06729_gb300 as pkg
+    from gpu_util import gpu_context
+    n, d = (64, 32, 2), (4e-9, 4e-9, 4e-9)
+    monkeypatch.setenv("MMX_AUTOTUNE", "0")
+    monkeypatch.setenv("MMX_TEST_STALL_TMA", "1")
+    integ = {"method": "RKDP54", "extrap_order": 4, "adaptive": True, "h": 1e-13, "tol": 1e-5}
+    mat = dict(MAT, A=1.3e-11, alpha=0.02)
+    ctx = gpu_context({"n": n, "d": d}, mat, {}, integ, "fp32")
+    try:
+        assert ctx.plan()["xi_tma"] == 1
+        ctx.set_m(torch.from_numpy(W.m_random(n, seed=4)).to("cuda", torch.float32))
+        with pytest.raises(pkg.MMXError) as ei:
+            ctx.run(1e-12)
+        assert ei.value.code == pkg.MMX_ERR_CUDA and "bounded device wait" in str(ei.value)
+        x = torch.ones(4, device="cuda")
+        assert float((2 * x).sum()) == 8.0
+    finally:
+        ctx.close()

@@ -1,7 +1,7 @@
 """1 ns trajectories of the 64 x 32 x 1 film (4 nm cells, RK4 at h = 0.1 ps,
 10,000 steps) on the GPU against the CPU oracle: within 1e-4 in m after
 1 ns, with full demag at every sub-step (FP64 and FP32 fields) and with the
-order-3 extrapolation companion run (FP64)."""
+order-3 extrapolation companion run (FP64 and FP32 fields)."""
 import functools
 
 import numpy as np
@@ -28,12 +28,12 @@ def _oracle(p):
     return m, st
 
 
-@pytest.mark.parametrize("prec,p", [("fp64", -1), ("fp64", 3), ("fp32", -1)])
+@pytest.mark.parametrize("prec,p", [("fp64", -1), ("fp64", 3), ("fp32", -1), ("fp32", 3)])
 def test_film_1ns_trajectory_within_1e4(prec, p):
     cfg = W.film_config1(seed=0)
     integ = dict(cfg["integrator"], extrap_order=p)
     got, gs = gpu_run(cfg["mesh"], cfg["material"], cfg["field"], integ, cfg["m0"], T_END, prec)
-    ref, rs = _oracle(p if prec == "fp64" else -1)
+    ref, rs = _oracle(p)
     assert gs["accepted"] == rs["accepted"] == 10000
     assert np.abs(got - ref).max() < 1e-4
     if prec == "fp64":
