@@ -156,12 +156,17 @@ int mmx_save_state(mmx_ctx *ctx, void *buf, size_t *len);
 int mmx_load_state(mmx_ctx *ctx, const void *buf, size_t len);
 
 /* Per-kernel-class device timing with CUDA events on the context stream.
- * While enabled, mmx_run launches its kernels one by one (no CUDA graph)
- * with an event pair around each; mmx_get_profile returns, per class
- * (0: x-forward FFT, 1: yz FFT + tensor multiply, 2: x-inverse FFT,
- * 3: LLG stage, 4: last stage + controller), the summed milliseconds and the
- * number of launches.  ms and launches point to arrays of MMX_NPROF. */
-#define MMX_NPROF 5
+ * While enabled, mmx_run runs each attempted step as a CUDA graph with an
+ * event-record node before and after every kernel (the host reads the loop
+ * flag between attempts, so runs are slower than without profiling, but
+ * the kernels themselves run back to back as in the step loop), and
+ * mmx_demag records and synchronises an event pair around each pass.
+ * mmx_get_profile returns, per class (0: x-forward FFT, 1: yz FFT + tensor
+ * multiply, 2: x-inverse FFT, 3: LLG stage, 4: last stage (Eq. 3 solution
+ * and error norm), 5: controller (Eq. 5 and the next attempt's
+ * coefficients)), the summed milliseconds and the number of launches.  ms
+ * and launches point to arrays of MMX_NPROF. */
+#define MMX_NPROF 6
 int mmx_set_profiling(mmx_ctx *ctx, int enable);
 int mmx_get_profile(mmx_ctx *ctx, double *ms, long long *launches);
 

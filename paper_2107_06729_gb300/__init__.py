@@ -28,9 +28,9 @@ MMX_ERR_TIMEOUT = -5
 MMX_ERR_STATE = -6
 MMX_FP64 = 0
 MMX_FP32_MIXED = 1
-MMX_NPROF = 5
+MMX_NPROF = 6
 METHODS = {"RK4": 0, "HEUN12": 1, "RK23": 2, "RKF45": 3, "RKCK45": 4, "RKDP54": 5, "RKF56": 6, "ABM2": 7}
-PROFILE_CLASSES = ["x_forward_fft", "yz_fft_tensor_multiply", "x_inverse_fft", "llg_stage", "llg_last_stage"]
+PROFILE_CLASSES = ["x_forward_fft", "yz_fft_tensor_multiply", "x_inverse_fft", "llg_stage", "llg_last_stage", "controller"]
 
 
 class mmx_mesh(ctypes.Structure):

@@ -3,8 +3,10 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "../../include/mmx.h"
 
@@ -12,15 +14,20 @@
 #define MMX_MAXP 6
 #define MMX_NHIST (MMX_MAXP + 1)
 
-// Coefficients of one stage for the current attempt, prepared by one warp
+// Coefficients of one stage for the current attempt, prepared by one CTA
 // (at the end of the previous attempt, or before the first one) so that the
-// stage kernels do no FP64 arithmetic.
+// stage kernels do no FP64 arithmetic.  `state` republishes the words of the
+// attempt's state that the stage kernels need, beside their coefficients, so
+// that one uniform load brings both.
 struct StageCoef {
-    double cb[MMX_MAXS];   // h b_{k+1,l}; at the last stage h c_l
-    double ce[MMX_MAXS];   // at the last stage h (c_l - c_hat_l)
-    double w[MMX_NHIST];   // Eq. 6 Lagrange weights at t0 + a_k h
-    double H[3];           // applied field at t0 + a_k h
-    float cbf[MMX_MAXS], cef[MMX_MAXS], wf[MMX_NHIST], Hf[3];
+    double cb[MMX_MAXS];       // h b_{k+1,l}; at the last stage h c_l
+    double ce[MMX_MAXS];       // at the last stage h (c_l - c_hat_l)
+    double w[MMX_NHIST + 1];   // Eq. 6 Lagrange weights at t0 + a_k h (one pad word)
+    double H[4];               // applied field at t0 + a_k h (one pad word)
+    float cbf[MMX_MAXS], cef[MMX_MAXS];
+    float cel[MMX_MAXS];       // ce - cef: low part of the FP32 split of ce (compensated error sum)
+    float wf[MMX_NHIST + 1], Hf[4];
+    int state[8];              // done, cur, fbase, head, f1_valid (copies; see publish_state)
 };
 
 // Integrator state kept in device memory; kernels read it at launch and the
@@ -34,8 +41,6 @@ struct DevState {
     double last_err;
     double h_prev;   // ABM2: last accepted step (0 after a (re)start)
     double hist_t[MMX_NHIST];   // times of the stored exact fields (Eq. 6)
-    unsigned long long err_bits;  // running max of the error norm (bit pattern)
-    unsigned int blocks_done;
     int cur;         // which magnetisation buffer holds m0
     int fbase;       // slot of F_1 in the stage-derivative ring (FSAL rotation)
     int f1_valid;    // F_1 for this t0 already computed
@@ -52,10 +57,12 @@ struct DevState {
     long long run_attempts;
     long long prime_attempts;  // attempts made by priming loops (launch accounting)
     unsigned long long t_start_ns, time_limit_ns;
-    StageCoef coef[MMX_MAXS];
+    StageCoef coef[MMX_MAXS];  // everything before coef is the "head" the controller copies
 };
 
 static_assert(sizeof(DevState) % 8 == 0, "DevState is copied as 8-byte words");
+static_assert(offsetof(DevState, coef) % 16 == 0 && sizeof(StageCoef) % 16 == 0,
+              "stage coefficients are read with 16-byte loads");
 
 struct TabArgs {
     int s, order, adaptive, fsal;
@@ -106,6 +113,8 @@ struct mmx_ctx {
     CtlArgs ctl;
     // device buffers (element type per precision)
     void *m[2], *Y[2], *F, *G, *hist, *S, *K, *twx, *twy, *twz;
+    void *mlo;   // FP32: low words of the compensated state of m[0] and m[1] ([2][3][n]); null in FP64
+    void *errpart;  // largest error norm of each CTA of the last stage
     void *Tb;    // split y/z path: y spectrum [kx][c nz + z][Py] (complex)
     bool split;  // the y-z column does not fit one CTA: YF, ZM, YI instead of YZ
     bool cluster;     // ... and a thread-block cluster per kx column runs it instead (YZC)
@@ -128,15 +137,31 @@ struct mmx_ctx {
     bool graph_ok[2];
     struct mmx_rnet *rnet = nullptr;  // learned residual at the extrapolated stages (mmx_set_residual)
     bool use_graphs;
-    // profiling
+    // profiling: an event pair around every timed launch.  Outside a graph
+    // the pair is synchronised at once; runs capture each attempt once more
+    // as a graph with event-record nodes around every kernel (pgexec, per
+    // loop kind) and read the pairs after each launch, so that the times are
+    // those of kernels running back to back on the device.
     bool profiling;
     double prof_ms[MMX_NPROF];
     long long prof_n[MMX_NPROF];
     cudaEvent_t ev_a, ev_b;
+    int prof_cap = -1;                 // loop kind whose profiled graph is being captured, else -1
+    std::vector<cudaEvent_t> pev[2];   // event pairs of the profiled graphs
+    std::vector<int> pcls[2];          // profile class of each pair
+    cudaGraphExec_t pgexec[2];
+    cudaGraph_t pgraph[2];
+    bool pgraph_ok[2] = {false, false};
     long long launches;
     long long launches_dev_at_sync;
     std::string err;
 };
+
+// mmx_api.cu: profiling event pairs (see mmx_ctx::prof_cap) and dropping
+// the captured graphs (after the stage sequence changed, and at destroy)
+void mmx_prof_begin(mmx_ctx *c, cudaStream_t s);
+void mmx_prof_end(mmx_ctx *c, cudaStream_t s, int cls);
+void mmx_drop_graphs(mmx_ctx *c);
 
 // kernels.cu
 int mmxk_setup_buffers(mmx_ctx *c, const double *Kspec_host);
@@ -148,6 +173,10 @@ void mmxk_demag(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int 
                 const void *src, int dst_mode, void *dst, const void *self_src);
 void mmxk_stage(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime_graph,
                 cudaGraphConditionalHandle cond, int use_cond);
+// stage_f32.cu / stage_f64.cu: the stage kernel instance for nf stage
+// derivatives and nh demag sources read, and the controller kernel
+const void *mmxk_stage_kernel(bool f64, int nf, int nh, bool last, bool stage0);
+const void *mmxk_control_kernel(bool f64);
 // rows per CTA of the plain x passes: the default, and setting a candidate
 // (raises the kernels' shared-memory limit; MMX_ERR_ARG if it does not fit)
 int mmxk_default_trows(const mmx_ctx *c);

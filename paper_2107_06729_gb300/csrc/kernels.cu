@@ -7,6 +7,18 @@ const void *mmxk_tab_fused(int kind, bool f64, int L);  // fft_fused_f32.cu / ff
 const void *mmxk_tab_split(int kind, bool f64, int L);  // fft_split.cu
 const void *mmxk_tab_pipe(int kind, bool f64, int L);   // fft_pipe.cu
 
+const void *mmxk_stage_tab_f32(int nf, int nh, bool last, bool stage0);  // stage_f32.cu
+const void *mmxk_stage_tab_f64(int nf, int nh, bool last, bool stage0);  // stage_f64.cu
+const void *mmxk_control_f32();
+const void *mmxk_control_f64();
+
+const void *mmxk_stage_kernel(bool f64, int nf, int nh, bool last, bool stage0)
+{
+    return f64 ? mmxk_stage_tab_f64(nf, nh, last, stage0) : mmxk_stage_tab_f32(nf, nh, last, stage0);
+}
+
+const void *mmxk_control_kernel(bool f64) { return f64 ? mmxk_control_f64() : mmxk_control_f32(); }
+
 const void *mmxk_kernel(int kind, bool f64, int L)
 {
     switch (kind) {

@@ -1797,20 +1797,43 @@ __global__ void __launch_bounds__(192, 2) k_yzc(const SplitArgs<T> a)
 template <typename T> struct PhysT {
     T wx, wy, wz, can, gp, alpha;
     T ku[3], msN00[3];
-    int nx, ny, nz, lgnx, lgny;
+    int n, nx, ny, nz, lgnx, lgny;
 };
 
 template <typename T> struct StageArgs {
-    T *m0, *m1, *Y0, *Y1, *F, *G, *hist;
+    const T *Yin;   // input Y_k of stage k >= 1 (stage 0 reads m0 = m[cur])
+    T *Yout;        // Y_{k+1} of a stage that is not the last
+    T *m0, *m1;     // the two magnetisation buffers; the attempt's m0 is m[cur]
+    T *mlo;         // FP32: low words of the compensated state, [2][3][n] (buffer b at b * 3n); null in FP64
+    T *F, *G, *hist;
+    T *errpart;     // last stage: the largest error norm of each CTA
     DevState *st;
+    PhysT<T> pt;
+    int k;          // stage index (0-based)
+    int ext;        // Eq. 6 from the history fields (else the exact field G)
+    int gdyn;       // stage 0 with a history: the exact field is history slot head
+    int fstatic;    // the stage-derivative ring never rotates (fbase = 0): slot addresses are static
+    int ns;         // stage-derivative slots
+    int fl[MMX_MAXS];  // indices l of the stage derivatives this stage reads (the template's NF of them)
+};
+
+// Arguments of the controller kernel that ends every attempt.
+template <typename T> struct CtlKArgs {
+    DevState *st;
+    const T *errpart;
+    int nparts;
     TabArgs tab;
     PhysArgs ph;
-    PhysT<T> pt;
     CtlArgs ctl;
-    int k, extrap, last, use_cond;
+    int use_cond;
     cudaGraphConditionalHandle cond;
 };
 
+// Stage kernel layout: one thread per cell (all three components), 128-thread
+// CTAs, eight per SM.  Every load whose address does not depend on the
+// attempt's state is issued first, with compile-time counts of the stage
+// derivatives (NF) and demag sources (NH) so that the loads are branch-free;
+// the stage's coefficients reach shared memory meanwhile.
 constexpr int ST_THREADS = 128;
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -1845,12 +1868,13 @@ __device__ __forceinline__ double root64(double x, int n1)
 }
 
 // The threads of one CTA fill the per-stage coefficients of the attempt that
-// starts at (st->t, st->h): Eq. 4 row weights times h, Eq. 3 weights times h,
-// Eq. 6 Lagrange weights (once the history is primed) and the applied field.
-// Lagrange weights: w_kj = prod_{q!=j} (a_k - s_q) / prod_{q!=j} (s_j - s_q)
-// with s_q = (t_q - t0)/h, the FP64 differences taken first.
-__device__ void prepare_coefs(DevState *st, const TabArgs &tab, const PhysArgs &ph, int p, double *sm_sig,
-                              double *sm_iden)
+// starts at (st->t, st->h) into coef[]: Eq. 4 row weights times h, Eq. 3
+// weights times h, Eq. 6 Lagrange weights (once the history is primed) and
+// the applied field.  Lagrange weights: w_kj = prod_{q!=j} (a_k - s_q) /
+// prod_{q!=j} (s_j - s_q) with s_q = (t_q - t0)/h, the FP64 differences
+// taken first.  st may be a shared-memory copy of the state's head.
+__device__ void prepare_coefs(const DevState *st, StageCoef *coef, const TabArgs &tab, const PhysArgs &ph, int p,
+                              double *sm_sig, double *sm_iden)
 {
     const int tid = threadIdx.x;
     const double h = st->h, t0 = st->t;
@@ -1868,7 +1892,7 @@ __device__ void prepare_coefs(DevState *st, const TabArgs &tab, const PhysArgs &
     __syncthreads();
     for (int it = tid; it < MMX_MAXS * MMX_MAXS; it += blockDim.x) {
         const int k = it / MMX_MAXS, l = it % MMX_MAXS;
-        StageCoef &C = st->coef[k];
+        StageCoef &C = coef[k];
         double cb = 0.0, ce = 0.0;
         if (tab.abm) {
             // ABM2: predictor P = m0 + h [(1 + w/2) F_n - (w/2) F_{n-1}]
@@ -1892,44 +1916,57 @@ __device__ void prepare_coefs(DevState *st, const TabArgs &tab, const PhysArgs &
         C.cb[l] = cb;
         C.ce[l] = ce;
         C.cbf[l] = (float)cb;
-        C.cef[l] = (float)ce;
+        const float hi = (float)ce;
+        C.cef[l] = hi;
+        C.cel[l] = (float)(ce - (double)hi);
     }
-    for (int it = tid; it < MMX_MAXS * MMX_NHIST; it += blockDim.x) {
-        const int k = it / MMX_NHIST, j = it % MMX_NHIST;
+    for (int it = tid; it < MMX_MAXS * (MMX_NHIST + 1); it += blockDim.x) {
+        const int k = it / (MMX_NHIST + 1), j = it % (MMX_NHIST + 1);
         double w = 0.0;
         if (primed && k < s && j < np1) {
             w = sm_iden[j];
             for (int q = 0; q < np1; ++q)
                 if (q != j) w *= tab.a[k] - sm_sig[q];
         }
-        st->coef[k].w[j] = w;
-        st->coef[k].wf[j] = (float)w;
+        coef[k].w[j] = w;
+        coef[k].wf[j] = (float)w;
     }
     for (int k = tid; k < MMX_MAXS; k += blockDim.x) {
         const double tk = t0 + tab.a[k] * h;
         const bool on = (tk >= ph.t_on) && (tk < ph.t_off);
         for (int c = 0; c < 3; ++c) {
             const double v = ph.H0[c] + (on ? ph.pulse[c] : 0.0);
-            st->coef[k].H[c] = v;
-            st->coef[k].Hf[c] = (float)v;
+            coef[k].H[c] = v;
+            coef[k].Hf[c] = (float)v;
         }
+        coef[k].H[3] = 0.0;
+        coef[k].Hf[3] = 0.0f;
+    }
+}
+
+// Copies of the state words the stage kernels read, next to each stage's
+// coefficients (written after every controller decision and by k_prepare).
+__device__ __forceinline__ void publish_state(const DevState *st, StageCoef *coef)
+{
+    for (int k = threadIdx.x; k < MMX_MAXS; k += blockDim.x) {
+        const int4 v = make_int4(st->done, st->cur, st->fbase, st->head);
+        *reinterpret_cast<int4 *>(&coef[k].state[0]) = v;
+        *reinterpret_cast<int4 *>(&coef[k].state[4]) = make_int4(st->f1_valid, 0, 0, 0);
     }
 }
 
 __global__ void k_prepare(DevState *st, const TabArgs tab, const PhysArgs ph, int p)
 {
     __shared__ double sm_sig[MMX_NHIST], sm_iden[MMX_NHIST];
-    if (st->done) return;
-    prepare_coefs(st, tab, ph, p, sm_sig, sm_iden);
+    if (!st->done) prepare_coefs(st, st->coef, tab, ph, p, sm_sig, sm_iden);
+    __syncthreads();
+    publish_state(st, st->coef);
 }
 
-// Eq. 5 controller on a shared-memory copy `st` of the device state (the
-// caller loads it and writes it back); the error accumulator and the block
-// counter live in global memory (gst) and are reset here.
-template <typename T> __device__ void controller(const StageArgs<T> &a, DevState *st, DevState *gst, double e)
+// Eq. 5 controller on a shared-memory copy `st` of the state's head (the
+// caller loads it and writes it back); e is the attempt's error norm.
+template <typename A> __device__ void controller(const A &a, DevState *st, double e)
 {
-    st->err_bits = 0;
-    st->blocks_done = 0;
     st->last_err = e;
     st->attempts++;
     st->run_attempts++;
@@ -2020,197 +2057,314 @@ template <typename T> __device__ void controller(const StageArgs<T> &a, DevState
     if (a.use_cond) cudaGraphSetConditional(a.cond, (unsigned)more);
 }
 
+// E += (hi + lo) v with E = eh + el carried as an unevaluated FP32 pair:
+// hi v split exactly by an FMA (Dekker / Ogita-Rump-Oishi TwoProduct), the
+// sum by Knuth's TwoSum; the rounding-free intrinsics keep the compiler from
+// contracting the error terms away.
+__device__ __forceinline__ void two_acc(float &eh, float &el, float hi, float lo, float v)
+{
+    const float p = __fmul_rn(hi, v);
+    const float pe = __fmaf_rn(hi, v, -p);
+    const float s = __fadd_rn(eh, p);
+    const float bp = __fsub_rn(s, eh);
+    const float se = __fadd_rn(__fsub_rn(eh, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    eh = s;
+    el = __fadd_rn(el, __fadd_rn(se, __fmaf_rn(lo, v, pe)));
+}
+
+// Knuth's TwoSum: s + e = a + b exactly (rounding-free intrinsics: no
+// contraction or reassociation).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+// Component c of the Landau-Lifshitz right-hand side (Eq. 1 in LL form) of
+// one cell from m and the effective field without anisotropy (hA, hB, hC);
+// the uniaxial anisotropy 2K/(mu0 Ms) (m . u) u is added here.
 template <typename T>
+__device__ __forceinline__ T ll_torque(const PhysT<T> &P, int c, T m0_, T m1_, T m2_, T hA, T hB, T hC)
+{
+    const T cm = P.can * (m0_ * P.ku[0] + m1_ * P.ku[1] + m2_ * P.ku[2]);
+    const T H0 = hA + cm * P.ku[0];
+    const T H1 = hB + cm * P.ku[1];
+    const T H2 = hC + cm * P.ku[2];
+    const T cxh0 = m1_ * H2 - m2_ * H1;
+    const T cxh1 = m2_ * H0 - m0_ * H2;
+    const T cxh2 = m0_ * H1 - m1_ * H0;
+    if (c == 0) return -P.gp * (cxh0 + P.alpha * (m1_ * cxh2 - m2_ * cxh1));
+    if (c == 1) return -P.gp * (cxh1 + P.alpha * (m2_ * cxh0 - m0_ * cxh2));
+    return -P.gp * (cxh2 + P.alpha * (m0_ * cxh1 - m1_ * cxh0));
+}
+
+template <typename T> __device__ __forceinline__ T coef_cb(const StageCoef &C, int l)
+{
+    if constexpr (sizeof(T) == 4) return C.cbf[l]; else return C.cb[l];
+}
+template <typename T> __device__ __forceinline__ T coef_w(const StageCoef &C, int j)
+{
+    if constexpr (sizeof(T) == 4) return C.wf[j]; else return C.w[j];
+}
+template <typename T> __device__ __forceinline__ T coef_H(const StageCoef &C, int c)
+{
+    if constexpr (sizeof(T) == 4) return C.Hf[c]; else return C.H[c];
+}
+
+
+// One RK stage k (Eq. 4), or with LAST the Eq. 3 solution, the embedded
+// error and its per-CTA maximum, for one cell per thread.  Reads: Y_k and its
+// six neighbours (x neighbours from the adjacent lanes), NH demag sources
+// (the exact non-self field, or the Eq. 6 history fields), the NF stage
+// derivatives fl[], and m0; writes F_k and Y_{k+1} (or m and, in FP32, the
+// compensated state's low words).  STAGE0: the input is m0 itself, and when
+// F_1 of this t0 is already known (a rejected retry, or FSAL) it is reused.
+template <typename T, int NF, int NH, bool LAST, bool STAGE0>
 __global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
 {
     pdl_entry();
-    __shared__ T s_w[MMX_NHIST];       // Eq. 6 weights
-    __shared__ T s_H[3];               // applied field at t0 + a_k h
-    __shared__ T s_cb[MMX_MAXS];       // h b_{k+1,l}  or  h c_l (last stage)
-    __shared__ T s_ce[MMX_MAXS];       // h (c_l - c_hat_l) (last stage)
+    __shared__ T s_cb[MMX_MAXS + 1];          // coefficient of each F read, then of F_k (index NF)
+    __shared__ T s_w[MMX_NHIST + 1];          // Eq. 6 weights (1 for the exact field)
+    __shared__ T s_H[4];                      // applied field at t0 + a_k h
+    __shared__ float s_eh[MMX_MAXS + 1], s_el[MMX_MAXS + 1];  // FP32 last stage: h (c - c_hat) as a pair
+    __shared__ double s_ed[MMX_MAXS + 1];                      // FP64 last stage
     __shared__ T s_red[ST_THREADS / 32];
-    __shared__ int s_last;
-    __shared__ double s_sig[MMX_NHIST], s_iden[MMX_NHIST];
     DevState *st = a.st;
-    if (st->done) {
-        if (a.last && a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
-        return;
-    }
-    const int k = a.k;
-    const int n = (int)a.ph.n;
-    const int cur = st->cur, fbase = st->fbase, head = st->head;
-    const bool f1v = (k == 0) && st->f1_valid;
-    const bool ext = a.extrap && k > 0;
-    const int np1 = a.ctl.p + 1;
-    const int s = a.tab.s;
+    const StageCoef &C = st->coef[a.k];
     if (threadIdx.x < 32) {
-        const StageCoef &C = st->coef[k];
         const int l = threadIdx.x;
-        if (l < MMX_MAXS) {
-            s_cb[l] = (sizeof(T) == 4) ? (T)C.cbf[l] : (T)C.cb[l];
-            s_ce[l] = (sizeof(T) == 4) ? (T)C.cef[l] : (T)C.ce[l];
-        }
-        if (l < MMX_NHIST) s_w[l] = (sizeof(T) == 4) ? (T)C.wf[l] : (T)C.w[l];
-        if (l < 3) s_H[l] = (sizeof(T) == 4) ? (T)C.Hf[l] : (T)C.H[l];
-    }
-    __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = i < n;
-    const int ns = a.ctl.nslots;
-    const size_t fstride = (size_t)3 * n;
-    T *Fk = a.F + (size_t)((fbase + k) % ns) * fstride;
-    const T *m0 = cur ? a.m1 : a.m0;
-    const PhysT<T> &P = a.pt;
-    const bool last = a.last != 0;
-    // Part of Eq. 4 (next stage input) or Eq. 3 (solution, embedded
-    // difference) that does not involve F_k: issued first so that these
-    // loads overlap the field evaluation.
-    T acc[3] = {0, 0, 0}, E[3] = {0, 0, 0};
-    if (valid) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) acc[c] = m0[c * n + i];
-        const int lmax = last ? s - 1 : k;
-#pragma unroll
-        for (int l = 0; l < MMX_MAXS - 1; ++l) {
-            if (l >= lmax) break;
-            const bool use = last ? (a.tab.c[l] != 0.0 || a.tab.e[l] != 0.0) : (a.tab.b[k + 1][l] != 0.0);
-            if (!use) continue;
-            const T *Fl = a.F + (size_t)((fbase + l) % ns) * fstride;
-            const T cb = s_cb[l], ce = s_ce[l];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const T v = Fl[c * n + i];
-                acc[c] += cb * v;
-                if (last) E[c] += ce * v;
-            }
-        }
-        // ABM2: F_{n-1} in slot s enters the predictor and the error (its
-        // coefficients are zero, and the slot unread, on a restart)
-        if (a.tab.abm && (s_cb[s] != (T)0 || s_ce[s] != (T)0)) {
-            const T *Fp = a.F + (size_t)((fbase + s) % ns) * fstride;
-            const T cb = s_cb[s], ce = s_ce[s];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const T v = Fp[c * n + i];
-                acc[c] += cb * v;
-                if (last) E[c] += ce * v;
-            }
-        }
-    }
-    T f[3] = {0, 0, 0};
-    if (valid) {
-        if (f1v) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) f[c] = Fk[c * n + i];
-        } else {
-            const T *Y = (k == 0) ? m0 : ((k & 1) ? a.Y1 : a.Y0);
-            const int x = i & (P.nx - 1);
-            const int y = (i >> P.lgnx) & (P.ny - 1);
-            const int z = i >> (P.lgnx + P.lgny);
-            const int sy = P.nx, sz = P.nx * P.ny;
-            const int xm = x > 0 ? i - 1 : i, xp = x < P.nx - 1 ? i + 1 : i;
-            const int ym = y > 0 ? i - sy : i, yp = y < P.ny - 1 ? i + sy : i;
-            const int zm = z > 0 ? i - sz : i, zp = z < P.nz - 1 ? i + sz : i;
-            T m[3], H[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const T *Yc = Y + c * n;
-                const T cen = Yc[i];
-                m[c] = cen;
-                H[c] = P.wx * (Yc[xp] - 2 * cen + Yc[xm]) + P.wy * (Yc[yp] - 2 * cen + Yc[ym]) +
-                       P.wz * (Yc[zp] - 2 * cen + Yc[zm]);
-            }
-            T g[3] = {0, 0, 0};
-            if (ext) {
-#pragma unroll
-                for (int j = 0; j < MMX_NHIST; ++j) {
-                    if (j >= np1) break;
-                    const T *Gj = a.hist + (size_t)j * fstride;
-                    const T w = s_w[j];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) g[c] += w * Gj[c * n + i];
+        for (int j = 0; j <= NF; ++j)
+            if (l == j) {
+                const int fl = (j < NF) ? a.fl[j] : a.k;
+                s_cb[j] = coef_cb<T>(C, fl);
+                if (LAST) {
+                    if constexpr (sizeof(T) == 4) {
+                        s_eh[j] = C.cef[fl];
+                        s_el[j] = C.cel[fl];
+                    } else {
+                        s_ed[j] = C.ce[fl];
+                    }
                 }
-            } else {
-                const T *Gk = (k == 0 && a.ctl.p >= 0) ? a.hist + (size_t)head * fstride : a.G;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) g[c] = Gk[c * n + i];
             }
-            const T mu = m[0] * P.ku[0] + m[1] * P.ku[1] + m[2] * P.ku[2];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) H[c] += P.can * mu * P.ku[c] + g[c] - P.msN00[c] * m[c] + s_H[c];
-            // Eq. 1 in Landau-Lifshitz form: F = -gp (m x H + alpha m x (m x H))
-            const T cxh0 = m[1] * H[2] - m[2] * H[1];
-            const T cxh1 = m[2] * H[0] - m[0] * H[2];
-            const T cxh2 = m[0] * H[1] - m[1] * H[0];
-            const T dd0 = m[1] * cxh2 - m[2] * cxh1;
-            const T dd1 = m[2] * cxh0 - m[0] * cxh2;
-            const T dd2 = m[0] * cxh1 - m[1] * cxh0;
-            f[0] = -P.gp * (cxh0 + P.alpha * dd0);
-            f[1] = -P.gp * (cxh1 + P.alpha * dd1);
-            f[2] = -P.gp * (cxh2 + P.alpha * dd2);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) Fk[c * n + i] = f[c];
-        }
+        if (l < NH) s_w[l] = a.ext ? coef_w<T>(C, l) : (T)1;
+        if (l < 3) s_H[l] = coef_H<T>(C, l);
     }
-    if (!last) {
-        // Eq. 4: Y_{k+1} = m0 + h sum_{l<=k} b_{k+1,l} F_l
-        if (valid) {
-            T *Yn = ((k + 1) & 1) ? a.Y1 : a.Y0;
+    const PhysT<T> &P = a.pt;
+    const int n = P.n;
+    const int i = blockIdx.x * ST_THREADS + threadIdx.x;
+    const bool valid = i < n;
+    const int lane = threadIdx.x & 31;
+    const size_t fs = (size_t)3 * n;
+    const int4 sv = *reinterpret_cast<const int4 *>(&C.state[0]);  // done, cur, fbase, head
+    const int fb = a.fstatic ? 0 : sv.z;
+
+    // stage derivatives of Eq. 4 / Eq. 3
+    T Fv[NF > 0 ? NF : 1][3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) Yn[c * n + i] = acc[c] + s_cb[k] * f[c];
-        }
-        if (ext && blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
-        return;
+    for (int j = 0; j < NF; ++j) {
+        const int slot = a.fstatic ? a.fl[j] : (fb + a.fl[j]) % a.ns;
+        const T *p = a.F + (size_t)slot * fs + i;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Fv[j][c] = valid ? p[(size_t)c * n] : (T)0;
     }
-    // Eq. 3: propagated solution, embedded difference, renormalisation
-    T err = 0;
-    if (valid) {
-        T M[3];
+    // demag sources
+    T Gv[NH][3];
+    {
+        const T *g = a.ext ? a.hist : (a.gdyn ? a.hist + (size_t)sv.w * fs : a.G);
+#pragma unroll
+        for (int j = 0; j < NH; ++j)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Gv[j][c] = valid ? g[(size_t)j * fs + (size_t)c * n + i] : (T)0;
+    }
+    // stage input and its neighbours
+    const T *Y = STAGE0 ? (sv.y ? a.m1 : a.m0) : a.Yin;
+    const int x = i & (P.nx - 1);
+    const int y = (i >> P.lgnx) & (P.ny - 1);
+    const int z = i >> (P.lgnx + P.lgny);
+    const int sy = P.nx, sz = P.nx * P.ny;
+    T c0[3], ym[3], yp[3], zm[3], zp[3], edge[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T *Yc = Y + (size_t)c * n;
+        c0[c] = valid ? Yc[i] : (T)0;
+        ym[c] = (valid && y > 0) ? Yc[i - sy] : c0[c];
+        yp[c] = (valid && y < P.ny - 1) ? Yc[i + sy] : c0[c];
+        zm[c] = (valid && z > 0) ? Yc[i - sz] : c0[c];
+        zp[c] = (valid && z < P.nz - 1) ? Yc[i + sz] : c0[c];
+        // x neighbours held by no lane of this warp
+        edge[c] = (valid && lane == 0 && x > 0) ? Yc[i - 1] : ((valid && lane == 31 && x < P.nx - 1) ? Yc[i + 1] : c0[c]);
+    }
+    // m0 (its buffer is the state's cur) and, in FP32, the compensated state's low words
+    const T *m0p = sv.y ? a.m1 : a.m0;
+    T mv[3], lv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        mv[c] = STAGE0 ? c0[c] : (valid ? m0p[(size_t)c * n + i] : (T)0);
+        lv[c] = (LAST && sizeof(T) == 4 && valid) ? a.mlo[(size_t)sv.y * fs + (size_t)c * n + i] : (T)0;
+    }
+    T Fk0[3] = {(T)0, (T)0, (T)0};
+    const bool f1v = STAGE0 && C.state[4] != 0;  // F_1 of this t0 is already in its slot
+    T *Fk = a.F + (size_t)((fb + a.k) % a.ns) * fs + i;
+    if (f1v && valid) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Fk0[c] = Fk[(size_t)c * n];
+    }
+    // x neighbours from the adjacent lanes (every lane takes part)
+    T xl[3], xr[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T up = __shfl_up_sync(0xffffffffu, c0[c], 1);
+        const T dn = __shfl_down_sync(0xffffffffu, c0[c], 1);
+        xl[c] = (x == 0) ? c0[c] : (lane > 0 ? up : edge[c]);
+        xr[c] = (x == P.nx - 1) ? c0[c] : (lane < 31 ? dn : edge[c]);
+    }
+    if (sv.x) return;  // the run is done (uniform: the same state word for every CTA)
+    __syncthreads();   // coefficients in shared memory
+
+    T f[3];
+    if (f1v) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) f[c] = Fk0[c];
+    } else {
+        T H[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            M[c] = acc[c] + s_cb[s - 1] * f[c];
-            E[c] += s_ce[s - 1] * f[c];
-        }
-        const T r = sqrt(M[0] * M[0] + M[1] * M[1] + M[2] * M[2]);
-        const T inv = (T)1 / r;
-        T *mo = cur ? a.m0 : a.m1;
+            T g = (T)0;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) mo[c * n + i] = M[c] * inv;
+            for (int j = 0; j < NH; ++j) g += s_w[j] * Gv[j][c];
+            // the non-self field and the self term are both of order Ms N00 and
+            // nearly cancel in thin films: subtract them first, in one rounding
+            const T d = fma(-P.msN00[c], c0[c], g) + s_H[c];
+            H[c] = P.wx * (xr[c] - 2 * c0[c] + xl[c]) + P.wy * (yp[c] - 2 * c0[c] + ym[c]) +
+                   P.wz * (zp[c] - 2 * c0[c] + zm[c]) + d;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) f[c] = ll_torque<T>(P, c, c0[0], c0[1], c0[2], H[0], H[1], H[2]);
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Fk[(size_t)c * n] = f[c];
+        }
+    }
+    if (a.ext && blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&st->extrap_evals), 1ULL);
+    // h sum_l b_l F_l over the reads and F_k; a zero coefficient drops its term
+    // (a slot with nothing valid in it, e.g. ABM2's F_{n-1} after a restart)
+    T inc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        T acc = s_cb[NF] * f[c];
+#pragma unroll
+        for (int j = 0; j < NF; ++j) acc += (s_cb[j] != (T)0) ? s_cb[j] * Fv[j][c] : (T)0;
+        inc[c] = acc;
+    }
+    if (!LAST) {
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) a.Yout[(size_t)c * n + i] = mv[c] + inc[c];
+        }
+        return;
+    }
+    // Eq. 3: solution, embedded difference, renormalisation.  In FP32 the
+    // state m is a compensated pair (hi, lo): the increment is added to hi
+    // exactly (TwoSum) with the rounding carried in lo, so that the per-step
+    // rounding of m does not accumulate over a trajectory.
+    T M[3], E[3], lo[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if constexpr (sizeof(T) == 4) {
+            float e;
+            two_sum(mv[c], inc[c], M[c], e);
+            lo[c] = lv[c] + e;
+            float eh = 0.f, el = 0.f;
+#pragma unroll
+            for (int j = 0; j < NF; ++j)
+                if (s_eh[j] != 0.f || s_el[j] != 0.f) two_acc(eh, el, s_eh[j], s_el[j], Fv[j][c]);
+            two_acc(eh, el, s_eh[NF], s_el[NF], f[c]);
+            E[c] = __fadd_rn(eh, el);
+        } else {
+            M[c] = mv[c] + inc[c];
+            lo[c] = (T)0;
+            double e = 0.0;
+#pragma unroll
+            for (int j = 0; j < NF; ++j)
+                if (s_ed[j] != 0.0) e = fma(s_ed[j], (double)Fv[j][c], e);
+            E[c] = (T)fma(s_ed[NF], (double)f[c], e);
+        }
+    }
+    T err = (T)0;
+    if (valid) {
+        const T r = sqrt(M[0] * M[0] + M[1] * M[1] + M[2] * M[2]);
         err = sqrt(E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
         if (!(err <= (T)3.0e38) || !(r == r) || r == (T)0) err = (T)INFINITY;
+        T *mo = sv.y ? a.m0 : a.m1;
+        if constexpr (sizeof(T) == 4) {
+            // (hi + lo) / r as a pair: hi' = hi inv rounded, its exact error by an
+            // FMA, lo' = that error + lo inv, renormalised (Fast2Sum); a rounded
+            // inv only rescales the three components alike
+            const float inv = 1.0f / r;
+            T *ml = a.mlo + (size_t)(sv.y ^ 1) * fs;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float q = __fmul_rn(M[c], inv);
+                const float l = __fmaf_rn(lo[c], inv, __fmaf_rn(M[c], inv, -q));
+                const float h = __fadd_rn(q, l);
+                mo[(size_t)c * n + i] = h;
+                ml[(size_t)c * n + i] = __fsub_rn(l, __fsub_rn(h, q));
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) mo[(size_t)c * n + i] = M[c] / r;
+        }
     }
-    if (ext && blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = err;
+    if (lane == 0) s_red[threadIdx.x >> 5] = err;
     __syncthreads();
     if (threadIdx.x == 0) {
-        T mx = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, s_red[w]);
-        atomicMax(&st->err_bits, (unsigned long long)__double_as_longlong((double)mx));
-        __threadfence();
-        const unsigned prev = atomicAdd(&st->blocks_done, 1u);
-        s_last = (prev == gridDim.x - 1) ? 1 : 0;
+        T mx = (T)0;
+#pragma unroll
+        for (int w = 0; w < ST_THREADS / 32; ++w) mx = fmax(mx, s_red[w]);
+        a.errpart[blockIdx.x] = mx;
+    }
+}
+
+// The end of every attempt (one CTA): the largest error norm over the last
+// stage's per-CTA maxima, the Eq. 5 controller on a shared-memory copy of
+// the state's head, the next attempt's coefficients, and the loop condition.
+template <typename T>
+__global__ void __launch_bounds__(256) k_control(const CtlKArgs<T> a)
+{
+    pdl_entry();
+    constexpr int HW = (int)(offsetof(DevState, coef) / 8);
+    __shared__ __align__(16) unsigned long long s_head[HW];
+    __shared__ double s_sig[MMX_NHIST], s_iden[MMX_NHIST];
+    __shared__ T s_m[8];
+    DevState *st = a.st;
+    unsigned long long *gw = reinterpret_cast<unsigned long long *>(st);
+    for (int w = threadIdx.x; w < HW; w += blockDim.x) s_head[w] = gw[w];
+    T e = (T)0;
+    for (int j = threadIdx.x; j < a.nparts; j += blockDim.x) e = fmax(e, a.errpart[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e = fmax(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = e;
+    __syncthreads();
+    DevState *sst = reinterpret_cast<DevState *>(s_head);
+    if (sst->done) {  // nothing ran (uniform)
+        if (a.use_cond && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        T mx = (T)0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, s_m[w]);
+        controller(a, sst, (double)mx);
     }
     __syncthreads();
-    if (s_last) {
-        // the state in shared memory: one coalesced read and one write-back
-        // instead of dozens of dependent global round trips in the controller
-        __shared__ __align__(16) DevState sst;
-        __threadfence();
-        const int nw = (int)(sizeof(DevState) / 8);
-        unsigned long long *gw = reinterpret_cast<unsigned long long *>(st);
-        unsigned long long *sw = reinterpret_cast<unsigned long long *>(&sst);
-        for (int i = threadIdx.x; i < nw; i += blockDim.x) sw[i] = ((volatile unsigned long long *)gw)[i];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const double e = __longlong_as_double((long long)atomicExch(&st->err_bits, 0ULL));
-            controller(a, &sst, st, e);
-        }
-        __syncthreads();
-        if (!sst.done) prepare_coefs(&sst, a.tab, a.ph, a.ctl.p, s_sig, s_iden);
-        __syncthreads();
-        for (int i = threadIdx.x; i < nw; i += blockDim.x) gw[i] = sw[i];
-    }
+    if (!sst->done) prepare_coefs(sst, st->coef, a.tab, a.ph, a.ctl.p, s_sig, s_iden);
+    publish_state(sst, st->coef);
+    __syncthreads();
+    for (int w = threadIdx.x; w < HW; w += blockDim.x) gw[w] = s_head[w];
 }
 
 // ----------------------------------------------------------- host helpers
@@ -2531,17 +2685,10 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
 
     const bool prof = c->profiling;
     auto timed = [&](int cls, auto launch) {
-        if (prof) cudaEventRecord(c->ev_a, s);
+        if (prof) mmx_prof_begin(c, s);
         launch();
         c->launches++;
-        if (prof) {
-            cudaEventRecord(c->ev_b, s);
-            cudaEventSynchronize(c->ev_b);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, c->ev_a, c->ev_b);
-            c->prof_ms[cls] += ms;
-            c->prof_n[cls]++;
-        }
+        if (prof) mmx_prof_end(c, s, cls);
     };
     // cluster-fused y-z pass: one cluster of yzc_C CTAs per kx column
     auto launch_yzc = [&]() {
@@ -2693,17 +2840,20 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
 template <typename T>
 void stage_t(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime, cudaGraphConditionalHandle cond, int use_cond)
 {
+    const TabArgs &tb = c->tab;
+    const int S = tb.s;
+    const bool last = (k == S - 1);
     StageArgs<T> a{};
+    a.Yin = (const T *)c->Y[k & 1];
+    a.Yout = (T *)c->Y[(k + 1) & 1];
     a.m0 = (T *)c->m[0];
     a.m1 = (T *)c->m[1];
-    a.Y0 = (T *)c->Y[0];
-    a.Y1 = (T *)c->Y[1];
+    a.mlo = (T *)c->mlo;
     a.F = (T *)c->F;
     a.G = (T *)c->G;
     a.hist = (T *)c->hist;
+    a.errpart = (T *)c->errpart;
     a.st = c->st;
-    a.tab = c->tab;
-    a.ph = c->ph;
     a.pt.wx = (T)c->ph.wx;
     a.pt.wy = (T)c->ph.wy;
     a.pt.wz = (T)c->ph.wz;
@@ -2714,32 +2864,58 @@ void stage_t(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime, cudaGraph
         a.pt.ku[q] = (T)c->ph.ku[q];
         a.pt.msN00[q] = (T)c->ph.msN00[q];
     }
+    a.pt.n = (int)c->n;
     a.pt.nx = c->nx;
     a.pt.ny = c->ny;
     a.pt.nz = c->nz;
     a.pt.lgnx = __builtin_ctz(c->nx);
     a.pt.lgny = __builtin_ctz(c->ny);
-    a.ctl = c->ctl;
-    a.ctl.prime = prime;
     a.k = k;
-    a.extrap = extrap;
-    a.last = (k == c->tab.s - 1);
-    a.use_cond = use_cond;
-    a.cond = cond;
-    const int grid = (int)((c->n + ST_THREADS - 1) / ST_THREADS);
-    const int cls = a.last ? 4 : 3;
-    if (c->profiling) cudaEventRecord(c->ev_a, s);
-    void *sargs[] = {(void *)&a};
-    launch_k(c, (const void *)k_stage<T>, dim3(grid), dim3(ST_THREADS), sargs, 0, s);
-    c->launches++;
-    if (c->profiling) {
-        cudaEventRecord(c->ev_b, s);
-        cudaEventSynchronize(c->ev_b);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, c->ev_a, c->ev_b);
-        c->prof_ms[cls] += ms;
-        c->prof_n[cls]++;
+    // the stage derivatives this stage reads: Eq. 4 row k + 1 (l < k with
+    // b_{k+1,l} != 0), at the last stage the l with c_l or c_l - c^_l != 0;
+    // ABM2 reads F_{n-1} (slot s) at both stages and F_n at the last
+    int nf = 0;
+    if (tb.abm) {
+        if (k > 0) a.fl[nf++] = 0;
+        a.fl[nf++] = S;
+    } else if (last) {
+        for (int l = 0; l < S - 1; ++l)
+            if (tb.c[l] != 0.0 || tb.e[l] != 0.0) a.fl[nf++] = l;
+    } else {
+        for (int l = 0; l < k; ++l)
+            if (tb.b[k + 1][l] != 0.0) a.fl[nf++] = l;
     }
+    const bool ext = extrap && k > 0;
+    const int nh = ext ? c->ctl.p + 1 : 1;
+    a.ext = ext ? 1 : 0;
+    a.gdyn = (k == 0 && c->ctl.p >= 0) ? 1 : 0;
+    // the ring of stage derivatives rotates only for FSAL without
+    // extrapolation and for ABM2; otherwise F_l is always slot l
+    a.fstatic = (c->ctl.p >= 0 && !tb.abm) ? 1 : 0;
+    a.ns = c->ctl.nslots;
+    const void *fn = mmxk_stage_kernel(sizeof(T) == 8, nf, nh, last, k == 0);
+    const int grid = (int)((c->n + ST_THREADS - 1) / ST_THREADS);
+    if (c->profiling) mmx_prof_begin(c, s);
+    void *sargs[] = {(void *)&a};
+    launch_k(c, fn, dim3(grid), dim3(ST_THREADS), sargs, 0, s);
+    c->launches++;
+    if (c->profiling) mmx_prof_end(c, s, last ? 4 : 3);
+    if (!last) return;
+    CtlKArgs<T> ca{};
+    ca.st = c->st;
+    ca.errpart = (const T *)c->errpart;
+    ca.nparts = grid;
+    ca.tab = c->tab;
+    ca.ph = c->ph;
+    ca.ctl = c->ctl;
+    ca.ctl.prime = prime;
+    ca.use_cond = use_cond;
+    ca.cond = cond;
+    if (c->profiling) mmx_prof_begin(c, s);
+    void *cargs[] = {(void *)&ca};
+    launch_k(c, mmxk_control_kernel(sizeof(T) == 8), dim3(1), dim3(256), cargs, 0, s);
+    c->launches++;
+    if (c->profiling) mmx_prof_end(c, s, 5);
 }
 
 template <typename T> void twiddles(int L, std::vector<cx<T>> &out)

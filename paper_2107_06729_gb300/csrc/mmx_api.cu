@@ -225,7 +225,8 @@ int kernels_per_attempt(const mmx_ctx *c, int prime)
     const int p = c->ctl.p;
     const int extrap = (p >= 0 && !prime);
     const int nd = c->nd;  // kernels per demag evaluation
-    return extrap ? nd + c->tab.s + (c->rnet ? 6 * (c->tab.s - 1) : 0) : (nd + 1) * c->tab.s;
+    // + 1: the controller kernel after the last stage
+    return extrap ? nd + c->tab.s + 1 + (c->rnet ? 6 * (c->tab.s - 1) : 0) : (nd + 1) * c->tab.s + 1;
 }
 
 int build_graph(mmx_ctx *c, int which)
@@ -260,10 +261,56 @@ int build_graph(mmx_ctx *c, int which)
     return 0;
 }
 
+// Profiled attempt graph of loop kind `which`: the body with an event pair
+// around every timed launch (no conditional node: the host reads the loop
+// flag after each attempt).
+int build_prof_graph(mmx_ctx *c, int which)
+{
+    if (c->pgraph_ok[which]) return 0;
+    const long long launches = c->launches;
+    c->pcls[which].clear();
+    c->prof_cap = which;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        body_kernels(c, c->cap_stream, which == 1 || c->ctl.p < 0, 0, 0);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(c->cap_stream, &g);
+        if (e == cudaSuccess) {
+            e = cudaGraphInstantiate(&c->pgexec[which], g, 0);
+            if (e == cudaSuccess) c->pgraph[which] = g;
+            else cudaGraphDestroy(g);
+        }
+    }
+    c->prof_cap = -1;
+    c->launches = launches;
+    if (e != cudaSuccess) return cuda_fail(c, e, "profiled attempt graph");
+    c->pgraph_ok[which] = true;
+    return 0;
+}
+
 // Runs attempts until the device says stop (done, or primed for which = 1).
 int run_loop(mmx_ctx *c, int which)
 {
     const int prime = (which == 1 || c->ctl.p < 0);
+    if (c->use_graphs && c->profiling) {
+        int rc = build_prof_graph(c, which);
+        if (rc) return rc;
+        for (;;) {
+            CK(cudaGraphLaunch(c->pgexec[which], c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            const std::vector<int> &cls = c->pcls[which];
+            for (size_t i = 0; i < cls.size(); ++i) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, c->pev[which][2 * i], c->pev[which][2 * i + 1]));
+                c->prof_ms[cls[i]] += ms;
+                c->prof_n[cls[i]]++;
+            }
+            rc = read_state(c);
+            if (rc) return rc;
+            c->launches += kernels_per_attempt(c, prime);
+            if (!c->h_st->loop_more) return 0;
+        }
+    }
     if (c->use_graphs && !c->profiling) {
         int rc = build_graph(c, which);
         if (rc) return rc;
@@ -451,6 +498,61 @@ int autotune(mmx_ctx *c)
 
 void mmx_set_thread_error(const char *msg) { g_create_err = msg ? msg : ""; }
 
+// Event pair around one timed launch; see mmx_ctx::prof_cap.
+void mmx_prof_begin(mmx_ctx *c, cudaStream_t s)
+{
+    if (c->prof_cap >= 0) {
+        const int w = c->prof_cap;
+        const size_t i = c->pcls[w].size();
+        while (c->pev[w].size() < 2 * i + 2) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return;
+            }
+            c->pev[w].push_back(e);
+        }
+        // an external record: a real event-record node in the captured graph
+        cudaEventRecordWithFlags(c->pev[w][2 * i], s, cudaEventRecordExternal);
+        return;
+    }
+    cudaEventRecord(c->ev_a, s);
+}
+
+void mmx_prof_end(mmx_ctx *c, cudaStream_t s, int cls)
+{
+    if (c->prof_cap >= 0) {
+        const int w = c->prof_cap;
+        const size_t i = c->pcls[w].size();
+        if (c->pev[w].size() < 2 * i + 2) return;  // no event could be made: this launch is not timed
+        cudaEventRecordWithFlags(c->pev[w][2 * i + 1], s, cudaEventRecordExternal);
+        c->pcls[w].push_back(cls);
+        return;
+    }
+    cudaEventRecord(c->ev_b, s);
+    cudaEventSynchronize(c->ev_b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev_a, c->ev_b);
+    c->prof_ms[cls] += ms;
+    c->prof_n[cls]++;
+}
+
+void mmx_drop_graphs(mmx_ctx *c)
+{
+    for (int i = 0; i < 2; ++i) {
+        if (c->graph_ok[i]) {
+            cudaGraphExecDestroy(c->gexec[i]);
+            cudaGraphDestroy(c->graph[i]);
+            c->graph_ok[i] = false;
+        }
+        if (c->pgraph_ok[i]) {
+            cudaGraphExecDestroy(c->pgexec[i]);
+            cudaGraphDestroy(c->pgraph[i]);
+            c->pgraph_ok[i] = false;
+        }
+    }
+}
+
 extern "C" {
 
 int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *field, const mmx_integrator *integ,
@@ -586,7 +688,11 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     const int nh = std::max(1, C.p + 1);
     bool ok = true;
     ok = ok && alloc(&c->m[0], fb) && alloc(&c->m[1], fb) && alloc(&c->Y[0], fb) && alloc(&c->Y[1], fb);
+    c->mlo = nullptr;
+    c->errpart = nullptr;
+    if (c->prec == MMX_FP32_MIXED) ok = ok && alloc(&c->mlo, 2 * fb);
     ok = ok && alloc(&c->F, fb * C.nslots) && alloc(&c->G, fb) && alloc(&c->hist, fb * nh);
+    ok = ok && alloc(&c->errpart, (size_t)((c->n + 127) / 128) * c->esz);
     ok = ok && alloc(&c->S, (size_t)c->rows * c->nx * 2 * c->esz);
     if (c->split && !c->cluster) ok = ok && alloc(&c->Tb, (size_t)c->nx * 3 * c->nz * c->Py * 2 * c->esz);
     ok = ok && alloc(&c->K, Kspec.size() * c->esz);
@@ -610,6 +716,7 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     }
     cudaMemset(c->m[0], 0, fb);
     cudaMemset(c->m[1], 0, fb);
+    if (c->mlo) cudaMemset(c->mlo, 0, 2 * fb);
     cudaMemset(c->F, 0, fb * C.nslots);
     cudaMemset(c->hist, 0, fb * nh);
     // pass configuration by timing, unless forced or switched off
@@ -652,6 +759,7 @@ int mmx_set_m(mmx_ctx *c, const void *m)
     int rc = read_state(c);
     if (rc) return rc;
     CK(cudaMemcpyAsync(c->m[0], m, (size_t)3 * c->n * c->esz, cudaMemcpyDefault, c->stream));
+    if (c->mlo) CK(cudaMemsetAsync(c->mlo, 0, (size_t)3 * c->n * c->esz, c->stream));  // low words of m[0]
     c->h_st->cur = 0;
     reset_history(c->h_st);
     return write_state(c);
@@ -702,8 +810,6 @@ static bool begin_run(mmx_ctx *c, double t_end, long long acc_more)
     s.t_start_ns = 0;
     const char *tl = getenv("MMX_TIME_LIMIT_S");
     s.time_limit_ns = (unsigned long long)((tl ? atof(tl) : 300.0) * 1e9);
-    s.err_bits = 0;
-    s.blocks_done = 0;
     const double rem = s.t_end - s.t;
     const int cl = (s.h_ctrl * (1.0 + 1e-9) >= rem) ? 1 : 0;
     s.h = cl ? rem : s.h_ctrl;
@@ -789,7 +895,7 @@ int mmx_save_state(mmx_ctx *c, void *buf, size_t *len)
     if (!c || !len) return MMX_ERR_ARG;
     const size_t fb = (size_t)3 * c->n * c->esz;
     const int nh = std::max(1, c->ctl.p + 1);
-    const size_t need = sizeof(BlobHeader) + sizeof(DevState) + fb * (2 + c->ctl.nslots + nh);
+    const size_t need = sizeof(BlobHeader) + sizeof(DevState) + fb * (2 + c->ctl.nslots + nh) + (c->mlo ? 2 * fb : 0);
     if (!buf) {
         *len = need;
         return MMX_OK;
@@ -810,6 +916,8 @@ int mmx_save_state(mmx_ctx *c, void *buf, size_t *len)
     CK(cudaMemcpy(p, c->F, fb * c->ctl.nslots, cudaMemcpyDeviceToHost));
     p += fb * c->ctl.nslots;
     CK(cudaMemcpy(p, c->hist, fb * nh, cudaMemcpyDeviceToHost));
+    p += fb * nh;
+    if (c->mlo) CK(cudaMemcpy(p, c->mlo, 2 * fb, cudaMemcpyDeviceToHost));
     *len = need;
     return MMX_OK;
 }
@@ -819,7 +927,7 @@ int mmx_load_state(mmx_ctx *c, const void *buf, size_t len)
     if (!c || !buf) return MMX_ERR_ARG;
     const size_t fb = (size_t)3 * c->n * c->esz;
     const int nh = std::max(1, c->ctl.p + 1);
-    const size_t need = sizeof(BlobHeader) + sizeof(DevState) + fb * (2 + c->ctl.nslots + nh);
+    const size_t need = sizeof(BlobHeader) + sizeof(DevState) + fb * (2 + c->ctl.nslots + nh) + (c->mlo ? 2 * fb : 0);
     if (len < need) return fail(c, MMX_ERR_ARG, "state blob too short");
     BlobHeader hd;
     memcpy(&hd, buf, sizeof(hd));
@@ -837,6 +945,8 @@ int mmx_load_state(mmx_ctx *c, const void *buf, size_t len)
     CK(cudaMemcpy(c->F, p, fb * c->ctl.nslots, cudaMemcpyHostToDevice));
     p += fb * c->ctl.nslots;
     CK(cudaMemcpy(c->hist, p, fb * nh, cudaMemcpyHostToDevice));
+    p += fb * nh;
+    if (c->mlo) CK(cudaMemcpy(c->mlo, p, 2 * fb, cudaMemcpyHostToDevice));
     c->h_st->done = 1;
     return write_state(c);
 }
@@ -885,13 +995,10 @@ void mmx_destroy(mmx_ctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
-    for (int i = 0; i < 2; ++i) {
-        if (c->graph_ok[i]) {
-            cudaGraphExecDestroy(c->gexec[i]);
-            cudaGraphDestroy(c->graph[i]);
-        }
-    }
-    void *bufs[] = {c->m[0], c->m[1], c->Y[0], c->Y[1], c->F, c->G, c->hist, c->S, c->K, c->twx, c->twy, c->twz, c->Tb,
+    mmx_drop_graphs(c);
+    for (int i = 0; i < 2; ++i)
+        for (cudaEvent_t e : c->pev[i]) cudaEventDestroy(e);
+    void *bufs[] = {c->m[0], c->m[1], c->mlo, c->errpart, c->Y[0], c->Y[1], c->F, c->G, c->hist, c->S, c->K, c->twx, c->twy, c->twz, c->Tb,
                     c->st};
     for (void *b : bufs)
         if (b) cudaFree(b);

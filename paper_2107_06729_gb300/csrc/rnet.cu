@@ -1278,12 +1278,7 @@ extern "C" int mmx_set_residual(mmx_ctx *c, mmx_rnet *net)
         return MMX_ERR_CUDA;
     }
     // the captured attempt graphs hold the old stage sequence
-    for (int i = 0; i < 2; ++i)
-        if (c->graph_ok[i]) {
-            cudaGraphExecDestroy(c->gexec[i]);
-            cudaGraphDestroy(c->graph[i]);
-            c->graph_ok[i] = false;
-        }
+    mmx_drop_graphs(c);
     c->rnet = net;
     return MMX_OK;
 }

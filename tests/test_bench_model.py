@@ -25,7 +25,30 @@ def test_fused_pass_model_per_cell():
     # FP64 doubles every term
     m8 = bench.demag_pass_bytes(n, 8, split=False)
     assert all(m8[k] == 2 * m[k] for k in m)
-    assert bench.byte_model({"mesh": {"n": n}}, 4) == m
+    bm = bench.byte_model({"mesh": {"n": n}, "integrator": {"extrap_order": 4}}, 4)
+    assert all(bm[k] == m[k] for k in m)
+
+
+def test_stage_model_per_cell_dp54_p4():
+    """DP54 with 4th-order extrapolation in FP32 (u = 12 B/cell): stage 1
+    reads m0 and the exact field and writes F_1 and Y_2 (4u = 48 B); stages
+    2..6 read Y_k, five history fields, the F_l with nonzero b and m0 and
+    write two fields: 120, 132, 144, 156, 156 B (b72 = 0); the last stage
+    reads Y_7, the history, F_l for l in {1, 3, 4, 5, 6} (c_2 = c_2 - c^_2 =
+    0) and m0 and writes F_7 and m: 168 B, plus the compensated state's low
+    words read and written in FP32: 192 B."""
+    cells = 256 * 128 * 4
+    mean, last = bench.stage_bytes(cells, 4, 4)
+    assert mean == pytest.approx((48 + 120 + 132 + 144 + 156 + 156) / 6 * cells)
+    assert last == 192 * cells
+    assert bench.stage_bytes(cells, 8, 4)[1] == 2 * 168 * cells
+    # the read pattern is the tableau's nonzero pattern (oracle's copy of the
+    # published coefficients)
+    import oracle as O
+    t = O.tableau("RKDP54")
+    for k, reads in bench.DP54_B_READ.items():
+        assert reads == [l for l in range(k) if t["b"][k + 1][l] != 0.0]
+    assert bench.DP54_LAST_READ == [l for l in range(6) if t["c"][l] != 0.0 or t["c"][l] != t["chat"][l]]
 
 
 def test_split_pass_model_of_the_large_box():
