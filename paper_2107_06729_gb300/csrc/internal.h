@@ -50,7 +50,7 @@ struct DevState {
     int status;
     int clipped;     // current attempt lands exactly on t_end
     int loop_more;   // last value handed to the graph's while condition
-    int fault;       // a bounded device wait gave up (the context is unusable)
+    int pad0_;
     long long accepted, rejected, exact_evals, extrap_evals, forced, attempts;
     long long acc_target;     // stop when accepted reaches this
     long long attempt_limit;  // attempts allowed in the current run
@@ -58,6 +58,10 @@ struct DevState {
     long long prime_attempts;  // attempts made by priming loops (launch accounting)
     unsigned long long t_start_ns, time_limit_ns;
     StageCoef coef[MMX_MAXS];  // everything before coef is the "head" the controller copies
+    // outside the head (the controller never writes these back):
+    int spec_src;  // m buffer the last stage wrote (the speculative demag passes read it)
+    int fault;     // a bounded device wait gave up (the context is unusable); sticky
+    int pad_[2];
 };
 
 static_assert(sizeof(DevState) % 8 == 0, "DevState is copied as 8-byte words");
@@ -103,6 +107,8 @@ struct mmx_ctx {
     size_t esz;
     cudaStream_t stream;
     cudaStream_t cap_stream;
+    cudaStream_t cap_stream2;       // second capture stream: the speculative demag passes
+    cudaEvent_t ev_fork, ev_join;   // fork and join of the two capture streams
     int nx, ny, nz;
     long long n;
     int Px, Py, Pz, Hy, Hz;
@@ -171,6 +177,12 @@ int mmxk_setup_buffers(mmx_ctx *c, const double *Kspec_host);
 //   self_src != NULL: subtract Ms N00 self_src (full field, as in mmx_demag)
 void mmxk_demag(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src_mode,
                 const void *src, int dst_mode, void *dst, const void *self_src);
+// the same passes, a subset of them: parts = 1 (x forward) | 2 (y-z, tensor
+// multiply) | 4 (x inverse); src_mode 2 reads m[spec_src]
+void mmxk_demag_parts(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src_mode, const void *src,
+                      int dst_mode, void *dst, const void *self_src, int parts);
+// the controller kernel that ends every attempt
+void mmxk_control(mmx_ctx *c, cudaStream_t s, int prime_graph, cudaGraphConditionalHandle cond, int use_cond);
 void mmxk_stage(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime_graph,
                 cudaGraphConditionalHandle cond, int use_cond);
 // stage_f32.cu / stage_f64.cu: the stage kernel instance for nf stage

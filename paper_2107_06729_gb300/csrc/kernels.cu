@@ -160,13 +160,27 @@ int mmxk_setup_buffers(mmx_ctx *c, const double *Kspec_host)
     return c->prec == MMX_FP64 ? setup_t<double>(c, Kspec_host) : setup_t<float>(c, Kspec_host);
 }
 
+void mmxk_demag_parts(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src_mode, const void *src,
+                      int dst_mode, void *dst, const void *self_src, int parts)
+{
+    if (c->prec == MMX_FP64)
+        demag_t<double>(c, s, st, stage0, src_mode, src, dst_mode, dst, self_src, parts);
+    else
+        demag_t<float>(c, s, st, stage0, src_mode, src, dst_mode, dst, self_src, parts);
+}
+
 void mmxk_demag(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src_mode, const void *src,
                 int dst_mode, void *dst, const void *self_src)
 {
+    mmxk_demag_parts(c, s, st, stage0, src_mode, src, dst_mode, dst, self_src, 7);
+}
+
+void mmxk_control(mmx_ctx *c, cudaStream_t s, int prime_graph, cudaGraphConditionalHandle cond, int use_cond)
+{
     if (c->prec == MMX_FP64)
-        demag_t<double>(c, s, st, stage0, src_mode, src, dst_mode, dst, self_src);
+        control_t<double>(c, s, prime_graph, cond, use_cond);
     else
-        demag_t<float>(c, s, st, stage0, src_mode, src, dst_mode, dst, self_src);
+        control_t<float>(c, s, prime_graph, cond, use_cond);
 }
 
 void mmxk_stage(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime_graph, cudaGraphConditionalHandle cond,

@@ -512,7 +512,7 @@ __device__ __forceinline__ void col_fft_any(const Pad<T> buf, int L, int base, i
 // ------------------------------------------------------------------ XF / XI
 template <typename T> struct XArgs {
     const T *src;        // src_mode 0
-    const T *msrc0, *msrc1;  // src_mode 1: m[cur]
+    const T *msrc0, *msrc1;  // src_mode 1: m[cur]; 2: m[spec_src] (the last stage's new m)
     T *dst;              // dst_mode 0
     T *hist;             // dst_mode 1: hist + head * 3n
     const T *self_src;   // optional: subtract Ms N00 self_src
@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(256, 2) k_xf(const XArgs<T> a)
         if (a.st->done) return;
         if (a.stage0 && a.st->f1_valid) return;
     }
-    const T *src = a.src_mode == 1 ? (a.st->cur ? a.msrc1 : a.msrc0) : a.src;
+    const T *src = a.src_mode == 0 ? a.src : ((a.src_mode == 1 ? a.st->cur : a.st->spec_src) ? a.msrc1 : a.msrc0);
     const int nx = a.nx, Px = 2 * nx, lgnx = ilog2(nx);
     constexpr int PXS = PX + XPAIR_GAP;  // pair stride: pairs land in different banks
     const int np = (a.trows + 1) >> 1;
@@ -1298,7 +1298,7 @@ __global__ void __launch_bounds__(256, 2) k_xf_p(const XArgs<T> a)
         if (a.stage0 && a.st->f1_valid) return;
     }
     constexpr int NX = PX / 2, PXS = PX + XPAIR_GAP;
-    const T *src = a.src_mode == 1 ? (a.st->cur ? a.msrc1 : a.msrc0) : a.src;
+    const T *src = a.src_mode == 0 ? a.src : ((a.src_mode == 1 ? a.st->cur : a.st->spec_src) ? a.msrc1 : a.msrc0);
     const int T_ = a.trows, np = T_ >> 1;
     const long long R = a.rows;
     const int nitems = (int)(R / T_);
@@ -1965,7 +1965,7 @@ __global__ void k_prepare(DevState *st, const TabArgs tab, const PhysArgs ph, in
 
 // Eq. 5 controller on a shared-memory copy `st` of the state's head (the
 // caller loads it and writes it back); e is the attempt's error norm.
-template <typename A> __device__ void controller(const A &a, DevState *st, double e)
+template <typename A> __device__ void controller(const A &a, DevState *st, double e, int fault)
 {
     st->last_err = e;
     st->attempts++;
@@ -1973,7 +1973,7 @@ template <typename A> __device__ void controller(const A &a, DevState *st, doubl
     if (a.ctl.prime) st->prime_attempts++;
     const double h = st->h;
     int more = 0;
-    if (st->fault) {  // a bounded wait of this attempt's kernels gave up: stop the run
+    if (fault) {  // a bounded wait of this attempt's kernels gave up: stop the run
         st->status = MMX_ERR_CUDA;
         st->done = 1;
     } else if (!(e <= 1.7976931348623157e308)) {  // NaN or Inf
@@ -2293,6 +2293,9 @@ __global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
             E[c] = (T)fma(s_ed[NF], (double)f[c], e);
         }
     }
+    // the buffer the new m goes to: the next attempt's speculative demag
+    // passes transform it while the controller decides (state outside the head)
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->spec_src = sv.y ^ 1;
     T err = (T)0;
     if (valid) {
         const T r = sqrt(M[0] * M[0] + M[1] * M[1] + M[2] * M[2]);
@@ -2358,7 +2361,7 @@ __global__ void __launch_bounds__(256) k_control(const CtlKArgs<T> a)
     if (threadIdx.x == 0) {
         T mx = (T)0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, s_m[w]);
-        controller(a, sst, (double)mx);
+        controller(a, sst, (double)mx, *(volatile int *)&st->fault);
     }
     __syncthreads();
     if (!sst->done) prepare_coefs(sst, st->coef, a.tab, a.ph, a.ctl.p, s_sig, s_iden);
@@ -2639,7 +2642,7 @@ inline void launch_k(const mmx_ctx *c, const void *f, dim3 grid, dim3 block, voi
 
 template <typename T>
 void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src_mode, const void *src, int dst_mode,
-             void *dst, const void *self_src)
+             void *dst, const void *self_src, int parts)
 {
     const int trows = c->trows ? c->trows : pick_trows(c);
     XArgs<T> xa{};
@@ -2739,7 +2742,7 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
         }
     };
     void *yargs[] = {(void *)&ya};
-    const void *xsrc = src_mode == 1 ? c->m[0] : src;
+    const void *xsrc = src_mode != 0 ? c->m[0] : src;
     if (pipe_ok<T>(c) && ((uintptr_t)xsrc & 15) == 0 && ((uintptr_t)c->m[1] & 15) == 0) {
         XArgs<T> xf = xa;
         xf.trows = XF_P_ROWS;
@@ -2772,10 +2775,11 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
         const long long n_y = (long long)c->nx * (3 * c->nz / sa.ry), n_z = (long long)c->nx * (c->Py / sa.W);
         const void *f_xf = mmxk_kernel(K_XFP, sizeof(T) == 8, c->Px), *f_yf = mmxk_kernel(K_YFP, sizeof(T) == 8, c->Py),
                    *f_yi = mmxk_kernel(K_YIP, sizeof(T) == 8, c->Py), *f_zm = mmxk_kernel(K_ZMP, sizeof(T) == 8, c->Pz);
-        timed(0, [&] {
-            launch_k(c, f_xf, dim3(persistent_grid(f_xf, txf, s_xf, n_x)), dim3(txf), xfa, s_xf, s);
-        });
-        timed(1, [&] {
+        if (parts & 1)
+            timed(0, [&] {
+                launch_k(c, f_xf, dim3(persistent_grid(f_xf, txf, s_xf, n_x)), dim3(txf), xfa, s_xf, s);
+            });
+        if (parts & 2) timed(1, [&] {
             if (c->cluster) {
                 launch_yzc();
                 return;
@@ -2795,11 +2799,13 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
             launch_k(c, f_yi, dim3(persistent_grid(f_yi, tyy, s_yi, n_y)), dim3(tyy), sargs, s_yi, s);
             c->launches += 2;
         });
-        timed(2, launch_xi);
+        if (parts & 4) timed(2, launch_xi);
         return;
     }
-    timed(0, [&] { launch_k(c, mmxk_kernel(K_XF, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s); });
-    if (c->cluster) {
+    if (parts & 1)
+        timed(0, [&] { launch_k(c, mmxk_kernel(K_XF, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s); });
+    if (!(parts & 2)) {
+    } else if (c->cluster) {
         timed(1, launch_yzc);
     } else if (!c->split) {
         timed(1, [&] { launch_k(c, mmxk_kernel(K_YZ, sizeof(T) == 8, c->Py), dim3(c->nx), dim3(YZ_THREADS), yargs, ys, s); });
@@ -2834,7 +2840,7 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
             c->launches += 2;
         });
     }
-    timed(2, launch_xi);
+    if (parts & 4) timed(2, launch_xi);
 }
 
 template <typename T>
@@ -2900,7 +2906,13 @@ void stage_t(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime, cudaGraph
     launch_k(c, fn, dim3(grid), dim3(ST_THREADS), sargs, 0, s);
     c->launches++;
     if (c->profiling) mmx_prof_end(c, s, last ? 4 : 3);
-    if (!last) return;
+}
+
+// The controller kernel that ends an attempt (after the last stage).
+template <typename T>
+void control_t(mmx_ctx *c, cudaStream_t s, int prime, cudaGraphConditionalHandle cond, int use_cond)
+{
+    const int grid = (int)((c->n + ST_THREADS - 1) / ST_THREADS);
     CtlKArgs<T> ca{};
     ca.st = c->st;
     ca.errpart = (const T *)c->errpart;

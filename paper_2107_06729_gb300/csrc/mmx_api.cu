@@ -201,13 +201,31 @@ void reset_history(DevState *s)
     s->h_prev = 0;  // ABM2 restarts with the Euler predictor
 }
 
+// Extrapolated attempts captured into a graph run speculatively: while the
+// controller decides on an attempt, the x and y-z demag passes of the next
+// attempt already transform the new m on a second stream (a rejected attempt
+// needs no new demag: its exact field and F_1 are kept, and the x-inverse
+// pass of the retry skips).  Such a body starts at the x-inverse pass; the
+// first attempt of a loop gets its x and y-z passes from front_kernels.
+bool speculative(const mmx_ctx *c, int prime) { return c->ctl.p >= 0 && !prime; }
+
+// x and y-z demag passes of m[cur] before a speculative attempt loop (they
+// skip, like the x-inverse pass, when F_1 of this t0 is still valid)
+void front_kernels(mmx_ctx *c, cudaStream_t s) { mmxk_demag_parts(c, s, c->st, 1, 1, nullptr, 1, c->G, nullptr, 3); }
+
 // One attempted step, launched on stream s.  prime: full demag at every
-// stage (priming or extrap_order < 0).
-int body_kernels(mmx_ctx *c, cudaStream_t s, int prime, cudaGraphConditionalHandle cond, int use_cond)
+// stage (priming or extrap_order < 0).  s2: second capture stream of a
+// speculative body (null: the whole attempt on s).
+int body_kernels(mmx_ctx *c, cudaStream_t s, int prime, cudaGraphConditionalHandle cond, int use_cond,
+                 cudaStream_t s2 = nullptr)
 {
     const int p = c->ctl.p;
     const int extrap = (p >= 0 && !prime);
-    mmxk_demag(c, s, c->st, 1, 1, nullptr, p >= 0 ? 1 : 0, c->G, nullptr);
+    const bool spec = s2 && speculative(c, prime);
+    if (spec)
+        mmxk_demag_parts(c, s, c->st, 1, 1, nullptr, 1, c->G, nullptr, 4);
+    else
+        mmxk_demag(c, s, c->st, 1, 1, nullptr, p >= 0 ? 1 : 0, c->G, nullptr);
     mmxk_stage(c, s, 0, extrap, prime && p >= 0, cond, use_cond);
     for (int k = 1; k < c->tab.s; ++k) {
         if (!extrap) mmxk_demag(c, s, c->st, 0, 0, c->Y[k & 1], 0, c->G, nullptr);
@@ -217,6 +235,16 @@ int body_kernels(mmx_ctx *c, cudaStream_t s, int prime, cudaGraphConditionalHand
         if (res) c->launches += mmxk_rnet_stage(c->rnet, c, s, k);
         mmxk_stage(c, s, k, res ? 0 : extrap, prime && p >= 0, cond, use_cond);
     }
+    if (!spec) {
+        mmxk_control(c, s, prime && p >= 0, cond, use_cond);
+        return 0;
+    }
+    cudaEventRecord(c->ev_fork, s);
+    cudaStreamWaitEvent(s2, c->ev_fork, 0);
+    mmxk_control(c, s, 0, cond, use_cond);
+    mmxk_demag_parts(c, s2, c->st, 0, 2, nullptr, 1, c->G, nullptr, 3);
+    cudaEventRecord(c->ev_join, s2);
+    cudaStreamWaitEvent(s, c->ev_join, 0);
     return 0;
 }
 
@@ -248,7 +276,7 @@ int build_graph(mmx_ctx *c, int which)
     CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    body_kernels(c, c->cap_stream, which == 1 || c->ctl.p < 0, h, 1);
+    body_kernels(c, c->cap_stream, which == 1 || c->ctl.p < 0, h, 1, c->cap_stream2);
     cudaGraph_t captured;
     CK(cudaStreamEndCapture(c->cap_stream, &captured));
     c->launches = launches;
@@ -272,7 +300,7 @@ int build_prof_graph(mmx_ctx *c, int which)
     c->prof_cap = which;
     cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-        body_kernels(c, c->cap_stream, which == 1 || c->ctl.p < 0, 0, 0);
+        body_kernels(c, c->cap_stream, which == 1 || c->ctl.p < 0, 0, 0, c->cap_stream2);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(c->cap_stream, &g);
         if (e == cudaSuccess) {
@@ -292,6 +320,10 @@ int build_prof_graph(mmx_ctx *c, int which)
 int run_loop(mmx_ctx *c, int which)
 {
     const int prime = (which == 1 || c->ctl.p < 0);
+    if (c->use_graphs && speculative(c, prime)) {
+        front_kernels(c, c->stream);
+        c->launches += c->nd - 1;
+    }
     if (c->use_graphs && c->profiling) {
         int rc = build_prof_graph(c, which);
         if (rc) return rc;
@@ -701,6 +733,9 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     ok = ok && alloc((void **)&c->st, sizeof(DevState));
     ok = ok && cudaMallocHost((void **)&c->h_st, sizeof(DevState)) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaEventCreate(&c->ev_a) == cudaSuccess && cudaEventCreate(&c->ev_b) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -1004,6 +1039,9 @@ void mmx_destroy(mmx_ctx *c)
         if (b) cudaFree(b);
     if (c->h_st) cudaFreeHost(c->h_st);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_a) cudaEventDestroy(c->ev_a);
     if (c->ev_b) cudaEventDestroy(c->ev_b);
     delete c;
@@ -1063,6 +1101,19 @@ int build_batch_graph(mmx_batch *b)
             cudaGraphNode_t gate, node;
             cudaGraphNodeParams cp{};
             cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+            if (e == cudaSuccess && speculative(c, which == 1 || c->ctl.p < 0)) {
+                // the first attempt's x and y-z passes, as a child graph
+                cudaGraph_t fg = nullptr;
+                cudaGraphNode_t fn;
+                e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed);
+                if (e == cudaSuccess) {
+                    front_kernels(c, c->cap_stream);
+                    e = cudaStreamEndCapture(c->cap_stream, &fg);
+                }
+                if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&fn, g, &prev, 1, fg);
+                if (fg) cudaGraphDestroy(fg);
+                if (e == cudaSuccess) prev = fn;
+            }
             if (e == cudaSuccess && mmxk_add_gate_node(g, &prev, 1, c, h, which, &gate)) e = cudaErrorUnknown;
             if (e == cudaSuccess) {
                 cp.type = cudaGraphNodeTypeConditional;
@@ -1075,7 +1126,7 @@ int build_batch_graph(mmx_batch *b)
                 e = cudaStreamBeginCaptureToGraph(c->cap_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeRelaxed);
             if (e == cudaSuccess) {
-                body_kernels(c, c->cap_stream, which == 1 || c->ctl.p < 0, h, 1);
+                body_kernels(c, c->cap_stream, which == 1 || c->ctl.p < 0, h, 1, c->cap_stream2);
                 cudaGraph_t captured;
                 e = cudaStreamEndCapture(c->cap_stream, &captured);
             }
@@ -1203,7 +1254,7 @@ int mmx_batch_run(mmx_batch *b, const double *t_end, int *status)
         const DevState &s = *c->h_st;
         const long long pa = s.prime_attempts - b->prime0[i];
         const int gates = c->ctl.p >= 0 ? 2 : 1;
-        c->launches += 1 + gates;
+        c->launches += 1 + gates + (speculative(c, c->ctl.p < 0) ? c->nd - 1 : 0);
         int r = MMX_OK;
         if (b->active[i]) {
             c->launches += pa * kernels_per_attempt(c, 1) + (s.run_attempts - pa) * kernels_per_attempt(c, c->ctl.p < 0);
