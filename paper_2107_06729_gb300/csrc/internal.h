@@ -25,8 +25,8 @@ struct StageCoef {
     double w[MMX_NHIST + 1];   // Eq. 6 Lagrange weights at t0 + a_k h (one pad word)
     double H[4];               // applied field at t0 + a_k h (one pad word)
     float cbf[MMX_MAXS], cef[MMX_MAXS];
-    float cel[MMX_MAXS];       // ce - cef: low part of the FP32 split of ce (compensated error sum)
     float wf[MMX_NHIST + 1], Hf[4];
+    float pad_[8];
     int state[8];              // done, cur, fbase, head, f1_valid (copies; see publish_state)
 };
 

@@ -1814,6 +1814,7 @@ template <typename T> struct StageArgs {
     int gdyn;       // stage 0 with a history: the exact field is history slot head
     int fstatic;    // the stage-derivative ring never rotates (fbase = 0): slot addresses are static
     int ns;         // stage-derivative slots
+    int zguard;     // a read slot may hold nothing valid (ABM2's F_{n-1}): zero coefficients drop it
     int fl[MMX_MAXS];  // indices l of the stage derivatives this stage reads (the template's NF of them)
 };
 
@@ -1916,9 +1917,7 @@ __device__ void prepare_coefs(const DevState *st, StageCoef *coef, const TabArgs
         C.cb[l] = cb;
         C.ce[l] = ce;
         C.cbf[l] = (float)cb;
-        const float hi = (float)ce;
-        C.cef[l] = hi;
-        C.cel[l] = (float)(ce - (double)hi);
+        C.cef[l] = (float)ce;
     }
     for (int it = tid; it < MMX_MAXS * (MMX_NHIST + 1); it += blockDim.x) {
         const int k = it / (MMX_NHIST + 1), j = it % (MMX_NHIST + 1);
@@ -2057,21 +2056,6 @@ template <typename A> __device__ void controller(const A &a, DevState *st, doubl
     if (a.use_cond) cudaGraphSetConditional(a.cond, (unsigned)more);
 }
 
-// E += (hi + lo) v with E = eh + el carried as an unevaluated FP32 pair:
-// hi v split exactly by an FMA (Dekker / Ogita-Rump-Oishi TwoProduct), the
-// sum by Knuth's TwoSum; the rounding-free intrinsics keep the compiler from
-// contracting the error terms away.
-__device__ __forceinline__ void two_acc(float &eh, float &el, float hi, float lo, float v)
-{
-    const float p = __fmul_rn(hi, v);
-    const float pe = __fmaf_rn(hi, v, -p);
-    const float s = __fadd_rn(eh, p);
-    const float bp = __fsub_rn(s, eh);
-    const float se = __fadd_rn(__fsub_rn(eh, __fsub_rn(s, bp)), __fsub_rn(p, bp));
-    eh = s;
-    el = __fadd_rn(el, __fadd_rn(se, __fmaf_rn(lo, v, pe)));
-}
-
 // Knuth's TwoSum: s + e = a + b exactly (rounding-free intrinsics: no
 // contraction or reassociation).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
@@ -2127,8 +2111,8 @@ __global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
     __shared__ T s_cb[MMX_MAXS + 1];          // coefficient of each F read, then of F_k (index NF)
     __shared__ T s_w[MMX_NHIST + 1];          // Eq. 6 weights (1 for the exact field)
     __shared__ T s_H[4];                      // applied field at t0 + a_k h
-    __shared__ float s_eh[MMX_MAXS + 1], s_el[MMX_MAXS + 1];  // FP32 last stage: h (c - c_hat) as a pair
-    __shared__ double s_ed[MMX_MAXS + 1];                      // FP64 last stage
+    __shared__ T s_ce[MMX_MAXS + 1];           // last stage: h (c - c_hat) of each read, then of F_k
+    __shared__ T s_cesum;                      // their sum, taken in FP64 (zero up to rounding)
     __shared__ T s_red[ST_THREADS / 32];
     DevState *st = a.st;
     const StageCoef &C = st->coef[a.k];
@@ -2139,15 +2123,14 @@ __global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
             if (l == j) {
                 const int fl = (j < NF) ? a.fl[j] : a.k;
                 s_cb[j] = coef_cb<T>(C, fl);
-                if (LAST) {
-                    if constexpr (sizeof(T) == 4) {
-                        s_eh[j] = C.cef[fl];
-                        s_el[j] = C.cel[fl];
-                    } else {
-                        s_ed[j] = C.ce[fl];
-                    }
-                }
+                if (LAST) s_ce[j] = (T)C.ce[fl];
             }
+        if (LAST && l == 0) {
+            double sum = C.ce[a.k];
+#pragma unroll
+            for (int j = 0; j < NF; ++j) sum += C.ce[a.fl[j]];
+            s_cesum = (T)sum;
+        }
         if (l < NH) s_w[l] = a.ext ? coef_w<T>(C, l) : (T)1;
         if (l < 3) s_H[l] = coef_H<T>(C, l);
     }
@@ -2158,51 +2141,70 @@ __global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
     const int lane = threadIdx.x & 31;
     const size_t fs = (size_t)3 * n;
     const int4 sv = *reinterpret_cast<const int4 *>(&C.state[0]);  // done, cur, fbase, head
-    const int fb = a.fstatic ? 0 : sv.z;
+    // (the branches below are uniform: taken on kernel arguments, so that the
+    // loads of the static branch do not wait for the state word)
 
     // stage derivatives of Eq. 4 / Eq. 3
     T Fv[NF > 0 ? NF : 1][3];
+    const int ic = valid ? i : n - 1;  // threads past the end read the last cell (no stores)
+    if (a.fstatic) {
 #pragma unroll
-    for (int j = 0; j < NF; ++j) {
-        const int slot = a.fstatic ? a.fl[j] : (fb + a.fl[j]) % a.ns;
-        const T *p = a.F + (size_t)slot * fs + i;
+        for (int j = 0; j < NF; ++j) {
+            const T *p = a.F + (size_t)a.fl[j] * fs + ic;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) Fv[j][c] = valid ? p[(size_t)c * n] : (T)0;
+            for (int c = 0; c < 3; ++c) Fv[j][c] = p[(size_t)c * n];
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NF; ++j) {
+            const T *p = a.F + (size_t)((sv.z + a.fl[j]) % a.ns) * fs + ic;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Fv[j][c] = p[(size_t)c * n];
+        }
     }
-    // demag sources
+    // demag sources: the history fields (Eq. 6), G, or at stage 0 with a
+    // history the exact field in history slot head
     T Gv[NH][3];
     {
-        const T *g = a.ext ? a.hist : (a.gdyn ? a.hist + (size_t)sv.w * fs : a.G);
+        const T *g = a.ext ? a.hist : a.G;
+        if (STAGE0 && a.gdyn) g = a.hist + (size_t)sv.w * fs;
 #pragma unroll
         for (int j = 0; j < NH; ++j)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) Gv[j][c] = valid ? g[(size_t)j * fs + (size_t)c * n + i] : (T)0;
+            for (int c = 0; c < 3; ++c) Gv[j][c] = g[(size_t)j * fs + (size_t)c * n + ic];
     }
+    const int fb = a.fstatic ? 0 : sv.z;
     // stage input and its neighbours
     const T *Y = STAGE0 ? (sv.y ? a.m1 : a.m0) : a.Yin;
-    const int x = i & (P.nx - 1);
-    const int y = (i >> P.lgnx) & (P.ny - 1);
-    const int z = i >> (P.lgnx + P.lgny);
+    const int x = ic & (P.nx - 1);
+    const int y = (ic >> P.lgnx) & (P.ny - 1);
+    const int z = ic >> (P.lgnx + P.lgny);
     const int sy = P.nx, sz = P.nx * P.ny;
-    T c0[3], ym[3], yp[3], zm[3], zp[3], edge[3];
+    // neighbour indices clamped at the free boundary (a missing neighbour is
+    // the cell itself) and at the end of the grid, so that every load is
+    // unconditional; the x neighbours come from L1 like the others
+    const int ixm = x > 0 ? ic - 1 : ic, ixp = x < P.nx - 1 ? ic + 1 : ic;
+    const int iym = y > 0 ? ic - sy : ic, iyp = y < P.ny - 1 ? ic + sy : ic;
+    const int izm = z > 0 ? ic - sz : ic, izp = z < P.nz - 1 ? ic + sz : ic;
+    T c0[3], xl[3], xr[3], ym[3], yp[3], zm[3], zp[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const T *Yc = Y + (size_t)c * n;
-        c0[c] = valid ? Yc[i] : (T)0;
-        ym[c] = (valid && y > 0) ? Yc[i - sy] : c0[c];
-        yp[c] = (valid && y < P.ny - 1) ? Yc[i + sy] : c0[c];
-        zm[c] = (valid && z > 0) ? Yc[i - sz] : c0[c];
-        zp[c] = (valid && z < P.nz - 1) ? Yc[i + sz] : c0[c];
-        // x neighbours held by no lane of this warp
-        edge[c] = (valid && lane == 0 && x > 0) ? Yc[i - 1] : ((valid && lane == 31 && x < P.nx - 1) ? Yc[i + 1] : c0[c]);
+        c0[c] = Yc[ic];
+        xl[c] = Yc[ixm];
+        xr[c] = Yc[ixp];
+        ym[c] = Yc[iym];
+        yp[c] = Yc[iyp];
+        zm[c] = Yc[izm];
+        zp[c] = Yc[izp];
     }
     // m0 (its buffer is the state's cur) and, in FP32, the compensated state's low words
     const T *m0p = sv.y ? a.m1 : a.m0;
     T mv[3], lv[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        mv[c] = STAGE0 ? c0[c] : (valid ? m0p[(size_t)c * n + i] : (T)0);
-        lv[c] = (LAST && sizeof(T) == 4 && valid) ? a.mlo[(size_t)sv.y * fs + (size_t)c * n + i] : (T)0;
+        mv[c] = STAGE0 ? c0[c] : m0p[(size_t)c * n + ic];
+        lv[c] = (LAST && sizeof(T) == 4) ? a.mlo[(size_t)sv.y * fs + (size_t)c * n + ic] : (T)0;
     }
     T Fk0[3] = {(T)0, (T)0, (T)0};
     const bool f1v = STAGE0 && C.state[4] != 0;  // F_1 of this t0 is already in its slot
@@ -2210,15 +2212,6 @@ __global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
     if (f1v && valid) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) Fk0[c] = Fk[(size_t)c * n];
-    }
-    // x neighbours from the adjacent lanes (every lane takes part)
-    T xl[3], xr[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const T up = __shfl_up_sync(0xffffffffu, c0[c], 1);
-        const T dn = __shfl_down_sync(0xffffffffu, c0[c], 1);
-        xl[c] = (x == 0) ? c0[c] : (lane > 0 ? up : edge[c]);
-        xr[c] = (x == P.nx - 1) ? c0[c] : (lane < 31 ? dn : edge[c]);
     }
     if (sv.x) return;  // the run is done (uniform: the same state word for every CTA)
     __syncthreads();   // coefficients in shared memory
@@ -2249,15 +2242,25 @@ __global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
     }
     if (a.ext && blockIdx.x == 0 && threadIdx.x == 0)
         atomicAdd(reinterpret_cast<unsigned long long *>(&st->extrap_evals), 1ULL);
-    // h sum_l b_l F_l over the reads and F_k; a zero coefficient drops its term
-    // (a slot with nothing valid in it, e.g. ABM2's F_{n-1} after a restart)
+    // h sum_l b_l F_l over the reads and F_k; with zguard a zero coefficient
+    // drops its term (ABM2's F_{n-1} slot holds nothing valid after a restart)
     T inc[3];
+    if (a.zguard) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        T acc = s_cb[NF] * f[c];
+        for (int c = 0; c < 3; ++c) {
+            T acc = s_cb[NF] * f[c];
 #pragma unroll
-        for (int j = 0; j < NF; ++j) acc += (s_cb[j] != (T)0) ? s_cb[j] * Fv[j][c] : (T)0;
-        inc[c] = acc;
+            for (int j = 0; j < NF; ++j) acc += (s_cb[j] != (T)0) ? s_cb[j] * Fv[j][c] : (T)0;
+            inc[c] = acc;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            T acc = s_cb[NF] * f[c];
+#pragma unroll
+            for (int j = 0; j < NF; ++j) acc += s_cb[j] * Fv[j][c];
+            inc[c] = acc;
+        }
     }
     if (!LAST) {
         if (valid) {
@@ -2269,7 +2272,11 @@ __global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
     // Eq. 3: solution, embedded difference, renormalisation.  In FP32 the
     // state m is a compensated pair (hi, lo): the increment is added to hi
     // exactly (TwoSum) with the rounding carried in lo, so that the per-step
-    // rounding of m does not accumulate over a trajectory.
+    // rounding of m does not accumulate over a trajectory.  The embedded
+    // difference E = h sum_l (c_l - c^_l) F_l is formed as sum_l ce_l (F_l -
+    // F_ref) + (sum_l ce_l) F_ref: the weights of an embedded pair sum to
+    // zero, so the large common part of the F_l cancels exactly in the
+    // differences instead of in the rounded sum.
     T M[3], E[3], lo[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -2277,21 +2284,16 @@ __global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
             float e;
             two_sum(mv[c], inc[c], M[c], e);
             lo[c] = lv[c] + e;
-            float eh = 0.f, el = 0.f;
-#pragma unroll
-            for (int j = 0; j < NF; ++j)
-                if (s_eh[j] != 0.f || s_el[j] != 0.f) two_acc(eh, el, s_eh[j], s_el[j], Fv[j][c]);
-            two_acc(eh, el, s_eh[NF], s_el[NF], f[c]);
-            E[c] = __fadd_rn(eh, el);
         } else {
             M[c] = mv[c] + inc[c];
             lo[c] = (T)0;
-            double e = 0.0;
-#pragma unroll
-            for (int j = 0; j < NF; ++j)
-                if (s_ed[j] != 0.0) e = fma(s_ed[j], (double)Fv[j][c], e);
-            E[c] = (T)fma(s_ed[NF], (double)f[c], e);
         }
+        const T ref = NF > 0 ? Fv[0][c] : f[c];
+        T acc = s_cesum * ref + s_ce[NF] * (f[c] - ref);
+#pragma unroll
+        for (int j = 1; j < NF; ++j)
+            if (!a.zguard || s_ce[j] != (T)0) acc += s_ce[j] * (Fv[j][c] - ref);
+        E[c] = acc;
     }
     // the buffer the new m goes to: the next attempt's speculative demag
     // passes transform it while the controller decides (state outside the head)
@@ -2899,6 +2901,7 @@ void stage_t(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime, cudaGraph
     // extrapolation and for ABM2; otherwise F_l is always slot l
     a.fstatic = (c->ctl.p >= 0 && !tb.abm) ? 1 : 0;
     a.ns = c->ctl.nslots;
+    a.zguard = tb.abm ? 1 : 0;
     const void *fn = mmxk_stage_kernel(sizeof(T) == 8, nf, nh, last, k == 0);
     const int grid = (int)((c->n + ST_THREADS - 1) / ST_THREADS);
     if (c->profiling) mmx_prof_begin(c, s);
