@@ -535,6 +535,151 @@ def equal_error(pkg, torch, dev, cfg, horizon_ps=2.0, tols=(3e-6, 1e-5, 3e-5, 1e
             "interpolated": in_ex and in_full}
 
 
+def eps_time(mbar, mref):
+    """Eq. 7 with its points taken as time samples of the mean magnetisation:
+    the mean over samples of |<m>(t_s) - <m>_ref(t_s)| (arrays [3, S])."""
+    return float(np.linalg.norm(np.asarray(mbar) - np.asarray(mref), axis=0).mean())
+
+
+def equal_error_timed(pkg, torch, dev, cfg, t0_ps=100.0, t1_ps=500.0, sample_ps=1.0,
+                      tols=(3e-6, 1e-5, 3e-5, 1e-4, 3e-4)):
+    """Equal-error comparison over the regime the headline steps time (after
+    the random start has relaxed): every run starts at t0 from the state of
+    the FP64 full-demag reference (e_max 1e-8) and integrates to t1; error =
+    Eq. 7 over the 1 ps samples of the mean magnetisation <m> (eps_time)
+    against the reference's samples, which stays meaningful once the
+    cell-level dynamics have diverged; speed = simulated ns per wall second of
+    an unsampled repeat of the same interval from the same start; log ns/s
+    interpolated linearly in log error; the ratio at the error the
+    extrapolated run reaches at the configured e_max."""
+    stream = torch.cuda.Stream(dev)
+    S = int(round((t1_ps - t0_ps) / sample_ps))
+    ts = [(t0_ps + sample_ps * (s + 1)) * 1e-12 for s in range(S)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def sampled(ctx, m):
+        out = np.zeros((3, S))
+        for s, t in enumerate(ts):
+            ctx.run(t)
+            ctx.get_m(m)
+            out[:, s] = m.double().mean(dim=(1, 2, 3)).cpu().numpy()
+        return out
+
+    with torch.cuda.stream(stream):
+        ref = pkg.Context(cfg["mesh"], cfg["material"], cfg["field"],
+                          dict(cfg["integrator"], extrap_order=-1, tol=1e-8), "fp64", stream)
+        m64 = torch.from_numpy(cfg["m0"]).to(dev, torch.float64)
+        ref.set_m(m64)
+        ref.run(t0_ps * 1e-12)
+        ref.get_m(m64)
+        start = m64.clone()
+        mref = sampled(ref, m64)
+        ref.close()
+        rows = {}
+        for mode, p in (("extrapolated", cfg["integrator"]["extrap_order"]), ("full", -1)):
+            rows[mode] = []
+            for tol in tols:
+                c = pkg.Context(cfg["mesh"], cfg["material"], cfg["field"],
+                                dict(cfg["integrator"], extrap_order=p, tol=tol), "fp32", stream)
+                m = start.to(torch.float32)
+                c.set_m(m)
+                c.set_time(t0_ps * 1e-12)
+                blob = c.save_state()
+                mbar = sampled(c, m)
+                st = c.stats()
+                c.load_state(blob)
+                torch.cuda.synchronize(dev)
+                ev[0].record(stream)
+                c.run(t1_ps * 1e-12)
+                ev[1].record(stream)
+                torch.cuda.synchronize(dev)
+                secs = ev[0].elapsed_time(ev[1]) / 1e3
+                rows[mode].append({"tol": tol, "eps_time": eps_time(mbar, mref),
+                                   "ns_per_s": round((t1_ps - t0_ps) * 1e-3 / secs, 4),
+                                   "accepted": st["accepted"]})
+                c.close()
+    tol0 = cfg["integrator"]["tol"]
+    target = [r for r in rows["extrapolated"] if r["tol"] == tol0]
+    eps_star = target[0]["eps_time"]
+    conv = {m: [{"eps": r["eps_time"], "ns_per_s": r["ns_per_s"]} for r in rows[m]] for m in rows}
+    v_ex, in_ex = speed_at_error(conv["extrapolated"], eps_star)
+    v_full, in_full = speed_at_error(conv["full"], eps_star)
+    return {"window_ps": [t0_ps, t1_ps], "sample_ps": sample_ps,
+            "metric": "Eq. 7 over 1 ps samples of <m> (eps_time)",
+            "reference": "GPU FP64, full demag at every stage, e_max 1e-8", "sweep": rows,
+            "eps_star": eps_star, "ns_per_s_extrapolated_at_eps_star": round(v_ex, 4),
+            "ns_per_s_full_at_eps_star": round(v_full, 4), "speedup_at_equal_error": round(v_ex / v_full, 3),
+            "interpolated": in_ex and in_full}
+
+
+def large3d_integration(pkg, torch, dev, sim_ps=2.0):
+    """The 512 x 512 x 16 box integrated with the method: Bogacki-Shampine
+    RK23 (adaptive, e_max 1e-5) with 2nd-order extrapolation and RK4 at
+    h = 100 fs with 3rd-order, each against full demag at every stage, in
+    simulated ns per wall second over sim_ps after a warm-up of 1 ps; and the
+    error of each mode (FP32) on the 64 x 64 x 4 sub-box of the same recipe
+    after 20 ps, Eq. 7 over cells against the GPU FP64 full-demag run at
+    e_max 1e-8 (RK23) or h = 10 fs (RK4)."""
+    cfg = W.film_large3d(seed=0)
+    stream = torch.cuda.Stream(dev)
+    modes = {"rk23_p2": {"method": "RK23", "extrap_order": 2}, "rk23_full": {"method": "RK23", "extrap_order": -1},
+             "rk4_p3": {"method": "RK4", "extrap_order": 3, "adaptive": False, "h": 1e-13},
+             "rk4_full": {"method": "RK4", "extrap_order": -1, "adaptive": False, "h": 1e-13}}
+    out = {"workload": "box_512x512x16_fp32", "mesh": list(cfg["mesh"]["n"]), "sim_ps": sim_ps}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(stream):
+        m0 = torch.from_numpy(cfg["m0_fn"]()).to(dev, torch.float32)
+        for name, over in modes.items():
+            c = pkg.Context(cfg["mesh"], cfg["material"], cfg["field"], dict(cfg["integrator"], **over), "fp32", stream)
+            c.set_m(m0)
+            c.run(1e-12)
+            s0 = c.stats()
+            torch.cuda.synchronize(dev)
+            ev[0].record(stream)
+            c.run((1.0 + sim_ps) * 1e-12)
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            s1 = c.stats()
+            secs = ev[0].elapsed_time(ev[1]) / 1e3
+            acc = s1["accepted"] - s0["accepted"]
+            out[name] = {"ns_per_s": round(sim_ps * 1e-3 / secs, 5), "ms_per_step": round(1e3 * secs / max(1, acc), 3),
+                         "accepted": acc, "rejected": s1["rejected"] - s0["rejected"]}
+            c.close()
+        out["speedup_rk23_p2_vs_full"] = round(out["rk23_p2"]["ns_per_s"] / out["rk23_full"]["ns_per_s"], 3)
+        out["speedup_rk4_p3_vs_full"] = round(out["rk4_p3"]["ns_per_s"] / out["rk4_full"]["ns_per_s"], 3)
+        # accuracy on the sub-box
+        n = (64, 64, 4)
+        d = cfg["mesh"]["d"]
+        sub = {"n": n, "d": d}
+        msub = torch.from_numpy(W.m_vortex(n, d, seed=0)).to(dev, torch.float64)
+        t_end = 20e-12
+        eps = {}
+        refs = {}
+        for meth, integ in (("RK23", dict(cfg["integrator"], extrap_order=-1, tol=1e-8)),
+                            ("RK4", {"method": "RK4", "extrap_order": -1, "adaptive": False, "h": 1e-14})):
+            c = pkg.Context(sub, cfg["material"], cfg["field"], integ, "fp64", stream)
+            m = msub.clone()
+            c.set_m(m)
+            c.run(t_end)
+            c.get_m(m)
+            torch.cuda.synchronize(dev)
+            refs[meth] = m.cpu().numpy()
+            c.close()
+        for name, over in modes.items():
+            c = pkg.Context(sub, cfg["material"], cfg["field"], dict(cfg["integrator"], **over), "fp32", stream)
+            m = msub.to(torch.float32)
+            c.set_m(m)
+            c.run(t_end)
+            c.get_m(m)
+            torch.cuda.synchronize(dev)
+            eps[name] = eps_eq7(m.double().cpu().numpy(), refs[over["method"]])
+            c.close()
+    out["eps_subbox_64x64x4_20ps"] = eps
+    out["note"] = ("FP32 fields; extrapolated and full modes on the same start (vortex plus noise, seed 0); "
+                   "error against GPU FP64 full demag (validated against the CPU oracle step for step)")
+    return out
+
+
 def run_mmx(args):
     import torch
     import paper_2107_06729_gb300 as pkg
@@ -708,6 +853,9 @@ def run_mmx(args):
         line["accuracy"] = [accuracy(pkg, torch, dev, cfg, 2.0), accuracy(pkg, torch, dev, cfg, args.chunk_ps)]
     if not args.no_equal_error:
         line["equal_error"] = equal_error(pkg, torch, dev, cfg)
+        line["equal_error_timed_regime"] = equal_error_timed(pkg, torch, dev, cfg)
+    if not args.no_large:
+        line["large3d_integration"] = large3d_integration(pkg, torch, dev)
     if not args.no_large:
         line["demag_roofline_large3d"] = large3d_demag(pkg, torch, dev)
     if not args.no_ensemble:
@@ -784,6 +932,8 @@ def main():
     ap.add_argument("--no-equal-error", action="store_true", help="skip the e_max sweep at equal error")
     ap.add_argument("--only-equal-error", action="store_true", help="only the e_max sweep at equal error")
     ap.add_argument("--only-residual", action="store_true", help="only the learned-residual net timing")
+    ap.add_argument("--only-large-integration", action="store_true",
+                    help="only the 512x512x16 integration (RK23 p=2, RK4 p=3 vs full) and its sub-box error")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mmx":
         args.warmup = 3
@@ -799,7 +949,15 @@ def main():
         import torch
         import paper_2107_06729_gb300 as pkg
         torch.cuda.set_device(0)
-        print(json.dumps({"equal_error": equal_error(pkg, torch, torch.device("cuda", 0), W.film_config2(seed=0))}),
+        dev = torch.device("cuda", 0)
+        cfg = W.film_config2(seed=0)
+        print(json.dumps({"equal_error": equal_error(pkg, torch, dev, cfg),
+                          "equal_error_timed_regime": equal_error_timed(pkg, torch, dev, cfg)}), flush=True)
+    elif args.only_large_integration:
+        import torch
+        import paper_2107_06729_gb300 as pkg
+        torch.cuda.set_device(0)
+        print(json.dumps({"large3d_integration": large3d_integration(pkg, torch, torch.device("cuda", 0))}),
               flush=True)
     elif args.only_residual:
         import torch

@@ -81,3 +81,13 @@ def test_speed_at_error_interpolates_in_log_log():
 def test_aggregate_is_all_units_over_the_slowest_rank():
     value, t_max = bench.aggregate(0.2, 1.5, 4, lambda x: 2.0 * x, lambda x: 4.0 * x)
     assert t_max == 3.0 and value == pytest.approx(0.8 / 3.0)
+
+
+def test_eps_time_is_eq7_over_time_samples():
+    """bench.eps_time (the bench's own copy, no oracle import on the product
+    path) equals the oracle's Eq. 7 over time samples of <m>."""
+    import oracle as O
+    rng = np.random.default_rng(3)
+    a, b = rng.normal(size=(3, 40)), rng.normal(size=(3, 40))
+    assert bench.eps_time(a, b) == pytest.approx(O.epsilon_time(a, b), rel=1e-14)
+    assert bench.eps_time(a, a) == 0.0
