@@ -94,16 +94,43 @@ int mmx_residual_sample(mmx_ctx *ctx, int p, const void *m_nodes_dev, const doub
 
 /* Attaches net to an FP32 context that extrapolates (extrap_order >= 0), or
  * detaches it (net = NULL).  While attached, every extrapolated stage k >= 2
- * of every attempt (Eq. 4-6) uses the non-self field G_ext + Ms r with r =
+ * of an attempt (Eq. 4-6) uses the non-self field G_ext + Ms r with r =
  * net(Y_k, G_ext / Ms) instead of G_ext; stage 1 and the priming steps keep
- * the exact evaluation, and step control is unchanged (Eq. 5).  The net's
- * parameters are read at each use (train it between runs if wanted); it must
- * outlive the attachment, including any batch built while it is attached,
- * and must not be used by another context's run at the same time.
- * MMX_ERR_ARG for an FP64 context, extrap_order < 0 or a net created for
- * fewer cells than the mesh.  Synchronises the context's stream and drops
- * its captured attempt graphs (rebuilt at the next run). */
+ * the exact evaluation.  Exact demag (Eq. 2) is the fallback: an attempt
+ * whose error estimate (Eq. 3-5) exceeds e_max is retried, with the step the
+ * controller proposes, with exact demag at every stage; and with a periodic
+ * check configured (mmx_set_residual_check) every check_every accepted
+ * steps one attempt runs with exact demag at every stage and compares the
+ * net's corrected field with the exact one at stage 2 — while the last check
+ * exceeds its tolerance, every attempt runs with exact demag.  The choice is
+ * made on the device by the controller (conditional graph nodes; no host
+ * round trip).  The net's parameters are read at each use (train it between
+ * runs if wanted); it must outlive the attachment, including any batch
+ * built while it is attached, and must not be used by another context's run
+ * at the same time.  Attaching resets the check state (the net counts as
+ * passing).  MMX_ERR_ARG for an FP64 context, extrap_order < 0 or a net
+ * created for fewer cells than the mesh; MMX_ERR_OOM when the check's
+ * scratch field (3 x cells FP32) cannot be allocated.  Synchronises the
+ * context's stream and drops its captured attempt graphs (rebuilt at the
+ * next run). */
 int mmx_set_residual(mmx_ctx *ctx, mmx_rnet *net);
+
+/* The periodic exact check of an attached net: every `every` accepted steps
+ * (0: never) one attempt runs with exact demag at every stage, and the net's
+ * corrected field at its stage 2 must satisfy max|G_net - G| <= tol max|G|
+ * (max over cells and components); otherwise the following attempts run
+ * with exact demag until a later check passes.  No counterpart in the
+ * paper (the learned residual is this library's addition).  Defaults: 0 and
+ * 0.  MMX_ERR_ARG for every < 0 or tol not finite and >= 0.  Synchronises
+ * the stream and drops the captured attempt graphs. */
+int mmx_set_residual_check(mmx_ctx *ctx, int every, double tol);
+
+/* Counters of the learned residual's fallback since the context was created:
+ * out4[0] attempts with the net rejected by the error estimate (each retried
+ * with exact demag), out4[1] periodic checks run, out4[2] checks that
+ * exceeded their tolerance, out4[3] 1 while the net passes (its last check
+ * within tolerance).  Synchronises the stream. */
+int mmx_residual_stats(mmx_ctx *ctx, long long *out4);
 
 #ifdef __cplusplus
 }

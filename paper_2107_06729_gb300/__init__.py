@@ -108,6 +108,8 @@ SIGNATURES = {
     "mmx_residual_sample": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_double), _VP,
                                            ctypes.c_double, _VP, _VP]),
     "mmx_set_residual": (ctypes.c_int, [_VP, _VP]),
+    "mmx_set_residual_check": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double]),
+    "mmx_residual_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
 }
 
 MMX_RNET_PARAMS = 63171
@@ -339,6 +341,16 @@ def mmx_residual_sample(ctx, p, m_nodes_dev, t_nodes, m_dev, t, x_dev, target_de
     return _check(rc, ctx)
 
 
+def mmx_set_residual_check(ctx, every, tol):
+    return _check(lib().mmx_set_residual_check(ctx, int(every), float(tol)), ctx)
+
+
+def mmx_residual_stats(ctx):
+    out = (ctypes.c_longlong * 4)()
+    _check(lib().mmx_residual_stats(ctx, out), ctx)
+    return {"fallbacks": out[0], "checks": out[1], "check_fails": out[2], "net_ok": out[3]}
+
+
 def mmx_set_residual(ctx, net):
     """Attaches the residual net (handle) to ctx's extrapolated stages; None detaches."""
     return _check(lib().mmx_set_residual(ctx, net), ctx)
@@ -482,6 +494,12 @@ class Context:
 
     def set_profiling(self, on):
         return mmx_set_profiling(self.handle, on)
+
+    def set_residual_check(self, every, tol):
+        return mmx_set_residual_check(self.handle, every, tol)
+
+    def residual_stats(self):
+        return mmx_residual_stats(self.handle)
 
     def set_residual(self, net):
         """Attaches an RNet (kept alive here) to the extrapolated stages; None detaches."""

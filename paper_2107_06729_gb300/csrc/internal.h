@@ -50,7 +50,15 @@ struct DevState {
     int status;
     int clipped;     // current attempt lands exactly on t_end
     int loop_more;   // last value handed to the graph's while condition
-    int pad0_;
+    // learned residual attached: which attempt body runs (0 the net at the
+    // extrapolated stages, 1 exact demag at every stage, 2 exact with the
+    // net checked at stage 2), chosen by the controller for the next attempt
+    int att_mode;    // body of the current attempt (set by the gate kernel)
+    int mode_next;
+    int since_check; // accepted steps since the last periodic check
+    int net_ok;      // the last check was within tolerance
+    unsigned int check_num_bits, check_den_bits;  // check: max |G_net - G|, max |G| (FP32 bits)
+    long long fallbacks, checks, check_fails;
     long long accepted, rejected, exact_evals, extrap_evals, forced, attempts;
     long long acc_target;     // stop when accepted reaches this
     long long attempt_limit;  // attempts allowed in the current run
@@ -96,6 +104,9 @@ struct CtlArgs {
     int prime;     // this graph primes the history: stop once primed
     double tol, hmin, hmax, cmin, cmax, safety;
     double cmin_pow, cmax_pow;  // cmin^(n+1), cmax^(n+1): clamp limits of Eq. 5
+    int has_net;       // a learned residual is attached: choose the next attempt's body
+    int check_every;   // periodic exact check every this many accepted steps (0: none)
+    double check_tol;  // check: max |G_net - G| <= check_tol max |G|
 };
 
 struct mmx_ctx {
@@ -108,6 +119,8 @@ struct mmx_ctx {
     cudaStream_t stream;
     cudaStream_t cap_stream;
     cudaStream_t cap_stream2;       // second capture stream: the speculative demag passes
+    cudaStream_t cap_stream3;       // capture of the conditional attempt bodies (learned residual)
+    void *Gc;                       // learned residual's check: the net-corrected field at stage 2
     cudaEvent_t ev_fork, ev_join;   // fork and join of the two capture streams
     int nx, ny, nz;
     long long n;
@@ -168,6 +181,11 @@ struct mmx_ctx {
 void mmx_prof_begin(mmx_ctx *c, cudaStream_t s);
 void mmx_prof_end(mmx_ctx *c, cudaStream_t s, int cls);
 void mmx_drop_graphs(mmx_ctx *c);
+// synchronises the context and applies f to its device state (read, edit,
+// write back); a copy of the state for reading only
+#include <functional>
+int mmx_state_edit(mmx_ctx *c, const std::function<void(DevState &)> &f);
+int mmx_state_read(mmx_ctx *c, DevState *out);
 
 // kernels.cu
 int mmxk_setup_buffers(mmx_ctx *c, const double *Kspec_host);
@@ -206,6 +224,13 @@ void mmxk_prepare(mmx_ctx *c, cudaStream_t s);
 // the learned residual at stage k of an extrapolated attempt: G = G_ext + Ms r
 // into c->G (launched on s); returns the number of kernels launched
 int mmxk_rnet_stage(struct mmx_rnet *net, mmx_ctx *c, cudaStream_t s, int k);
+// the periodic check at stage k of an exact attempt: the net's corrected
+// field G_ext + Ms r against the exact G (maxima into the state); kernels launched
+int mmxk_rnet_check(struct mmx_rnet *net, mmx_ctx *c, cudaStream_t s, int k);
+// the gate at the top of an attempt body with the learned residual: makes
+// the chosen body current and sets the three bodies' conditions
+void mmxk_mode_gate(mmx_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h0, cudaGraphConditionalHandle h1,
+                    cudaGraphConditionalHandle h2, int use);
 int mmxk_add_prepare_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t nd, mmx_ctx *c, cudaGraphNode_t *out);
 int mmxk_add_gate_node(cudaGraph_t g, const cudaGraphNode_t *deps, size_t nd, mmx_ctx *c,
                        cudaGraphConditionalHandle h, int prime_loop, cudaGraphNode_t *out);

@@ -40,6 +40,27 @@ void mmxk_prepare(mmx_ctx *c, cudaStream_t s)
     c->launches++;
 }
 
+// Top of an attempt body with the learned residual: the body the controller
+// chose becomes the current one, and exactly one body's condition is set.
+__global__ void k_mode_gate(DevState *st, cudaGraphConditionalHandle h0, cudaGraphConditionalHandle h1,
+                            cudaGraphConditionalHandle h2, int use)
+{
+    const int mode = st->done ? -1 : st->mode_next;
+    if (mode >= 0) st->att_mode = mode;
+    if (use) {
+        cudaGraphSetConditional(h0, mode == 0 ? 1u : 0u);
+        cudaGraphSetConditional(h1, mode == 1 ? 1u : 0u);
+        cudaGraphSetConditional(h2, mode == 2 ? 1u : 0u);
+    }
+}
+
+void mmxk_mode_gate(mmx_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h0, cudaGraphConditionalHandle h1,
+                    cudaGraphConditionalHandle h2, int use)
+{
+    k_mode_gate<<<1, 1, 0, s>>>(c->st, h0, h1, h2, use);
+    c->launches++;
+}
+
 // Sets the while condition of one loop of a batched run from the device state
 // before the loop starts: a member that is done, or (priming loop) already
 // primed, skips the loop.  Batched graphs do not reset conditions at launch.

@@ -2031,6 +2031,26 @@ template <typename A> __device__ void controller(const A &a, DevState *st, doubl
             st->rejected++;
             st->f1_valid = 1;
         }
+        if (a.ctl.has_net) {
+            // learned residual: exact demag at every stage for the retry of a
+            // rejected attempt, and for every attempt while the last periodic
+            // check of the net failed; a check after every check_every steps
+            const int mode = st->att_mode;
+            if (mode == 2) {
+                st->checks++;
+                const float num = __uint_as_float(st->check_num_bits), den = __uint_as_float(st->check_den_bits);
+                st->net_ok = ((double)num <= a.ctl.check_tol * (double)den) ? 1 : 0;
+                if (!st->net_ok) st->check_fails++;
+                st->since_check = 0;
+            }
+            if (!accept && mode == 0) st->fallbacks++;
+            if (accept && mode != 2) st->since_check++;
+            int next = (accept && st->net_ok) ? 0 : 1;
+            if (accept && a.ctl.check_every > 0 && st->since_check >= a.ctl.check_every) next = 2;
+            st->mode_next = next;
+            st->check_num_bits = 0u;
+            st->check_den_bits = 0u;
+        }
         bool done = (st->t >= st->t_end) || (st->accepted >= st->acc_target);
         if (!done && st->run_attempts >= st->attempt_limit) {
             st->status = MMX_ERR_TIMEOUT;

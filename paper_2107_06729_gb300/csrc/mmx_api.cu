@@ -248,6 +248,84 @@ int body_kernels(mmx_ctx *c, cudaStream_t s, int prime, cudaGraphConditionalHand
     return 0;
 }
 
+// One attempt of a context with the learned residual attached, in body
+// `mode`: 0 the net's correction G_ext + Ms r at the extrapolated stages,
+// 1 exact demag at every stage (the fallback), 2 exact demag with the net's
+// correction checked against it at stage 2 (the periodic check).  With s2
+// the body is speculative (it starts at the x-inverse pass and ends with the
+// controller beside the next attempt's x and y-z passes), else whole.
+int res_body(mmx_ctx *c, cudaStream_t s, int mode, cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s2)
+{
+    if (s2)
+        mmxk_demag_parts(c, s, c->st, 1, 1, nullptr, 1, c->G, nullptr, 4);
+    else
+        mmxk_demag(c, s, c->st, 1, 1, nullptr, 1, c->G, nullptr);
+    mmxk_stage(c, s, 0, 0, 0, cond, use_cond);
+    for (int k = 1; k < c->tab.s; ++k) {
+        if (mode == 0) {
+            c->launches += mmxk_rnet_stage(c->rnet, c, s, k);
+        } else {
+            mmxk_demag(c, s, c->st, 0, 0, c->Y[k & 1], 0, c->G, nullptr);
+            if (mode == 2 && k == 1) c->launches += mmxk_rnet_check(c->rnet, c, s, k);
+        }
+        mmxk_stage(c, s, k, 0, 0, cond, use_cond);
+    }
+    if (!s2) {
+        mmxk_control(c, s, 0, cond, use_cond);
+        return 0;
+    }
+    cudaEventRecord(c->ev_fork, s);
+    cudaStreamWaitEvent(s2, c->ev_fork, 0);
+    mmxk_control(c, s, 0, cond, use_cond);
+    mmxk_demag_parts(c, s2, c->st, 0, 2, nullptr, 1, c->G, nullptr, 3);
+    cudaEventRecord(c->ev_join, s2);
+    cudaStreamWaitEvent(s, c->ev_join, 0);
+    return 0;
+}
+
+// The attempt body of a while loop (handle hw) of a context with the
+// learned residual, built into `body`: a gate kernel, then one conditional
+// IF node per body mode (exactly one of which runs), each captured from
+// res_body.
+int build_res_body(mmx_ctx *c, cudaGraph_t body, cudaGraphConditionalHandle hw)
+{
+    cudaGraphConditionalHandle hm[3];
+    for (int i = 0; i < 3; ++i) CK(cudaGraphConditionalHandleCreate(&hm[i], body, 0, 0));
+    CK(cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    mmxk_mode_gate(c, c->cap_stream, hm[0], hm[1], hm[2], 1);
+    cudaError_t e = cudaSuccess;
+    for (int mode = 0; mode < 3 && e == cudaSuccess; ++mode) {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        const cudaGraphEdgeData *ed = nullptr;
+        size_t nd = 0;
+        e = cudaStreamGetCaptureInfo(c->cap_stream, &cs, nullptr, &g, &deps, &ed, &nd);
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hm[mode];
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, deps, ed, nd, &cp);
+        if (e == cudaSuccess)
+            e = cudaStreamUpdateCaptureDependencies(c->cap_stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCaptureToGraph(c->cap_stream3, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            res_body(c, c->cap_stream3, mode, hw, 1, c->cap_stream2);
+            cudaGraph_t sub;
+            e = cudaStreamEndCapture(c->cap_stream3, &sub);
+        }
+    }
+    cudaGraph_t outer;
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &outer);
+    if (e != cudaSuccess) return cuda_fail(c, e, "attempt bodies of the learned residual");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "attempt bodies of the learned residual");
+    return 0;
+}
+
 int kernels_per_attempt(const mmx_ctx *c, int prime)
 {
     const int p = c->ctl.p;
@@ -275,10 +353,15 @@ int build_graph(mmx_ctx *c, int which)
     cudaGraphNode_t node;
     CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    CK(cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    body_kernels(c, c->cap_stream, which == 1 || c->ctl.p < 0, h, 1, c->cap_stream2);
-    cudaGraph_t captured;
-    CK(cudaStreamEndCapture(c->cap_stream, &captured));
+    if (c->rnet && which == 0) {
+        const int rc = build_res_body(c, body, h);
+        if (rc) return rc;
+    } else {
+        CK(cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        body_kernels(c, c->cap_stream, which == 1 || c->ctl.p < 0, h, 1, c->cap_stream2);
+        cudaGraph_t captured;
+        CK(cudaStreamEndCapture(c->cap_stream, &captured));
+    }
     c->launches = launches;
     c->profiling = prof;
     cudaGraphExec_t ex;
@@ -320,9 +403,19 @@ int build_prof_graph(mmx_ctx *c, int which)
 int run_loop(mmx_ctx *c, int which)
 {
     const int prime = (which == 1 || c->ctl.p < 0);
-    if (c->use_graphs && speculative(c, prime)) {
+    if (c->use_graphs && speculative(c, prime) && !(c->rnet && c->profiling)) {
         front_kernels(c, c->stream);
         c->launches += c->nd - 1;
+    }
+    if (c->rnet && which == 0 && (c->profiling || !c->use_graphs)) {
+        // one attempt at a time, the body chosen on the host from the state
+        for (;;) {
+            mmxk_mode_gate(c, c->stream, 0, 0, 0, 0);
+            res_body(c, c->stream, c->h_st->mode_next, 0, 0, nullptr);
+            int rc = read_state(c);
+            if (rc) return rc;
+            if (!c->h_st->loop_more) return 0;
+        }
     }
     if (c->use_graphs && c->profiling) {
         int rc = build_prof_graph(c, which);
@@ -569,6 +662,22 @@ void mmx_prof_end(mmx_ctx *c, cudaStream_t s, int cls)
     c->prof_n[cls]++;
 }
 
+int mmx_state_edit(mmx_ctx *c, const std::function<void(DevState &)> &f)
+{
+    int rc = read_state(c);
+    if (rc) return rc;
+    f(*c->h_st);
+    return write_state(c);
+}
+
+int mmx_state_read(mmx_ctx *c, DevState *out)
+{
+    int rc = read_state(c);
+    if (rc) return rc;
+    *out = *c->h_st;
+    return 0;
+}
+
 void mmx_drop_graphs(mmx_ctx *c)
 {
     for (int i = 0; i < 2; ++i) {
@@ -734,6 +843,8 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     ok = ok && cudaMallocHost((void **)&c->h_st, sizeof(DevState)) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&c->cap_stream3, cudaStreamNonBlocking) == cudaSuccess;
+    c->Gc = nullptr;
     ok = ok && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaEventCreate(&c->ev_a) == cudaSuccess && cudaEventCreate(&c->ev_b) == cudaSuccess;
@@ -777,6 +888,7 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     s.h = integ->h;
     s.t_end = 0;
     s.done = 1;
+    s.net_ok = 1;  // a learned residual, once attached, starts as passing its check
     reset_history(&s);
     if (cudaMemcpy(c->st, c->h_st, sizeof(DevState), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
@@ -1040,6 +1152,8 @@ void mmx_destroy(mmx_ctx *c)
     if (c->h_st) cudaFreeHost(c->h_st);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
+    if (c->cap_stream3) cudaStreamDestroy(c->cap_stream3);
+    if (c->Gc) cudaFree(c->Gc);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_a) cudaEventDestroy(c->ev_a);
@@ -1122,13 +1236,17 @@ int build_batch_graph(mmx_batch *b)
                 cp.conditional.size = 1;
                 e = cudaGraphAddNode(&node, g, &gate, nullptr, 1, &cp);
             }
-            if (e == cudaSuccess)
-                e = cudaStreamBeginCaptureToGraph(c->cap_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                                  cudaStreamCaptureModeRelaxed);
-            if (e == cudaSuccess) {
-                body_kernels(c, c->cap_stream, which == 1 || c->ctl.p < 0, h, 1, c->cap_stream2);
-                cudaGraph_t captured;
-                e = cudaStreamEndCapture(c->cap_stream, &captured);
+            if (e == cudaSuccess && c->rnet && which == 0) {
+                if (build_res_body(c, cp.conditional.phGraph_out[0], h)) e = cudaErrorUnknown;
+            } else {
+                if (e == cudaSuccess)
+                    e = cudaStreamBeginCaptureToGraph(c->cap_stream, cp.conditional.phGraph_out[0], nullptr, nullptr,
+                                                      0, cudaStreamCaptureModeRelaxed);
+                if (e == cudaSuccess) {
+                    body_kernels(c, c->cap_stream, which == 1 || c->ctl.p < 0, h, 1, c->cap_stream2);
+                    cudaGraph_t captured;
+                    e = cudaStreamEndCapture(c->cap_stream, &captured);
+                }
             }
             if (e != cudaSuccess) {
                 c->launches = launches;

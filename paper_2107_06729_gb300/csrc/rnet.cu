@@ -701,11 +701,11 @@ __global__ void k_rnet_cast_tc_t(const float *__restrict__ P, __nv_bfloat16 *__r
 // kernel's) into G, and the net's packed input (Y_k, G_ext / Ms)
 __global__ void k_res_stage_in(DevState *st, int k, int np1, const float *__restrict__ hist,
                                const float *__restrict__ Y, long long n, float inv_Ms, float *__restrict__ G,
-                               __nv_bfloat16 *__restrict__ a0)
+                               __nv_bfloat16 *__restrict__ a0, int count)
 {
     if (st->done) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
+    if (count && blockIdx.x == 0 && threadIdx.x == 0) st->extrap_evals++;
     if (i >= n) return;
     const float *wf = st->coef[k].wf;
     float g[3] = {0.0f, 0.0f, 0.0f};
@@ -736,6 +736,32 @@ __global__ void k_res_stage_out(const DevState *st, const float *__restrict__ r,
     if (st->done) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n3) G[i] += Ms * r[i];
+}
+
+// periodic check: the net-corrected field Gc + Ms r against the exact field
+// G of the same stage; the maxima of |difference| and |G| into the state
+// (non-negative FP32 values compare as their bit patterns)
+__global__ void k_res_check_cmp(DevState *st, const float *__restrict__ r, const float *__restrict__ Gc,
+                                const float *__restrict__ G, long long n3, float Ms)
+{
+    __shared__ unsigned int s_num, s_den;
+    if (threadIdx.x == 0) {
+        s_num = 0u;
+        s_den = 0u;
+    }
+    __syncthreads();
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n3) {
+        const float g = G[i];
+        const float d = fabsf(Gc[i] + Ms * r[i] - g);
+        atomicMax(&s_num, __float_as_uint(d == d ? d : INFINITY));
+        atomicMax(&s_den, __float_as_uint(fabsf(g)));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicMax(&st->check_num_bits, s_num);
+        atomicMax(&st->check_den_bits, s_den);
+    }
 }
 
 // training pairs: xg (T, [3][cells]) = sum_j w_j G_j
@@ -1243,10 +1269,31 @@ int mmxk_rnet_stage(mmx_rnet *net, mmx_ctx *c, cudaStream_t s, int k)
     net->fault = &c->st->fault;
     k_res_stage_in<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->st, k, c->ctl.p + 1, (const float *)c->hist,
                                                              (const float *)c->Y[k & 1], n, (float)(1.0 / c->mat.Ms),
-                                                             (float *)c->G, net->a[0]);
+                                                             (float *)c->G, net->a[0], 1);
     forward_layers(net, c->nx, c->ny, c->nz);
     k_res_stage_out<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(c->st, net->r, 3 * n, (float)c->mat.Ms,
                                                                   (float *)c->G);
+    net->s = keep;
+    net->fault = keep_fault;
+    net->nx = c->nx;
+    net->ny = c->ny;
+    net->nz = c->nz;
+    return 6;
+}
+
+int mmxk_rnet_check(mmx_rnet *net, mmx_ctx *c, cudaStream_t s, int k)
+{
+    const long long n = c->n;
+    cudaStream_t keep = net->s;
+    int *keep_fault = net->fault;
+    net->s = s;
+    net->fault = &c->st->fault;
+    k_res_stage_in<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->st, k, c->ctl.p + 1, (const float *)c->hist,
+                                                             (const float *)c->Y[k & 1], n, (float)(1.0 / c->mat.Ms),
+                                                             (float *)c->Gc, net->a[0], 0);
+    forward_layers(net, c->nx, c->ny, c->nz);
+    k_res_check_cmp<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(c->st, net->r, (const float *)c->Gc,
+                                                                  (const float *)c->G, 3 * n, (float)c->mat.Ms);
     net->s = keep;
     net->fault = keep_fault;
     net->nx = c->nx;
@@ -1277,8 +1324,55 @@ extern "C" int mmx_set_residual(mmx_ctx *c, mmx_rnet *net)
         c->err = std::string("mmx_set_residual: ") + cudaGetErrorString(e);
         return MMX_ERR_CUDA;
     }
+    if (net && !c->Gc && cudaMalloc(&c->Gc, (size_t)3 * c->n * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        c->Gc = nullptr;
+        c->err = "mmx_set_residual: device allocation failed";
+        return MMX_ERR_OOM;
+    }
     // the captured attempt graphs hold the old stage sequence
     mmx_drop_graphs(c);
     c->rnet = net;
+    c->ctl.has_net = net ? 1 : 0;
+    // the next attempt uses the net; the periodic check starts afresh
+    if (int rc = mmx_state_edit(c, [](DevState &st) {
+            st.mode_next = 0;
+            st.att_mode = 0;
+            st.since_check = 0;
+            st.net_ok = 1;
+            st.check_num_bits = 0u;
+            st.check_den_bits = 0u;
+        }))
+        return rc;
+    return MMX_OK;
+}
+
+extern "C" int mmx_set_residual_check(mmx_ctx *c, int every, double tol)
+{
+    if (!c) return MMX_ERR_ARG;
+    if (every < 0 || !(tol >= 0) || !std::isfinite(tol)) {
+        c->err = "mmx_set_residual_check: need every >= 0 and a finite tol >= 0";
+        return MMX_ERR_ARG;
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("mmx_set_residual_check: ") + cudaGetErrorString(e);
+        return MMX_ERR_CUDA;
+    }
+    mmx_drop_graphs(c);
+    c->ctl.check_every = every;
+    c->ctl.check_tol = tol;
+    return MMX_OK;
+}
+
+extern "C" int mmx_residual_stats(mmx_ctx *c, long long *out4)
+{
+    if (!c || !out4) return MMX_ERR_ARG;
+    DevState st;
+    if (int rc = mmx_state_read(c, &st)) return rc;
+    out4[0] = st.fallbacks;
+    out4[1] = st.checks;
+    out4[2] = st.check_fails;
+    out4[3] = st.net_ok;
     return MMX_OK;
 }
