@@ -155,13 +155,15 @@ def byte_model(cfg, esz):
     return model
 
 
-def demag_pass_bytes(n_xyz, esz, split):
+def demag_pass_bytes(n_xyz, esz, split, self_term=False):
     """Algorithmic bytes of one exact demag evaluation (the pass model):
     XF reads m (3 r/cell) and writes the packed half spectrum (3 c/cell,
     c = 2r); the fused YZ pass reads and writes that spectrum once and reads
     the tensor octant; the split path instead writes the y spectrum (Py/ny
     times larger), reads and rewrites it with the tensor in ZM, and reads it
-    back in YI; XI reads the spectrum and writes the field."""
+    back in YI; XI reads the spectrum and writes the field, and when it
+    returns the full field (self_term) it also reads m again for the
+    -Ms N(0) m term."""
     nx, ny, nz = n_xyz
     n = nx * ny * nz
     Py = 2 * ny if ny > 1 else 1
@@ -169,7 +171,7 @@ def demag_pass_bytes(n_xyz, esz, split):
     c = 2 * esz
     kbytes = (nx + 1) * (Py // 2 + 1) * (Pz // 2 + 1) * 6 * esz
     xf = 3 * n * esz + 3 * n * c
-    xi = 3 * n * c + 3 * n * esz
+    xi = 3 * n * c + 3 * n * esz + (3 * n * esz if self_term else 0)
     if not split:
         return {"x_forward_fft": xf, "yz_fft_tensor_multiply": 2 * 3 * n * c + kbytes, "x_inverse_fft": xi}
     rowsy = 3 * nx * nz * Py  # complex words of the y spectrum
@@ -203,7 +205,8 @@ def large3d_demag(pkg, torch, dev, iters=20):
         prof = ctx.profile()
         ctx.set_profiling(False)
     ctx.close()
-    model = demag_pass_bytes(cfg["mesh"]["n"], 4, split=True)
+    # mmx_demag returns the full field: XI subtracts the self term, reading m
+    model = demag_pass_bytes(cfg["mesh"]["n"], 4, split=True, self_term=True)
     total = sum(model.values())
     peak, src = peaks()
     per_kernel = {}

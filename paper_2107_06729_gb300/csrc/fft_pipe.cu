@@ -9,6 +9,10 @@ const void *mmxk_tab_pipe(int kind, bool f64, int L)
     case K_YIP: return f64 ? yip_fn<double>(L) : yip_fn<float>(L);
     case K_ZMP: return f64 ? zmp_fn<double>(L) : zmp_fn<float>(L);
     case K_XIT: return f64 ? nullptr : xit_fn<float>(L);
+    case K_YF4: return f64 || L != 1024 ? nullptr : (const void *)k_yf4<float>;
+    case K_YI4: return f64 || L != 1024 ? nullptr : (const void *)k_yi4<float>;
+    case K_XF4: return f64 || L != 1024 ? nullptr : (const void *)k_xf4<float>;
+    case K_XI4: return f64 || L != 1024 ? nullptr : (const void *)k_xi_t<float, 1024, true>;
     }
     return nullptr;
 }

@@ -135,6 +135,9 @@ struct mmx_ctx {
     void *mlo;   // FP32: low words of the compensated state of m[0] and m[1] ([2][3][n]); null in FP64
     void *errpart;  // largest error norm of each CTA of the last stage
     void *Tb;    // split y/z path: y spectrum [kx][c nz + z][Py] (complex)
+    void *tw4 = nullptr;  // FP32 split path with a 1024-point axis: four-step twiddles [k2][n1] = w1024^(n1 k2)
+    bool r4 = false;      // the 1024-point y passes run as four-step register transforms
+    bool r4x = false;     // ... and the 1024-point x passes
     bool split;  // the y-z column does not fit one CTA: YF, ZM, YI instead of YZ
     bool cluster;     // ... and a thread-block cluster per kx column runs it instead (YZC)
     int yzc_C, yzc_W; // cluster size and z sub-tile width of YZC

@@ -44,7 +44,7 @@
 #include "internal.h"
 
 // kernel families, instantiated in separate translation units
-enum MmxKernelKind { K_XF, K_XI, K_YZ, K_YF, K_YI, K_ZM, K_XFP, K_YFP, K_YIP, K_ZMP, K_ZMR, K_XIT };
+enum MmxKernelKind { K_XF, K_XI, K_YZ, K_YF, K_YI, K_ZM, K_XFP, K_YFP, K_YIP, K_ZMP, K_ZMR, K_XIT, K_YF4, K_YI4, K_XF4, K_XI4 };
 // pointer to the instance of `kind` for precision (f64) and transform length L
 const void *mmxk_kernel(int kind, bool f64, int L);
 // the cluster-fused y-z pass (FP32) for lengths Py and Pz, or NULL
@@ -232,6 +232,78 @@ template <typename T, bool INV> struct Dft<T, 16, INV> {
         }
     }
 };
+
+// 32 points: DFT-16 of the even and of the odd samples, joined by the 32nd
+// roots of unity w^k = exp(-+2 pi i k / 32), k = 0..15 (cos(k pi / 16) and
+// sin(k pi / 16) from the nine values cos(j pi / 16), j = 0..8)
+template <typename T, bool INV> __device__ __forceinline__ cx<T> w32(int k)
+{
+    const T c[9] = {(T)1.0,
+                    (T)0.98078528040323044912618223613424,
+                    (T)0.92387953251128675612818318939679,
+                    (T)0.83146961230254523707878837761791,
+                    (T)0.70710678118654752440084436210485,
+                    (T)0.55557023301960222474283081394853,
+                    (T)0.38268343236508977172845998403040,
+                    (T)0.19509032201612826784828486847702,
+                    (T)0.0};
+    const T cr = k <= 8 ? c[k] : -c[16 - k];
+    const T sr = k <= 8 ? c[8 - k] : c[k - 8];
+    return mk(cr, INV ? sr : -sr);
+}
+template <typename T, bool INV> struct Dft<T, 32, INV> {
+    static __device__ __forceinline__ void run(cx<T> *v)
+    {
+        cx<T> e[16], o[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            e[k] = v[2 * k];
+            o[k] = v[2 * k + 1];
+        }
+        Dft<T, 16, INV>::run(e);
+        Dft<T, 16, INV>::run(o);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const cx<T> t = (k == 0) ? o[0] : cmul(o[k], w32<T, INV>(k));
+            v[k] = cadd(e[k], t);
+            v[k + 16] = csub(e[k], t);
+        }
+    }
+};
+// 32-point DFT of a sequence whose upper 16 samples are zero (v[16..31] are
+// not read): even outputs are the DFT-16 of the samples, odd outputs the
+// DFT-16 of the samples times w^n (decimation in frequency)
+template <typename T, bool INV> __device__ __forceinline__ void dft32_in16(cx<T> *v)
+{
+    cx<T> a[16], b[16];
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+        a[n] = v[n];
+        b[n] = n == 0 ? v[0] : cmul(v[n], w32<T, INV>(n));
+    }
+    Dft<T, 16, INV>::run(a);
+    Dft<T, 16, INV>::run(b);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        v[2 * j] = a[j];
+        v[2 * j + 1] = b[j];
+    }
+}
+// the lower 16 outputs of a 32-point DFT (v[16..31] are left undefined):
+// DFT-16 of the even and of the odd samples joined without the upper half
+template <typename T, bool INV> __device__ __forceinline__ void dft32_out16(cx<T> *v)
+{
+    cx<T> e[16], o[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        e[k] = v[2 * k];
+        o[k] = v[2 * k + 1];
+    }
+    Dft<T, 16, INV>::run(e);
+    Dft<T, 16, INV>::run(o);
+#pragma unroll
+    for (int n = 0; n < 16; ++n) v[n] = cadd(e[n], n == 0 ? o[0] : cmul(o[n], w32<T, INV>(n)));
+}
 
 // A batch of `count` transforms of length L held in shared memory; transform
 // tr starts at (tr >> lg_lo) * s_hi + (tr & (2^lg_lo - 1)) * s_lo and its
@@ -518,6 +590,7 @@ template <typename T> struct XArgs {
     const T *self_src;   // optional: subtract Ms N00 self_src
     cx<T> *S;
     const cx<T> *tw;
+    const cx<T> *tw4;    // four-step twiddles of 1024 points, [k2][n1] = w1024^(n1 k2)
     DevState *st;
     long long rows, n;
     int nx, trows, stage0, src_mode, dst_mode, plane;  // plane = ny*nz
@@ -783,10 +856,45 @@ struct BulkStage {
     }
 };
 
+// ---- four-step register transforms of 1024 points (FP32 passes of the
+// large meshes).  1024 = 32 x 32: lane n1 of a warp holds x[n1 + 32 n2] in
+// register n2 and transforms over n2; a multiply by w1024^(n1 k2) and one
+// transpose through a 32 x 33 shared tile hand lane k2 the values of every
+// n1, which it transforms again: X[k2 + 32 k1] ends in register k1.  Per
+// point that is one shared-memory store and one load (the Stockham stages
+// in shared memory take three of each), and the global loads and stores are
+// direct and lane-consecutive.  One warp per row, no CTA barrier.
+constexpr int R4_WARPS = 4;   // rows per CTA (one per warp)
+constexpr int R4_PITCH = 33;  // transpose tile pitch (complex words): conflict-free rows and columns
+constexpr size_t r4_smem() { return (size_t)R4_WARPS * 32 * R4_PITCH * sizeof(cx<float>); }
+
+// v[k2] *= w1024^(+-lane k2) from the [k2][n1] table (lane-consecutive reads)
+template <typename T, bool INV> __device__ __forceinline__ void r4_twiddle(cx<T> *v, const cx<T> *__restrict__ tw4)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 1; k < 32; ++k) {
+        cx<T> w = tw4[32 * k + lane];
+        if (INV) w.y = -w.y;
+        v[k] = cmul(v[k], w);
+    }
+}
+// register k of lane l -> register l of lane k
+template <typename T> __device__ __forceinline__ void r4_transpose(cx<T> *v, cx<T> *tile)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) tile[k * R4_PITCH + lane] = v[k];
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = tile[lane * R4_PITCH + k];
+    __syncwarp();
+}
+
 constexpr int XIT_ROWS = 8;  // rows per tile: four pair rows, one warp each
 constexpr unsigned long long XIT_WAIT_NS = 2000000000ULL;  // 2 s
 
-template <typename T, int PX>
+template <typename T, int PX, bool R4 = false>
 __global__ void __launch_bounds__(32 * XIT_ROWS / 2, 3) k_xi_t(const XArgs<T> a, const __grid_constant__ CUtensorMap tm)
 {
     pdl_entry();
@@ -863,10 +971,49 @@ __global__ void __launch_bounds__(32 * XIT_ROWS / 2, 3) k_xi_t(const XArgs<T> a,
             pend = true;
         }
         const int w = threadIdx.x >> 5;
-        if (w < NP) WarpFFT<T, true, PX, 1>::run(work.at(w * PXS), 1, a.tw, false, true);
-        __syncthreads();
-        xi_store<T, PXS>(work, a, out, (long long)tile * TR, TR, R);
-        __syncthreads();  // work is refilled by the next tile
+        if constexpr (R4) {
+            // four-step 1024-point inverse on pair row w, stored straight from
+            // registers: lane n1 ends with x[n1 + 32 n2], n2 < 16, of both rows
+            static_assert(PX == 1024 && sizeof(T) == 4, "four-step XI: FP32, 1024 points");
+            if (w < NP) {
+                const int lane = threadIdx.x & 31;
+                const Pad<T> z = work.at(w * PXS);
+                cx<T> v[32];
+#pragma unroll
+                for (int k = 0; k < 32; ++k) v[k] = z[lane + 32 * k];
+                Dft<T, 32, true>::run(v);
+                r4_twiddle<T, true>(v, a.tw4);
+                // the row's own padded words hold the 32 x 33 transpose tile
+                const int b0 = w * PXS;
+                r4_transpose(v, work.p + b0 + (b0 >> 4));
+                dft32_out16<T, true>(v);
+                const long long ra = (long long)tile * TR + 2 * w;
+                const int lgpl = ilog2(a.plane);
+                const T msa = (T)a.msN00[(int)(ra >> lgpl)], msb = (T)a.msN00[(int)((ra + 1) >> lgpl)];
+                T *oa = out + ra * NX, *ob = oa + NX;
+                if (a.self_src) {
+                    const T *sa = a.self_src + ra * NX, *sb = sa + NX;
+#pragma unroll
+                    for (int n = 0; n < 16; ++n) {
+                        const int x = lane + 32 * n;
+                        oa[x] = v[n].x - msa * __ldg(sa + x);
+                        ob[x] = v[n].y - msb * __ldg(sb + x);
+                    }
+                } else {
+#pragma unroll
+                    for (int n = 0; n < 16; ++n) {
+                        oa[lane + 32 * n] = v[n].x;
+                        ob[lane + 32 * n] = v[n].y;
+                    }
+                }
+            }
+            __syncthreads();  // work is refilled by the next tile
+        } else {
+            if (w < NP) WarpFFT<T, true, PX, 1>::run(work.at(w * PXS), 1, a.tw, false, true);
+            __syncthreads();
+            xi_store<T, PXS>(work, a, out, (long long)tile * TR, TR, R);
+            __syncthreads();  // work is refilled by the next tile
+        }
     }
     if (failed) {
         if (threadIdx.x == 0 && a.fault) atomicExch(a.fault, 1);
@@ -887,22 +1034,23 @@ template <typename T> struct YZArgs {
     int nx, ny, nz, Py, Pz, Hy, Hz, stage0;
 };
 
+// The tensor octant is stored component-major, K[kx][z][comp][y] (comp:
+// xx, yy, zz, xy, xz, yz), so that a warp reading 32 consecutive ky of one
+// component reads 128 contiguous bytes.  Records beyond Py/2 (Pz/2) are the
+// mirrored ones: odd in ky for xy and yz, odd in kz for xz and yz.
 template <typename T>
 __device__ __forceinline__ void load_K(const T *K, int kx, int Hy, int Hz, int Py, int Pz, int ky, int kz, T k6[6])
 {
     const bool fy = ky > (Py >> 1), fz = kz > (Pz >> 1);
     const int y = fy ? Py - ky : ky, z = fz ? Pz - kz : kz;
-    // one 6-component record as three aligned pairs through the read-only path
-    using V2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
-    const V2 *q = reinterpret_cast<const V2 *>(K + ((size_t)((size_t)kx * Hz + z) * Hy + y) * 6);
-    const V2 p0 = __ldg(q), p1 = __ldg(q + 1), p2 = __ldg(q + 2);
+    const T *q = K + (size_t)((size_t)kx * Hz + z) * 6 * Hy + y;
     const T sy = fy ? (T)-1 : (T)1, sz = fz ? (T)-1 : (T)1;
-    k6[0] = (T)p0.x;
-    k6[1] = (T)p0.y;
-    k6[2] = (T)p1.x;
-    k6[3] = sy * (T)p1.y;
-    k6[4] = sz * (T)p2.x;
-    k6[5] = sy * sz * (T)p2.y;
+    k6[0] = __ldg(q);
+    k6[1] = __ldg(q + Hy);
+    k6[2] = __ldg(q + 2 * Hy);
+    k6[3] = sy * __ldg(q + 3 * Hy);
+    k6[4] = sz * __ldg(q + 4 * Hy);
+    k6[5] = sy * sz * __ldg(q + 5 * Hy);
 }
 
 template <typename T>
@@ -1040,6 +1188,7 @@ template <typename T> struct SplitArgs {
     cx<T> *Tb;     // [kx][c*nz + z][ky]
     const T *K;
     const cx<T> *twy, *twz;
+    const cx<T> *tw4;  // four-step twiddles of 1024 points, [k2][n1] = w1024^(n1 k2)
     DevState *st;
     long long rows;  // 3 ny nz
     int nx, ny, nz, Py, Pz, Hy, Hz, stage0, ry, W;
@@ -1252,6 +1401,14 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
@@ -1445,6 +1602,171 @@ __global__ void __launch_bounds__(256, 2) k_yi_p(const SplitArgs<T> a)
     }
 }
 
+// YF of a 1024-point y axis: row (kx, c nz + z) of S (ny = 512 samples) to
+// the row of Tb (1024 ky); the packed kx = 0 column is separated as in k_yf_p
+template <typename T>
+__global__ void __launch_bounds__(32 * R4_WARPS, 4) k_yf4(const SplitArgs<T> a)
+{
+    pdl_entry();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    if (a.st) {
+        if (a.st->done) return;
+        if (a.stage0 && a.st->f1_valid) return;
+    }
+    constexpr int PY = 1024, NY = 512, half = PY / 2;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    cx<T> *tile = reinterpret_cast<cx<T> *>(smraw) + w * 32 * R4_PITCH;
+    const int nrows = 3 * a.nz;
+    const long long row = (long long)blockIdx.x * R4_WARPS + w;
+    if (row >= (long long)a.nx * nrows) return;
+    const int kx = (int)(row / nrows), r = (int)(row - (long long)kx * nrows);
+    const cx<T> *src = a.S + (size_t)kx * a.rows + (size_t)r * NY;
+    cx<T> *dst = a.Tb + ((size_t)kx * nrows + r) * PY;
+    cx<T> v[32];
+#pragma unroll
+    for (int n = 0; n < 16; ++n) v[n] = src[lane + 32 * n];
+    dft32_in16<T, false>(v);
+    r4_twiddle<T, false>(v, a.tw4);
+    r4_transpose(v, tile);
+    Dft<T, 32, false>::run(v);
+    if (kx != 0) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) dst[lane + 32 * k] = v[k];
+        return;
+    }
+    // packed kx = 0 column: the spectra of the two real x-spectra, A in the
+    // slots below PY/2 and B above, from U(q) and U(PY - q)
+#pragma unroll
+    for (int k = 0; k < 32; ++k) tile[k * R4_PITCH + lane] = v[k];
+    __syncwarp();
+    auto U = [&](int q) { return tile[(q >> 5) * R4_PITCH + (q & 31)]; };
+    for (int k = 0; k < 32; ++k) {
+        const int q = lane + 32 * k;
+        cx<T> o;
+        if (q == 0 || q == half) {
+            o = U(q);
+        } else if (q < half) {
+            const cx<T> z = U(q), zm = U(PY - q);
+            o = mk((T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y));
+        } else {
+            const cx<T> z = U(PY - q), zm = U(q);
+            o = mk((T)0.5 * (z.y + zm.y), (T)0.5 * (zm.x - z.x));
+        }
+        dst[q] = o;
+    }
+}
+
+// YI of a 1024-point y axis: row of Tb (1024 ky) to the row of S (the first
+// ny = 512 samples); the packed kx = 0 column is recombined as in k_yi_p
+template <typename T>
+__global__ void __launch_bounds__(32 * R4_WARPS, 4) k_yi4(const SplitArgs<T> a)
+{
+    pdl_entry();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    if (a.st) {
+        if (a.st->done) return;
+        if (a.stage0 && a.st->f1_valid) return;
+    }
+    constexpr int PY = 1024, NY = 512;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    cx<T> *tile = reinterpret_cast<cx<T> *>(smraw) + w * 32 * R4_PITCH;
+    const int nrows = 3 * a.nz;
+    const long long row = (long long)blockIdx.x * R4_WARPS + w;
+    if (row >= (long long)a.nx * nrows) return;
+    const int kx = (int)(row / nrows), r = (int)(row - (long long)kx * nrows);
+    const cx<T> *src = a.Tb + ((size_t)kx * nrows + r) * PY;
+    cx<T> *dst = a.S + (size_t)kx * a.rows + (size_t)r * NY;
+    cx<T> v[32];
+    if (kx != 0) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = src[lane + 32 * k];
+    } else {
+        const YIView<T> u{src, PY};
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = u[lane + 32 * k];
+    }
+    // lane k1 holds X[k1 + 32 k2] in register k2
+    Dft<T, 32, true>::run(v);
+    r4_twiddle<T, true>(v, a.tw4);
+    r4_transpose(v, tile);
+    dft32_out16<T, true>(v);
+#pragma unroll
+    for (int n = 0; n < 16; ++n) dst[lane + 32 * n] = v[n];
+}
+
+// XF of a 1024-point x axis (nx = 512), persistent: items of 16 rows (eight
+// pair rows, one warp each) arrive by one bulk copy into a staging buffer,
+// whose next copy starts as soon as the warps hold their rows in registers,
+// so it overlaps the transforms and the stores.  The pair's two real rows
+// are the real and imaginary parts of one 1024-point transform (four-step,
+// in registers); the spectra, in natural order in each warp's tile, are split
+// into the two rows' half spectra and stored transposed, S[kx][row], 16
+// consecutive rows per kx (128-byte segments).  Tiles are 1058 words apart
+// (2 mod 16): the 16 rows of one kx, and of kx + 1, fall in distinct banks.
+constexpr int XF4_ROWS = 16;
+constexpr int XF4_TS = 1058;
+constexpr size_t xf4_smem()
+{
+    return (size_t)(XF4_ROWS / 2) * XF4_TS * sizeof(cx<float>) + (size_t)XF4_ROWS * 512 * sizeof(float) + 16;
+}
+template <typename T>
+__global__ void __launch_bounds__(32 * XF4_ROWS / 2, 2) k_xf4(const XArgs<T> a)
+{
+    pdl_entry();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    if (a.st) {
+        if (a.st->done) return;
+        if (a.stage0 && a.st->f1_valid) return;
+    }
+    constexpr int PX = 1024, NX = 512, TR = XF4_ROWS;
+    constexpr unsigned BYTES = (unsigned)TR * NX * sizeof(T);
+    const T *src = a.src_mode == 0 ? a.src : ((a.src_mode == 1 ? a.st->cur : a.st->spec_src) ? a.msrc1 : a.msrc0);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    cx<T> *const tiles = reinterpret_cast<cx<T> *>(smraw);
+    cx<T> *tile = tiles + w * XF4_TS;
+    T *stg = reinterpret_cast<T *>(tiles + (TR / 2) * XF4_TS);
+    BulkStage bs;
+    bs.init(reinterpret_cast<uint64_t *>(stg + TR * NX));
+    const long long R = a.rows;
+    const int nitems = (int)(R / TR);  // rows % 16 == 0
+    int item = blockIdx.x;
+    if (item < nitems) bs.issue(stg, src + (size_t)item * TR * NX, BYTES);
+    for (; item < nitems; item += gridDim.x) {
+        if (!bs.wait(a.fault, XIT_WAIT_NS)) return;
+        const T *ra = stg + (size_t)(2 * w) * NX, *rb = ra + NX;
+        cx<T> v[32];
+#pragma unroll
+        for (int n = 0; n < 16; ++n) v[n] = mk(ra[lane + 32 * n], rb[lane + 32 * n]);
+        __syncthreads();  // staging consumed: the next item's copy overlaps the rest
+        const int next = item + (int)gridDim.x;
+        if (next < nitems) bs.issue(stg, src + (size_t)next * TR * NX, BYTES);
+        dft32_in16<T, false>(v);
+        r4_twiddle<T, false>(v, a.tw4);
+        r4_transpose(v, tile);
+        Dft<T, 32, false>::run(v);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) tile[k * R4_PITCH + lane] = v[k];
+        __syncthreads();
+        const long long r0 = (long long)item * TR;
+        for (int idx = threadIdx.x; idx < NX * TR; idx += blockDim.x) {
+            const int k = idx >> 4, t = idx & (TR - 1);
+            const cx<T> *z = tiles + (t >> 1) * XF4_TS;
+            auto Z = [&](int q) { return z[(q >> 5) * R4_PITCH + (q & 31)]; };
+            cx<T> o;
+            if (k == 0) {
+                const cx<T> z0 = Z(0), zn = Z(NX);
+                o = (t & 1) ? mk(z0.y, zn.y) : mk(z0.x, zn.x);
+            } else {
+                const cx<T> zk = Z(k), zm = Z(PX - k);
+                const T hlf = (T)0.5;
+                o = (t & 1) ? mk(hlf * (zk.y + zm.y), hlf * (zm.x - zk.x)) : mk(hlf * (zk.x + zm.x), hlf * (zk.y - zm.y));
+            }
+            a.S[(long long)k * R + r0 + t] = o;
+        }
+        __syncthreads();  // the tiles are refilled by the next item
+    }
+}
+
 template <typename T, int PZ>
 __global__ void __launch_bounds__(YZ_THREADS, 2) k_zm_p(const SplitArgs<T> a)
 {
@@ -1546,7 +1868,14 @@ __global__ void __launch_bounds__(YZ_THREADS, 2) k_zm_p(const SplitArgs<T> a)
 // its z column straight from global memory (a warp reads 32 consecutive ky:
 // coalesced), transforms it in registers, and exchanges with the other two
 // components only through a [c][kz][w] tile for the tensor multiply
-// (consecutive threads touch consecutive words: no bank conflicts).
+// (consecutive threads touch consecutive words: no bank conflicts).  In the
+// multiply, thread (j, w) takes the points kz = j, j + 3, ... of its own ky,
+// so the tensor row address is computed once per thread; the tensor is read
+// component-major (one 128-byte line per warp and component).  ky tiles of
+// one kx column are adjacent in launch order, so the tensor records shared by
+// ky and Py - ky (and the column's rows) are read from L2 by the second tile
+// instead of DRAM.  The 32-point z transforms (the box's) take the pruned
+// constant-twiddle forms: 16 inputs in, 16 outputs back.
 template <typename T, int PZ>
 __global__ void __launch_bounds__(192, 4) k_zm_r(const SplitArgs<T> a)
 {
@@ -1560,40 +1889,56 @@ __global__ void __launch_bounds__(192, 4) k_zm_r(const SplitArgs<T> a)
     const int W = a.W, Py = a.Py, nz = a.nz, Pz = PZ;
     const int lgW = ilog2(W);
     const int nrows = 3 * nz, plane = PZ * W;
-    // ky tiles of one kx column are adjacent in launch order, so the tensor
-    // records shared by ky and Py - ky (and the column's rows) are read from
-    // L2 by the second tile instead of DRAM
     const int kx = blockIdx.y, ky0 = blockIdx.x * W;
     const int c = threadIdx.x >> lgW, w = threadIdx.x & (W - 1);
     cx<T> *g = a.Tb + ((size_t)kx * nrows + (size_t)c * nz) * Py + ky0 + w;
     cx<T> v[PZ];
+    constexpr bool R32 = PZ == 32;
 #pragma unroll
     for (int z = 0; z < PZ; ++z) v[z] = z < PZ / 2 ? g[(size_t)z * Py] : mk<T>(0, 0);  // Pz = 2 nz
-    RegFFT<T, PZ, 1, false>::run(v, a.twz);
+    if constexpr (R32)
+        dft32_in16<T, false>(v);
+    else
+        RegFFT<T, PZ, 1, false>::run(v, a.twz);
 #pragma unroll
     for (int kz = 0; kz < PZ; ++kz) B[c * plane + kz * W + w] = v[kz];
     __syncthreads();
-    const int half = Py >> 1;
+    const int half = Py >> 1, slot = ky0 + w;
+    if (kx != 0 || (slot != 0 && slot != half)) {
+        // the packed kx = 0 column holds kx = 0 below Py/2 and kx = nx above
+        const int kxe = kx != 0 ? kx : (slot < half ? 0 : a.nx);
+        const int ys = (kx != 0 || slot < half) ? slot : Py - slot;
+        const bool fy = ys > half;
+        const T sy = fy ? (T)-1 : (T)1;
+        const int Hy = a.Hy;
+        const T *kb = a.K + (size_t)kxe * a.Hz * 6 * Hy + (fy ? Py - ys : ys);
 #pragma unroll 4
-    for (int q = threadIdx.x; q < plane; q += blockDim.x) {
-        const int ww = q & (W - 1), kz = q >> lgW, slot = ky0 + ww;
-        if (kx != 0 || (slot != 0 && slot != half)) {
+        for (int kz = c; kz < PZ; kz += 3) {
+            const bool fz = kz > (PZ >> 1);
+            const T sz = fz ? (T)-1 : (T)1;
+            const T *kr = kb + (size_t)(fz ? PZ - kz : kz) * 6 * Hy;
             T k6[6];
-            if (kx != 0)
-                load_K(a.K, kx, a.Hy, a.Hz, Py, Pz, slot, kz, k6);
-            else if (slot < half)
-                load_K(a.K, 0, a.Hy, a.Hz, Py, Pz, slot, kz, k6);
-            else
-                load_K(a.K, a.nx, a.Hy, a.Hz, Py, Pz, Py - slot, kz, k6);
+            k6[0] = __ldg(kr);
+            k6[1] = __ldg(kr + Hy);
+            k6[2] = __ldg(kr + 2 * Hy);
+            k6[3] = sy * __ldg(kr + 3 * Hy);
+            k6[4] = sz * __ldg(kr + 4 * Hy);
+            k6[5] = sy * sz * __ldg(kr + 5 * Hy);
+            const int q = kz * W + w;
             cx<T> hx, hy, hz;
             apply_K(k6, B[q], B[plane + q], B[2 * plane + q], hx, hy, hz);
             B[q] = hx;
             B[plane + q] = hy;
             B[2 * plane + q] = hz;
-        } else {
+        }
+    } else {
+        // slots 0 and Py/2 of the packed column: each holds A + i B of the
+        // kx = 0 and kx = nx spectra; the pair (kz, Pz - kz) is taken by the
+        // thread of the smaller kz through P = (K0 + Kn) / 2, Q = (K0 - Kn) / 2
+        for (int kz = c; kz < PZ; kz += 3) {
             const int kzm = (Pz - kz) & (Pz - 1);
             if (kz > kzm) continue;
-            const int qm = kzm * W + ww;
+            const int q = kz * W + w, qm = kzm * W + w;
             T k0[6], kn[6], P[6], Q[6];
             load_K(a.K, 0, a.Hy, a.Hz, Py, Pz, slot, kz, k0);
             load_K(a.K, a.nx, a.Hy, a.Hz, Py, Pz, slot, kz, kn);
@@ -1622,7 +1967,10 @@ __global__ void __launch_bounds__(192, 4) k_zm_r(const SplitArgs<T> a)
     __syncthreads();
 #pragma unroll
     for (int kz = 0; kz < PZ; ++kz) v[kz] = B[c * plane + kz * W + w];
-    RegFFT<T, PZ, 1, true>::run(v, a.twz);
+    if constexpr (R32)
+        dft32_out16<T, true>(v);
+    else
+        RegFFT<T, PZ, 1, true>::run(v, a.twz);
 #pragma unroll
     for (int z = 0; z < PZ; ++z)
         if (z < PZ / 2) g[(size_t)z * Py] = v[z];
@@ -2552,6 +2900,8 @@ template <typename T> const void *zmp_fn(int L)
 // register-column ZM: ky tile of W values (3 W threads, at most 192) and
 // the longest z transform it holds in registers
 int zmr_w(const mmx_ctx *c) { return std::min(c->Py, 64); }
+// its shared memory: the [c][kz][w] exchange tile
+template <typename T> size_t zmr_smem(int Pz, int W) { return (size_t)3 * Pz * W * sizeof(cx<T>); }
 template <typename T> constexpr int zmr_max() { return sizeof(T) == 4 ? 32 : 16; }
 
 // pipelined large-mesh passes: rows per item and shared-memory sizes
@@ -2676,6 +3026,7 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
     xa.self_src = (const T *)self_src;
     xa.S = (cx<T> *)c->S;
     xa.tw = (const cx<T> *)c->twx;
+    xa.tw4 = (const cx<T> *)c->tw4;
     xa.st = const_cast<DevState *>(st);
     xa.rows = c->rows;
     xa.n = c->n;
@@ -2754,7 +3105,7 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
     // XI: TMA tiles through a persistent CTA per SM where set up, else plain
     auto launch_xi = [&]() {
         if (c->xi_tma) {
-            const void *f = mmxk_kernel(K_XIT, false, c->Px);
+            const void *f = mmxk_kernel(c->r4x ? K_XI4 : K_XIT, false, c->Px);
             const size_t sm = xit_smem(c);
             void *targs[] = {(void *)&xa, (void *)&c->xi_tmap};
             launch_k(c, f, dim3(persistent_grid(f, 32 * XIT_ROWS / 2, sm, c->rows / XIT_ROWS)), dim3(32 * XIT_ROWS / 2),
@@ -2775,6 +3126,7 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
         sa.K = (const T *)c->K;
         sa.twy = (const cx<T> *)c->twy;
         sa.twz = (const cx<T> *)c->twz;
+        sa.tw4 = (const cx<T> *)c->tw4;
         sa.st = const_cast<DevState *>(st);
         sa.rows = c->rows;
         sa.nx = c->nx;
@@ -2799,26 +3151,39 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
                    *f_yi = mmxk_kernel(K_YIP, sizeof(T) == 8, c->Py), *f_zm = mmxk_kernel(K_ZMP, sizeof(T) == 8, c->Pz);
         if (parts & 1)
             timed(0, [&] {
-                launch_k(c, f_xf, dim3(persistent_grid(f_xf, txf, s_xf, n_x)), dim3(txf), xfa, s_xf, s);
+                if (c->r4x) {
+                    const void *f4 = mmxk_kernel(K_XF4, false, c->Px);
+                    launch_k(c, f4, dim3(persistent_grid(f4, 32 * XF4_ROWS / 2, xf4_smem(), c->rows / XF4_ROWS)),
+                             dim3(32 * XF4_ROWS / 2), xfa, xf4_smem(), s);
+                }
+                else
+                    launch_k(c, f_xf, dim3(persistent_grid(f_xf, txf, s_xf, n_x)), dim3(txf), xfa, s_xf, s);
             });
         if (parts & 2) timed(1, [&] {
             if (c->cluster) {
                 launch_yzc();
                 return;
             }
-            launch_k(c, f_yf, dim3(persistent_grid(f_yf, tyy, s_yf, n_y)), dim3(tyy), sargs, s_yf, s);
+            const unsigned g4 = (unsigned)(((long long)c->nx * 3 * c->nz + R4_WARPS - 1) / R4_WARPS);
+            if (c->r4)
+                launch_k(c, mmxk_kernel(K_YF4, false, c->Py), dim3(g4), dim3(32 * R4_WARPS), sargs, r4_smem(), s);
+            else
+                launch_k(c, f_yf, dim3(persistent_grid(f_yf, tyy, s_yf, n_y)), dim3(tyy), sargs, s_yf, s);
             if (c->Pz <= zmr_max<T>()) {
                 SplitArgs<T> sr = sa;
                 sr.W = zmr_w(c);
                 void *rargs[] = {(void *)&sr};
-                const size_t s_r = (size_t)3 * c->Pz * sr.W * sizeof(cx<T>);
+                const size_t s_r = zmr_smem<T>(c->Pz, sr.W);
                 launch_k(c, mmxk_kernel(K_ZMR, sizeof(T) == 8, c->Pz), dim3(c->Py / sr.W, c->nx),
                                  dim3(3 * sr.W), rargs, s_r, s);
             } else {
                 launch_k(c, f_zm, dim3(persistent_grid(f_zm, YZ_THREADS, s_zm, n_z)), dim3(YZ_THREADS), sargs,
                                  s_zm, s);
             }
-            launch_k(c, f_yi, dim3(persistent_grid(f_yi, tyy, s_yi, n_y)), dim3(tyy), sargs, s_yi, s);
+            if (c->r4)
+                launch_k(c, mmxk_kernel(K_YI4, false, c->Py), dim3(g4), dim3(32 * R4_WARPS), sargs, r4_smem(), s);
+            else
+                launch_k(c, f_yi, dim3(persistent_grid(f_yi, tyy, s_yi, n_y)), dim3(tyy), sargs, s_yi, s);
             c->launches += 2;
         });
         if (parts & 4) timed(2, launch_xi);
@@ -2986,9 +3351,12 @@ inline bool raise_smem_limit(const void *f, size_t bytes)
 
 template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
 {
-    const size_t nK = (size_t)(c->nx + 1) * c->Hz * c->Hy * 6;
+    // [kx][z][y][comp] (host set-up) to the component-major [kx][z][comp][y]
+    const size_t nK = (size_t)(c->nx + 1) * c->Hz * c->Hy * 6, Hy = (size_t)c->Hy;
     std::vector<T> Kh(nK);
-    for (size_t i = 0; i < nK; ++i) Kh[i] = (T)Kspec[i];
+    for (size_t kz = 0; kz < nK / (6 * Hy); ++kz)
+        for (size_t y = 0; y < Hy; ++y)
+            for (size_t q = 0; q < 6; ++q) Kh[(kz * 6 + q) * Hy + y] = (T)Kspec[(kz * Hy + y) * 6 + q];
     if (cudaMemcpy(c->K, Kh.data(), nK * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
     std::vector<cx<T>> tw;
     twiddles<T>(c->Px, tw);
@@ -2997,10 +3365,24 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
     if (cudaMemcpy(c->twy, tw.data(), c->Py * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
     twiddles<T>(c->Pz, tw);
     if (cudaMemcpy(c->twz, tw.data(), c->Pz * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess) return MMX_ERR_CUDA;
+    c->r4 = c->r4x = false;
+    if (c->tw4 && sizeof(T) == 4) {
+        // [k2][n1] = w1024^(n1 k2), n1 k2 < 1024
+        twiddles<T>(1024, tw);
+        std::vector<cx<T>> t4(1024);
+        for (int k = 0; k < 32; ++k)
+            for (int n = 0; n < 32; ++n) t4[32 * k + n] = tw[n * k];
+        if (cudaMemcpy(c->tw4, t4.data(), 1024 * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess)
+            return MMX_ERR_CUDA;
+        c->r4 = c->Py == 1024 && getenv("MMX_NO_R4") == nullptr;
+        c->r4x = c->Px == 1024 && getenv("MMX_NO_R4") == nullptr;
+        if (c->r4x && !raise_smem_limit(mmxk_kernel(K_XF4, false, 1024), xf4_smem())) return MMX_ERR_CUDA;
+    }
     c->xi_tma = c->xi_tma_ok = false;
     if (sizeof(T) == 4 && c->allow_tma && c->rows % XIT_ROWS == 0 && mmxk_kernel(K_XIT, false, c->Px) &&
         xit_smem(c) <= 227 * 1024 && getenv("MMX_NO_TMA") == nullptr) {
-        if (encode_xi_tmap(c) && raise_smem_limit(mmxk_kernel(K_XIT, false, c->Px), xit_smem(c)))
+        if (encode_xi_tmap(c) && raise_smem_limit(mmxk_kernel(K_XIT, false, c->Px), xit_smem(c)) &&
+            (!c->r4x || raise_smem_limit(mmxk_kernel(K_XI4, false, c->Px), xit_smem(c))))
             c->xi_tma = c->xi_tma_ok = true;
         cudaGetLastError();
     }
@@ -3021,6 +3403,7 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
                                                       {mmxk_kernel(K_ZMP, sizeof(T) == 8, c->Pz), zmp_smem<T>(c)}};
         for (const auto &f : fk)
             if (f.second > 48 * 1024 && !raise_smem_limit(f.first, f.second)) return MMX_ERR_CUDA;
+
     }
     if (c->split) {
         const size_t sy = yf_smem<T>(c, split_rows<T>(c)), sz = zm_smem<T>(c);

@@ -65,6 +65,10 @@ def test_split_pass_model_of_the_large_box():
     tensor = 513 * 513 * 17 * 6 * 4
     assert m["yz_fft_tensor_multiply"] == (24 * cells + yspec) + (2 * yspec + tensor) + (yspec + 24 * cells)
     assert sum(m.values()) == pytest.approx(1.41e9, rel=0.01)
+    # the full field (mmx_demag) also reads m in XI for the self term
+    mf = bench.demag_pass_bytes(n, 4, split=True, self_term=True)
+    assert mf["x_inverse_fft"] - m["x_inverse_fft"] == 12 * cells
+    assert mf["x_forward_fft"] == m["x_forward_fft"]
 
 
 def test_speed_at_error_interpolates_in_log_log():
