@@ -477,3 +477,35 @@ def test_periodic_check_keeps_a_good_net():
     finally:
         ctx.close()
         zero.close()
+
+
+def test_trained_net_error_and_speed_against_plain_extrapolation():
+    """The learned residual in the integrator's own terms: a net trained on
+    RK4 sub-step snapshots (the config-5 recipe of bench.residual_config5 at
+    32 x 32 x 2) is attached to DP54 p = 4 (FP32, exact-demag fallback on)
+    and compared with plain extrapolation at each e_max: Eq. 7 error against
+    an FP64 full-demag run, and simulated ns/s.  The net must learn (loss
+    falls, held-out gain > 1) and keep the run within the fallback's bound of
+    the plain run's error; the speed at equal error is reported (the net's
+    forward costs several exact demag evaluations of this mesh)."""
+    import os
+    import sys
+    torch = torch_cuda()
+    import paper_2107_06729_gb300 as pkg
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    res = bench.residual_config5(pkg, torch, torch.device("cuda", 0), n=(32, 32, 2), n_samples=480, epochs=2,
+                                 tols=(1e-5, 3e-5), horizon_ps=5.0, seed=3)
+    print("config-5 recipe at 32x32x2:", res["gain_held_out"], res["at_equal_error"], res["sweep"])
+    assert res["samples"] == 480
+    first, last = res["loss_first_last"]
+    assert np.isfinite(first) and last < first
+    assert res["gain_held_out"] > 1.0
+    for plain, withnet in zip(res["sweep"]["extrapolated"], res["sweep"]["extrapolated_plus_net"]):
+        assert plain["tol"] == withnet["tol"]
+        assert np.isfinite(plain["eps"]) and np.isfinite(withnet["eps"])
+        assert plain["ns_per_s"] > 0 and withnet["ns_per_s"] > 0
+        # accepted steps all passed the same error test as the plain run's
+        assert withnet["eps"] <= 3.0 * plain["eps"] + 1e-6
+    eq = res["at_equal_error"]
+    assert eq["net_ns_per_s"] > 0 and eq["plain_ns_per_s"] > 0
