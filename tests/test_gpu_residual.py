@@ -494,7 +494,7 @@ def test_trained_net_error_and_speed_against_plain_extrapolation():
     import paper_2107_06729_gb300 as pkg
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import bench
-    res = bench.residual_config5(pkg, torch, torch.device("cuda", 0), n=(32, 32, 2), n_samples=480, epochs=2,
+    res = bench.residual_config5(pkg, torch, torch.device("cuda", 0), n=(32, 32, 2), n_samples=480, epochs=2, lr=1e-3,
                                  tols=(1e-5, 3e-5), horizon_ps=5.0, seed=3)
     print("config-5 recipe at 32x32x2:", res["gain_held_out"], res["at_equal_error"], res["sweep"])
     assert res["samples"] == 480
