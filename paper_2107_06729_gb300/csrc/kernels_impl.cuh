@@ -977,6 +977,13 @@ __global__ void __launch_bounds__(32 * XIT_ROWS / 2, 3) k_xi_t(const XArgs<T> a,
             static_assert(PX == 1024 && sizeof(T) == 4, "four-step XI: FP32, 1024 points");
             if (w < NP) {
                 const int lane = threadIdx.x & 31;
+                const long long ra = (long long)tile * TR + 2 * w;
+                if (a.self_src) {
+                    // the pair's two m rows (4 KB, one 128-byte line per lane)
+                    // start toward L2 now; they are read after the transforms
+                    const char *pf = reinterpret_cast<const char *>(a.self_src + ra * NX) + 128 * lane;
+                    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(pf));
+                }
                 const Pad<T> z = work.at(w * PXS);
                 cx<T> v[32];
 #pragma unroll
@@ -987,7 +994,6 @@ __global__ void __launch_bounds__(32 * XIT_ROWS / 2, 3) k_xi_t(const XArgs<T> a,
                 const int b0 = w * PXS;
                 r4_transpose(v, work.p + b0 + (b0 >> 4));
                 dft32_out16<T, true>(v);
-                const long long ra = (long long)tile * TR + 2 * w;
                 const int lgpl = ilog2(a.plane);
                 const T msa = (T)a.msN00[(int)(ra >> lgpl)], msb = (T)a.msN00[(int)((ra + 1) >> lgpl)];
                 T *oa = out + ra * NX, *ob = oa + NX;
@@ -1747,21 +1753,29 @@ __global__ void __launch_bounds__(32 * XF4_ROWS / 2, 2) k_xf4(const XArgs<T> a)
 #pragma unroll
         for (int k = 0; k < 32; ++k) tile[k * R4_PITCH + lane] = v[k];
         __syncthreads();
-        const long long r0 = (long long)item * TR;
-        for (int idx = threadIdx.x; idx < NX * TR; idx += blockDim.x) {
-            const int k = idx >> 4, t = idx & (TR - 1);
+        // thread (kb, t) of the 16 x 16 CTA stores row t at kx = kb + 16 j:
+        // the tile word of kx, (kx >> 5) * 33 + (kx & 31), is a compile-time
+        // offset from kb for every j, and so is that of PX - kx
+        {
+            const int t = threadIdx.x & (TR - 1), kb = threadIdx.x >> 4;
             const cx<T> *z = tiles + (t >> 1) * XF4_TS;
-            auto Z = [&](int q) { return z[(q >> 5) * R4_PITCH + (q & 31)]; };
-            cx<T> o;
-            if (k == 0) {
-                const cx<T> z0 = Z(0), zn = Z(NX);
-                o = (t & 1) ? mk(z0.y, zn.y) : mk(z0.x, zn.x);
-            } else {
-                const cx<T> zk = Z(k), zm = Z(PX - k);
-                const T hlf = (T)0.5;
-                o = (t & 1) ? mk(hlf * (zk.y + zm.y), hlf * (zm.x - zk.x)) : mk(hlf * (zk.x + zm.x), hlf * (zk.y - zm.y));
+            const bool odd = t & 1;
+            cx<T> *dst = a.S + (size_t)kb * R + (size_t)item * TR + t;
+            const T hlf = (T)0.5;
+#pragma unroll 8
+            for (int j = 0; j < NX / 16; ++j) {
+                // kx = kb + 16 j pairs with PX - kx, except kx = 0, which
+                // pairs with NX (the Nyquist word)
+                const cx<T> zk = z[(j >> 1) * R4_PITCH + 16 * (j & 1) + kb];
+                const int m = (j == 0 && kb == 0) ? NX : PX - 16 * j - kb;
+                const cx<T> zm = z[(m >> 5) * R4_PITCH + (m & 31)];
+                cx<T> o;
+                if (j == 0 && kb == 0)  // kx = 0: DC and Nyquist of both rows (zm is Z[NX])
+                    o = odd ? mk(zk.y, zm.y) : mk(zk.x, zm.x);
+                else
+                    o = odd ? mk(hlf * (zk.y + zm.y), hlf * (zm.x - zk.x)) : mk(hlf * (zk.x + zm.x), hlf * (zk.y - zm.y));
+                dst[(size_t)j * 16 * R] = o;
             }
-            a.S[(long long)k * R + r0 + t] = o;
         }
         __syncthreads();  // the tiles are refilled by the next item
     }
