@@ -423,38 +423,6 @@ def residual_net(pkg, torch, dev, iters=50):
         trn_s = ev[3].elapsed_time(ev[4]) / 1e3 / 10
         net.close()
         ctx.close()
-        # the same forward on the other layer kernels, for comparison
-        other = {}
-        # training step with the FP32 SIMT input gradients
-        os.environ["MMX_RNET_SIMT_BWD"] = "1"
-        try:
-            net3 = pkg.RNet(cells, W.rnet_params(0), stream)
-        finally:
-            del os.environ["MMX_RNET_SIMT_BWD"]
-        net3.train_step(xd, td, 1e-4)
-        ev[0].record(stream)
-        for _ in range(10):
-            pkg.mmx_rnet_train_step(net3.handle, n, xd, td, 1e-4)
-        ev[1].record(stream)
-        torch.cuda.synchronize(dev)
-        trn_simt_s = ev[0].elapsed_time(ev[1]) / 1e3 / 10
-        net3.close()
-        for name, env in (("tcgen05_2buf", {"MMX_RNET_NBUF": "2"}), ("mma_sync", {"MMX_RNET_MMA_SYNC": "1"})):
-            os.environ.update(env)
-            try:
-                net2 = pkg.RNet(cells, W.rnet_params(0), stream)
-            finally:
-                for k in env:
-                    del os.environ[k]
-            for _ in range(5):
-                net2.forward(xd, r)
-            ev[0].record(stream)
-            for _ in range(iters):
-                net2.forward(xd, r)
-            ev[1].record(stream)
-            torch.cuda.synchronize(dev)
-            other[name] = round(ev[0].elapsed_time(ev[1]) / 1e3 / iters * 1e6, 2)
-            net2.close()
         # in the stage loop: 5 ps of DP54 p = 4 (FP32) on the same film, plain
         # extrapolation against the net attached (zero parameters: same steps)
         integ = {"method": "RKDP54", "extrap_order": 4, "adaptive": True, "h": 1e-13, "tol": 1e-5}
@@ -484,13 +452,11 @@ def residual_net(pkg, torch, dev, iters=50):
     return {"workload": "residual_net_128x128x4_forward", "bound": "tensor", "achieved": round(ach, 2),
             "peak": peak, "unit": "TFLOP/s", "frac": round(ach / peak, 4), "peak_source": src,
             "flops_per_forward": flops, "us_per_forward": round(fwd_s * 1e6, 2),
-            "us_per_forward_other_kernels": other,
             "exact_demag_us_same_mesh": round(dmg_s * 1e6, 2), "train_step_us": round(trn_s * 1e6, 1),
-            "train_step_us_simt_input_grad": round(trn_simt_s * 1e6, 1),
             "in_stage_loop_dp54_p4_5ps": loop,
             "note": "4 conv launches + input pack per forward (tcgen05.mma 128xNx16 BF16, FP32 accumulate in "
-                    "TMEM; the mma.sync m16n8k16 kernels beside it); "
-                    "algorithmic flops of the real channel counts; inputs (1.5 MB) stay in L2"}
+                    "TMEM); training step = forward, loss, input and weight gradients on the tensor cores, "
+                    "Adam; algorithmic flops of the real channel counts; inputs (1.5 MB) stay in L2"}
 
 
 def ensemble(pkg, torch, dev, chunk_ps, steps, warmup):

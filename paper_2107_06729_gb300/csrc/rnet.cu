@@ -3,21 +3,17 @@
 // no learned part; this net predicts its error from the stage state.
 //
 // Forward: each 3x3x3 layer is an implicit GEMM, M = cells, N = output
-// channels, K = 27 taps x input channels.  Default kernel (k_rnet_conv_tc):
-// tcgen05.mma 128 x N x 16 on the 5th-generation tensor cores with FP32
-// accumulators in TMEM; the input halo sits in shared memory in the
-// canonical K-major layout so that every tap's A operand is the same layout
-// at a shifted start address; each k-chunk plane of the halo is one 5-D
-// tensor-memory-access copy (zero-filled outside the mesh) and the weights
-// arrive by one bulk copy per CTA.
-// Alternative (MMX_RNET_MMA_SYNC=1, k_rnet_conv): mma.sync m16n8k16 with
-// ldmatrix A fragments from a channels-last halo (cell stride padded by 16
-// bytes so that each 8-row ldmatrix phase hits distinct banks) and B
-// fragments through L1.  Bias, ReLU and the BF16 rounding of the output are
-// fused into both.
-// Backward (training only): FP32 SIMT kernels for the input gradient (one
-// thread per cell and channel) and the weight gradient (per tap, chunks of
-// cells staged in shared memory, atomics into the FP32 gradient).
+// channels, K = 27 taps x input channels (k_rnet_conv_tc): tcgen05.mma
+// 128 x N x 16 on the 5th-generation tensor cores with FP32 accumulators in
+// TMEM; the input halo sits in shared memory in the canonical K-major layout
+// so that every tap's A operand is the same layout at a shifted start
+// address; each k-chunk plane of the halo is one 5-D tensor-memory-access
+// copy (zero-filled outside the mesh) and the weights arrive by one bulk
+// copy per CTA.  Bias, ReLU and the BF16 rounding of the output are fused.
+// Backward (training only), also on the tensor cores: the input gradient is
+// the same kernel with tap-flipped, transposed weights (the output gradient
+// rounded to BF16 where it enters), the weight gradient a GEMM over cells
+// (k_rnet_wgrad_tc, below).
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 #include <math.h>
@@ -33,51 +29,23 @@
 
 namespace {
 
-constexpr int RN_TX = 32, RN_TY = 4;  // tile of cells per CTA (4 warps, one y row each)
+constexpr int RN_TY = 4;  // tile rows per CTA (4 warps, one y row each)
 constexpr int NLAYER = 4;
 constexpr int CIN[NLAYER] = {6, 32, 32, 32}, COUT[NLAYER] = {32, 32, 32, 3};
-constexpr int CINP[NLAYER] = {16, 32, 32, 32}, COUTP[NLAYER] = {32, 32, 32, 8};
+constexpr int CINP[NLAYER] = {16, 32, 32, 32};
 
 constexpr long long p_off(int l)
 {
     return l == 0 ? 0 : p_off(l - 1) + 27LL * COUT[l - 1] * CIN[l - 1] + COUT[l - 1];
 }
-constexpr long long w_off(int l)
-{
-    return l == 0 ? 0 : w_off(l - 1) + 27LL * COUTP[l - 1] * CINP[l - 1];
-}
 static_assert(p_off(NLAYER) == MMX_RNET_PARAMS, "parameter count");
 // the same offsets as scalars, for device code
-constexpr long long WO1 = 13824, WO2 = 41472, WO3 = 69120, WQ_TOTAL = 76032;
 constexpr long long PO1 = 5216, PO2 = 32896, PO3 = 60576;
-static_assert(w_off(1) == WO1 && w_off(2) == WO2 && w_off(3) == WO3 && w_off(4) == WQ_TOTAL, "weight offsets");
 static_assert(p_off(1) == PO1 && p_off(2) == PO2 && p_off(3) == PO3, "parameter offsets");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void ldmatrix_x4(uint32_t r[4], uint32_t addr)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-template <int CINP_>
-constexpr size_t conv_smem()
-{
-    return (size_t)3 * (RN_TY + 2) * (RN_TX + 2) * (CINP_ + 8) * 2;
 }
 
 // x (FP32, [6][cells]) -> layer-0 input (BF16, [cells][16], channels 6..15 zero)
@@ -91,89 +59,6 @@ __global__ void k_rnet_pack(const float *__restrict__ x, long long n, __nv_bfloa
     uint4 *dst = (uint4 *)(a0 + i * 16);
     dst[0] = ((const uint4 *)v)[0];
     dst[1] = ((const uint4 *)v)[1];
-}
-
-// One layer: out = act(b + sum_t W_t in(shifted by t)).  Hidden layers write
-// BF16 [cells][32] after ReLU; the last layer writes FP32 [3][cells].
-template <int CINP_, int COUTP_, bool LAST>
-__global__ void __launch_bounds__(128) k_rnet_conv(const __nv_bfloat16 *__restrict__ in,
-                                                   const __nv_bfloat16 *__restrict__ Wq,
-                                                   const float *__restrict__ bias, int cout, void *out, int nx,
-                                                   int ny, int nz)
-{
-    constexpr int CS = CINP_ + 8;
-    constexpr int HX = RN_TX + 2, HY = RN_TY + 2;
-    constexpr int V = CINP_ / 8;  // 16-byte vectors per cell
-    extern __shared__ __align__(16) unsigned char rn_smem[];
-    __nv_bfloat16 *hal = (__nv_bfloat16 *)rn_smem;  // [3][HY][HX][CS]
-    const int x0 = blockIdx.x * RN_TX, y0 = blockIdx.y * RN_TY, z = blockIdx.z;
-    for (int e = threadIdx.x; e < 3 * HY * HX * V; e += blockDim.x) {
-        const int v = e % V, cell = e / V;
-        const int hx = cell % HX, hy = (cell / HX) % HY, hz = cell / (HX * HY);
-        const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z + hz - 1;
-        uint4 val = make_uint4(0u, 0u, 0u, 0u);
-        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
-            val = ((const uint4 *)(in + ((size_t)(gz * ny + gy) * nx + gx) * CINP_))[v];
-        *(uint4 *)(hal + (size_t)cell * CS + v * 8) = val;
-    }
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, q = lane & 3;
-    constexpr int NT = COUTP_ / 8;
-    float acc[2][NT][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[mt][nt][j] = 0.0f;
-    // ldmatrix: lanes 0-7 / 8-15 give rows 0-7 / 8-15 at k 0-7, lanes 16-31 the same rows at k 8-15
-    const int lrow = (lane & 7) + ((lane >> 3) & 1) * 8, lk = (lane >> 4) * 8;
-    const uint32_t hal_s = smem_u32(hal);
-    for (int t = 0; t < 27; ++t) {
-        const int tz = t / 9, ty = (t / 3) % 3, tx = t % 3;
-        const int cell0 = (tz * HY + warp + ty) * HX + lrow + tx;
-        const __nv_bfloat16 *Wt = Wq + (size_t)t * COUTP_ * CINP_;
-#pragma unroll
-        for (int kc = 0; kc < CINP_ / 16; ++kc) {
-            uint32_t a[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-                ldmatrix_x4(a[mt], hal_s + (uint32_t)(((cell0 + mt * 16) * CS + kc * 16 + lk) * 2));
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const __nv_bfloat16 *wp = Wt + (nt * 8 + g) * CINP_ + kc * 16 + 2 * q;
-                const uint32_t b0 = __ldg((const unsigned int *)wp);
-                const uint32_t b1 = __ldg((const unsigned int *)(wp + 8));
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) mma_bf16(acc[mt][nt], a[mt], b0, b1);
-            }
-        }
-    }
-    const int y = y0 + warp;
-    const size_t ncell = (size_t)nx * ny * nz;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int x = x0 + mt * 16 + g + half * 8;
-            if (x >= nx || y >= ny) continue;
-            const size_t cell = ((size_t)z * ny + y) * nx + x;
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const int col = nt * 8 + 2 * q;
-                const float v0 = acc[mt][nt][half * 2], v1 = acc[mt][nt][half * 2 + 1];
-                if (!LAST) {
-                    const __nv_bfloat162 h =
-                        __floats2bfloat162_rn(fmaxf(v0 + bias[col], 0.0f), fmaxf(v1 + bias[col + 1], 0.0f));
-                    *(__nv_bfloat162 *)((__nv_bfloat16 *)out + cell * 32 + col) = h;
-                } else {
-                    float *r = (float *)out;
-                    if (col < cout) r[col * ncell + cell] = v0 + bias[col];
-                    if (col + 1 < cout) r[(col + 1) * ncell + cell] = v1 + bias[col + 1];
-                }
-            }
-        }
 }
 
 // ---- tcgen05 version of the layer ------------------------------------------
@@ -207,10 +92,10 @@ constexpr unsigned long long TC_WAIT_NS = 1000000000ULL;
 // go to different ones, so that they do not wait on each other's results
 constexpr int TC_NACC = 4;
 
-__host__ __device__ constexpr size_t tc_smem(int cinp, int n, int nbuf)
+__host__ __device__ constexpr size_t tc_smem(int cinp, int n)
 {
     // 128 bytes of alignment slack, halo planes, weights, 4 mbarriers + TMEM slot
-    return 128 + (size_t)nbuf * (cinp / 8) * TC_NE * 16 + (size_t)27 * (cinp / 8) * n * 16 + 64;
+    return 128 + (size_t)(cinp / 8) * TC_NE * 16 + (size_t)27 * (cinp / 8) * n * 16 + 64;
 }
 
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes)
@@ -273,7 +158,7 @@ __device__ __forceinline__ void tc_load_halo(const CUtensorMap *tm, uint32_t hb,
 // FP32 [3][cells] out); 2: input gradient of a layer (tap-flipped, transposed
 // weights; FP32 [cells][32] out, masked by ReLU' of the layer input `mask`,
 // and its BF16 copy in out2)
-template <int CINP_, int N_, int MODE, int NBUF>
+template <int CINP_, int N_, int MODE>
 __global__ void __launch_bounds__(128) k_rnet_conv_tc(const __grid_constant__ CUtensorMap tmap,
                                                       const __nv_bfloat16 *__restrict__ Wtc,
                                                       const float *__restrict__ bias, int cout, void *out, int nx,
@@ -283,8 +168,8 @@ __global__ void __launch_bounds__(128) k_rnet_conv_tc(const __grid_constant__ CU
     constexpr int KC = CINP_ / 8;  // 16-byte k-chunks per cell
     extern __shared__ __align__(128) unsigned char tc_smem_raw[];
     unsigned char *base = tc_smem_raw + ((128u - (smem_u32(tc_smem_raw) & 127u)) & 127u);
-    uint4 *hal2 = (uint4 *)base;                       // halo planes [NBUF][KC][TC_NE], 128-byte aligned
-    uint4 *wsm = hal2 + NBUF * KC * TC_NE;             // [27][KC][N_]
+    uint4 *hal2 = (uint4 *)base;                       // halo planes [KC][TC_NE], 128-byte aligned
+    uint4 *wsm = hal2 + KC * TC_NE;                    // [27][KC][N_]
     uint64_t *mbar = (uint64_t *)(wsm + 27 * KC * N_); // [0] MMAs done, [1] weights, [2 + b] halo buffer b
     uint32_t *tmem_slot = (uint32_t *)(mbar + 4);
     constexpr uint32_t WBYTES = 27u * KC * N_ * 16u;
@@ -300,7 +185,7 @@ __global__ void __launch_bounds__(128) k_rnet_conv_tc(const __grid_constant__ CU
     if (threadIdx.x == 32)
         for (int i = 0; i < 4; ++i) tc_mbar_init(smem_u32(mbar + i));
     // pad rows (never written by the copies): zero in every plane
-    for (int e = threadIdx.x; e < NBUF * KC * (TC_NE - TC_ROWS); e += blockDim.x) {
+    for (int e = threadIdx.x; e < KC * (TC_NE - TC_ROWS); e += blockDim.x) {
         const int v = e / (TC_NE - TC_ROWS), r = e % (TC_NE - TC_ROWS);
         hal2[v * TC_NE + (r < TC_PAD ? r : TC_ROWS + r)] = make_uint4(0u, 0u, 0u, 0u);
     }
@@ -339,7 +224,7 @@ __global__ void __launch_bounds__(128) k_rnet_conv_tc(const __grid_constant__ CU
     for (int tile = blockIdx.x, it = 0; tile < ntiles; tile += gridDim.x, ++it) {
         int x0, y0, z;
         tile_xyz(tile, x0, y0, z);
-        const int b = NBUF == 2 ? (it & 1) : 0;
+        const int b = 0;
         const int next = tile + (int)gridDim.x;
         // this tile's MMAs overwrite the accumulators the previous tile's TMEM
         // loads read before the barrier that ended that iteration
@@ -384,14 +269,6 @@ __global__ void __launch_bounds__(128) k_rnet_conv_tc(const __grid_constant__ CU
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb)
                              : "memory");
-                // two buffers: the other one was last read by the previous tile's MMAs, which completed
-                if (NBUF == 2 && hok && next < ntiles) {
-                    int nx0, ny0, nz0;
-                    tile_xyz(next, nx0, ny0, nz0);
-                    tc_load_halo<KC>(&tmap, hal_s + (uint32_t)((b ^ 1) * KC * TC_NE) * 16u, smem_u32(mbar + 2 + (b ^ 1)),
-                                     nx0, ny0, nz0);
-                    pending = true;
-                }
             }
             __syncwarp();  // the other lanes of the issuing warp do not spin beside it
         }
@@ -400,8 +277,8 @@ __global__ void __launch_bounds__(128) k_rnet_conv_tc(const __grid_constant__ CU
             if (lane == 0) atomicExch(fault, 1);
             ok = tc_mbar_wait(mb, it & 1, TC_WAIT_NS);  // let the MMAs in flight finish before TMEM is freed
         }
-        // one buffer: this tile's MMAs are done with it, so the next tile's halo can come in now
-        if (NBUF == 1 && threadIdx.x == 0 && ok && next < ntiles) {
+        // this tile's MMAs are done with the buffer, so the next tile's halo can come in now
+        if (threadIdx.x == 0 && ok && next < ntiles) {
             int nx0, ny0, nz0;
             tile_xyz(next, nx0, ny0, nz0);
             tc_load_halo<KC>(&tmap, hal_s, smem_u32(mbar + 2), nx0, ny0, nz0);
@@ -488,7 +365,7 @@ __global__ void __launch_bounds__(128) k_rnet_conv_tc(const __grid_constant__ CU
     }
     // a halo copy still in flight (only after a lost barrier phase): let it land first
     if (threadIdx.x == 0 && pending) {
-        for (int bb = 0; bb < NBUF; ++bb) (void)tc_mbar_wait(smem_u32(mbar + 2 + bb), uses[bb] & 1, TC_WAIT_NS);
+        (void)tc_mbar_wait(smem_u32(mbar + 2), uses[0] & 1, TC_WAIT_NS);
     }
     if (threadIdx.x == 0 && (int)blockIdx.x >= ntiles) (void)tc_mbar_wait(mw, 0, TC_WAIT_NS);
     if (warp == 0)
@@ -528,84 +405,231 @@ __global__ void k_rnet_loss(const float *__restrict__ r, const float *__restrict
     }
 }
 
-// gradient with respect to the layer input, masked by ReLU' of that input:
-// dzp[p][c] = [A[p][c] > 0] sum_t sum_o W_t[o][c] dz[p - t][o]
-template <int COUTP_>
-__global__ void __launch_bounds__(256) k_rnet_dgrad(const float *__restrict__ dz, const __nv_bfloat16 *__restrict__ Wq,
-                                                    int cout, const __nv_bfloat16 *__restrict__ A,
-                                                    float *__restrict__ dzp, int nx, int ny, int nz)
+// N consecutive FP32 accumulator columns of this warp's 32 TMEM lanes
+template <int N>
+__device__ __forceinline__ void tmem_load(uint32_t taddr, float *v)
 {
-    const long long n = (long long)nx * ny * nz;
-    const int c = threadIdx.x & 31;
-    const long long p = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (p >= n) return;
-    const int x = (int)(p % nx), y = (int)((p / nx) % ny), z = (int)(p / ((long long)nx * ny));
-    float acc = 0.0f;
-    for (int t = 0; t < 27; ++t) {
-        const int qx = x - (t % 3 - 1), qy = y - ((t / 3) % 3 - 1), qz = z - (t / 9 - 1);
-        if (qx < 0 || qx >= nx || qy < 0 || qy >= ny || qz < 0 || qz >= nz) continue;
-        const float *d = dz + (((long long)qz * ny + qy) * nx + qx) * COUTP_;
-        const __nv_bfloat16 *w = Wq + (size_t)t * COUTP_ * 32 + c;
-        for (int o = 0; o < cout; ++o) acc += __bfloat162float(w[o * 32]) * d[o];
+    uint32_t u[N];
+    if constexpr (N == 32) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+            : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+              "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]),
+              "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]),
+              "=r"(u[23]), "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]),
+              "=r"(u[30]), "=r"(u[31])
+            : "r"(taddr));
+    } else {
+        static_assert(N == 16, "N is 16 or 32");
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+              "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+            : "r"(taddr));
     }
-    dzp[p * 32 + c] = (__bfloat162float(A[p * 32 + c]) > 0.0f) ? acc : 0.0f;
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int c = 0; c < N; ++c) v[c] = __uint_as_float(u[c]);
 }
 
-// weight (and, at the centre tap, bias) gradient of one layer:
-// gW[t][o][c] += sum_p dz[p][o] A[p + t][c] over a chunk of cells
-template <int CINP_, int COUTP_>
-__global__ void __launch_bounds__(256) k_rnet_wgrad(const float *__restrict__ dz, const __nv_bfloat16 *__restrict__ A,
-                                                    int cin, int cout, float *gW, float *gb, int nx, int ny, int nz,
-                                                    int chunk)
+// ---- weight and bias gradients -------------------------------------------
+// gW[t][o][c] = sum_p dz[p][o] A[p + d_t][c] (d_t the offset of tap t) is,
+// with q = p + d_t, sum_q dz[q - d_t][o] A[q][c]: per CTA a GEMM on the
+// tensor cores, D[(tx, o)][c] += sum_q dzs[(tx, o)][q] A[c][q] over tiles of
+// WG_TC cells q along x, one accumulator per (tz, ty) tap "slab" of the CTA's
+// slab group (grid.y = tz: ty = 0..2).  The 3 x COUTP rows (tx, o) of a slab
+// are dz shifted by the x-tap; the other rows of its 128-row MMA are the
+// next slab's rows (or zero) and are never read back.  dz (FP32) enters as a
+// BF16 pair hi + lo, two MMAs into the same accumulator (about 16 bits), so
+// the gradient keeps FP32-like accuracy; the activations are BF16 already.
+// Both operands are built by the threads in shared memory in the canonical
+// K-major layout without swizzle (8-row core matrices of 16-byte rows): a
+// 16-byte row holds 8 consecutive cells of one (tx, o) or of one c.  The
+// accumulators stay in TMEM over all tiles of the CTA; at the end the CTA
+// writes its partial sums to scratch [cta][27][COUTP][CINP], which a second
+// kernel adds up.  Every wait is bounded; on expiry the kernel sets *fault,
+// waits once more for its own MMAs and frees its TMEM.
+constexpr int WG_TKC = 2;          // 16-byte k-chunks (8 cells each) per tile: one MMA k-step
+constexpr int WG_TC = 8 * WG_TKC;  // cells per tile
+template <int COUTP_> __host__ __device__ constexpr int wg_gs() { return 3 * COUTP_ / 8; }  // row groups per slab
+// row groups per k-chunk: three slabs, plus the rows the last slab's MMA reads beyond its own
+template <int COUTP_> __host__ __device__ constexpr int wg_groups() { return 2 * wg_gs<COUTP_>() + 16; }
+template <int CINP_, int COUTP_> __host__ __device__ constexpr size_t wg_smem()
 {
-    constexpr int SUB = 64;
-    constexpr int PAIRS = COUTP_ * CINP_;
-    constexpr int PT = (PAIRS + 255) / 256;
-    __shared__ float s_dz[SUB][COUTP_];
-    __shared__ float s_A[SUB][CINP_ + 1];
-    const long long n = (long long)nx * ny * nz;
-    const int t = blockIdx.y;
-    const int dxx = t % 3 - 1, dyy = (t / 3) % 3 - 1, dzz = t / 9 - 1;
-    const long long c0 = (long long)blockIdx.x * chunk;
-    const long long c1 = min(c0 + chunk, n);
-    float acc[PT];
-#pragma unroll
-    for (int k = 0; k < PT; ++k) acc[k] = 0.0f;
-    float bacc = 0.0f;
-    for (long long s0 = c0; s0 < c1; s0 += SUB) {
-        for (int e = threadIdx.x; e < SUB * COUTP_; e += blockDim.x) {
-            const long long p = s0 + e / COUTP_;
-            s_dz[e / COUTP_][e % COUTP_] = (p < c1) ? dz[p * COUTP_ + e % COUTP_] : 0.0f;
-        }
-        for (int e = threadIdx.x; e < SUB * CINP_; e += blockDim.x) {
-            const long long p = s0 + e / CINP_;
-            float v = 0.0f;
-            if (p < c1) {
-                const int x = (int)(p % nx) + dxx, y = (int)((p / nx) % ny) + dyy,
-                          z = (int)(p / ((long long)nx * ny)) + dzz;
-                if (x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz)
-                    v = __bfloat162float(A[(((long long)z * ny + y) * nx + x) * CINP_ + e % CINP_]);
-            }
-            s_A[e / CINP_][e % CINP_] = v;
-        }
-        __syncthreads();
-        for (int i = 0; i < SUB; ++i) {
-#pragma unroll
-            for (int k = 0; k < PT; ++k) {
-                const int j = threadIdx.x + k * 256;
-                if (j < PAIRS) acc[k] += s_dz[i][j / CINP_] * s_A[i][j % CINP_];
-            }
-            if (t == 13 && threadIdx.x < COUTP_) bacc += s_dz[i][threadIdx.x];
-        }
-        __syncthreads();
+    return 128 + (size_t)2 * WG_TKC * wg_groups<COUTP_>() * 128 + (size_t)WG_TKC * (CINP_ / 8) * 128 + 64;
+}
+
+template <int CINP_, int COUTP_>
+__global__ void __launch_bounds__(128) k_rnet_wgrad_tc(const float *__restrict__ dz,
+                                                       const __nv_bfloat16 *__restrict__ A, float *__restrict__ part,
+                                                       int nx, int ny, int nz, int *fault)
+{
+    constexpr int GS = wg_gs<COUTP_>(), NG = wg_groups<COUTP_>(), KCB = CINP_ / 8;
+    constexpr uint32_t NCOL = 3 * CINP_;  // accumulator columns: three slabs of N = CINP
+    constexpr uint32_t NALLOC = NCOL <= 32 ? 32 : (NCOL <= 64 ? 64 : (NCOL <= 128 ? 128 : 256));
+    extern __shared__ __align__(128) unsigned char wg_raw[];
+    unsigned char *base = wg_raw + ((128u - (smem_u32(wg_raw) & 127u)) & 127u);
+    uint4 *dzs = (uint4 *)base;                     // [hi / lo][WG_TKC][NG][8] 16-byte rows
+    uint4 *as = dzs + 2 * WG_TKC * NG * 8;          // [WG_TKC][KCB][8]
+    uint64_t *mbar = (uint64_t *)(as + WG_TKC * KCB * 8);
+    uint32_t *tmem_slot = (uint32_t *)(mbar + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tz = blockIdx.y;
+    const int txc = (nx + WG_TC - 1) / WG_TC;
+    const long long ntiles = (long long)txc * ny * nz;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                     "r"(NALLOC)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
+    if (threadIdx.x == 32) tc_mbar_init(smem_u32(mbar));
+    // rows never written (beyond the last slab) stay zero
+    for (int e = threadIdx.x; e < 2 * WG_TKC * NG * 8 + WG_TKC * KCB * 8; e += blockDim.x)
+        dzs[e] = make_uint4(0u, 0u, 0u, 0u);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t mb = smem_u32(mbar), dz_s = smem_u32(dzs), a_s = smem_u32(as);
+    bool ok = true;
+    int it = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int xt = (int)(tile % txc);
+        const long long rest = tile / txc;
+        const int y = (int)(rest % ny), z = (int)(rest / ny), x0 = xt * WG_TC;
+        // dz rows: slab s (ty), x-tap tx, channel o, k-chunk kc; cell q = x0 + 8 kc + e
+        // takes dz at q - d: (x - (tx - 1), y - (s - 1), z - (tz - 1)), zero outside the mesh.
+        // Consecutive threads take consecutive o: each load of a warp reads one 128-byte run.
+        for (int r = threadIdx.x; r < 9 * COUTP_ * WG_TKC; r += blockDim.x) {
+            const int o = r % COUTP_;
+            int rr = r / COUTP_;
+            const int tx = rr % 3;
+            rr /= 3;
+            const int sl = rr % 3, kc = rr / 3;
+            const int yy = y - (sl - 1), zz = z - (tz - 1);
+            const bool rowok = yy >= 0 && yy < ny && zz >= 0 && zz < nz;
+            const float *src = dz + (((long long)(rowok ? zz : 0) * ny + (rowok ? yy : 0)) * nx) * COUTP_ + o;
+            __align__(16) __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
-    for (int k = 0; k < PT; ++k) {
-        const int j = threadIdx.x + k * 256;
-        const int o = j / CINP_, c = j % CINP_;
-        if (j < PAIRS && o < cout && c < cin) atomicAdd(&gW[((size_t)t * cout + o) * cin + c], acc[k]);
+            for (int e = 0; e < 8; ++e) {
+                const int xx = x0 + 8 * kc + e - (tx - 1);
+                const float v = (rowok && xx >= 0 && xx < nx) ? src[(long long)xx * COUTP_] : 0.0f;
+                hi[e] = __float2bfloat16_rn(v);
+                lo[e] = __float2bfloat16_rn(v - __bfloat162float(hi[e]));
+            }
+            const int m = tx * COUTP_ + o, g = sl * GS + (m >> 3);
+            dzs[((0 * WG_TKC + kc) * NG + g) * 8 + (m & 7)] = *(const uint4 *)hi;
+            dzs[((1 * WG_TKC + kc) * NG + g) * 8 + (m & 7)] = *(const uint4 *)lo;
+        }
+        // activations: row c, k-chunk kc, unshifted; cells beyond nx zero
+        for (int r = threadIdx.x; r < CINP_ * WG_TKC; r += blockDim.x) {
+            const int c = r % CINP_, kc = r / CINP_;
+            const __nv_bfloat16 *src = A + (((long long)z * ny + y) * nx) * CINP_ + c;
+            __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int xx = x0 + 8 * kc + e;
+                v[e] = xx < nx ? src[(long long)xx * CINP_] : __float2bfloat16_rn(0.0f);
+            }
+            as[(kc * KCB + (c >> 3)) * 8 + (c & 7)] = *(const uint4 *)v;
+        }
+        // the operands written by the threads become visible to the tensor cores
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (threadIdx.x == 0) {
+            constexpr uint32_t idesc = umma_idesc_bf16<CINP_>();
+#pragma unroll
+            for (int sl = 0; sl < 3; ++sl)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int ks = 0; ks < WG_TKC / 2; ++ks) {
+                        const uint64_t ad = umma_desc(
+                            dz_s + (uint32_t)(((h * WG_TKC + 2 * ks) * NG + sl * GS) * 8) * 16u, NG * 128u, 128u);
+                        const uint64_t bd = umma_desc(a_s + (uint32_t)(2 * ks * KCB * 8) * 16u, KCB * 128u, 128u);
+                        // the first MMA into each slab's accumulator overwrites it
+                        const uint32_t acc = (it > 0 || h > 0 || ks > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                tmem + (uint32_t)(sl * CINP_)),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                            : "memory");
+                    }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb)
+                         : "memory");
+        }
+        __syncwarp();
+        // the MMAs read the operands: the next tile may only overwrite them afterwards
+        bool done = tc_mbar_wait(mb, it & 1, TC_WAIT_NS);
+        if (!done) {
+            if (lane == 0) atomicExch(fault, 1);
+            done = tc_mbar_wait(mb, it & 1, TC_WAIT_NS);  // let the MMAs in flight finish before TMEM is freed
+        }
+        ok = __syncthreads_and(ok && done) != 0;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (!ok) break;
     }
-    if (t == 13 && threadIdx.x < cout) atomicAdd(&gb[threadIdx.x], bacc);
+    // partial sums of this CTA: warp w reads TMEM lanes 32w..32w+31 (MMA rows m)
+    if (ok) {
+        const int m = warp * 32 + lane;
+        const bool mine = m < 3 * COUTP_;
+        const int tx = m / COUTP_, o = m % COUTP_;
+#pragma unroll
+        for (int sl = 0; sl < 3; ++sl) {
+            float v[CINP_];
+            tmem_load<CINP_>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(sl * CINP_), v);
+            if (mine) {
+                const int t = tz * 9 + sl * 3 + tx;
+                float4 *dst = (float4 *)(part + (((size_t)blockIdx.x * 27 + t) * COUTP_ + o) * CINP_);
+#pragma unroll
+                for (int q = 0; q < CINP_ / 4; ++q)
+                    dst[q] = it > 0 ? make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3])
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NALLOC) : "memory");
+}
+
+// gW[t][o][c] (o < cout, c < cin) = sum over the CTAs' partial sums
+template <int CINP_, int COUTP_>
+__global__ void k_rnet_wgrad_sum(const float *__restrict__ part, int nparts, int cin, int cout, float *__restrict__ gW)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 27 * cout * cin) return;
+    const int c = i % cin, o = (i / cin) % cout, t = i / (cin * cout);
+    const float *p = part + ((size_t)t * COUTP_ + o) * CINP_ + c;
+    float sum = 0.0f;
+    for (int b = 0; b < nparts; ++b) sum += p[(size_t)b * 27 * COUTP_ * CINP_];
+    gW[i] = sum;
+}
+
+// gb[o] = sum_p dz[p][o]: per CTA a shared sum over a range of cells, then
+// one atomic per channel
+template <int COUTP_>
+__global__ void __launch_bounds__(256) k_rnet_bgrad(const float *__restrict__ dz, long long n, int cout,
+                                                    float *__restrict__ gb)
+{
+    __shared__ float s[COUTP_];
+    if (threadIdx.x < COUTP_) s[threadIdx.x] = 0.0f;
+    __syncthreads();
+    constexpr int PER = 256 / COUTP_;  // cells per pass of the CTA
+    const int o = threadIdx.x % COUTP_;
+    float acc = 0.0f;
+    for (long long p = (long long)blockIdx.x * PER + threadIdx.x / COUTP_; p < n; p += (long long)gridDim.x * PER)
+        acc += dz[p * COUTP_ + o];
+    atomicAdd(&s[o], acc);
+    __syncthreads();
+    if (threadIdx.x < cout) atomicAdd(&gb[threadIdx.x], s[threadIdx.x]);
 }
 
 __global__ void k_rnet_adam(float *__restrict__ P, float *__restrict__ M, float *__restrict__ Vv,
@@ -619,28 +643,6 @@ __global__ void k_rnet_adam(float *__restrict__ P, float *__restrict__ M, float 
     M[i] = m;
     Vv[i] = v;
     P[i] -= lr * (m * c1) / (sqrtf(v * c2) + 1e-8f);
-}
-
-// BF16 weights, padded to [27][COUTP][CINP] per layer, from the FP32 master parameters
-__global__ void k_rnet_cast(const float *__restrict__ P, __nv_bfloat16 *__restrict__ Wq)
-{
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= WQ_TOTAL) return;
-    long long j, po;
-    int cin, cout, cinp, coutp;
-    if (i < WO1) {
-        j = i, po = 0, cin = 6, cout = 32, cinp = 16, coutp = 32;
-    } else if (i < WO2) {
-        j = i - WO1, po = PO1, cin = 32, cout = 32, cinp = 32, coutp = 32;
-    } else if (i < WO3) {
-        j = i - WO2, po = PO2, cin = 32, cout = 32, cinp = 32, coutp = 32;
-    } else {
-        j = i - WO3, po = PO3, cin = 32, cout = 3, cinp = 32, coutp = 8;
-    }
-    const int cp = (int)(j % cinp), op = (int)((j / cinp) % coutp), t = (int)(j / (cinp * coutp));
-    float v = 0.0f;
-    if (cp < cin && op < cout) v = P[po + ((long long)t * cout + op) * cin + cp];
-    Wq[i] = __float2bfloat16_rn(v);
 }
 
 // the same weights in the tensor-core layers' shared-memory layout:
@@ -791,22 +793,19 @@ struct mmx_rnet {
     cudaStream_t s = nullptr;
     long long max_cells = 0;
     float *P = nullptr, *Pm = nullptr, *Pv = nullptr, *grad = nullptr;
-    __nv_bfloat16 *Wq = nullptr, *Wtc = nullptr, *Wtt = nullptr;
+    __nv_bfloat16 *Wtc = nullptr, *Wtt = nullptr;
     __nv_bfloat16 *dz3b = nullptr, *dzAb = nullptr, *dzBb = nullptr;  // BF16 copies of the output gradients
     __nv_bfloat16 *a[NLAYER] = {nullptr, nullptr, nullptr, nullptr};
     float *r = nullptr, *dz3 = nullptr, *dzA = nullptr, *dzB = nullptr;
     double *loss_d = nullptr;
     int *fault = nullptr;  // set by a tensor-core layer whose bounded wait ran out
     int nsm = 1;
-    int tc_nbuf = 1;       // MMX_RNET_NBUF: halo buffers per tensor-core CTA (1 or 2)
+    float *part = nullptr;   // weight gradient: partial sums [nsm][27][32][32] of the CTAs
     CUtensorMap tm[NLAYER];  // 5-D views of the layer inputs for the halo copies
     CUtensorMap tmg[3];      // the same for the gradients dz3b, dzAb, dzBb
-    bool simt_bwd = false;   // MMX_RNET_SIMT_BWD=1: the FP32 SIMT input-gradient kernels
     int tm_nx = 0, tm_ny = 0, tm_nz = 0;
     bool tm_ok = false;
-    bool require_tc = false;  // MMX_RNET_REQUIRE_TC=1: no fallback when the halo copies cannot be encoded
     int grid_cap = 0;         // MMX_RNET_GRID_CAP=n: at most n persistent CTAs (0: two per SM)
-    bool mma_sync = false; // MMX_RNET_MMA_SYNC=1: the mma.sync layers instead of tcgen05
     int step = 0;
     int nx = 0, ny = 0, nz = 0;
     std::string err;
@@ -829,29 +828,27 @@ int rfail(mmx_rnet *net, int code, const std::string &msg)
 std::once_flag smem_once;
 cudaError_t smem_status = cudaSuccess;
 
-template <int NB>
 cudaError_t set_tc_smem()
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<16, 32, 0, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)tc_smem(16, 32, NB))) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<16, 32, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tc_smem(16, 32))) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<32, 32, 0, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)tc_smem(32, 32, NB))) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<32, 32, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tc_smem(32, 32))) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<16, 32, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)tc_smem(16, 32, 1))) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<16, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tc_smem(16, 32))) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<32, 32, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)tc_smem(32, 32, 1))) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<32, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tc_smem(32, 32))) != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(k_rnet_conv_tc<32, 16, 1, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tc_smem(32, 16, NB));
+    return cudaFuncSetAttribute(k_rnet_conv_tc<32, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tc_smem(32, 16));
 }
 
-// the four layers on the tensor-core kernels; NB halo buffers per CTA
-// (1: two CTAs per SM overlap each other; 2: one CTA per SM overlaps its own copies)
-template <int NB>
+// the four layers on the tensor-core kernels (two persistent CTAs per SM
+// overlap each other's halo copies)
 void forward_tc(mmx_rnet *net, int nx, int ny, int nz);
 
 // 5-D view (8 channels, k-chunk, x, y, z) of channels-last BF16 activations
@@ -897,22 +894,7 @@ bool halo_maps(mmx_rnet *net, int nx, int ny, int nz)
     return ok;
 }
 
-cudaError_t raise_conv_smem_once()
-{
-    cudaError_t e;
-    if ((e = set_tc_smem<1>()) != cudaSuccess) return e;
-    if ((e = set_tc_smem<2>()) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_rnet_conv<16, 32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)conv_smem<16>())) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_rnet_conv<32, 32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)conv_smem<32>())) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_rnet_conv<32, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)conv_smem<32>())) != cudaSuccess)
-        return e;
-    return cudaSuccess;
-}
+cudaError_t raise_conv_smem_once() { return set_tc_smem(); }
 
 // the shared-memory limits of every layer kernel, raised once per process
 cudaError_t raise_conv_smem()
@@ -937,51 +919,54 @@ int check_mesh(mmx_rnet *net, int nx, int ny, int nz)
     return MMX_OK;
 }
 
-// forward through all layers from the packed input a[0]; output in net->r
-void forward_layers(mmx_rnet *net, int nx, int ny, int nz)
+// forward through all layers from the packed input a[0]; output in net->r.
+// MMX_ERR_CUDA when the tensor maps of the halo copies cannot be encoded.
+int forward_layers(mmx_rnet *net, int nx, int ny, int nz)
 {
-    if (!net->mma_sync && halo_maps(net, nx, ny, nz)) {
-        if (net->tc_nbuf == 2)
-            forward_tc<2>(net, nx, ny, nz);
-        else
-            forward_tc<1>(net, nx, ny, nz);
-        return;
-    }
-    const dim3 grid((nx + RN_TX - 1) / RN_TX, (ny + RN_TY - 1) / RN_TY, nz);
-    k_rnet_conv<16, 32, false><<<grid, 128, conv_smem<16>(), net->s>>>(net->a[0], net->Wq + w_off(0),
-                                                                       net->P + p_off(0) + 27 * 32 * 6, 32,
-                                                                       net->a[1], nx, ny, nz);
-    k_rnet_conv<32, 32, false><<<grid, 128, conv_smem<32>(), net->s>>>(net->a[1], net->Wq + w_off(1),
-                                                                       net->P + p_off(1) + 27 * 32 * 32, 32,
-                                                                       net->a[2], nx, ny, nz);
-    k_rnet_conv<32, 32, false><<<grid, 128, conv_smem<32>(), net->s>>>(net->a[2], net->Wq + w_off(2),
-                                                                       net->P + p_off(2) + 27 * 32 * 32, 32,
-                                                                       net->a[3], nx, ny, nz);
-    k_rnet_conv<32, 8, true><<<grid, 128, conv_smem<32>(), net->s>>>(net->a[3], net->Wq + w_off(3),
-                                                                     net->P + p_off(3) + 27 * 3 * 32, 3, net->r,
-                                                                     nx, ny, nz);
+    if (!halo_maps(net, nx, ny, nz))
+        return rfail(net, MMX_ERR_CUDA, "the tensor maps of the layer inputs could not be encoded");
+    forward_tc(net, nx, ny, nz);
+    return MMX_OK;
 }
 
-template <int NB>
 void forward_tc(mmx_rnet *net, int nx, int ny, int nz)
 {
     const long long tiles = (long long)((nx + TC_TX - 1) / TC_TX) * ((ny + RN_TY - 1) / RN_TY) * nz;
-    long long cap = (long long)net->nsm * (NB == 1 ? 2 : 1);
+    long long cap = (long long)net->nsm * 2;
     if (net->grid_cap > 0 && net->grid_cap < cap) cap = net->grid_cap;
     const dim3 g((unsigned)(tiles < cap ? tiles : cap));
-    k_rnet_conv_tc<16, 32, 0, NB><<<g, 128, tc_smem(16, 32, NB), net->s>>>(
+    k_rnet_conv_tc<16, 32, 0><<<g, 128, tc_smem(16, 32), net->s>>>(
         net->tm[0], net->Wtc, net->P + p_off(0) + 27 * 32 * 6, 32, net->a[1], nx, ny, nz, net->fault, nullptr, nullptr);
-    k_rnet_conv_tc<32, 32, 0, NB><<<g, 128, tc_smem(32, 32, NB), net->s>>>(
+    k_rnet_conv_tc<32, 32, 0><<<g, 128, tc_smem(32, 32), net->s>>>(
         net->tm[1], net->Wtc + TCO1, net->P + p_off(1) + 27 * 32 * 32, 32, net->a[2], nx, ny, nz, net->fault, nullptr, nullptr);
-    k_rnet_conv_tc<32, 32, 0, NB><<<g, 128, tc_smem(32, 32, NB), net->s>>>(
+    k_rnet_conv_tc<32, 32, 0><<<g, 128, tc_smem(32, 32), net->s>>>(
         net->tm[2], net->Wtc + TCO2, net->P + p_off(2) + 27 * 32 * 32, 32, net->a[3], nx, ny, nz, net->fault, nullptr, nullptr);
-    k_rnet_conv_tc<32, 16, 1, NB><<<g, 128, tc_smem(32, 16, NB), net->s>>>(
+    k_rnet_conv_tc<32, 16, 1><<<g, 128, tc_smem(32, 16), net->s>>>(
         net->tm[3], net->Wtc + TCO3, net->P + p_off(3) + 27 * 3 * 32, 3, net->r, nx, ny, nz, net->fault, nullptr, nullptr);
+}
+
+// weight and bias gradients of one layer into gW ([27][cout][cin], then
+// b[cout]): the tensor-core partial sums per CTA, their sum, the bias sum
+template <int CINP_, int COUTP_>
+void wgrad_layer(mmx_rnet *net, const float *dz, const __nv_bfloat16 *A, int cin, int cout, float *gW, int nx, int ny,
+                 int nz)
+{
+    const long long n = (long long)nx * ny * nz;
+    const long long tiles = (long long)((nx + WG_TC - 1) / WG_TC) * ny * nz;
+    long long g = net->nsm;
+    if (net->grid_cap > 0 && net->grid_cap < g) g = net->grid_cap;
+    if (tiles < g) g = tiles;
+    k_rnet_wgrad_tc<CINP_, COUTP_><<<dim3((unsigned)g, 3), 128, wg_smem<CINP_, COUTP_>(), net->s>>>(
+        dz, A, net->part, nx, ny, nz, net->fault);
+    const int nw = 27 * cout * cin;
+    k_rnet_wgrad_sum<CINP_, COUTP_><<<(unsigned)((nw + 255) / 256), 256, 0, net->s>>>(net->part, (int)g, cin, cout,
+                                                                                      gW);
+    const long long nb = (n + 1023) / 1024;
+    k_rnet_bgrad<COUTP_><<<(unsigned)(nb < 1024 ? nb : 1024), 256, 0, net->s>>>(dz, n, cout, gW + nw);
 }
 
 int refresh_weights(mmx_rnet *net)
 {
-    k_rnet_cast<<<(unsigned)((WQ_TOTAL + 255) / 256), 256, 0, net->s>>>(net->P, net->Wq);
     k_rnet_cast_tc<<<(unsigned)((TC_TOTAL + 255) / 256), 256, 0, net->s>>>(net->P, net->Wtc);
     k_rnet_cast_tc_t<<<(unsigned)((TT_TOTAL + 255) / 256), 256, 0, net->s>>>(net->P, net->Wtt);
     RCK(cudaGetLastError());
@@ -1040,7 +1025,6 @@ extern "C" int mmx_rnet_create(long long max_cells, void *cuda_stream, mmx_rnet 
     const size_t P = MMX_RNET_PARAMS * sizeof(float);
     bool ok = cudaMalloc(&net->P, P) == cudaSuccess && cudaMalloc(&net->Pm, P) == cudaSuccess &&
               cudaMalloc(&net->Pv, P) == cudaSuccess && cudaMalloc(&net->grad, P) == cudaSuccess &&
-              cudaMalloc(&net->Wq, WQ_TOTAL * sizeof(__nv_bfloat16)) == cudaSuccess &&
               cudaMalloc(&net->Wtc, TC_TOTAL * sizeof(__nv_bfloat16)) == cudaSuccess &&
               cudaMalloc(&net->Wtt, TT_TOTAL * sizeof(__nv_bfloat16)) == cudaSuccess &&
               cudaMalloc(&net->dz3b, max_cells * 16 * sizeof(__nv_bfloat16)) == cudaSuccess &&
@@ -1064,16 +1048,13 @@ extern "C" int mmx_rnet_create(long long max_cells, void *cuda_stream, mmx_rnet 
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&net->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || net->nsm < 1)
         net->nsm = 1;
-    const char *ms = getenv("MMX_RNET_MMA_SYNC");
-    net->mma_sync = ms && atoi(ms) != 0;
-    const char *sb = getenv("MMX_RNET_SIMT_BWD");
-    net->simt_bwd = sb && atoi(sb) != 0;
+    if (cudaMalloc(&net->part, (size_t)net->nsm * 27 * 32 * 32 * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        mmx_rnet_destroy(net);
+        return MMX_ERR_OOM;
+    }
     const char *gcap = getenv("MMX_RNET_GRID_CAP");
     net->grid_cap = gcap ? atoi(gcap) : 0;
-    const char *rq = getenv("MMX_RNET_REQUIRE_TC");
-    net->require_tc = rq && atoi(rq) != 0;
-    const char *nb = getenv("MMX_RNET_NBUF");
-    net->tc_nbuf = (nb && atoi(nb) == 2) ? 2 : 1;
     if (raise_conv_smem() != cudaSuccess || cudaMemsetAsync(net->fault, 0, sizeof(int), net->s) != cudaSuccess ||
         cudaMemsetAsync(net->P, 0, P, net->s) != cudaSuccess ||
         cudaMemsetAsync(net->Pm, 0, P, net->s) != cudaSuccess ||
@@ -1113,10 +1094,8 @@ extern "C" int mmx_rnet_forward(mmx_rnet *net, int nx, int ny, int nz, const flo
     if (!net || !x_dev) return rfail(net, MMX_ERR_ARG, "NULL argument");
     if (int rc = check_mesh(net, nx, ny, nz)) return rc;
     const long long n = (long long)nx * ny * nz;
-    if (!net->mma_sync && net->require_tc && !halo_maps(net, nx, ny, nz))
-        return rfail(net, MMX_ERR_ARG, "the halo tensor maps cannot be encoded for this mesh");
     k_rnet_pack<<<(unsigned)((n + 255) / 256), 256, 0, net->s>>>(x_dev, n, net->a[0]);
-    forward_layers(net, nx, ny, nz);
+    if (int rc = forward_layers(net, nx, ny, nz)) return rc;
     if (r_dev) RCK(cudaMemcpyAsync(r_dev, net->r, n * 3 * sizeof(float), cudaMemcpyDeviceToDevice, net->s));
     RCK(cudaGetLastError());
     net->nx = nx;
@@ -1137,45 +1116,29 @@ extern "C" int mmx_rnet_train_step(mmx_rnet *net, int nx, int ny, int nz, const 
     RCK(cudaMemsetAsync(net->grad, 0, MMX_RNET_PARAMS * sizeof(float), s));
     k_rnet_loss<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(net->r, target_dev, n, net->dz3, net->dz3b,
                                                            net->loss_d);
-    // input gradients on the tensor cores (dz rounded to BF16 where it enters), or FP32 SIMT
-    const bool tc_bwd = !net->simt_bwd && halo_maps(net, nx, ny, nz);
+    // input gradients on the tensor cores (dz rounded to BF16 where it enters);
+    // weight gradients on the tensor cores (dz as a BF16 pair hi + lo)
+    if (!halo_maps(net, nx, ny, nz))
+        return rfail(net, MMX_ERR_CUDA, "the tensor maps of the layer inputs could not be encoded");
     const long long tiles = (long long)((nx + TC_TX - 1) / TC_TX) * ((ny + RN_TY - 1) / RN_TY) * nz;
     long long gcap_bwd = 2LL * net->nsm;
     if (net->grid_cap > 0 && net->grid_cap < gcap_bwd) gcap_bwd = net->grid_cap;
     const dim3 gt((unsigned)(tiles < gcap_bwd ? tiles : gcap_bwd));
-    const int chunk = 1024;
-    const dim3 wg((unsigned)((n + chunk - 1) / chunk), 27);
-    const unsigned dg = (unsigned)((n + 7) / 8);
     float *G = net->grad;
     // layer 3 (32 -> 3)
-    k_rnet_wgrad<32, 8><<<wg, 256, 0, s>>>(net->dz3, net->a[3], 32, 3, G + p_off(3), G + p_off(3) + 27 * 3 * 32,
-                                           nx, ny, nz, chunk);
-    if (tc_bwd)
-        k_rnet_conv_tc<16, 32, 2, 1><<<gt, 128, tc_smem(16, 32, 1), s>>>(net->tmg[0], net->Wtt, nullptr, 32, net->dzA,
-                                                                         nx, ny, nz, net->fault, net->a[3], net->dzAb);
-    else
-        k_rnet_dgrad<8><<<dg, 256, 0, s>>>(net->dz3, net->Wq + w_off(3), 3, net->a[3], net->dzA, nx, ny, nz);
+    wgrad_layer<32, 8>(net, net->dz3, net->a[3], 32, 3, G + p_off(3), nx, ny, nz);
+    k_rnet_conv_tc<16, 32, 2><<<gt, 128, tc_smem(16, 32), s>>>(net->tmg[0], net->Wtt, nullptr, 32, net->dzA, nx, ny,
+                                                               nz, net->fault, net->a[3], net->dzAb);
     // layer 2
-    k_rnet_wgrad<32, 32><<<wg, 256, 0, s>>>(net->dzA, net->a[2], 32, 32, G + p_off(2),
-                                            G + p_off(2) + 27 * 32 * 32, nx, ny, nz, chunk);
-    if (tc_bwd)
-        k_rnet_conv_tc<32, 32, 2, 1><<<gt, 128, tc_smem(32, 32, 1), s>>>(net->tmg[1], net->Wtt + TT2, nullptr, 32,
-                                                                         net->dzB, nx, ny, nz, net->fault, net->a[2],
-                                                                         net->dzBb);
-    else
-        k_rnet_dgrad<32><<<dg, 256, 0, s>>>(net->dzA, net->Wq + w_off(2), 32, net->a[2], net->dzB, nx, ny, nz);
+    wgrad_layer<32, 32>(net, net->dzA, net->a[2], 32, 32, G + p_off(2), nx, ny, nz);
+    k_rnet_conv_tc<32, 32, 2><<<gt, 128, tc_smem(32, 32), s>>>(net->tmg[1], net->Wtt + TT2, nullptr, 32, net->dzB,
+                                                               nx, ny, nz, net->fault, net->a[2], net->dzBb);
     // layer 1
-    k_rnet_wgrad<32, 32><<<wg, 256, 0, s>>>(net->dzB, net->a[1], 32, 32, G + p_off(1),
-                                            G + p_off(1) + 27 * 32 * 32, nx, ny, nz, chunk);
-    if (tc_bwd)
-        k_rnet_conv_tc<32, 32, 2, 1><<<gt, 128, tc_smem(32, 32, 1), s>>>(net->tmg[2], net->Wtt + TT1, nullptr, 32,
-                                                                         net->dzA, nx, ny, nz, net->fault, net->a[1],
-                                                                         net->dzAb);
-    else
-        k_rnet_dgrad<32><<<dg, 256, 0, s>>>(net->dzB, net->Wq + w_off(1), 32, net->a[1], net->dzA, nx, ny, nz);
+    wgrad_layer<32, 32>(net, net->dzB, net->a[1], 32, 32, G + p_off(1), nx, ny, nz);
+    k_rnet_conv_tc<32, 32, 2><<<gt, 128, tc_smem(32, 32), s>>>(net->tmg[2], net->Wtt + TT1, nullptr, 32, net->dzA,
+                                                               nx, ny, nz, net->fault, net->a[1], net->dzAb);
     // layer 0 (6 -> 32; input padded to 16 channels)
-    k_rnet_wgrad<16, 32><<<wg, 256, 0, s>>>(net->dzA, net->a[0], 6, 32, G + p_off(0), G + p_off(0) + 27 * 32 * 6,
-                                            nx, ny, nz, chunk);
+    wgrad_layer<16, 32>(net, net->dzA, net->a[0], 6, 32, G + p_off(0), nx, ny, nz);
     net->step++;
     const double c1 = 1.0 / (1.0 - pow(0.9, net->step)), c2 = 1.0 / (1.0 - pow(0.999, net->step));
     k_rnet_adam<<<(MMX_RNET_PARAMS + 255) / 256, 256, 0, s>>>(net->P, net->Pm, net->Pv, G, MMX_RNET_PARAMS, lr,
@@ -1222,7 +1185,7 @@ extern "C" void mmx_rnet_destroy(mmx_rnet *net)
 {
     if (!net) return;
     if (net->s) cudaStreamSynchronize(net->s);
-    void *bufs[] = {net->P,   net->Pm,  net->Pv,  net->grad, net->Wq,  net->a[0],  net->a[1], net->a[2],
+    void *bufs[] = {net->P,   net->Pm,  net->Pv,  net->grad, net->part, net->a[0],  net->a[1], net->a[2],
                     net->a[3], net->r, net->dz3, net->dzA,  net->dzB, net->loss_d, net->fault, net->Wtc,
                     net->Wtt,  net->dz3b, net->dzAb, net->dzBb};
     for (void *b : bufs)
@@ -1270,7 +1233,7 @@ int mmxk_rnet_stage(mmx_rnet *net, mmx_ctx *c, cudaStream_t s, int k)
     k_res_stage_in<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->st, k, c->ctl.p + 1, (const float *)c->hist,
                                                              (const float *)c->Y[k & 1], n, (float)(1.0 / c->mat.Ms),
                                                              (float *)c->G, net->a[0], 1);
-    forward_layers(net, c->nx, c->ny, c->nz);
+    (void)forward_layers(net, c->nx, c->ny, c->nz);  // cannot fail: the maps were encoded at attach time
     k_res_stage_out<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(c->st, net->r, 3 * n, (float)c->mat.Ms,
                                                                   (float *)c->G);
     net->s = keep;
@@ -1291,7 +1254,7 @@ int mmxk_rnet_check(mmx_rnet *net, mmx_ctx *c, cudaStream_t s, int k)
     k_res_stage_in<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->st, k, c->ctl.p + 1, (const float *)c->hist,
                                                              (const float *)c->Y[k & 1], n, (float)(1.0 / c->mat.Ms),
                                                              (float *)c->Gc, net->a[0], 0);
-    forward_layers(net, c->nx, c->ny, c->nz);
+    (void)forward_layers(net, c->nx, c->ny, c->nz);  // cannot fail: the maps were encoded at attach time
     k_res_check_cmp<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(c->st, net->r, (const float *)c->Gc,
                                                                   (const float *)c->G, 3 * n, (float)c->mat.Ms);
     net->s = keep;
@@ -1317,6 +1280,10 @@ extern "C" int mmx_set_residual(mmx_ctx *c, mmx_rnet *net)
         if (c->n > net->max_cells) {
             c->err = "mmx_set_residual: the mesh has more cells than the net was created for";
             return MMX_ERR_ARG;
+        }
+        if (!halo_maps(net, c->nx, c->ny, c->nz)) {
+            c->err = "mmx_set_residual: the tensor maps of the net's layer inputs could not be encoded";
+            return MMX_ERR_CUDA;
         }
     }
     cudaError_t e = cudaStreamSynchronize(c->stream);
