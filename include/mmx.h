@@ -173,22 +173,20 @@ int mmx_get_profile(mmx_ctx *ctx, double *ms, long long *launches);
 /* Configuration of the exact demag evaluation chosen for this context.  At
  * mmx_create the library times the candidate configurations of its FFT
  * passes on the context's own buffers and keeps the fastest (unless the
- * environment forces one: MMX_AUTOTUNE=0, MMX_FORCE_SPLIT, MMX_FORCE_CLUSTER,
- * MMX_NO_TMA, MMX_TROWS); results are cached per mesh and precision for the
- * life of the process.  The candidates:
+ * environment forces one: MMX_AUTOTUNE=0, MMX_FORCE_SPLIT, MMX_NO_TMA,
+ * MMX_TROWS); results are cached per mesh and precision for the life of the
+ * process.  The candidates:
  *   x_rows   rows of the x transforms per CTA in the plain x passes (2-16);
  *   xi_tma   inverse x pass fed by tensor-memory-access tile copies (FP32);
+ * and, set by the mesh:
  *   yz_pass  0: one CTA transforms a whole y-z column (meshes where it
- *            fits); 1: split y / z passes through an HBM y spectrum;
- *            2: one thread-block cluster of cluster_ctas CTAs per column,
- *            the y spectrum kept in distributed shared memory (FP32).
+ *            fits); 1: split y / z passes through an HBM y spectrum.
  * demag_us is the timed evaluation of the chosen configuration (0 when not
  * tuned); kernels_per_demag the launches of one evaluation. */
 typedef struct {
     int yz_pass;
     int x_rows;
     int xi_tma;
-    int cluster_ctas;
     int tuned;
     int kernels_per_demag;
     double demag_us;

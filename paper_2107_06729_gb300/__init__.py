@@ -65,7 +65,7 @@ class mmx_stats(ctypes.Structure):
 
 class mmx_plan(ctypes.Structure):
     _fields_ = [("yz_pass", ctypes.c_int), ("x_rows", ctypes.c_int), ("xi_tma", ctypes.c_int),
-                ("cluster_ctas", ctypes.c_int), ("tuned", ctypes.c_int), ("kernels_per_demag", ctypes.c_int),
+                ("tuned", ctypes.c_int), ("kernels_per_demag", ctypes.c_int),
                 ("demag_us", ctypes.c_double)]
 
 

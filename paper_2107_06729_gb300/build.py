@@ -15,7 +15,7 @@ LIB = os.path.join(HERE, "libmmx.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["kernels.cu", "stage_f32.cu", "stage_f64.cu", "fft_fused_f32.cu", "fft_fused_f64.cu", "fft_split.cu", "fft_pipe.cu",
-           "fft_cluster.cu", "mmx_api.cu", "static_demag.cu", "rnet.cu", "tensor_host.cpp"]
+           "mmx_api.cu", "static_demag.cu", "rnet.cu", "tensor_host.cpp"]
 
 
 def _deps():

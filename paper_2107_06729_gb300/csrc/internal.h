@@ -139,10 +139,7 @@ struct mmx_ctx {
     bool r4 = false;      // the 1024-point y passes run as four-step register transforms
     bool r4x = false;     // ... and the 1024-point x passes
     bool split;  // the y-z column does not fit one CTA: YF, ZM, YI instead of YZ
-    bool cluster;     // ... and a thread-block cluster per kx column runs it instead (YZC)
-    int yzc_C, yzc_W; // cluster size and z sub-tile width of YZC
     int nd;           // kernels per exact demag evaluation
-    bool pdl;         // kernels launched as programmatic dependent launches
     bool allow_tma;   // TMA passes allowed (the context owns a fault word)
     bool stall_test;  // MMX_TEST_STALL_TMA: the TMA XI's waits run out (failure-path test)
     bool xi_tma_ok;   // the TMA XI is set up for this mesh
@@ -217,9 +214,6 @@ int mmxk_default_trows(const mmx_ctx *c);
 // registers); taller meshes take the split passes
 int mmxk_yz_max_pz(const mmx_ctx *c);
 int mmxk_set_trows(mmx_ctx *c, int trows);
-// decides whether the cluster-fused y-z pass runs a split-size mesh (sets
-// cluster, yzc_C, yzc_W); 0 or MMX_ERR_CUDA
-int mmxk_cluster_plan(mmx_ctx *c);
 // fills DevState::coef for the attempt described by the device state
 void mmxk_prepare(mmx_ctx *c, cudaStream_t s);
 // batched runs: the same preparation as an explicit graph node, and a node

@@ -115,49 +115,6 @@ int mmxk_set_trows(mmx_ctx *c, int tr)
     return 0;
 }
 
-int mmxk_cluster_plan(mmx_ctx *c)
-{
-    c->cluster = false;
-    c->yzc_C = 0;
-    c->yzc_W = 0;
-    if (c->prec != MMX_FP32_MIXED || !mmxk_yzc_kernel(c->Py, c->Pz)) return 0;
-    int dev = 0, ok = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&ok, cudaDevAttrClusterLaunch, dev) != cudaSuccess || !ok) {
-        cudaGetLastError();
-        return 0;
-    }
-    const void *fn = mmxk_yzc_kernel(c->Py, c->Pz);
-    for (int C = 2; C <= 8 && c->nz % C == 0; C *= 2) {
-        const int W = std::min(64, c->Py / C);
-        const size_t smem = yzc_smem(c, C, W);
-        if (smem > 110 * 1024) continue;
-        if (!raise_smem_limit(fn, smem)) return MMX_ERR_CUDA;
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3((unsigned)(c->nx * C));
-        cfg.blockDim = dim3((unsigned)yzc_threads(W));
-        cfg.dynamicSmemBytes = smem;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = (unsigned)C;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess) {
-            cudaGetLastError();
-            return 0;
-        }
-        if (nclusters < 1) continue;
-        c->cluster = true;
-        c->yzc_C = C;
-        c->yzc_W = W;
-        return 0;
-    }
-    return 0;
-}
-
 size_t mmxk_split_smem_bytes(const mmx_ctx *c)
 {
     if (c->prec == MMX_FP64) return std::max(yf_smem<double>(c, split_rows<double>(c)), zm_smem<double>(c));

@@ -27,7 +27,6 @@
 // self term), the Landau-Lifshitz torque, and the next stage input.  The
 // last stage forms the propagated and embedded solutions, renormalises,
 // reduces the error norm, and its last CTA runs the controller of Eq. 5.
-#include <cooperative_groups.h>
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -47,8 +46,6 @@
 enum MmxKernelKind { K_XF, K_XI, K_YZ, K_YF, K_YI, K_ZM, K_XFP, K_YFP, K_YIP, K_ZMP, K_ZMR, K_XIT, K_YF4, K_YI4, K_XF4, K_XI4 };
 // pointer to the instance of `kind` for precision (f64) and transform length L
 const void *mmxk_kernel(int kind, bool f64, int L);
-// the cluster-fused y-z pass (FP32) for lengths Py and Pz, or NULL
-const void *mmxk_yzc_kernel(int Py, int Pz);
 
 namespace {
 
@@ -70,16 +67,6 @@ template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b)
     return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 template <typename T> __device__ __forceinline__ cx<T> cscale(T s, cx<T> a) { return mk(s * a.x, s * a.y); }
-
-// Programmatic dependent launch: wait until the kernel before this one in
-// the stream has completed and its writes are visible (a no-op for a launch
-// without the attribute), then allow the next kernel's CTAs to be scheduled,
-// so that they are resident and waiting here when this kernel ends.
-__device__ __forceinline__ void pdl_entry()
-{
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-}
 
 // Twiddles w^r, r = 1..R-1, of one radix-R butterfly.  FP64 reads each from
 // the table; FP32 reads w^1 only and forms the powers by complex products
@@ -617,7 +604,6 @@ int items_for(int L, int threads)
 template <typename T, int PX>
 __global__ void __launch_bounds__(256, 2) k_xf(const XArgs<T> a)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
     if (a.st) {
@@ -714,7 +700,6 @@ __device__ __forceinline__ void xi_store(const Pad<T> work, const XArgs<T> &a, T
 template <typename T, int PX>
 __global__ void __launch_bounds__(256, 2) k_xi(const XArgs<T> a)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
     int head = 0;
@@ -897,7 +882,6 @@ constexpr unsigned long long XIT_WAIT_NS = 2000000000ULL;  // 2 s
 template <typename T, int PX, bool R4 = false>
 __global__ void __launch_bounds__(32 * XIT_ROWS / 2, 3) k_xi_t(const XArgs<T> a, const __grid_constant__ CUtensorMap tm)
 {
-    pdl_entry();
     static_assert(sizeof(T) == 4, "TMA XI: FP32 spectrum (8-byte elements)");
     extern __shared__ __align__(1024) unsigned char smtma[];
     int head = 0;
@@ -1070,7 +1054,6 @@ __device__ __forceinline__ void apply_K(const T k[6], cx<T> mx, cx<T> my, cx<T> 
 template <typename T, int PY>
 __global__ void __launch_bounds__(YZ_THREADS, 2) k_yz(const YZArgs<T> a)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> B{reinterpret_cast<cx<T> *>(smraw), 0};
     if (a.st) {
@@ -1204,7 +1187,6 @@ template <typename T> struct SplitArgs {
 template <typename T, int PY>
 __global__ void __launch_bounds__(256, 2) k_yf(const SplitArgs<T> a)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
     if (a.st) {
@@ -1254,7 +1236,6 @@ __global__ void __launch_bounds__(256, 2) k_yf(const SplitArgs<T> a)
 template <typename T, int PZ>
 __global__ void __launch_bounds__(YZ_THREADS) k_zm(const SplitArgs<T> a)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> B{reinterpret_cast<cx<T> *>(smraw), 0};
     if (a.st) {
@@ -1348,7 +1329,6 @@ __global__ void __launch_bounds__(YZ_THREADS) k_zm(const SplitArgs<T> a)
 template <typename T, int PY>
 __global__ void __launch_bounds__(256, 2) k_yi(const SplitArgs<T> a)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     const Pad<T> sm{reinterpret_cast<cx<T> *>(smraw), 0};
     if (a.st) {
@@ -1454,7 +1434,6 @@ template <typename T> struct YIView {
 template <typename T, int PX>
 __global__ void __launch_bounds__(256, 2) k_xf_p(const XArgs<T> a)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     if (a.st) {
         if (a.st->done) return;
@@ -1506,7 +1485,6 @@ __global__ void __launch_bounds__(256, 2) k_xf_p(const XArgs<T> a)
 template <typename T, int PY>
 __global__ void __launch_bounds__(256, 2) k_yf_p(const SplitArgs<T> a)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     if (a.st) {
         if (a.st->done) return;
@@ -1563,7 +1541,6 @@ __global__ void __launch_bounds__(256, 2) k_yf_p(const SplitArgs<T> a)
 template <typename T, int PY>
 __global__ void __launch_bounds__(256, 2) k_yi_p(const SplitArgs<T> a)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     if (a.st) {
         if (a.st->done) return;
@@ -1613,7 +1590,6 @@ __global__ void __launch_bounds__(256, 2) k_yi_p(const SplitArgs<T> a)
 template <typename T>
 __global__ void __launch_bounds__(32 * R4_WARPS, 4) k_yf4(const SplitArgs<T> a)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     if (a.st) {
         if (a.st->done) return;
@@ -1667,7 +1643,6 @@ __global__ void __launch_bounds__(32 * R4_WARPS, 4) k_yf4(const SplitArgs<T> a)
 template <typename T>
 __global__ void __launch_bounds__(32 * R4_WARPS, 4) k_yi4(const SplitArgs<T> a)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     if (a.st) {
         if (a.st->done) return;
@@ -1718,7 +1693,6 @@ constexpr size_t xf4_smem()
 template <typename T>
 __global__ void __launch_bounds__(32 * XF4_ROWS / 2, 2) k_xf4(const XArgs<T> a)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     if (a.st) {
         if (a.st->done) return;
@@ -1784,7 +1758,6 @@ __global__ void __launch_bounds__(32 * XF4_ROWS / 2, 2) k_xf4(const XArgs<T> a)
 template <typename T, int PZ>
 __global__ void __launch_bounds__(YZ_THREADS, 2) k_zm_p(const SplitArgs<T> a)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     if (a.st) {
         if (a.st->done) return;
@@ -1893,7 +1866,6 @@ __global__ void __launch_bounds__(YZ_THREADS, 2) k_zm_p(const SplitArgs<T> a)
 template <typename T, int PZ>
 __global__ void __launch_bounds__(192, 4) k_zm_r(const SplitArgs<T> a)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     cx<T> *B = reinterpret_cast<cx<T> *>(smraw);
     if (a.st) {
@@ -1988,169 +1960,6 @@ __global__ void __launch_bounds__(192, 4) k_zm_r(const SplitArgs<T> a)
 #pragma unroll
     for (int z = 0; z < PZ; ++z)
         if (z < PZ / 2) g[(size_t)z * Py] = v[z];
-}
-
-// ---------------------------------------------- cluster-fused y-z pass (YZC)
-// For meshes whose y-z column does not fit one CTA.  A cluster of C CTAs
-// takes one kx column.  CTA j holds the rows (c nz + z) in [j RC, (j+1) RC)
-// (RC = 3 nz / C) in shared memory and transforms them along y (the packed
-// kx = 0 column is then separated into its two real-x spectra, A in the slots
-// below Py/2 and B above, as in YF).  It then owns the ky slots
-// [j Py/C, (j+1) Py/C): per sub-tile of W slots, each thread gathers one
-// (c, ky) column over z from the rows of all CTAs through distributed shared
-// memory, transforms it along z in registers, the tensor multiply runs on a
-// shared tile, and the inverse z transforms are written back in place.  Last,
-// every CTA recombines (kx = 0) and transforms its rows back along y.  The
-// y spectrum never leaves the cluster: one read and one write of the x
-// spectrum per evaluation, plus the tensor.
-template <typename T, int PY, int PZ>
-__global__ void __launch_bounds__(192, 2) k_yzc(const SplitArgs<T> a)
-{
-    pdl_entry();
-    namespace cg = cooperative_groups;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    cg::cluster_group cl = cg::this_cluster();
-    if (a.st) {
-        // the state is not written during an evaluation: every CTA of the
-        // cluster takes the same decision, before any cluster barrier
-        if (a.st->done) return;
-        if (a.stage0 && a.st->f1_valid) return;
-    }
-    const int C = (int)cl.num_blocks(), j = (int)cl.block_rank();
-    const int RC = a.ry, W = a.W, nz = a.nz, ny = a.ny;
-    const int kx = blockIdx.x / C;
-    cx<T> *ybuf = reinterpret_cast<cx<T> *>(smraw);
-    cx<T> *B = ybuf + padded_words((size_t)RC * PY);
-    const Pad<T> Y{ybuf, 0};
-    constexpr int half = PY / 2;
-    const int wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    cx<T> *S = a.S + (size_t)kx * a.rows + (size_t)j * RC * ny;
-    const int lgny = ilog2(ny);
-
-    // 1. own rows, forward along y (input zero above ny)
-    for (int idx = threadIdx.x; idx < RC * ny; idx += blockDim.x) {
-        const int r = idx >> lgny, y = idx & (ny - 1);
-        Y[r * PY + y] = S[idx];
-    }
-    __syncthreads();
-    for (int r = wp; r < RC; r += nw) WarpFFT<T, false, PY, 1>::run(Y.at(r * PY), 1, a.twy, true, false);
-    if (kx == 0) {
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < RC * (half - 1); idx += blockDim.x) {
-            const int r = idx / (half - 1), q = 1 + idx - r * (half - 1);
-            const Pad<T> u = Y.at(r * PY);
-            const cx<T> z = u[q], zm = u[PY - q];
-            u[q] = mk((T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y));       // A(q)
-            u[PY - q] = mk((T)0.5 * (z.y + zm.y), (T)0.5 * (zm.x - z.x));  // B(q)
-        }
-    }
-    cl.sync();
-
-    // 2. the owned ky slots: z transform, tensor multiply, inverse z
-    const int lgW = ilog2(W), plane = PZ * W, Wc = PY / C;
-    const bool zt = threadIdx.x < 3 * W;
-    const int c = zt ? (int)threadIdx.x >> lgW : 0, ww = (int)threadIdx.x & (W - 1);
-    for (int s0 = j * Wc; s0 < (j + 1) * Wc; s0 += W) {
-        const int slot = s0 + ww;
-        cx<T> v[PZ];
-        if (zt) {
-#pragma unroll
-            for (int z = 0; z < PZ; ++z) {
-                if (z < PZ / 2) {  // Pz = 2 nz
-                    const int row = c * nz + z, own = row / RC, lr = row - own * RC;
-                    const Pad<T> R{cl.map_shared_rank(ybuf, own), 0};
-                    v[z] = R[lr * PY + slot];
-                } else {
-                    v[z] = mk<T>(0, 0);
-                }
-            }
-            RegFFT<T, PZ, 1, false>::run(v, a.twz);
-#pragma unroll
-            for (int kz = 0; kz < PZ; ++kz) B[c * plane + kz * W + ww] = v[kz];
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int q = threadIdx.x; q < plane; q += blockDim.x) {
-            const int qw = q & (W - 1), kz = q >> lgW, sl = s0 + qw;
-            if (kx != 0 || (sl != 0 && sl != half)) {
-                T k6[6];
-                if (kx != 0)
-                    load_K(a.K, kx, a.Hy, a.Hz, PY, PZ, sl, kz, k6);
-                else if (sl < half)
-                    load_K(a.K, 0, a.Hy, a.Hz, PY, PZ, sl, kz, k6);
-                else
-                    load_K(a.K, a.nx, a.Hy, a.Hz, PY, PZ, PY - sl, kz, k6);
-                cx<T> hx, hy, hz;
-                apply_K(k6, B[q], B[plane + q], B[2 * plane + q], hx, hy, hz);
-                B[q] = hx;
-                B[plane + q] = hy;
-                B[2 * plane + q] = hz;
-            } else {
-                // slots 0 and Py/2 of the packed column: A and B share the
-                // slot; separate them along z with the mirror kz -> -kz
-                const int kzm = (PZ - kz) & (PZ - 1);
-                if (kz > kzm) continue;
-                const int qm = kzm * W + qw;
-                T k0[6], kn[6], P[6], Q[6];
-                load_K(a.K, 0, a.Hy, a.Hz, PY, PZ, sl, kz, k0);
-                load_K(a.K, a.nx, a.Hy, a.Hz, PY, PZ, sl, kz, kn);
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    P[i] = (T)0.5 * (k0[i] + kn[i]);
-                    Q[i] = (T)0.5 * (k0[i] - kn[i]);
-                }
-                const cx<T> ux = B[q], uy = B[plane + q], uz = B[2 * plane + q];
-                const cx<T> vx = B[qm], vy = B[plane + qm], vz = B[2 * plane + qm];
-                cx<T> a1, a2, a3, b1, b2, b3;
-                apply_K(P, ux, uy, uz, a1, a2, a3);
-                apply_K(Q, mk(vx.x, -vx.y), mk(vy.x, -vy.y), mk(vz.x, -vz.y), b1, b2, b3);
-                B[q] = cadd(a1, b1);
-                B[plane + q] = cadd(a2, b2);
-                B[2 * plane + q] = cadd(a3, b3);
-                if (qm != q) {
-                    apply_K(P, vx, vy, vz, a1, a2, a3);
-                    apply_K(Q, mk(ux.x, -ux.y), mk(uy.x, -uy.y), mk(uz.x, -uz.y), b1, b2, b3);
-                    B[qm] = cadd(a1, b1);
-                    B[plane + qm] = cadd(a2, b2);
-                    B[2 * plane + qm] = cadd(a3, b3);
-                }
-            }
-        }
-        __syncthreads();
-        if (zt) {
-#pragma unroll
-            for (int kz = 0; kz < PZ; ++kz) v[kz] = B[c * plane + kz * W + ww];
-            RegFFT<T, PZ, 1, true>::run(v, a.twz);
-#pragma unroll
-            for (int z = 0; z < PZ; ++z) {
-                if (z < PZ / 2) {
-                    const int row = c * nz + z, own = row / RC, lr = row - own * RC;
-                    const Pad<T> R{cl.map_shared_rank(ybuf, own), 0};
-                    R[lr * PY + slot] = v[z];
-                }
-            }
-        }
-        __syncthreads();  // B is refilled by the next sub-tile
-    }
-    cl.sync();
-
-    // 3. own rows back along y (kx = 0: U = A + i B first), truncated to ny
-    if (kx == 0) {
-        for (int idx = threadIdx.x; idx < RC * (half - 1); idx += blockDim.x) {
-            const int r = idx / (half - 1), q = 1 + idx - r * (half - 1);
-            const Pad<T> u = Y.at(r * PY);
-            const cx<T> av = u[q], bv = u[PY - q];
-            u[q] = mk(av.x - bv.y, av.y + bv.x);
-            u[PY - q] = mk(av.x + bv.y, bv.x - av.y);
-        }
-        __syncthreads();
-    }
-    for (int r = wp; r < RC; r += nw) WarpFFT<T, true, PY, 1>::run(Y.at(r * PY), 1, a.twy, false, true);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < RC * ny; idx += blockDim.x) {
-        const int r = idx >> lgny, y = idx & (ny - 1);
-        S[idx] = Y[r * PY + y];
-    }
 }
 
 // ------------------------------------------------------------------ stages
@@ -2489,7 +2298,6 @@ template <typename T> __device__ __forceinline__ T coef_H(const StageCoef &C, in
 template <typename T, int NF, int NH, bool LAST, bool STAGE0>
 __global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
 {
-    pdl_entry();
     __shared__ T s_cb[MMX_MAXS + 1];          // coefficient of each F read, then of F_k (index NF)
     __shared__ T s_w[MMX_NHIST + 1];          // Eq. 6 weights (1 for the exact field)
     __shared__ T s_H[4];                      // applied field at t0 + a_k h
@@ -2723,7 +2531,6 @@ __global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
 template <typename T>
 __global__ void __launch_bounds__(256) k_control(const CtlKArgs<T> a)
 {
-    pdl_entry();
     constexpr int HW = (int)(offsetof(DevState, coef) / 8);
     __shared__ __align__(16) unsigned long long s_head[HW];
     __shared__ double s_sig[MMX_NHIST], s_iden[MMX_NHIST];
@@ -2980,24 +2787,6 @@ template <typename T> const void *zmr_fn(int L)
     return nullptr;
 }
 
-// cluster-fused y-z pass: rows per CTA, shared memory and threads
-int yzc_rows(const mmx_ctx *c, int C) { return 3 * c->nz / C; }
-size_t yzc_smem(const mmx_ctx *c, int C, int W)
-{
-    return padded_words((size_t)yzc_rows(c, C) * c->Py) * sizeof(cx<float>) + (size_t)3 * c->Pz * W * sizeof(cx<float>);
-}
-int yzc_threads(int W) { return std::max(32, (3 * W + 31) / 32 * 32); }
-template <int PY> const void *yzc_fn_z(int Pz)
-{
-    switch (Pz) {
-    case 4: return (const void *)k_yzc<float, PY, 4>;
-    case 8: return (const void *)k_yzc<float, PY, 8>;
-    case 16: return (const void *)k_yzc<float, PY, 16>;
-    case 32: return (const void *)k_yzc<float, PY, 32>;
-    }
-    return nullptr;
-}
-
 template <typename T> const void *zm_fn(int L)
 {
     switch (L) { MMX_LEN_CASES(k_zm, T) }
@@ -3009,21 +2798,11 @@ template <typename T> const void *yi_fn(int L)
     return nullptr;
 }
 
-// Launches f on stream s; with c->pdl as a programmatic dependent launch
-// (the kernels start with pdl_entry, so ordering is that of the stream).
-inline void launch_k(const mmx_ctx *c, const void *f, dim3 grid, dim3 block, void **args, size_t smem, cudaStream_t s)
+// Launches f on stream s (a kernel-pointer launch: the instances live in
+// several translation units behind the kernel table).
+inline void launch_k(const mmx_ctx *, const void *f, dim3 grid, dim3 block, void **args, size_t smem, cudaStream_t s)
 {
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = c->pdl ? 1 : 0;
-    cudaLaunchKernelExC(&cfg, f, args);
+    cudaLaunchKernel(f, grid, block, args, smem, s);
 }
 
 template <typename T>
@@ -3079,40 +2858,6 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
         launch();
         c->launches++;
         if (prof) mmx_prof_end(c, s, cls);
-    };
-    // cluster-fused y-z pass: one cluster of yzc_C CTAs per kx column
-    auto launch_yzc = [&]() {
-        SplitArgs<T> za{};
-        za.S = (cx<T> *)c->S;
-        za.K = (const T *)c->K;
-        za.twy = (const cx<T> *)c->twy;
-        za.twz = (const cx<T> *)c->twz;
-        za.st = const_cast<DevState *>(st);
-        za.rows = c->rows;
-        za.nx = c->nx;
-        za.ny = c->ny;
-        za.nz = c->nz;
-        za.Py = c->Py;
-        za.Pz = c->Pz;
-        za.Hy = c->Hy;
-        za.Hz = c->Hz;
-        za.stage0 = stage0;
-        za.ry = yzc_rows(c, c->yzc_C);
-        za.W = c->yzc_W;
-        void *zargs[] = {(void *)&za};
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3((unsigned)(c->nx * c->yzc_C));
-        cfg.blockDim = dim3((unsigned)yzc_threads(c->yzc_W));
-        cfg.dynamicSmemBytes = yzc_smem(c, c->yzc_C, c->yzc_W);
-        cfg.stream = s;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = (unsigned)c->yzc_C;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        cudaLaunchKernelExC(&cfg, mmxk_yzc_kernel(c->Py, c->Pz), zargs);
     };
     const int xt = x_threads<T>(c, trows);
     void *xargs[] = {(void *)&xa};
@@ -3174,10 +2919,6 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
                     launch_k(c, f_xf, dim3(persistent_grid(f_xf, txf, s_xf, n_x)), dim3(txf), xfa, s_xf, s);
             });
         if (parts & 2) timed(1, [&] {
-            if (c->cluster) {
-                launch_yzc();
-                return;
-            }
             const unsigned g4 = (unsigned)(((long long)c->nx * 3 * c->nz + R4_WARPS - 1) / R4_WARPS);
             if (c->r4)
                 launch_k(c, mmxk_kernel(K_YF4, false, c->Py), dim3(g4), dim3(32 * R4_WARPS), sargs, r4_smem(), s);
@@ -3206,8 +2947,6 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
     if (parts & 1)
         timed(0, [&] { launch_k(c, mmxk_kernel(K_XF, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s); });
     if (!(parts & 2)) {
-    } else if (c->cluster) {
-        timed(1, launch_yzc);
     } else if (!c->split) {
         timed(1, [&] { launch_k(c, mmxk_kernel(K_YZ, sizeof(T) == 8, c->Py), dim3(c->nx), dim3(YZ_THREADS), yargs, ys, s); });
     } else {

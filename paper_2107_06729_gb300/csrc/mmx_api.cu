@@ -495,16 +495,14 @@ std::shared_ptr<const std::vector<double>> tensor_for(const mmx_host_tensor_args
 
 // ------------------------------------------------------------ autotuner
 // Pass configurations of one exact demag evaluation: rows per CTA of the
-// plain x passes, XI with TMA tile loads or plain, and for meshes whose y-z
-// column does not fit one CTA the split passes or the thread-block-cluster
-// pass.  After about 20 ms of warm-up evaluations, each candidate is timed
-// twice, round robin (CUDA events, one warm-up and three evaluations of a
-// seeded pseudo-random field on the context's own buffers), and the fastest
-// minimum kept;
-// results are cached per mesh and precision for the process.
+// plain x passes and XI with TMA tile loads or plain.  After about 20 ms of
+// warm-up evaluations, each candidate is timed twice, round robin (CUDA
+// events, one warm-up and three evaluations of a seeded pseudo-random field
+// on the context's own buffers), and the fastest minimum kept; results are
+// cached per mesh and precision for the process.
 struct Plan {
     int trows;
-    bool xi_tma, cluster;
+    bool xi_tma;
     double us;
 };
 struct PlanKey {
@@ -533,8 +531,7 @@ void apply_plan(mmx_ctx *c, const Plan &p)
 {
     mmxk_set_trows(c, p.trows);
     c->xi_tma = p.xi_tma && c->xi_tma_ok;
-    c->cluster = p.cluster && c->yzc_C > 0;
-    c->nd = (c->split && !c->cluster) ? 5 : 3;
+    c->nd = c->split ? 5 : 3;
     c->demag_us = p.us;
 }
 
@@ -578,17 +575,9 @@ int autotune(mmx_ctx *c)
         if (mmxk_set_trows(c, tr) == 0) rows.push_back(tr);
     const int tr0 = mmxk_default_trows(c);
     if (std::find(rows.begin(), rows.end(), tr0) == rows.end()) rows.push_back(tr0);
-    // cluster candidate: sets yzc_C / yzc_W when feasible
-    bool cl_ok = false;
-    if (c->split) {
-        mmxk_cluster_plan(c);
-        cl_ok = c->cluster;
-        c->cluster = false;
-    }
     std::vector<Plan> cand;
-    for (int cl = 0; cl <= (cl_ok ? 1 : 0); ++cl)
-        for (int xt = 0; xt <= (c->xi_tma_ok ? 1 : 0); ++xt)
-            for (int tr : rows) cand.push_back(Plan{tr, xt == 1, cl == 1, 1e30});
+    for (int xt = 0; xt <= (c->xi_tma_ok ? 1 : 0); ++xt)
+        for (int tr : rows) cand.push_back(Plan{tr, xt == 1, 1e30});
     // bring the clocks up first (about 20 ms of evaluations), then two
     // round-robin passes over the candidates, keeping each one's minimum
     apply_plan(c, cand[0]);
@@ -604,9 +593,9 @@ int autotune(mmx_ctx *c)
         if (p.us < best.us) best = p;
     if (getenv("MMX_AUTOTUNE_LOG"))
         for (const Plan &p : cand)
-            fprintf(stderr, "mmx autotune %dx%dx%d %s: x_rows %d xi_tma %d cluster %d -> %.1f us%s\n", c->nx, c->ny,
-                    c->nz, c->prec == MMX_FP64 ? "fp64" : "fp32", p.trows, (int)p.xi_tma, (int)p.cluster, p.us,
-                    (&p == &best || (p.trows == best.trows && p.xi_tma == best.xi_tma && p.cluster == best.cluster))
+            fprintf(stderr, "mmx autotune %dx%dx%d %s: x_rows %d xi_tma %d -> %.1f us%s\n", c->nx, c->ny, c->nz,
+                    c->prec == MMX_FP64 ? "fp64" : "fp32", p.trows, (int)p.xi_tma, p.us,
+                    (&p == &best || (p.trows == best.trows && p.xi_tma == best.xi_tma))
                         ? "  (kept)"
                         : "");
     apply_plan(c, best);
@@ -727,9 +716,7 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     c->rows = 3LL * c->ny * c->nz;
     c->use_graphs = getenv("MMX_NO_GRAPH") == nullptr;
     // fused y-z pass while one column fits comfortably in one CTA, else the
-    // split passes; MMX_FORCE_SPLIT forces the split passes, MMX_FORCE_CLUSTER
-    // the thread-block-cluster pass where it applies (on GB300 it measures
-    // slower than the split passes at 512 x 512 x 16, so it is not the default)
+    // split passes; MMX_FORCE_SPLIT forces the split passes
     const bool big = mmxk_yz_smem_bytes(c) > 160 * 1024 || c->Pz > mmxk_yz_max_pz(c);
     if (c->Pz > mmxk_yz_max_pz(c) && c->Py < 2) {
         g_create_err = "ny = 1 with nz above 8 (FP32) or 4 (FP64) is not supported";
@@ -737,25 +724,12 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
         return MMX_ERR_ARG;
     }
     const bool force_split = getenv("MMX_FORCE_SPLIT") != nullptr;
-    const bool force_cluster = getenv("MMX_FORCE_CLUSTER") != nullptr && !force_split;
-    c->split = (big || force_split || force_cluster) && c->Py >= 2;
-    c->cluster = false;
-    if (c->split && force_cluster && mmxk_cluster_plan(c) != 0) {
-        cudaGetLastError();
-        g_create_err = "cluster set-up failed";
-        delete c;
-        return MMX_ERR_CUDA;
-    }
-    if (force_cluster && !c->cluster) c->split = big && c->Py >= 2;
-    c->nd = (c->split && !c->cluster) ? 5 : 3;
+    c->split = (big || force_split) && c->Py >= 2;
+    c->nd = c->split ? 5 : 3;
     c->allow_tma = true;
     c->stall_test = getenv("MMX_TEST_STALL_TMA") != nullptr;
-    // programmatic dependent launches measured slower on GB300 for both the
-    // film and the large box (resident waiting CTAs cost more than the launch
-    // latency they hide), so they are opt-in
-    c->pdl = getenv("MMX_PDL") != nullptr;
     c->trows = mmxk_default_trows(c);
-    if (mmxk_x_smem_bytes(c) > 227 * 1024 || (c->split && !c->cluster && mmxk_split_smem_bytes(c) > 227 * 1024) ||
+    if (mmxk_x_smem_bytes(c) > 227 * 1024 || (c->split && mmxk_split_smem_bytes(c) > 227 * 1024) ||
         (!c->split && mmxk_yz_smem_bytes(c) > 227 * 1024)) {
         g_create_err = "mesh too large for the FFT passes";
         delete c;
@@ -835,11 +809,11 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     ok = ok && alloc(&c->F, fb * C.nslots) && alloc(&c->G, fb) && alloc(&c->hist, fb * nh);
     ok = ok && alloc(&c->errpart, (size_t)((c->n + 127) / 128) * c->esz);
     ok = ok && alloc(&c->S, (size_t)c->rows * c->nx * 2 * c->esz);
-    if (c->split && !c->cluster) ok = ok && alloc(&c->Tb, (size_t)c->nx * 3 * c->nz * c->Py * 2 * c->esz);
+    if (c->split) ok = ok && alloc(&c->Tb, (size_t)c->nx * 3 * c->nz * c->Py * 2 * c->esz);
     ok = ok && alloc(&c->K, Kspec.size() * c->esz);
     ok = ok && alloc(&c->twx, (size_t)c->Px * 2 * c->esz) && alloc(&c->twy, (size_t)c->Py * 2 * c->esz) &&
          alloc(&c->twz, (size_t)c->Pz * 2 * c->esz);
-    if (c->prec == MMX_FP32_MIXED && c->split && !c->cluster && (c->Px == 1024 || c->Py == 1024))
+    if (c->prec == MMX_FP32_MIXED && c->split && (c->Px == 1024 || c->Py == 1024))
         ok = ok && alloc(&c->tw4, (size_t)1024 * 2 * c->esz);
     ok = ok && alloc((void **)&c->st, sizeof(DevState));
     ok = ok && cudaMallocHost((void **)&c->h_st, sizeof(DevState)) == cudaSuccess;
@@ -871,16 +845,12 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     {
         const char *at = getenv("MMX_AUTOTUNE");
         const char *trs = getenv("MMX_TROWS");
-        const bool forced = force_split || force_cluster || getenv("MMX_NO_TMA") != nullptr || trs != nullptr;
+        const bool forced = force_split || getenv("MMX_NO_TMA") != nullptr || trs != nullptr;
         if (trs) mmxk_set_trows(c, atoi(trs));
         if (!forced && !(at && at[0] == '0') && autotune(c) != 0) {
             g_create_err = "autotuning the demag passes failed";
             mmx_destroy(c);
             return MMX_ERR_CUDA;
-        }
-        if (c->cluster && c->Tb) {  // the cluster pass keeps the y spectrum on chip
-            cudaFree(c->Tb);
-            c->Tb = nullptr;
         }
     }
     DevState &s = *c->h_st;
@@ -1124,10 +1094,9 @@ int mmx_get_profile(mmx_ctx *c, double *ms, long long *launches)
 int mmx_get_plan(const mmx_ctx *c, mmx_plan *out)
 {
     if (!c || !out) return MMX_ERR_ARG;
-    out->yz_pass = !c->split ? 0 : (c->cluster ? 2 : 1);
+    out->yz_pass = c->split ? 1 : 0;
     out->x_rows = c->trows;
     out->xi_tma = c->xi_tma ? 1 : 0;
-    out->cluster_ctas = c->cluster ? c->yzc_C : 0;
     out->tuned = c->tuned ? 1 : 0;
     out->demag_us = c->tuned ? c->demag_us : 0.0;
     out->kernels_per_demag = c->nd;

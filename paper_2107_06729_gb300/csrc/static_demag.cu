@@ -79,9 +79,7 @@ extern "C" int mmx_demag_static(const mmx_mesh *mesh, double Ms, int precision, 
     c.profiling = false;
     c.launches = 0;
     c.split = false;  // the fused y-z pass only: no room for a second spectrum
-    c.cluster = false;
     c.nd = 3;
-    c.pdl = false;
     c.allow_tma = false;  // no device state word to report a bounded wait in
     c.stall_test = false;
     c.xi_tma = c.xi_tma_ok = false;

@@ -130,9 +130,10 @@ def test_live_contexts_of_one_length_keep_their_shared_memory():
         small.close()
 
 
-CLUSTER_SHAPES = [((16, 64, 4), (2e-9, 2e-9, 1e-9)), ((4, 64, 2), (1e-9, 3e-9, 2e-9)),
-                  ((8, 128, 16), (2e-9, 2e-9, 2e-9)), ((2, 256, 8), (1e-9, 1e-9, 1e-9)),
-                  ((32, 64, 8), (3e-9, 2e-9, 1e-9))]
+# more shapes of the split passes, forced (FP32): y lengths 128-512, z lengths 4-32
+SPLIT_SHAPES = [((16, 64, 4), (2e-9, 2e-9, 1e-9)), ((4, 64, 2), (1e-9, 3e-9, 2e-9)),
+                ((8, 128, 16), (2e-9, 2e-9, 2e-9)), ((2, 256, 8), (1e-9, 1e-9, 1e-9)),
+                ((32, 64, 8), (3e-9, 2e-9, 1e-9))]
 
 
 def _launches_of_one_demag(n, d, m, prec):
@@ -151,23 +152,20 @@ def _launches_of_one_demag(n, d, m, prec):
         ctx.close()
 
 
-@pytest.mark.parametrize("n,d", CLUSTER_SHAPES)
-def test_cluster_yz_path_matches_oracle(n, d, monkeypatch):
-    """The thread-block-cluster y-z pass (one cluster per kx column, the y
-    spectrum exchanged through distributed shared memory), forced on meshes
-    small enough for the oracle: XF, YZC, XI = three launches."""
-    monkeypatch.setenv("MMX_FORCE_CLUSTER", "1")
+@pytest.mark.parametrize("n,d", SPLIT_SHAPES)
+def test_forced_split_passes_match_oracle_fp32(n, d, monkeypatch):
+    """XF, YF, ZM, YI, XI (five launches) on meshes small enough for the oracle."""
+    monkeypatch.setenv("MMX_FORCE_SPLIT", "1")
     m = W.m_random(n, seed=sum(n) + 11)
     ref = O.demag_fft(O.newell_octant(*n, *d), MAT["Ms"], m)
     got, launches = _launches_of_one_demag(n, d, m, "fp32")
-    assert launches == 3
+    assert launches == 5
     assert rel_max(got, ref) < 1e-5
 
 
-def test_large_column_fp32_split_and_cluster_paths_match_oracle(monkeypatch):
+def test_large_column_fp32_split_path_matches_oracle():
     """16 x 128 x 16: the y-z column (256 x 32 x 3 complex words, 221 KB)
-    does not fit one CTA.  By default the split passes run it (five
-    launches); forced, one thread-block cluster per kx column (three)."""
+    does not fit one CTA, so the split passes run it (five launches)."""
     n, d = (16, 128, 16), (2e-9, 2e-9, 2e-9)
     m = W.m_vortex(n, d, seed=2)
     ref = O.demag_fft(O.newell_octant(*n, *d), MAT["Ms"], m)
@@ -175,9 +173,6 @@ def test_large_column_fp32_split_and_cluster_paths_match_oracle(monkeypatch):
     assert launches == 5 and rel_max(got, ref) < 1e-5
     got, launches = _launches_of_one_demag(n, d, m, "fp64")
     assert launches == 5 and rel_max(got, ref) < 1e-12
-    monkeypatch.setenv("MMX_FORCE_CLUSTER", "1")
-    got, launches = _launches_of_one_demag(n, d, m, "fp32")
-    assert launches == 3 and rel_max(got, ref) < 1e-5
 
 
 @pytest.mark.parametrize("env", [{"MMX_AUTOTUNE": "0"}, {"MMX_NO_TMA": "1"}, {"MMX_TROWS": "2"},
@@ -210,9 +205,7 @@ def test_autotuned_plan_is_reported():
     big = gpu_context({"n": (16, 128, 16), "d": (2e-9,) * 3}, MAT, {}, {"method": "RK4", "h": 1e-13}, "fp32")
     try:
         p = big.plan()
-        assert p["yz_pass"] in (1, 2)
-        assert p["kernels_per_demag"] == (5 if p["yz_pass"] == 1 else 3)
-        assert (p["cluster_ctas"] > 1) == (p["yz_pass"] == 2)
+        assert p["yz_pass"] == 1 and p["kernels_per_demag"] == 5
     finally:
         big.close()
 

@@ -134,41 +134,6 @@ def test_split_path_integrator_matches_oracle(method, p, monkeypatch):
     assert np.abs(got - ref).max() < 1e-10
 
 
-@pytest.mark.parametrize("method,p", [("RKDP54", 4), ("RK23", 2)])
-def test_cluster_path_integrator_matches_split_path_and_oracle(method, p, monkeypatch):
-    """FP32 integration with the cluster y-z pass forced, against the same
-    run on the split passes (same transforms in the same order) and the FP64
-    oracle."""
-    n, d = (8, 64, 4), (4e-9, 4e-9, 4e-9)
-    mesh = {"n": n, "d": d}
-    integ = {"method": method, "extrap_order": p, "adaptive": True, "h": 1e-13, "tol": 1e-5}
-    m0 = W.m_smooth(n, seed=4)
-    t_end = 3e-12
-    monkeypatch.setenv("MMX_FORCE_CLUSTER", "1")
-    got, gs = gpu_run(mesh, MAT, FLD, integ, m0, t_end, "fp32")
-    monkeypatch.delenv("MMX_FORCE_CLUSTER")
-    monkeypatch.setenv("MMX_FORCE_SPLIT", "1")
-    spl, ss = gpu_run(mesh, MAT, FLD, integ, m0, t_end, "fp32")
-    ref, rs = oracle_run(mesh, MAT, FLD, integ, m0, t_end)
-    assert gs["accepted"] == ss["accepted"]
-    assert np.abs(got - spl).max() < 1e-6
-    assert np.abs(got - ref).max() < 1e-4
-
-
-def test_programmatic_dependent_launch_option_matches_oracle(monkeypatch):
-    """MMX_PDL=1 launches every kernel as a programmatic dependent launch;
-    the kernels wait at entry, so results equal the oracle step for step."""
-    monkeypatch.setenv("MMX_PDL", "1")
-    n, d = (16, 8, 2), (4e-9, 4e-9, 4e-9)
-    mesh = {"n": n, "d": d}
-    integ = {"method": "RKDP54", "extrap_order": 4, "adaptive": True, "h": 1e-13, "tol": 1e-5}
-    m0 = W.m_uniform_noise(n, seed=3, noise=0.2)
-    got, gs = gpu_run(mesh, MAT, FLD, integ, m0, 5e-12, "fp64")
-    ref, rs = oracle_run(mesh, MAT, FLD, integ, m0, 5e-12)
-    assert gs["accepted"] == rs["accepted"] and gs["rejected"] == rs["rejected"]
-    assert np.abs(got - ref).max() < 1e-10
-
-
 def test_large_box_recipe_on_a_subbox_matches_oracle():
     """The 512 x 512 x 16 box's recipe (2 nm cells, Py, vortex with noise,
     RK23 with p = 2) on a 64 x 64 x 4 sub-box, FP64, step for step against
