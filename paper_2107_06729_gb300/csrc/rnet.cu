@@ -455,9 +455,14 @@ constexpr int WG_TC = 8 * WG_TKC;  // cells per tile
 template <int COUTP_> __host__ __device__ constexpr int wg_gs() { return 3 * COUTP_ / 8; }  // row groups per slab
 // row groups per k-chunk: three slabs, plus the rows the last slab's MMA reads beyond its own
 template <int COUTP_> __host__ __device__ constexpr int wg_groups() { return 2 * wg_gs<COUTP_>() + 16; }
+// dynamic shared memory of one CTA: the operands need about 22 KB, but the
+// launch asks for 56 KB so that at most four CTAs share an SM and their
+// TMEM allocations (at most 128 of the 512 columns each) always fit: no CTA
+// ever waits in tcgen05.alloc
 template <int CINP_, int COUTP_> __host__ __device__ constexpr size_t wg_smem()
 {
-    return 128 + (size_t)2 * WG_TKC * wg_groups<COUTP_>() * 128 + (size_t)WG_TKC * (CINP_ / 8) * 128 + 64;
+    constexpr size_t need = 128 + (size_t)2 * WG_TKC * wg_groups<COUTP_>() * 128 + (size_t)WG_TKC * (CINP_ / 8) * 128 + 64;
+    return need > 56 * 1024 ? need : 56 * 1024;
 }
 
 template <int CINP_, int COUTP_>
@@ -842,6 +847,15 @@ cudaError_t set_tc_smem()
         return e;
     if ((e = cudaFuncSetAttribute(k_rnet_conv_tc<32, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)tc_smem(32, 32))) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_rnet_wgrad_tc<32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)wg_smem<32, 8>())) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_rnet_wgrad_tc<32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)wg_smem<32, 32>())) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_rnet_wgrad_tc<16, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)wg_smem<16, 32>())) != cudaSuccess)
         return e;
     return cudaFuncSetAttribute(k_rnet_conv_tc<32, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)tc_smem(32, 16));
