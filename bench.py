@@ -503,6 +503,7 @@ def ensemble(pkg, torch, dev, chunk_ps, steps, warmup):
         batch_s = ev[0].elapsed_time(ev[1]) / 1e3
         a1, r1 = counts()
         l1 = launches()
+        per_member = [c.stats() for c in ctxs]
         # the same chunks, film after film through mmx_run (graphs built first)
         for c, blob in zip(ctxs, blobs):
             c.load_state(blob)
@@ -521,8 +522,14 @@ def ensemble(pkg, torch, dev, chunk_ps, steps, warmup):
         seq_s = ev[2].elapsed_time(ev[3]) / 1e3
         a2, r2 = counts()
         b.close()
+        # attempts of each film over the timed steps (its own step sizes)
+        att = [st["accepted"] + st["rejected"] for st in per_member]
+        for c, blob in zip(ctxs, blobs):
+            c.load_state(blob)
+        att = [x - (c.stats()["accepted"] + c.stats()["rejected"]) for x, c in zip(att, ctxs)]
     for c in ctxs:
         c.close()
+    lock = lockstep_bound(pkg, torch, dev, ens, cells, max(att) / steps, 1e3 * batch_s / steps)
     sim_ns = len(ens) * steps * dt * 1e9
     return {"workload": "ensemble_64_films_32-256sq_x1-2_rkf45_p4_fp32", "samples": len(ens), "cells": cells,
             "metric": "simulated ns summed over the films per second", "unit": "sample-ns/s",
@@ -532,9 +539,51 @@ def ensemble(pkg, torch, dev, chunk_ps, steps, warmup):
             "accepted": a1 - a0, "rejected": r1 - r0,
             "sequential_accepted": a2 - a0,
             "gpu_launches": l1 - l0, "setup_s": round(setup, 1),
+            "attempts_per_step": {"max": max(att) / steps, "mean": float(np.mean(att)) / steps},
+            "lockstep_descriptor_table_bound": lock,
             "note": "one mmx_batch_run (one graph launch, 64 independent device-side loops) per step vs "
                     "64 mmx_run calls per step; ensemble state 1.5M cells (about 300 MB with stage "
                     "buffers, larger than L2)"}
+
+
+def lockstep_bound(pkg, torch, dev, ens, cells, max_attempts, batch_ms):
+    """Measured bound on the descriptor-table alternative to the batch graph:
+    one launch per pass over all films, all films attempting steps in
+    lockstep, so that every film takes as many attempts as the stiffest.  Its
+    attempt costs at least one attempt of a single film holding all the
+    ensemble's cells (the same passes over the same bytes, without the
+    per-film shapes): films of 1024 x 512 x 2 and 1024 x 1024 x 2 cells of
+    4 nm (mesh sides are powers of two), RKF45 p = 4, FP32, the ensemble's
+    first film's material and field, each timed over 2 ps after 1 ps of
+    warm-up, the time per attempt interpolated linearly to the ensemble's
+    cell count."""
+    s0 = ens[0]
+    stream = torch.cuda.Stream(dev)
+    pts = []
+    for n in ((1024, 512, 2), (1024, 1024, 2)):
+        mesh = {"n": n, "d": (4e-9, 4e-9, 4e-9)}
+        with torch.cuda.stream(stream):
+            ctx = pkg.Context(mesh, s0["material"], s0["field"], s0["integrator"], "fp32", stream)
+            ctx.set_m(torch.from_numpy(W.m_uniform_noise(n, noise=0.3, seed=5)).to(dev, torch.float32))
+            ctx.run(1e-12)
+            st0 = ctx.stats()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            ctx.run(3e-12)
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            st1 = ctx.stats()
+            ctx.close()
+        n_att = (st1["accepted"] + st1["rejected"]) - (st0["accepted"] + st0["rejected"])
+        pts.append((int(np.prod(n)), ev[0].elapsed_time(ev[1]) * 1e3 / max(1, n_att)))
+    (c0, u0), (c1, u1) = pts
+    us_att = u0 + (u1 - u0) * (cells - c0) / (c1 - c0)
+    bound_ms = max_attempts * us_att / 1e3
+    return {"aggregate_films_us_per_attempt": {str(c): round(u, 2) for c, u in pts}, "ensemble_cells": cells,
+            "us_per_attempt_at_ensemble_cells": round(us_att, 2),
+            "stiffest_film_attempts_per_step": max_attempts, "lockstep_ms_per_step_at_least": round(bound_ms, 3),
+            "batch_graph_ms_per_step": round(batch_ms, 3),
+            "batch_graph_faster_by_at_least": round(bound_ms / batch_ms, 3)}
 
 
 def peak_src_note(src):
