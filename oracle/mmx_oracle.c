@@ -796,10 +796,15 @@ static int attempt_step(om_sim *S, double h, int *stop_err)
         S->st.rejected++;
         return 0;
     }
-    /* accept: renormalise (R5) */
+    /* accept: renormalise (R5); a cell without material (m = 0, reading R11:
+     * the vacuum between the particles of an array) has no torque and stays 0 */
     for (long i = 0; i < n; i++) {
         double mx = S->M1[i], my = S->M1[n + i], mz = S->M1[2 * n + i];
         double r = sqrt(mx * mx + my * my + mz * mz);
+        if (r == 0.0) {
+            S->m[i] = S->m[n + i] = S->m[2 * n + i] = 0.0;
+            continue;
+        }
         S->m[i] = mx / r; S->m[n + i] = my / r; S->m[2 * n + i] = mz / r;
     }
     S->st.accepted++;

@@ -2492,13 +2492,17 @@ __global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
     if (valid) {
         const T r = sqrt(M[0] * M[0] + M[1] * M[1] + M[2] * M[2]);
         err = sqrt(E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
-        if (!(err <= (T)3.0e38) || !(r == r) || r == (T)0) err = (T)INFINITY;
+        // a cell without material (m = 0: no torque, so every stage derivative
+        // and the new state stay exactly 0) stays 0; any other zero or
+        // non-finite state rejects the attempt
+        const bool empty = r == (T)0 && err == (T)0;
+        if (!(err <= (T)3.0e38) || !(r == r) || (r == (T)0 && !empty)) err = (T)INFINITY;
         T *mo = sv.y ? a.m0 : a.m1;
         if constexpr (sizeof(T) == 4) {
             // (hi + lo) / r as a pair: hi' = hi inv rounded, its exact error by an
             // FMA, lo' = that error + lo inv, renormalised (Fast2Sum); a rounded
             // inv only rescales the three components alike
-            const float inv = 1.0f / r;
+            const float inv = empty ? 0.0f : 1.0f / r;
             T *ml = a.mlo + (size_t)(sv.y ^ 1) * fs;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -2510,7 +2514,7 @@ __global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
             }
         } else {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) mo[(size_t)c * n + i] = M[c] / r;
+            for (int c = 0; c < 3; ++c) mo[(size_t)c * n + i] = empty ? (T)0 : M[c] / r;
         }
     }
 #pragma unroll

@@ -13,6 +13,10 @@ prints one JSON line per experiment:
   the error against the reference.
 * ``fixed_step_sweep``: RK4 at h = 100 .. 500 fs with p = 3 and with full
   demag, the error against the reference.
+* ``checker_fixed_step`` (Fig. 3 analog): the checkerboard particle-array
+  stand-in (see ``checker_config``), every method at fixed steps of
+  100 .. 1000 fs in FP64, full and extrapolated demag, Eq. 7 over the 1 ps
+  samples of <m> against an h = 10 fs reference.
 
 The slab stands in for the paper's 3.2 um x 1.6 um x 20 nm Py slab with
 5 nm cells (640 x 320 x 4, S-state start, field (-20, 1, 0) kA/m): the mesh
@@ -157,18 +161,103 @@ def fixed_step_sweep(pkg, torch, cfg, ref, t_end):
     return {"experiment": "fixed_step_sweep", "method": "RK4", "rows": rows}
 
 
+# ---------------------------------------------------- checkerboard array --
+# Fig. 3 analog.  The paper's array: 300 nm x 300 nm x 5 nm, the Standard
+# Problem 4 material (Py), particles interacting only through the demag
+# field, relaxed at zero field, then field (20, 1, 0) kA/m for 3 ns with
+# <m> recorded every 1 ps; fixed steps, FP64, the full-demag and the
+# extrapolated result of every method against a reference.  Declared
+# stand-in (the particle geometry is not given): 64 x 64 x 1 cells of 5 nm
+# (320 nm square), particles of 4 x 4 cells (20 nm) on alternate squares of
+# a checkerboard, the cells between them without material (m = 0), so that
+# exchange acts inside each particle only; the start relaxed from +x with
+# noise at alpha = 0.5 in zero field for 500 ps (FP64, DP54, e_max 1e-8);
+# the reference one RKDP54 run with full demag at h = 10 fs.
+CHECKER_METHODS = [("HEUN12", 1), ("ABM2", 1), ("RK23", 2), ("RK4", 3), ("RKF45", 4), ("RKCK45", 4),
+                   ("RKDP54", 4), ("RKF56", 5)]
+CHECKER_H_FS = (100, 200, 250, 500, 1000)  # divide the 1 ps sampling interval
+
+
+def checker_config(pkg, torch, seed=0):
+    n = (64, 64, 1)
+    mesh = {"n": n, "d": (5e-9, 5e-9, 5e-9)}
+    mat = {"Ms": 8e5, "A": 1.3e-11, "K": 0.0, "ku": (1.0, 0.0, 0.0), "alpha": 0.02, "gamma": W.GAMMA}
+    mask = W.checkerboard_mask(n, 4)
+    m0 = W.m_uniform_noise(n, direction=(1.0, 0.0, 0.0), noise=0.1, seed=seed) * mask
+    relax = dict(mat, alpha=0.5)
+    ctx = pkg.Context(mesh, relax, {}, _adaptive("RKDP54", -1, tol=1e-8), "fp64")
+    try:
+        m = torch.from_numpy(m0).to("cuda", torch.float64)
+        ctx.set_m(m)
+        ctx.run(500e-12)
+        ctx.get_m(m)
+        m0 = m.cpu().numpy()
+    finally:
+        ctx.close()
+    return {"name": "checkerboard_64x64x1_5nm_4x4_particles", "mesh": mesh, "material": mat,
+            "field": {"H0": (20e3, 1e3, 0.0)}, "m0": m0, "mask": mask}
+
+
+def _mag_mean_history(pkg, torch, cfg, integ, t_end, dt=1e-12):
+    """<m> over the magnetic cells every dt up to t_end ([3, S]), FP64."""
+    nmag = float(cfg["mask"].sum())
+    ctx = pkg.Context(cfg["mesh"], cfg["material"], cfg["field"], integ, "fp64")
+    try:
+        m = torch.from_numpy(cfg["m0"]).to("cuda", torch.float64)
+        ctx.set_m(m)
+        out = []
+        for k in range(1, int(round(t_end / dt)) + 1):
+            ctx.run(k * dt)
+            ctx.get_m(m)
+            out.append((m.sum(dim=(1, 2, 3)) / nmag).cpu().numpy())
+        return np.stack(out, axis=1), ctx.stats()
+    finally:
+        ctx.close()
+
+
+def checker_fixed_step(pkg, torch, cfg, t_end):
+    """Every method at fixed steps h (no controller), full demag and Eq. 6
+    with p matched to the method order; Eq. 7 over the 1 ps samples of <m>
+    against the reference."""
+    ref, _ = _mag_mean_history(pkg, torch, cfg, {"method": "RKDP54", "extrap_order": -1, "adaptive": False,
+                                                 "h": 10e-15}, t_end)
+    rows = []
+    for method, p in CHECKER_METHODS:
+        for h_fs in CHECKER_H_FS:
+            row = {"method": method, "p": p, "h_fs": h_fs}
+            for name, pp in (("full", -1), ("extrap", p)):
+                integ = {"method": method, "extrap_order": pp, "adaptive": False, "h": h_fs * 1e-15}
+                hist, st = _mag_mean_history(pkg, torch, cfg, integ, t_end)
+                row["eps_" + name] = eps_time(hist, ref)
+                row["steps_" + name] = st["accepted"]
+            rows.append(row)
+    return {"experiment": "checker_fixed_step", "precision": "fp64", "reference": "RKDP54 full demag, h = 10 fs",
+            "rows": rows}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--t-end-ps", type=float, default=200.0)
-    ap.add_argument("--only", choices=["method_sweep", "order_sweep", "fixed_step_sweep"])
+    ap.add_argument("--only", choices=["method_sweep", "order_sweep", "fixed_step_sweep", "checker_fixed_step"])
+    ap.add_argument("--checker-t-end-ps", type=float, default=3000.0,
+                    help="horizon of the checkerboard experiment (the paper's 3 ns)")
     ap.add_argument("--eps-time", action="store_true",
                     help="also Eq. 7 over 1 ps samples of <m> in the method sweep (extra untimed chunked runs)")
     args = ap.parse_args(argv)
     import torch
     import paper_2107_06729_gb300 as pkg
+    t0 = time.time()
+    if args.only in (None, "checker_fixed_step"):
+        ccfg = checker_config(pkg, torch)
+        out = checker_fixed_step(pkg, torch, ccfg, args.checker_t_end_ps * 1e-12)
+        out["workload"] = ccfg["name"]
+        out["t_end_ps"] = args.checker_t_end_ps
+        print(json.dumps(out), flush=True)
+        if args.only:
+            print(json.dumps({"experiment": "done", "wall_s": round(time.time() - t0, 1)}), flush=True)
+            return
     cfg = slab_config()
     t_end = args.t_end_ps * 1e-12
-    t0 = time.time()
     ref, rst, rsecs = _run(pkg, torch, cfg, _adaptive("RKDP54", -1, tol=1e-9), "fp64", t_end)
     print(json.dumps({"experiment": "reference", "workload": cfg["name"], "t_end_ps": args.t_end_ps,
                       "method": "RKDP54", "p": -1, "tol": 1e-9, "precision": "fp64", "steps": rst["accepted"],

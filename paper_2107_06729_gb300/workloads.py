@@ -45,6 +45,17 @@ def m_random(n, seed=0):
     return _normalise(rng.normal(size=(3, nz, ny, nx)))
 
 
+def checkerboard_mask(n, p):
+    """[1, nz, ny, nx] array: 1 on the cells of p x p squares of a
+    checkerboard (the square holding cell (0, 0) occupied), 0 elsewhere --
+    a particle array in vacuum (cells with m = 0 hold no material)."""
+    nx, ny, nz = n
+    x = np.arange(nx) // p
+    y = np.arange(ny) // p
+    occ = ((x.reshape(1, nx) + y.reshape(ny, 1)) % 2 == 0).astype(np.float64)
+    return np.broadcast_to(occ, (nz, ny, nx)).reshape(1, nz, ny, nx).copy()
+
+
 def m_vortex(n, d, core_radius=10e-9, noise=0.05, seed=0):
     """In-plane curl (-y, x)/r around the film centre, out-of-plane core
     m_z = exp(-r^2 / core_radius^2), plus U(-noise, noise), renormalised."""

@@ -147,3 +147,28 @@ def test_large_box_recipe_on_a_subbox_matches_oracle():
     assert gs["accepted"] == rs["accepted"] and gs["rejected"] == rs["rejected"]
     assert gs["exact_evals"] == rs["exact_evals"] and gs["extrap_evals"] == rs["extrap_evals"]
     assert np.abs(got - ref).max() < 1e-10
+
+
+@pytest.mark.parametrize("prec,method,p", [("fp64", "RKDP54", 4), ("fp64", "RKCK45", 4), ("fp64", "RKF56", 5),
+                                           ("fp32", "RKDP54", 4)])
+def test_checkerboard_particle_array_matches_oracle(prec, method, p):
+    """The checkerboard stand-in of the particle array (4 x 4-cell particles
+    on alternate squares of a 32 x 32 x 1 mesh, 5 nm cells, no exchange,
+    field (20, 1, 0) kA/m): the cells between the particles hold no
+    material (m = 0, reading R11) and must stay exactly 0; FP64 step for
+    step against the oracle, FP32 within 1e-4 after 5 ps."""
+    n = (32, 32, 1)
+    mesh = {"n": n, "d": (5e-9, 5e-9, 5e-9)}
+    mat = {"Ms": 8e5, "A": 0.0, "K": 0.0, "alpha": 0.02, "gamma": W.GAMMA}
+    fld = {"H0": (20e3, 1e3, 0.0)}
+    mask = W.checkerboard_mask(n, 4)
+    m0 = W.m_uniform_noise(n, direction=(0.0, 1.0, 0.0), noise=0.05, seed=8) * mask
+    integ = {"method": method, "extrap_order": p, "adaptive": True, "h": 1e-13, "tol": 1e-5}
+    got, gs = gpu_run(mesh, mat, fld, integ, m0, 5e-12, prec)
+    ref, rs = oracle_run(mesh, mat, fld, integ, m0, 5e-12)
+    assert np.all(got[:, mask[0] == 0] == 0.0)
+    if prec == "fp64":
+        assert gs["accepted"] == rs["accepted"] and gs["rejected"] == rs["rejected"]
+        assert np.abs(got - ref).max() < 1e-10
+    else:
+        assert np.abs(got - ref).max() < 1e-4

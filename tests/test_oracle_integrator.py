@@ -329,6 +329,57 @@ def test_single_cell_extrapolated_equals_full():
             assert np.abs(out[0] - o).max() < 1e-13
 
 
+# ------------------------------------------ cells without material (R11) --
+@pytest.mark.parametrize("method,p", [("RKDP54", 4), ("RK4", -1), ("RKF56", 5)])
+def test_one_particle_in_vacuum_equals_the_single_cell_mesh(method, p):
+    """A magnetic cell surrounded by cells with m = 0 (no material) moves
+    exactly like the same cell alone on a 1 x 1 x 1 mesh: the empty cells
+    add nothing to its demag sum (only the self term remains), their m = 0
+    in its exchange stencil only adds a field parallel to m (no torque), and
+    they stay exactly 0 themselves."""
+    mesh1 = {"n": (1, 1, 1), "d": (4e-9, 4e-9, 4e-9)}
+    mesh4 = {"n": (4, 4, 1), "d": (4e-9, 4e-9, 4e-9)}
+    mat = {"Ms": 8e5, "A": 1.3e-11, "K": 5e4, "ku": (1.0, 0.0, 0.0), "alpha": 0.05, "gamma": W.GAMMA}
+    fld = {"H0": (2e4, -1e4, 5e3)}
+    mc = np.array([0.36, 0.48, 0.8])
+    m1 = mc.reshape(3, 1, 1, 1)
+    m4 = np.zeros((3, 1, 4, 4))
+    m4[:, 0, 2, 1] = mc
+    integ = {"method": method, "extrap_order": p, "adaptive": method != "RK4", "h": 1e-13, "tol": 1e-6}
+    a = O.Simulation(mesh1, mat, fld, integ, m1)
+    b = O.Simulation(mesh4, mat, fld, integ, m4)
+    a.run(10e-12)
+    b.run(10e-12)
+    ma, mb = a.m(), b.m()
+    assert a.stats()["accepted"] == b.stats()["accepted"]
+    assert np.abs(mb[:, 0, 2, 1] - ma[:, 0, 0, 0]).max() < 1e-12
+    mb[:, 0, 2, 1] = 0.0
+    assert np.all(mb == 0.0)
+    # the particle did move
+    assert np.abs(ma[:, 0, 0, 0] - mc).max() > 1e-2
+
+
+def test_checkerboard_particles_keep_the_vacuum_empty_and_unit_length():
+    """The checkerboard stand-in (2 x 2-cell particles on alternate squares,
+    no exchange): after 5 ps the empty squares are still exactly 0 and the
+    particle cells unit vectors; with the array's dipolar coupling the
+    particles' states differ from the uncoupled single-particle motion."""
+    n = (8, 8, 1)
+    mesh = {"n": n, "d": (5e-9, 5e-9, 5e-9)}
+    mat = {"Ms": 8e5, "A": 0.0, "K": 0.0, "alpha": 0.02, "gamma": W.GAMMA}
+    fld = {"H0": (20e3, 1e3, 0.0)}
+    mask = W.checkerboard_mask(n, 2)
+    m0 = W.m_uniform_noise(n, direction=(0.0, 1.0, 0.0), noise=0.05, seed=3) * mask
+    s = O.Simulation(mesh, mat, fld, {"method": "RKDP54", "extrap_order": 4, "adaptive": True, "h": 1e-13,
+                                      "tol": 1e-6}, m0)
+    s.run(5e-12)
+    m = s.m()
+    assert np.all(m[:, mask[0] == 0] == 0.0)
+    r = np.linalg.norm(m, axis=0)[mask[0] == 1]
+    assert np.abs(r - 1.0).max() < 1e-12
+    assert np.abs(m - m0).max() > 1e-3
+
+
 def test_adaptive_controller_rejects_and_tracks_tolerance():
     n, d = (8, 8, 1), (4e-9, 4e-9, 4e-9)
     mat = {"Ms": 8e5, "A": 1.3e-11, "K": 0.0, "alpha": 0.02, "gamma": W.GAMMA}
