@@ -138,6 +138,8 @@ struct mmx_ctx {
     void *tw4 = nullptr;  // FP32 split path with a 1024-point axis: four-step twiddles [k2][n1] = w1024^(n1 k2)
     bool r4 = false;      // the 1024-point y passes run as four-step register transforms
     bool r4x = false;     // ... and the 1024-point x passes
+    void *tw512 = nullptr;  // FP32 with a 512-point x axis: four-step twiddles [k2][n1] = w512^(n1 k2), k2 < 16
+    bool r4xh = false;      // the 512-point x-forward pass runs as a four-step register transform
     bool split;  // the y-z column does not fit one CTA: YF, ZM, YI instead of YZ
     int nd;           // kernels per exact demag evaluation
     bool allow_tma;   // TMA passes allowed (the context owns a fault word)

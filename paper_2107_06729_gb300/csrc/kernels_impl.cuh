@@ -43,7 +43,7 @@
 #include "internal.h"
 
 // kernel families, instantiated in separate translation units
-enum MmxKernelKind { K_XF, K_XI, K_YZ, K_YF, K_YI, K_ZM, K_XFP, K_YFP, K_YIP, K_ZMP, K_ZMR, K_XIT, K_YF4, K_YI4, K_XF4, K_XI4 };
+enum MmxKernelKind { K_XF, K_XI, K_YZ, K_YF, K_YI, K_ZM, K_XFP, K_YFP, K_YIP, K_ZMP, K_ZMR, K_XIT, K_YF4, K_YI4, K_XF4, K_XI4, K_XF4H };
 // pointer to the instance of `kind` for precision (f64) and transform length L
 const void *mmxk_kernel(int kind, bool f64, int L);
 
@@ -1755,6 +1755,117 @@ __global__ void __launch_bounds__(32 * XF4_ROWS / 2, 2) k_xf4(const XArgs<T> a)
     }
 }
 
+// XF of a 512-point x axis (nx = 256; the film), four-step 16 x 32: lane n1
+// of the warp holds x[n1 + 32 n2] (n2 < 8 nonzero), transforms over n2 in
+// registers (a 16-point DFT of eight samples), multiplies by w512^(n1 k2)
+// ([k2][n1] table), and one transpose through a 16 x 33 tile hands lane k2
+// (lanes 0-15) all 32 n1 for a 32-point transform: X[k2 + 16 k1] in register
+// k1.  One pair of real rows per warp, 16 rows per CTA (one bulk copy); the
+// spectra, in natural order in pair-row regions 530 words apart (2 mod 16:
+// the 16 rows of kx and kx + 1 in distinct banks), are split and stored
+// transposed as in k_xf4.  On the film's 1536 rows the pass is latency-
+// bound: the shorter dependent chain per warp is what counts.
+constexpr int XF4H_PRS = 530;  // pair-row region stride (complex words)
+constexpr size_t xf4h_smem()
+{
+    return (size_t)(XF4_ROWS / 2) * XF4H_PRS * sizeof(cx<float>) + (size_t)XF4_ROWS * 256 * sizeof(float) + 16;
+}
+// 16-point DFT of a sequence whose upper 8 samples are zero (v[8..15] not read)
+template <typename T, bool INV> __device__ __forceinline__ void dft16_in8(cx<T> *v)
+{
+    const T c1 = (T)0.92387953251128675612818318939678;  // cos(pi/8)
+    const T s1 = (T)0.38268343236508977172845998403040;  // sin(pi/8)
+    const T r = (T)0.70710678118654752440084436210485;   // sqrt(1/2)
+    const T sg = INV ? (T)1 : (T)-1;
+    const cx<T> w[8] = {mk((T)1, (T)0), mk(c1, sg * s1), mk(r, sg * r), mk(s1, sg * c1),
+                        mk((T)0, sg),   mk(-s1, sg * c1), mk(-r, sg * r), mk(-c1, sg * s1)};
+    cx<T> a[8], b[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+        a[n] = v[n];
+        b[n] = n == 0 ? v[0] : cmul(v[n], w[n]);
+    }
+    Dft<T, 8, INV>::run(a);
+    Dft<T, 8, INV>::run(b);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        v[2 * j] = a[j];
+        v[2 * j + 1] = b[j];
+    }
+}
+template <typename T>
+__global__ void __launch_bounds__(32 * XF4_ROWS / 2) k_xf4h(const XArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    if (a.st) {
+        if (a.st->done) return;
+        if (a.stage0 && a.st->f1_valid) return;
+    }
+    constexpr int PX = 512, NX = 256, TR = XF4_ROWS;
+    constexpr unsigned BYTES = (unsigned)TR * NX * sizeof(T);
+    const T *src = a.src_mode == 0 ? a.src : ((a.src_mode == 1 ? a.st->cur : a.st->spec_src) ? a.msrc1 : a.msrc0);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    cx<T> *const regs = reinterpret_cast<cx<T> *>(smraw);
+    cx<T> *reg = regs + w * XF4H_PRS;
+    T *stg = reinterpret_cast<T *>(regs + (TR / 2) * XF4H_PRS);
+    BulkStage bs;
+    bs.init(reinterpret_cast<uint64_t *>(stg + TR * NX));
+    const long long R = a.rows;
+    const int nitems = (int)(R / TR);  // rows % 16 == 0
+    int item = blockIdx.x;
+    if (item < nitems) bs.issue(stg, src + (size_t)item * TR * NX, BYTES);
+    for (; item < nitems; item += gridDim.x) {
+        if (!bs.wait(a.fault, XIT_WAIT_NS)) return;
+        const T *ra = stg + (size_t)(2 * w) * NX, *rb = ra + NX;
+        cx<T> v[32];
+#pragma unroll
+        for (int n = 0; n < 8; ++n) v[n] = mk(ra[lane + 32 * n], rb[lane + 32 * n]);
+        __syncthreads();  // staging consumed: the next item's copy overlaps the rest
+        const int next = item + (int)gridDim.x;
+        if (next < nitems) bs.issue(stg, src + (size_t)next * TR * NX, BYTES);
+        dft16_in8<T, false>(v);
+        // w512^(n1 k2) from the [k2][n1] table
+#pragma unroll
+        for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], a.tw4[32 * k + lane]);
+        // transpose: lane n1 writes row k2; lane k2 (< 16) reads all n1 of it
+#pragma unroll
+        for (int k = 0; k < 16; ++k) reg[k * R4_PITCH + lane] = v[k];
+        __syncwarp();
+        if (lane < 16) {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) v[k] = reg[lane * R4_PITCH + k];
+        }
+        __syncwarp();
+        if (lane < 16) {
+            Dft<T, 32, false>::run(v);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) reg[lane + 16 * k] = v[k];
+        }
+        __syncthreads();
+        // thread (kb, t) stores row t at kx = kb + 16 j, j < 16
+        {
+            const int t = threadIdx.x & (TR - 1), kb = threadIdx.x >> 4;
+            const cx<T> *z = regs + (t >> 1) * XF4H_PRS;
+            const bool odd = t & 1;
+            cx<T> *dst = a.S + (size_t)kb * R + (size_t)item * TR + t;
+            const T hlf = (T)0.5;
+#pragma unroll 8
+            for (int j = 0; j < NX / 16; ++j) {
+                const int kx = kb + 16 * j;
+                const cx<T> zk = z[kx];
+                const cx<T> zm = z[kx == 0 ? NX : PX - kx];
+                cx<T> o;
+                if (kx == 0)  // DC and Nyquist of both rows
+                    o = odd ? mk(zk.y, zm.y) : mk(zk.x, zm.x);
+                else
+                    o = odd ? mk(hlf * (zk.y + zm.y), hlf * (zm.x - zk.x)) : mk(hlf * (zk.x + zm.x), hlf * (zk.y - zm.y));
+                dst[(size_t)j * 16 * R] = o;
+            }
+        }
+        __syncthreads();  // the regions are refilled by the next item
+    }
+}
+
 template <typename T, int PZ>
 __global__ void __launch_bounds__(YZ_THREADS, 2) k_zm_p(const SplitArgs<T> a)
 {
@@ -2823,7 +2934,7 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
     xa.self_src = (const T *)self_src;
     xa.S = (cx<T> *)c->S;
     xa.tw = (const cx<T> *)c->twx;
-    xa.tw4 = (const cx<T> *)c->tw4;
+    xa.tw4 = (const cx<T> *)(c->Px == 512 ? c->tw512 : c->tw4);
     xa.st = const_cast<DevState *>(st);
     xa.rows = c->rows;
     xa.n = c->n;
@@ -2914,7 +3025,11 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
                    *f_yi = mmxk_kernel(K_YIP, sizeof(T) == 8, c->Py), *f_zm = mmxk_kernel(K_ZMP, sizeof(T) == 8, c->Pz);
         if (parts & 1)
             timed(0, [&] {
-                if (c->r4x) {
+                if (c->r4xh) {
+                    const void *f4 = mmxk_kernel(K_XF4H, false, 512);
+                    launch_k(c, f4, dim3(persistent_grid(f4, 32 * XF4_ROWS / 2, xf4h_smem(), c->rows / XF4_ROWS)),
+                             dim3(32 * XF4_ROWS / 2), xfa, xf4h_smem(), s);
+                } else if (c->r4x) {
                     const void *f4 = mmxk_kernel(K_XF4, false, c->Px);
                     launch_k(c, f4, dim3(persistent_grid(f4, 32 * XF4_ROWS / 2, xf4_smem(), c->rows / XF4_ROWS)),
                              dim3(32 * XF4_ROWS / 2), xfa, xf4_smem(), s);
@@ -2949,7 +3064,15 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
         return;
     }
     if (parts & 1)
-        timed(0, [&] { launch_k(c, mmxk_kernel(K_XF, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s); });
+        timed(0, [&] {
+            if (c->r4xh && (((uintptr_t)xsrc | (uintptr_t)c->m[1]) & 15) == 0) {
+                const void *f4 = mmxk_kernel(K_XF4H, false, 512);
+                launch_k(c, f4, dim3(persistent_grid(f4, 32 * XF4_ROWS / 2, xf4h_smem(), c->rows / XF4_ROWS)),
+                         dim3(32 * XF4_ROWS / 2), xargs, xf4h_smem(), s);
+            } else {
+                launch_k(c, mmxk_kernel(K_XF, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s);
+            }
+        });
     if (!(parts & 2)) {
     } else if (!c->split) {
         timed(1, [&] { launch_k(c, mmxk_kernel(K_YZ, sizeof(T) == 8, c->Py), dim3(c->nx), dim3(YZ_THREADS), yargs, ys, s); });
@@ -3134,6 +3257,18 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
         c->r4 = c->Py == 1024 && getenv("MMX_NO_R4") == nullptr;
         c->r4x = c->Px == 1024 && getenv("MMX_NO_R4") == nullptr;
         if (c->r4x && !raise_smem_limit(mmxk_kernel(K_XF4, false, 1024), xf4_smem())) return MMX_ERR_CUDA;
+    }
+    c->r4xh = false;
+    if (c->tw512 && sizeof(T) == 4) {
+        // [k2][n1] = w512^(n1 k2), k2 < 16, n1 < 32
+        twiddles<T>(512, tw);
+        std::vector<cx<T>> t4(512);
+        for (int k = 0; k < 16; ++k)
+            for (int n = 0; n < 32; ++n) t4[32 * k + n] = tw[n * k];
+        if (cudaMemcpy(c->tw512, t4.data(), 512 * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess)
+            return MMX_ERR_CUDA;
+        c->r4xh = c->rows % XF4_ROWS == 0 && getenv("MMX_NO_R4") == nullptr;
+        if (c->r4xh && !raise_smem_limit(mmxk_kernel(K_XF4H, false, 512), xf4h_smem())) return MMX_ERR_CUDA;
     }
     c->xi_tma = c->xi_tma_ok = false;
     if (sizeof(T) == 4 && c->allow_tma && c->rows % XIT_ROWS == 0 && mmxk_kernel(K_XIT, false, c->Px) &&
