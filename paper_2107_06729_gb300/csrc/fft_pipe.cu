@@ -14,6 +14,7 @@ const void *mmxk_tab_pipe(int kind, bool f64, int L)
     case K_XF4: return f64 || L != 1024 ? nullptr : (const void *)k_xf4<float>;
     case K_XI4: return f64 || L != 1024 ? nullptr : (const void *)k_xi_t<float, 1024, true>;
     case K_XF4H: return f64 || L != 512 ? nullptr : (const void *)k_xf4h<float>;
+    case K_XI4H: return f64 || L != 512 ? nullptr : (const void *)k_xi_t<float, 512, true>;
     }
     return nullptr;
 }

@@ -43,7 +43,7 @@
 #include "internal.h"
 
 // kernel families, instantiated in separate translation units
-enum MmxKernelKind { K_XF, K_XI, K_YZ, K_YF, K_YI, K_ZM, K_XFP, K_YFP, K_YIP, K_ZMP, K_ZMR, K_XIT, K_YF4, K_YI4, K_XF4, K_XI4, K_XF4H };
+enum MmxKernelKind { K_XF, K_XI, K_YZ, K_YF, K_YI, K_ZM, K_XFP, K_YFP, K_YIP, K_ZMP, K_ZMR, K_XIT, K_YF4, K_YI4, K_XF4, K_XI4, K_XF4H, K_XI4H };
 // pointer to the instance of `kind` for precision (f64) and transform length L
 const void *mmxk_kernel(int kind, bool f64, int L);
 
@@ -955,7 +955,60 @@ __global__ void __launch_bounds__(32 * XIT_ROWS / 2, 3) k_xi_t(const XArgs<T> a,
             pend = true;
         }
         const int w = threadIdx.x >> 5;
-        if constexpr (R4) {
+        if constexpr (R4 && PX == 512) {
+            // four-step 512-point inverse (32 x 16) on pair row w: lane k1
+            // holds Z[k1 + 32 k2] and transforms over k2 (16 points), the
+            // product with w512^(-n1 k1) and one transpose hand lane n1 < 16
+            // all 32 k1, whose transform gives x[n1 + 16 n2], n2 < 16, of
+            // both rows, stored straight from registers
+            static_assert(sizeof(T) == 4, "four-step XI: FP32");
+            if (w < NP) {
+                const int lane = threadIdx.x & 31;
+                const long long ra = (long long)tile * TR + 2 * w;
+                const Pad<T> z = work.at(w * PXS);
+                cx<T> v[32];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) v[k] = z[lane + 32 * k];
+                Dft<T, 16, true>::run(v);
+#pragma unroll
+                for (int k = 1; k < 16; ++k) {
+                    const cx<T> tw = a.tw4[32 * k + lane];
+                    v[k] = cmul(v[k], mk(tw.x, -tw.y));
+                }
+                const int b0 = w * PXS;
+                cx<T> *tl = work.p + b0 + (b0 >> 4);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) tl[k * R4_PITCH + lane] = v[k];
+                __syncwarp();
+                if (lane < 16) {
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) v[k] = tl[lane * R4_PITCH + k];
+                }
+                __syncwarp();
+                if (lane < 16) {
+                    dft32_out16<T, true>(v);
+                    const int lgpl = ilog2(a.plane);
+                    const T msa = (T)a.msN00[(int)(ra >> lgpl)], msb = (T)a.msN00[(int)((ra + 1) >> lgpl)];
+                    T *oa = out + ra * NX, *ob = oa + NX;
+                    if (a.self_src) {
+                        const T *sa = a.self_src + ra * NX, *sb = sa + NX;
+#pragma unroll
+                        for (int n = 0; n < 16; ++n) {
+                            const int x = lane + 16 * n;
+                            oa[x] = v[n].x - msa * __ldg(sa + x);
+                            ob[x] = v[n].y - msb * __ldg(sb + x);
+                        }
+                    } else {
+#pragma unroll
+                        for (int n = 0; n < 16; ++n) {
+                            oa[lane + 16 * n] = v[n].x;
+                            ob[lane + 16 * n] = v[n].y;
+                        }
+                    }
+                }
+            }
+            __syncthreads();  // work is refilled by the next tile
+        } else if constexpr (R4) {
             // four-step 1024-point inverse on pair row w, stored straight from
             // registers: lane n1 ends with x[n1 + 32 n2], n2 < 16, of both rows
             static_assert(PX == 1024 && sizeof(T) == 4, "four-step XI: FP32, 1024 points");
@@ -2979,7 +3032,7 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
     // XI: TMA tiles through a persistent CTA per SM where set up, else plain
     auto launch_xi = [&]() {
         if (c->xi_tma) {
-            const void *f = mmxk_kernel(c->r4x ? K_XI4 : K_XIT, false, c->Px);
+            const void *f = mmxk_kernel(c->r4x ? K_XI4 : (c->r4xih ? K_XI4H : K_XIT), false, c->Px);
             const size_t sm = xit_smem(c);
             void *targs[] = {(void *)&xa, (void *)&c->xi_tmap};
             launch_k(c, f, dim3(persistent_grid(f, 32 * XIT_ROWS / 2, sm, c->rows / XIT_ROWS)), dim3(32 * XIT_ROWS / 2),
@@ -3258,7 +3311,7 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
         c->r4x = c->Px == 1024 && getenv("MMX_NO_R4") == nullptr;
         if (c->r4x && !raise_smem_limit(mmxk_kernel(K_XF4, false, 1024), xf4_smem())) return MMX_ERR_CUDA;
     }
-    c->r4xh = false;
+    c->r4xh = c->r4xih = false;
     if (c->tw512 && sizeof(T) == 4) {
         // [k2][n1] = w512^(n1 k2), k2 < 16, n1 < 32
         twiddles<T>(512, tw);
@@ -3269,12 +3322,14 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
             return MMX_ERR_CUDA;
         c->r4xh = c->rows % XF4_ROWS == 0 && getenv("MMX_NO_R4") == nullptr;
         if (c->r4xh && !raise_smem_limit(mmxk_kernel(K_XF4H, false, 512), xf4h_smem())) return MMX_ERR_CUDA;
+        c->r4xih = getenv("MMX_NO_R4") == nullptr;
     }
     c->xi_tma = c->xi_tma_ok = false;
     if (sizeof(T) == 4 && c->allow_tma && c->rows % XIT_ROWS == 0 && mmxk_kernel(K_XIT, false, c->Px) &&
         xit_smem(c) <= 227 * 1024 && getenv("MMX_NO_TMA") == nullptr) {
         if (encode_xi_tmap(c) && raise_smem_limit(mmxk_kernel(K_XIT, false, c->Px), xit_smem(c)) &&
-            (!c->r4x || raise_smem_limit(mmxk_kernel(K_XI4, false, c->Px), xit_smem(c))))
+            (!c->r4x || raise_smem_limit(mmxk_kernel(K_XI4, false, c->Px), xit_smem(c))) &&
+            (!c->r4xih || raise_smem_limit(mmxk_kernel(K_XI4H, false, c->Px), xit_smem(c))))
             c->xi_tma = c->xi_tma_ok = true;
         cudaGetLastError();
     }
