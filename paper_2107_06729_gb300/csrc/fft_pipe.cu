@@ -13,7 +13,8 @@ const void *mmxk_tab_pipe(int kind, bool f64, int L)
     case K_YI4: return f64 || L != 1024 ? nullptr : (const void *)k_yi4<float>;
     case K_XF4: return f64 || L != 1024 ? nullptr : (const void *)k_xf4<float>;
     case K_XI4: return f64 || L != 1024 ? nullptr : (const void *)k_xi_t<float, 1024, true>;
-    case K_XF4H: return f64 || L != 512 ? nullptr : (const void *)k_xf4h<float>;
+    // K_XF4H: L = rows per item (16 or 8) of the 512-point pass
+    case K_XF4H: return f64 ? nullptr : (L == 16 ? (const void *)k_xf4h<float, 16> : (L == 8 ? (const void *)k_xf4h<float, 8> : nullptr));
     case K_XI4H: return f64 || L != 512 ? nullptr : (const void *)k_xi_t<float, 512, true>;
     }
     return nullptr;

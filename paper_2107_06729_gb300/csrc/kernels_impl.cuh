@@ -1818,10 +1818,14 @@ __global__ void __launch_bounds__(32 * XF4_ROWS / 2, 2) k_xf4(const XArgs<T> a)
 // the 16 rows of kx and kx + 1 in distinct banks), are split and stored
 // transposed as in k_xf4.  On the film's 1536 rows the pass is latency-
 // bound: the shorter dependent chain per warp is what counts.
-constexpr int XF4H_PRS = 530;  // pair-row region stride (complex words)
-constexpr size_t xf4h_smem()
+// Items of TR = 16 rows (eight warps), or 8 (four warps) where 16-row items
+// would leave SMs idle (the film: 96 items).  Pair-row regions are PRS words
+// apart: 530 (2 mod 16) for 16 rows, 532 (4 mod 16) for 8, so that the rows
+// and the consecutive kx a warp reads in the store loop hit distinct banks.
+template <int TR> __host__ __device__ constexpr int xf4h_prs() { return TR == 16 ? 530 : 532; }
+template <int TR> constexpr size_t xf4h_smem()
 {
-    return (size_t)(XF4_ROWS / 2) * XF4H_PRS * sizeof(cx<float>) + (size_t)XF4_ROWS * 256 * sizeof(float) + 16;
+    return (size_t)(TR / 2) * xf4h_prs<TR>() * sizeof(cx<float>) + (size_t)TR * 256 * sizeof(float) + 16;
 }
 // 16-point DFT of a sequence whose upper 8 samples are zero (v[8..15] not read)
 template <typename T, bool INV> __device__ __forceinline__ void dft16_in8(cx<T> *v)
@@ -1846,15 +1850,15 @@ template <typename T, bool INV> __device__ __forceinline__ void dft16_in8(cx<T> 
         v[2 * j + 1] = b[j];
     }
 }
-template <typename T>
-__global__ void __launch_bounds__(32 * XF4_ROWS / 2) k_xf4h(const XArgs<T> a)
+template <typename T, int TR>
+__global__ void __launch_bounds__(32 * TR / 2) k_xf4h(const XArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     if (a.st) {
         if (a.st->done) return;
         if (a.stage0 && a.st->f1_valid) return;
     }
-    constexpr int PX = 512, NX = 256, TR = XF4_ROWS;
+    constexpr int PX = 512, NX = 256, XF4H_PRS = xf4h_prs<TR>();
     constexpr unsigned BYTES = (unsigned)TR * NX * sizeof(T);
     const T *src = a.src_mode == 0 ? a.src : ((a.src_mode == 1 ? a.st->cur : a.st->spec_src) ? a.msrc1 : a.msrc0);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1895,16 +1899,17 @@ __global__ void __launch_bounds__(32 * XF4_ROWS / 2) k_xf4h(const XArgs<T> a)
             for (int k = 0; k < 32; ++k) reg[lane + 16 * k] = v[k];
         }
         __syncthreads();
-        // thread (kb, t) stores row t at kx = kb + 16 j, j < 16
+        // thread (kb, t) stores row t at kx = kb + KB j (KB = 256 / TR kx per pass)
         {
-            const int t = threadIdx.x & (TR - 1), kb = threadIdx.x >> 4;
+            constexpr int KB = 32 * TR / 2 / TR, LGTR = TR == 16 ? 4 : 3;
+            const int t = threadIdx.x & (TR - 1), kb = threadIdx.x >> LGTR;
             const cx<T> *z = regs + (t >> 1) * XF4H_PRS;
             const bool odd = t & 1;
             cx<T> *dst = a.S + (size_t)kb * R + (size_t)item * TR + t;
             const T hlf = (T)0.5;
 #pragma unroll 8
-            for (int j = 0; j < NX / 16; ++j) {
-                const int kx = kb + 16 * j;
+            for (int j = 0; j < NX / KB; ++j) {
+                const int kx = kb + KB * j;
                 const cx<T> zk = z[kx];
                 const cx<T> zm = z[kx == 0 ? NX : PX - kx];
                 cx<T> o;
@@ -1912,12 +1917,15 @@ __global__ void __launch_bounds__(32 * XF4_ROWS / 2) k_xf4h(const XArgs<T> a)
                     o = odd ? mk(zk.y, zm.y) : mk(zk.x, zm.x);
                 else
                     o = odd ? mk(hlf * (zk.y + zm.y), hlf * (zm.x - zk.x)) : mk(hlf * (zk.x + zm.x), hlf * (zk.y - zm.y));
-                dst[(size_t)j * 16 * R] = o;
+                dst[(size_t)j * KB * R] = o;
             }
         }
         __syncthreads();  // the regions are refilled by the next item
     }
 }
+// rows per item of the 512-point four-step XF: 16 unless that leaves fewer
+// than two items per SM
+inline int xf4h_rows(const mmx_ctx *c) { return (c->rows / 16 >= 2 * 152) ? 16 : 8; }
 
 template <typename T, int PZ>
 __global__ void __launch_bounds__(YZ_THREADS, 2) k_zm_p(const SplitArgs<T> a)
@@ -3079,9 +3087,10 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
         if (parts & 1)
             timed(0, [&] {
                 if (c->r4xh) {
-                    const void *f4 = mmxk_kernel(K_XF4H, false, 512);
-                    launch_k(c, f4, dim3(persistent_grid(f4, 32 * XF4_ROWS / 2, xf4h_smem(), c->rows / XF4_ROWS)),
-                             dim3(32 * XF4_ROWS / 2), xfa, xf4h_smem(), s);
+                    const int tr = xf4h_rows(c);
+                    const size_t sm = tr == 16 ? xf4h_smem<16>() : xf4h_smem<8>();
+                    const void *f4 = mmxk_kernel(K_XF4H, false, tr);
+                    launch_k(c, f4, dim3(persistent_grid(f4, 16 * tr, sm, c->rows / tr)), dim3(16 * tr), xfa, sm, s);
                 } else if (c->r4x) {
                     const void *f4 = mmxk_kernel(K_XF4, false, c->Px);
                     launch_k(c, f4, dim3(persistent_grid(f4, 32 * XF4_ROWS / 2, xf4_smem(), c->rows / XF4_ROWS)),
@@ -3119,9 +3128,10 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
     if (parts & 1)
         timed(0, [&] {
             if (c->r4xh && (((uintptr_t)xsrc | (uintptr_t)c->m[1]) & 15) == 0) {
-                const void *f4 = mmxk_kernel(K_XF4H, false, 512);
-                launch_k(c, f4, dim3(persistent_grid(f4, 32 * XF4_ROWS / 2, xf4h_smem(), c->rows / XF4_ROWS)),
-                         dim3(32 * XF4_ROWS / 2), xargs, xf4h_smem(), s);
+                const int tr = xf4h_rows(c);
+                const size_t sm = tr == 16 ? xf4h_smem<16>() : xf4h_smem<8>();
+                const void *f4 = mmxk_kernel(K_XF4H, false, tr);
+                launch_k(c, f4, dim3(persistent_grid(f4, 16 * tr, sm, c->rows / tr)), dim3(16 * tr), xargs, sm, s);
             } else {
                 launch_k(c, mmxk_kernel(K_XF, sizeof(T) == 8, c->Px), dim3(xgrid), dim3(xt), xargs, xs, s);
             }
@@ -3320,8 +3330,10 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
             for (int n = 0; n < 32; ++n) t4[32 * k + n] = tw[n * k];
         if (cudaMemcpy(c->tw512, t4.data(), 512 * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess)
             return MMX_ERR_CUDA;
-        c->r4xh = c->rows % XF4_ROWS == 0 && getenv("MMX_NO_R4") == nullptr;
-        if (c->r4xh && !raise_smem_limit(mmxk_kernel(K_XF4H, false, 512), xf4h_smem())) return MMX_ERR_CUDA;
+        c->r4xh = c->rows % 16 == 0 && getenv("MMX_NO_R4") == nullptr;
+        if (c->r4xh && (!raise_smem_limit(mmxk_kernel(K_XF4H, false, 16), xf4h_smem<16>()) ||
+                        !raise_smem_limit(mmxk_kernel(K_XF4H, false, 8), xf4h_smem<8>())))
+            return MMX_ERR_CUDA;
         c->r4xih = getenv("MMX_NO_R4") == nullptr;
     }
     c->xi_tma = c->xi_tma_ok = false;
