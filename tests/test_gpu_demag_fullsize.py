@@ -51,14 +51,15 @@ def _dense_case(n, d, prec, seed):
 FILM = ((256, 128, 4), (2.5e-9, 2.5e-9, 1e-9))
 
 
-@pytest.mark.parametrize("env", [{}, {"MMX_AUTOTUNE": "0"}, {"MMX_NO_TMA": "1"}])
+@pytest.mark.parametrize("env", [{}, {"MMX_AUTOTUNE": "0"}, {"MMX_NO_TMA": "1"}, {"MMX_NO_R4": "1"}])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_film_256x128x4_matches_oracle(prec, env, monkeypatch):
-    """The bench's film: FP32 runs k_xf<float,512>, k_yz<float,256> and the
-    tensor-copy k_xi_t<float,512> (plain k_xi<float,512> with MMX_NO_TMA);
-    FP64 runs the CTA-wide 512-point x transforms and k_yz<double,256>."""
-    if prec == "fp64" and env.get("MMX_NO_TMA"):
-        pytest.skip("FP64 has no tensor-copy pass")
+    """The bench's film: FP32 runs the four-step k_xf4h<float,8>, k_yz<float,256>
+    and the tensor-copy four-step k_xi_t<float,512,true> (plain k_xi<float,512>
+    with MMX_NO_TMA; the Stockham k_xf<float,512> and k_xi_t<float,512> with
+    MMX_NO_R4); FP64 runs the CTA-wide 512-point x transforms and k_yz<double,256>."""
+    if prec == "fp64" and (env.get("MMX_NO_TMA") or env.get("MMX_NO_R4")):
+        pytest.skip("FP64 has neither the tensor-copy nor the four-step passes")
     for k, v in env.items():
         monkeypatch.setenv(k, v)
     n, d = FILM
@@ -77,10 +78,14 @@ LONG_CASES = [
     (((8, 512, 2), (2e-9, 2e-9, 2e-9)), {}),
     # y padded to 512 in FP64: fused k_yz<double,512> with CTA-wide stages
     (((8, 256, 2), (1e-9, 2e-9, 3e-9)), {}),
-    # pipelined split passes, forced: k_xf_p<float,1024>, k_yf_p / k_yi_p <float,64>, k_xi_t<float,1024>
+    # split passes, forced: four-step k_xf4 / k_xi_t<float,1024,true>, k_yf_p / k_yi_p <float,64>
     (((512, 32, 2), (2e-9, 2e-9, 2e-9)), {"MMX_FORCE_SPLIT": "1"}),
-    # pipelined split passes, forced: k_yf_p / k_yi_p <float,1024>, k_zm_r<float,4>
+    # ... and the Stockham k_xf_p<float,1024>, k_xi_t<float,1024> instead
+    (((512, 32, 2), (2e-9, 2e-9, 2e-9)), {"MMX_FORCE_SPLIT": "1", "MMX_NO_R4": "1"}),
+    # split passes, forced: four-step k_yf4 / k_yi4, k_zm_r<float,4>
     (((32, 512, 2), (2e-9, 2e-9, 2e-9)), {"MMX_FORCE_SPLIT": "1"}),
+    # ... and the Stockham k_yf_p / k_yi_p <float,1024> instead
+    (((32, 512, 2), (2e-9, 2e-9, 2e-9)), {"MMX_FORCE_SPLIT": "1", "MMX_NO_R4": "1"}),
     # the box's z length: k_zm_r<float,32> / k_zm<double,32> behind the split passes
     (((32, 32, 16), (2e-9, 2e-9, 2e-9)), {"MMX_FORCE_SPLIT": "1"}),
 ]
@@ -90,8 +95,8 @@ LONG_CASES = [
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_long_transforms_match_oracle(case, env, prec, monkeypatch):
     n, d = case
-    if prec == "fp64" and env.get("MMX_NO_TMA"):
-        pytest.skip("FP64 has no tensor-copy pass")
+    if prec == "fp64" and (env.get("MMX_NO_TMA") or env.get("MMX_NO_R4")):
+        pytest.skip("FP64 has neither the tensor-copy nor the four-step passes")
     for k, v in env.items():
         monkeypatch.setenv(k, v)
     assert _dense_case(n, d, prec, seed=sum(n) + 5) < TOL[prec]
