@@ -9,7 +9,10 @@
  *     text of the last error of a context is available from mmx_last_error.
  *   - Magnetisation arrays hold unit vectors m = M/Ms in SoA layout
  *     [3][nz][ny][nx] (x fastest), element type double for MMX_FP64 and float
- *     for MMX_FP32_MIXED.  Fields are in A/m, lengths in m, times in s.
+ *     for MMX_FP32_MIXED.  A cell whose m is exactly (0, 0, 0) holds no
+ *     material (vacuum, e.g. between the particles of an array, Sec. III):
+ *     it adds nothing to the demag field, feels no torque and stays 0.
+ *     Fields are in A/m, lengths in m, times in s.
  *   - Every pointer passed in stays owned by the caller.  The library owns the
  *     device buffers it allocates in mmx_create (spectra, stage buffers,
  *     history of exact demag fields) and frees them in mmx_destroy.
