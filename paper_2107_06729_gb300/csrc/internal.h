@@ -141,6 +141,7 @@ struct mmx_ctx {
     void *tw512 = nullptr;  // FP32 with a 512-point x axis: four-step twiddles [k2][n1] = w512^(n1 k2), k2 < 16
     bool r4xh = false;      // the 512-point x-forward pass runs as a four-step register transform
     bool r4xih = false;     // ... and the 512-point x-inverse pass
+    void *tw4y = nullptr;   // FP32 fused y-z pass with Py = 256: four-step twiddles [k2][n1] = w256^(n1 k2)
     bool split;  // the y-z column does not fit one CTA: YF, ZM, YI instead of YZ
     int nd;           // kernels per exact demag evaluation
     bool allow_tma;   // TMA passes allowed (the context owns a fault word)

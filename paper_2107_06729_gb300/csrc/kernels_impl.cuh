@@ -1068,10 +1068,73 @@ __global__ void __launch_bounds__(32 * XIT_ROWS / 2, 3) k_xi_t(const XArgs<T> a,
 }
 
 // ---------------------------------------------------------------------- YZ
+// ---- four-step y transforms of 256 points inside the fused y-z pass (FP32)
+// 256 = 8 x 32, four rows per warp.  Forward: lane n1 holds x[n1 + 32 n2]
+// (n2 < 4 nonzero: the padded row), an 8-point DFT over n2, the product with
+// w256^(n1 k2) ([k2][n1] table), a transpose through the warp's tile
+// [row][k2][n1] (33-word rows), and lane (row, k2) takes the 32-point DFT
+// over n1: X[k2 + 8 k1].  Inverse: lane k1 holds X[k1 + 32 k2], an inverse
+// 8-point DFT over k2, w256^(-n1 k1), the transpose, and lane (row, n1) the
+// inverse 32-point DFT over k1 of which the first 16 outputs are the rows'
+// samples x[n1 + 8 n2], n2 < 16 (the truncated half).  The rows live in the
+// pass's padded shared-memory view; every lane reads all its inputs before
+// the warp writes any result, so the rows are transformed in place.
+constexpr int Y4_TILE = 4 * 8 * R4_PITCH;  // complex words per warp
+template <typename T, bool INV>
+__device__ __forceinline__ void yz_y4_rows(const Pad<T> B, int plane, int lgnz, int r0, int nrows,
+                                           const cx<T> *__restrict__ tw4, cx<T> *tile)
+{
+    constexpr int PY = 256;
+    const int lane = threadIdx.x & 31;
+    auto row = [&](int r) { return B.at((r >> lgnz) * plane + (r & ((1 << lgnz) - 1)) * PY); };
+    // step 1, each of the (up to) four rows in turn
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (r0 + q >= nrows) break;
+        const Pad<T> x = row(r0 + q);
+        cx<T> v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = (INV || k < 4) ? x[lane + 32 * k] : mk<T>(0, 0);
+        Dft<T, 8, INV>::run(v);
+#pragma unroll
+        for (int k = 1; k < 8; ++k) {
+            cx<T> w = tw4[32 * k + lane];
+            if (INV) w.y = -w.y;
+            v[k] = cmul(v[k], w);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) tile[(q * 8 + k) * R4_PITCH + lane] = v[k];
+    }
+    __syncwarp();
+    // step 2: lane (row q, index k) over the 32 entries of tile row (q, k)
+    const int q = lane >> 3, k = lane & 7;
+    const bool act = r0 + q < nrows;
+    cx<T> v[32];
+    if (act) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = tile[(q * 8 + k) * R4_PITCH + j];
+    }
+    __syncwarp();
+    if (act) {
+        const Pad<T> x = row(r0 + q);
+        if constexpr (!INV) {
+            Dft<T, 32, false>::run(v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) x[k + 8 * j] = v[j];
+        } else {
+            dft32_out16<T, true>(v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) x[k + 8 * j] = v[j];
+        }
+    }
+    __syncwarp();
+}
+
 template <typename T> struct YZArgs {
     cx<T> *S;
     const T *K;  // [(kx*Hz + kz)*Hy + ky][6]
     const cx<T> *twy, *twz;
+    const cx<T> *tw4y;  // FP32, Py = 256: four-step twiddles [k2][n1] = w256^(n1 k2), k2 < 8 (else null)
     DevState *st;
     long long rows;
     int nx, ny, nz, Py, Pz, Hy, Hz, stage0;
@@ -1126,7 +1189,13 @@ __global__ void __launch_bounds__(YZ_THREADS, 2) k_yz(const YZArgs<T> a)
     const FftShape fy{Py, 3 * nz, lgnz, plane, Py, 1};
     // Pz <= reg_max_len<T>() here: taller columns take the split passes
     const int nwarp = blockDim.x >> 5, warp = threadIdx.x >> 5;
-    if constexpr (PY > 1) {
+    constexpr bool Y4 = sizeof(T) == 4 && PY == 256;
+    cx<T> *y4tile = reinterpret_cast<cx<T> *>(smraw) + padded_words((size_t)3 * plane) + warp * Y4_TILE;
+    if (Y4 && a.tw4y) {
+        for (int r0 = 4 * warp; r0 < 3 * nz; r0 += 4 * nwarp)
+            yz_y4_rows<T, false>(B, plane, lgnz, r0, 3 * nz, a.tw4y, y4tile);
+        __syncthreads();
+    } else if constexpr (PY > 1) {
         if constexpr (PY <= warp_max_len<T>()) {
             for (int tr = warp; tr < 3 * nz; tr += nwarp)
                 WarpFFT<T, false, PY, 1>::run(B.at((tr >> lgnz) * plane + (tr & (nz - 1)) * PY), 1, a.twy, true,
@@ -1195,7 +1264,11 @@ __global__ void __launch_bounds__(YZ_THREADS, 2) k_yz(const YZArgs<T> a)
             col_fft_any<T, true>(B, Pz, (tr >> lgPy) * plane + (tr & (Py - 1)), Py, a.twz);
         __syncthreads();
     }
-    if constexpr (PY > 1) {
+    if (Y4 && a.tw4y) {
+        for (int r0 = 4 * warp; r0 < 3 * nz; r0 += 4 * nwarp)
+            yz_y4_rows<T, true>(B, plane, lgnz, r0, 3 * nz, a.tw4y, y4tile);
+        __syncthreads();
+    } else if constexpr (PY > 1) {
         if constexpr (PY <= warp_max_len<T>()) {
             for (int tr = warp; tr < 3 * nz; tr += nwarp)
                 WarpFFT<T, true, PY, 1>::run(B.at((tr >> lgnz) * plane + (tr & (nz - 1)) * PY), 1, a.twy, false,
@@ -2743,6 +2816,13 @@ template <typename T> size_t x_smem(const mmx_ctx *c, int trows)
     return padded_words((size_t)((trows + 1) / 2) * (2 * c->nx + XPAIR_GAP)) * sizeof(cx<T>);
 }
 template <typename T> size_t yz_smem(const mmx_ctx *c) { return padded_words((size_t)3 * c->Py * c->Pz) * sizeof(cx<T>); }
+// launch size of the fused y-z pass: the spectrum, plus the four-step y
+// transforms' transpose tiles (one per warp that takes four of the 3 nz rows)
+template <typename T> size_t yz_launch_smem(const mmx_ctx *c)
+{
+    const int nw = std::min(YZ_THREADS / 32, (3 * c->nz + 3) / 4);
+    return yz_smem<T>(c) + (c->tw4y && sizeof(T) == 4 ? (size_t)nw * Y4_TILE * sizeof(cx<T>) : 0);
+}
 
 // split path: rows per YF/YI CTA (about 32 KB of shared memory), ky tile of ZM
 template <typename T> int split_rows(const mmx_ctx *c)
@@ -3026,7 +3106,8 @@ void demag_t(mmx_ctx *c, cudaStream_t s, const DevState *st, int stage0, int src
     ya.Hy = c->Hy;
     ya.Hz = c->Hz;
     ya.stage0 = stage0;
-    const size_t ys = yz_smem<T>(c);
+    ya.tw4y = sizeof(T) == 4 ? (const cx<T> *)c->tw4y : nullptr;
+    const size_t ys = yz_launch_smem<T>(c);
 
     const bool prof = c->profiling;
     auto timed = [&](int cls, auto launch) {
@@ -3321,6 +3402,15 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
         c->r4x = c->Px == 1024 && getenv("MMX_NO_R4") == nullptr;
         if (c->r4x && !raise_smem_limit(mmxk_kernel(K_XF4, false, 1024), xf4_smem())) return MMX_ERR_CUDA;
     }
+    if (c->tw4y && sizeof(T) == 4) {
+        // [k2][n1] = w256^(n1 k2), k2 < 8, n1 < 32
+        twiddles<T>(256, tw);
+        std::vector<cx<T>> t4(256);
+        for (int k = 0; k < 8; ++k)
+            for (int n = 0; n < 32; ++n) t4[32 * k + n] = tw[n * k];
+        if (cudaMemcpy(c->tw4y, t4.data(), 256 * sizeof(cx<T>), cudaMemcpyHostToDevice) != cudaSuccess)
+            return MMX_ERR_CUDA;
+    }
     c->r4xh = c->r4xih = false;
     if (c->tw512 && sizeof(T) == 4) {
         // [k2][n1] = w512^(n1 k2), k2 < 16, n1 < 32
@@ -3346,7 +3436,7 @@ template <typename T> int setup_t(mmx_ctx *c, const double *Kspec)
         cudaGetLastError();
     }
     const int trows = c->trows ? c->trows : pick_trows(c);
-    const size_t xs = x_smem<T>(c, trows), ys = yz_smem<T>(c);
+    const size_t xs = x_smem<T>(c, trows), ys = yz_launch_smem<T>(c);
     const void *xk[] = {mmxk_kernel(K_XF, sizeof(T) == 8, c->Px), mmxk_kernel(K_XI, sizeof(T) == 8, c->Px)};
     if (xs > 48 * 1024)
         for (const void *f : xk)

@@ -816,6 +816,8 @@ int mmx_create(const mmx_mesh *mesh, const mmx_material *mat, const mmx_field *f
     if (c->prec == MMX_FP32_MIXED && c->split && (c->Px == 1024 || c->Py == 1024))
         ok = ok && alloc(&c->tw4, (size_t)1024 * 2 * c->esz);
     if (c->prec == MMX_FP32_MIXED && c->Px == 512) ok = ok && alloc(&c->tw512, (size_t)512 * 2 * c->esz);
+    if (c->prec == MMX_FP32_MIXED && !c->split && c->Py == 256 && getenv("MMX_NO_R4") == nullptr)
+        ok = ok && alloc(&c->tw4y, (size_t)256 * 2 * c->esz);
     ok = ok && alloc((void **)&c->st, sizeof(DevState));
     ok = ok && cudaMallocHost((void **)&c->h_st, sizeof(DevState)) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
@@ -1118,7 +1120,7 @@ void mmx_destroy(mmx_ctx *c)
     for (int i = 0; i < 2; ++i)
         for (cudaEvent_t e : c->pev[i]) cudaEventDestroy(e);
     void *bufs[] = {c->m[0], c->m[1], c->mlo, c->errpart, c->Y[0], c->Y[1], c->F, c->G, c->hist, c->S, c->K, c->twx, c->twy, c->twz, c->Tb,
-                    c->tw4, c->tw512, c->st};
+                    c->tw4, c->tw512, c->tw4y, c->st};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->h_st) cudaFreeHost(c->h_st);
