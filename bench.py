@@ -80,41 +80,72 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, period_ms=50):
         self.index = index
-        self.rows = []
+        self.period_ms = period_ms
+        self.rows = []  # (arrival time, fields)
         self.proc = None
+        self.window = None
 
-    def start(self):
+    def start(self, wait_s=5.0):
+        """Start nvidia-smi and wait (bounded) for its first row, so that the
+        sampler is already live when the timed region begins."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.period_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t_end = time.monotonic() + wait_s
+            while not self.rows and time.monotonic() < t_end and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.monotonic(), [x.strip() for x in line.split(",")]))
+
+    def begin(self):
+        self.window = [time.monotonic(), None]
+
+    def end(self):
+        if self.window:
+            self.window[1] = time.monotonic()
 
     def stop(self):
         if self.proc:
+            # one more period so that a sample taken at the end of the window arrives
+            time.sleep(self.period_ms / 1e3)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.rows)}
-        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        rows = list(self.rows)
+        inside = rows
+        if self.window and self.window[1] is not None:
+            t0, t1 = self.window[0], self.window[1] + self.period_ms / 1e3
+            inside = [r for r in rows if t0 <= r[0] <= t1]
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(inside),
+               "period_ms": self.period_ms}
+        if not inside and rows:
+            # region shorter than one sampling period: the samples on either side of it
+            t0 = self.window[0] if self.window else rows[0][0]
+            before = [r for r in rows if r[0] < t0][-1:]
+            after = [r for r in rows if r[0] >= t0][:1]
+            inside = before + after
+            out["samples"] = 0
+            out["adjacent_samples"] = len(inside)
+        fields = [r[1] for r in inside]
+        sm = [float(r[1]) for r in fields if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in fields if len(r) > 2 and r[2].replace(".", "").isdigit()]
         if sm:
             out["sm_mhz"] = statistics.median(sm)
         if mx:
             out["sm_max_mhz"] = max(mx)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        for r in fields:
             for i, nm in enumerate(names):
                 if len(r) > 5 + i and r[5 + i].lower() == "active" and nm not in out["reasons"]:
                     out["reasons"].append(nm)
@@ -878,6 +909,7 @@ def run_mmx(args):
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
+        sampler.begin()
         for i in range(args.steps):
             flush.fill_(float(i))
             evs[i][0].record(stream)
@@ -885,6 +917,7 @@ def run_mmx(args):
             ctx.run(t)
             evs[i][1].record(stream)
         torch.cuda.synchronize(dev)
+        sampler.end()
         if world > 1:
             dist.barrier()
         clocks = sampler.stop()

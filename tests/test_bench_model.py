@@ -95,3 +95,26 @@ def test_eps_time_is_eq7_over_time_samples():
     a, b = rng.normal(size=(3, 40)), rng.normal(size=(3, 40))
     assert bench.eps_time(a, b) == pytest.approx(O.epsilon_time(a, b), rel=1e-14)
     assert bench.eps_time(a, a) == 0.0
+
+
+def _row(sm, max_sm=2070, reasons=("Not Active",) * 4):
+    return ["0", str(sm), str(max_sm), "900.0", "0x0"] + list(reasons)
+
+
+def test_clock_sampler_keeps_the_timed_window():
+    s = bench.ClockSampler(0, period_ms=50)
+    s.rows = [(0.90, _row(1000)), (1.00, _row(2070)), (1.05, _row(2055)), (1.10, _row(2070)),
+              (1.40, _row(1200, reasons=("Active", "Active", "Not Active", "Not Active")))]
+    s.window = [0.99, 1.12]
+    out = s.stop()
+    assert out["samples"] == 3 and out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == []                     # the throttled sample lies outside the window
+
+
+def test_clock_sampler_region_shorter_than_a_period():
+    s = bench.ClockSampler(0, period_ms=200)
+    s.rows = [(1.00, _row(2070)), (1.60, _row(2040, reasons=("Not Active",) * 3 + ("Active",)))]
+    s.window = [1.05, 1.10]
+    out = s.stop()
+    assert out["samples"] == 0 and out["adjacent_samples"] == 2
+    assert out["sm_mhz"] == 2055.0 and out["reasons"] == ["sw_power_cap"]
