@@ -168,7 +168,12 @@ int mmx_load_state(mmx_ctx *ctx, const void *buf, size_t len);
  * multiply, 2: x-inverse FFT, 3: LLG stage, 4: last stage (Eq. 3 solution
  * and error norm), 5: controller (Eq. 5 and the next attempt's
  * coefficients)), the summed milliseconds and the number of launches.  ms
- * and launches point to arrays of MMX_NPROF. */
+ * and launches point to arrays of MMX_NPROF.  enable: 0 off, 1 an event
+ * pair around every launch, 2 the same except that the stage kernels of an
+ * extrapolated attempt (every stage but the last; no demag pass runs between
+ * them) share one pair, so that class 3 then times them back to back without
+ * event-record nodes between them and counts every launch of the run; any
+ * other value is MMX_ERR_ARG.  Switching the mode clears the sums. */
 #define MMX_NPROF 6
 int mmx_set_profiling(mmx_ctx *ctx, int enable);
 int mmx_get_profile(mmx_ctx *ctx, double *ms, long long *launches);

@@ -213,7 +213,7 @@ def mmx_load_state(ctx, blob):
 
 
 def mmx_set_profiling(ctx, enable):
-    return _check(lib().mmx_set_profiling(ctx, int(bool(enable))), ctx)
+    return _check(lib().mmx_set_profiling(ctx, int(enable)), ctx)
 
 
 def mmx_get_profile(ctx):

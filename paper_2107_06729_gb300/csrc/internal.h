@@ -166,12 +166,17 @@ struct mmx_ctx {
     // loop kind) and read the pairs after each launch, so that the times are
     // those of kernels running back to back on the device.
     bool profiling;
+    // mode 2: the stage kernels of an extrapolated attempt that run back to
+    // back (every stage but the last, no demag pass between them) share one
+    // event pair, which then counts all of their launches
+    bool prof_group = false;
     double prof_ms[MMX_NPROF];
     long long prof_n[MMX_NPROF];
     cudaEvent_t ev_a, ev_b;
     int prof_cap = -1;                 // loop kind whose profiled graph is being captured, else -1
     std::vector<cudaEvent_t> pev[2];   // event pairs of the profiled graphs
     std::vector<int> pcls[2];          // profile class of each pair
+    std::vector<int> pcnt[2];          // launches each pair spans
     cudaGraphExec_t pgexec[2];
     cudaGraph_t pgraph[2];
     bool pgraph_ok[2] = {false, false};
@@ -183,7 +188,7 @@ struct mmx_ctx {
 // mmx_api.cu: profiling event pairs (see mmx_ctx::prof_cap) and dropping
 // the captured graphs (after the stage sequence changed, and at destroy)
 void mmx_prof_begin(mmx_ctx *c, cudaStream_t s);
-void mmx_prof_end(mmx_ctx *c, cudaStream_t s, int cls);
+void mmx_prof_end(mmx_ctx *c, cudaStream_t s, int cls, int count = 1);
 void mmx_drop_graphs(mmx_ctx *c);
 // synchronises the context and applies f to its device state (read, edit,
 // write back); a copy of the state for reading only

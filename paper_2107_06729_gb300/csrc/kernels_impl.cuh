@@ -3313,11 +3313,15 @@ void stage_t(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime, cudaGraph
     a.zguard = tb.abm ? 1 : 0;
     const void *fn = mmxk_stage_kernel(sizeof(T) == 8, nf, nh, last, k == 0);
     const int grid = (int)((c->n + ST_THREADS - 1) / ST_THREADS);
-    if (c->profiling) mmx_prof_begin(c, s);
+    // grouped profiling: stages 0 .. S-2 of an extrapolated attempt without
+    // the learned residual follow each other with no other launch between
+    // them and share one event pair
+    const bool grp = c->profiling && c->prof_group && extrap && !c->rnet && !last;
+    if (c->profiling && (!grp || k == 0)) mmx_prof_begin(c, s);
     void *sargs[] = {(void *)&a};
     launch_k(c, fn, dim3(grid), dim3(ST_THREADS), sargs, 0, s);
     c->launches++;
-    if (c->profiling) mmx_prof_end(c, s, last ? 4 : 3);
+    if (c->profiling && (!grp || k == S - 2)) mmx_prof_end(c, s, last ? 4 : 3, grp ? S - 1 : 1);
 }
 
 // The controller kernel that ends an attempt (after the last stage).

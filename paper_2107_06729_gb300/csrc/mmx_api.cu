@@ -380,6 +380,7 @@ int build_prof_graph(mmx_ctx *c, int which)
     if (c->pgraph_ok[which]) return 0;
     const long long launches = c->launches;
     c->pcls[which].clear();
+    c->pcnt[which].clear();
     c->prof_cap = which;
     cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
@@ -428,7 +429,7 @@ int run_loop(mmx_ctx *c, int which)
                 float ms = 0.f;
                 CK(cudaEventElapsedTime(&ms, c->pev[which][2 * i], c->pev[which][2 * i + 1]));
                 c->prof_ms[cls[i]] += ms;
-                c->prof_n[cls[i]]++;
+                c->prof_n[cls[i]] += c->pcnt[which][i];
             }
             rc = read_state(c);
             if (rc) return rc;
@@ -633,7 +634,7 @@ void mmx_prof_begin(mmx_ctx *c, cudaStream_t s)
     cudaEventRecord(c->ev_a, s);
 }
 
-void mmx_prof_end(mmx_ctx *c, cudaStream_t s, int cls)
+void mmx_prof_end(mmx_ctx *c, cudaStream_t s, int cls, int count)
 {
     if (c->prof_cap >= 0) {
         const int w = c->prof_cap;
@@ -641,6 +642,7 @@ void mmx_prof_end(mmx_ctx *c, cudaStream_t s, int cls)
         if (c->pev[w].size() < 2 * i + 2) return;  // no event could be made: this launch is not timed
         cudaEventRecordWithFlags(c->pev[w][2 * i + 1], s, cudaEventRecordExternal);
         c->pcls[w].push_back(cls);
+        c->pcnt[w].push_back(count);
         return;
     }
     cudaEventRecord(c->ev_b, s);
@@ -648,7 +650,7 @@ void mmx_prof_end(mmx_ctx *c, cudaStream_t s, int cls)
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev_a, c->ev_b);
     c->prof_ms[cls] += ms;
-    c->prof_n[cls]++;
+    c->prof_n[cls] += count;
 }
 
 int mmx_state_edit(mmx_ctx *c, const std::function<void(DevState &)> &f)
@@ -1075,7 +1077,18 @@ int mmx_load_state(mmx_ctx *c, const void *buf, size_t len)
 
 int mmx_set_profiling(mmx_ctx *c, int enable)
 {
-    if (!c) return MMX_ERR_ARG;
+    if (!c || enable < 0 || enable > 2) return MMX_ERR_ARG;
+    const bool group = enable == 2;
+    if (group != c->prof_group) {
+        // the profiled attempt graphs hold the other mode's event pairs
+        for (int i = 0; i < 2; ++i)
+            if (c->pgraph_ok[i]) {
+                cudaGraphExecDestroy(c->pgexec[i]);
+                cudaGraphDestroy(c->pgraph[i]);
+                c->pgraph_ok[i] = false;
+            }
+        c->prof_group = group;
+    }
     c->profiling = enable != 0;
     for (int i = 0; i < MMX_NPROF; ++i) {
         c->prof_ms[i] = 0;

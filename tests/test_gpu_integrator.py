@@ -94,6 +94,42 @@ def test_checkpoint_resume_is_bitwise(method, p):
         c.close()
 
 
+def test_profiling_modes_time_every_launch_and_leave_the_run_unchanged():
+    """Per-launch (1) and grouped (2) profiling count the same launches per
+    kernel class (grouped: one event pair over stages 0 .. S-2 of each
+    extrapolated attempt, counting all of them), and neither changes the
+    trajectory of a run without profiling (0)."""
+    torch = torch_cuda()
+    import paper_2107_06729_gb300 as pkg
+    n, d = (32, 16, 4), (2.5e-9, 2.5e-9, 1e-9)
+    integ = {"method": "RKDP54", "extrap_order": 4, "adaptive": True, "h": 1e-13, "tol": 1e-5}
+    m0 = torch.from_numpy(W.m_uniform_noise(n, seed=4, noise=0.2)).to("cuda", torch.float32)
+    res = {}
+    for mode in (0, 1, 2):
+        ctx = gpu_context({"n": n, "d": d}, MAT, FLD, integ, "fp32")
+        ctx.set_m(m0)
+        ctx.run(1e-12)  # primes the history
+        ctx.set_profiling(mode)
+        ctx.run(3e-12)
+        prof = ctx.profile()
+        out = torch.empty_like(m0)
+        ctx.get_m(out)
+        with pytest.raises(pkg.MMXError) as ei:
+            ctx.set_profiling(3)
+        assert ei.value.code == pkg.MMX_ERR_ARG
+        res[mode] = (out, prof, ctx.stats())
+        ctx.close()
+    assert torch.equal(res[1][0], res[0][0]) and torch.equal(res[2][0], res[0][0])
+    assert res[1][2]["accepted"] == res[2][2]["accepted"] == res[0][2]["accepted"]
+    p1, p2 = res[1][1], res[2][1]
+    assert all(v[1] == 0 for v in res[0][1].values())
+    for k in p1:
+        assert p2[k][1] == p1[k][1], k
+    # DP54: six stage kernels before the last one in every attempt
+    assert p1["llg_stage"][1] > 0 and p1["llg_stage"][1] % 6 == 0 and p2["llg_stage"][0] > 0
+    assert p1["llg_last_stage"][1] == p2["llg_last_stage"][1] == p1["llg_stage"][1] // 6
+
+
 def test_nonfinite_input_is_reported():
     torch = torch_cuda()
     import paper_2107_06729_gb300 as pkg
