@@ -42,9 +42,10 @@ L2_FLUSH_BYTES = 512 << 20
 # and pass; an entry is dropped whenever its kernel changes.
 NCU_TRAFFIC = {
     ("film_256x128x4_dp54_p4_fp32", "yz_fft_tensor_multiply"): 7198464 + 0,  # k_yz<float, 256>
-    # mean over the six stage kernels of one attempt (k_stage<0,1,0,1> .. <4,5,0,0>)
-    ("film_256x128x4_dp54_p4_fp32", "llg_stage"): 13380000 + 0,
-    ("film_256x128x4_dp54_p4_fp32", "llg_last_stage"): 20467712 + 0,  # k_stage<5,5,1,0>
+    # mean over the six stage kernels of one attempt (k_stage<0,1,0,1> .. <4,5,0,0>;
+    # stage 6 also writes the new state: DP54 is FSAL)
+    ("film_256x128x4_dp54_p4_fp32", "llg_stage"): 13646421 + 0,
+    ("film_256x128x4_dp54_p4_fp32", "llg_last_stage"): 17323264 + 0,  # k_stage<5,5,1,0>
 }
 
 
@@ -165,15 +166,18 @@ def stage_bytes(n, esz, p):
     DP54 attempt (u = 3 components x esz per cell): stage 0 reads m0 (its
     field input and the base of Eq. 4) and the exact non-self field, stage
     k >= 1 reads Y_k, the p + 1 history fields of Eq. 6, the F_l it needs and
-    m0; each writes F_k and Y_{k+1}; the last stage reads Y_7, the history,
-    its F_l and m0 and writes F_7 and the new m, and in FP32 also reads and
-    writes the low words of the compensated state (one u each).  Neighbour
+    m0; each writes F_k and Y_{k+1}.  DP54 is FSAL (Y_7 is the Eq. 3
+    solution), so stage 5 also writes the new m and, in FP32, reads and
+    writes the low words of the compensated state (one u each); the last
+    stage then reads Y_7, the history and its F_l and writes F_7.  Neighbour
     values of the exchange stencil are the same cells' data (cache hits), not
     extra bytes.  Returns (mean bytes of a non-last stage launch, bytes of
     the last)."""
     u = 3 * esz * n
+    lo = 2 if esz == 4 else 0
     stages = [4 * u] + [(1 + (p + 1) + len(DP54_B_READ[k]) + 1 + 2) * u for k in range(1, 6)]
-    last = (1 + (p + 1) + len(DP54_LAST_READ) + 1 + 2 + (2 if esz == 4 else 0)) * u
+    stages[5] += (1 + lo) * u
+    last = (1 + (p + 1) + len(DP54_LAST_READ) + 1) * u
     return sum(stages) / len(stages), last
 
 

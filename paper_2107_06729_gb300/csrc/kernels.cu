@@ -34,6 +34,16 @@ const void *mmxk_kernel(int kind, bool f64, int L)
 }
 
 
+bool mmxk_fsal_solution(const mmx_ctx *c)
+{
+    const TabArgs &t = c->tab;
+    const int S = t.s;
+    if (t.abm || !t.fsal || S < 2 || t.c[S - 1] != 0.0) return false;
+    for (int l = 0; l < S - 1; ++l)
+        if (t.b[S - 1][l] != t.c[l]) return false;
+    return true;
+}
+
 void mmxk_prepare(mmx_ctx *c, cudaStream_t s)
 {
     k_prepare<<<1, 256, 0, s>>>(c->st, c->tab, c->ph, c->ctl.p);

@@ -2231,6 +2231,8 @@ template <typename T> struct StageArgs {
     int fstatic;    // the stage-derivative ring never rotates (fbase = 0): slot addresses are static
     int ns;         // stage-derivative slots
     int zguard;     // a read slot may hold nothing valid (ABM2's F_{n-1}): zero coefficients drop it
+    int sol;        // FSAL tableau (its last Eq. 4 row equals the Eq. 3 weights): stage S-2 writes the new
+                    // state from Y_S, and the last stage (sol set too) only adds F_S and the error norm
     int fl[MMX_MAXS];  // indices l of the stage derivatives this stage reads (the template's NF of them)
 };
 
@@ -2533,6 +2535,50 @@ template <typename T> __device__ __forceinline__ T coef_H(const StageCoef &C, in
 }
 
 
+// The Eq. 3 solution m0 + inc as the new state (buffer `nb` of m and, in
+// FP32, of the low words), renormalised; returns |m0 + inc| (0: a cell
+// without material, which stays 0).  In FP32 the state is a compensated pair
+// (hi, lo): the increment is added to hi exactly (TwoSum) with the rounding
+// carried in lo, so that the per-step rounding of m does not accumulate over
+// a trajectory; (hi + lo) / r is formed as a pair: hi' = hi inv rounded, its
+// exact error by an FMA, lo' = that error + lo inv, renormalised (Fast2Sum);
+// a rounded inv only rescales the three components alike.
+template <typename T>
+__device__ __forceinline__ T put_state(const StageArgs<T> &a, int nb, int n, int i, const T mv[3], const T lv[3],
+                                       const T inc[3])
+{
+    T M[3], lo[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if constexpr (sizeof(T) == 4) {
+            float e;
+            two_sum(mv[c], inc[c], M[c], e);
+            lo[c] = lv[c] + e;
+        } else {
+            M[c] = mv[c] + inc[c];
+            lo[c] = (T)0;
+        }
+    }
+    const T r = sqrt(M[0] * M[0] + M[1] * M[1] + M[2] * M[2]);
+    T *mo = nb ? a.m1 : a.m0;
+    if constexpr (sizeof(T) == 4) {
+        const float inv = r == 0.0f ? 0.0f : 1.0f / r;
+        T *ml = a.mlo + (size_t)nb * 3 * n;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float q = __fmul_rn(M[c], inv);
+            const float l = __fmaf_rn(lo[c], inv, __fmaf_rn(M[c], inv, -q));
+            const float h = __fadd_rn(q, l);
+            mo[(size_t)c * n + i] = h;
+            ml[(size_t)c * n + i] = __fsub_rn(l, __fsub_rn(h, q));
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) mo[(size_t)c * n + i] = r == (T)0 ? (T)0 : M[c] / r;
+    }
+    return r;
+}
+
 // One RK stage k (Eq. 4), or with LAST the Eq. 3 solution, the embedded
 // error and its per-CTA maximum, for one cell per thread.  Reads: Y_k and its
 // six neighbours (x neighbours from the adjacent lanes), NH demag sources
@@ -2635,11 +2681,15 @@ __global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
     }
     // m0 (its buffer is the state's cur) and, in FP32, the compensated state's low words
     const T *m0p = sv.y ? a.m1 : a.m0;
+    // (the last stage of an FSAL tableau whose solution stage S-2 already
+    // wrote needs neither; stage S-2 then reads the low words)
+    const bool need_m0 = !(LAST && a.sol);
+    const bool need_lo = sizeof(T) == 4 && (LAST ? !a.sol : a.sol != 0);
     T mv[3], lv[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        mv[c] = STAGE0 ? c0[c] : m0p[(size_t)c * n + ic];
-        lv[c] = (LAST && sizeof(T) == 4) ? a.mlo[(size_t)sv.y * fs + (size_t)c * n + ic] : (T)0;
+        mv[c] = STAGE0 ? c0[c] : (need_m0 ? m0p[(size_t)c * n + ic] : (T)0);
+        lv[c] = need_lo ? a.mlo[(size_t)sv.y * fs + (size_t)c * n + ic] : (T)0;
     }
     T Fk0[3] = {(T)0, (T)0, (T)0};
     const bool f1v = STAGE0 && C.state[4] != 0;  // F_1 of this t0 is already in its slot
@@ -2701,28 +2751,23 @@ __global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
         if (valid) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) a.Yout[(size_t)c * n + i] = mv[c] + inc[c];
+            // FSAL: Y_S = m0 + h sum_l c_l F_l is the Eq. 3 solution; the new
+            // state is written here so that the next attempt's demag passes
+            // can transform it while the last stage runs
+            if (a.sol) put_state<T>(a, sv.y ^ 1, n, i, mv, lv, inc);
         }
+        // the buffer the new m goes to (state outside the head)
+        if (a.sol && blockIdx.x == 0 && threadIdx.x == 0) st->spec_src = sv.y ^ 1;
         return;
     }
-    // Eq. 3: solution, embedded difference, renormalisation.  In FP32 the
-    // state m is a compensated pair (hi, lo): the increment is added to hi
-    // exactly (TwoSum) with the rounding carried in lo, so that the per-step
-    // rounding of m does not accumulate over a trajectory.  The embedded
-    // difference E = h sum_l (c_l - c^_l) F_l is formed as sum_l ce_l (F_l -
-    // F_ref) + (sum_l ce_l) F_ref: the weights of an embedded pair sum to
-    // zero, so the large common part of the F_l cancels exactly in the
+    // Eq. 3: solution (put_state), embedded difference, renormalisation.  The
+    // embedded difference E = h sum_l (c_l - c^_l) F_l is formed as sum_l
+    // ce_l (F_l - F_ref) + (sum_l ce_l) F_ref: the weights of an embedded pair
+    // sum to zero, so the large common part of the F_l cancels exactly in the
     // differences instead of in the rounded sum.
-    T M[3], E[3], lo[3];
+    T E[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        if constexpr (sizeof(T) == 4) {
-            float e;
-            two_sum(mv[c], inc[c], M[c], e);
-            lo[c] = lv[c] + e;
-        } else {
-            M[c] = mv[c] + inc[c];
-            lo[c] = (T)0;
-        }
         const T ref = NF > 0 ? Fv[0][c] : f[c];
         T acc = s_cesum * ref + s_ce[NF] * (f[c] - ref);
 #pragma unroll
@@ -2732,35 +2777,18 @@ __global__ void __launch_bounds__(ST_THREADS, 8) k_stage(const StageArgs<T> a)
     }
     // the buffer the new m goes to: the next attempt's speculative demag
     // passes transform it while the controller decides (state outside the head)
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->spec_src = sv.y ^ 1;
+    if (!a.sol && blockIdx.x == 0 && threadIdx.x == 0) st->spec_src = sv.y ^ 1;
     T err = (T)0;
     if (valid) {
-        const T r = sqrt(M[0] * M[0] + M[1] * M[1] + M[2] * M[2]);
+        // with sol the new state came from Y_S (this stage's input c0) in stage S-2
+        const T r = a.sol ? sqrt(c0[0] * c0[0] + c0[1] * c0[1] + c0[2] * c0[2])
+                          : put_state<T>(a, sv.y ^ 1, n, i, mv, lv, inc);
         err = sqrt(E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
         // a cell without material (m = 0: no torque, so every stage derivative
         // and the new state stay exactly 0) stays 0; any other zero or
         // non-finite state rejects the attempt
         const bool empty = r == (T)0 && err == (T)0;
         if (!(err <= (T)3.0e38) || !(r == r) || (r == (T)0 && !empty)) err = (T)INFINITY;
-        T *mo = sv.y ? a.m0 : a.m1;
-        if constexpr (sizeof(T) == 4) {
-            // (hi + lo) / r as a pair: hi' = hi inv rounded, its exact error by an
-            // FMA, lo' = that error + lo inv, renormalised (Fast2Sum); a rounded
-            // inv only rescales the three components alike
-            const float inv = empty ? 0.0f : 1.0f / r;
-            T *ml = a.mlo + (size_t)(sv.y ^ 1) * fs;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float q = __fmul_rn(M[c], inv);
-                const float l = __fmaf_rn(lo[c], inv, __fmaf_rn(M[c], inv, -q));
-                const float h = __fadd_rn(q, l);
-                mo[(size_t)c * n + i] = h;
-                ml[(size_t)c * n + i] = __fsub_rn(l, __fsub_rn(h, q));
-            }
-        } else {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) mo[(size_t)c * n + i] = empty ? (T)0 : M[c] / r;
-        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
@@ -3311,6 +3339,7 @@ void stage_t(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime, cudaGraph
     a.fstatic = (c->ctl.p >= 0 && !tb.abm) ? 1 : 0;
     a.ns = c->ctl.nslots;
     a.zguard = tb.abm ? 1 : 0;
+    a.sol = (mmxk_fsal_solution(c) && (last || k == S - 2)) ? 1 : 0;
     const void *fn = mmxk_stage_kernel(sizeof(T) == 8, nf, nh, last, k == 0);
     const int grid = (int)((c->n + ST_THREADS - 1) / ST_THREADS);
     // grouped profiling: stages 0 .. S-2 of an extrapolated attempt without

@@ -203,9 +203,11 @@ void reset_history(DevState *s)
 
 // Extrapolated attempts captured into a graph run speculatively: while the
 // controller decides on an attempt, the x and y-z demag passes of the next
-// attempt already transform the new m on a second stream (a rejected attempt
-// needs no new demag: its exact field and F_1 are kept, and the x-inverse
-// pass of the retry skips).  Such a body starts at the x-inverse pass; the
+// attempt already transform the new m on a second stream (for an FSAL
+// tableau, whose new state stage S-2 writes, already while the last stage
+// runs; a rejected attempt needs no new demag: its exact field and F_1 are
+// kept, and the x-inverse pass of the retry skips).  Such a body starts at
+// the x-inverse pass; the
 // first attempt of a loop gets its x and y-z passes from front_kernels.
 bool speculative(const mmx_ctx *c, int prime) { return c->ctl.p >= 0 && !prime; }
 
@@ -222,11 +224,20 @@ int body_kernels(mmx_ctx *c, cudaStream_t s, int prime, cudaGraphConditionalHand
     const int p = c->ctl.p;
     const int extrap = (p >= 0 && !prime);
     const bool spec = s2 && speculative(c, prime);
+    // an FSAL tableau's stage S-2 writes the new state: the next attempt's x
+    // and y-z passes then start beside the last stage, not after it
+    const bool early = spec && !c->rnet && mmxk_fsal_solution(c);
+    auto fork = [&] {
+        cudaEventRecord(c->ev_fork, s);
+        cudaStreamWaitEvent(s2, c->ev_fork, 0);
+        mmxk_demag_parts(c, s2, c->st, 0, 2, nullptr, 1, c->G, nullptr, 3);
+    };
     if (spec)
         mmxk_demag_parts(c, s, c->st, 1, 1, nullptr, 1, c->G, nullptr, 4);
     else
         mmxk_demag(c, s, c->st, 1, 1, nullptr, p >= 0 ? 1 : 0, c->G, nullptr);
     mmxk_stage(c, s, 0, extrap, prime && p >= 0, cond, use_cond);
+    if (early && c->tab.s == 2) fork();
     for (int k = 1; k < c->tab.s; ++k) {
         if (!extrap) mmxk_demag(c, s, c->st, 0, 0, c->Y[k & 1], 0, c->G, nullptr);
         // learned residual: its kernels leave G = G_ext + Ms r in c->G, which the
@@ -234,15 +245,18 @@ int body_kernels(mmx_ctx *c, cudaStream_t s, int prime, cudaGraphConditionalHand
         const bool res = extrap && c->rnet;
         if (res) c->launches += mmxk_rnet_stage(c->rnet, c, s, k);
         mmxk_stage(c, s, k, res ? 0 : extrap, prime && p >= 0, cond, use_cond);
+        if (early && k == c->tab.s - 2) fork();
     }
     if (!spec) {
         mmxk_control(c, s, prime && p >= 0, cond, use_cond);
         return 0;
     }
-    cudaEventRecord(c->ev_fork, s);
-    cudaStreamWaitEvent(s2, c->ev_fork, 0);
+    if (!early) {
+        cudaEventRecord(c->ev_fork, s);
+        cudaStreamWaitEvent(s2, c->ev_fork, 0);
+    }
     mmxk_control(c, s, 0, cond, use_cond);
-    mmxk_demag_parts(c, s2, c->st, 0, 2, nullptr, 1, c->G, nullptr, 3);
+    if (!early) mmxk_demag_parts(c, s2, c->st, 0, 2, nullptr, 1, c->G, nullptr, 3);
     cudaEventRecord(c->ev_join, s2);
     cudaStreamWaitEvent(s, c->ev_join, 0);
     return 0;

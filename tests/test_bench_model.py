@@ -33,15 +33,21 @@ def test_stage_model_per_cell_dp54_p4():
     """DP54 with 4th-order extrapolation in FP32 (u = 12 B/cell): stage 1
     reads m0 and the exact field and writes F_1 and Y_2 (4u = 48 B); stages
     2..6 read Y_k, five history fields, the F_l with nonzero b and m0 and
-    write two fields: 120, 132, 144, 156, 156 B (b72 = 0); the last stage
-    reads Y_7, the history, F_l for l in {1, 3, 4, 5, 6} (c_2 = c_2 - c^_2 =
-    0) and m0 and writes F_7 and m: 168 B, plus the compensated state's low
-    words read and written in FP32: 192 B."""
+    write two fields: 120, 132, 144, 156, 156 B (b72 = 0); DP54 is FSAL, so
+    stage 6 also writes the new m and reads and writes the compensated
+    state's low words in FP32: 156 + 36 = 192 B; the last stage reads Y_7,
+    the history and F_l for l in {1, 3, 4, 5, 6} (c_2 = c_2 - c^_2 = 0) and
+    writes F_7: 144 B."""
     cells = 256 * 128 * 4
     mean, last = bench.stage_bytes(cells, 4, 4)
-    assert mean == pytest.approx((48 + 120 + 132 + 144 + 156 + 156) / 6 * cells)
-    assert last == 192 * cells
-    assert bench.stage_bytes(cells, 8, 4)[1] == 2 * 168 * cells
+    assert mean == pytest.approx((48 + 120 + 132 + 144 + 156 + 192) / 6 * cells)
+    assert last == 144 * cells
+    m8, last8 = bench.stage_bytes(cells, 8, 4)
+    assert last8 == 2 * 144 * cells and m8 == pytest.approx(2 * (48 + 120 + 132 + 144 + 156 + 168) / 6 * cells)
+    # FSAL: the last Eq. 4 row equals the Eq. 3 weights and c_7 = 0
+    import oracle as O
+    t = O.tableau("RKDP54")
+    assert list(t["b"][6][:6]) == list(t["c"][:6]) and t["c"][6] == 0.0
     # the read pattern is the tableau's nonzero pattern (oracle's copy of the
     # published coefficients)
     import oracle as O
