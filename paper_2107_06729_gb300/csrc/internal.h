@@ -190,10 +190,10 @@ struct mmx_ctx {
 void mmx_prof_begin(mmx_ctx *c, cudaStream_t s);
 void mmx_prof_end(mmx_ctx *c, cudaStream_t s, int cls, int count = 1);
 void mmx_drop_graphs(mmx_ctx *c);
-// kernels.cu: an FSAL tableau whose input of the last stage, Y_S, is the
-// Eq. 3 solution (last Eq. 4 row equal to the solution weights, c_S = 0):
-// stage S-2 then writes the new state
-bool mmxk_fsal_solution(const mmx_ctx *c);
+// kernels.cu: stage S-2 writes the new state (and the speculative demag
+// passes fork after it): an FSAL tableau, whose last-stage input Y_S is the
+// Eq. 3 solution, on a mesh with the fused y-z pass
+bool mmxk_early_solution(const mmx_ctx *c);
 // synchronises the context and applies f to its device state (read, edit,
 // write back); a copy of the state for reading only
 #include <functional>

@@ -34,11 +34,16 @@ const void *mmxk_kernel(int kind, bool f64, int L)
 }
 
 
-bool mmxk_fsal_solution(const mmx_ctx *c)
+bool mmxk_early_solution(const mmx_ctx *c)
 {
+    // FSAL: the last Eq. 4 row equals the Eq. 3 weights and c_S = 0.  Only
+    // where the passes are latency-bound (the fused y-z pass: the column fits
+    // one CTA): on meshes with the split passes the stage kernels and the
+    // passes are HBM-bound, and running the passes beside the last stage
+    // measured slower (512 x 512 x 16, RK23 p = 2: 0.645 -> 0.682 ms per step)
     const TabArgs &t = c->tab;
     const int S = t.s;
-    if (t.abm || !t.fsal || S < 2 || t.c[S - 1] != 0.0) return false;
+    if (c->split || t.abm || !t.fsal || S < 2 || t.c[S - 1] != 0.0) return false;
     for (int l = 0; l < S - 1; ++l)
         if (t.b[S - 1][l] != t.c[l]) return false;
     return true;

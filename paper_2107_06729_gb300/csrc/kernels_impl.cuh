@@ -2231,8 +2231,9 @@ template <typename T> struct StageArgs {
     int fstatic;    // the stage-derivative ring never rotates (fbase = 0): slot addresses are static
     int ns;         // stage-derivative slots
     int zguard;     // a read slot may hold nothing valid (ABM2's F_{n-1}): zero coefficients drop it
-    int sol;        // FSAL tableau (its last Eq. 4 row equals the Eq. 3 weights): stage S-2 writes the new
-                    // state from Y_S, and the last stage (sol set too) only adds F_S and the error norm
+    int sol;        // FSAL tableau (its last Eq. 4 row equals the Eq. 3 weights) on a fused-pass mesh: stage
+                    // S-2 writes the new state from Y_S, and the last stage (sol set too) only adds F_S and
+                    // the error norm
     int fl[MMX_MAXS];  // indices l of the stage derivatives this stage reads (the template's NF of them)
 };
 
@@ -3339,7 +3340,7 @@ void stage_t(mmx_ctx *c, cudaStream_t s, int k, int extrap, int prime, cudaGraph
     a.fstatic = (c->ctl.p >= 0 && !tb.abm) ? 1 : 0;
     a.ns = c->ctl.nslots;
     a.zguard = tb.abm ? 1 : 0;
-    a.sol = (mmxk_fsal_solution(c) && (last || k == S - 2)) ? 1 : 0;
+    a.sol = (mmxk_early_solution(c) && (last || k == S - 2)) ? 1 : 0;
     const void *fn = mmxk_stage_kernel(sizeof(T) == 8, nf, nh, last, k == 0);
     const int grid = (int)((c->n + ST_THREADS - 1) / ST_THREADS);
     // grouped profiling: stages 0 .. S-2 of an extrapolated attempt without

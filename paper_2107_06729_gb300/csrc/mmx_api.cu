@@ -204,9 +204,9 @@ void reset_history(DevState *s)
 // Extrapolated attempts captured into a graph run speculatively: while the
 // controller decides on an attempt, the x and y-z demag passes of the next
 // attempt already transform the new m on a second stream (for an FSAL
-// tableau, whose new state stage S-2 writes, already while the last stage
-// runs; a rejected attempt needs no new demag: its exact field and F_1 are
-// kept, and the x-inverse pass of the retry skips).  Such a body starts at
+// tableau on a fused-pass mesh, whose new state stage S-2 writes, already
+// while the last stage runs; a rejected attempt needs no new demag: its exact
+// field and F_1 are kept, and the x-inverse pass of the retry skips).  Such a body starts at
 // the x-inverse pass; the
 // first attempt of a loop gets its x and y-z passes from front_kernels.
 bool speculative(const mmx_ctx *c, int prime) { return c->ctl.p >= 0 && !prime; }
@@ -224,9 +224,9 @@ int body_kernels(mmx_ctx *c, cudaStream_t s, int prime, cudaGraphConditionalHand
     const int p = c->ctl.p;
     const int extrap = (p >= 0 && !prime);
     const bool spec = s2 && speculative(c, prime);
-    // an FSAL tableau's stage S-2 writes the new state: the next attempt's x
-    // and y-z passes then start beside the last stage, not after it
-    const bool early = spec && !c->rnet && mmxk_fsal_solution(c);
+    // stage S-2 writes the new state (FSAL tableau, fused y-z pass): the next
+    // attempt's x and y-z passes then start beside the last stage, not after it
+    const bool early = spec && !c->rnet && mmxk_early_solution(c);
     auto fork = [&] {
         cudaEventRecord(c->ev_fork, s);
         cudaStreamWaitEvent(s2, c->ev_fork, 0);
