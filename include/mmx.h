@@ -165,9 +165,10 @@ int mmx_load_state(mmx_ctx *ctx, const void *buf, size_t len);
  * the kernels themselves run back to back as in the step loop), and
  * mmx_demag records and synchronises an event pair around each pass.
  * mmx_get_profile returns, per class (0: x-forward FFT, 1: yz FFT + tensor
- * multiply, 2: x-inverse FFT, 3: LLG stage, 4: last stage (Eq. 3 solution
- * and error norm), 5: controller (Eq. 5 and the next attempt's
- * coefficients)), the summed milliseconds and the number of launches.  ms
+ * multiply, 2: x-inverse FFT, 3: LLG stage, 4: last stage (error norm, and
+ * the Eq. 3 solution unless stage S-2 of an FSAL tableau formed it), 5:
+ * controller (Eq. 5 and the next attempt's coefficients)), the summed
+ * milliseconds and the number of launches.  ms
  * and launches point to arrays of MMX_NPROF.  enable: 0 off, 1 an event
  * pair around every launch, 2 the same except that the stage kernels of an
  * extrapolated attempt (every stage but the last; no demag pass runs between

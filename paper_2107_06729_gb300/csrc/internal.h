@@ -31,7 +31,7 @@ struct StageCoef {
 };
 
 // Integrator state kept in device memory; kernels read it at launch and the
-// controller (last block of the last stage) updates it.  Everything the host
+// controller kernel that ends each attempt updates it.  Everything the host
 // needs to resume a run lives here.
 struct DevState {
     double t;        // start time t0 of the current attempt
@@ -67,7 +67,7 @@ struct DevState {
     unsigned long long t_start_ns, time_limit_ns;
     StageCoef coef[MMX_MAXS];  // everything before coef is the "head" the controller copies
     // outside the head (the controller never writes these back):
-    int spec_src;  // m buffer the last stage wrote (the speculative demag passes read it)
+    int spec_src;  // m buffer the attempt's new state went to (the speculative demag passes read it)
     int fault;     // a bounded device wait gave up (the context is unusable); sticky
     int pad_[2];
 };

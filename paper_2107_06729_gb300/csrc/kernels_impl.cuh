@@ -25,8 +25,9 @@
 // field (6-point exchange Laplacian with free boundaries, uniaxial
 // anisotropy, Zeeman, demag exact or extrapolated by Eq. 6 minus the exact
 // self term), the Landau-Lifshitz torque, and the next stage input.  The
-// last stage forms the propagated and embedded solutions, renormalises,
-// reduces the error norm, and its last CTA runs the controller of Eq. 5.
+// last stage forms the embedded difference and the per-CTA maximum of its
+// norm, and the renormalised solution unless stage S-2 of an FSAL tableau
+// already wrote it; a one-CTA controller kernel then runs Eq. 5.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -571,7 +572,7 @@ __device__ __forceinline__ void col_fft_any(const Pad<T> buf, int L, int base, i
 // ------------------------------------------------------------------ XF / XI
 template <typename T> struct XArgs {
     const T *src;        // src_mode 0
-    const T *msrc0, *msrc1;  // src_mode 1: m[cur]; 2: m[spec_src] (the last stage's new m)
+    const T *msrc0, *msrc1;  // src_mode 1: m[cur]; 2: m[spec_src] (the attempt's new m)
     T *dst;              // dst_mode 0
     T *hist;             // dst_mode 1: hist + head * 3n
     const T *self_src;   // optional: subtract Ms N00 self_src

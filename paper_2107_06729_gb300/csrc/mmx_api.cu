@@ -2,9 +2,9 @@
 //
 // The integration loop runs on the device: one CUDA graph holds a
 // conditional WHILE node whose body is one attempted step (Eq. 3-4 stages,
-// demag FFTs where the schedule needs them); the controller of Eq. 5 in the
-// last stage kernel decides acceptance, the next step and whether the loop
-// continues.  A second graph with full demag at every stage primes the
+// demag FFTs where the schedule needs them); the controller kernel of Eq. 5
+// that ends each attempt decides acceptance, the next step and whether the
+// loop continues.  A second graph with full demag at every stage primes the
 // extrapolation history (the first p steps, Sec. II after Eq. 6).
 #include <cuda_runtime.h>
 
