@@ -98,6 +98,8 @@ def test_stage_counts_match_paper():
     assert O.tableau("RK4")["s"] == g["RK4"]
     T = O.tableau("RK23")  # 4 stages, FSAL: 3 new evaluations per step
     assert T["fsal"] and T["s"] - 1 == g["RK23"]
+    # FSAL: the last stage's input is the solution (last row = solution weights, c_s = 0)
+    assert np.allclose(T["b"][-1, :-1], T["c"][:-1]) and T["c"][-1] == 0
     assert O.tableau("RKF56")["s"] == g["RKF56"]
     D = O.tableau("RKDP54")
     assert D["fsal"] and np.allclose(D["b"][-1, :-1], D["c"][:-1]) and D["c"][-1] == 0
